@@ -1,0 +1,268 @@
+"""Oracle: the ROK4E Rosenbrock-Krylov integrator (Sec. 4, Algorithm 1), FP64.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the library imports this module.
+
+The integrator follows Algorithm 1 step by step:
+
+1. Arnoldi on K_M(J_n, f_n) gives Q_n (N x m) and H_n (m x m), m <= M
+   (Sec. 4.1).  Modified Gram-Schmidt with one full reorthogonalisation
+   pass; breakdown when the orthogonalised vector has lost all but 1e-12 of
+   the norm of J q_j, which leaves an invariant subspace of dimension m.
+2. For each stage i the transformed stage equation (Eq. s_stage_row_transformed)
+   is solved with the low-rank inverse of Eq. solve_kry_jac:
+     F_i = f(u_n + h sum_j alpha_ij k_j) + sum_j (gamma_ij/gamma) k_j
+     k_i = F_i - Q (I - (I - h gamma H)^-1) Q^T F_i - sum_j (gamma_ij/gamma) k_j
+   Stages 3 and 4 share the argument of f (alpha_4j = alpha_3j, alpha_43 = 0),
+   so f is evaluated 3 times per attempt, the first being f_n itself.
+3. u* = u_n + h sum b_j k_j, u^ = u_n + h sum bhat_j k_j, the normalised
+   error, the PI controller of Sec. 4.3 and accept/reject.
+
+Readings of the text (where it is silent or garbled):
+* Table coeff_rok4e prints two rows labelled b_2 and bhat_2; the values are
+  b = (b1, b2, b3, b4) with b3 = 0 (the text states b3 = 0) and
+  bhat = (bhat1, bhat2, bhat3, bhat4) with bhat4 = 0.  Only this reading
+  satisfies the order conditions (tests pin it).
+* Eq. s_stage_row lacks the factor h in front of A_n sum gamma_ij k_j; the
+  transformed form and Algorithm 1 imply it.
+* err = sqrt(mean(((u^ - u*) / (atol + rtol |u*|))^2)) (RMS norm).
+* PI control h* = h min(5, max(0.2, 0.8 err_n^beta / err*^alpha)),
+  alpha = 0.7/4, beta = 0.4/4, err_n = error of the last accepted step
+  (1 before the first), both errors floored at 1e-10; a non-finite error
+  rejects with factor 0.2.
+* h starts at h0 (default t_end), is clipped to t_end - t, and the
+  integration ends when t_end - t <= 1e-12 t_end.  A rejected step reuses
+  Q_n, H_n and f_n, which depend on u_n only.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+GAMMA = 0.572816062482135
+# gamma_ij (i > j), zero-based stage indices
+GAMMA_IJ = np.array([
+    [0.0, 0.0, 0.0, 0.0],
+    [-0.602765307997356, 0.0, 0.0, 0.0],
+    [-1.389195789724843, 1.072950969011413, 0.0, 0.0],
+    [0.992356412977094, -1.390032613873701, -0.440875890223325, 0.0],
+])
+ALPHA_IJ = np.array([
+    [0.0, 0.0, 0.0, 0.0],
+    [0.432364435748567, 0.0, 0.0, 0.0],
+    [-0.514211316876170, 1.382271144617360, 0.0, 0.0],
+    [-0.514211316876170, 1.382271144617360, 0.0, 0.0],
+])
+B = np.array([0.194335256262729, 0.483167813989227, 0.0, 0.322496929748044])
+BHAT = np.array([-0.217819895945721, 1.03130847478467, 0.186511421161047, 0.0])
+ORDER = 4
+PI_ALPHA = 0.7 / ORDER
+PI_BETA = 0.4 / ORDER
+FAC_MIN, FAC_MAX, SAFETY = 0.2, 5.0, 0.8
+ERR_FLOOR = 1e-10
+BREAKDOWN_TOL = 1e-12
+T_END_TOL = 1e-12
+
+STATUS_OK, STATUS_MAX_ATTEMPTS, STATUS_NONFINITE, STATUS_STEP_UNDERFLOW = 0, 1, 2, 3
+
+
+def arnoldi(jv, f, M):
+    """Orthonormal Q (N x m) and Hessenberg H (m x m) with H = Q^T J Q on K_M(J, f)."""
+    N = f.shape[0]
+    M = min(M, N)
+    beta = np.linalg.norm(f)
+    if M == 0 or beta == 0.0 or not np.isfinite(beta):
+        return np.zeros((N, 0)), np.zeros((0, 0))
+    Q = np.zeros((N, M))
+    H = np.zeros((M, M))
+    Q[:, 0] = f / beta
+    m = M
+    for j in range(M):
+        w = jv(Q[:, j])
+        w0 = np.linalg.norm(w)
+        for _pass in range(2):
+            for i in range(j + 1):
+                hij = Q[:, i] @ w
+                H[i, j] += hij
+                w = w - hij * Q[:, i]
+        hn = np.linalg.norm(w)
+        if j + 1 == M:
+            break
+        if hn <= BREAKDOWN_TOL * w0 or hn == 0.0:
+            m = j + 1
+            break
+        H[j + 1, j] = hn
+        Q[:, j + 1] = w / hn
+    return Q[:, :m], H[:m, :m]
+
+
+def attempt(f, u, fn, Q, H, h):
+    """One ROK4E attempt of size h from u with f(u) = fn.  Returns (u*, u^, n_f)."""
+    m = Q.shape[1]
+    L = np.eye(m) - h * GAMMA * H
+    ks = []
+    n_f = 0
+    f_prev_arg = None
+    f_prev_val = None
+    for i in range(4):
+        arg = u + h * sum((ALPHA_IJ[i, j] * ks[j] for j in range(i)), np.zeros_like(u))
+        if i == 0:
+            fi = fn
+        elif f_prev_arg is not None and np.array_equal(arg, f_prev_arg):
+            fi = f_prev_val  # stage 4 shares stage 3's argument (alpha_4j = alpha_3j)
+        else:
+            fi = f(arg)
+            n_f += 1
+        f_prev_arg, f_prev_val = arg, fi
+        G = sum((GAMMA_IJ[i, j] / GAMMA * ks[j] for j in range(i)), np.zeros_like(u))
+        F = fi + G
+        if m > 0:
+            z = Q.T @ F
+            y = np.linalg.solve(L, z)
+            k = F - Q @ (z - y) - G
+        else:
+            k = F - G
+        ks.append(k)
+    u_star = u + h * sum(B[j] * ks[j] for j in range(4))
+    u_hat = u + h * sum(BHAT[j] * ks[j] for j in range(4))
+    return u_star, u_hat, n_f
+
+
+def error_norm(u_star, u_hat, rtol, atol):
+    sc = atol + rtol * np.abs(u_star)
+    return float(np.sqrt(np.mean(((u_hat - u_star) / sc) ** 2)))
+
+
+def pi_factor(err, err_prev):
+    if not np.isfinite(err):
+        return FAC_MIN
+    e = max(err, ERR_FLOOR)
+    return min(FAC_MAX, max(FAC_MIN, SAFETY * err_prev**PI_BETA / e**PI_ALPHA))
+
+
+def integrate(f, jv_at, u0, t_end, rtol, atol, M, *, h0=None, max_attempts=100000,
+              replay=None, fixed_h=None, record=False):
+    """Algorithm 1 over [0, t_end] from u0.
+
+    f(u)          right-hand side (constant splitting source already included)
+    jv_at(u)      returns a function v -> J(u) v (analytic or finite difference)
+    replay        optional sequence of (h, accepted) attempts to follow instead of
+                  the controller's own decisions (the error is still computed)
+    fixed_h       fixed step size, no error control (all steps accepted)
+    Returns (u, info) with info: h_last, n_accept, n_reject, n_f, n_jv, status,
+    errs (per attempt) and trace [(h, accepted)] when record or replay.
+    """
+    u = np.array(u0, dtype=float)
+    t = 0.0
+    h = t_end if h0 is None or h0 <= 0 else float(h0)
+    if fixed_h is not None:
+        h = float(fixed_h)
+    err_prev = 1.0
+    info = dict(n_accept=0, n_reject=0, n_f=0, n_jv=0, status=STATUS_OK, errs=[], trace=[])
+    fn = f(u)
+    info["n_f"] += 1
+    jv = jv_at(u)
+    Q, H = arnoldi(jv, fn, M)
+    info["n_jv"] += Q.shape[1]
+    n_att = 0
+    h_last = h
+    n_fixed = None if fixed_h is None else int(round(t_end / fixed_h))
+    while True:
+        if n_fixed is not None:
+            if info["n_accept"] >= n_fixed:
+                break
+        elif t_end - t <= T_END_TOL * t_end:
+            break
+        if n_att >= max_attempts:
+            info["status"] = STATUS_MAX_ATTEMPTS
+            break
+        if replay is not None:
+            if n_att >= len(replay):
+                break
+            h, acc_forced = replay[n_att]
+        elif n_fixed is None:
+            h = min(h, t_end - t)
+        u_star, u_hat, nf = attempt(f, u, fn, Q, H, h)
+        info["n_f"] += nf
+        n_att += 1
+        err = error_norm(u_star, u_hat, rtol, atol)
+        info["errs"].append(err)
+        if n_fixed is not None:
+            accept = True
+            h_new = h
+        else:
+            h_new = h * pi_factor(err, err_prev)
+            accept = bool(np.isfinite(err) and err <= 1.0)
+            if replay is not None:
+                accept = bool(acc_forced)
+        if record or replay is not None:
+            info["trace"].append((h, accept))
+        if accept:
+            if not np.all(np.isfinite(u_star)):
+                info["status"] = STATUS_NONFINITE
+                break
+            u = u_star
+            t += h
+            if n_fixed is None:
+                err_prev = max(err, ERR_FLOOR)
+            info["n_accept"] += 1
+            h_last = h_new
+            h = h_new
+            done = (info["n_accept"] >= n_fixed) if n_fixed is not None else (t_end - t <= T_END_TOL * t_end)
+            if not done:
+                fn = f(u)
+                info["n_f"] += 1
+                jv = jv_at(u)
+                Q, H = arnoldi(jv, fn, M)
+                info["n_jv"] += Q.shape[1]
+        else:
+            info["n_reject"] += 1
+            h = h_new
+            if replay is None and h < 1e-12 * t_end:
+                info["status"] = STATUS_STEP_UNDERFLOW
+                break
+    info["h_last"] = h_last
+    info["t"] = t
+    return u, info
+
+
+def reactor(kin, p, src=None, jv_mode="analytic"):
+    """(f, jv_at) pair for one constant-pressure cell with an optional constant source."""
+    def f(u):
+        return kin.rhs(u, p, src)
+
+    if jv_mode == "analytic":
+        def jv_at(u):
+            J = kin.jacobian(u, p)
+            return lambda v: J @ v
+    elif jv_mode == "fd":
+        def jv_at(u):
+            f0 = kin.rhs(u, p, src)
+            scale = np.sqrt(np.finfo(float).eps) * (1.0 + np.linalg.norm(u))
+
+            def jv(v):
+                nv = np.linalg.norm(v)
+                if nv == 0.0:
+                    return np.zeros_like(v)
+                d = scale / nv
+                return (kin.rhs(u + d * v, p, src) - f0) / d
+            return jv
+    else:
+        raise ValueError(jv_mode)
+    return f, jv_at
+
+
+def integrate_cells(kin, U, p, dt, rtol, atol, M, *, src=None, h0=None, jv_mode="analytic",
+                    max_attempts=100000, replay=None, fixed_h=None, record=False):
+    """Integrate each row of U independently (pure-Python loop over cells)."""
+    U = np.asarray(U, dtype=float)
+    out = np.empty_like(U)
+    infos = []
+    for c in range(U.shape[0]):
+        s = None if src is None else src[c]
+        f, jv_at = reactor(kin, p, s, jv_mode)
+        hc = None if h0 is None else (h0[c] if np.ndim(h0) else h0)
+        rp = None if replay is None else replay[c]
+        out[c], inf = integrate(f, jv_at, U[c], dt, rtol, atol, M, h0=hc, max_attempts=max_attempts,
+                                replay=rp, fixed_h=fixed_h, record=record)
+        infos.append(inf)
+    return out, infos

@@ -1,0 +1,224 @@
+"""Pins of the oracle's ROK4E integrator (Sec. 4.1-4.3, Algorithm 1).
+
+* At full Krylov dimension M = N the projected Jacobian equals the exact one
+  (Sec. 4.1), so one ROK4E attempt must equal a classical ROW step of the
+  untransformed form Eq. s_stage_row solved with a dense LU -- a textbook
+  routine independent of the oracle's transformed stages, Arnoldi and Woodbury
+  solve.
+* Fixed-step order 4 on a linear system against the matrix exponential, and
+  the degradation to order 3 when M < p (the Krylov condition needs M >= p).
+* Steady-state preservation (Def. steady_state_preserving): f(u) = 0 exactly
+  leaves u unchanged bit for bit.
+* Linear invariants (element totals, sum of Y) survive a full adaptive step.
+"""
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import rok4e
+from oracle.kinetics import Kinetics, element_totals
+from synth.fields import WORKLOADS, initial_state, mechanism_for
+
+
+def dense_row_step(f, J, u, h):
+    """Classical ROW step, Eq. s_stage_row with the exact Jacobian (and the h on
+    the A_n sum gamma_ij k_j term), solved with a dense linear solve."""
+    g = rok4e.GAMMA
+    A = np.eye(len(u)) - h * g * J
+    ks = []
+    for i in range(4):
+        arg = u + h * sum((rok4e.ALPHA_IJ[i, j] * ks[j] for j in range(i)), np.zeros_like(u))
+        rhs = f(arg) + h * J @ sum((rok4e.GAMMA_IJ[i, j] * ks[j] for j in range(i)), np.zeros_like(u))
+        ks.append(np.linalg.solve(A, rhs))
+    return (u + h * sum(rok4e.B[j] * ks[j] for j in range(4)),
+            u + h * sum(rok4e.BHAT[j] * ks[j] for j in range(4)))
+
+
+def _nonlinear_system(n, seed):
+    rng = np.random.default_rng(seed)
+    L = rng.normal(size=(n, n)) - 3 * np.eye(n)
+    c = rng.normal(size=n)
+
+    def f(u):
+        return L @ u + c + 0.3 * np.sin(u) * u[::-1]
+
+    def jac(u):
+        J = L + 0.3 * np.diag(np.cos(u) * u[::-1])
+        J = J + 0.3 * np.diag(np.sin(u))[:, ::-1]
+        return J
+    return f, jac
+
+
+def test_nonlinear_system_jacobian_is_exact():
+    f, jac = _nonlinear_system(7, 3)
+    u = np.linspace(-1, 1, 7)
+    J = jac(u)
+    eps = 1e-7
+    Jfd = np.column_stack([(f(u + eps * e) - f(u - eps * e)) / (2 * eps) for e in np.eye(7)])
+    assert np.max(np.abs(J - Jfd)) < 1e-7
+
+
+@pytest.mark.parametrize("n,h", [(6, 0.05), (9, 0.3), (12, 1.0)])
+def test_full_krylov_dimension_equals_dense_row(n, h):
+    f, jac = _nonlinear_system(n, n)
+    u = np.random.default_rng(1).normal(size=n)
+    fn = f(u)
+    J = jac(u)
+    Q, H = rok4e.arnoldi(lambda v: J @ v, fn, n)
+    assert Q.shape[1] == n
+    assert np.max(np.abs(Q.T @ Q - np.eye(n))) < 1e-13
+    assert np.max(np.abs(Q @ H @ Q.T - J)) < 1e-12 * np.max(np.abs(J))
+    us, uh, nf = rok4e.attempt(f, u, fn, Q, H, h)
+    ur, urh = dense_row_step(f, J, u, h)
+    scale = np.max(np.abs(ur))
+    assert np.max(np.abs(us - ur)) < 1e-13 * scale
+    assert np.max(np.abs(uh - urh)) < 1e-13 * scale
+    assert nf == 2  # stages 2 and 3; stage 4 reuses stage 3's f
+
+
+def test_chemistry_full_krylov_equals_dense_row():
+    w = WORKLOADS["small"]
+    kin = Kinetics(mechanism_for(w))
+    u = initial_state(w)[5]
+    p = 101325.0
+    f = lambda x: kin.rhs(x, p)
+    J = kin.jacobian(u, p)
+    N = len(u)
+    fn = f(u)
+    Q, H = rok4e.arnoldi(lambda v: J @ v, fn, N)
+    h = 2e-9
+    us, uh, _ = rok4e.attempt(f, u, fn, Q, H, h)
+    ur, urh = dense_row_step(f, J, u, h)
+    # (an early breakdown leaves an invariant subspace, on which the step is exact too)
+    assert np.max(np.abs(us - ur) / (1e-10 + np.abs(ur))) < 1e-8
+
+
+def _linear_problem(n=8, seed=5):
+    rng = np.random.default_rng(seed)
+    V = rng.normal(size=(n, n))
+    lam = -np.logspace(-0.5, 1.0, n)
+    L = V @ np.diag(lam) @ np.linalg.inv(V)
+    c = rng.normal(size=n)
+    u0 = rng.normal(size=n)
+    return L, c, u0
+
+
+def _fixed_step_error(M, n_steps, L, c, u0, T=1.0):
+    f = lambda u: L @ u + c
+    jv_at = lambda u: (lambda v: L @ v)
+    u, info = rok4e.integrate(f, jv_at, u0, T, 1.0, 1.0, M, fixed_h=T / n_steps)
+    assert info["n_accept"] == n_steps
+    # exact: u(T) = e^{LT} u0 + L^{-1}(e^{LT} - I) c
+    E = scipy.linalg.expm(L * T)
+    exact = E @ u0 + np.linalg.solve(L, (E - np.eye(len(u0))) @ c)
+    return np.max(np.abs(u - exact))
+
+
+def _fitted_order(M, L, c, u0, steps=(16, 32, 64, 128, 256)):
+    errs = np.array([_fixed_step_error(M, n, L, c, u0) for n in steps])
+    return np.polyfit(np.log(1.0 / np.array(steps)), np.log(errs), 1)[0]  # err ~ h^p
+
+
+@pytest.mark.parametrize("seed", [5, 6, 7])
+def test_order_four_on_linear_system(seed):
+    L, c, u0 = _linear_problem(seed=seed)
+    assert 3.7 < _fitted_order(4, L, c, u0) < 4.3
+    assert 3.7 < _fitted_order(8, L, c, u0) < 4.3  # M = N: classical ROW
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_krylov_dimension_below_order_loses_order(seed):
+    L, c, u0 = _linear_problem(seed=seed)
+    assert 2.6 < _fitted_order(3, L, c, u0) < 3.3
+
+
+def test_embedded_local_error_order():
+    L, c, u0 = _linear_problem()
+    f = lambda u: L @ u + c
+    fn = f(u0)
+    Q, H = rok4e.arnoldi(lambda v: L @ v, fn, 4)
+    d = []
+    for h in (0.02, 0.01):
+        us, uh, _ = rok4e.attempt(f, u0, fn, Q, H, h)
+        d.append(np.max(np.abs(uh - us)))
+    # u* - u^ = O(h^4): halving h divides the estimate by ~16
+    assert 12 < d[0] / d[1] < 20
+
+
+def test_steady_state_is_preserved_bit_exact():
+    w = WORKLOADS["small"]
+    kin = Kinetics(mechanism_for(w))
+    p = 101325.0
+    for u in initial_state(w)[:4]:
+        src = -kin.rhs(u, p)  # balancing source: f(u) = R(u) - R(u) = 0 exactly
+        f, jv_at = rok4e.reactor(kin, p, src)
+        assert np.all(f(u) == 0.0)
+        out, info = rok4e.integrate(f, jv_at, u, w.dt, w.rtol, w.atol, 4)
+        assert np.array_equal(out, u)
+        assert info["n_accept"] == 1 and info["n_reject"] == 0
+
+
+def test_linear_invariants_conserved():
+    w = WORKLOADS["small"]
+    mech = mechanism_for(w)
+    kin = Kinetics(mech)
+    p = 101325.0
+    U = initial_state(w)[:6]
+    out, infos = rok4e.integrate_cells(kin, U, p, w.dt, w.rtol, w.atol, 4)
+    ns = mech.n_species
+    e0 = element_totals(mech, U[:, :ns])
+    e1 = element_totals(mech, out[:, :ns])
+    assert np.max(np.abs(e1 - e0) / np.abs(e0).max()) < 1e-12
+    assert np.max(np.abs(out[:, :ns].sum(1) - U[:, :ns].sum(1))) < 1e-13
+    # and the state really moved
+    assert np.max(np.abs(out - U)[:, :ns]) > 1e-4
+
+
+def test_adaptive_error_control_tracks_tolerance():
+    w = WORKLOADS["small"]
+    kin = Kinetics(mechanism_for(w))
+    p = 101325.0
+    U = initial_state(w)[:3]
+    ref, _ = rok4e.integrate_cells(kin, U, p, w.dt, 1e-11, 1e-15, 4)
+    errs = []
+    for rtol in (1e-4, 1e-6, 1e-8):
+        out, _ = rok4e.integrate_cells(kin, U, p, w.dt, rtol, rtol * 1e-4, 4)
+        errs.append(np.max(np.abs(out - ref) / (np.abs(ref) + 1e-6)))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[1] < 1e-4
+
+
+def test_fd_and_analytic_jacobian_vector_modes_agree():
+    w = WORKLOADS["small"]
+    kin = Kinetics(mechanism_for(w))
+    p = 101325.0
+    U = initial_state(w)[:3]
+    a, _ = rok4e.integrate_cells(kin, U, p, w.dt, w.rtol, w.atol, 4, jv_mode="analytic")
+    b, _ = rok4e.integrate_cells(kin, U, p, w.dt, w.rtol, w.atol, 4, jv_mode="fd")
+    assert np.max(np.abs(a - b)[:, :-1]) < 1e-5
+    assert np.max(np.abs(a - b)[:, -1]) < 1e-2
+
+
+def test_replay_reproduces_free_run():
+    w = WORKLOADS["small"]
+    kin = Kinetics(mechanism_for(w))
+    p = 101325.0
+    U = initial_state(w)[:2]
+    a, ia = rok4e.integrate_cells(kin, U, p, w.dt, w.rtol, w.atol, 4, record=True)
+    b, ib = rok4e.integrate_cells(kin, U, p, w.dt, w.rtol, w.atol, 4, replay=[i["trace"] for i in ia])
+    assert np.array_equal(a, b)
+
+
+def test_arnoldi_breakdown_on_invariant_subspace():
+    # J = diag with f in the span of two eigenvectors: K_M has dimension 2
+    J = np.diag([-1.0, -2.0, -3.0, -4.0, -5.0])
+    f = np.array([1.0, 1.0, 0.0, 0.0, 0.0])
+    Q, H = rok4e.arnoldi(lambda v: J @ v, f, 4)
+    assert Q.shape[1] == 2
+    assert np.allclose(np.sort(np.linalg.eigvals(H).real), [-2.0, -1.0])
+
+
+def test_zero_rhs_gives_empty_basis():
+    Q, H = rok4e.arnoldi(lambda v: v, np.zeros(4), 4)
+    assert Q.shape == (4, 0)

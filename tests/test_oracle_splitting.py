@@ -1,0 +1,207 @@
+"""Pins of the oracle's splitting (Sec. 3) and the 1-D reaction-diffusion step.
+
+* Scalar linear analysis: the two-substep schemes with exact sub-flows equal the
+  recurrence u_{n+1} = R u_n - Q (a + b) with the closed forms; the printed
+  limits (R -> I for h -> inf, the |B| -> inf limits, the 5.99 bound, the
+  |B| > 3|A| criterion).
+* Steady-state preservation (Def. steady_state_preserving) for the balanced
+  methods and its failure for Strang with an O(h^3) one-step deviation.
+* Scalar PSR (Eq. scalar_psr): turning points Da_E = 15.90, Da_I = 832.84.
+* Second-order convergence of Simpler splitting.
+* 1-D diffusion without chemistry: the Simpler step is second-order accurate
+  against the exact solution of the semi-discrete diffusion equation.
+"""
+
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.optimize
+from scipy.integrate import solve_ivp
+
+from oracle import splitting as sp
+from oracle.kinetics import Kinetics
+from synth.mechanism import single_reaction_mechanism
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")
+
+
+def _paper(name):
+    for line in open(GOLDEN):
+        if line.startswith(name + " ") or line.startswith(name + "\t"):
+            return float(line.split()[1])
+    raise KeyError(name)
+
+
+def _linear(A, B, a, b):
+    fT = sp.exact_linear_flow(A, a)
+    fR = sp.exact_linear_flow(B, b)
+    return fT, fR, (lambda u: A * u + a), (lambda u: B * u + b)
+
+
+@pytest.mark.parametrize("A,B,h", [(-1.0, -7.0, 0.37), (-0.3, -40.0, 2.0), (-2.0, -0.5, 0.05)])
+def test_simpler_recurrence_matches_two_substep_scheme(A, B, h):
+    a, b = 0.4, -0.9
+    fT, fR, Top, _ = _linear(A, B, a, b)
+    step = lambda u: sp.simpler_step(u, h, Top, fT, fR)
+    R, Q = sp.simpler_R_Q(A, B, h)
+    for u in (0.0, 1.0, -2.5):
+        assert step(u) == pytest.approx(R * u - Q * (a + b), rel=1e-13, abs=1e-14)
+
+
+@pytest.mark.parametrize("A,B,h", [(-1.0, -7.0, 0.37), (-0.3, -40.0, 2.0)])
+def test_simple_balanced_recurrence_matches_scheme(A, B, h):
+    a, b = 0.4, -0.9
+    fT, fR, Top, Rop = _linear(A, B, a, b)
+    R, Q = sp.simple_R_Q(A, B, h)
+    step = lambda u: sp.simple_balanced_step(u, h, Top, Rop, fT, fR, reaction_first=False)
+    for u in (0.0, 1.0):
+        assert step(u) == pytest.approx(R * u - Q * (a + b), rel=1e-13, abs=1e-14)
+    # reaction first: the same map with A and B exchanged
+    R2, Q2 = sp.simple_R_Q(B, A, h)
+    step2 = lambda u: sp.simple_balanced_step(u, h, Top, Rop, fT, fR, reaction_first=True)
+    for u in (0.0, 1.0):
+        assert step2(u) == pytest.approx(R2 * u - Q2 * (a + b), rel=1e-13, abs=1e-14)
+
+
+def test_simpler_limits():
+    # h -> inf: R -> 1 (Eq. simpler_large_h)
+    R, _ = sp.simpler_R_Q(-1.0, -5.0, 200.0)
+    assert R == pytest.approx(1.0, abs=1e-12)
+    # |B| -> inf: R -> 1 - alpha (the printed 1 - alpha^2 does not follow from R)
+    A, h = -1.0, 0.8
+    R, _ = sp.simpler_R_Q(A, -1e9, h)
+    alpha = np.exp(A * h / 2)
+    assert R == pytest.approx(1 - alpha, rel=1e-8)
+    assert abs(R - (1 - alpha**2)) > 0.1
+    # stable for all h > 0 with A, B < 0 (|R| < 1; R -> 1 only as h -> inf)
+    for h in np.logspace(-3, 3, 61):
+        for B in (-0.1, -1.0, -10.0, -1e4):
+            R = sp.simpler_R_Q(-1.0, B, h)[0]
+            assert abs(R) < 1.0 or (h > 30 and abs(R) <= 1.0)
+
+
+def test_simple_balanced_limits():
+    A = -1.0
+    # h -> inf.  The printed R gives (1 - B/A)/2; Eq. simple_large_h prints
+    # (I + A^-1 B)/2, a sign slip.  With the printed R the method is stable for
+    # all h exactly when |B| < 3|A| (the text prints "|B| > 3|A|", which would
+    # contradict its own remark that stiff B destabilises the method).
+    for B in (-2.0, -5.0):
+        R, _ = sp.simple_R_Q(A, B, 300.0)
+        assert R == pytest.approx(0.5 * (1 - B / A), rel=1e-10)
+    ratio = _paper("simple_balanced_ratio_bound")
+    R, _ = sp.simple_R_Q(A, A * ratio * 0.99, 300.0)
+    assert abs(R) < 1.0
+    R, _ = sp.simple_R_Q(A, A * ratio * 1.01, 300.0)
+    assert abs(R) > 1.0
+    # |B| >> |A| (A -> 0 at fixed B h): R -> (1 + beta)(2 + B h)/4 and the |B| h < 5.99 bound
+    h = 0.3
+    for Bh in (1.0, 4.0, 5.5):
+        B = -Bh / h
+        lim = 0.25 * (1 + np.exp(B * h)) * (2 + B * h)
+        Rbig, _ = sp.simple_R_Q(A * 1e-9, B, h)
+        assert Rbig == pytest.approx(lim, rel=1e-6, abs=1e-9)
+    x = scipy.optimize.brentq(lambda x: 0.25 * (1 + np.exp(-x)) * (2 - x) + 1, 3.0, 8.0)
+    assert x == pytest.approx(_paper("simple_balanced_Bh_bound"), abs=0.005)
+
+
+def test_steady_state_preservation():
+    A, B, a, b = -1.0, -30.0, 0.4, 2.1
+    fT, fR, Top, Rop = _linear(A, B, a, b)
+    u_inf = -(a + b) / (A + B)
+    for h in (0.01, 0.3, 5.0):
+        assert sp.simpler_step(u_inf, h, Top, fT, fR) == pytest.approx(u_inf, rel=1e-14)
+        assert sp.simple_balanced_step(u_inf, h, Top, Rop, fT, fR) == pytest.approx(u_inf, rel=1e-14)
+    dev = [abs(sp.strang_step(u_inf, h, fT, fR) - u_inf) for h in (0.02, 0.01)]
+    assert dev[0] > 1e-6
+    assert 6.0 < dev[0] / dev[1] < 10.0  # O(h^3)
+
+
+def test_scalar_psr_turning_points():
+    T_in, T_ad, T_a = _paper("psr_T_in"), _paper("psr_T_ad"), _paper("psr_T_a")
+    Da = lambda T: sp.psr_steady_Da(T, T_in, T_ad, T_a)
+    dDa = lambda T: (Da(T * (1 + 1e-7)) - Da(T * (1 - 1e-7))) / (2e-7 * T)
+    T_ign = scipy.optimize.brentq(dDa, 0.151, 0.4)  # local max of Da(T): ignition
+    T_ext = scipy.optimize.brentq(dDa, 0.5, 1.1)  # local min: extinction
+    assert Da(T_ign) == pytest.approx(_paper("psr_Da_ignition"), abs=0.01)
+    assert Da(T_ext) == pytest.approx(_paper("psr_Da_extinction"), abs=0.01)
+
+
+def _psr_flows(Da):
+    def flow_R(T, dt, src):
+        s = solve_ivp(lambda t, y: sp.psr_rhs_parts(y, Da)[0] + src, (0, dt), [T], rtol=1e-12,
+                      atol=1e-14, method="LSODA")
+        return s.y[0, -1]
+
+    def flow_T(T, dt, src):
+        s = solve_ivp(lambda t, y: sp.psr_rhs_parts(y, Da)[1] + src, (0, dt), [T], rtol=1e-12,
+                      atol=1e-14, method="LSODA")
+        return s.y[0, -1]
+    return flow_T, flow_R
+
+
+def test_simpler_second_order_on_scalar_psr():
+    Da = 100.0
+    T0, t_end = 0.6, 2.0
+    flow_T, flow_R = _psr_flows(Da)
+    Top = lambda T: sp.psr_rhs_parts(T, Da)[1]
+    ref = solve_ivp(lambda t, y: sum(sp.psr_rhs_parts(y, Da)), (0, t_end), [T0], rtol=1e-12,
+                    atol=1e-14, method="LSODA").y[0, -1]
+    errs = []
+    for n in (8, 16, 32):
+        T = T0
+        for _ in range(n):
+            T = sp.simpler_step(T, t_end / n, Top, flow_T, flow_R)
+        errs.append(abs(T - ref))
+    slopes = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all((slopes > 1.8) & (slopes < 2.3)), (errs, slopes)
+
+
+def test_laplacian_exact_for_quadratics_and_conservative():
+    n, dx = 20, 0.1
+    x = (np.arange(n) + 0.5) * dx
+    U = (3 * x**2 - x + 1.0)[:, None]
+    L = sp.laplacian_neumann(U, dx)
+    assert np.allclose(L[1:-1, 0], 6.0, rtol=1e-9)
+    V = np.random.default_rng(0).normal(size=(n, 3))
+    assert np.allclose(sp.laplacian_neumann(V, dx).sum(axis=0), 0.0, atol=1e-9)
+
+
+def test_ssprk3_is_third_order():
+    lam = -1.3
+    errs = [abs(sp.ssprk3(np.array([1.0]), h, lambda v: lam * v)[0] - np.exp(lam * h)) for h in (0.1, 0.05)]
+    assert 14.0 < errs[0] / errs[1] < 18.0  # local error O(h^4)
+
+
+def _inert_mechanism():
+    # one reaction with negligible rate: chemistry is effectively off
+    return single_reaction_mechanism([0, 1], [2], [(0, 1, 1, 0), (0, 1, 0, 1), (0, 2, 1, 1)],
+                                     1e-300, 0.0, 0.0, reversible=False)
+
+
+def test_simpler_1d_diffusion_second_order():
+    mech = _inert_mechanism()
+    kin = Kinetics(mech)
+    n, length, D = 32, 1e-2, 1e-4
+    dx = length / n
+    x = (np.arange(n) + 0.5) * dx
+    U0 = np.empty((n, 4))
+    U0[:, 0] = 0.2 + 0.1 * np.cos(np.pi * x / length)
+    U0[:, 1] = 0.5
+    U0[:, 2] = 1 - U0[:, 0] - U0[:, 1]
+    U0[:, 3] = 1000.0 + 300.0 * np.cos(2 * np.pi * x / length)
+    # exact semi-discrete solution: exp(t D L) U0 with the Neumann Laplacian matrix
+    Lm = sp.laplacian_neumann(np.eye(n), dx)
+    t_end = 4e-5
+    exact = scipy.linalg.expm(t_end * D * Lm) @ U0
+    errs = []
+    for steps in (4, 8, 16):
+        U = U0.copy()
+        h = t_end / steps
+        for _ in range(steps):
+            U, _, infos, _ = sp.simpler_split_step_1d(kin, U, 101325.0, h, D, dx, 1e-8, 1e-12, 4)
+        errs.append(np.max(np.abs(U[:, 3] - exact[:, 3])))
+    slopes = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all((slopes > 1.8) & (slopes < 2.4)), (errs, slopes)
