@@ -1,0 +1,334 @@
+"""Benchmark: Simpler balanced split steps of the 1-D reaction-diffusion workload.
+
+One bench step = one Simpler balanced split step (Eq. simpler_balanced) of the
+1-D reaction-diffusion system: 2048 points on 1 cm, a 30-species /
+150-reaction synthetic mechanism (4 third-body, 2 Troe falloff reactions),
+tanh temperature front 300 -> 2000 K, dt = 1e-7 s, ROK4E with M = 4,
+rtol 1e-6, atol 1e-10: transport T(U_n), the per-cell ROK4E reaction
+sub-step with the constant source T(U_n), and the SSP-RK3 transport
+correction over dt/2.  Metric: cell-steps/s = points x split steps / time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank integrates its own independent domain
+(seeded per rank): weak scaling, no data-path collective.  ``--impl reference``
+times the FP64 numpy oracle on the host cores on a bounded sample of the same
+workload (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "flame1d"
+D_DIFF = 1.0e-4  # m^2/s
+LENGTH = 1.0e-2  # m
+P_ATM = 101325.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+# ------------------------------------------------------------- work model
+def flop_model(mech, M):
+    """Algorithmic FP64 operation counts (flops, FMA = 2) of the kernels' units.
+
+    Returns dict(rhs, rhs_exp, jvp, arnoldi, attempt) per unit.  Transcendentals
+    are counted separately (rhs_exp) and converted with the measured cost of
+    one FP64 exp in FMA-equivalents."""
+    ns, nr = mech.n_species, mech.n_reactions
+    N = ns + 1
+    kind = np.asarray(mech.kind)
+    n_tb = int((kind == 1).sum())
+    n_troe = int((kind == 2).sum())
+    nnz = 0
+    for j in range(nr):
+        net = {}
+        for s, n in zip(mech.rxn_sp[j], mech.rxn_nu[j]):
+            if s >= 0:
+                net[s] = net.get(s, 0) + n
+        nnz += sum(1 for v in net.values() if v != 0)
+    rhs = ns * 40 + nr * 16 + 2 * nnz + (n_tb + n_troe) * 2 * ns + n_troe * 40 + 10
+    rhs_exp = 2 * ns + nr + 7 * n_troe + 1
+    jvp = ns * 25 + nr * 26 + 2 * nnz + (n_tb + n_troe) * (2 * ns + 4) + 10
+    arnoldi = 3 * N + M * 5 * N + 8 * N * M * (M + 1) // 2
+    attempt = 4 * N * (4 * M + 6) + 22 * N + (2 * M**3) // 3 + 8 * M * M
+    return dict(rhs=rhs, rhs_exp=rhs_exp, jvp=jvp, arnoldi=arnoldi, attempt=attempt)
+
+
+def algorithmic_flops(model, stats, M, exp_fma):
+    """Total FP64 flops (exp counted as exp_fma FMAs) implied by per-cell stats."""
+    st = np.asarray(stats, dtype=np.int64).reshape(-1, 4)
+    n_acc, n_rej, n_rhs = st[:, 0].sum(), st[:, 1].sum(), st[:, 2].sum()
+    n_arn = np.maximum(st[:, 0], 1).sum()
+    rhs_total = n_rhs * (model["rhs"] + 2 * exp_fma * model["rhs_exp"])
+    return float(rhs_total + n_arn * (M * model["jvp"] + model["arnoldi"]) + (n_acc + n_rej) * model["attempt"])
+
+
+# -------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu_index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- arms
+def build_inputs(rank):
+    from synth.fields import WORKLOADS, field_tanh_front, mechanism_for
+
+    w = WORKLOADS[WORKLOAD]
+    mech = mechanism_for(w)
+    _, U = field_tanh_front(w.n_cells, w.n_species, w.field_seed + 97 * rank)
+    return w, mech, U
+
+
+def cpu_oracle_sample(w, mech, U, n_cells, seconds_hint=None):
+    """Time the oracle's Simpler split step on a stratified sample of cells:
+    transport over the whole grid, the ROK4E reaction sub-step on n_cells."""
+    from oracle import splitting as osp
+    from oracle.kinetics import Kinetics
+
+    kin = Kinetics(mech)
+    npts = U.shape[0]
+    dx = LENGTH / npts
+    cells = list(np.linspace(0, npts - 1, n_cells).astype(int))
+    t0 = time.perf_counter()
+    osp.simpler_split_step_1d(kin, U, P_ATM, w.dt, D_DIFF, dx, w.rtol, w.atol, w.krylov_dim, cells=cells)
+    dt = time.perf_counter() - t0
+    return n_cells / dt, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    w, mech, U = build_inputs(0)
+    per_step = 1
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, mech, U, per_step)
+    t_total = 0.0
+    cells_total = 0
+    for k in range(args.steps):
+        _, dt = cpu_oracle_sample(w, mech, U, per_step)
+        t_total += dt
+        cells_total += per_step
+    value = cells_total / t_total
+    line = {
+        "impl": "reference", "metric": "cell-steps/s", "value": value, "unit": "cell-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "flame1d 1-D reaction-diffusion, 2048 points, 30 species / 150 reactions, "
+                               "Simpler split steps of 1e-7 s, ROK4E M=4, rtol 1e-6, atol 1e-10",
+                   "oracle_sample": f"{per_step} cell(s) per step through the FP64 numpy oracle"},
+        "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} stratified cell per step x {args.steps} steps of the initial field"},
+        "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_1712_00953_gb300 as rk
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist = dist_mod
+        dist.init_process_group("nccl", device_id=dev)
+    w, mech, U0 = build_inputs(rank)
+    npts, N = U0.shape
+    dx = LENGTH / npts
+    M = w.krylov_dim
+    m = rk.mech_load(mech)
+    stream = torch.cuda.current_stream()
+    U = torch.tensor(U0, device=dev)
+    hc = torch.zeros(npts, dtype=torch.float64, device=dev)
+    ws = torch.empty(rk.simpler_split_step_workspace_size(m, npts, M), dtype=torch.uint8, device=dev)
+    stats_all = torch.zeros(max(args.steps, 1), npts, 4, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in kev:  # materialise the events so their handles can be passed down
+        a.record(stream)
+        b.record(stream)
+
+    def step(stats=None, events=None):
+        rk.simpler_split_step(m, U, w.dt, D_DIFF, dx, w.rtol, w.atol, M, h_cell=hc, stats=stats,
+                              opts=rk.Opts(events=events), workspace=ws, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))  # evict the previous step's data from L2 (outside the timed events)
+            ev[k][0].record(stream)
+            step(stats_all[k], kev[k])
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kern_ms = [a.elapsed_time(b) for a, b in kev]
+    t_total = sum(step_ms) * 1e-3
+    if dist:
+        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    value = world * npts * args.steps / t_total
+
+    # ---- end to end through the public API with host buffers
+    pinned = torch.tensor(U.cpu().numpy(), dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 50))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        U.copy_(pinned, non_blocking=True)
+        step()
+        pinned.copy_(U, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_t = e0.elapsed_time(e1) * 1e-3
+    e2e_value = world * npts * e2e_steps / e2e_t
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+
+    # ---- roofline of the dominant kernel (FP64 ALU)
+    fma64 = rk.probe_throughput(0)
+    exp64 = rk.probe_throughput(2)
+    exp_fma = fma64 / exp64
+    model = flop_model(mech, M)
+    st = stats_all.cpu().numpy()
+    flops = algorithmic_flops(model, st, M, exp_fma)
+    kern_total = sum(kern_ms) * 1e-3
+    achieved = flops / kern_total / 1e12
+    peak_nominal = 1.25  # TFLOP/s FP64 (GB300 nominal)
+    peak_meas = 2.0 * fma64 / 1e12
+    bad = int((st[:, :, 3] != 0).sum())
+
+    # ---- CPU baseline: the oracle on a bounded sample of the initial field
+    cpu_v, cpu_t = cpu_oracle_sample(w, mech, U0, args.cpu_cells)
+
+    clocks = clk.summary()
+    line = {
+        "metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "flame1d 1-D reaction-diffusion, 2048 points, 30 species / 150 reactions "
+                               "(4 third-body, 2 Troe), Simpler split steps of 1e-7 s, ROK4E M=4, rtol 1e-6, "
+                               "atol 1e-10, FP64", "points": npts, "l2": "flushed (256 MB write) between steps",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_nominal, "unit": "TFLOP/s",
+                     "frac": achieved / peak_nominal, "traffic": None,
+                     "kernel": "rok4e_integrate_kernel<32>", "kernel_ms_per_step": 1e3 * kern_total / args.steps,
+                     "peak_probe_fp64": peak_meas, "frac_of_probe": achieved / peak_meas,
+                     "exp_cost_fma": exp_fma, "algorithmic_tflop_per_step": flops / args.steps / 1e12},
+        "cpu_baseline": {"value": cpu_v, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.cpu_cells} stratified cells of the initial field, one split step "
+                                   f"({cpu_t:.1f} s)"},
+        "e2e": {"value": e2e_value, "unit": "cell-steps/s", "h2d_bytes_per_step": int(U.numel() * 8),
+                "d2h_bytes_per_step": int(U.numel() * 8), "steps": e2e_steps},
+        "gpu_launches": 5 * args.steps,
+        "clocks": clocks,
+        "cells_failed": bad,
+        "substeps_per_cell_step": float(st[:, :, 0].mean()),
+        "attempts_per_cell_step": float((st[:, :, 0] + st[:, :, 1]).mean()),
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-cells", type=int, default=48)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,215 @@
+/*
+ * rok4e.h -- C ABI of the GB300 ROK4E / Simpler-splitting library.
+ *
+ * The library integrates the reaction operator of a reacting-flow solver cell
+ * by cell with ROK4E, the four-stage, fourth-order Rosenbrock-Krylov scheme of
+ * Wu, Ma & Ihme, "Efficient time stepping for reactive turbulent simulations
+ * with stiff chemistry" (arXiv:1712.00953), Sec. 4 and Algorithm 1, inside the
+ * Simpler balanced splitting step of Sec. 3.4 (Eq. simpler_balanced).
+ *
+ * Conventions shared by every call:
+ *  - State rows.  A cell state is u = (Y_1 .. Y_Ns, T): Ns mass fractions and
+ *    the temperature in K, N = Ns + 1 doubles, rows contiguous (row-major
+ *    [ncell x N]).  Pressure p is in Pa and constant during a call (the cells
+ *    are constant-pressure adiabatic reactors; the paper's Eq. cv_reactor uses
+ *    the constant-volume form of the same source term).
+ *  - Memory.  Arrays passed to compute calls are DEVICE pointers owned by the
+ *    caller unless stated otherwise; only the mechanism handle is owned by the
+ *    library.  Compute calls never allocate: scratch comes from the caller's
+ *    workspace argument (size from the matching *_workspace_size call).
+ *  - Streams.  `stream` is a cudaStream_t passed as void*; NULL is the legacy
+ *    default stream.  Compute calls are asynchronous and stream-ordered; a
+ *    return value of 0 means the launch was issued.
+ *  - Errors.  Calls return RK_OK (0) or a negative RK_E_* code and never throw.
+ *    rk_status_string() names a code; rk_last_error() returns a message for
+ *    the most recent failure on the calling thread.  Per-cell integration
+ *    failures (attempt cap, step-size underflow) do not fail the call: they
+ *    are reported in the per-cell statistics.
+ */
+#ifndef ROK4E_H
+#define ROK4E_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes --------------------------------------------------------- */
+#define RK_OK 0
+#define RK_E_INVALID_ARGUMENT (-1)  /* null pointer, bad size or option          */
+#define RK_E_MECH_INVALID (-2)      /* mechanism failed validation              */
+#define RK_E_CUDA (-3)              /* a CUDA runtime call failed               */
+#define RK_E_UNSUPPORTED (-4)       /* size beyond what the kernels support     */
+#define RK_E_WORKSPACE (-5)         /* workspace missing or too small           */
+
+/* ---- per-cell status codes (stats[4*cell + 3]) ---------------------------- */
+#define RK_CELL_OK 0
+#define RK_CELL_MAX_ATTEMPTS 1      /* attempt cap reached before t_end          */
+#define RK_CELL_NONFINITE 2         /* an accepted state was not finite          */
+#define RK_CELL_STEP_UNDERFLOW 3    /* h fell below 1e-12 dt after rejections    */
+
+/* Limits of this build. */
+#define RK_MAX_SPECIES 254          /* species indices are packed in 8 bits     */
+#define RK_MAX_KRYLOV 8             /* largest Krylov dimension M               */
+
+/* ---- mechanism -------------------------------------------------------------
+ * Description of a gas-phase mechanism (host pointers, read during the call).
+ * Thermodynamics: NASA-7 polynomials.  Kinetics: kf = A T^b exp(-Ea/(R T));
+ * reversible reactions use kr = kf / Kc with Kc from the species Gibbs
+ * functions (standard pressure 101325 Pa); third-body reactions multiply the
+ * rate by [M] = sum_k eff_k C_k; Troe falloff reactions use
+ * k = k_inf Pr/(1+Pr) F with Pr = k0 [M] / k_inf and the Troe form of F.
+ * The paper delegates these kinetics to Cantera (Sec. 4.4); the library
+ * implements the textbook forms.
+ *
+ *  elem        int32[Ns*4]   atom counts of C, H, O, N per species
+ *  W           f64[Ns]       molar masses, kg/mol (> 0)
+ *  nasa        f64[Ns*17]    T_lo, T_mid, T_hi, low-range a1..a7, high-range a1..a7
+ *  rxn_sp      int32[Nr*4]   slots 0,1: reactant species, slots 2,3: product
+ *                            species, -1 = empty slot
+ *  rxn_nu      int32[Nr*4]   signed stoichiometric coefficients of the slots
+ *                            (reactants < 0, products > 0); at most two
+ *                            molecules per side
+ *  arrh        f64[Nr*3]     A (cm, mol, s units), b, Ea (J/mol); for a Troe
+ *                            reaction the high-pressure limit
+ *  reversible  uint8[Nr]     1 = reversible
+ *  kind        int32[Nr]     0 elementary, 1 third body (+M), 2 Troe falloff (+M)
+ *  eff         f64[Nr*Ns]    third-body efficiencies (read for kind 1 and 2)
+ *  falloff     f64[Nr*7]     A0 (cm, mol, s), b0, Ea0 (J/mol), a, T***, T*, T**
+ *                            (T** <= 0 omits that term); read for kind 2
+ */
+typedef struct rk_mech_desc {
+  int32_t n_species;
+  int32_t n_reactions;
+  const int32_t* elem;
+  const double* W;
+  const double* nasa;
+  const int32_t* rxn_sp;
+  const int32_t* rxn_nu;
+  const double* arrh;
+  const uint8_t* reversible;
+  const int32_t* kind;
+  const double* eff;
+  const double* falloff;
+} rk_mech_desc;
+
+typedef struct rk_mech rk_mech; /* opaque, library-owned, immutable after load */
+
+/* Validate a description on the host only (no GPU needed): index ranges,
+ * signs, at most two molecules per side, integer element balance
+ * sum_k nu_kj a_ek = 0 for every reaction and element, positive W and A,
+ * Troe parameters, NASA-7 ranges and continuity of cp, h and s at T_mid
+ * (relative 1e-3).  Returns RK_OK or RK_E_MECH_INVALID and writes a message
+ * into msg (may be NULL). */
+int rk_mech_validate(const rk_mech_desc* desc, char* msg, size_t msg_len);
+
+/* Validate, pack and upload a mechanism to the current CUDA device.  *out
+ * receives a handle owned by the library; free it with rk_mech_free.  The
+ * handle may be used from any stream of that device. */
+int rk_mech_load(const rk_mech_desc* desc, rk_mech** out);
+
+/* Release a handle (NULL is accepted).  Synchronises the device. */
+int rk_mech_free(rk_mech* mech);
+
+/* Sizes of a loaded mechanism (any output pointer may be NULL). */
+int rk_mech_info(const rk_mech* mech, int32_t* n_species, int32_t* n_reactions,
+                 size_t* device_bytes);
+
+/* ---- chemistry source term ---------------------------------------------------
+ * dYdt[c] = f(Y[c]) + src[c] for every cell c, with f the constant-pressure
+ * reactor source: dY_k/dt = W_k w_k / rho, dT/dt = -sum_k h_k w_k / (rho c_p),
+ * w = nu^T q the net molar production rates (Eq. cv_reactor read at constant
+ * pressure).  Y, src, dYdt: device [ncell x N]; src may be NULL (zero source).
+ * dYdt must not alias Y. */
+int rk_chem_rhs(const rk_mech* mech, const double* Y, const double* src, double p,
+                double* dYdt, int64_t ncell, void* stream);
+
+/* Jacobian-vector products JV[c] = J(Y[c]) V[c].  mode 0: analytic (exact
+ * derivative of rk_chem_rhs); mode 1: forward difference
+ * (f(u + d v) - f(u)) / d with d = sqrt(eps) (1 + ||u||_2) / ||v||_2, as in
+ * the matrix-free products of Sec. 4.3.  All arrays device [ncell x N]. */
+int rk_chem_jvp(const rk_mech* mech, const double* Y, const double* V, double p, double* JV,
+                int64_t ncell, int32_t mode, void* stream);
+
+/* ---- ROK4E integration (Sec. 4, Algorithm 1) ---------------------------------
+ * Options; pass NULL for defaults (all zero fields mean "default"). */
+typedef struct rk_opts {
+  int32_t jv_mode;        /* 0 analytic Jacobian-vector products (default), 1 finite difference */
+  int32_t max_attempts;   /* per-cell cap on attempted steps; <= 0: 100000 */
+  int32_t lanes_per_cell; /* 0 auto; 8, 16 or 32 lanes of a warp share one cell */
+  int32_t cells_per_block;/* 0 auto (as many as shared memory allows) */
+  double h0;              /* first step when h_cell is NULL or holds <= 0; <= 0: dt */
+  double fixed_h;         /* > 0: fixed steps of this size, no error control */
+  int32_t trace_cap;      /* attempts recorded per cell into trace (0: none) */
+  int32_t reserved0;
+  double* trace;          /* device [ncell x trace_cap]: +h accepted, -h rejected, 0 unused */
+  void* ev_begin;         /* optional cudaEvent_t recorded on the stream right before the */
+  void* ev_end;           /* integration kernel and right after it (timing hook), or NULL */
+} rk_opts;
+
+/* Bytes of workspace rk_rok4e_integrate needs (a small work-queue counter). */
+size_t rk_rok4e_workspace_size(const rk_mech* mech, int64_t ncell, int32_t krylov_dim,
+                               const rk_opts* opts);
+
+/* Integrate every cell over [0, dt] with ROK4E and adaptive PI step control
+ * (Algorithm 1):
+ *   Arnoldi on K_M(J_n, f_n) gives Q_n, H_n (Sec. 4.1); each stage solves the
+ *   transformed form (Eq. s_stage_row_transformed) with the low-rank inverse
+ *   (Eq. solve_kry_jac); the embedded order-3 solution gives the error
+ *   err = sqrt(mean(((u^ - u*)/(atol + rtol |u*|))^2)); the PI controller
+ *   h* = h min(5, max(0.2, 0.8 err_n^0.1 / err*^0.175)) (Sec. 4.3) sets the
+ *   next step; steps are clipped to the end of the interval.
+ *  Y         device [ncell x N], in: u(0), out: u(dt)
+ *  src       device [ncell x N] constant source added to f (the balancing
+ *            constant -c_n = T(U_n) of Simpler splitting), or NULL
+ *  h_cell    device [ncell] in/out: first step (<= 0: opts->h0 / dt) and, on
+ *            return, the proposed next step; or NULL
+ *  krylov_dim  M in 1..8 (clamped to N); M >= 4 keeps order 4
+ *  stats     device int32 [ncell x 4]: accepted steps, rejected steps, RHS
+ *            evaluations, status (RK_CELL_*); or NULL
+ *  workspace device memory of rk_rok4e_workspace_size bytes
+ * Cells are independent; one persistent launch processes them from a shared
+ * work queue. */
+int rk_rok4e_integrate(const rk_mech* mech, double* Y, const double* src, double* h_cell,
+                       int64_t ncell, double p, double dt, double rtol, double atol,
+                       int32_t krylov_dim, const rk_opts* opts, int32_t* stats, void* workspace,
+                       size_t workspace_bytes, void* stream);
+
+/* ---- Simpler balanced splitting of a 1-D reaction-diffusion system -----------
+ * One step of Eq. simpler_balanced on a uniform 1-D grid of npts cells with
+ * transport T(U) = D d^2U/dx^2 applied to every state component (constant
+ * diffusivity, unit Lewis number; second-order central differences with
+ * zero-gradient ends):
+ *   c_n = -T(U_n);
+ *   reaction:  dU/dt = R(U) - c_n over dt from U_n   (ROK4E, per cell);
+ *   transport: dU/dt = T(U) + c_n over dt/2           (one SSP-RK3 step).
+ *  U       device [npts x N] in/out;  h_cell as in rk_rok4e_integrate.
+ *  stats   as in rk_rok4e_integrate (reaction sub-step), or NULL. */
+size_t rk_simpler_split_step_workspace_size(const rk_mech* mech, int64_t npts,
+                                            int32_t krylov_dim, const rk_opts* opts);
+int rk_simpler_split_step(const rk_mech* mech, double* U, double* h_cell, int64_t npts, double p,
+                          double dt, double D, double dx, double rtol, double atol,
+                          int32_t krylov_dim, const rk_opts* opts, int32_t* stats,
+                          void* workspace, size_t workspace_bytes, void* stream);
+
+/* Transport operator alone: TU = D d^2U/dx^2 (same discretisation). */
+int rk_diffusion_1d(const double* U, double* TU, int64_t npts, int32_t nvar, double D, double dx,
+                    void* stream);
+
+/* ---- diagnostics ---------------------------------------------------------------
+ * Throughput probes of the arithmetic units used by the roofline:
+ *  kind 0: FP64 FMA, 1: FP32 FMA, 2: FP64 exp().  Launches a dependent-FMA
+ *  grid sized to the device and returns the operation rate (ops/s) measured
+ *  with CUDA events in *ops_per_s.  Synchronous. */
+int rk_probe_throughput(int32_t kind, double* ops_per_s);
+
+const char* rk_status_string(int32_t code);
+int rk_last_error(char* buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ROK4E_H */

@@ -1,0 +1,223 @@
+"""GB300 ROK4E reaction step and Simpler balanced splitting (arXiv:1712.00953).
+
+Thin Python binding over the C ABI of ``librok4e.so`` (include/rok4e.h).  The
+functions keep the C names without the ``rk_`` prefix and only marshal
+arguments: tensors must be contiguous float64 CUDA tensors; every step of the
+computation runs in the library's CUDA kernels.  PyTorch supplies device
+memory and streams.  The library is loaded on first use; every call raises
+ImportError if it has not been built (there is no fallback path).
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native
+from ._native import RkMechDesc, RkOpts
+
+_LIB = None
+
+
+def _L():
+    global _LIB
+    if _LIB is None:
+        _LIB = _native.load()
+    return _LIB
+
+__all__ = ["Mechanism", "mech_load", "mech_validate", "chem_rhs", "chem_jvp", "rok4e_integrate",
+           "rok4e_workspace_size", "simpler_split_step", "simpler_split_step_workspace_size",
+           "diffusion_1d", "probe_throughput", "Opts", "RokError", "STATS_FIELDS"]
+
+STATS_FIELDS = ("n_accept", "n_reject", "n_rhs", "status")
+
+
+class RokError(RuntimeError):
+    pass
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        msg = _native.last_error(_L())
+        raise RokError(f"{what}: {_L().rk_status_string(rc).decode()} ({rc}): {msg}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, name, n_elems=None, dtype=torch.float64):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} CUDA tensor")
+    if n_elems is not None and t.numel() < n_elems:
+        raise ValueError(f"{name} has {t.numel()} elements, needs {n_elems}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class _HostDesc:
+    """Keeps the numpy arrays of a description alive while the C call reads them."""
+
+    def __init__(self, mech):
+        self.arrays = dict(
+            elem=np.ascontiguousarray(mech.elem, dtype=np.int32),
+            W=np.ascontiguousarray(mech.W, dtype=np.float64),
+            nasa=np.ascontiguousarray(mech.nasa, dtype=np.float64),
+            rxn_sp=np.ascontiguousarray(mech.rxn_sp, dtype=np.int32),
+            rxn_nu=np.ascontiguousarray(mech.rxn_nu, dtype=np.int32),
+            arrh=np.ascontiguousarray(mech.arrh, dtype=np.float64),
+            reversible=np.ascontiguousarray(mech.reversible, dtype=np.uint8),
+            kind=np.ascontiguousarray(mech.kind, dtype=np.int32),
+            eff=np.ascontiguousarray(mech.eff, dtype=np.float64),
+            falloff=np.ascontiguousarray(mech.falloff, dtype=np.float64),
+        )
+        a = self.arrays
+        self.desc = RkMechDesc(int(mech.W.shape[0]), int(mech.arrh.shape[0]),
+                               *(a[k].ctypes.data for k in ("elem", "W", "nasa", "rxn_sp", "rxn_nu", "arrh",
+                                                            "reversible", "kind", "eff", "falloff")))
+
+
+def mech_validate(mech) -> str:
+    """Host-only validation; returns '' when valid, else the reason."""
+    hd = _HostDesc(mech)
+    buf = ctypes.create_string_buffer(512)
+    rc = _L().rk_mech_validate(ctypes.byref(hd.desc), buf, 512)
+    return "" if rc == 0 else buf.value.decode(errors="replace")
+
+
+class Mechanism:
+    """A mechanism uploaded to the current CUDA device (rk_mech_load)."""
+
+    def __init__(self, mech):
+        hd = _HostDesc(mech)
+        h = ctypes.c_void_p()
+        _check(_L().rk_mech_load(ctypes.byref(hd.desc), ctypes.byref(h)), "rk_mech_load")
+        self.handle = h
+        self.n_species = int(mech.W.shape[0])
+        self.n_reactions = int(mech.arrh.shape[0])
+        self.n_state = self.n_species + 1
+
+    def info(self):
+        ns, nr, nb = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
+        _check(_L().rk_mech_info(self.handle, ctypes.byref(ns), ctypes.byref(nr), ctypes.byref(nb)), "rk_mech_info")
+        return ns.value, nr.value, nb.value
+
+    def free(self):
+        if self.handle:
+            _L().rk_mech_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def mech_load(mech) -> Mechanism:
+    return Mechanism(mech)
+
+
+class Opts:
+    """Integration options (rk_opts); None fields keep the library defaults."""
+
+    def __init__(self, jv_mode=0, max_attempts=0, lanes_per_cell=0, cells_per_block=0, h0=0.0, fixed_h=0.0,
+                 trace=None, events=None):
+        self.jv_mode, self.max_attempts = jv_mode, max_attempts
+        self.lanes_per_cell, self.cells_per_block = lanes_per_cell, cells_per_block
+        self.h0, self.fixed_h = h0, fixed_h
+        self.trace = trace  # CUDA float64 tensor [ncell, cap] or None
+        self.events = events  # (begin, end) torch.cuda.Event pair around the integration kernel
+
+    def c(self):
+        cap = 0 if self.trace is None else int(self.trace.shape[-1])
+        tp = None if self.trace is None else _dptr(self.trace, "trace")
+        eb = ee = None
+        if self.events is not None:
+            eb, ee = (ctypes.c_void_p(e.cuda_event) for e in self.events)
+        return RkOpts(self.jv_mode, self.max_attempts, self.lanes_per_cell, self.cells_per_block, self.h0,
+                      self.fixed_h, cap, 0, tp, eb, ee)
+
+
+def _ncell(Y, m):
+    if Y.dim() != 2 or Y.shape[1] != m.n_state:
+        raise ValueError(f"state must be [ncell, {m.n_state}]")
+    return int(Y.shape[0])
+
+
+def chem_rhs(m: Mechanism, Y, p, src=None, out=None, stream=None):
+    n = _ncell(Y, m)
+    out = torch.empty_like(Y) if out is None else out
+    _check(_L().rk_chem_rhs(m.handle, _dptr(Y, "Y"), _dptr(src, "src", Y.numel()), float(p),
+                            _dptr(out, "out", Y.numel()), n, _stream_ptr(stream)), "rk_chem_rhs")
+    return out
+
+
+def chem_jvp(m: Mechanism, Y, V, p, mode=0, out=None, stream=None):
+    n = _ncell(Y, m)
+    out = torch.empty_like(Y) if out is None else out
+    _check(_L().rk_chem_jvp(m.handle, _dptr(Y, "Y"), _dptr(V, "V", Y.numel()), float(p),
+                            _dptr(out, "out", Y.numel()), n, int(mode), _stream_ptr(stream)), "rk_chem_jvp")
+    return out
+
+
+def rok4e_workspace_size(m: Mechanism, ncell: int, krylov_dim: int, opts: Opts | None = None) -> int:
+    oc = (opts or Opts()).c()
+    return int(_L().rk_rok4e_workspace_size(m.handle, int(ncell), int(krylov_dim), ctypes.byref(oc)))
+
+
+def rok4e_integrate(m: Mechanism, Y, dt, rtol, atol, krylov_dim=4, *, p=101325.0, src=None, h_cell=None,
+                    opts: Opts | None = None, stats=None, workspace=None, stream=None):
+    """Integrate every row of Y over dt in place (rk_rok4e_integrate)."""
+    n = _ncell(Y, m)
+    oc = (opts or Opts()).c()
+    if workspace is None:
+        nb = rok4e_workspace_size(m, n, krylov_dim, opts)
+        workspace = torch.empty(nb, dtype=torch.uint8, device=Y.device)
+    _check(_L().rk_rok4e_integrate(m.handle, _dptr(Y, "Y"), _dptr(src, "src", Y.numel()),
+                                   _dptr(h_cell, "h_cell", n), n, float(p), float(dt), float(rtol), float(atol),
+                                   int(krylov_dim), ctypes.byref(oc),
+                                   _dptr(stats, "stats", 4 * n, torch.int32),
+                                   _dptr(workspace, "workspace", dtype=torch.uint8), workspace.numel(),
+                                   _stream_ptr(stream)), "rk_rok4e_integrate")
+    return Y
+
+
+def simpler_split_step_workspace_size(m: Mechanism, npts: int, krylov_dim: int, opts: Opts | None = None) -> int:
+    oc = (opts or Opts()).c()
+    return int(_L().rk_simpler_split_step_workspace_size(m.handle, int(npts), int(krylov_dim), ctypes.byref(oc)))
+
+
+def simpler_split_step(m: Mechanism, U, dt, D, dx, rtol, atol, krylov_dim=4, *, p=101325.0, h_cell=None,
+                       opts: Opts | None = None, stats=None, workspace=None, stream=None):
+    """One Simpler balanced split step of the 1-D reaction-diffusion system, in place."""
+    n = _ncell(U, m)
+    oc = (opts or Opts()).c()
+    if workspace is None:
+        nb = simpler_split_step_workspace_size(m, n, krylov_dim, opts)
+        workspace = torch.empty(nb, dtype=torch.uint8, device=U.device)
+    _check(_L().rk_simpler_split_step(m.handle, _dptr(U, "U"), _dptr(h_cell, "h_cell", n), n, float(p), float(dt),
+                                      float(D), float(dx), float(rtol), float(atol), int(krylov_dim),
+                                      ctypes.byref(oc), _dptr(stats, "stats", 4 * n, torch.int32),
+                                      _dptr(workspace, "workspace", dtype=torch.uint8), workspace.numel(),
+                                      _stream_ptr(stream)), "rk_simpler_split_step")
+    return U
+
+
+def diffusion_1d(U, D, dx, out=None, stream=None):
+    out = torch.empty_like(U) if out is None else out
+    _check(_L().rk_diffusion_1d(_dptr(U, "U"), _dptr(out, "out", U.numel()), int(U.shape[0]), int(U.shape[1]),
+                                float(D), float(dx), _stream_ptr(stream)), "rk_diffusion_1d")
+    return out
+
+
+def probe_throughput(kind: int) -> float:
+    """Measured rate (ops/s) of 0: FP64 FMA, 1: FP32 FMA, 2: FP64 exp."""
+    v = ctypes.c_double()
+    _check(_L().rk_probe_throughput(int(kind), ctypes.byref(v)), "rk_probe_throughput")
+    return v.value

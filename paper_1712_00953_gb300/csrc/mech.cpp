@@ -1,0 +1,269 @@
+// Host-side mechanism validation and packing (no CUDA).
+//
+// The checks enforce what the kernels rely on: species indices fit in 8 bits
+// (with one value left for the "empty slot" sentinel), at most two molecules
+// on each side of a reaction, integer element balance, positive molar masses
+// and pre-exponential factors, valid Troe parameters and NASA-7 polynomials
+// that are continuous at T_mid.  Packing converts A from cm-mol-s to SI units
+// (m^3/mol per concentration order), divides out the polynomial coefficients
+// the kernels use (see internal.h) and builds the species-major list of
+// stoichiometric coefficients used for the deterministic gather w = nu^T q.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "rok4e.h"
+
+namespace rk {
+namespace {
+
+constexpr double R_GAS = 8.314462618;
+
+int64_t align16(int64_t x) { return (x + 15) & ~int64_t(15); }
+
+bool fail(std::string* err, const char* fmt, int a = 0, int b = 0) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), fmt, a, b);
+  if (err) *err = buf;
+  return false;
+}
+
+// cp/R, h/RT, s/R of one NASA-7 coefficient set at T (validation only)
+void nasa_eval(const double* a, double T, double* cp, double* h, double* s) {
+  *cp = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
+  *h = a[0] + T * (a[1] / 2 + T * (a[2] / 3 + T * (a[3] / 4 + T * a[4] / 5))) + a[5] / T;
+  *s = a[0] * log(T) + T * (a[1] + T * (a[2] / 2 + T * (a[3] / 3 + T * a[4] / 4))) + a[6];
+}
+
+bool close_rel(double x, double y, double tol) {
+  return fabs(x - y) <= tol * std::max(1.0, std::max(fabs(x), fabs(y)));
+}
+
+}  // namespace
+
+bool pack_mechanism(const void* vdesc, HostMech* out, std::string* err) {
+  const rk_mech_desc* d = static_cast<const rk_mech_desc*>(vdesc);
+  if (!d) return fail(err, "null mechanism description");
+  const int ns = d->n_species, nr = d->n_reactions;
+  if (ns < 1 || ns > RK_MAX_SPECIES) return fail(err, "n_species %d outside 1..%d", ns, RK_MAX_SPECIES);
+  if (nr < 0 || nr > (1 << 20)) return fail(err, "n_reactions %d invalid", nr);
+  if (!d->elem || !d->W || !d->nasa) return fail(err, "null species array");
+  if (nr > 0 && (!d->rxn_sp || !d->rxn_nu || !d->arrh || !d->reversible || !d->kind))
+    return fail(err, "null reaction array");
+
+  // ---- species checks
+  for (int k = 0; k < ns; ++k) {
+    if (!(d->W[k] > 0.0) || !isfinite(d->W[k])) return fail(err, "species %d: molar mass must be > 0", k);
+    for (int e = 0; e < 4; ++e)
+      if (d->elem[4 * k + e] < 0) return fail(err, "species %d: negative atom count", k);
+    const double* nk = d->nasa + 17 * (size_t)k;
+    for (int i = 0; i < 17; ++i)
+      if (!isfinite(nk[i])) return fail(err, "species %d: non-finite NASA-7 entry %d", k, i);
+    if (!(nk[0] > 0.0 && nk[0] < nk[1] && nk[1] < nk[2]))
+      return fail(err, "species %d: NASA-7 ranges need 0 < T_lo < T_mid < T_hi", k);
+    double c1, h1, s1, c2, h2, s2;
+    nasa_eval(nk + 3, nk[1], &c1, &h1, &s1);
+    nasa_eval(nk + 10, nk[1], &c2, &h2, &s2);
+    if (!close_rel(c1, c2, 1e-3) || !close_rel(h1, h2, 1e-3) || !close_rel(s1, s2, 1e-3))
+      return fail(err, "species %d: NASA-7 polynomials discontinuous at T_mid", k);
+  }
+
+  // ---- reaction checks
+  int n_troe = 0, n_tb = 0;
+  for (int j = 0; j < nr; ++j) {
+    const int* sp = d->rxn_sp + 4 * (size_t)j;
+    const int* nu = d->rxn_nu + 4 * (size_t)j;
+    int mol_r = 0, mol_p = 0;
+    long long bal[4] = {0, 0, 0, 0};
+    for (int s = 0; s < 4; ++s) {
+      if (sp[s] < 0) {
+        if (nu[s] != 0) return fail(err, "reaction %d: coefficient on an empty slot %d", j, s);
+        continue;
+      }
+      if (sp[s] >= ns) return fail(err, "reaction %d: species index out of range in slot %d", j, s);
+      if (s < 2 && nu[s] >= 0) return fail(err, "reaction %d: reactant slot %d needs nu < 0", j, s);
+      if (s >= 2 && nu[s] <= 0) return fail(err, "reaction %d: product slot %d needs nu > 0", j, s);
+      if (s < 2) mol_r += -nu[s];
+      else mol_p += nu[s];
+      for (int e = 0; e < 4; ++e) bal[e] += (long long)nu[s] * d->elem[4 * (size_t)sp[s] + e];
+    }
+    if (sp[0] >= 0 && sp[1] >= 0 && sp[0] == sp[1]) return fail(err, "reaction %d: repeated reactant slot", j);
+    if (sp[2] >= 0 && sp[3] >= 0 && sp[2] == sp[3]) return fail(err, "reaction %d: repeated product slot", j);
+    if (mol_r < 1 || mol_p < 1) return fail(err, "reaction %d: needs at least one reactant and one product", j);
+    if (mol_r > 2 || mol_p > 2) return fail(err, "reaction %d: at most two molecules per side are supported", j);
+    for (int e = 0; e < 4; ++e)
+      if (bal[e] != 0) return fail(err, "reaction %d: element %d not balanced", j, e);
+    const double* ar = d->arrh + 3 * (size_t)j;
+    if (!(ar[0] > 0.0) || !isfinite(ar[0]) || !isfinite(ar[1]) || !isfinite(ar[2]))
+      return fail(err, "reaction %d: Arrhenius parameters must be finite with A > 0", j);
+    const int kind = d->kind[j];
+    if (kind < 0 || kind > 2) return fail(err, "reaction %d: kind %d not in {0,1,2}", j, kind);
+    if (kind > 0) {
+      if (!d->eff) return fail(err, "reaction %d: third-body efficiencies missing", j);
+      for (int k = 0; k < ns; ++k) {
+        const double e = d->eff[(size_t)j * ns + k];
+        if (!(e >= 0.0) || !isfinite(e)) return fail(err, "reaction %d: bad efficiency for species %d", j, k);
+      }
+    }
+    if (kind == 2) {
+      if (!d->falloff) return fail(err, "reaction %d: falloff parameters missing", j);
+      const double* fo = d->falloff + 7 * (size_t)j;
+      if (!(fo[0] > 0.0) || !isfinite(fo[0]) || !isfinite(fo[1]) || !isfinite(fo[2]))
+        return fail(err, "reaction %d: low-pressure Arrhenius parameters must be finite with A0 > 0", j);
+      if (!isfinite(fo[3]) || !(fo[4] > 0.0) || !(fo[5] > 0.0) || !isfinite(fo[6]) || !isfinite(fo[4]) ||
+          !isfinite(fo[5]))
+        return fail(err, "reaction %d: Troe parameters need finite a, T***>0, T*>0, T**", j);
+      ++n_troe;
+    }
+    if (kind == 1) ++n_tb;
+  }
+
+  // ---- reaction order: Troe, third body, elementary (stable)
+  std::vector<int32_t> perm;
+  perm.reserve(nr);
+  for (int want : {2, 1, 0})
+    for (int j = 0; j < nr; ++j)
+      if (d->kind[j] == want) perm.push_back(j);
+
+  // ---- species-major stoichiometry list (net coefficients, packed order)
+  std::vector<std::vector<std::pair<int, double>>> rows(ns);
+  for (int r = 0; r < nr; ++r) {
+    const int j = perm[r];
+    double net[RK_MAX_SPECIES + 1];
+    int touched[4];
+    int nt = 0;
+    for (int s = 0; s < 4; ++s) {
+      const int k = d->rxn_sp[4 * (size_t)j + s];
+      if (k < 0) continue;
+      bool seen = false;
+      for (int t = 0; t < nt; ++t) seen |= (touched[t] == k);
+      if (!seen) {
+        touched[nt++] = k;
+        net[k] = 0.0;
+      }
+      net[k] += d->rxn_nu[4 * (size_t)j + s];
+    }
+    for (int t = 0; t < nt; ++t)
+      if (net[touched[t]] != 0.0) rows[touched[t]].push_back({r, net[touched[t]]});
+  }
+  int nnz = 0;
+  for (auto& row : rows) nnz += (int)row.size();
+
+  // ---- layout
+  MechLayout L;
+  L.ns = ns;
+  L.nr = nr;
+  L.ntb = n_troe + n_tb;
+  L.nnz = nnz;
+  int64_t off = 0;
+  auto take = [&](int64_t bytes) {
+    const int64_t o = off;
+    off = align16(off + bytes);
+    return o;
+  };
+  L.off_W = take(8 * ns);
+  L.off_invW = take(8 * ns);
+  L.off_Tmid = take(8 * ns);
+  L.off_lo = take(8 * (int64_t)NCOEF * ns);
+  L.off_hi = take(8 * (int64_t)NCOEF * ns);
+  L.off_lnA = take(8 * (int64_t)nr);
+  L.off_b = take(8 * (int64_t)nr);
+  L.off_EaR = take(8 * (int64_t)nr);
+  L.off_eff = take(8 * (int64_t)L.ntb * ns);
+  L.off_fo = take(8 * (int64_t)L.ntb * FO_STRIDE);
+  L.off_csr_nu = take(8 * (int64_t)nnz);
+  L.off_slots = take(4 * (int64_t)nr);
+  L.off_meta = take(4 * (int64_t)nr);
+  L.off_csr_ptr = take(4 * (int64_t)(ns + 1));
+  L.off_csr_j = take(4 * (int64_t)nnz);
+  L.bytes = align16(off);
+
+  std::vector<unsigned char> buf((size_t)L.bytes, 0);
+  auto D = [&](int64_t o) { return reinterpret_cast<double*>(buf.data() + o); };
+  auto I = [&](int64_t o) { return reinterpret_cast<int32_t*>(buf.data() + o); };
+  auto U = [&](int64_t o) { return reinterpret_cast<uint32_t*>(buf.data() + o); };
+
+  for (int k = 0; k < ns; ++k) {
+    D(L.off_W)[k] = d->W[k];
+    D(L.off_invW)[k] = 1.0 / d->W[k];
+    const double* nk = d->nasa + 17 * (size_t)k;
+    D(L.off_Tmid)[k] = nk[1];
+    for (int range = 0; range < 2; ++range) {
+      const double* a = nk + 3 + 7 * range;
+      double* c = D(range == 0 ? L.off_lo : L.off_hi);
+      const double v[NCOEF] = {a[0],       a[1],       a[2],       a[3],       a[4],      a[1] / 2.0,
+                               a[2] / 3.0, a[3] / 4.0, a[4] / 5.0, a[5],       a[2] / 2.0, a[3] / 3.0,
+                               a[4] / 4.0, a[6],       2.0 * a[2], 3.0 * a[3], 4.0 * a[4]};
+      for (int i = 0; i < NCOEF; ++i) c[(size_t)i * ns + k] = v[i];
+    }
+  }
+  int slot_tb = 0;
+  for (int r = 0; r < nr; ++r) {
+    const int j = perm[r];
+    const int* sp = d->rxn_sp + 4 * (size_t)j;
+    const int* nu = d->rxn_nu + 4 * (size_t)j;
+    // expand to at most two molecules per side; ns is the empty sentinel
+    int mr[2] = {ns, ns}, mp[2] = {ns, ns};
+    int ir = 0, ip = 0;
+    int mol_r = 0, mol_p = 0;
+    for (int s = 0; s < 4; ++s) {
+      if (sp[s] < 0) continue;
+      const int n = nu[s] < 0 ? -nu[s] : nu[s];
+      for (int t = 0; t < n; ++t) {
+        if (s < 2) mr[ir++] = sp[s];
+        else mp[ip++] = sp[s];
+      }
+      if (s < 2) mol_r += n;
+      else mol_p += n;
+    }
+    U(L.off_slots)[r] = (uint32_t)mr[0] | ((uint32_t)mr[1] << 8) | ((uint32_t)mp[0] << 16) | ((uint32_t)mp[1] << 24);
+    const int kind = d->kind[j];
+    const int order = mol_r + (kind == 1 ? 1 : 0);  // concentration order of the forward rate
+    const double* ar = d->arrh + 3 * (size_t)j;
+    D(L.off_lnA)[r] = log(ar[0]) + (order - 1) * log(1e-6);
+    D(L.off_b)[r] = ar[1];
+    D(L.off_EaR)[r] = ar[2] / R_GAS;
+    int slot = 0;
+    if (kind > 0) {
+      slot = slot_tb++;
+      for (int k = 0; k < ns; ++k) D(L.off_eff)[(size_t)slot * ns + k] = d->eff[(size_t)j * ns + k];
+      if (kind == 2) {
+        const double* fo = d->falloff + 7 * (size_t)j;
+        double* o = D(L.off_fo) + (size_t)slot * FO_STRIDE;
+        o[0] = log(fo[0]) + mol_r * log(1e-6);  // k0 has one more concentration order
+        o[1] = fo[1];
+        o[2] = fo[2] / R_GAS;
+        o[3] = fo[3];
+        o[4] = 1.0 / fo[4];
+        o[5] = 1.0 / fo[5];
+        o[6] = fo[6];
+        o[7] = 0.0;
+      }
+    }
+    const int rev = d->reversible[j] ? 1 : 0;
+    const int dnu = mol_p - mol_r;  // -1, 0 or 1
+    I(L.off_meta)[r] = kind | (rev << 2) | ((dnu + 4) << 4) | (slot << 8);
+  }
+  int pos = 0;
+  for (int k = 0; k < ns; ++k) {
+    I(L.off_csr_ptr)[k] = pos;
+    for (auto& e : rows[k]) {
+      I(L.off_csr_j)[pos] = e.first;
+      D(L.off_csr_nu)[pos] = e.second;
+      ++pos;
+    }
+  }
+  I(L.off_csr_ptr)[ns] = pos;
+
+  out->L = L;
+  out->packed.swap(buf);
+  out->perm.swap(perm);
+  return true;
+}
+
+}  // namespace rk

@@ -1,0 +1,1316 @@
+// GB300 (sm_103a) kernels of the ROK4E reaction step and the Simpler split step.
+//
+// Mapping.  A "group" of G consecutive lanes of a warp (G = 32 by default:
+// one warp per cell) integrates one cell at a time.  Vector loops over the
+// N = Ns + 1 state entries, the Ns species and the Nr reactions are strided by
+// G; dot products and norms are butterfly (xor) shuffle reductions, which give
+// bit-identical results on every lane so that all lanes of a group take the
+// same control-flow decisions.  All per-cell vectors (state, f_n, the Krylov
+// basis, the four stage vectors, species and reaction work arrays) live in
+// shared memory next to a per-block copy of the mechanism.
+//
+// Batching.  The integration kernel is persistent: one wave of blocks sized
+// to the device, each group repeatedly takes the next cell index from a
+// global atomic counter (work stealing), so cells needing 1 or 200 substeps
+// share one launch without a tail of idle blocks.
+//
+// Arithmetic.  FP64 throughout.  Two restatements differ from a literal
+// transcription of the kinetics while computing the same quantities:
+//  * 1/Kc_j = exp(Delta G_j/RT) (RT/p_ref)^dnu_j is formed as a product of the
+//    per-species factors exp(+-g_k/RT) (2 exponentials per species instead of
+//    one per reaction), falling back to one exponential per reaction when a
+//    species has |g/RT| > 170 (where a product of four factors could overflow);
+//  * w = nu^T q is a gather over a species-major list (deterministic order).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+
+#include "internal.h"
+#include "rok4e.h"
+
+namespace rk {
+
+// ---------------------------------------------------------------- constants
+constexpr double R_GAS = 8.314462618;
+constexpr double P_REF = 101325.0;
+constexpr double GAM = 0.572816062482135;
+// Table coeff_rok4e (Sec. 4.2); b3 = 0, bhat4 = 0.
+constexpr double G21 = -0.602765307997356;
+constexpr double G31 = -1.389195789724843, G32 = 1.072950969011413;
+constexpr double G41 = 0.992356412977094, G42 = -1.390032613873701, G43 = -0.440875890223325;
+constexpr double A21 = 0.432364435748567;
+constexpr double A31 = -0.514211316876170, A32 = 1.382271144617360;
+constexpr double B1 = 0.194335256262729, B2 = 0.483167813989227, B3 = 0.0, B4 = 0.322496929748044;
+constexpr double BH1 = -0.217819895945721, BH2 = 1.03130847478467, BH3 = 0.186511421161047, BH4 = 0.0;
+// PI controller (Sec. 4.3), p = 4
+constexpr double PI_ALPHA = 0.7 / 4.0, PI_BETA = 0.4 / 4.0;
+constexpr double FAC_MIN = 0.2, FAC_MAX = 5.0, SAFETY = 0.8, ERR_FLOOR = 1e-10;
+constexpr double BREAKDOWN_TOL = 1e-12, T_END_TOL = 1e-12, H_MIN_FRAC = 1e-12;
+constexpr double G_OVERFLOW = 170.0;
+constexpr int MAXM = RK_MAX_KRYLOV;
+
+// --------------------------------------------------------------- error state
+static thread_local std::string g_last_error;
+static int set_error(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+static int cuda_error(cudaError_t e, const char* where) {
+  return set_error(RK_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------------- views
+struct MechView {
+  int ns, nr, ntb;
+  const double *W, *invW, *Tmid, *lo, *hi, *lnA, *bexp, *EaR, *eff, *fo, *csr_nu;
+  const uint32_t* slots;
+  const int32_t *meta, *csr_ptr, *csr_j;
+};
+
+__host__ __device__ inline MechView make_view(const unsigned char* base, const MechLayout& L) {
+  MechView m;
+  m.ns = L.ns;
+  m.nr = L.nr;
+  m.ntb = L.ntb;
+  m.W = reinterpret_cast<const double*>(base + L.off_W);
+  m.invW = reinterpret_cast<const double*>(base + L.off_invW);
+  m.Tmid = reinterpret_cast<const double*>(base + L.off_Tmid);
+  m.lo = reinterpret_cast<const double*>(base + L.off_lo);
+  m.hi = reinterpret_cast<const double*>(base + L.off_hi);
+  m.lnA = reinterpret_cast<const double*>(base + L.off_lnA);
+  m.bexp = reinterpret_cast<const double*>(base + L.off_b);
+  m.EaR = reinterpret_cast<const double*>(base + L.off_EaR);
+  m.eff = reinterpret_cast<const double*>(base + L.off_eff);
+  m.fo = reinterpret_cast<const double*>(base + L.off_fo);
+  m.csr_nu = reinterpret_cast<const double*>(base + L.off_csr_nu);
+  m.slots = reinterpret_cast<const uint32_t*>(base + L.off_slots);
+  m.meta = reinterpret_cast<const int32_t*>(base + L.off_meta);
+  m.csr_ptr = reinterpret_cast<const int32_t*>(base + L.off_csr_ptr);
+  m.csr_j = reinterpret_cast<const int32_t*>(base + L.off_csr_j);
+  return m;
+}
+
+// Per-cell shared-memory slot (offsets in doubles from the slot base).
+struct SlotLayout {
+  int N, ns, nr, ntb, M;
+  int u, src, fn, arg, fr, F, w, Q, K;        // N-vectors (Q: M of them, K: 4)
+  int C, dC, cp, hRT, dcp, gRT, E, Einv, om;  // species (+1 sentinel entry)
+  int q, kc, krc;                             // reactions
+  int tb;                                     // [ntb][4]: [M], dk/d[M], dlnk/dT, 1/Kc
+  int H, LU, piv, red;                        // small
+  int stride;
+};
+
+static SlotLayout make_slot(const MechLayout& L, int M) {
+  SlotLayout s;
+  s.N = L.ns + 1;
+  s.ns = L.ns;
+  s.nr = L.nr;
+  s.ntb = L.ntb;
+  s.M = M;
+  int o = 0;
+  auto take = [&](int n) {
+    const int r = o;
+    o += (n + 1) & ~1;  // keep 16-byte alignment
+    return r;
+  };
+  const int N = s.N, ns1 = L.ns + 1;
+  s.u = take(N);
+  s.src = take(N);
+  s.fn = take(N);
+  s.arg = take(N);
+  s.fr = take(N);
+  s.F = take(N);
+  s.w = take(N);
+  const int Nq = (N + 1) & ~1;  // stride between Krylov / stage vectors
+  s.Q = take(Nq * M);
+  s.K = take(4 * Nq);
+  s.C = take(ns1);
+  s.dC = take(ns1);
+  s.cp = take(ns1);
+  s.hRT = take(ns1);
+  s.dcp = take(ns1);
+  s.gRT = take(ns1);
+  s.E = take(ns1);
+  s.Einv = take(ns1);
+  s.om = take(ns1);
+  s.q = take(L.nr > 0 ? L.nr : 1);
+  s.kc = take(L.nr > 0 ? L.nr : 1);
+  s.krc = take(L.nr > 0 ? L.nr : 1);
+  s.tb = take(4 * (L.ntb > 0 ? L.ntb : 1));
+  s.H = take(MAXM * MAXM);
+  s.LU = take(MAXM * MAXM);
+  s.piv = take(MAXM);
+  s.red = take(4);
+  s.stride = (o + 3) & ~3;
+  return s;
+}
+
+// A group of G lanes inside one warp.
+template <int G>
+struct Grp {
+  unsigned mask;
+  int lane;
+  __device__ Grp() {
+    const int l = threadIdx.x & 31;
+    lane = l % G;
+    mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (l - lane));
+  }
+  __device__ __forceinline__ void sync() const { __syncwarp(mask); }
+  __device__ __forceinline__ double sum(double v) const {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
+    return v;
+  }
+  __device__ __forceinline__ double max(double v) const {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(mask, v, o, G));
+    return v;
+  }
+  __device__ __forceinline__ int any(int v) const {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(mask, v, o, G);
+    return v;
+  }
+};
+
+// Scalars of the last right-hand-side evaluation that the analytic
+// Jacobian-vector product needs (uniform across the group).
+struct CellScalars {
+  double T, invT, lnT, S, rho, invrho, cb, Sh;
+};
+
+struct SlotPtrs {
+  double *u, *src, *fn, *arg, *fr, *F, *w, *Q, *K;
+  double *C, *dC, *cp, *hRT, *dcp, *gRT, *E, *Einv, *om, *q, *kc, *krc, *tb;
+  double *H, *LU, *piv, *red;
+  int Nq;  // stride between Krylov / stage vectors
+};
+
+__device__ inline SlotPtrs slot_ptrs(double* b, const SlotLayout& s) {
+  SlotPtrs p;
+  p.u = b + s.u;
+  p.src = b + s.src;
+  p.fn = b + s.fn;
+  p.arg = b + s.arg;
+  p.fr = b + s.fr;
+  p.F = b + s.F;
+  p.w = b + s.w;
+  p.Q = b + s.Q;
+  p.K = b + s.K;
+  p.C = b + s.C;
+  p.dC = b + s.dC;
+  p.cp = b + s.cp;
+  p.hRT = b + s.hRT;
+  p.dcp = b + s.dcp;
+  p.gRT = b + s.gRT;
+  p.E = b + s.E;
+  p.Einv = b + s.Einv;
+  p.om = b + s.om;
+  p.q = b + s.q;
+  p.kc = b + s.kc;
+  p.krc = b + s.krc;
+  p.tb = b + s.tb;
+  p.H = b + s.H;
+  p.LU = b + s.LU;
+  p.piv = b + s.piv;
+  p.red = b + s.red;
+  p.Nq = (s.N + 1) & ~1;
+  return p;
+}
+
+// ------------------------------------------------------------ chemistry RHS
+// out = f(uu) + src (src may be null).  uu, out: N-vectors in shared memory
+// (out must not alias uu).  When `cache` is set, the values the analytic
+// Jacobian-vector product reuses are kept (rate coefficients, w, d(cp/R)/dT
+// and the cell scalars).  Not inlined: chem_rhs and the integrator execute the
+// same instructions, so R(u) - R(u) is exactly zero in a steady-state cell.
+template <int G>
+__device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, const double* uu,
+                                      const double* src, double p, double* out, bool cache,
+                                      CellScalars* cs) {
+  const Grp<G> g;
+  const int ns = m.ns;
+  const double T = uu[ns];
+  const double invT = 1.0 / T;
+  const double lnT = log(T);
+  // species pass 1: thermo, Gibbs factors, sum Y/W
+  double S = 0.0, gmax = 0.0;
+  for (int k = g.lane; k < ns; k += G) {
+    const double* c = (T < m.Tmid[k]) ? m.lo : m.hi;
+    const double a1 = c[k], a2 = c[ns + k], a3 = c[2 * ns + k], a4 = c[3 * ns + k], a5 = c[4 * ns + k];
+    const double cp = fma(fma(fma(fma(a5, T, a4), T, a3), T, a2), T, a1);
+    const double hp = fma(fma(fma(c[8 * ns + k], T, c[7 * ns + k]), T, c[6 * ns + k]), T, c[5 * ns + k]);
+    const double hrt = fma(hp, T, a1) + c[9 * ns + k] * invT;
+    const double sp = fma(fma(fma(c[12 * ns + k], T, c[11 * ns + k]), T, c[10 * ns + k]), T, a2);
+    const double sr = fma(a1, lnT, fma(sp, T, c[13 * ns + k]));
+    const double grt = hrt - sr;
+    s.cp[k] = cp;
+    s.hRT[k] = hrt;
+    s.gRT[k] = grt;
+    gmax = fmax(gmax, fabs(grt));
+    if (cache) s.dcp[k] = fma(fma(c[16 * ns + k], T, c[15 * ns + k]), T, c[14 * ns + k]) * T + a2;
+    S = fma(uu[k], m.invW[k], S);
+  }
+  S = g.sum(S);
+  gmax = g.max(gmax);
+  const bool direct_kc = !(gmax <= G_OVERFLOW);  // also true for NaN
+  const double rho = p / (R_GAS * T * S);
+  const double invrho = 1.0 / rho;
+  for (int k = g.lane; k < ns; k += G) {
+    s.C[k] = rho * uu[k] * m.invW[k];
+    if (!direct_kc) {
+      s.E[k] = exp(s.gRT[k]);
+      s.Einv[k] = exp(-s.gRT[k]);
+    }
+  }
+  g.sync();
+  // reactions: rate coefficients and rates of progress
+  const double RTp = R_GAS * T / P_REF;
+  const double invRTp = P_REF / (R_GAS * T);
+  const double lnRTp = log(RTp);
+  for (int j = g.lane; j < m.nr; j += G) {
+    const uint32_t sl = m.slots[j];
+    const int ra = sl & 255, rb = (sl >> 8) & 255, pa = (sl >> 16) & 255, pb = sl >> 24;
+    const int meta = m.meta[j];
+    const int kind = meta & 3;
+    const bool rev = (meta >> 2) & 1;
+    const int dnu = ((meta >> 4) & 15) - 4;
+    double k = exp(m.lnA[j] + m.bexp[j] * lnT - m.EaR[j] * invT);
+    const double Pf = s.C[ra] * s.C[rb];
+    const double Pb = s.C[pa] * s.C[pb];
+    double rfac = 0.0;  // 1/Kc
+    if (rev) {
+      if (!direct_kc) {
+        const double pf = dnu > 0 ? RTp : (dnu < 0 ? invRTp : 1.0);
+        rfac = s.E[pa] * s.Einv[ra] * s.E[pb] * s.Einv[rb] * pf;
+      } else {
+        rfac = exp(s.gRT[pa] + s.gRT[pb] - s.gRT[ra] - s.gRT[rb] + dnu * lnRTp);
+      }
+    }
+    double mfac = 1.0;
+    if (kind != 0) {
+      const int slot = meta >> 8;
+      const double* e = m.eff + (size_t)slot * ns;
+      double Mc = 0.0;
+      for (int q = 0; q < ns; ++q) Mc = fma(e[q], s.C[q], Mc);
+      double dkdM = 0.0, dlnk = (m.bexp[j] + m.EaR[j] * invT) * invT;
+      if (kind == 1) {
+        mfac = Mc;
+      } else {
+        const double* fo = m.fo + (size_t)slot * FO_STRIDE;
+        const double k0 = exp(fo[0] + fo[1] * lnT - fo[2] * invT);
+        const double dlnk0 = (fo[1] + fo[2] * invT) * invT;
+        double Pr = k0 * Mc / k;
+        if (!(Pr > 1e-300)) Pr = 1e-300;
+        const double a = fo[3];
+        const double e3 = exp(-T * fo[4]), e1 = exp(-T * fo[5]);
+        const double e2 = fo[6] > 0.0 ? exp(-fo[6] * invT) : 0.0;
+        const double Fc = (1.0 - a) * e3 + a * e1 + e2;
+        const double lFc = log10(Fc);
+        const double cc = -0.4 - 0.67 * lFc;
+        const double nn = 0.75 - 1.27 * lFc;
+        const double L = log10(Pr);
+        const double x = L + cc;
+        const double D = nn - 0.14 * x;
+        const double f1 = x / D;
+        const double den = 1.0 + f1 * f1;
+        const double lF = lFc / den;
+        const double F = exp10(lF);
+        const double onePr = 1.0 + Pr;
+        const double dlF_dL = -lFc * 2.0 * f1 / (den * den) * nn / (D * D);
+        const double df1 = (-0.67 * D + 1.1762 * x) / (D * D);
+        const double dlF_dlFc = 1.0 / den - lFc * 2.0 * f1 / (den * den) * df1;
+        const double dFc = -(1.0 - a) * fo[4] * e3 - a * fo[5] * e1 + (fo[6] > 0.0 ? fo[6] * invT * invT * e2 : 0.0);
+        const double gg = 1.0 / onePr + dlF_dL;
+        dlnk = dlnk + gg * (dlnk0 - dlnk) + dlF_dlFc * dFc / Fc;
+        dkdM = k0 * F / onePr * gg;
+        k = k * Pr / onePr * F;
+      }
+      if (cache) {
+        double* t = s.tb + 4 * (meta >> 8);
+        t[0] = Mc;
+        t[1] = dkdM;
+        t[2] = dlnk;
+        t[3] = rfac;
+      }
+    }
+    const double kr = k * rfac;
+    s.q[j] = mfac * (k * Pf - kr * Pb);
+    if (cache) {
+      s.kc[j] = k;
+      s.krc[j] = kr;
+    }
+  }
+  g.sync();
+  // species pass 2: w = nu^T q, dY/dt and the sums of the temperature equation
+  double Sh = 0.0, cb = 0.0;
+  for (int k = g.lane; k < ns; k += G) {
+    double om = 0.0;
+    const int e0 = m.csr_ptr[k], e1 = m.csr_ptr[k + 1];
+    for (int e = e0; e < e1; ++e) om = fma(m.csr_nu[e], s.q[m.csr_j[e]], om);
+    if (cache) s.om[k] = om;
+    const double r = __dmul_rn(__dmul_rn(m.W[k], om), invrho);
+    out[k] = src ? __dadd_rn(r, src[k]) : r;
+    Sh = fma(s.hRT[k], om, Sh);
+    cb = fma(uu[k] * s.cp[k], m.invW[k], cb);
+  }
+  Sh = g.sum(Sh);
+  cb = g.sum(cb);
+  if (g.lane == 0) {
+    const double r = -T * Sh / (rho * cb);
+    out[ns] = src ? __dadd_rn(r, src[ns]) : r;
+  }
+  if (cache) {
+    cs->T = T;
+    cs->invT = invT;
+    cs->lnT = lnT;
+    cs->S = S;
+    cs->rho = rho;
+    cs->invrho = invrho;
+    cs->cb = cb;
+    cs->Sh = Sh;
+  }
+  g.sync();
+}
+
+// Analytic Jacobian-vector product out = J(u_n) v, using the values cached by
+// the last rhs_eval(..., cache = true) at u_n.  v, out: N-vectors.
+template <int G>
+__device__ __noinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, const double* uu,
+                                      const CellScalars& cs, const double* v, double* out) {
+  const Grp<G> g;
+  const int ns = m.ns;
+  const double vT = v[ns];
+  const double T = cs.T, invT = cs.invT;
+  double a = 0.0;
+  for (int k = g.lane; k < ns; k += G) a = fma(v[k], m.invW[k], a);
+  a = g.sum(a);
+  const double drr = -(a / cs.S + vT * invT);  // d rho / rho
+  for (int k = g.lane; k < ns; k += G) s.dC[k] = fma(s.C[k], drr, cs.rho * v[k] * m.invW[k]);
+  g.sync();
+  for (int j = g.lane; j < m.nr; j += G) {
+    const uint32_t sl = m.slots[j];
+    const int ra = sl & 255, rb = (sl >> 8) & 255, pa = (sl >> 16) & 255, pb = sl >> 24;
+    const int meta = m.meta[j];
+    const int kind = meta & 3;
+    const int dnu = ((meta >> 4) & 15) - 4;
+    const double Pf = s.C[ra] * s.C[rb];
+    const double Pb = s.C[pa] * s.C[pb];
+    const double dPf = fma(s.dC[ra], s.C[rb], s.C[ra] * s.dC[rb]);
+    const double dPb = fma(s.dC[pa], s.C[pb], s.C[pa] * s.dC[pb]);
+    const double k = s.kc[j], kr = s.krc[j];
+    double dlnk = (m.bexp[j] + m.EaR[j] * invT) * invT;
+    const double dlnKc = (s.hRT[pa] + s.hRT[pb] - s.hRT[ra] - s.hRT[rb] - dnu) * invT;
+    if (kind == 2) dlnk = s.tb[4 * (meta >> 8) + 2];
+    double dq = k * fma(dlnk * vT, Pf, dPf) - kr * fma((dlnk - dlnKc) * vT, Pb, dPb);
+    if (kind != 0) {
+      const double* t = s.tb + 4 * (meta >> 8);
+      const double* e = m.eff + (size_t)(meta >> 8) * ns;
+      double dM = 0.0;
+      for (int q = 0; q < ns; ++q) dM = fma(e[q], s.dC[q], dM);
+      if (kind == 1) dq = t[0] * dq + dM * (k * Pf - kr * Pb);
+      else dq = dq + t[1] * dM * (Pf - t[3] * Pb);
+    }
+    s.q[j] = dq;
+  }
+  g.sync();
+  double dSh = 0.0, dcb = 0.0;
+  for (int k = g.lane; k < ns; k += G) {
+    double dom = 0.0;
+    const int e0 = m.csr_ptr[k], e1 = m.csr_ptr[k + 1];
+    for (int e = e0; e < e1; ++e) dom = fma(m.csr_nu[e], s.q[m.csr_j[e]], dom);
+    const double om = s.om[k];
+    out[k] = m.W[k] * (dom - om * drr) * cs.invrho;
+    dSh = fma(s.hRT[k], dom, fma((s.cp[k] - s.hRT[k]) * invT * vT, om, dSh));
+    dcb = fma(fma(uu[k] * s.dcp[k], vT, v[k] * s.cp[k]), m.invW[k], dcb);
+  }
+  dSh = g.sum(dSh);
+  dcb = g.sum(dcb);
+  if (g.lane == 0) {
+    out[ns] = (-(vT * cs.Sh + T * dSh) + T * cs.Sh * (drr + dcb / cs.cb)) / (cs.rho * cs.cb);
+  }
+  g.sync();
+}
+
+// ----------------------------------------------------------------- helpers
+template <int G>
+__device__ inline double group_dot(const Grp<G>& g, const double* a, const double* b, int N) {
+  double acc = 0.0;
+  for (int e = g.lane; e < N; e += G) acc = fma(a[e], b[e], acc);
+  return g.sum(acc);
+}
+
+// J v into out: analytic, or forward difference with the oracle's increment.
+template <int G>
+__device__ inline void apply_jv(const MechView& m, const SlotPtrs& s, const CellScalars& cs, int jv_mode,
+                                double p, double unorm, const double* v, double* out, int* n_rhs) {
+  const Grp<G> g;
+  const int N = m.ns + 1;
+  if (jv_mode == 0) {
+    jvp_eval<G>(m, s, s.u, cs, v, out);
+    return;
+  }
+  const double nv = sqrt(group_dot<G>(g, v, v, N));
+  if (nv == 0.0) {
+    for (int e = g.lane; e < N; e += G) out[e] = 0.0;
+    g.sync();
+    return;
+  }
+  const double d = sqrt(2.220446049250313e-16) * (1.0 + unorm) / nv;
+  for (int e = g.lane; e < N; e += G) s.arg[e] = s.u[e] + d * v[e];
+  g.sync();
+  CellScalars dummy;
+  rhs_eval<G>(m, s, s.arg, s.src, p, out, false, &dummy);
+  *n_rhs += 1;
+  for (int e = g.lane; e < N; e += G) out[e] = (out[e] - s.fn[e]) / d;
+  g.sync();
+}
+
+// Arnoldi with classical Gram-Schmidt and one reorthogonalisation pass on
+// K_M(J_n, f_n) (Sec. 4.1).  Returns the dimension m <= M; Q and H in the slot.
+template <int G>
+__device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& cs, int M, int jv_mode,
+                       double p, int* n_rhs) {
+  const Grp<G> g;
+  const int N = m.ns + 1;
+  const int Nq = s.Nq;
+  if (M > N) M = N;
+  for (int i = g.lane; i < MAXM * MAXM; i += G) s.H[i] = 0.0;
+  const double beta = sqrt(group_dot<G>(g, s.fn, s.fn, N));
+  if (M <= 0 || !(beta > 0.0) || !isfinite(beta)) {
+    g.sync();
+    return 0;
+  }
+  double unorm = 0.0;
+  if (jv_mode != 0) unorm = sqrt(group_dot<G>(g, s.u, s.u, N));
+  for (int e = g.lane; e < N; e += G) s.Q[e] = s.fn[e] / beta;
+  g.sync();
+  int mdim = M;
+  for (int j = 0; j < M; ++j) {
+    apply_jv<G>(m, s, cs, jv_mode, p, unorm, s.Q + j * Nq, s.w, n_rhs);
+    const double w0 = sqrt(group_dot<G>(g, s.w, s.w, N));
+    double hcol[MAXM];
+#pragma unroll
+    for (int i = 0; i < MAXM; ++i) hcol[i] = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+      double part[MAXM];
+#pragma unroll
+      for (int i = 0; i < MAXM; ++i) part[i] = 0.0;
+      for (int e = g.lane; e < N; e += G) {
+        const double we = s.w[e];
+#pragma unroll
+        for (int i = 0; i < MAXM; ++i)
+          if (i <= j) part[i] = fma(s.Q[i * Nq + e], we, part[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < MAXM; ++i)
+        if (i <= j) part[i] = g.sum(part[i]);
+      for (int e = g.lane; e < N; e += G) {
+        double we = s.w[e];
+#pragma unroll
+        for (int i = 0; i < MAXM; ++i)
+          if (i <= j) we = fma(-part[i], s.Q[i * Nq + e], we);
+        s.w[e] = we;
+      }
+#pragma unroll
+      for (int i = 0; i < MAXM; ++i) hcol[i] += part[i];
+    }
+    const double hn = sqrt(group_dot<G>(g, s.w, s.w, N));
+    if (g.lane == 0) {
+#pragma unroll
+      for (int i = 0; i < MAXM; ++i)
+        if (i <= j) s.H[i * MAXM + j] = hcol[i];
+    }
+    if (j + 1 == M) break;
+    if (hn <= BREAKDOWN_TOL * w0 || hn == 0.0) {
+      mdim = j + 1;
+      break;
+    }
+    if (g.lane == 0) s.H[(j + 1) * MAXM + j] = hn;
+    for (int e = g.lane; e < N; e += G) s.Q[(j + 1) * Nq + e] = s.w[e] / hn;
+    g.sync();
+  }
+  g.sync();
+  return mdim;
+}
+
+// LU factorisation with partial pivoting of I - h gamma H (m x m), by lane 0.
+template <int G>
+__device__ inline void factor_small(const SlotPtrs& s, int mdim, double h) {
+  const Grp<G> g;
+  if (g.lane == 0) {
+    double* A = s.LU;
+    for (int i = 0; i < mdim; ++i)
+      for (int j = 0; j < mdim; ++j) A[i * MAXM + j] = (i == j ? 1.0 : 0.0) - h * GAM * s.H[i * MAXM + j];
+    for (int c = 0; c < mdim; ++c) {
+      int pr = c;
+      double best = fabs(A[c * MAXM + c]);
+      for (int r = c + 1; r < mdim; ++r)
+        if (fabs(A[r * MAXM + c]) > best) {
+          best = fabs(A[r * MAXM + c]);
+          pr = r;
+        }
+      s.piv[c] = (double)pr;
+      if (pr != c)
+        for (int j = 0; j < mdim; ++j) {
+          const double t = A[c * MAXM + j];
+          A[c * MAXM + j] = A[pr * MAXM + j];
+          A[pr * MAXM + j] = t;
+        }
+      const double inv = 1.0 / A[c * MAXM + c];
+      for (int r = c + 1; r < mdim; ++r) {
+        const double l = A[r * MAXM + c] * inv;
+        A[r * MAXM + c] = l;
+        for (int j = c + 1; j < mdim; ++j) A[r * MAXM + j] = fma(-l, A[c * MAXM + j], A[r * MAXM + j]);
+      }
+    }
+  }
+  g.sync();
+}
+
+// Solve (I - h gamma H) y = z in place (every lane, redundantly).
+__device__ inline void solve_small(const SlotPtrs& s, int mdim, double* z) {
+  for (int c = 0; c < mdim; ++c) {
+    const int pr = (int)s.piv[c];
+    if (pr != c) {
+      const double t = z[c];
+      z[c] = z[pr];
+      z[pr] = t;
+    }
+  }
+  for (int r = 1; r < mdim; ++r)
+    for (int c = 0; c < r; ++c) z[r] = fma(-s.LU[r * MAXM + c], z[c], z[r]);
+  for (int r = mdim - 1; r >= 0; --r) {
+    for (int c = r + 1; c < mdim; ++c) z[r] = fma(-s.LU[r * MAXM + c], z[c], z[r]);
+    z[r] = z[r] / s.LU[r * MAXM + r];
+  }
+}
+
+// ------------------------------------------------------- integration kernel
+struct IntegrateParams {
+  const unsigned char* mech;  // packed mechanism (global)
+  MechLayout L;
+  SlotLayout S;
+  double* Y;
+  const double* src;
+  double* h_cell;
+  int64_t ncell;
+  double p, dt, rtol, atol, h0, fixed_h;
+  int M, jv_mode, max_attempts, trace_cap;
+  double* trace;
+  int32_t* stats;
+  unsigned long long* counter;
+};
+
+template <int G>
+__device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const IntegrateParams& P, int64_t cell) {
+  const Grp<G> g;
+  const int ns = m.ns, N = ns + 1, Nq = s.Nq;
+  for (int e = g.lane; e < N; e += G) {
+    s.u[e] = P.Y[cell * N + e];
+    s.src[e] = P.src ? P.src[cell * N + e] : 0.0;
+  }
+  g.sync();
+  const double* srcp = P.src ? s.src : nullptr;
+  const bool fixed = P.fixed_h > 0.0;
+  const double dt = P.dt;
+  double h = P.h0 > 0.0 ? P.h0 : dt;
+  if (P.h_cell) {
+    const double hc = P.h_cell[cell];
+    if (hc > 0.0) h = hc;
+  }
+  if (fixed) h = P.fixed_h;
+  const long long n_fixed = fixed ? llround(dt / P.fixed_h) : 0;
+  double t = 0.0, err_prev = 1.0, h_last = h;
+  int n_acc = 0, n_rej = 0, n_rhs = 0, status = RK_CELL_OK, n_att = 0;
+  CellScalars cs;
+  rhs_eval<G>(m, s, s.u, srcp, P.p, s.fn, true, &cs);
+  n_rhs += 1;
+  int mdim = arnoldi<G>(m, s, cs, P.M, P.jv_mode, P.p, &n_rhs);
+  double* K0 = s.K;
+  double* K1 = s.K + Nq;
+  double* K2 = s.K + 2 * Nq;
+  double* K3 = s.K + 3 * Nq;
+  constexpr double g21 = G21 / GAM, g31 = G31 / GAM, g32 = G32 / GAM;
+  constexpr double g41 = G41 / GAM, g42 = G42 / GAM, g43 = G43 / GAM;
+  while (true) {
+    if (fixed) {
+      if (n_acc >= n_fixed) break;
+    } else if (dt - t <= T_END_TOL * dt) {
+      break;
+    }
+    if (n_att >= P.max_attempts) {
+      status = RK_CELL_MAX_ATTEMPTS;
+      break;
+    }
+    if (!fixed) h = fmin(h, dt - t);
+    factor_small<G>(s, mdim, h);
+    // ---- four stages (Algorithm 1); f is evaluated at stages 2 and 3 only
+    for (int i = 0; i < 4; ++i) {
+      const double* fi;
+      if (i == 0) {
+        fi = s.fn;
+      } else if (i == 1 || i == 2) {
+        for (int e = g.lane; e < N; e += G) {
+          const double acc = (i == 1) ? A21 * K0[e] : fma(A32, K1[e], A31 * K0[e]);
+          s.arg[e] = s.u[e] + h * acc;
+        }
+        g.sync();
+        rhs_eval<G>(m, s, s.arg, srcp, P.p, s.fr, false, &cs);
+        n_rhs += 1;
+        fi = s.fr;
+      } else {
+        fi = s.fr;  // alpha_4j = alpha_3j: same argument as stage 3
+      }
+      double* Ki = s.K + i * Nq;
+      double part[MAXM];
+#pragma unroll
+      for (int l = 0; l < MAXM; ++l) part[l] = 0.0;
+      for (int e = g.lane; e < N; e += G) {
+        double Ge = 0.0;
+        if (i == 1) Ge = g21 * K0[e];
+        else if (i == 2) Ge = fma(g32, K1[e], g31 * K0[e]);
+        else if (i == 3) Ge = fma(g43, K2[e], fma(g42, K1[e], g41 * K0[e]));
+        const double Fe = fi[e] + Ge;
+        s.F[e] = Fe;
+        s.w[e] = Ge;
+#pragma unroll
+        for (int l = 0; l < MAXM; ++l)
+          if (l < mdim) part[l] = fma(s.Q[l * Nq + e], Fe, part[l]);
+      }
+      double z[MAXM], y[MAXM];
+#pragma unroll
+      for (int l = 0; l < MAXM; ++l) {
+        z[l] = (l < mdim) ? g.sum(part[l]) : 0.0;
+        y[l] = z[l];
+      }
+      solve_small(s, mdim, y);
+      for (int e = g.lane; e < N; e += G) {
+        double acc = 0.0;
+#pragma unroll
+        for (int l = 0; l < MAXM; ++l)
+          if (l < mdim) acc = fma(s.Q[l * Nq + e], z[l] - y[l], acc);
+        Ki[e] = (s.F[e] - acc) - s.w[e];
+      }
+      g.sync();
+    }
+    // ---- solutions, error estimate
+    double part = 0.0;
+    int bad = 0;
+    for (int e = g.lane; e < N; e += G) {
+      const double k0 = K0[e], k1 = K1[e], k2 = K2[e], k3 = K3[e];
+      const double ue = s.u[e];
+      const double us = ue + h * fma(B4, k3, fma(B3, k2, fma(B2, k1, B1 * k0)));
+      const double uh = ue + h * fma(BH4, k3, fma(BH3, k2, fma(BH2, k1, BH1 * k0)));
+      const double d = (uh - us) / (P.atol + P.rtol * fabs(us));
+      part = fma(d, d, part);
+      bad |= !isfinite(us);
+      s.arg[e] = us;
+    }
+    const double err = sqrt(g.sum(part) / N);
+    bad = g.any(bad);
+    const int att = n_att;
+    n_att += 1;
+    bool accept;
+    double hnew;
+    if (fixed) {
+      accept = true;
+      hnew = h;
+    } else {
+      double fac;
+      if (!isfinite(err)) {
+        fac = FAC_MIN;
+      } else {
+        const double ee = fmax(err, ERR_FLOOR);
+        fac = fmin(FAC_MAX, fmax(FAC_MIN, SAFETY * pow(err_prev, PI_BETA) / pow(ee, PI_ALPHA)));
+      }
+      hnew = h * fac;
+      accept = isfinite(err) && err <= 1.0;
+    }
+    if (P.trace && att < P.trace_cap && g.lane == 0) P.trace[cell * P.trace_cap + att] = accept ? h : -h;
+    if (accept) {
+      if (bad) {
+        status = RK_CELL_NONFINITE;
+        break;
+      }
+      for (int e = g.lane; e < N; e += G) s.u[e] = s.arg[e];
+      g.sync();
+      t += h;
+      if (!fixed) err_prev = fmax(err, ERR_FLOOR);
+      n_acc += 1;
+      h_last = hnew;
+      h = hnew;
+      const bool done = fixed ? (n_acc >= n_fixed) : (dt - t <= T_END_TOL * dt);
+      if (!done) {
+        rhs_eval<G>(m, s, s.u, srcp, P.p, s.fn, true, &cs);
+        n_rhs += 1;
+        mdim = arnoldi<G>(m, s, cs, P.M, P.jv_mode, P.p, &n_rhs);
+      }
+    } else {
+      n_rej += 1;
+      h = hnew;
+      if (h < H_MIN_FRAC * dt) {
+        status = RK_CELL_STEP_UNDERFLOW;
+        break;
+      }
+    }
+  }
+  for (int e = g.lane; e < N; e += G) P.Y[cell * N + e] = s.u[e];
+  if (g.lane == 0) {
+    if (P.h_cell) P.h_cell[cell] = h_last;
+    if (P.stats) {
+      P.stats[4 * cell + 0] = n_acc;
+      P.stats[4 * cell + 1] = n_rej;
+      P.stats[4 * cell + 2] = n_rhs;
+      P.stats[4 * cell + 3] = status;
+    }
+  }
+  g.sync();
+}
+
+// Copy the packed mechanism into shared memory (16-byte vector copies).
+__device__ inline void load_mech(unsigned char* dst, const unsigned char* src, int64_t bytes) {
+  const int64_t n16 = bytes / 16;
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+  for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) d4[i] = s4[i];
+}
+
+__device__ inline void init_sentinels(const SlotPtrs& s, int ns, int lane) {
+  if (lane == 0) {
+    s.C[ns] = 1.0;
+    s.dC[ns] = 0.0;
+    s.hRT[ns] = 0.0;
+    s.gRT[ns] = 0.0;
+    s.E[ns] = 1.0;
+    s.Einv[ns] = 1.0;
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(512) rok4e_integrate_kernel(IntegrateParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  load_mech(smem, P.mech, P.L.bytes);
+  __syncthreads();
+  const MechView m = make_view(smem, P.L);
+  const Grp<G> g;
+  const int gid = threadIdx.x / G;
+  double* base = reinterpret_cast<double*>(smem + P.L.bytes) + (size_t)gid * P.S.stride;
+  const SlotPtrs s = slot_ptrs(base, P.S);
+  init_sentinels(s, m.ns, g.lane);
+  g.sync();
+  while (true) {
+    unsigned long long cell = 0;
+    if (g.lane == 0) cell = atomicAdd(P.counter, 1ull);
+    cell = __shfl_sync(g.mask, cell, 0, G);
+    if (cell >= (unsigned long long)P.ncell) break;
+    integrate_cell<G>(m, s, P, (int64_t)cell);
+  }
+}
+
+// One group per cell: f(u) + src, or J(u) v.
+struct PointParams {
+  const unsigned char* mech;
+  MechLayout L;
+  SlotLayout S;
+  const double* Y;
+  const double* src;
+  const double* V;
+  double* out;
+  int64_t ncell;
+  double p;
+  int mode;  // 0 rhs, 1 analytic jvp, 2 finite-difference jvp
+};
+
+template <int G>
+__global__ void __launch_bounds__(512) chem_point_kernel(PointParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  load_mech(smem, P.mech, P.L.bytes);
+  __syncthreads();
+  const MechView m = make_view(smem, P.L);
+  const Grp<G> g;
+  const int gid = threadIdx.x / G;
+  const int gpb = blockDim.x / G;
+  const int64_t cell = (int64_t)blockIdx.x * gpb + gid;
+  if (cell >= P.ncell) return;
+  double* base = reinterpret_cast<double*>(smem + P.L.bytes) + (size_t)gid * P.S.stride;
+  const SlotPtrs s = slot_ptrs(base, P.S);
+  init_sentinels(s, m.ns, g.lane);
+  const int N = m.ns + 1;
+  for (int e = g.lane; e < N; e += G) {
+    s.u[e] = P.Y[cell * N + e];
+    s.src[e] = P.src ? P.src[cell * N + e] : 0.0;
+    if (P.V) s.F[e] = P.V[cell * N + e];
+  }
+  g.sync();
+  CellScalars cs;
+  if (P.mode == 0) {
+    rhs_eval<G>(m, s, s.u, P.src ? s.src : nullptr, P.p, s.fr, false, &cs);
+    for (int e = g.lane; e < N; e += G) P.out[cell * N + e] = s.fr[e];
+    return;
+  }
+  rhs_eval<G>(m, s, s.u, nullptr, P.p, s.fn, true, &cs);
+  int n_rhs = 0;
+  double unorm = 0.0;
+  if (P.mode == 2) unorm = sqrt(group_dot<G>(g, s.u, s.u, N));
+  // s.src is zero here, so the finite difference sees the bare source term
+  apply_jv<G>(m, s, cs, P.mode == 1 ? 0 : 1, P.p, unorm, s.F, s.w, &n_rhs);
+  for (int e = g.lane; e < N; e += G) P.out[cell * N + e] = s.w[e];
+}
+
+// ---------------------------------------------------------- 1-D transport
+// TU = D (U[i-1] - 2 U[i] + U[i+1]) / dx^2 with zero-gradient ends, and the
+// three SSP-RK3 stages of dU/dt = T(U) - Tn over dt/2 (Shu-Osher form).
+__device__ inline double lap1d(const double* U, int64_t i, int v, int64_t n, int nv) {
+  const int64_t im = i > 0 ? i - 1 : 0, ip = i + 1 < n ? i + 1 : n - 1;
+  return U[im * nv + v] - 2.0 * U[i * nv + v] + U[ip * nv + v];
+}
+
+__global__ void diffusion_kernel(const double* __restrict__ U, double* __restrict__ TU, int64_t n, int nv,
+                                 double D, double inv_dx2) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * nv) return;
+  const int64_t i = idx / nv;
+  const int v = (int)(idx - i * nv);
+  TU[idx] = D * (lap1d(U, i, v, n, nv) * inv_dx2);
+}
+
+// stage 0: V1 = U1 + k g(U1); stage 1: V2 = 3/4 U1 + 1/4 (V1 + k g(V1));
+// stage 2: U = 1/3 U1 + 2/3 (V2 + k g(V2)), with g(V) = D lap V - Tn.
+__global__ void ssprk3_stage_kernel(int stage, const double* __restrict__ U1, const double* __restrict__ X,
+                                    const double* __restrict__ Tn, double* Out, int64_t n, int nv, double D,
+                                    double inv_dx2, double k) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * nv) return;
+  const int64_t i = idx / nv;
+  const int v = (int)(idx - i * nv);
+  const double gX = D * (lap1d(X, i, v, n, nv) * inv_dx2) - Tn[idx];
+  const double xk = X[idx] + k * gX;
+  double r;
+  if (stage == 0) r = xk;
+  else if (stage == 1) r = 0.75 * U1[idx] + 0.25 * xk;
+  else r = U1[idx] / 3.0 + (2.0 / 3.0) * xk;
+  Out[idx] = r;
+}
+
+// ------------------------------------------------------------------ probes
+__global__ void probe_fp64_kernel(double* out, int iters, double a) {
+  double x0 = threadIdx.x * 1e-9, x1 = x0 + 1e-3, x2 = x0 + 2e-3, x3 = x0 + 3e-3;
+  double x4 = x0 + 4e-3, x5 = x0 + 5e-3, x6 = x0 + 6e-3, x7 = x0 + 7e-3;
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, a); x1 = fma(x1, a, a); x2 = fma(x2, a, a); x3 = fma(x3, a, a);
+    x4 = fma(x4, a, a); x5 = fma(x5, a, a); x6 = fma(x6, a, a); x7 = fma(x7, a, a);
+  }
+  const double r = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+  if (r == 12345.678) out[0] = r;
+}
+__global__ void probe_fp32_kernel(float* out, int iters, float a) {
+  float x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = threadIdx.x * 1e-9f + j * 1e-3f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = fmaf(x[j], a, a);
+  }
+  float r = 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) r += x[j];
+  if (r == 12345.678f) out[0] = r;
+}
+__global__ void probe_exp_kernel(double* out, int iters) {
+  double x0 = -threadIdx.x * 1e-6, x1 = x0 - 0.25, x2 = x0 - 0.5, x3 = x0 - 0.75;
+  for (int i = 0; i < iters; ++i) {
+    x0 = exp(x0) - 1.5; x1 = exp(x1) - 1.5; x2 = exp(x2) - 1.5; x3 = exp(x3) - 1.5;
+  }
+  const double r = x0 + x1 + x2 + x3;
+  if (r == 12345.678) out[0] = r;
+}
+
+}  // namespace rk
+
+// =============================================================================
+// Host side
+// =============================================================================
+using namespace rk;
+
+struct rk_mech {
+  HostMech host;
+  unsigned char* dev = nullptr;
+  int device = 0;
+};
+
+namespace {
+
+struct LaunchPlan {
+  int G = 32;
+  int cells_per_block = 1;
+  size_t smem = 0;
+  int blocks = 1;
+};
+
+int device_props(int* n_sm, size_t* smem_optin) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  int v = 0;
+  e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaDeviceGetAttribute");
+  *n_sm = v;
+  e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaDeviceGetAttribute");
+  *smem_optin = (size_t)v;
+  return RK_OK;
+}
+
+template <int G, typename K>
+int plan_for(K kernel, const rk_mech* mech, const SlotLayout& S, int want_cells, int64_t ncell, bool persistent,
+             LaunchPlan* plan) {
+  int n_sm = 0;
+  size_t smem_max = 0;
+  int rc = device_props(&n_sm, &smem_max);
+  if (rc) return rc;
+  const size_t mech_bytes = (size_t)mech->host.L.bytes;
+  const size_t slot_bytes = (size_t)S.stride * sizeof(double);
+  if (mech_bytes + slot_bytes > smem_max)
+    return set_error(RK_E_UNSUPPORTED, "mechanism plus one cell's work arrays exceed shared memory");
+  int cells = (int)((smem_max - mech_bytes) / slot_bytes);
+  cells = cells > 512 / G ? 512 / G : cells;
+  if (want_cells > 0 && want_cells < cells) cells = want_cells;
+  if (!persistent && (int64_t)cells > ncell) cells = (int)(ncell > 0 ? ncell : 1);
+  size_t smem = mech_bytes + (size_t)cells * slot_bytes;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, cells * G, smem);
+  if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  while (per_sm == 0 && cells > 1) {  // registers limit: shrink the block
+    cells /= 2;
+    smem = mech_bytes + (size_t)cells * slot_bytes;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, cells * G, smem);
+    if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  }
+  if (per_sm == 0) return set_error(RK_E_UNSUPPORTED, "integration kernel cannot be resident on an SM");
+  plan->G = G;
+  plan->cells_per_block = cells;
+  plan->smem = smem;
+  const int64_t need = (ncell + cells - 1) / cells;
+  int64_t blocks = persistent ? (int64_t)per_sm * n_sm : need;
+  if (persistent && blocks > need) blocks = need;
+  plan->blocks = (int)(blocks > 0 ? blocks : 1);
+  return RK_OK;
+}
+
+int check_mech(const rk_mech* mech) {
+  if (!mech || !mech->dev) return set_error(RK_E_INVALID_ARGUMENT, "null mechanism handle");
+  return RK_OK;
+}
+
+int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_cell, int64_t ncell, double p,
+                   double dt, double rtol, double atol, int32_t M, const rk_opts* opts, int32_t* stats,
+                   void* workspace, size_t workspace_bytes, cudaStream_t stream) {
+  int rc = check_mech(mech);
+  if (rc) return rc;
+  if (ncell < 0) return set_error(RK_E_INVALID_ARGUMENT, "ncell < 0");
+  if (ncell == 0) return RK_OK;
+  if (!Y) return set_error(RK_E_INVALID_ARGUMENT, "null state array");
+  if (!(dt > 0.0) || !isfinite(dt)) return set_error(RK_E_INVALID_ARGUMENT, "dt must be finite and > 0");
+  if (!(rtol >= 0.0) || !(atol >= 0.0) || !(rtol + atol > 0.0))
+    return set_error(RK_E_INVALID_ARGUMENT, "tolerances must be >= 0 with rtol + atol > 0");
+  if (!(p > 0.0) || !isfinite(p)) return set_error(RK_E_INVALID_ARGUMENT, "pressure must be finite and > 0");
+  if (M < 1 || M > RK_MAX_KRYLOV) return set_error(RK_E_INVALID_ARGUMENT, "krylov_dim outside 1..8");
+  rk_opts o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.jv_mode != 0 && o.jv_mode != 1) return set_error(RK_E_INVALID_ARGUMENT, "jv_mode must be 0 or 1");
+  if (o.trace_cap < 0 || (o.trace_cap > 0 && !o.trace))
+    return set_error(RK_E_INVALID_ARGUMENT, "trace_cap > 0 needs a trace array");
+  if (o.fixed_h < 0.0 || !isfinite(o.fixed_h)) return set_error(RK_E_INVALID_ARGUMENT, "fixed_h must be >= 0");
+  const int G = o.lanes_per_cell == 0 ? 32 : o.lanes_per_cell;
+  if (G != 8 && G != 16 && G != 32) return set_error(RK_E_INVALID_ARGUMENT, "lanes_per_cell must be 0, 8, 16 or 32");
+  if (!workspace || workspace_bytes < sizeof(unsigned long long))
+    return set_error(RK_E_WORKSPACE, "workspace missing or smaller than rk_rok4e_workspace_size");
+  const int N = mech->host.L.ns + 1;
+  const int Meff = M > N ? N : M;
+  IntegrateParams P;
+  P.mech = mech->dev;
+  P.L = mech->host.L;
+  P.S = make_slot(mech->host.L, Meff);
+  P.Y = Y;
+  P.src = src;
+  P.h_cell = h_cell;
+  P.ncell = ncell;
+  P.p = p;
+  P.dt = dt;
+  P.rtol = rtol;
+  P.atol = atol;
+  P.h0 = o.h0;
+  P.fixed_h = o.fixed_h;
+  P.M = Meff;
+  P.jv_mode = o.jv_mode;
+  P.max_attempts = o.max_attempts > 0 ? o.max_attempts : 100000;
+  P.trace_cap = o.trace_cap;
+  P.trace = o.trace;
+  P.stats = stats;
+  P.counter = reinterpret_cast<unsigned long long*>(workspace);
+  cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
+  LaunchPlan plan;
+  if (o.ev_begin) {
+    e = cudaEventRecord((cudaEvent_t)o.ev_begin, stream);
+    if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+  }
+  if (G == 32) {
+    rc = plan_for<32>(rok4e_integrate_kernel<32>, mech, P.S, o.cells_per_block, ncell, true, &plan);
+    if (rc) return rc;
+    rok4e_integrate_kernel<32><<<plan.blocks, plan.cells_per_block * 32, plan.smem, stream>>>(P);
+  } else if (G == 16) {
+    rc = plan_for<16>(rok4e_integrate_kernel<16>, mech, P.S, o.cells_per_block, ncell, true, &plan);
+    if (rc) return rc;
+    rok4e_integrate_kernel<16><<<plan.blocks, plan.cells_per_block * 16, plan.smem, stream>>>(P);
+  } else {
+    rc = plan_for<8>(rok4e_integrate_kernel<8>, mech, P.S, o.cells_per_block, ncell, true, &plan);
+    if (rc) return rc;
+    rok4e_integrate_kernel<8><<<plan.blocks, plan.cells_per_block * 8, plan.smem, stream>>>(P);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "rok4e_integrate_kernel launch");
+  if (o.ev_end) {
+    e = cudaEventRecord((cudaEvent_t)o.ev_end, stream);
+    if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+  }
+  return RK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rk_mech_validate(const rk_mech_desc* desc, char* msg, size_t msg_len) {
+  HostMech hm;
+  std::string err;
+  const bool ok = pack_mechanism(desc, &hm, &err);
+  if (msg && msg_len > 0) {
+    snprintf(msg, msg_len, "%s", ok ? "" : err.c_str());
+  }
+  return ok ? RK_OK : set_error(RK_E_MECH_INVALID, err);
+}
+
+int rk_mech_load(const rk_mech_desc* desc, rk_mech** out) {
+  if (!out) return set_error(RK_E_INVALID_ARGUMENT, "null output handle");
+  *out = nullptr;
+  rk_mech* m = new rk_mech();
+  std::string err;
+  if (!pack_mechanism(desc, &m->host, &err)) {
+    delete m;
+    return set_error(RK_E_MECH_INVALID, err);
+  }
+  cudaError_t e = cudaGetDevice(&m->device);
+  if (e == cudaSuccess) e = cudaMalloc(&m->dev, (size_t)m->host.L.bytes);
+  if (e == cudaSuccess) e = cudaMemcpy(m->dev, m->host.packed.data(), (size_t)m->host.L.bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (m->dev) cudaFree(m->dev);
+    delete m;
+    return cuda_error(e, "rk_mech_load");
+  }
+  *out = m;
+  return RK_OK;
+}
+
+int rk_mech_free(rk_mech* mech) {
+  if (!mech) return RK_OK;
+  cudaError_t e = cudaSuccess;
+  if (mech->dev) {
+    e = cudaDeviceSynchronize();
+    cudaFree(mech->dev);
+  }
+  delete mech;
+  return e == cudaSuccess ? RK_OK : cuda_error(e, "rk_mech_free");
+}
+
+int rk_mech_info(const rk_mech* mech, int32_t* n_species, int32_t* n_reactions, size_t* device_bytes) {
+  if (!mech) return set_error(RK_E_INVALID_ARGUMENT, "null mechanism handle");
+  if (n_species) *n_species = mech->host.L.ns;
+  if (n_reactions) *n_reactions = mech->host.L.nr;
+  if (device_bytes) *device_bytes = (size_t)mech->host.L.bytes;
+  return RK_OK;
+}
+
+static int point_call(const rk_mech* mech, const double* Y, const double* src, const double* V, double p,
+                      double* out, int64_t ncell, int mode, void* stream) {
+  int rc = check_mech(mech);
+  if (rc) return rc;
+  if (ncell < 0) return set_error(RK_E_INVALID_ARGUMENT, "ncell < 0");
+  if (ncell == 0) return RK_OK;
+  if (!Y || !out || (mode > 0 && !V)) return set_error(RK_E_INVALID_ARGUMENT, "null array");
+  if (out == Y) return set_error(RK_E_INVALID_ARGUMENT, "output must not alias the state");
+  if (!(p > 0.0)) return set_error(RK_E_INVALID_ARGUMENT, "pressure must be > 0");
+  PointParams P;
+  P.mech = mech->dev;
+  P.L = mech->host.L;
+  P.S = make_slot(mech->host.L, 1);
+  P.Y = Y;
+  P.src = src;
+  P.V = V;
+  P.out = out;
+  P.ncell = ncell;
+  P.p = p;
+  P.mode = mode;
+  LaunchPlan plan;
+  rc = plan_for<32>(chem_point_kernel<32>, mech, P.S, 8, ncell, false, &plan);
+  if (rc) return rc;
+  chem_point_kernel<32><<<plan.blocks, plan.cells_per_block * 32, plan.smem, (cudaStream_t)stream>>>(P);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RK_OK : cuda_error(e, "chem_point_kernel launch");
+}
+
+int rk_chem_rhs(const rk_mech* mech, const double* Y, const double* src, double p, double* dYdt, int64_t ncell,
+                void* stream) {
+  return point_call(mech, Y, src, nullptr, p, dYdt, ncell, 0, stream);
+}
+
+int rk_chem_jvp(const rk_mech* mech, const double* Y, const double* V, double p, double* JV, int64_t ncell,
+                int32_t mode, void* stream) {
+  if (mode != 0 && mode != 1) return set_error(RK_E_INVALID_ARGUMENT, "mode must be 0 or 1");
+  return point_call(mech, Y, nullptr, V, p, JV, ncell, mode == 0 ? 1 : 2, stream);
+}
+
+size_t rk_rok4e_workspace_size(const rk_mech* mech, int64_t ncell, int32_t krylov_dim, const rk_opts* opts) {
+  (void)mech;
+  (void)ncell;
+  (void)krylov_dim;
+  (void)opts;
+  return 256;
+}
+
+int rk_rok4e_integrate(const rk_mech* mech, double* Y, const double* src, double* h_cell, int64_t ncell, double p,
+                       double dt, double rtol, double atol, int32_t krylov_dim, const rk_opts* opts,
+                       int32_t* stats, void* workspace, size_t workspace_bytes, void* stream) {
+  return integrate_impl(mech, Y, src, h_cell, ncell, p, dt, rtol, atol, krylov_dim, opts, stats, workspace,
+                        workspace_bytes, (cudaStream_t)stream);
+}
+
+size_t rk_simpler_split_step_workspace_size(const rk_mech* mech, int64_t npts, int32_t krylov_dim,
+                                            const rk_opts* opts) {
+  if (!mech || npts < 0) return 0;
+  const size_t n = (size_t)npts * (size_t)(mech->host.L.ns + 1);
+  return 256 + 3 * ((n * sizeof(double) + 255) & ~(size_t)255) +
+         rk_rok4e_workspace_size(mech, npts, krylov_dim, opts);
+}
+
+int rk_diffusion_1d(const double* U, double* TU, int64_t npts, int32_t nvar, double D, double dx, void* stream) {
+  if (npts < 0 || nvar < 1) return set_error(RK_E_INVALID_ARGUMENT, "bad sizes");
+  if (npts == 0) return RK_OK;
+  if (!U || !TU || U == TU) return set_error(RK_E_INVALID_ARGUMENT, "null or aliased array");
+  if (!(dx > 0.0)) return set_error(RK_E_INVALID_ARGUMENT, "dx must be > 0");
+  const int64_t n = npts * nvar;
+  diffusion_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(U, TU, npts, nvar, D,
+                                                                                  1.0 / (dx * dx));
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RK_OK : cuda_error(e, "diffusion_kernel launch");
+}
+
+int rk_simpler_split_step(const rk_mech* mech, double* U, double* h_cell, int64_t npts, double p, double dt,
+                          double D, double dx, double rtol, double atol, int32_t krylov_dim, const rk_opts* opts,
+                          int32_t* stats, void* workspace, size_t workspace_bytes, void* stream) {
+  int rc = check_mech(mech);
+  if (rc) return rc;
+  if (npts < 0) return set_error(RK_E_INVALID_ARGUMENT, "npts < 0");
+  if (npts == 0) return RK_OK;
+  if (!U) return set_error(RK_E_INVALID_ARGUMENT, "null state array");
+  if (!(dx > 0.0) || !(D >= 0.0)) return set_error(RK_E_INVALID_ARGUMENT, "need dx > 0 and D >= 0");
+  const size_t need = rk_simpler_split_step_workspace_size(mech, npts, krylov_dim, opts);
+  if (!workspace || workspace_bytes < need) return set_error(RK_E_WORKSPACE, "workspace too small");
+  const int nv = mech->host.L.ns + 1;
+  const int64_t n = npts * nv;
+  const size_t vec = ((size_t)n * sizeof(double) + 255) & ~(size_t)255;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  double* Tn = reinterpret_cast<double*>(ws + 256);
+  double* V1 = reinterpret_cast<double*>(ws + 256 + vec);
+  double* V2 = reinterpret_cast<double*>(ws + 256 + 2 * vec);
+  void* ws_int = ws + 256 + 3 * vec;
+  const size_t ws_int_bytes = workspace_bytes - (256 + 3 * vec);
+  cudaStream_t st = (cudaStream_t)stream;
+  const double inv_dx2 = 1.0 / (dx * dx);
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  // c_n = -T(U_n)
+  diffusion_kernel<<<nb, 256, 0, st>>>(U, Tn, npts, nv, D, inv_dx2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "diffusion_kernel launch");
+  // reaction sub-step over dt with the constant source T(U_n)
+  rc = integrate_impl(mech, U, Tn, h_cell, npts, p, dt, rtol, atol, krylov_dim, opts, stats, ws_int, ws_int_bytes,
+                      st);
+  if (rc) return rc;
+  // transport correction over dt/2: one SSP-RK3 step of dU/dt = T(U) - T(U_n)
+  const double k = 0.5 * dt;
+  ssprk3_stage_kernel<<<nb, 256, 0, st>>>(0, U, U, Tn, V1, npts, nv, D, inv_dx2, k);
+  ssprk3_stage_kernel<<<nb, 256, 0, st>>>(1, U, V1, Tn, V2, npts, nv, D, inv_dx2, k);
+  ssprk3_stage_kernel<<<nb, 256, 0, st>>>(2, U, V2, Tn, U, npts, nv, D, inv_dx2, k);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? RK_OK : cuda_error(e, "ssprk3_stage_kernel launch");
+}
+
+int rk_probe_throughput(int32_t kind, double* ops_per_s) {
+  if (!ops_per_s || kind < 0 || kind > 2) return set_error(RK_E_INVALID_ARGUMENT, "bad probe arguments");
+  int n_sm = 0;
+  size_t smem = 0;
+  int rc = device_props(&n_sm, &smem);
+  if (rc) return rc;
+  void* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, 64);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc");
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const int threads = 512, blocks = n_sm * 4;
+  const int iters = kind == 2 ? 2000 : (kind == 0 ? 20000 : 200000);
+  double ops = 0.0;
+  float ms = 0.f;
+  for (int rep = 0; rep < 2; ++rep) {  // first launch warms up
+    cudaEventRecord(a);
+    if (kind == 0) {
+      probe_fp64_kernel<<<blocks, threads>>>((double*)buf, iters, 0.999999);
+      ops = (double)blocks * threads * iters * 8.0;
+    } else if (kind == 1) {
+      probe_fp32_kernel<<<blocks, threads>>>((float*)buf, iters, 0.999999f);
+      ops = (double)blocks * threads * iters * 8.0;
+    } else {
+      probe_exp_kernel<<<blocks, threads>>>((double*)buf, iters);
+      ops = (double)blocks * threads * iters * 4.0;
+    }
+    cudaEventRecord(b);
+    cudaEventSynchronize(b);
+  }
+  e = cudaGetLastError();
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_error(e, "probe launch");
+  *ops_per_s = ops / (ms * 1e-3);
+  return RK_OK;
+}
+
+const char* rk_status_string(int32_t code) {
+  switch (code) {
+    case RK_OK: return "ok";
+    case RK_E_INVALID_ARGUMENT: return "invalid argument";
+    case RK_E_MECH_INVALID: return "mechanism invalid";
+    case RK_E_CUDA: return "CUDA error";
+    case RK_E_UNSUPPORTED: return "unsupported size";
+    case RK_E_WORKSPACE: return "workspace missing or too small";
+    default: return "unknown status";
+  }
+}
+
+int rk_last_error(char* buf, size_t len) {
+  if (buf && len > 0) snprintf(buf, len, "%s", g_last_error.c_str());
+  return RK_OK;
+}
+
+}  // extern "C"
