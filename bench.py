@@ -142,16 +142,21 @@ def build_inputs(rank):
     return w, mech, U
 
 
-def cpu_oracle_sample(w, mech, U, n_cells, seconds_hint=None):
-    """Time the oracle's Simpler split step on a stratified sample of cells:
-    transport over the whole grid, the ROK4E reaction sub-step on n_cells."""
+def stratified_cells(npts, n_cells, offset=0):
+    """n_cells cell indices spread over the grid (golden-ratio sequence)."""
+    return [int((offset + i) * 0.6180339887498949 * npts) % npts for i in range(n_cells)]
+
+
+def cpu_oracle_sample(w, mech, U, cells):
+    """Time the oracle's Simpler split step on a sample of cells: transport over
+    the whole grid, the ROK4E reaction sub-step on the listed cells."""
     from oracle import splitting as osp
     from oracle.kinetics import Kinetics
 
     kin = Kinetics(mech)
     npts = U.shape[0]
     dx = LENGTH / npts
-    cells = list(np.linspace(0, npts - 1, n_cells).astype(int))
+    n_cells = len(cells)
     t0 = time.perf_counter()
     osp.simpler_split_step_1d(kin, U, P_ATM, w.dt, D_DIFF, dx, w.rtol, w.atol, w.krylov_dim, cells=cells)
     dt = time.perf_counter() - t0
@@ -163,12 +168,13 @@ def run_reference(args, rank, world):
         return 0
     w, mech, U = build_inputs(0)
     per_step = 1
-    for _ in range(args.warmup):
-        cpu_oracle_sample(w, mech, U, per_step)
+    npts = U.shape[0]
+    for k in range(args.warmup):
+        cpu_oracle_sample(w, mech, U, stratified_cells(npts, per_step, 1000 + k))
     t_total = 0.0
     cells_total = 0
     for k in range(args.steps):
-        _, dt = cpu_oracle_sample(w, mech, U, per_step)
+        _, dt = cpu_oracle_sample(w, mech, U, stratified_cells(npts, per_step, k))
         t_total += dt
         cells_total += per_step
     value = cells_total / t_total
@@ -181,10 +187,29 @@ def run_reference(args, rank, world):
                                "Simpler split steps of 1e-7 s, ROK4E M=4, rtol 1e-6, atol 1e-10",
                    "oracle_sample": f"{per_step} cell(s) per step through the FP64 numpy oracle"},
         "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{per_step} stratified cell per step x {args.steps} steps of the initial field"},
+                         "sample": f"{per_step} cell per step (golden-ratio sequence over the grid) x "
+                                   f"{args.steps} steps, one split step of the initial field each"},
         "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
+    return 0
+
+
+def run_plain(args):
+    """Untimed split steps of the workload (the small case used for ncu captures)."""
+    import torch
+
+    import paper_1712_00953_gb300 as rk
+
+    w, mech, U0 = build_inputs(0)
+    m = rk.mech_load(mech)
+    U = torch.tensor(U0, device="cuda")
+    hc = torch.zeros(U.shape[0], dtype=torch.float64, device="cuda")
+    for _ in range(args.plain_steps):
+        rk.simpler_split_step(m, U, w.dt, D_DIFF, LENGTH / U.shape[0], w.rtol, w.atol, w.krylov_dim, h_cell=hc,
+                              opts=rk.Opts(lanes_per_cell=args.lanes))
+    torch.cuda.synchronize()
+    print(json.dumps({"plain_steps": args.plain_steps, "T_max": float(U[:, -1].max())}))
     return 0
 
 
@@ -220,11 +245,13 @@ def run_ours(args, rank, world, local_rank):
 
     def step(stats=None, events=None):
         rk.simpler_split_step(m, U, w.dt, D_DIFF, dx, w.rtol, w.atol, M, h_cell=hc, stats=stats,
-                              opts=rk.Opts(events=events), workspace=ws, stream=stream)
+                              opts=rk.Opts(events=events, lanes_per_cell=args.lanes), workspace=ws,
+                              stream=stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    U_start, hc_start = U.clone(), hc.clone()  # the end-to-end pass replays the same steps
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -247,9 +274,12 @@ def run_ours(args, rank, world, local_rank):
         t_total = float(t.item())
     value = world * npts * args.steps / t_total
 
-    # ---- end to end through the public API with host buffers
-    pinned = torch.tensor(U.cpu().numpy(), dtype=torch.float64).pin_memory()
-    e2e_steps = max(1, min(args.steps, 50))
+    # ---- end to end through the public API with host buffers: the same steps
+    # from the same state, with the state copied in from pinned host memory and
+    # the result copied back every step
+    pinned = U_start.cpu().pin_memory()
+    hc.copy_(hc_start)
+    e2e_steps = args.steps
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -281,7 +311,7 @@ def run_ours(args, rank, world, local_rank):
     bad = int((st[:, :, 3] != 0).sum())
 
     # ---- CPU baseline: the oracle on a bounded sample of the initial field
-    cpu_v, cpu_t = cpu_oracle_sample(w, mech, U0, args.cpu_cells)
+    cpu_v, cpu_t = cpu_oracle_sample(w, mech, U0, stratified_cells(npts, args.cpu_cells))
 
     clocks = clk.summary()
     line = {
@@ -298,14 +328,15 @@ def run_ours(args, rank, world, local_rank):
                      "peak_probe_fp64": peak_meas, "frac_of_probe": achieved / peak_meas,
                      "exp_cost_fma": exp_fma, "algorithmic_tflop_per_step": flops / args.steps / 1e12},
         "cpu_baseline": {"value": cpu_v, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.cpu_cells} stratified cells of the initial field, one split step "
-                                   f"({cpu_t:.1f} s)"},
+                         "sample": f"{args.cpu_cells} cells spread over the grid (golden-ratio sequence), one "
+                                   f"split step of the initial field ({cpu_t:.1f} s)"},
         "e2e": {"value": e2e_value, "unit": "cell-steps/s", "h2d_bytes_per_step": int(U.numel() * 8),
                 "d2h_bytes_per_step": int(U.numel() * 8), "steps": e2e_steps},
         "gpu_launches": 5 * args.steps,
         "clocks": clocks,
         "cells_failed": bad,
         "substeps_per_cell_step": float(st[:, :, 0].mean()),
+        "max_substeps_per_cell_step": int(st[:, :, 0].max()),
         "attempts_per_cell_step": float((st[:, :, 0] + st[:, :, 1]).mean()),
     }
     print(json.dumps(line))
@@ -319,6 +350,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-cells", type=int, default=48)
+    ap.add_argument("--plain-steps", type=int, default=0,
+                    help="run this many untimed split steps and exit (profiling case)")
+    ap.add_argument("--lanes", type=int, default=0, help="lanes per cell (0: library default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -327,6 +361,8 @@ def main():
     local_rank = _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.plain_steps > 0:
+        return run_plain(args)
     return run_ours(args, rank, world, local_rank)
 
 

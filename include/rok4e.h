@@ -205,6 +205,13 @@ int rk_diffusion_1d(const double* U, double* TU, int64_t npts, int32_t nvar, dou
  *  with CUDA events in *ops_per_s.  Synchronous. */
 int rk_probe_throughput(int32_t kind, double* ops_per_s);
 
+/* The kernels' table-driven exponential on a device array (for testing it
+ * against the CUDA math library): which 0: y = exp(x); 1: exp(x) and 2:
+ * exp(-x) from the shared-reduction pair.  Method: Tang, ACM TOMS 15(2),
+ * 1989, with a 128-entry table; the paper itself delegates kinetics to
+ * Cantera and prints no exponential. */
+int rk_eval_exp(const double* x, double* y, int64_t n, int32_t which, void* stream);
+
 const char* rk_status_string(int32_t code);
 int rk_last_error(char* buf, size_t len);
 

@@ -29,7 +29,7 @@ def _L():
 
 __all__ = ["Mechanism", "mech_load", "mech_validate", "chem_rhs", "chem_jvp", "rok4e_integrate",
            "rok4e_workspace_size", "simpler_split_step", "simpler_split_step_workspace_size",
-           "diffusion_1d", "probe_throughput", "Opts", "RokError", "STATS_FIELDS"]
+           "diffusion_1d", "probe_throughput", "eval_exp", "Opts", "RokError", "STATS_FIELDS"]
 
 STATS_FIELDS = ("n_accept", "n_reject", "n_rhs", "status")
 
@@ -213,6 +213,14 @@ def diffusion_1d(U, D, dx, out=None, stream=None):
     out = torch.empty_like(U) if out is None else out
     _check(_L().rk_diffusion_1d(_dptr(U, "U"), _dptr(out, "out", U.numel()), int(U.shape[0]), int(U.shape[1]),
                                 float(D), float(dx), _stream_ptr(stream)), "rk_diffusion_1d")
+    return out
+
+
+def eval_exp(x, which=0, out=None, stream=None):
+    """The kernels' table-driven exp on a CUDA float64 tensor (0: exp(x), 1/2: exp(+-x) pair)."""
+    out = torch.empty_like(x) if out is None else out
+    _check(_L().rk_eval_exp(_dptr(x, "x"), _dptr(out, "out", x.numel()), x.numel(), int(which),
+                            _stream_ptr(stream)), "rk_eval_exp")
     return out
 
 

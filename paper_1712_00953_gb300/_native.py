@@ -70,6 +70,8 @@ SIGNATURES = {
     "rk_diffusion_1d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_void_p]),
     "rk_probe_throughput": (ctypes.c_int, [ctypes.c_int32, c_double_p]),
+    "rk_eval_exp": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                   ctypes.c_void_p]),
     "rk_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
     "rk_last_error": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t]),
 }

@@ -30,6 +30,7 @@
 #include <mutex>
 #include <string>
 
+#include "exp2_table.h"
 #include "internal.h"
 #include "rok4e.h"
 
@@ -51,8 +52,72 @@ constexpr double BH1 = -0.217819895945721, BH2 = 1.03130847478467, BH3 = 0.18651
 constexpr double PI_ALPHA = 0.7 / 4.0, PI_BETA = 0.4 / 4.0;
 constexpr double FAC_MIN = 0.2, FAC_MAX = 5.0, SAFETY = 0.8, ERR_FLOOR = 1e-10;
 constexpr double BREAKDOWN_TOL = 1e-12, T_END_TOL = 1e-12, H_MIN_FRAC = 1e-12;
-constexpr double G_OVERFLOW = 170.0;
+constexpr int G_OVERFLOW_HI = 0x40654000;  // high word of 170.0
 constexpr int MAXM = RK_MAX_KRYLOV;
+constexpr int EXP_TAB_BYTES = RK_EXP2_TABLE_N * 8;  // leads the dynamic shared memory
+
+__constant__ double c_exp2_table[RK_EXP2_TABLE_N] = {RK_EXP2_TABLE_VALUES};
+
+// ------------------------------------------------- table-driven exponential
+// exp(x) by Tang's table-driven method (ACM TOMS 15(2), 1989) with a 128-entry
+// table of 2^(j/128): x = (128 m + j) ln2/128 + r with |r| <= ln2/256,
+// exp(x) = 2^m 2^(j/128) (1 + p(r)), p the degree-5 Taylor polynomial of
+// e^r - 1 (truncation < 1e-18 relative).  k = 128 m + j comes from adding a
+// 1.5 2^52 shifter, r from a two-part ln2/128, and the final scaling by 2^m is
+// an integer add to the exponent field, so the fast path costs 10 FP64
+// operations.  |x| >= 708, infinities and NaN take the library exp().
+constexpr double EXP_SHIFTER = 6755399441055744.0;  // 1.5 * 2^52
+
+__device__ __forceinline__ double exp_scale(double y, int e) {
+  return __hiloint2double(__double2hiint(y) + (e << 20), __double2loint(y));
+}
+
+__device__ __forceinline__ double exp_fast(double x, const double* __restrict__ tab) {
+  if ((__double2hiint(x) & 0x7fffffff) >= 0x40862000) return exp(x);
+  const double kt = fma(x, RK_N_OVER_LN2, EXP_SHIFTER);
+  const int k = __double2loint(kt);
+  const double kd = kt - EXP_SHIFTER;
+  double r = fma(-kd, RK_LN2_OVER_N_HI, x);
+  r = fma(-kd, RK_LN2_OVER_N_LO, r);
+  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+  q = fma(q, r, 1.0 / 6.0);
+  q = fma(q, r, 0.5);
+  const double p = fma(r * r, q, r);
+  const double t = tab[k & (RK_EXP2_TABLE_N - 1)];
+  return exp_scale(fma(t, p, t), k >> 7);
+}
+
+// (exp(x), exp(-x)) sharing one argument reduction.
+__device__ __forceinline__ void exp_pm(double x, const double* __restrict__ tab, double* ep, double* em) {
+  if ((__double2hiint(x) & 0x7fffffff) >= 0x40862000) {
+    *ep = exp(x);
+    *em = exp(-x);
+    return;
+  }
+  const double kt = fma(x, RK_N_OVER_LN2, EXP_SHIFTER);
+  const int k = __double2loint(kt);
+  const double kd = kt - EXP_SHIFTER;
+  double r = fma(-kd, RK_LN2_OVER_N_HI, x);
+  r = fma(-kd, RK_LN2_OVER_N_LO, r);
+  const double r2 = r * r;
+  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+  q = fma(q, r, 1.0 / 6.0);
+  q = fma(q, r, 0.5);
+  const double pp = fma(r2, q, r);
+  double qm = fma(-r, 1.0 / 120.0, 1.0 / 24.0);
+  qm = fma(qm, -r, 1.0 / 6.0);
+  qm = fma(qm, -r, 0.5);
+  const double pm = fma(r2, qm, -r);
+  const double tp = tab[k & (RK_EXP2_TABLE_N - 1)];
+  const int km = -k;
+  const double tm = tab[km & (RK_EXP2_TABLE_N - 1)];
+  *ep = exp_scale(fma(tp, pp, tp), k >> 7);
+  *em = exp_scale(fma(tm, pm, tm), km >> 7);
+}
+
+__device__ inline void load_exp_table(double* dst) {
+  for (int i = threadIdx.x; i < RK_EXP2_TABLE_N; i += blockDim.x) dst[i] = c_exp2_table[i];
+}
 
 // --------------------------------------------------------------- error state
 static thread_local std::string g_last_error;
@@ -67,6 +132,7 @@ static int cuda_error(cudaError_t e, const char* where) {
 // ------------------------------------------------------------------- views
 struct MechView {
   int ns, nr, ntb;
+  const double* etab;  // 2^(j/128) table in shared memory
   const double *W, *invW, *Tmid, *lo, *hi, *lnA, *bexp, *EaR, *eff, *fo, *csr_nu;
   const uint32_t* slots;
   const int32_t *meta, *csr_ptr, *csr_j;
@@ -77,6 +143,7 @@ __host__ __device__ inline MechView make_view(const unsigned char* base, const M
   m.ns = L.ns;
   m.nr = L.nr;
   m.ntb = L.ntb;
+  m.etab = nullptr;
   m.W = reinterpret_cast<const double*>(base + L.off_W);
   m.invW = reinterpret_cast<const double*>(base + L.off_invW);
   m.Tmid = reinterpret_cast<const double*>(base + L.off_Tmid);
@@ -172,6 +239,11 @@ struct Grp {
     for (int o = G / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(mask, v, o, G));
     return v;
   }
+  __device__ __forceinline__ int imax(int v) const {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v = ::max(v, __shfl_xor_sync(mask, v, o, G));
+    return v;
+  }
   __device__ __forceinline__ int any(int v) const {
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(mask, v, o, G);
@@ -182,7 +254,7 @@ struct Grp {
 // Scalars of the last right-hand-side evaluation that the analytic
 // Jacobian-vector product needs (uniform across the group).
 struct CellScalars {
-  double T, invT, lnT, S, rho, invrho, cb, Sh;
+  double T, invT, lnT, S, invS, rho, invrho, cb, invcb, Sh;
 };
 
 struct SlotPtrs {
@@ -240,7 +312,8 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
   const double invT = 1.0 / T;
   const double lnT = log(T);
   // species pass 1: thermo, Gibbs factors, sum Y/W
-  double S = 0.0, gmax = 0.0;
+  double S = 0.0;
+  int ghi = 0;  // max over species of the high word of |g/RT| (integer compare)
   for (int k = g.lane; k < ns; k += G) {
     const double* c = (T < m.Tmid[k]) ? m.lo : m.hi;
     const double a1 = c[k], a2 = c[ns + k], a3 = c[2 * ns + k], a4 = c[3 * ns + k], a5 = c[4 * ns + k];
@@ -253,27 +326,25 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     s.cp[k] = cp;
     s.hRT[k] = hrt;
     s.gRT[k] = grt;
-    gmax = fmax(gmax, fabs(grt));
+    ghi = max(ghi, __double2hiint(grt) & 0x7fffffff);
     if (cache) s.dcp[k] = fma(fma(c[16 * ns + k], T, c[15 * ns + k]), T, c[14 * ns + k]) * T + a2;
     S = fma(uu[k], m.invW[k], S);
   }
   S = g.sum(S);
-  gmax = g.max(gmax);
-  const bool direct_kc = !(gmax <= G_OVERFLOW);  // also true for NaN
+  ghi = g.imax(ghi);
+  const bool direct_kc = ghi >= G_OVERFLOW_HI;  // |g/RT| >= 170, also NaN
   const double rho = p / (R_GAS * T * S);
   const double invrho = 1.0 / rho;
   for (int k = g.lane; k < ns; k += G) {
     s.C[k] = rho * uu[k] * m.invW[k];
-    if (!direct_kc) {
-      s.E[k] = exp(s.gRT[k]);
-      s.Einv[k] = exp(-s.gRT[k]);
-    }
+    if (!direct_kc) exp_pm(s.gRT[k], m.etab, &s.E[k], &s.Einv[k]);
   }
   g.sync();
   // reactions: rate coefficients and rates of progress
   const double RTp = R_GAS * T / P_REF;
   const double invRTp = P_REF / (R_GAS * T);
   const double lnRTp = log(RTp);
+  const double m_lnRTp = -lnRTp;
   for (int j = g.lane; j < m.nr; j += G) {
     const uint32_t sl = m.slots[j];
     const int ra = sl & 255, rb = (sl >> 8) & 255, pa = (sl >> 16) & 255, pb = sl >> 24;
@@ -281,7 +352,7 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     const int kind = meta & 3;
     const bool rev = (meta >> 2) & 1;
     const int dnu = ((meta >> 4) & 15) - 4;
-    double k = exp(m.lnA[j] + m.bexp[j] * lnT - m.EaR[j] * invT);
+    double k = exp_fast(m.lnA[j] + m.bexp[j] * lnT - m.EaR[j] * invT, m.etab);
     const double Pf = s.C[ra] * s.C[rb];
     const double Pb = s.C[pa] * s.C[pb];
     double rfac = 0.0;  // 1/Kc
@@ -290,7 +361,8 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
         const double pf = dnu > 0 ? RTp : (dnu < 0 ? invRTp : 1.0);
         rfac = s.E[pa] * s.Einv[ra] * s.E[pb] * s.Einv[rb] * pf;
       } else {
-        rfac = exp(s.gRT[pa] + s.gRT[pb] - s.gRT[ra] - s.gRT[rb] + dnu * lnRTp);
+        const double dl = dnu > 0 ? lnRTp : (dnu < 0 ? m_lnRTp : 0.0);
+        rfac = exp_fast(s.gRT[pa] + s.gRT[pb] - s.gRT[ra] - s.gRT[rb] + dl, m.etab);
       }
     }
     double mfac = 1.0;
@@ -304,13 +376,13 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
         mfac = Mc;
       } else {
         const double* fo = m.fo + (size_t)slot * FO_STRIDE;
-        const double k0 = exp(fo[0] + fo[1] * lnT - fo[2] * invT);
+        const double k0 = exp_fast(fo[0] + fo[1] * lnT - fo[2] * invT, m.etab);
         const double dlnk0 = (fo[1] + fo[2] * invT) * invT;
         double Pr = k0 * Mc / k;
         if (!(Pr > 1e-300)) Pr = 1e-300;
         const double a = fo[3];
-        const double e3 = exp(-T * fo[4]), e1 = exp(-T * fo[5]);
-        const double e2 = fo[6] > 0.0 ? exp(-fo[6] * invT) : 0.0;
+        const double e3 = exp_fast(-T * fo[4], m.etab), e1 = exp_fast(-T * fo[5], m.etab);
+        const double e2 = fo[6] > 0.0 ? exp_fast(-fo[6] * invT, m.etab) : 0.0;
         const double Fc = (1.0 - a) * e3 + a * e1 + e2;
         const double lFc = log10(Fc);
         const double cc = -0.4 - 0.67 * lFc;
@@ -321,7 +393,7 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
         const double f1 = x / D;
         const double den = 1.0 + f1 * f1;
         const double lF = lFc / den;
-        const double F = exp10(lF);
+        const double F = exp_fast(lF * 2.302585092994046, m.etab);  // 10^lF
         const double onePr = 1.0 + Pr;
         const double dlF_dL = -lFc * 2.0 * f1 / (den * den) * nn / (D * D);
         const double df1 = (-0.67 * D + 1.1762 * x) / (D * D);
@@ -371,9 +443,11 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     cs->invT = invT;
     cs->lnT = lnT;
     cs->S = S;
+    cs->invS = 1.0 / S;
     cs->rho = rho;
     cs->invrho = invrho;
     cs->cb = cb;
+    cs->invcb = 1.0 / cb;
     cs->Sh = Sh;
   }
   g.sync();
@@ -391,7 +465,7 @@ __device__ __noinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, cons
   double a = 0.0;
   for (int k = g.lane; k < ns; k += G) a = fma(v[k], m.invW[k], a);
   a = g.sum(a);
-  const double drr = -(a / cs.S + vT * invT);  // d rho / rho
+  const double drr = -fma(a, cs.invS, vT * invT);  // d rho / rho
   for (int k = g.lane; k < ns; k += G) s.dC[k] = fma(s.C[k], drr, cs.rho * v[k] * m.invW[k]);
   g.sync();
   for (int j = g.lane; j < m.nr; j += G) {
@@ -406,7 +480,8 @@ __device__ __noinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, cons
     const double dPb = fma(s.dC[pa], s.C[pb], s.C[pa] * s.dC[pb]);
     const double k = s.kc[j], kr = s.krc[j];
     double dlnk = (m.bexp[j] + m.EaR[j] * invT) * invT;
-    const double dlnKc = (s.hRT[pa] + s.hRT[pb] - s.hRT[ra] - s.hRT[rb] - dnu) * invT;
+    const double dnud = dnu > 0 ? 1.0 : (dnu < 0 ? -1.0 : 0.0);
+    const double dlnKc = (s.hRT[pa] + s.hRT[pb] - s.hRT[ra] - s.hRT[rb] - dnud) * invT;
     if (kind == 2) dlnk = s.tb[4 * (meta >> 8) + 2];
     double dq = k * fma(dlnk * vT, Pf, dPf) - kr * fma((dlnk - dlnKc) * vT, Pb, dPb);
     if (kind != 0) {
@@ -433,7 +508,7 @@ __device__ __noinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, cons
   dSh = g.sum(dSh);
   dcb = g.sum(dcb);
   if (g.lane == 0) {
-    out[ns] = (-(vT * cs.Sh + T * dSh) + T * cs.Sh * (drr + dcb / cs.cb)) / (cs.rho * cs.cb);
+    out[ns] = (-(vT * cs.Sh + T * dSh) + T * cs.Sh * (drr + dcb * cs.invcb)) * (cs.invrho * cs.invcb);
   }
   g.sync();
 }
@@ -489,7 +564,8 @@ __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& 
   }
   double unorm = 0.0;
   if (jv_mode != 0) unorm = sqrt(group_dot<G>(g, s.u, s.u, N));
-  for (int e = g.lane; e < N; e += G) s.Q[e] = s.fn[e] / beta;
+  const double ibeta = 1.0 / beta;
+  for (int e = g.lane; e < N; e += G) s.Q[e] = s.fn[e] * ibeta;
   g.sync();
   int mdim = M;
   for (int j = 0; j < M; ++j) {
@@ -533,7 +609,8 @@ __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& 
       break;
     }
     if (g.lane == 0) s.H[(j + 1) * MAXM + j] = hn;
-    for (int e = g.lane; e < N; e += G) s.Q[(j + 1) * Nq + e] = s.w[e] / hn;
+    const double ihn = 1.0 / hn;
+    for (int e = g.lane; e < N; e += G) s.Q[(j + 1) * Nq + e] = s.w[e] * ihn;
     g.sync();
   }
   g.sync();
@@ -569,12 +646,14 @@ __device__ inline void factor_small(const SlotPtrs& s, int mdim, double h) {
         A[r * MAXM + c] = l;
         for (int j = c + 1; j < mdim; ++j) A[r * MAXM + j] = fma(-l, A[c * MAXM + j], A[r * MAXM + j]);
       }
+      A[c * MAXM + c] = inv;  // the diagonal is kept as its reciprocal
     }
   }
   g.sync();
 }
 
-// Solve (I - h gamma H) y = z in place (every lane, redundantly).
+// Solve (I - h gamma H) y = z in place (every lane, redundantly; the factor
+// stores reciprocal pivots, so the solve has no divisions).
 __device__ inline void solve_small(const SlotPtrs& s, int mdim, double* z) {
   for (int c = 0; c < mdim; ++c) {
     const int pr = (int)s.piv[c];
@@ -588,7 +667,7 @@ __device__ inline void solve_small(const SlotPtrs& s, int mdim, double* z) {
     for (int c = 0; c < r; ++c) z[r] = fma(-s.LU[r * MAXM + c], z[c], z[r]);
   for (int r = mdim - 1; r >= 0; --r) {
     for (int c = r + 1; c < mdim; ++c) z[r] = fma(-s.LU[r * MAXM + c], z[c], z[r]);
-    z[r] = z[r] / s.LU[r * MAXM + r];
+    z[r] = z[r] * s.LU[r * MAXM + r];
   }
 }
 
@@ -606,6 +685,7 @@ struct IntegrateParams {
   double* trace;
   int32_t* stats;
   unsigned long long* counter;
+  unsigned long long qstride;  // queue position q takes cell (q * qstride) mod ncell
 };
 
 template <int G>
@@ -627,7 +707,7 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
   }
   if (fixed) h = P.fixed_h;
   const long long n_fixed = fixed ? llround(dt / P.fixed_h) : 0;
-  double t = 0.0, err_prev = 1.0, h_last = h;
+  double t = 0.0, ln_err_prev = 0.0, h_last = h;  // err_n = 1 before the first step
   int n_acc = 0, n_rej = 0, n_rhs = 0, status = RK_CELL_OK, n_att = 0;
   CellScalars cs;
   rhs_eval<G>(m, s, s.u, srcp, P.p, s.fn, true, &cs);
@@ -710,28 +790,30 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
       const double uh = ue + h * fma(BH4, k3, fma(BH3, k2, fma(BH2, k1, BH1 * k0)));
       const double d = (uh - us) / (P.atol + P.rtol * fabs(us));
       part = fma(d, d, part);
-      bad |= !isfinite(us);
+      bad |= (__double2hiint(us) & 0x7ff00000) == 0x7ff00000;
       s.arg[e] = us;
     }
-    const double err = sqrt(g.sum(part) / N);
+    const double err = sqrt(g.sum(part) * (1.0 / N));
     bad = g.any(bad);
     const int att = n_att;
     n_att += 1;
     bool accept;
-    double hnew;
+    double hnew, ln_err = 0.0;
     if (fixed) {
       accept = true;
       hnew = h;
     } else {
-      double fac;
-      if (!isfinite(err)) {
-        fac = FAC_MIN;
-      } else {
-        const double ee = fmax(err, ERR_FLOOR);
-        fac = fmin(FAC_MAX, fmax(FAC_MIN, SAFETY * pow(err_prev, PI_BETA) / pow(ee, PI_ALPHA)));
+      // h* = h min(5, max(0.2, 0.8 err_n^beta / err*^alpha)) with the powers
+      // as exp(beta ln err_n - alpha ln err*) (ln err_n kept from acceptance)
+      const bool fin = (__double2hiint(err) & 0x7ff00000) != 0x7ff00000;
+      double fac = FAC_MIN;
+      ln_err = 0.0;
+      if (fin) {
+        ln_err = log(fmax(err, ERR_FLOOR));
+        fac = fmin(FAC_MAX, fmax(FAC_MIN, SAFETY * exp_fast(PI_BETA * ln_err_prev - PI_ALPHA * ln_err, m.etab)));
       }
       hnew = h * fac;
-      accept = isfinite(err) && err <= 1.0;
+      accept = fin && err <= 1.0;
     }
     if (P.trace && att < P.trace_cap && g.lane == 0) P.trace[cell * P.trace_cap + att] = accept ? h : -h;
     if (accept) {
@@ -742,7 +824,7 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
       for (int e = g.lane; e < N; e += G) s.u[e] = s.arg[e];
       g.sync();
       t += h;
-      if (!fixed) err_prev = fmax(err, ERR_FLOOR);
+      if (!fixed) ln_err_prev = ln_err;
       n_acc += 1;
       h_last = hnew;
       h = hnew;
@@ -796,20 +878,25 @@ __device__ inline void init_sentinels(const SlotPtrs& s, int ns, int lane) {
 template <int G>
 __global__ void __launch_bounds__(512) rok4e_integrate_kernel(IntegrateParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  load_mech(smem, P.mech, P.L.bytes);
+  load_exp_table(reinterpret_cast<double*>(smem));
+  load_mech(smem + EXP_TAB_BYTES, P.mech, P.L.bytes);
   __syncthreads();
-  const MechView m = make_view(smem, P.L);
+  MechView m = make_view(smem + EXP_TAB_BYTES, P.L);
+  m.etab = reinterpret_cast<const double*>(smem);
   const Grp<G> g;
   const int gid = threadIdx.x / G;
-  double* base = reinterpret_cast<double*>(smem + P.L.bytes) + (size_t)gid * P.S.stride;
+  double* base = reinterpret_cast<double*>(smem + EXP_TAB_BYTES + P.L.bytes) + (size_t)gid * P.S.stride;
   const SlotPtrs s = slot_ptrs(base, P.S);
   init_sentinels(s, m.ns, g.lane);
   g.sync();
   while (true) {
-    unsigned long long cell = 0;
-    if (g.lane == 0) cell = atomicAdd(P.counter, 1ull);
-    cell = __shfl_sync(g.mask, cell, 0, G);
-    if (cell >= (unsigned long long)P.ncell) break;
+    unsigned long long q = 0;
+    if (g.lane == 0) q = atomicAdd(P.counter, 1ull);
+    q = __shfl_sync(g.mask, q, 0, G);
+    if (q >= (unsigned long long)P.ncell) break;
+    // Interleave the queue over the cell index: neighbouring cells (e.g. the
+    // hot side of a flame) spread over all SMs instead of filling a few.
+    const unsigned long long cell = (q * P.qstride) % (unsigned long long)P.ncell;
     integrate_cell<G>(m, s, P, (int64_t)cell);
   }
 }
@@ -831,15 +918,17 @@ struct PointParams {
 template <int G>
 __global__ void __launch_bounds__(512) chem_point_kernel(PointParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  load_mech(smem, P.mech, P.L.bytes);
+  load_exp_table(reinterpret_cast<double*>(smem));
+  load_mech(smem + EXP_TAB_BYTES, P.mech, P.L.bytes);
   __syncthreads();
-  const MechView m = make_view(smem, P.L);
+  MechView m = make_view(smem + EXP_TAB_BYTES, P.L);
+  m.etab = reinterpret_cast<const double*>(smem);
   const Grp<G> g;
   const int gid = threadIdx.x / G;
   const int gpb = blockDim.x / G;
   const int64_t cell = (int64_t)blockIdx.x * gpb + gid;
   if (cell >= P.ncell) return;
-  double* base = reinterpret_cast<double*>(smem + P.L.bytes) + (size_t)gid * P.S.stride;
+  double* base = reinterpret_cast<double*>(smem + EXP_TAB_BYTES + P.L.bytes) + (size_t)gid * P.S.stride;
   const SlotPtrs s = slot_ptrs(base, P.S);
   init_sentinels(s, m.ns, g.lane);
   const int N = m.ns + 1;
@@ -900,6 +989,21 @@ __global__ void ssprk3_stage_kernel(int stage, const double* __restrict__ U1, co
 }
 
 // ------------------------------------------------------------------ probes
+__global__ void exp_eval_kernel(const double* __restrict__ x, double* __restrict__ y, int64_t n, int which) {
+  __shared__ double tab[RK_EXP2_TABLE_N];
+  load_exp_table(tab);
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (which == 0) {
+    y[i] = exp_fast(x[i], tab);
+  } else {
+    double ep, em;
+    exp_pm(x[i], tab, &ep, &em);
+    y[i] = which == 1 ? ep : em;
+  }
+}
+
 __global__ void probe_fp64_kernel(double* out, int iters, double a) {
   double x0 = threadIdx.x * 1e-9, x1 = x0 + 1e-3, x2 = x0 + 2e-3, x3 = x0 + 3e-3;
   double x4 = x0 + 4e-3, x5 = x0 + 5e-3, x6 = x0 + 6e-3, x7 = x0 + 7e-3;
@@ -975,7 +1079,7 @@ int plan_for(K kernel, const rk_mech* mech, const SlotLayout& S, int want_cells,
   size_t smem_max = 0;
   int rc = device_props(&n_sm, &smem_max);
   if (rc) return rc;
-  const size_t mech_bytes = (size_t)mech->host.L.bytes;
+  const size_t mech_bytes = (size_t)mech->host.L.bytes + EXP_TAB_BYTES;
   const size_t slot_bytes = (size_t)S.stride * sizeof(double);
   if (mech_bytes + slot_bytes > smem_max)
     return set_error(RK_E_UNSUPPORTED, "mechanism plus one cell's work arrays exceed shared memory");
@@ -1004,6 +1108,23 @@ int plan_for(K kernel, const rk_mech* mech, const SlotLayout& S, int want_cells,
   if (persistent && blocks > need) blocks = need;
   plan->blocks = (int)(blocks > 0 ? blocks : 1);
   return RK_OK;
+}
+
+// A stride coprime with n near n * 0.618 (golden-ratio interleave of the queue).
+unsigned long long queue_stride(int64_t n) {
+  if (n <= 2) return 1;
+  unsigned long long st = (unsigned long long)((double)n * 0.6180339887498949);
+  if (st < 1) st = 1;
+  auto gcd = [](unsigned long long a, unsigned long long b) {
+    while (b) {
+      const unsigned long long t = a % b;
+      a = b;
+      b = t;
+    }
+    return a;
+  };
+  while (gcd(st, (unsigned long long)n) != 1) ++st;
+  return st % (unsigned long long)n;
 }
 
 int check_mech(const rk_mech* mech) {
@@ -1058,6 +1179,7 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   P.trace = o.trace;
   P.stats = stats;
   P.counter = reinterpret_cast<unsigned long long*>(workspace);
+  P.qstride = queue_stride(ncell);
   cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
   LaunchPlan plan;
@@ -1294,6 +1416,15 @@ int rk_probe_throughput(int32_t kind, double* ops_per_s) {
   if (e != cudaSuccess) return cuda_error(e, "probe launch");
   *ops_per_s = ops / (ms * 1e-3);
   return RK_OK;
+}
+
+int rk_eval_exp(const double* x, double* y, int64_t n, int32_t which, void* stream) {
+  if (n < 0 || which < 0 || which > 2) return set_error(RK_E_INVALID_ARGUMENT, "bad exp arguments");
+  if (n == 0) return RK_OK;
+  if (!x || !y) return set_error(RK_E_INVALID_ARGUMENT, "null array");
+  exp_eval_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, y, n, which);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RK_OK : cuda_error(e, "exp_eval_kernel launch");
 }
 
 const char* rk_status_string(int32_t code) {

@@ -315,3 +315,29 @@ def test_simpler_split_step_1d_parity(rk):
         Uo, h_or, _, _ = osp.simpler_split_step_1d(kin, Uo, P, w.dt, D, dx, w.rtol, w.atol, 4,
                                                    h_cell=h_or, replay=[_replay_of(r) for r in tr])
         _assert_state_close(Ug.cpu().numpy(), Uo, mech.n_species, f"split step {step}")
+
+
+def _ulps(a, b):
+    ia = a.view(np.int64)
+    ib = b.view(np.int64)
+    return np.abs(ia - ib)
+
+
+def test_table_exp_matches_cuda_exp(rk):
+    """The kernels' table-driven exp (Tang 1989) against CUDA's exp: within 2 ulp
+    on the fast path, identical on the fallback range and special values."""
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.uniform(-707.9, 707.9, 400000), rng.uniform(-3, 3, 200000),
+                        rng.uniform(-1e-3, 1e-3, 50000), np.linspace(-745, 709.7, 5001),
+                        [0.0, -0.0, 1e-300, -1e-300, 708.0, -708.0, 709.78, -745.2, np.inf, -np.inf, np.nan]])
+    xt = torch.tensor(x, device="cuda")
+    ref = torch.exp(xt).cpu().numpy()
+    for which, sign in ((0, 1.0), (1, 1.0), (2, -1.0)):
+        y = rk.eval_exp(xt, which).cpu().numpy()
+        r = ref if sign > 0 else torch.exp(-xt).cpu().numpy()
+        fin = np.isfinite(r) & (r > 1e-300) & (r < 1e300)
+        assert np.max(_ulps(y[fin], r[fin])) <= 2
+        nf = ~fin
+        np.testing.assert_array_equal(np.isnan(y[nf]), np.isnan(r[nf]))
+        ok = ~np.isnan(r[nf])
+        assert np.all(np.abs(y[nf][ok] - r[nf][ok]) <= 1e-300 + 4e-16 * np.abs(r[nf][ok]))
