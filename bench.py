@@ -36,6 +36,7 @@ D_DIFF = 1.0e-4  # m^2/s
 LENGTH = 1.0e-2  # m
 P_ATM = 101325.0
 L2_FLUSH_BYTES = 256 << 20
+PREC = {"fp64": 0, "mixed": 1}
 
 
 def _env_int(k, d):
@@ -207,7 +208,8 @@ def run_plain(args):
     hc = torch.zeros(U.shape[0], dtype=torch.float64, device="cuda")
     for _ in range(args.plain_steps):
         rk.simpler_split_step(m, U, w.dt, D_DIFF, LENGTH / U.shape[0], w.rtol, w.atol, w.krylov_dim, h_cell=hc,
-                              opts=rk.Opts(lanes_per_cell=args.lanes))
+                              opts=rk.Opts(lanes_per_cell=args.lanes, cells_per_block=args.cells_per_block,
+                                           precision=PREC[args.precision]))
     torch.cuda.synchronize()
     print(json.dumps({"plain_steps": args.plain_steps, "T_max": float(U[:, -1].max())}))
     return 0
@@ -245,13 +247,31 @@ def run_ours(args, rank, world, local_rank):
 
     def step(stats=None, events=None):
         rk.simpler_split_step(m, U, w.dt, D_DIFF, dx, w.rtol, w.atol, M, h_cell=hc, stats=stats,
-                              opts=rk.Opts(events=events, lanes_per_cell=args.lanes), workspace=ws,
+                              opts=rk.Opts(events=events, lanes_per_cell=args.lanes, cells_per_block=args.cells_per_block, precision=PREC[args.precision]), workspace=ws,
                               stream=stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    U_start, hc_start = U.clone(), hc.clone()  # the end-to-end pass replays the same steps
+    U_start, hc_start = U.clone(), hc.clone()  # every pass below replays the same steps
+
+    def restore():
+        U.copy_(U_start)
+        hc.copy_(hc_start)
+
+    # ---- the split step captured once in a CUDA graph, replayed every step
+    stats_step = torch.zeros(npts, 4, dtype=torch.int32, device=dev)
+    graph = torch.cuda.CUDAGraph()
+    cap_stream = torch.cuda.Stream(device=dev)
+    cap_stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(cap_stream):
+        with torch.cuda.graph(graph, stream=cap_stream, capture_error_mode="relaxed"):
+            rk.simpler_split_step(m, U, w.dt, D_DIFF, dx, w.rtol, w.atol, M, h_cell=hc, stats=stats_step,
+                                  opts=rk.Opts(lanes_per_cell=args.lanes, cells_per_block=args.cells_per_block, precision=PREC[args.precision]), workspace=ws, stream=cap_stream)
+    torch.cuda.current_stream().wait_stream(cap_stream)
+    torch.cuda.synchronize()
+    restore()
+    torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -259,14 +279,14 @@ def run_ours(args, rank, world, local_rank):
         for k in range(args.steps):
             flush.fill_(float(k))  # evict the previous step's data from L2 (outside the timed events)
             ev[k][0].record(stream)
-            step(stats_all[k], kev[k])
+            graph.replay()
             ev[k][1].record(stream)
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    U_graph = U.clone()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    kern_ms = [a.elapsed_time(b) for a, b in kev]
     t_total = sum(step_ms) * 1e-3
     if dist:
         t = torch.tensor([t_total], device=dev, dtype=torch.float64)
@@ -274,11 +294,21 @@ def run_ours(args, rank, world, local_rank):
         t_total = float(t.item())
     value = world * npts * args.steps / t_total
 
+    # ---- roofline pass: the same steps launched eagerly, the integration
+    # kernel bracketed by events on its own launch stream, per-step statistics
+    restore()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        step(stats_all[k], kev[k])
+    torch.cuda.synchronize()
+    kern_ms = [a.elapsed_time(b) for a, b in kev]
+    graph_matches_eager = bool(torch.equal(U, U_graph))
+
     # ---- end to end through the public API with host buffers: the same steps
     # from the same state, with the state copied in from pinned host memory and
     # the result copied back every step
+    restore()
     pinned = U_start.cpu().pin_memory()
-    hc.copy_(hc_start)
     e2e_steps = args.steps
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -317,11 +347,13 @@ def run_ours(args, rank, world, local_rank):
     line = {
         "metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f64+f32 (mixed)", "data": "synthetic",
         "config": {"workload": "flame1d 1-D reaction-diffusion, 2048 points, 30 species / 150 reactions "
                                "(4 third-body, 2 Troe), Simpler split steps of 1e-7 s, ROK4E M=4, rtol 1e-6, "
-                               "atol 1e-10, FP64", "points": npts, "l2": "flushed (256 MB write) between steps",
-                   "parallelism": f"replicas x{world}"},
+                               "atol 1e-10", "precision": args.precision, "points": npts,
+                   "l2": "flushed (256 MB write) between steps", "parallelism": f"replicas x{world}",
+                   "lanes_per_cell": args.lanes or 32, "cells_per_block": args.cells_per_block},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_nominal, "unit": "TFLOP/s",
                      "frac": achieved / peak_nominal, "traffic": None,
                      "kernel": "rok4e_integrate_kernel<32>", "kernel_ms_per_step": 1e3 * kern_total / args.steps,
@@ -333,6 +365,8 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": "cell-steps/s", "h2d_bytes_per_step": int(U.numel() * 8),
                 "d2h_bytes_per_step": int(U.numel() * 8), "steps": e2e_steps},
         "gpu_launches": 5 * args.steps,
+        "cuda_graph": {"timed_region": "one captured split step replayed per step",
+                       "matches_eager_bitwise": graph_matches_eager},
         "clocks": clocks,
         "cells_failed": bad,
         "substeps_per_cell_step": float(st[:, :, 0].mean()),
@@ -353,6 +387,8 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=0,
                     help="run this many untimed split steps and exit (profiling case)")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per cell (0: library default)")
+    ap.add_argument("--cells-per-block", type=int, default=4, help="cells per block (0: library default)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

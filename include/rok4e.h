@@ -129,9 +129,18 @@ int rk_chem_rhs(const rk_mech* mech, const double* Y, const double* src, double 
 /* Jacobian-vector products JV[c] = J(Y[c]) V[c].  mode 0: analytic (exact
  * derivative of rk_chem_rhs); mode 1: forward difference
  * (f(u + d v) - f(u)) / d with d = sqrt(eps) (1 + ||u||_2) / ||v||_2, as in
- * the matrix-free products of Sec. 4.3.  All arrays device [ncell x N]. */
+ * the matrix-free products of Sec. 4.3; mode 2: the analytic product
+ * evaluated in FP32 (the mixed-precision integrator's J v).  All arrays
+ * device [ncell x N]. */
 int rk_chem_jvp(const rk_mech* mech, const double* Y, const double* V, double p, double* JV,
                 int64_t ncell, int32_t mode, void* stream);
+
+/* Mixed-precision source term: as rk_chem_rhs, with the forward-rate
+ * exponentials and w = nu^T q in FP32 while the Gibbs factors, 1/Kc, the
+ * rates of progress q = m (k prod C - k/Kc prod C) and the assembly of f stay
+ * FP64 (the right-hand side the mixed-precision integrator uses). */
+int rk_chem_rhs_mixed(const rk_mech* mech, const double* Y, const double* src, double p,
+                      double* dYdt, int64_t ncell, void* stream);
 
 /* ---- ROK4E integration (Sec. 4, Algorithm 1) ---------------------------------
  * Options; pass NULL for defaults (all zero fields mean "default"). */
@@ -143,7 +152,11 @@ typedef struct rk_opts {
   double h0;              /* first step when h_cell is NULL or holds <= 0; <= 0: dt */
   double fixed_h;         /* > 0: fixed steps of this size, no error control */
   int32_t trace_cap;      /* attempts recorded per cell into trace (0: none) */
-  int32_t reserved0;
+  int32_t precision;      /* 0: FP64 throughout (default); 1: mixed -- forward-rate
+                             exponentials, w = nu^T q, Jacobian-vector products and
+                             Arnoldi inner products in FP32; Gibbs factors, 1/Kc,
+                             rates of progress, stage solves, error norm and state
+                             update in FP64 */
   double* trace;          /* device [ncell x trace_cap]: +h accepted, -h rejected, 0 unused */
   void* ev_begin;         /* optional cudaEvent_t recorded on the stream right before the */
   void* ev_end;           /* integration kernel and right after it (timing hook), or NULL */
@@ -200,7 +213,8 @@ int rk_diffusion_1d(const double* U, double* TU, int64_t npts, int32_t nvar, dou
 
 /* ---- diagnostics ---------------------------------------------------------------
  * Throughput probes of the arithmetic units used by the roofline:
- *  kind 0: FP64 FMA, 1: FP32 FMA, 2: FP64 exp().  Launches a dependent-FMA
+ *  kind 0: FP64 FMA, 1: FP32 FMA, 2: FP64 exp(), 3: double<->float
+ *  conversions.  Launches a dependent-operation
  *  grid sized to the device and returns the operation rate (ops/s) measured
  *  with CUDA events in *ops_per_s.  Synchronous. */
 int rk_probe_throughput(int32_t kind, double* ops_per_s);

@@ -27,7 +27,7 @@ def _L():
         _LIB = _native.load()
     return _LIB
 
-__all__ = ["Mechanism", "mech_load", "mech_validate", "chem_rhs", "chem_jvp", "rok4e_integrate",
+__all__ = ["Mechanism", "mech_load", "mech_validate", "chem_rhs", "chem_rhs_mixed", "chem_jvp", "rok4e_integrate",
            "rok4e_workspace_size", "simpler_split_step", "simpler_split_step_workspace_size",
            "diffusion_1d", "probe_throughput", "eval_exp", "Opts", "RokError", "STATS_FIELDS"]
 
@@ -127,12 +127,13 @@ class Opts:
     """Integration options (rk_opts); None fields keep the library defaults."""
 
     def __init__(self, jv_mode=0, max_attempts=0, lanes_per_cell=0, cells_per_block=0, h0=0.0, fixed_h=0.0,
-                 trace=None, events=None):
+                 trace=None, events=None, precision=0):
         self.jv_mode, self.max_attempts = jv_mode, max_attempts
         self.lanes_per_cell, self.cells_per_block = lanes_per_cell, cells_per_block
         self.h0, self.fixed_h = h0, fixed_h
         self.trace = trace  # CUDA float64 tensor [ncell, cap] or None
         self.events = events  # (begin, end) torch.cuda.Event pair around the integration kernel
+        self.precision = precision  # 0 FP64, 1 mixed (FP32 rates/contraction/J v/inner products)
 
     def c(self):
         cap = 0 if self.trace is None else int(self.trace.shape[-1])
@@ -141,7 +142,7 @@ class Opts:
         if self.events is not None:
             eb, ee = (ctypes.c_void_p(e.cuda_event) for e in self.events)
         return RkOpts(self.jv_mode, self.max_attempts, self.lanes_per_cell, self.cells_per_block, self.h0,
-                      self.fixed_h, cap, 0, tp, eb, ee)
+                      self.fixed_h, cap, self.precision, tp, eb, ee)
 
 
 def _ncell(Y, m):
@@ -155,6 +156,14 @@ def chem_rhs(m: Mechanism, Y, p, src=None, out=None, stream=None):
     out = torch.empty_like(Y) if out is None else out
     _check(_L().rk_chem_rhs(m.handle, _dptr(Y, "Y"), _dptr(src, "src", Y.numel()), float(p),
                             _dptr(out, "out", Y.numel()), n, _stream_ptr(stream)), "rk_chem_rhs")
+    return out
+
+
+def chem_rhs_mixed(m: Mechanism, Y, p, src=None, out=None, stream=None):
+    n = _ncell(Y, m)
+    out = torch.empty_like(Y) if out is None else out
+    _check(_L().rk_chem_rhs_mixed(m.handle, _dptr(Y, "Y"), _dptr(src, "src", Y.numel()), float(p),
+                                  _dptr(out, "out", Y.numel()), n, _stream_ptr(stream)), "rk_chem_rhs_mixed")
     return out
 
 

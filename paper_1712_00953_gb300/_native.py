@@ -37,7 +37,7 @@ class RkOpts(ctypes.Structure):
         ("h0", ctypes.c_double),
         ("fixed_h", ctypes.c_double),
         ("trace_cap", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
         ("trace", ctypes.c_void_p),
         ("ev_begin", ctypes.c_void_p),
         ("ev_end", ctypes.c_void_p),
@@ -54,6 +54,8 @@ SIGNATURES = {
                                    ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "rk_chem_jvp": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                    ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p]),
+    "rk_chem_rhs_mixed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "rk_rok4e_workspace_size": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                                   ctypes.POINTER(RkOpts)]),
     "rk_rok4e_integrate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,

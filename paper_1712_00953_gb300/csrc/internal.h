@@ -40,6 +40,8 @@ struct MechLayout {
   int64_t off_slots = 0;  // uint32 per reaction: ra | rb<<8 | pa<<16 | pb<<24 (ns = empty)
   int64_t off_meta = 0;   // int32 per reaction: kind | rev<<2 | (dnu+4)<<4 | slot<<8
   int64_t off_csr_ptr = 0, off_csr_j = 0;
+  // FP32 copies read by the reduced-precision Jacobian-vector product
+  int64_t off_Wf = 0, off_invWf = 0, off_bf = 0, off_EaRf = 0, off_efff = 0, off_csr_nuf = 0;
   int64_t bytes = 0;
 };
 

@@ -181,6 +181,12 @@ bool pack_mechanism(const void* vdesc, HostMech* out, std::string* err) {
   L.off_meta = take(4 * (int64_t)nr);
   L.off_csr_ptr = take(4 * (int64_t)(ns + 1));
   L.off_csr_j = take(4 * (int64_t)nnz);
+  L.off_Wf = take(4 * (int64_t)ns);
+  L.off_invWf = take(4 * (int64_t)ns);
+  L.off_bf = take(4 * (int64_t)nr);
+  L.off_EaRf = take(4 * (int64_t)nr);
+  L.off_efff = take(4 * (int64_t)L.ntb * ns);
+  L.off_csr_nuf = take(4 * (int64_t)nnz);
   L.bytes = align16(off);
 
   std::vector<unsigned char> buf((size_t)L.bytes, 0);
@@ -259,6 +265,17 @@ bool pack_mechanism(const void* vdesc, HostMech* out, std::string* err) {
     }
   }
   I(L.off_csr_ptr)[ns] = pos;
+  auto F = [&](int64_t o) { return reinterpret_cast<float*>(buf.data() + o); };
+  for (int k = 0; k < ns; ++k) {
+    F(L.off_Wf)[k] = (float)D(L.off_W)[k];
+    F(L.off_invWf)[k] = (float)D(L.off_invW)[k];
+  }
+  for (int r = 0; r < nr; ++r) {
+    F(L.off_bf)[r] = (float)D(L.off_b)[r];
+    F(L.off_EaRf)[r] = (float)D(L.off_EaR)[r];
+  }
+  for (int i = 0; i < L.ntb * ns; ++i) F(L.off_efff)[i] = (float)D(L.off_eff)[i];
+  for (int i = 0; i < nnz; ++i) F(L.off_csr_nuf)[i] = (float)D(L.off_csr_nu)[i];
 
   out->L = L;
   out->packed.swap(buf);

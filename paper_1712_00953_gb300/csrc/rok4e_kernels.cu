@@ -115,6 +115,19 @@ __device__ __forceinline__ void exp_pm(double x, const double* __restrict__ tab,
   *em = exp_scale(fma(tm, pm, tm), km >> 7);
 }
 
+// exp(x) with an FP32 core for the mixed-precision mode: x log2 e = n + f
+// with n an integer (FP64, shifter trick) and |f| <= 1/2; 2^f from the FP32
+// exp2f; the scaling by 2^n is an integer add to the exponent.  Relative
+// error ~3e-7 (the FP32 exp2f); FP64 ops: 3 plus two conversions.
+__device__ __forceinline__ double exp_mixed(double x) {
+  if ((__double2hiint(x) & 0x7fffffff) >= 0x40862000) return exp(x);
+  const double t = fma(x, 1.4426950408889634, EXP_SHIFTER);
+  const int n = __double2loint(t);
+  const double nd = t - EXP_SHIFTER;
+  const float f = __double2float_rn(fma(x, 1.4426950408889634, -nd));
+  return exp_scale((double)exp2f(f), n);
+}
+
 __device__ inline void load_exp_table(double* dst) {
   for (int i = threadIdx.x; i < RK_EXP2_TABLE_N; i += blockDim.x) dst[i] = c_exp2_table[i];
 }
@@ -136,6 +149,7 @@ struct MechView {
   const double *W, *invW, *Tmid, *lo, *hi, *lnA, *bexp, *EaR, *eff, *fo, *csr_nu;
   const uint32_t* slots;
   const int32_t *meta, *csr_ptr, *csr_j;
+  const float *Wf, *invWf, *bf, *EaRf, *efff, *csr_nuf;  // FP32 copies
 };
 
 __host__ __device__ inline MechView make_view(const unsigned char* base, const MechLayout& L) {
@@ -159,6 +173,12 @@ __host__ __device__ inline MechView make_view(const unsigned char* base, const M
   m.meta = reinterpret_cast<const int32_t*>(base + L.off_meta);
   m.csr_ptr = reinterpret_cast<const int32_t*>(base + L.off_csr_ptr);
   m.csr_j = reinterpret_cast<const int32_t*>(base + L.off_csr_j);
+  m.Wf = reinterpret_cast<const float*>(base + L.off_Wf);
+  m.invWf = reinterpret_cast<const float*>(base + L.off_invWf);
+  m.bf = reinterpret_cast<const float*>(base + L.off_bf);
+  m.EaRf = reinterpret_cast<const float*>(base + L.off_EaRf);
+  m.efff = reinterpret_cast<const float*>(base + L.off_efff);
+  m.csr_nuf = reinterpret_cast<const float*>(base + L.off_csr_nuf);
   return m;
 }
 
@@ -170,10 +190,12 @@ struct SlotLayout {
   int q, kc, krc;                             // reactions
   int tb;                                     // [ntb][4]: [M], dk/d[M], dlnk/dT, 1/Kc
   int H, LU, piv, red;                        // small
+  int fbase;  // FP32 region (mixed precision only), offset in doubles
+  int fC, fdC, fh, fcp, fdcp, fom, fq, fkc, fkr, ftb, fQ, fw;  // offsets in floats from fbase
   int stride;
 };
 
-static SlotLayout make_slot(const MechLayout& L, int M) {
+static SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false) {
   SlotLayout s;
   s.N = L.ns + 1;
   s.ns = L.ns;
@@ -214,6 +236,30 @@ static SlotLayout make_slot(const MechLayout& L, int M) {
   s.LU = take(MAXM * MAXM);
   s.piv = take(MAXM);
   s.red = take(4);
+  s.fbase = o;
+  int fo = 0;
+  auto ftake = [&](int n) {
+    const int r = fo;
+    fo += (n + 3) & ~3;  // 16-byte alignment
+    return r;
+  };
+  if (mixed) {
+    s.fC = ftake(ns1);
+    s.fdC = ftake(ns1);
+    s.fh = ftake(ns1);
+    s.fcp = ftake(ns1);
+    s.fdcp = ftake(ns1);
+    s.fom = ftake(ns1);
+    s.fq = ftake(L.nr > 0 ? L.nr : 1);
+    s.fkc = ftake(L.nr > 0 ? L.nr : 1);
+    s.fkr = ftake(L.nr > 0 ? L.nr : 1);
+    s.ftb = ftake(4 * (L.ntb > 0 ? L.ntb : 1));
+    s.fQ = ftake(Nq * M);
+    s.fw = ftake(Nq);
+  } else {
+    s.fC = s.fdC = s.fh = s.fcp = s.fdcp = s.fom = s.fq = s.fkc = s.fkr = s.ftb = s.fQ = s.fw = 0;
+  }
+  o += (fo + 1) / 2;
   s.stride = (o + 3) & ~3;
   return s;
 }
@@ -229,7 +275,8 @@ struct Grp {
     mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (l - lane));
   }
   __device__ __forceinline__ void sync() const { __syncwarp(mask); }
-  __device__ __forceinline__ double sum(double v) const {
+  template <typename T>
+  __device__ __forceinline__ T sum(T v) const {
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
     return v;
@@ -251,6 +298,58 @@ struct Grp {
   }
 };
 
+// Sum K values (K a power of two, K <= G) across the G lanes of a group; on
+// return every lane holds all K sums.  Reduce-scatter: at each of the first
+// log2 K butterfly levels a lane keeps half of its values and adds its
+// partner's copy of that half, so the adds per lane are K - 1 + log2(G/K)
+// instead of K log2 G; the sums are then broadcast from the lanes that hold
+// them.  All lanes end with bit-identical values.
+template <int G, int K, typename T>
+__device__ __forceinline__ void sum_many(const Grp<G>& g, T (&v)[K]) {
+  static_assert((K & (K - 1)) == 0 && K <= G, "K must be a power of two <= G");
+  constexpr int LG = (G == 32 ? 5 : G == 16 ? 4 : G == 8 ? 3 : G == 4 ? 2 : G == 2 ? 1 : 0);
+  constexpr int LK = (K == 8 ? 3 : K == 4 ? 2 : K == 2 ? 1 : 0);
+#pragma unroll
+  for (int l = 0; l < LK; ++l) {
+    const int o = G >> (l + 1);
+    const int half = K >> (l + 1);
+    const bool hi = (g.lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      const T send = hi ? v[j] : v[j + half];
+      const T keep = hi ? v[j + half] : v[j];
+      v[j] = keep + __shfl_xor_sync(g.mask, send, o, G);
+    }
+  }
+#pragma unroll
+  for (int o = G >> (LK + 1); o > 0; o >>= 1) v[0] += __shfl_xor_sync(g.mask, v[0], o, G);
+  const T mine = v[0];
+#pragma unroll
+  for (int t = 0; t < K; ++t) v[t] = __shfl_sync(g.mask, mine, t << (LG - LK), G);
+}
+
+// Sum the first n (<= MAXM) entries of v across the group (entries past n
+// must be zero); dispatches on n to the smallest power-of-two reduction.
+template <int G, typename T>
+__device__ __forceinline__ void sum_first(const Grp<G>& g, T (&v)[MAXM], int n) {
+  static_assert(G >= MAXM, "a group needs at least MAXM lanes");
+  if (n <= 1) {
+    v[0] = g.sum(v[0]);
+  } else if (n <= 2) {
+    T t[2] = {v[0], v[1]};
+    sum_many<G, 2>(g, t);
+    v[0] = t[0];
+    v[1] = t[1];
+  } else if (n <= 4) {
+    T t[4] = {v[0], v[1], v[2], v[3]};
+    sum_many<G, 4>(g, t);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = t[i];
+  } else {
+    sum_many<G, MAXM>(g, v);
+  }
+}
+
 // Scalars of the last right-hand-side evaluation that the analytic
 // Jacobian-vector product needs (uniform across the group).
 struct CellScalars {
@@ -261,6 +360,7 @@ struct SlotPtrs {
   double *u, *src, *fn, *arg, *fr, *F, *w, *Q, *K;
   double *C, *dC, *cp, *hRT, *dcp, *gRT, *E, *Einv, *om, *q, *kc, *krc, *tb;
   double *H, *LU, *piv, *red;
+  float *fC, *fdC, *fh, *fcp, *fdcp, *fom, *fq, *fkc, *fkr, *ftb, *fQ, *fw;  // mixed precision
   int Nq;  // stride between Krylov / stage vectors
 };
 
@@ -292,6 +392,19 @@ __device__ inline SlotPtrs slot_ptrs(double* b, const SlotLayout& s) {
   p.LU = b + s.LU;
   p.piv = b + s.piv;
   p.red = b + s.red;
+  float* f = reinterpret_cast<float*>(b + s.fbase);
+  p.fC = f + s.fC;
+  p.fdC = f + s.fdC;
+  p.fh = f + s.fh;
+  p.fcp = f + s.fcp;
+  p.fdcp = f + s.fdcp;
+  p.fom = f + s.fom;
+  p.fq = f + s.fq;
+  p.fkc = f + s.fkc;
+  p.fkr = f + s.fkr;
+  p.ftb = f + s.ftb;
+  p.fQ = f + s.fQ;
+  p.fw = f + s.fw;
   p.Nq = (s.N + 1) & ~1;
   return p;
 }
@@ -302,7 +415,7 @@ __device__ inline SlotPtrs slot_ptrs(double* b, const SlotLayout& s) {
 // Jacobian-vector product reuses are kept (rate coefficients, w, d(cp/R)/dT
 // and the cell scalars).  Not inlined: chem_rhs and the integrator execute the
 // same instructions, so R(u) - R(u) is exactly zero in a steady-state cell.
-template <int G>
+template <int G, bool MIXED = false>
 __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, const double* uu,
                                       const double* src, double p, double* out, bool cache,
                                       CellScalars* cs) {
@@ -327,7 +440,15 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     s.hRT[k] = hrt;
     s.gRT[k] = grt;
     ghi = max(ghi, __double2hiint(grt) & 0x7fffffff);
-    if (cache) s.dcp[k] = fma(fma(c[16 * ns + k], T, c[15 * ns + k]), T, c[14 * ns + k]) * T + a2;
+    if (cache) {
+      const double dcp = fma(fma(c[16 * ns + k], T, c[15 * ns + k]), T, c[14 * ns + k]) * T + a2;
+      s.dcp[k] = dcp;
+      if (MIXED) {
+        s.fh[k] = __double2float_rn(hrt);
+        s.fcp[k] = __double2float_rn(cp);
+        s.fdcp[k] = __double2float_rn(dcp);
+      }
+    }
     S = fma(uu[k], m.invW[k], S);
   }
   S = g.sum(S);
@@ -335,9 +456,30 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
   const bool direct_kc = ghi >= G_OVERFLOW_HI;  // |g/RT| >= 170, also NaN
   const double rho = p / (R_GAS * T * S);
   const double invrho = 1.0 / rho;
+  // concentrations, Gibbs factors, and (for up to MAXM pressure-dependent
+  // reactions) the third-body concentrations [M]_t = sum_k eff_tk C_k
+  const bool coop_tb = m.ntb > 0 && m.ntb <= MAXM;
+  double mp[MAXM];
+#pragma unroll
+  for (int t = 0; t < MAXM; ++t) mp[t] = 0.0;
   for (int k = g.lane; k < ns; k += G) {
-    s.C[k] = rho * uu[k] * m.invW[k];
+    const double Ck = rho * uu[k] * m.invW[k];
+    s.C[k] = Ck;
+    if (MIXED && cache) s.fC[k] = __double2float_rn(Ck);
     if (!direct_kc) exp_pm(s.gRT[k], m.etab, &s.E[k], &s.Einv[k]);
+    if (coop_tb) {
+#pragma unroll
+      for (int t = 0; t < MAXM; ++t)
+        if (t < m.ntb) mp[t] = fma(m.eff[t * ns + k], Ck, mp[t]);
+    }
+  }
+  if (coop_tb) {
+    sum_first<G>(g, mp, m.ntb);
+    if (g.lane == 0) {
+#pragma unroll
+      for (int t = 0; t < MAXM; ++t)
+        if (t < m.ntb) s.tb[4 * t] = mp[t];
+    }
   }
   g.sync();
   // reactions: rate coefficients and rates of progress
@@ -345,6 +487,7 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
   const double invRTp = P_REF / (R_GAS * T);
   const double lnRTp = log(RTp);
   const double m_lnRTp = -lnRTp;
+  double shq = 0.0;  // mixed mode: heat release sum_j q_j Delta H_j / RT in FP64
   for (int j = g.lane; j < m.nr; j += G) {
     const uint32_t sl = m.slots[j];
     const int ra = sl & 255, rb = (sl >> 8) & 255, pa = (sl >> 16) & 255, pb = sl >> 24;
@@ -352,7 +495,8 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     const int kind = meta & 3;
     const bool rev = (meta >> 2) & 1;
     const int dnu = ((meta >> 4) & 15) - 4;
-    double k = exp_fast(m.lnA[j] + m.bexp[j] * lnT - m.EaR[j] * invT, m.etab);
+    const double lnk = m.lnA[j] + m.bexp[j] * lnT - m.EaR[j] * invT;
+    double k = MIXED ? exp_mixed(lnk) : exp_fast(lnk, m.etab);
     const double Pf = s.C[ra] * s.C[rb];
     const double Pb = s.C[pa] * s.C[pb];
     double rfac = 0.0;  // 1/Kc
@@ -368,17 +512,21 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     double mfac = 1.0;
     if (kind != 0) {
       const int slot = meta >> 8;
-      const double* e = m.eff + (size_t)slot * ns;
-      double Mc = 0.0;
-      for (int q = 0; q < ns; ++q) Mc = fma(e[q], s.C[q], Mc);
+      double Mc;
+      if (coop_tb) {
+        Mc = s.tb[4 * slot];
+      } else {
+        const double* e = m.eff + (size_t)slot * ns;
+        Mc = 0.0;
+        for (int q = 0; q < ns; ++q) Mc = fma(e[q], s.C[q], Mc);
+      }
       double dkdM = 0.0, dlnk = (m.bexp[j] + m.EaR[j] * invT) * invT;
       if (kind == 1) {
         mfac = Mc;
       } else {
         const double* fo = m.fo + (size_t)slot * FO_STRIDE;
         const double k0 = exp_fast(fo[0] + fo[1] * lnT - fo[2] * invT, m.etab);
-        const double dlnk0 = (fo[1] + fo[2] * invT) * invT;
-        double Pr = k0 * Mc / k;
+        double Pr = k0 * Mc * (1.0 / k);
         if (!(Pr > 1e-300)) Pr = 1e-300;
         const double a = fo[3];
         const double e3 = exp_fast(-T * fo[4], m.etab), e1 = exp_fast(-T * fo[5], m.etab);
@@ -387,22 +535,25 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
         const double lFc = log10(Fc);
         const double cc = -0.4 - 0.67 * lFc;
         const double nn = 0.75 - 1.27 * lFc;
-        const double L = log10(Pr);
-        const double x = L + cc;
+        const double x = log10(Pr) + cc;
         const double D = nn - 0.14 * x;
-        const double f1 = x / D;
-        const double den = 1.0 + f1 * f1;
-        const double lF = lFc / den;
-        const double F = exp_fast(lF * 2.302585092994046, m.etab);  // 10^lF
-        const double onePr = 1.0 + Pr;
-        const double dlF_dL = -lFc * 2.0 * f1 / (den * den) * nn / (D * D);
-        const double df1 = (-0.67 * D + 1.1762 * x) / (D * D);
-        const double dlF_dlFc = 1.0 / den - lFc * 2.0 * f1 / (den * den) * df1;
-        const double dFc = -(1.0 - a) * fo[4] * e3 - a * fo[5] * e1 + (fo[6] > 0.0 ? fo[6] * invT * invT * e2 : 0.0);
-        const double gg = 1.0 / onePr + dlF_dL;
-        dlnk = dlnk + gg * (dlnk0 - dlnk) + dlF_dlFc * dFc / Fc;
-        dkdM = k0 * F / onePr * gg;
-        k = k * Pr / onePr * F;
+        const double iD = 1.0 / D;
+        const double f1 = x * iD;
+        const double iden = 1.0 / (1.0 + f1 * f1);
+        const double F = exp_fast(lFc * iden * 2.302585092994046, m.etab);  // 10^(lFc / (1 + f1^2))
+        const double iOnePr = 1.0 / (1.0 + Pr);
+        if (cache) {  // d ln k / dT and d k / d[M] for the analytic J v
+          const double dlnk0 = (fo[1] + fo[2] * invT) * invT;
+          const double w2 = lFc * 2.0 * f1 * iden * iden;
+          const double dlF_dL = -w2 * nn * iD * iD;
+          const double df1 = (-0.67 * D + 1.1762 * x) * iD * iD;
+          const double dlF_dlFc = iden - w2 * df1;
+          const double dFc = -(1.0 - a) * fo[4] * e3 - a * fo[5] * e1 + (fo[6] > 0.0 ? fo[6] * invT * invT * e2 : 0.0);
+          const double gg = iOnePr + dlF_dL;
+          dlnk = dlnk + gg * (dlnk0 - dlnk) + dlF_dlFc * dFc * (1.0 / Fc);
+          dkdM = k0 * F * iOnePr * gg;
+        }
+        k = k * Pr * iOnePr * F;
       }
       if (cache) {
         double* t = s.tb + 4 * (meta >> 8);
@@ -410,30 +561,57 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
         t[1] = dkdM;
         t[2] = dlnk;
         t[3] = rfac;
+        if (MIXED) {
+          float* tf = s.ftb + 4 * (meta >> 8);
+          tf[0] = __double2float_rn(Mc);
+          tf[1] = __double2float_rn(dkdM);
+          tf[2] = __double2float_rn(dlnk);
+          tf[3] = __double2float_rn(rfac);
+        }
       }
     }
     const double kr = k * rfac;
-    s.q[j] = mfac * (k * Pf - kr * Pb);
+    const double qj = mfac * (k * Pf - kr * Pb);
+    s.q[j] = qj;
+    if (MIXED) {
+      s.fq[j] = __double2float_rn(qj);
+      shq = fma(qj, s.hRT[pa] + s.hRT[pb] - s.hRT[ra] - s.hRT[rb], shq);
+    }
     if (cache) {
       s.kc[j] = k;
       s.krc[j] = kr;
+      if (MIXED) {
+        s.fkc[j] = __double2float_rn(k);
+        s.fkr[j] = __double2float_rn(kr);
+      }
     }
   }
   g.sync();
   // species pass 2: w = nu^T q, dY/dt and the sums of the temperature equation
-  double Sh = 0.0, cb = 0.0;
+  double Sh = MIXED ? shq : 0.0, cb = 0.0;
   for (int k = g.lane; k < ns; k += G) {
     double om = 0.0;
     const int e0 = m.csr_ptr[k], e1 = m.csr_ptr[k + 1];
-    for (int e = e0; e < e1; ++e) om = fma(m.csr_nu[e], s.q[m.csr_j[e]], om);
+    if (MIXED) {  // w = nu^T q in FP32 (q itself was formed in FP64)
+      float omf = 0.f;
+      for (int e = e0; e < e1; ++e) omf = fmaf(m.csr_nuf[e], s.fq[m.csr_j[e]], omf);
+      om = (double)omf;
+      if (cache) s.fom[k] = omf;
+    } else {
+      for (int e = e0; e < e1; ++e) om = fma(m.csr_nu[e], s.q[m.csr_j[e]], om);
+    }
     if (cache) s.om[k] = om;
     const double r = __dmul_rn(__dmul_rn(m.W[k], om), invrho);
     out[k] = src ? __dadd_rn(r, src[k]) : r;
-    Sh = fma(s.hRT[k], om, Sh);
+    if (!MIXED) Sh = fma(s.hRT[k], om, Sh);
     cb = fma(uu[k] * s.cp[k], m.invW[k], cb);
   }
-  Sh = g.sum(Sh);
-  cb = g.sum(cb);
+  {
+    double t2[2] = {Sh, cb};
+    sum_many<G, 2>(g, t2);
+    Sh = t2[0];
+    cb = t2[1];
+  }
   if (g.lane == 0) {
     const double r = -T * Sh / (rho * cb);
     out[ns] = src ? __dadd_rn(r, src[ns]) : r;
@@ -466,7 +644,20 @@ __device__ __noinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, cons
   for (int k = g.lane; k < ns; k += G) a = fma(v[k], m.invW[k], a);
   a = g.sum(a);
   const double drr = -fma(a, cs.invS, vT * invT);  // d rho / rho
-  for (int k = g.lane; k < ns; k += G) s.dC[k] = fma(s.C[k], drr, cs.rho * v[k] * m.invW[k]);
+  const bool coop_tb = m.ntb > 0 && m.ntb <= MAXM;
+  double mp[MAXM];
+#pragma unroll
+  for (int t = 0; t < MAXM; ++t) mp[t] = 0.0;
+  for (int k = g.lane; k < ns; k += G) {
+    const double dCk = fma(s.C[k], drr, cs.rho * v[k] * m.invW[k]);
+    s.dC[k] = dCk;
+    if (coop_tb) {
+#pragma unroll
+      for (int t = 0; t < MAXM; ++t)
+        if (t < m.ntb) mp[t] = fma(m.eff[t * ns + k], dCk, mp[t]);
+    }
+  }
+  if (coop_tb) sum_first<G>(g, mp, m.ntb);  // d[M]_t, identical on every lane
   g.sync();
   for (int j = g.lane; j < m.nr; j += G) {
     const uint32_t sl = m.slots[j];
@@ -485,10 +676,17 @@ __device__ __noinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, cons
     if (kind == 2) dlnk = s.tb[4 * (meta >> 8) + 2];
     double dq = k * fma(dlnk * vT, Pf, dPf) - kr * fma((dlnk - dlnKc) * vT, Pb, dPb);
     if (kind != 0) {
-      const double* t = s.tb + 4 * (meta >> 8);
-      const double* e = m.eff + (size_t)(meta >> 8) * ns;
+      const int slot = meta >> 8;
+      const double* t = s.tb + 4 * slot;
       double dM = 0.0;
-      for (int q = 0; q < ns; ++q) dM = fma(e[q], s.dC[q], dM);
+      if (coop_tb) {
+#pragma unroll
+        for (int q = 0; q < MAXM; ++q)
+          if (q == slot) dM = mp[q];
+      } else {
+        const double* e = m.eff + (size_t)slot * ns;
+        for (int q = 0; q < ns; ++q) dM = fma(e[q], s.dC[q], dM);
+      }
       if (kind == 1) dq = t[0] * dq + dM * (k * Pf - kr * Pb);
       else dq = dq + t[1] * dM * (Pf - t[3] * Pb);
     }
@@ -505,11 +703,102 @@ __device__ __noinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, cons
     dSh = fma(s.hRT[k], dom, fma((s.cp[k] - s.hRT[k]) * invT * vT, om, dSh));
     dcb = fma(fma(uu[k] * s.dcp[k], vT, v[k] * s.cp[k]), m.invW[k], dcb);
   }
-  dSh = g.sum(dSh);
-  dcb = g.sum(dcb);
+  {
+    double t2[2] = {dSh, dcb};
+    sum_many<G, 2>(g, t2);
+    dSh = t2[0];
+    dcb = t2[1];
+  }
   if (g.lane == 0) {
     out[ns] = (-(vT * cs.Sh + T * dSh) + T * cs.Sh * (drr + dcb * cs.invcb)) * (cs.invrho * cs.invcb);
   }
+  g.sync();
+}
+
+// Reduced-precision analytic J v (mixed mode): the same derivative as
+// jvp_eval evaluated in FP32 from the FP32 copies cached by
+// rhs_eval<G, true>(..., cache = true).  v and out stay FP64 vectors.
+template <int G>
+__device__ __noinline__ void jvp_eval_f32(const MechView& m, const SlotPtrs& s, const double* uu,
+                                          const CellScalars& cs, const double* v, double* out) {
+  const Grp<G> g;
+  const int ns = m.ns;
+  const float vT = __double2float_rn(v[ns]);
+  const float T = __double2float_rn(cs.T), invT = __double2float_rn(cs.invT);
+  const float invS = __double2float_rn(cs.invS), rho = __double2float_rn(cs.rho);
+  const float invrho = __double2float_rn(cs.invrho), Sh = __double2float_rn(cs.Sh);
+  const float invcb = __double2float_rn(cs.invcb);
+  float a = 0.f;
+  for (int k = g.lane; k < ns; k += G) a = fmaf(__double2float_rn(v[k]), m.invWf[k], a);
+  a = g.sum(a);
+  const float drr = -fmaf(a, invS, vT * invT);
+  const bool coop_tb = m.ntb > 0 && m.ntb <= MAXM;
+  float mp[MAXM];
+#pragma unroll
+  for (int t = 0; t < MAXM; ++t) mp[t] = 0.f;
+  for (int k = g.lane; k < ns; k += G) {
+    const float dCk = fmaf(s.fC[k], drr, rho * __double2float_rn(v[k]) * m.invWf[k]);
+    s.fdC[k] = dCk;
+    if (coop_tb) {
+#pragma unroll
+      for (int t = 0; t < MAXM; ++t)
+        if (t < m.ntb) mp[t] = fmaf(m.efff[t * ns + k], dCk, mp[t]);
+    }
+  }
+  if (coop_tb) sum_first<G>(g, mp, m.ntb);
+  g.sync();
+  for (int j = g.lane; j < m.nr; j += G) {
+    const uint32_t sl = m.slots[j];
+    const int ra = sl & 255, rb = (sl >> 8) & 255, pa = (sl >> 16) & 255, pb = sl >> 24;
+    const int meta = m.meta[j];
+    const int kind = meta & 3;
+    const int dnu = ((meta >> 4) & 15) - 4;
+    const float Pf = s.fC[ra] * s.fC[rb];
+    const float Pb = s.fC[pa] * s.fC[pb];
+    const float dPf = fmaf(s.fdC[ra], s.fC[rb], s.fC[ra] * s.fdC[rb]);
+    const float dPb = fmaf(s.fdC[pa], s.fC[pb], s.fC[pa] * s.fdC[pb]);
+    const float k = s.fkc[j], kr = s.fkr[j];
+    float dlnk = (m.bf[j] + m.EaRf[j] * invT) * invT;
+    const float dnud = dnu > 0 ? 1.f : (dnu < 0 ? -1.f : 0.f);
+    const float dlnKc = (s.fh[pa] + s.fh[pb] - s.fh[ra] - s.fh[rb] - dnud) * invT;
+    if (kind == 2) dlnk = s.ftb[4 * (meta >> 8) + 2];
+    float dq = k * fmaf(dlnk * vT, Pf, dPf) - kr * fmaf((dlnk - dlnKc) * vT, Pb, dPb);
+    if (kind != 0) {
+      const int slot = meta >> 8;
+      const float* t = s.ftb + 4 * slot;
+      float dM = 0.f;
+      if (coop_tb) {
+#pragma unroll
+        for (int q = 0; q < MAXM; ++q)
+          if (q == slot) dM = mp[q];
+      } else {
+        const float* e = m.efff + (size_t)slot * ns;
+        for (int q = 0; q < ns; ++q) dM = fmaf(e[q], s.fdC[q], dM);
+      }
+      if (kind == 1) dq = t[0] * dq + dM * (k * Pf - kr * Pb);
+      else dq = dq + t[1] * dM * (Pf - t[3] * Pb);
+    }
+    s.fq[j] = dq;
+  }
+  g.sync();
+  float dSh = 0.f, dcb = 0.f;
+  for (int k = g.lane; k < ns; k += G) {
+    float dom = 0.f;
+    const int e0 = m.csr_ptr[k], e1 = m.csr_ptr[k + 1];
+    for (int e = e0; e < e1; ++e) dom = fmaf(m.csr_nuf[e], s.fq[m.csr_j[e]], dom);
+    const float om = s.fom[k];
+    const float vk = __double2float_rn(v[k]);
+    out[k] = (double)(m.Wf[k] * (dom - om * drr) * invrho);
+    dSh = fmaf(s.fh[k], dom, fmaf((s.fcp[k] - s.fh[k]) * invT * vT, om, dSh));
+    dcb = fmaf(fmaf(__double2float_rn(uu[k]) * s.fdcp[k], vT, vk * s.fcp[k]), m.invWf[k], dcb);
+  }
+  {
+    float t2[2] = {dSh, dcb};
+    sum_many<G, 2>(g, t2);
+    dSh = t2[0];
+    dcb = t2[1];
+  }
+  if (g.lane == 0) out[ns] = (double)((-(vT * Sh + T * dSh) + T * Sh * (drr + dcb * invcb)) * (invrho * invcb));
   g.sync();
 }
 
@@ -522,13 +811,14 @@ __device__ inline double group_dot(const Grp<G>& g, const double* a, const doubl
 }
 
 // J v into out: analytic, or forward difference with the oracle's increment.
-template <int G>
+template <int G, bool MIXED = false>
 __device__ inline void apply_jv(const MechView& m, const SlotPtrs& s, const CellScalars& cs, int jv_mode,
                                 double p, double unorm, const double* v, double* out, int* n_rhs) {
   const Grp<G> g;
   const int N = m.ns + 1;
   if (jv_mode == 0) {
-    jvp_eval<G>(m, s, s.u, cs, v, out);
+    if (MIXED) jvp_eval_f32<G>(m, s, s.u, cs, v, out);
+    else jvp_eval<G>(m, s, s.u, cs, v, out);
     return;
   }
   const double nv = sqrt(group_dot<G>(g, v, v, N));
@@ -541,15 +831,25 @@ __device__ inline void apply_jv(const MechView& m, const SlotPtrs& s, const Cell
   for (int e = g.lane; e < N; e += G) s.arg[e] = s.u[e] + d * v[e];
   g.sync();
   CellScalars dummy;
-  rhs_eval<G>(m, s, s.arg, s.src, p, out, false, &dummy);
+  rhs_eval<G, MIXED>(m, s, s.arg, s.src, p, out, false, &dummy);
   *n_rhs += 1;
   for (int e = g.lane; e < N; e += G) out[e] = (out[e] - s.fn[e]) / d;
   g.sync();
 }
 
+template <int G>
+__device__ inline float group_dot_f(const Grp<G>& g, const double* a, const double* b, int N) {
+  float acc = 0.f;
+  for (int e = g.lane; e < N; e += G) acc = fmaf(__double2float_rn(a[e]), __double2float_rn(b[e]), acc);
+  return g.sum(acc);
+}
+
 // Arnoldi with classical Gram-Schmidt and one reorthogonalisation pass on
 // K_M(J_n, f_n) (Sec. 4.1).  Returns the dimension m <= M; Q and H in the slot.
-template <int G>
+// MIXED: the inner products and norms run in FP32 (the vector updates stay
+// FP64); the breakdown test then uses 1e-5 instead of 1e-12, the level below
+// which an FP32 residual norm is rounding noise.
+template <int G, bool MIXED = false>
 __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& cs, int M, int jv_mode,
                        double p, int* n_rhs) {
   const Grp<G> g;
@@ -557,7 +857,7 @@ __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& 
   const int Nq = s.Nq;
   if (M > N) M = N;
   for (int i = g.lane; i < MAXM * MAXM; i += G) s.H[i] = 0.0;
-  const double beta = sqrt(group_dot<G>(g, s.fn, s.fn, N));
+  const double beta = MIXED ? (double)sqrtf(group_dot_f<G>(g, s.fn, s.fn, N)) : sqrt(group_dot<G>(g, s.fn, s.fn, N));
   if (M <= 0 || !(beta > 0.0) || !isfinite(beta)) {
     g.sync();
     return 0;
@@ -565,52 +865,74 @@ __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& 
   double unorm = 0.0;
   if (jv_mode != 0) unorm = sqrt(group_dot<G>(g, s.u, s.u, N));
   const double ibeta = 1.0 / beta;
-  for (int e = g.lane; e < N; e += G) s.Q[e] = s.fn[e] * ibeta;
+  for (int e = g.lane; e < N; e += G) {
+    const double qe = s.fn[e] * ibeta;
+    s.Q[e] = qe;
+    if (MIXED) s.fQ[e] = __double2float_rn(qe);
+  }
   g.sync();
+  constexpr double brk = MIXED ? 1e-5 : BREAKDOWN_TOL;
   int mdim = M;
   for (int j = 0; j < M; ++j) {
-    apply_jv<G>(m, s, cs, jv_mode, p, unorm, s.Q + j * Nq, s.w, n_rhs);
-    const double w0 = sqrt(group_dot<G>(g, s.w, s.w, N));
+    apply_jv<G, MIXED>(m, s, cs, jv_mode, p, unorm, s.Q + j * Nq, s.w, n_rhs);
+    const double w0 = MIXED ? (double)sqrtf(group_dot_f<G>(g, s.w, s.w, N)) : sqrt(group_dot<G>(g, s.w, s.w, N));
     double hcol[MAXM];
 #pragma unroll
     for (int i = 0; i < MAXM; ++i) hcol[i] = 0.0;
     for (int pass = 0; pass < 2; ++pass) {
-      double part[MAXM];
+      double hp[MAXM];
+      if (MIXED) {
+        float part[MAXM];
 #pragma unroll
-      for (int i = 0; i < MAXM; ++i) part[i] = 0.0;
-      for (int e = g.lane; e < N; e += G) {
-        const double we = s.w[e];
+        for (int i = 0; i < MAXM; ++i) part[i] = 0.f;
+        for (int e = g.lane; e < N; e += G) {
+          const float we = __double2float_rn(s.w[e]);
 #pragma unroll
-        for (int i = 0; i < MAXM; ++i)
-          if (i <= j) part[i] = fma(s.Q[i * Nq + e], we, part[i]);
+          for (int i = 0; i < MAXM; ++i)
+            if (i <= j) part[i] = fmaf(s.fQ[i * Nq + e], we, part[i]);
+        }
+        sum_first<G>(g, part, j + 1);
+#pragma unroll
+        for (int i = 0; i < MAXM; ++i) hp[i] = (double)part[i];
+      } else {
+#pragma unroll
+        for (int i = 0; i < MAXM; ++i) hp[i] = 0.0;
+        for (int e = g.lane; e < N; e += G) {
+          const double we = s.w[e];
+#pragma unroll
+          for (int i = 0; i < MAXM; ++i)
+            if (i <= j) hp[i] = fma(s.Q[i * Nq + e], we, hp[i]);
+        }
+        sum_first<G>(g, hp, j + 1);
       }
-#pragma unroll
-      for (int i = 0; i < MAXM; ++i)
-        if (i <= j) part[i] = g.sum(part[i]);
       for (int e = g.lane; e < N; e += G) {
         double we = s.w[e];
 #pragma unroll
         for (int i = 0; i < MAXM; ++i)
-          if (i <= j) we = fma(-part[i], s.Q[i * Nq + e], we);
+          if (i <= j) we = fma(-hp[i], s.Q[i * Nq + e], we);
         s.w[e] = we;
       }
 #pragma unroll
-      for (int i = 0; i < MAXM; ++i) hcol[i] += part[i];
+      for (int i = 0; i < MAXM; ++i) hcol[i] += hp[i];
     }
-    const double hn = sqrt(group_dot<G>(g, s.w, s.w, N));
+    const double hn = MIXED ? (double)sqrtf(group_dot_f<G>(g, s.w, s.w, N)) : sqrt(group_dot<G>(g, s.w, s.w, N));
     if (g.lane == 0) {
 #pragma unroll
       for (int i = 0; i < MAXM; ++i)
         if (i <= j) s.H[i * MAXM + j] = hcol[i];
     }
     if (j + 1 == M) break;
-    if (hn <= BREAKDOWN_TOL * w0 || hn == 0.0) {
+    if (hn <= brk * w0 || hn == 0.0) {
       mdim = j + 1;
       break;
     }
     if (g.lane == 0) s.H[(j + 1) * MAXM + j] = hn;
     const double ihn = 1.0 / hn;
-    for (int e = g.lane; e < N; e += G) s.Q[(j + 1) * Nq + e] = s.w[e] * ihn;
+    for (int e = g.lane; e < N; e += G) {
+      const double qe = s.w[e] * ihn;
+      s.Q[(j + 1) * Nq + e] = qe;
+      if (MIXED) s.fQ[(j + 1) * Nq + e] = __double2float_rn(qe);
+    }
     g.sync();
   }
   g.sync();
@@ -681,14 +1003,14 @@ struct IntegrateParams {
   double* h_cell;
   int64_t ncell;
   double p, dt, rtol, atol, h0, fixed_h;
-  int M, jv_mode, max_attempts, trace_cap;
+  int M, jv_mode, max_attempts, trace_cap, precision;
   double* trace;
   int32_t* stats;
   unsigned long long* counter;
   unsigned long long qstride;  // queue position q takes cell (q * qstride) mod ncell
 };
 
-template <int G>
+template <int G, bool MIXED>
 __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const IntegrateParams& P, int64_t cell) {
   const Grp<G> g;
   const int ns = m.ns, N = ns + 1, Nq = s.Nq;
@@ -710,9 +1032,9 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
   double t = 0.0, ln_err_prev = 0.0, h_last = h;  // err_n = 1 before the first step
   int n_acc = 0, n_rej = 0, n_rhs = 0, status = RK_CELL_OK, n_att = 0;
   CellScalars cs;
-  rhs_eval<G>(m, s, s.u, srcp, P.p, s.fn, true, &cs);
+  rhs_eval<G, MIXED>(m, s, s.u, srcp, P.p, s.fn, true, &cs);
   n_rhs += 1;
-  int mdim = arnoldi<G>(m, s, cs, P.M, P.jv_mode, P.p, &n_rhs);
+  int mdim = arnoldi<G, MIXED>(m, s, cs, P.M, P.jv_mode, P.p, &n_rhs);
   double* K0 = s.K;
   double* K1 = s.K + Nq;
   double* K2 = s.K + 2 * Nq;
@@ -742,7 +1064,7 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
           s.arg[e] = s.u[e] + h * acc;
         }
         g.sync();
-        rhs_eval<G>(m, s, s.arg, srcp, P.p, s.fr, false, &cs);
+        rhs_eval<G, MIXED>(m, s, s.arg, srcp, P.p, s.fr, false, &cs);
         n_rhs += 1;
         fi = s.fr;
       } else {
@@ -764,10 +1086,11 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
         for (int l = 0; l < MAXM; ++l)
           if (l < mdim) part[l] = fma(s.Q[l * Nq + e], Fe, part[l]);
       }
+      if (mdim > 0) sum_first<G>(g, part, mdim);
       double z[MAXM], y[MAXM];
 #pragma unroll
       for (int l = 0; l < MAXM; ++l) {
-        z[l] = (l < mdim) ? g.sum(part[l]) : 0.0;
+        z[l] = (l < mdim) ? part[l] : 0.0;
         y[l] = z[l];
       }
       solve_small(s, mdim, y);
@@ -830,9 +1153,9 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
       h = hnew;
       const bool done = fixed ? (n_acc >= n_fixed) : (dt - t <= T_END_TOL * dt);
       if (!done) {
-        rhs_eval<G>(m, s, s.u, srcp, P.p, s.fn, true, &cs);
+        rhs_eval<G, MIXED>(m, s, s.u, srcp, P.p, s.fn, true, &cs);
         n_rhs += 1;
-        mdim = arnoldi<G>(m, s, cs, P.M, P.jv_mode, P.p, &n_rhs);
+        mdim = arnoldi<G, MIXED>(m, s, cs, P.M, P.jv_mode, P.p, &n_rhs);
       }
     } else {
       n_rej += 1;
@@ -864,6 +1187,7 @@ __device__ inline void load_mech(unsigned char* dst, const unsigned char* src, i
   for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) d4[i] = s4[i];
 }
 
+template <bool MIXED = false>
 __device__ inline void init_sentinels(const SlotPtrs& s, int ns, int lane) {
   if (lane == 0) {
     s.C[ns] = 1.0;
@@ -872,10 +1196,15 @@ __device__ inline void init_sentinels(const SlotPtrs& s, int ns, int lane) {
     s.gRT[ns] = 0.0;
     s.E[ns] = 1.0;
     s.Einv[ns] = 1.0;
+    if (MIXED) {
+      s.fC[ns] = 1.f;
+      s.fdC[ns] = 0.f;
+      s.fh[ns] = 0.f;
+    }
   }
 }
 
-template <int G>
+template <int G, bool MIXED>
 __global__ void __launch_bounds__(512) rok4e_integrate_kernel(IntegrateParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   load_exp_table(reinterpret_cast<double*>(smem));
@@ -887,7 +1216,7 @@ __global__ void __launch_bounds__(512) rok4e_integrate_kernel(IntegrateParams P)
   const int gid = threadIdx.x / G;
   double* base = reinterpret_cast<double*>(smem + EXP_TAB_BYTES + P.L.bytes) + (size_t)gid * P.S.stride;
   const SlotPtrs s = slot_ptrs(base, P.S);
-  init_sentinels(s, m.ns, g.lane);
+  init_sentinels<MIXED>(s, m.ns, g.lane);
   g.sync();
   while (true) {
     unsigned long long q = 0;
@@ -897,7 +1226,7 @@ __global__ void __launch_bounds__(512) rok4e_integrate_kernel(IntegrateParams P)
     // Interleave the queue over the cell index: neighbouring cells (e.g. the
     // hot side of a flame) spread over all SMs instead of filling a few.
     const unsigned long long cell = (q * P.qstride) % (unsigned long long)P.ncell;
-    integrate_cell<G>(m, s, P, (int64_t)cell);
+    integrate_cell<G, MIXED>(m, s, P, (int64_t)cell);
   }
 }
 
@@ -912,7 +1241,7 @@ struct PointParams {
   double* out;
   int64_t ncell;
   double p;
-  int mode;  // 0 rhs, 1 analytic jvp, 2 finite-difference jvp
+  int mode;  // 0 rhs, 1 analytic jvp, 2 finite-difference jvp, 3 mixed rhs, 4 FP32 analytic jvp
 };
 
 template <int G>
@@ -930,7 +1259,8 @@ __global__ void __launch_bounds__(512) chem_point_kernel(PointParams P) {
   if (cell >= P.ncell) return;
   double* base = reinterpret_cast<double*>(smem + EXP_TAB_BYTES + P.L.bytes) + (size_t)gid * P.S.stride;
   const SlotPtrs s = slot_ptrs(base, P.S);
-  init_sentinels(s, m.ns, g.lane);
+  if (P.mode >= 3) init_sentinels<true>(s, m.ns, g.lane);
+  else init_sentinels<false>(s, m.ns, g.lane);
   const int N = m.ns + 1;
   for (int e = g.lane; e < N; e += G) {
     s.u[e] = P.Y[cell * N + e];
@@ -939,9 +1269,16 @@ __global__ void __launch_bounds__(512) chem_point_kernel(PointParams P) {
   }
   g.sync();
   CellScalars cs;
-  if (P.mode == 0) {
-    rhs_eval<G>(m, s, s.u, P.src ? s.src : nullptr, P.p, s.fr, false, &cs);
+  if (P.mode == 0 || P.mode == 3) {
+    if (P.mode == 3) rhs_eval<G, true>(m, s, s.u, P.src ? s.src : nullptr, P.p, s.fr, false, &cs);
+    else rhs_eval<G>(m, s, s.u, P.src ? s.src : nullptr, P.p, s.fr, false, &cs);
     for (int e = g.lane; e < N; e += G) P.out[cell * N + e] = s.fr[e];
+    return;
+  }
+  if (P.mode == 4) {
+    rhs_eval<G, true>(m, s, s.u, nullptr, P.p, s.fn, true, &cs);
+    jvp_eval_f32<G>(m, s, s.u, cs, s.F, s.w);
+    for (int e = g.lane; e < N; e += G) P.out[cell * N + e] = s.w[e];
     return;
   }
   rhs_eval<G>(m, s, s.u, nullptr, P.p, s.fn, true, &cs);
@@ -1026,6 +1363,15 @@ __global__ void probe_fp32_kernel(float* out, int iters, float a) {
 #pragma unroll
   for (int j = 0; j < 8; ++j) r += x[j];
   if (r == 12345.678f) out[0] = r;
+}
+__global__ void probe_cvt_kernel(double* out, int iters) {
+  double x0 = 1.0 + threadIdx.x * 1e-9, x1 = x0 + 0.25, x2 = x0 + 0.5, x3 = x0 + 0.75;
+  for (int i = 0; i < iters; ++i) {  // two conversions and one FP32 multiply per step
+    x0 = (double)((float)x0 * 0.9999999f); x1 = (double)((float)x1 * 0.9999999f);
+    x2 = (double)((float)x2 * 0.9999999f); x3 = (double)((float)x3 * 0.9999999f);
+  }
+  const double r = x0 + x1 + x2 + x3;
+  if (r == 12345.678) out[0] = r;
 }
 __global__ void probe_exp_kernel(double* out, int iters) {
   double x0 = -threadIdx.x * 1e-6, x1 = x0 - 0.25, x2 = x0 - 0.5, x3 = x0 - 0.75;
@@ -1152,6 +1498,8 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   if (o.trace_cap < 0 || (o.trace_cap > 0 && !o.trace))
     return set_error(RK_E_INVALID_ARGUMENT, "trace_cap > 0 needs a trace array");
   if (o.fixed_h < 0.0 || !isfinite(o.fixed_h)) return set_error(RK_E_INVALID_ARGUMENT, "fixed_h must be >= 0");
+  if (o.precision != 0 && o.precision != 1) return set_error(RK_E_INVALID_ARGUMENT, "precision must be 0 or 1");
+  const bool mixed = o.precision == 1;
   const int G = o.lanes_per_cell == 0 ? 32 : o.lanes_per_cell;
   if (G != 8 && G != 16 && G != 32) return set_error(RK_E_INVALID_ARGUMENT, "lanes_per_cell must be 0, 8, 16 or 32");
   if (!workspace || workspace_bytes < sizeof(unsigned long long))
@@ -1161,7 +1509,8 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   IntegrateParams P;
   P.mech = mech->dev;
   P.L = mech->host.L;
-  P.S = make_slot(mech->host.L, Meff);
+  P.S = make_slot(mech->host.L, Meff, mixed);
+  P.precision = o.precision;
   P.Y = Y;
   P.src = src;
   P.h_cell = h_cell;
@@ -1187,19 +1536,23 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
     e = cudaEventRecord((cudaEvent_t)o.ev_begin, stream);
     if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
   }
+#define RK_LAUNCH(GG, MX)                                                                          \
+  do {                                                                                             \
+    rc = plan_for<GG>(rok4e_integrate_kernel<GG, MX>, mech, P.S, o.cells_per_block, ncell, true, &plan); \
+    if (rc) return rc;                                                                             \
+    rok4e_integrate_kernel<GG, MX><<<plan.blocks, plan.cells_per_block * GG, plan.smem, stream>>>(P); \
+  } while (0)
   if (G == 32) {
-    rc = plan_for<32>(rok4e_integrate_kernel<32>, mech, P.S, o.cells_per_block, ncell, true, &plan);
-    if (rc) return rc;
-    rok4e_integrate_kernel<32><<<plan.blocks, plan.cells_per_block * 32, plan.smem, stream>>>(P);
+    if (mixed) RK_LAUNCH(32, true);
+    else RK_LAUNCH(32, false);
   } else if (G == 16) {
-    rc = plan_for<16>(rok4e_integrate_kernel<16>, mech, P.S, o.cells_per_block, ncell, true, &plan);
-    if (rc) return rc;
-    rok4e_integrate_kernel<16><<<plan.blocks, plan.cells_per_block * 16, plan.smem, stream>>>(P);
+    if (mixed) RK_LAUNCH(16, true);
+    else RK_LAUNCH(16, false);
   } else {
-    rc = plan_for<8>(rok4e_integrate_kernel<8>, mech, P.S, o.cells_per_block, ncell, true, &plan);
-    if (rc) return rc;
-    rok4e_integrate_kernel<8><<<plan.blocks, plan.cells_per_block * 8, plan.smem, stream>>>(P);
+    if (mixed) RK_LAUNCH(8, true);
+    else RK_LAUNCH(8, false);
   }
+#undef RK_LAUNCH
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "rok4e_integrate_kernel launch");
   if (o.ev_end) {
@@ -1275,7 +1628,7 @@ static int point_call(const rk_mech* mech, const double* Y, const double* src, c
   PointParams P;
   P.mech = mech->dev;
   P.L = mech->host.L;
-  P.S = make_slot(mech->host.L, 1);
+  P.S = make_slot(mech->host.L, 1, mode >= 3);
   P.Y = Y;
   P.src = src;
   P.V = V;
@@ -1298,8 +1651,13 @@ int rk_chem_rhs(const rk_mech* mech, const double* Y, const double* src, double 
 
 int rk_chem_jvp(const rk_mech* mech, const double* Y, const double* V, double p, double* JV, int64_t ncell,
                 int32_t mode, void* stream) {
-  if (mode != 0 && mode != 1) return set_error(RK_E_INVALID_ARGUMENT, "mode must be 0 or 1");
-  return point_call(mech, Y, nullptr, V, p, JV, ncell, mode == 0 ? 1 : 2, stream);
+  if (mode < 0 || mode > 2) return set_error(RK_E_INVALID_ARGUMENT, "mode must be 0, 1 or 2");
+  return point_call(mech, Y, nullptr, V, p, JV, ncell, mode == 0 ? 1 : (mode == 1 ? 2 : 4), stream);
+}
+
+int rk_chem_rhs_mixed(const rk_mech* mech, const double* Y, const double* src, double p, double* dYdt,
+                      int64_t ncell, void* stream) {
+  return point_call(mech, Y, src, nullptr, p, dYdt, ncell, 3, stream);
 }
 
 size_t rk_rok4e_workspace_size(const rk_mech* mech, int64_t ncell, int32_t krylov_dim, const rk_opts* opts) {
@@ -1378,7 +1736,7 @@ int rk_simpler_split_step(const rk_mech* mech, double* U, double* h_cell, int64_
 }
 
 int rk_probe_throughput(int32_t kind, double* ops_per_s) {
-  if (!ops_per_s || kind < 0 || kind > 2) return set_error(RK_E_INVALID_ARGUMENT, "bad probe arguments");
+  if (!ops_per_s || kind < 0 || kind > 3) return set_error(RK_E_INVALID_ARGUMENT, "bad probe arguments");
   int n_sm = 0;
   size_t smem = 0;
   int rc = device_props(&n_sm, &smem);
@@ -1390,7 +1748,7 @@ int rk_probe_throughput(int32_t kind, double* ops_per_s) {
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   const int threads = 512, blocks = n_sm * 4;
-  const int iters = kind == 2 ? 2000 : (kind == 0 ? 20000 : 200000);
+  const int iters = kind == 2 ? 2000 : (kind == 0 ? 20000 : (kind == 3 ? 20000 : 200000));
   double ops = 0.0;
   float ms = 0.f;
   for (int rep = 0; rep < 2; ++rep) {  // first launch warms up
@@ -1401,9 +1759,12 @@ int rk_probe_throughput(int32_t kind, double* ops_per_s) {
     } else if (kind == 1) {
       probe_fp32_kernel<<<blocks, threads>>>((float*)buf, iters, 0.999999f);
       ops = (double)blocks * threads * iters * 8.0;
-    } else {
+    } else if (kind == 2) {
       probe_exp_kernel<<<blocks, threads>>>((double*)buf, iters);
       ops = (double)blocks * threads * iters * 4.0;
+    } else {
+      probe_cvt_kernel<<<blocks, threads>>>((double*)buf, iters);
+      ops = (double)blocks * threads * iters * 8.0;  // conversions
     }
     cudaEventRecord(b);
     cudaEventSynchronize(b);

@@ -1,0 +1,129 @@
+"""GPU checks of the mixed-precision path (the ``mixed`` workload).
+
+Mixed precision keeps FP64 for the Gibbs factors and 1/Kc, the rates of
+progress, the heat release, the stage solves, the error norm and the state
+update, and runs the forward-rate exponentials, w = nu^T q, the
+Jacobian-vector products and the Arnoldi inner products in FP32.  Its error
+against the FP64 oracle is measured on the oracle's replay of the mixed run's
+own step sequence, and against the FP64 GPU path on the same workload.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+P = 101325.0
+
+
+@pytest.fixture(scope="module")
+def rk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1712_00953_gb300 as rk
+
+    return rk
+
+
+def _mech(name):
+    from synth.fields import WORKLOADS, mechanism_for
+
+    return WORKLOADS[name], mechanism_for(WORKLOADS[name])
+
+
+@pytest.mark.parametrize("name", ["small", "mixed"])
+def test_mixed_rhs_close_to_oracle(rk, name):
+    from oracle.kinetics import Kinetics
+    from synth.fields import field_uniform
+
+    w, mech = _mech(name)
+    kin = Kinetics(mech)
+    U = field_uniform(64, mech.n_species, 13, 500.0, 2500.0)
+    m = rk.mech_load(mech)
+    out = rk.chem_rhs_mixed(m, torch.tensor(U, device="cuda"), P).cpu().numpy()
+    ref = np.array([kin.rhs(u, P) for u in U])
+    ns = mech.n_species
+    scale = np.max(np.abs(ref[:, :ns]), axis=1, keepdims=True)
+    assert np.max(np.abs(out[:, :ns] - ref[:, :ns]) / scale) < 2e-6
+    # the temperature equation is assembled from an FP64 heat release
+    assert np.max(np.abs(out[:, ns] - ref[:, ns]) / np.abs(ref[:, ns])) < 2e-6
+
+
+@pytest.mark.parametrize("name", ["small", "mixed"])
+def test_fp32_jvp_close_to_oracle(rk, name):
+    from oracle.kinetics import Kinetics
+    from synth.fields import field_uniform
+
+    w, mech = _mech(name)
+    kin = Kinetics(mech)
+    U = field_uniform(48, mech.n_species, 17, 600.0, 2500.0)
+    V = np.random.default_rng(2).normal(size=U.shape)
+    V /= np.linalg.norm(V, axis=1, keepdims=True)
+    m = rk.mech_load(mech)
+    out = rk.chem_jvp(m, torch.tensor(U, device="cuda"), torch.tensor(V, device="cuda"), P, mode=2).cpu().numpy()
+    ref = np.array([kin.jvp(u, P, v) for u, v in zip(U, V)])
+    scale = np.max(np.abs(ref), axis=1, keepdims=True)
+    assert np.max(np.abs(out - ref) / scale) < 1e-4
+
+
+def _run(rk, mech, U, w, precision, cap=8192, M=4):
+    m = rk.mech_load(mech)
+    Y = torch.tensor(U, device="cuda")
+    n = U.shape[0]
+    st = torch.zeros(n, 4, dtype=torch.int32, device="cuda")
+    tr = torch.zeros(n, cap, dtype=torch.float64, device="cuda")
+    rk.rok4e_integrate(m, Y, w.dt, w.rtol, w.atol, M, stats=st, opts=rk.Opts(precision=precision, trace=tr))
+    torch.cuda.synchronize()
+    return Y.cpu().numpy(), st.cpu().numpy(), tr.cpu().numpy()
+
+
+def test_mixed_integration_error_vs_fp64_oracle(rk):
+    """Mixed-precision ROK4E on the small workload, replayed through the FP64
+    oracle: the error stays within the library's bar (|dY| <= 1e-8 + 1e-6|Y|,
+    |dT| <= 1e-6 K)."""
+    from oracle import rok4e as orok
+    from oracle.kinetics import Kinetics
+    from synth.fields import initial_state
+
+    w, mech = _mech("small")
+    U = initial_state(w)[::8]
+    out, st, tr = _run(rk, mech, U, w, 1)
+    assert np.all(st[:, 3] == 0)
+    ref, _ = orok.integrate_cells(Kinetics(mech), U, P, w.dt, w.rtol, w.atol, 4,
+                                  replay=[[(abs(h), h > 0) for h in r if h != 0.0] for r in tr])
+    ns = mech.n_species
+    dY = np.abs(out[:, :ns] - ref[:, :ns])
+    dT = np.abs(out[:, ns] - ref[:, ns])
+    excess = dY - (1e-8 + 1e-6 * np.abs(ref[:, :ns]))
+    print(f"mixed vs FP64 oracle (replay): max |dY| {dY.max():.3e}, max |dT| {dT.max():.3e} K")
+    assert excess.max() <= 0.0, excess.max()
+    assert dT.max() <= 1e-6, dT.max()
+
+
+def test_mixed_split_steps_vs_fp64_gpu(rk):
+    """Mixed and FP64 Simpler split steps on the 1-D workload's field: the
+    per-species difference after 5 steps stays at the level of the adaptive
+    integrator's own tolerance."""
+    from synth.fields import field_tanh_front
+
+    w, mech = _mech("mixed")
+    m = rk.mech_load(mech)
+    _, U0 = field_tanh_front(512, mech.n_species, w.field_seed)
+    dx = 1e-2 / 512
+    res = {}
+    for prec in (0, 1):
+        U = torch.tensor(U0, device="cuda")
+        hc = torch.zeros(512, dtype=torch.float64, device="cuda")
+        for _ in range(5):
+            rk.simpler_split_step(m, U, w.dt, 1e-4, dx, w.rtol, w.atol, 4, h_cell=hc,
+                                  opts=rk.Opts(precision=prec))
+        torch.cuda.synchronize()
+        res[prec] = U.cpu().numpy()
+    ns = mech.n_species
+    dY = np.abs(res[1][:, :ns] - res[0][:, :ns])
+    dT = np.abs(res[1][:, ns] - res[0][:, ns])
+    print(f"mixed vs FP64 GPU after 5 split steps: max |dY| {dY.max():.3e} (per species "
+          f"{np.array2string(dY.max(axis=0), precision=1)}), max |dT| {dT.max():.3e} K")
+    assert np.all(np.isfinite(res[1]))
+    assert dY.max() < 1e-5 and dT.max() < 1e-2

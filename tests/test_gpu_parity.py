@@ -332,12 +332,67 @@ def test_table_exp_matches_cuda_exp(rk):
                         [0.0, -0.0, 1e-300, -1e-300, 708.0, -708.0, 709.78, -745.2, np.inf, -np.inf, np.nan]])
     xt = torch.tensor(x, device="cuda")
     ref = torch.exp(xt).cpu().numpy()
+    tiny = np.finfo(float).tiny
     for which, sign in ((0, 1.0), (1, 1.0), (2, -1.0)):
         y = rk.eval_exp(xt, which).cpu().numpy()
         r = ref if sign > 0 else torch.exp(-xt).cpu().numpy()
-        fin = np.isfinite(r) & (r > 1e-300) & (r < 1e300)
-        assert np.max(_ulps(y[fin], r[fin])) <= 2
-        nf = ~fin
-        np.testing.assert_array_equal(np.isnan(y[nf]), np.isnan(r[nf]))
-        ok = ~np.isnan(r[nf])
-        assert np.all(np.abs(y[nf][ok] - r[nf][ok]) <= 1e-300 + 4e-16 * np.abs(r[nf][ok]))
+        normal = np.isfinite(r) & (r >= tiny)
+        assert np.max(_ulps(y[normal], r[normal])) <= 2
+        # NaN, infinities, zero and subnormal results come from the library path
+        other = ~normal
+        assert np.array_equal(np.isnan(y[other]), np.isnan(r[other]))
+        keep = other & ~np.isnan(r)
+        assert np.array_equal(y[keep], r[keep])
+
+
+def test_cuda_graph_capture_matches_eager(rk):
+    """The split step captured once in a CUDA graph and replayed gives the same
+    bits as the eager calls."""
+    from synth.fields import field_tanh_front
+
+    w, mech = _mech("flame1d")
+    m = rk.mech_load(mech)
+    _, U0 = field_tanh_front(256, mech.n_species, w.field_seed)
+    dx = 1e-2 / 256
+    ws = torch.empty(rk.simpler_split_step_workspace_size(m, 256, 4), dtype=torch.uint8, device="cuda")
+    Ue = torch.tensor(U0, device="cuda")
+    he = torch.zeros(256, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        rk.simpler_split_step(m, Ue, w.dt, 1e-4, dx, w.rtol, w.atol, 4, h_cell=he, workspace=ws)
+    Ug = torch.tensor(U0, device="cuda")
+    hg = torch.zeros(256, dtype=torch.float64, device="cuda")
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s, capture_error_mode="relaxed"):
+            rk.simpler_split_step(m, Ug, w.dt, 1e-4, dx, w.rtol, w.atol, 4, h_cell=hg, workspace=ws, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    Ug.copy_(torch.tensor(U0, device="cuda"))
+    hg.zero_()
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(Ug, Ue)
+    assert torch.equal(hg, he)
+
+
+def test_autotuner_picks_a_valid_shape(rk, tmp_path):
+    from paper_1712_00953_gb300 import autotune
+    from synth.fields import initial_state
+
+    w, mech = _mech("small")
+    m = rk.mech_load(mech)
+    Y = torch.tensor(initial_state(w), device="cuda")
+    path = str(tmp_path / "tune.json")
+    o = autotune.tune(m, Y, w.dt, w.rtol, w.atol, 4, cache_path=path, reps=1)
+    assert (o.lanes_per_cell, o.cells_per_block) in autotune.CANDIDATES
+    o2 = autotune.tune(m, Y, w.dt, w.rtol, w.atol, 4, cache_path=path, reps=1)  # cached
+    assert (o2.lanes_per_cell, o2.cells_per_block) == (o.lanes_per_cell, o.cells_per_block)
+    Y1 = Y.clone()
+    rk.rok4e_integrate(m, Y1, w.dt, w.rtol, w.atol, 4, opts=o)
+    Y2 = Y.clone()
+    rk.rok4e_integrate(m, Y2, w.dt, w.rtol, w.atol, 4)
+    torch.cuda.synchronize()
+    _assert_state_close(Y1.cpu().numpy(), Y2.cpu().numpy(), mech.n_species, "tuned vs default")
