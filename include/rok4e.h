@@ -152,11 +152,12 @@ typedef struct rk_opts {
   double h0;              /* first step when h_cell is NULL or holds <= 0; <= 0: dt */
   double fixed_h;         /* > 0: fixed steps of this size, no error control */
   int32_t trace_cap;      /* attempts recorded per cell into trace (0: none) */
-  int32_t precision;      /* 0: FP64 throughout (default); 1: mixed -- forward-rate
-                             exponentials, w = nu^T q, Jacobian-vector products and
-                             Arnoldi inner products in FP32; Gibbs factors, 1/Kc,
-                             rates of progress, stage solves, error norm and state
-                             update in FP64 */
+  int32_t precision;      /* 0: FP64 throughout (default).  1: mixed -- forward-rate
+                             exponentials, w = nu^T q and the Arnoldi inner products
+                             in FP32; Gibbs factors, 1/Kc, rates of progress, heat
+                             release, Jacobian-vector products, stage solves, error
+                             norm and state update in FP64.  2: as 1 with the
+                             Jacobian-vector products in FP32 as well */
   double* trace;          /* device [ncell x trace_cap]: +h accepted, -h rejected, 0 unused */
   void* ev_begin;         /* optional cudaEvent_t recorded on the stream right before the */
   void* ev_end;           /* integration kernel and right after it (timing hook), or NULL */

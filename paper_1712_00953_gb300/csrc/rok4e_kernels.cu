@@ -813,11 +813,12 @@ __device__ inline double group_dot(const Grp<G>& g, const double* a, const doubl
 // J v into out: analytic, or forward difference with the oracle's increment.
 template <int G, bool MIXED = false>
 __device__ inline void apply_jv(const MechView& m, const SlotPtrs& s, const CellScalars& cs, int jv_mode,
-                                double p, double unorm, const double* v, double* out, int* n_rhs) {
+                                double p, double unorm, const double* v, double* out, int* n_rhs,
+                                bool fp32_jv = false) {
   const Grp<G> g;
   const int N = m.ns + 1;
   if (jv_mode == 0) {
-    if (MIXED) jvp_eval_f32<G>(m, s, s.u, cs, v, out);
+    if (MIXED && fp32_jv) jvp_eval_f32<G>(m, s, s.u, cs, v, out);
     else jvp_eval<G>(m, s, s.u, cs, v, out);
     return;
   }
@@ -851,7 +852,7 @@ __device__ inline float group_dot_f(const Grp<G>& g, const double* a, const doub
 // which an FP32 residual norm is rounding noise.
 template <int G, bool MIXED = false>
 __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& cs, int M, int jv_mode,
-                       double p, int* n_rhs) {
+                       double p, int* n_rhs, bool fp32_jv = false) {
   const Grp<G> g;
   const int N = m.ns + 1;
   const int Nq = s.Nq;
@@ -874,7 +875,7 @@ __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& 
   constexpr double brk = MIXED ? 1e-5 : BREAKDOWN_TOL;
   int mdim = M;
   for (int j = 0; j < M; ++j) {
-    apply_jv<G, MIXED>(m, s, cs, jv_mode, p, unorm, s.Q + j * Nq, s.w, n_rhs);
+    apply_jv<G, MIXED>(m, s, cs, jv_mode, p, unorm, s.Q + j * Nq, s.w, n_rhs, fp32_jv);
     const double w0 = MIXED ? (double)sqrtf(group_dot_f<G>(g, s.w, s.w, N)) : sqrt(group_dot<G>(g, s.w, s.w, N));
     double hcol[MAXM];
 #pragma unroll
@@ -1021,6 +1022,7 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
   g.sync();
   const double* srcp = P.src ? s.src : nullptr;
   const bool fixed = P.fixed_h > 0.0;
+  const bool fp32_jv = P.precision == 2;
   const double dt = P.dt;
   double h = P.h0 > 0.0 ? P.h0 : dt;
   if (P.h_cell) {
@@ -1034,7 +1036,7 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
   CellScalars cs;
   rhs_eval<G, MIXED>(m, s, s.u, srcp, P.p, s.fn, true, &cs);
   n_rhs += 1;
-  int mdim = arnoldi<G, MIXED>(m, s, cs, P.M, P.jv_mode, P.p, &n_rhs);
+  int mdim = arnoldi<G, MIXED>(m, s, cs, P.M, P.jv_mode, P.p, &n_rhs, fp32_jv);
   double* K0 = s.K;
   double* K1 = s.K + Nq;
   double* K2 = s.K + 2 * Nq;
@@ -1155,7 +1157,7 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
       if (!done) {
         rhs_eval<G, MIXED>(m, s, s.u, srcp, P.p, s.fn, true, &cs);
         n_rhs += 1;
-        mdim = arnoldi<G, MIXED>(m, s, cs, P.M, P.jv_mode, P.p, &n_rhs);
+        mdim = arnoldi<G, MIXED>(m, s, cs, P.M, P.jv_mode, P.p, &n_rhs, fp32_jv);
       }
     } else {
       n_rej += 1;
@@ -1498,8 +1500,8 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   if (o.trace_cap < 0 || (o.trace_cap > 0 && !o.trace))
     return set_error(RK_E_INVALID_ARGUMENT, "trace_cap > 0 needs a trace array");
   if (o.fixed_h < 0.0 || !isfinite(o.fixed_h)) return set_error(RK_E_INVALID_ARGUMENT, "fixed_h must be >= 0");
-  if (o.precision != 0 && o.precision != 1) return set_error(RK_E_INVALID_ARGUMENT, "precision must be 0 or 1");
-  const bool mixed = o.precision == 1;
+  if (o.precision < 0 || o.precision > 2) return set_error(RK_E_INVALID_ARGUMENT, "precision must be 0, 1 or 2");
+  const bool mixed = o.precision >= 1;
   const int G = o.lanes_per_cell == 0 ? 32 : o.lanes_per_cell;
   if (G != 8 && G != 16 && G != 32) return set_error(RK_E_INVALID_ARGUMENT, "lanes_per_cell must be 0, 8, 16 or 32");
   if (!workspace || workspace_bytes < sizeof(unsigned long long))
@@ -1622,7 +1624,8 @@ static int point_call(const rk_mech* mech, const double* Y, const double* src, c
   if (rc) return rc;
   if (ncell < 0) return set_error(RK_E_INVALID_ARGUMENT, "ncell < 0");
   if (ncell == 0) return RK_OK;
-  if (!Y || !out || (mode > 0 && !V)) return set_error(RK_E_INVALID_ARGUMENT, "null array");
+  const bool needs_v = mode == 1 || mode == 2 || mode == 4;
+  if (!Y || !out || (needs_v && !V)) return set_error(RK_E_INVALID_ARGUMENT, "null array");
   if (out == Y) return set_error(RK_E_INVALID_ARGUMENT, "output must not alias the state");
   if (!(p > 0.0)) return set_error(RK_E_INVALID_ARGUMENT, "pressure must be > 0");
   PointParams P;
