@@ -208,6 +208,31 @@ int rk_simpler_split_step(const rk_mech* mech, double* U, double* h_cell, int64_
                           int32_t krylov_dim, const rk_opts* opts, int32_t* stats,
                           void* workspace, size_t workspace_bytes, void* stream);
 
+/* Allocation-free variant of rk_simpler_split_step (the paper has no
+ * counterpart: this is a library convenience).  Some callers cannot allocate
+ * device memory when they take a step -- a solver whose memory pools are
+ * fixed before the time loop starts, a host code with no CUDA allocator of its
+ * own, or a loop that must not allocate for timing reasons -- so this entry
+ * point takes no workspace and calls no cudaMalloc, cudaFree or allocating
+ * library routine.  Its scratch (the transport term T(U_n), two SSP-RK3 stage
+ * buffers and the work-queue counter) lives in one static device array of
+ * RK_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until the
+ * process exits; npts x (n_species + 1) must fit in it (about 174,000 values:
+ * 2048 points of a 30-species mechanism use 63,488), else the call returns
+ * RK_E_UNSUPPORTED with the limit in rk_last_error.
+ *  - The first call on a device looks the array's device address up (once per
+ *    device, with that device current); make that first call before any stream
+ *    capture.
+ *  - Every call on a device shares the one array and finds the previous call's
+ *    contents there (the parts that must start from zero are cleared by the
+ *    call).  Calls that overlap on the GPU -- on different streams, or from
+ *    several host threads -- race on it: order them on one stream.
+ * Arguments and results are those of rk_simpler_split_step. */
+#define RK_NOALLOC_SCRATCH_BYTES (4u << 20)
+int rk_simpler_split_step_noalloc(const rk_mech* mech, double* U, double* h_cell, int64_t npts, double p,
+                                  double dt, double D, double dx, double rtol, double atol,
+                                  int32_t krylov_dim, const rk_opts* opts, int32_t* stats, void* stream);
+
 /* Transport operator alone: TU = D d^2U/dx^2 (same discretisation). */
 int rk_diffusion_1d(const double* U, double* TU, int64_t npts, int32_t nvar, double D, double dx,
                     void* stream);

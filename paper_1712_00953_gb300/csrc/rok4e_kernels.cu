@@ -1738,6 +1738,55 @@ int rk_simpler_split_step(const rk_mech* mech, double* U, double* h_cell, int64_
   return e == cudaSuccess ? RK_OK : cuda_error(e, "ssprk3_stage_kernel launch");
 }
 
+// ---- allocation-free split step ---------------------------------------------
+// Scratch for rk_simpler_split_step_noalloc: a fixed array in device memory that
+// every GPU loading this library reserves until the process exits.  Host code
+// may not pass the symbol itself to a kernel (on the host it names a host-side
+// placeholder), so its device address is looked up once per device with
+// cudaGetSymbolAddress, with that device current, and cached.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RK_NOALLOC_SCRATCH_BYTES];
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[256] = {nullptr};
+
+static int noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 256) return set_error(RK_E_UNSUPPORTED, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress");
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return RK_OK;
+}
+
+int rk_simpler_split_step_noalloc(const rk_mech* mech, double* U, double* h_cell, int64_t npts, double p, double dt,
+                                  double D, double dx, double rtol, double atol, int32_t krylov_dim,
+                                  const rk_opts* opts, int32_t* stats, void* stream) {
+  int rc = check_mech(mech);
+  if (rc) return rc;
+  if (npts < 0) return set_error(RK_E_INVALID_ARGUMENT, "npts < 0");
+  const size_t need = rk_simpler_split_step_workspace_size(mech, npts, krylov_dim, opts);
+  if (need > (size_t)RK_NOALLOC_SCRATCH_BYTES) {
+    char msg[256];
+    snprintf(msg, sizeof(msg),
+             "npts x (n_species + 1) = %lld values needs %zu bytes of scratch; the static scratch holds %zu "
+             "(at most %zu values): use rk_simpler_split_step with a workspace",
+             (long long)(npts * (mech->host.L.ns + 1)), need, (size_t)RK_NOALLOC_SCRATCH_BYTES,
+             (size_t)((RK_NOALLOC_SCRATCH_BYTES - 512 - 256 * 3) / (3 * sizeof(double))));
+    return set_error(RK_E_UNSUPPORTED, msg);
+  }
+  void* scratch = nullptr;
+  rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  return rk_simpler_split_step(mech, U, h_cell, npts, p, dt, D, dx, rtol, atol, krylov_dim, opts, stats, scratch,
+                               (size_t)RK_NOALLOC_SCRATCH_BYTES, stream);
+}
+
 int rk_probe_throughput(int32_t kind, double* ops_per_s) {
   if (!ops_per_s || kind < 0 || kind > 3) return set_error(RK_E_INVALID_ARGUMENT, "bad probe arguments");
   int n_sm = 0;
