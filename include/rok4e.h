@@ -135,10 +135,11 @@ int rk_chem_rhs(const rk_mech* mech, const double* Y, const double* src, double 
 int rk_chem_jvp(const rk_mech* mech, const double* Y, const double* V, double p, double* JV,
                 int64_t ncell, int32_t mode, void* stream);
 
-/* Mixed-precision source term: as rk_chem_rhs, with the forward-rate
- * exponentials and w = nu^T q in FP32 while the Gibbs factors, 1/Kc, the
- * rates of progress q = m (k prod C - k/Kc prod C) and the assembly of f stay
- * FP64 (the right-hand side the mixed-precision integrator uses). */
+/* Mixed-precision source term: as rk_chem_rhs, with w = nu^T q in FP32 while
+ * the rate coefficients, Gibbs factors, 1/Kc, the rates of progress
+ * q = m (k prod C - k/Kc prod C), the heat release sum_j q_j Delta H_j and the
+ * assembly of f stay FP64 (the right-hand side the mixed-precision integrator
+ * uses). */
 int rk_chem_rhs_mixed(const rk_mech* mech, const double* Y, const double* src, double p,
                       double* dYdt, int64_t ncell, void* stream);
 
@@ -152,18 +153,19 @@ typedef struct rk_opts {
   double h0;              /* first step when h_cell is NULL or holds <= 0; <= 0: dt */
   double fixed_h;         /* > 0: fixed steps of this size, no error control */
   int32_t trace_cap;      /* attempts recorded per cell into trace (0: none) */
-  int32_t precision;      /* 0: FP64 throughout (default).  1: mixed -- forward-rate
-                             exponentials, w = nu^T q and the Arnoldi inner products
-                             in FP32; Gibbs factors, 1/Kc, rates of progress, heat
-                             release, Jacobian-vector products, stage solves, error
-                             norm and state update in FP64.  2: as 1 with the
+  int32_t precision;      /* 0: FP64 throughout (default).  1: mixed -- w = nu^T q and
+                             the Arnoldi inner products in FP32; rate coefficients,
+                             Gibbs factors, 1/Kc, rates of progress, heat release,
+                             Jacobian-vector products, stage solves, error norm and
+                             state update in FP64.  2: as 1 with the
                              Jacobian-vector products in FP32 as well */
   double* trace;          /* device [ncell x trace_cap]: +h accepted, -h rejected, 0 unused */
   void* ev_begin;         /* optional cudaEvent_t recorded on the stream right before the */
   void* ev_end;           /* integration kernel and right after it (timing hook), or NULL */
 } rk_opts;
 
-/* Bytes of workspace rk_rok4e_integrate needs (a small work-queue counter). */
+/* Bytes of workspace rk_rok4e_integrate needs: a work-queue counter, a
+ * histogram and the queue order (768 bytes + 4 bytes per cell, rounded). */
 size_t rk_rok4e_workspace_size(const rk_mech* mech, int64_t ncell, int32_t krylov_dim,
                                const rk_opts* opts);
 
@@ -185,7 +187,11 @@ size_t rk_rok4e_workspace_size(const rk_mech* mech, int64_t ncell, int32_t krylo
  *            evaluations, status (RK_CELL_*); or NULL
  *  workspace device memory of rk_rok4e_workspace_size bytes
  * Cells are independent; one persistent launch processes them from a shared
- * work queue. */
+ * work queue.  When h_cell is given (and steps are adaptive) the queue hands
+ * out cells longest-expected-first, the expected substep count being dt/h_cell
+ * binned on a quarter-octave log scale; otherwise it interleaves the cell
+ * index so that neighbouring cells spread over the SMs.  The order changes
+ * only the schedule: each cell's result is the same bits either way. */
 int rk_rok4e_integrate(const rk_mech* mech, double* Y, const double* src, double* h_cell,
                        int64_t ncell, double p, double dt, double rtol, double atol,
                        int32_t krylov_dim, const rk_opts* opts, int32_t* stats, void* workspace,
@@ -232,6 +238,24 @@ int rk_simpler_split_step(const rk_mech* mech, double* U, double* h_cell, int64_
 int rk_simpler_split_step_noalloc(const rk_mech* mech, double* U, double* h_cell, int64_t npts, double p,
                                   double dt, double D, double dx, double rtol, double atol,
                                   int32_t krylov_dim, const rk_opts* opts, int32_t* stats, void* stream);
+
+/* Any of the splittings of Sec. 3 on the same 1-D system (one step, in place):
+ *  scheme 0  Simpler balanced (Eq. simpler_balanced) -- as rk_simpler_split_step
+ *  scheme 1  Strang (Sec. 3.1): T over dt/2, R over dt, T over dt/2
+ *  scheme 2  simple balanced, c_n = (R(U_n) - T(U_n))/2 (Sec. 3.3), reaction
+ *            first as in the paper's PSR tests: R - c over dt/2, T + c over dt,
+ *            R - c over dt/2
+ *  scheme 3  simple balanced, transport first (Eq. balanced): T + c over dt/2,
+ *            R - c over dt, T + c over dt/2
+ * Transport sub-steps are one SSP-RK3 step of their length; reaction sub-steps
+ * are rk_rok4e_integrate with the step's constant source, h_cell carrying over
+ * between them.  Workspace: rk_split_step_workspace_size. */
+size_t rk_split_step_workspace_size(const rk_mech* mech, int64_t npts, int32_t krylov_dim, int32_t scheme,
+                                    const rk_opts* opts);
+int rk_split_step(const rk_mech* mech, double* U, double* h_cell, int64_t npts, double p, double dt,
+                  double D, double dx, double rtol, double atol, int32_t krylov_dim, int32_t scheme,
+                  const rk_opts* opts, int32_t* stats, void* workspace, size_t workspace_bytes,
+                  void* stream);
 
 /* Transport operator alone: TU = D d^2U/dx^2 (same discretisation). */
 int rk_diffusion_1d(const double* U, double* TU, int64_t npts, int32_t nvar, double D, double dx,

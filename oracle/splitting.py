@@ -135,6 +135,55 @@ def ssprk3(U, dt, g):
     return U / 3.0 + 2.0 / 3.0 * (u2 + dt * g(u2))
 
 
+SCHEMES = ("simpler", "strang", "simple_balanced", "simple_balanced_transport_first")
+
+
+def split_step_1d(kin, U, p, dt, D, dx, rtol, atol, M, scheme="simpler", *, h_cell=None, jv_mode="analytic",
+                  max_attempts=100000):
+    """One split step of the 1-D reaction-diffusion system with any of the
+    splittings of Sec. 3.  Transport sub-steps are one SSP-RK3 step of their
+    length; reaction sub-steps are ROK4E per cell with the step's constant
+    source.  ``h_cell`` (per-cell first step, updated in place) carries over
+    between reaction sub-steps.  Returns the new field.
+
+    simpler                          Eq. simpler_balanced (c_n = -T(U_n))
+    strang                           T over h/2, R over h, T over h/2
+    simple_balanced                  c_n = (R - T)/2, reaction first:
+                                     R - c over h/2, T + c over h, R - c over h/2
+    simple_balanced_transport_first  Eq. balanced with c_n = (R - T)/2
+    """
+    U = np.asarray(U, dtype=float)
+    n = U.shape[0]
+    hc = np.zeros(n) if h_cell is None else h_cell
+
+    def flow_T(V, t, c):  # dU/dt = T(U) + c over t
+        return ssprk3(V, t, lambda X: diffusion_op(X, D, dx) + c)
+
+    def flow_R(V, t, src):  # dU/dt = R(U) + src over t, cell by cell
+        out = V.copy()
+        for i in range(n):
+            s = None if np.isscalar(src) and src == 0.0 else src[i]
+            f, jv_at = rok4e.reactor(kin, p, s, jv_mode)
+            out[i], inf = rok4e.integrate(f, jv_at, V[i], t, rtol, atol, M, h0=hc[i], max_attempts=max_attempts)
+            hc[i] = inf["h_last"]
+        return out
+
+    if scheme == "simpler":
+        Tn = diffusion_op(U, D, dx)
+        return flow_T(flow_R(U, dt, Tn), dt / 2, -Tn)
+    if scheme == "strang":
+        return strang_step(U, dt, flow_T, flow_R)
+    Rn = np.array([kin.rhs(u, p) for u in U])
+    c = 0.5 * (Rn - diffusion_op(U, D, dx))
+    if scheme == "simple_balanced":
+        u1 = flow_R(U, dt / 2, -c)
+        u2 = flow_T(u1, dt, c)
+        return flow_R(u2, dt / 2, -c)
+    if scheme == "simple_balanced_transport_first":
+        return balanced_step(U, dt, c, flow_T, flow_R)
+    raise ValueError(scheme)
+
+
 def simpler_split_step_1d(kin, U, p, dt, D, dx, rtol, atol, M, *, h_cell=None,
                           jv_mode="analytic", max_attempts=100000, replay=None, record=False,
                           cells=None):

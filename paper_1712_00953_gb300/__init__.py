@@ -29,7 +29,7 @@ def _L():
 
 __all__ = ["Mechanism", "mech_load", "mech_validate", "chem_rhs", "chem_rhs_mixed", "chem_jvp", "rok4e_integrate",
            "rok4e_workspace_size", "simpler_split_step", "simpler_split_step_workspace_size",
-           "diffusion_1d", "probe_throughput", "eval_exp", "Opts", "RokError", "STATS_FIELDS"]
+           "diffusion_1d", "probe_throughput", "eval_exp", "split_step", "SCHEMES", "Opts", "RokError", "STATS_FIELDS"]
 
 STATS_FIELDS = ("n_accept", "n_reject", "n_rhs", "status")
 
@@ -215,6 +215,26 @@ def simpler_split_step(m: Mechanism, U, dt, D, dx, rtol, atol, krylov_dim=4, *, 
                                       ctypes.byref(oc), _dptr(stats, "stats", 4 * n, torch.int32),
                                       _dptr(workspace, "workspace", dtype=torch.uint8), workspace.numel(),
                                       _stream_ptr(stream)), "rk_simpler_split_step")
+    return U
+
+
+SCHEMES = {"simpler": 0, "strang": 1, "simple_balanced": 2, "simple_balanced_transport_first": 3}
+
+
+def split_step(m: Mechanism, U, dt, D, dx, rtol, atol, krylov_dim=4, scheme="simpler", *, p=101325.0,
+               h_cell=None, opts: Opts | None = None, stats=None, workspace=None, stream=None):
+    """One split step (any scheme of SCHEMES) of the 1-D reaction-diffusion system, in place."""
+    n = _ncell(U, m)
+    sc = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    oc = (opts or Opts()).c()
+    if workspace is None:
+        nb = int(_L().rk_split_step_workspace_size(m.handle, n, int(krylov_dim), sc, ctypes.byref(oc)))
+        workspace = torch.empty(nb, dtype=torch.uint8, device=U.device)
+    _check(_L().rk_split_step(m.handle, _dptr(U, "U"), _dptr(h_cell, "h_cell", n), n, float(p), float(dt),
+                              float(D), float(dx), float(rtol), float(atol), int(krylov_dim), sc, ctypes.byref(oc),
+                              _dptr(stats, "stats", 4 * n, torch.int32),
+                              _dptr(workspace, "workspace", dtype=torch.uint8), workspace.numel(),
+                              _stream_ptr(stream)), "rk_split_step")
     return U
 
 

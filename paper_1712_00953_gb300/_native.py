@@ -74,6 +74,13 @@ SIGNATURES = {
                                                      ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                      ctypes.c_double, ctypes.c_int32, ctypes.POINTER(RkOpts),
                                                      ctypes.c_void_p, ctypes.c_void_p]),
+    "rk_split_step_workspace_size": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                                       ctypes.c_int32, ctypes.POINTER(RkOpts)]),
+    "rk_split_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.POINTER(RkOpts), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                     ctypes.c_void_p]),
     "rk_diffusion_1d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_void_p]),
     "rk_probe_throughput": (ctypes.c_int, [ctypes.c_int32, c_double_p]),

@@ -115,19 +115,6 @@ __device__ __forceinline__ void exp_pm(double x, const double* __restrict__ tab,
   *em = exp_scale(fma(tm, pm, tm), km >> 7);
 }
 
-// exp(x) with an FP32 core for the mixed-precision mode: x log2 e = n + f
-// with n an integer (FP64, shifter trick) and |f| <= 1/2; 2^f from the FP32
-// exp2f; the scaling by 2^n is an integer add to the exponent.  Relative
-// error ~3e-7 (the FP32 exp2f); FP64 ops: 3 plus two conversions.
-__device__ __forceinline__ double exp_mixed(double x) {
-  if ((__double2hiint(x) & 0x7fffffff) >= 0x40862000) return exp(x);
-  const double t = fma(x, 1.4426950408889634, EXP_SHIFTER);
-  const int n = __double2loint(t);
-  const double nd = t - EXP_SHIFTER;
-  const float f = __double2float_rn(fma(x, 1.4426950408889634, -nd));
-  return exp_scale((double)exp2f(f), n);
-}
-
 __device__ inline void load_exp_table(double* dst) {
   for (int i = threadIdx.x; i < RK_EXP2_TABLE_N; i += blockDim.x) dst[i] = c_exp2_table[i];
 }
@@ -496,7 +483,7 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     const bool rev = (meta >> 2) & 1;
     const int dnu = ((meta >> 4) & 15) - 4;
     const double lnk = m.lnA[j] + m.bexp[j] * lnT - m.EaR[j] * invT;
-    double k = MIXED ? exp_mixed(lnk) : exp_fast(lnk, m.etab);
+    double k = exp_fast(lnk, m.etab);
     const double Pf = s.C[ra] * s.C[rb];
     const double Pb = s.C[pa] * s.C[pb];
     double rfac = 0.0;  // 1/Kc
@@ -994,6 +981,66 @@ __device__ inline void solve_small(const SlotPtrs& s, int mdim, double* z) {
   }
 }
 
+// ------------------------------------------------ cost-ordered work queue
+// Cells are handed out longest-expected-first: the expected substep count of
+// a cell is dt / h with h its carried step (h_cell), binned on a quarter-octave
+// log scale; a counting sort (per-block histograms reserved in one atomic per
+// bin, then scattered) writes the queue order.  Cells with no carried step or
+// h >= dt land in the cheapest bin.
+constexpr int ORDER_BINS = 64;
+constexpr int ORDER_THREADS = 256;
+
+__device__ __forceinline__ int cost_bin(double h, double dt) {
+  if (!(h > 0.0) || !(h < dt)) return 0;
+  const float r = __double2float_rn(dt) / __double2float_rn(h);
+  const int b = (int)(4.0f * __log2f(r));
+  return b < 0 ? 0 : (b >= ORDER_BINS ? ORDER_BINS - 1 : b);
+}
+
+__global__ void __launch_bounds__(ORDER_THREADS) order_count_kernel(const double* __restrict__ h, int64_t n,
+                                                                    int64_t chunk, double dt, unsigned* hist) {
+  __shared__ unsigned sh[ORDER_BINS];
+  for (int i = threadIdx.x; i < ORDER_BINS; i += blockDim.x) sh[i] = 0u;
+  __syncthreads();
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&sh[cost_bin(h[i], dt)], 1u);
+  __syncthreads();
+  for (int i = threadIdx.x; i < ORDER_BINS; i += blockDim.x)
+    if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+__global__ void order_scan_kernel(const unsigned* hist, unsigned* cursor) {
+  if (threadIdx.x == 0) {
+    unsigned acc = 0u;
+    for (int b = ORDER_BINS - 1; b >= 0; --b) {  // most expensive bin first
+      cursor[b] = acc;
+      acc += hist[b];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(ORDER_THREADS) order_scatter_kernel(const double* __restrict__ h, int64_t n,
+                                                                      int64_t chunk, double dt, unsigned* cursor,
+                                                                      int32_t* perm) {
+  __shared__ unsigned cnt[ORDER_BINS], base[ORDER_BINS];
+  for (int i = threadIdx.x; i < ORDER_BINS; i += blockDim.x) cnt[i] = 0u;
+  __syncthreads();
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&cnt[cost_bin(h[i], dt)], 1u);
+  __syncthreads();
+  for (int i = threadIdx.x; i < ORDER_BINS; i += blockDim.x) {
+    base[i] = cnt[i] ? atomicAdd(&cursor[i], cnt[i]) : 0u;
+    cnt[i] = 0u;
+  }
+  __syncthreads();
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const int b = cost_bin(h[i], dt);
+    perm[base[b] + atomicAdd(&cnt[b], 1u)] = (int32_t)i;
+  }
+}
+
 // ------------------------------------------------------- integration kernel
 struct IntegrateParams {
   const unsigned char* mech;  // packed mechanism (global)
@@ -1009,6 +1056,7 @@ struct IntegrateParams {
   int32_t* stats;
   unsigned long long* counter;
   unsigned long long qstride;  // queue position q takes cell (q * qstride) mod ncell
+  const int32_t* order;        // or, when set, cell order[q] (longest expected first)
 };
 
 template <int G, bool MIXED>
@@ -1227,7 +1275,8 @@ __global__ void __launch_bounds__(512) rok4e_integrate_kernel(IntegrateParams P)
     if (q >= (unsigned long long)P.ncell) break;
     // Interleave the queue over the cell index: neighbouring cells (e.g. the
     // hot side of a flame) spread over all SMs instead of filling a few.
-    const unsigned long long cell = (q * P.qstride) % (unsigned long long)P.ncell;
+    const unsigned long long cell =
+        P.order ? (unsigned long long)P.order[q] : (q * P.qstride) % (unsigned long long)P.ncell;
     integrate_cell<G, MIXED>(m, s, P, (int64_t)cell);
   }
 }
@@ -1300,6 +1349,13 @@ __device__ inline double lap1d(const double* U, int64_t i, int v, int64_t n, int
   return U[im * nv + v] - 2.0 * U[i * nv + v] + U[ip * nv + v];
 }
 
+// c = (a R + b T) elementwise (the balancing constants of the splittings)
+__global__ void axpby_kernel(const double* __restrict__ R, const double* __restrict__ T, double a, double b,
+                             double* __restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a * R[i] + b * T[i];
+}
+
 __global__ void diffusion_kernel(const double* __restrict__ U, double* __restrict__ TU, int64_t n, int nv,
                                  double D, double inv_dx2) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1310,15 +1366,17 @@ __global__ void diffusion_kernel(const double* __restrict__ U, double* __restric
 }
 
 // stage 0: V1 = U1 + k g(U1); stage 1: V2 = 3/4 U1 + 1/4 (V1 + k g(V1));
-// stage 2: U = 1/3 U1 + 2/3 (V2 + k g(V2)), with g(V) = D lap V - Tn.
+// stage 2: U = 1/3 U1 + 2/3 (V2 + k g(V2)), with g(V) = D lap V + sigma S
+// (S a constant source array, or null for pure transport).
 __global__ void ssprk3_stage_kernel(int stage, const double* __restrict__ U1, const double* __restrict__ X,
-                                    const double* __restrict__ Tn, double* Out, int64_t n, int nv, double D,
-                                    double inv_dx2, double k) {
+                                    const double* __restrict__ S, double sigma, double* Out, int64_t n, int nv,
+                                    double D, double inv_dx2, double k) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * nv) return;
   const int64_t i = idx / nv;
   const int v = (int)(idx - i * nv);
-  const double gX = D * (lap1d(X, i, v, n, nv) * inv_dx2) - Tn[idx];
+  const double dX = D * (lap1d(X, i, v, n, nv) * inv_dx2);
+  const double gX = S ? fma(sigma, S[idx], dX) : dX;
   const double xk = X[idx] + k * gX;
   double r;
   if (stage == 0) r = xk;
@@ -1504,7 +1562,7 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   const bool mixed = o.precision >= 1;
   const int G = o.lanes_per_cell == 0 ? 32 : o.lanes_per_cell;
   if (G != 8 && G != 16 && G != 32) return set_error(RK_E_INVALID_ARGUMENT, "lanes_per_cell must be 0, 8, 16 or 32");
-  if (!workspace || workspace_bytes < sizeof(unsigned long long))
+  if (!workspace || workspace_bytes < rk_rok4e_workspace_size(mech, ncell, M, opts))
     return set_error(RK_E_WORKSPACE, "workspace missing or smaller than rk_rok4e_workspace_size");
   const int N = mech->host.L.ns + 1;
   const int Meff = M > N ? N : M;
@@ -1529,10 +1587,26 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   P.trace_cap = o.trace_cap;
   P.trace = o.trace;
   P.stats = stats;
-  P.counter = reinterpret_cast<unsigned long long*>(workspace);
+  unsigned char* wsb = static_cast<unsigned char*>(workspace);
+  P.counter = reinterpret_cast<unsigned long long*>(wsb);
   P.qstride = queue_stride(ncell);
-  cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), stream);
+  P.order = nullptr;
+  cudaError_t e = cudaMemsetAsync(wsb, 0, 768, stream);  // counter, histogram, cursors
   if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
+  if (h_cell && ncell > 1 && !(o.fixed_h > 0.0) && ncell < (int64_t)INT32_MAX) {
+    unsigned* hist = reinterpret_cast<unsigned*>(wsb + 256);
+    unsigned* cursor = reinterpret_cast<unsigned*>(wsb + 512);
+    int32_t* perm = reinterpret_cast<int32_t*>(wsb + 768);
+    int64_t nblk = (ncell + 4095) / 4096;
+    if (nblk > 1024) nblk = 1024;
+    const int64_t chunk = (ncell + nblk - 1) / nblk;
+    order_count_kernel<<<(unsigned)nblk, ORDER_THREADS, 0, stream>>>(h_cell, ncell, chunk, dt, hist);
+    order_scan_kernel<<<1, 32, 0, stream>>>(hist, cursor);
+    order_scatter_kernel<<<(unsigned)nblk, ORDER_THREADS, 0, stream>>>(h_cell, ncell, chunk, dt, cursor, perm);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "work-queue ordering launch");
+    P.order = perm;
+  }
   LaunchPlan plan;
   if (o.ev_begin) {
     e = cudaEventRecord((cudaEvent_t)o.ev_begin, stream);
@@ -1665,10 +1739,11 @@ int rk_chem_rhs_mixed(const rk_mech* mech, const double* Y, const double* src, d
 
 size_t rk_rok4e_workspace_size(const rk_mech* mech, int64_t ncell, int32_t krylov_dim, const rk_opts* opts) {
   (void)mech;
-  (void)ncell;
   (void)krylov_dim;
   (void)opts;
-  return 256;
+  // work-queue counter, order histogram and cursors, and the queue order
+  const size_t order = ncell > 0 ? (size_t)ncell * sizeof(int32_t) : 0;
+  return 768 + ((order + 255) & ~(size_t)255);
 }
 
 int rk_rok4e_integrate(const rk_mech* mech, double* Y, const double* src, double* h_cell, int64_t ncell, double p,
@@ -1731,11 +1806,89 @@ int rk_simpler_split_step(const rk_mech* mech, double* U, double* h_cell, int64_
   if (rc) return rc;
   // transport correction over dt/2: one SSP-RK3 step of dU/dt = T(U) - T(U_n)
   const double k = 0.5 * dt;
-  ssprk3_stage_kernel<<<nb, 256, 0, st>>>(0, U, U, Tn, V1, npts, nv, D, inv_dx2, k);
-  ssprk3_stage_kernel<<<nb, 256, 0, st>>>(1, U, V1, Tn, V2, npts, nv, D, inv_dx2, k);
-  ssprk3_stage_kernel<<<nb, 256, 0, st>>>(2, U, V2, Tn, U, npts, nv, D, inv_dx2, k);
+  ssprk3_stage_kernel<<<nb, 256, 0, st>>>(0, U, U, Tn, -1.0, V1, npts, nv, D, inv_dx2, k);
+  ssprk3_stage_kernel<<<nb, 256, 0, st>>>(1, U, V1, Tn, -1.0, V2, npts, nv, D, inv_dx2, k);
+  ssprk3_stage_kernel<<<nb, 256, 0, st>>>(2, U, V2, Tn, -1.0, U, npts, nv, D, inv_dx2, k);
   e = cudaGetLastError();
   return e == cudaSuccess ? RK_OK : cuda_error(e, "ssprk3_stage_kernel launch");
+}
+
+// One SSP-RK3 step of dU/dt = D d^2U/dx^2 + sigma S over t, in place (V1, V2 scratch).
+static int transport_step(double* U, const double* S, double sigma, double t, double D, double dx, int64_t npts,
+                          int nv, double* V1, double* V2, cudaStream_t st) {
+  const int64_t n = npts * nv;
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  const double inv_dx2 = 1.0 / (dx * dx);
+  ssprk3_stage_kernel<<<nb, 256, 0, st>>>(0, U, U, S, sigma, V1, npts, nv, D, inv_dx2, t);
+  ssprk3_stage_kernel<<<nb, 256, 0, st>>>(1, U, V1, S, sigma, V2, npts, nv, D, inv_dx2, t);
+  ssprk3_stage_kernel<<<nb, 256, 0, st>>>(2, U, V2, S, sigma, U, npts, nv, D, inv_dx2, t);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RK_OK : cuda_error(e, "ssprk3_stage_kernel launch");
+}
+
+size_t rk_split_step_workspace_size(const rk_mech* mech, int64_t npts, int32_t krylov_dim, int32_t scheme,
+                                    const rk_opts* opts) {
+  if (!mech || npts < 0) return 0;
+  (void)scheme;
+  const size_t n = (size_t)npts * (size_t)(mech->host.L.ns + 1);
+  return 256 + 4 * ((n * sizeof(double) + 255) & ~(size_t)255) +
+         rk_rok4e_workspace_size(mech, npts, krylov_dim, opts);
+}
+
+int rk_split_step(const rk_mech* mech, double* U, double* h_cell, int64_t npts, double p, double dt, double D,
+                  double dx, double rtol, double atol, int32_t krylov_dim, int32_t scheme, const rk_opts* opts,
+                  int32_t* stats, void* workspace, size_t workspace_bytes, void* stream) {
+  int rc = check_mech(mech);
+  if (rc) return rc;
+  if (scheme < 0 || scheme > 3) return set_error(RK_E_INVALID_ARGUMENT, "scheme must be 0..3");
+  if (npts < 0) return set_error(RK_E_INVALID_ARGUMENT, "npts < 0");
+  if (npts == 0) return RK_OK;
+  if (!U) return set_error(RK_E_INVALID_ARGUMENT, "null state array");
+  if (!(dx > 0.0) || !(D >= 0.0) || !(dt > 0.0)) return set_error(RK_E_INVALID_ARGUMENT, "need dx, dt > 0, D >= 0");
+  const size_t need = rk_split_step_workspace_size(mech, npts, krylov_dim, scheme, opts);
+  if (!workspace || workspace_bytes < need) return set_error(RK_E_WORKSPACE, "workspace too small");
+  const int nv = mech->host.L.ns + 1;
+  const int64_t n = npts * nv;
+  const size_t vec = ((size_t)n * sizeof(double) + 255) & ~(size_t)255;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  double* Tn = reinterpret_cast<double*>(ws + 256);
+  double* V1 = reinterpret_cast<double*>(ws + 256 + vec);
+  double* V2 = reinterpret_cast<double*>(ws + 256 + 2 * vec);
+  double* Cn = reinterpret_cast<double*>(ws + 256 + 3 * vec);
+  void* ws_int = ws + 256 + 4 * vec;
+  const size_t ws_int_bytes = workspace_bytes - (256 + 4 * vec);
+  cudaStream_t st = (cudaStream_t)stream;
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  auto react = [&](const double* src, double t) {
+    return integrate_impl(mech, U, src, h_cell, npts, p, t, rtol, atol, krylov_dim, opts, stats, ws_int,
+                          ws_int_bytes, st);
+  };
+  cudaError_t e;
+  if (scheme == 0) {  // Simpler: c_n = -T(U_n); R - c_n over dt; T + c_n over dt/2
+    diffusion_kernel<<<nb, 256, 0, st>>>(U, Tn, npts, nv, D, 1.0 / (dx * dx));
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "diffusion_kernel launch");
+    if ((rc = react(Tn, dt))) return rc;
+    return transport_step(U, Tn, -1.0, 0.5 * dt, D, dx, npts, nv, V1, V2, st);
+  }
+  if (scheme == 1) {  // Strang: T over dt/2, R over dt, T over dt/2
+    if ((rc = transport_step(U, nullptr, 0.0, 0.5 * dt, D, dx, npts, nv, V1, V2, st))) return rc;
+    if ((rc = react(nullptr, dt))) return rc;
+    return transport_step(U, nullptr, 0.0, 0.5 * dt, D, dx, npts, nv, V1, V2, st);
+  }
+  // simple balanced: c_n = (R(U_n) - T(U_n)) / 2; Cn holds -c_n = (T - R) / 2
+  if ((rc = point_call(mech, U, nullptr, nullptr, p, Cn, npts, 0, stream))) return rc;
+  diffusion_kernel<<<nb, 256, 0, st>>>(U, Tn, npts, nv, D, 1.0 / (dx * dx));
+  axpby_kernel<<<nb, 256, 0, st>>>(Cn, Tn, -0.5, 0.5, Cn, n);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "balancing constant launch");
+  if (scheme == 2) {  // reaction first: R - c over dt/2, T + c over dt, R - c over dt/2
+    if ((rc = react(Cn, 0.5 * dt))) return rc;
+    if ((rc = transport_step(U, Cn, -1.0, dt, D, dx, npts, nv, V1, V2, st))) return rc;
+    return react(Cn, 0.5 * dt);
+  }
+  // transport first (Eq. balanced): T + c over dt/2, R - c over dt, T + c over dt/2
+  if ((rc = transport_step(U, Cn, -1.0, 0.5 * dt, D, dx, npts, nv, V1, V2, st))) return rc;
+  if ((rc = react(Cn, dt))) return rc;
+  return transport_step(U, Cn, -1.0, 0.5 * dt, D, dx, npts, nv, V1, V2, st);
 }
 
 // ---- allocation-free split step ---------------------------------------------
