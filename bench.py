@@ -212,7 +212,7 @@ def run_plain(args):
     for _ in range(args.plain_steps):
         rk.simpler_split_step(m, U, w.dt, D_DIFF, LENGTH / U.shape[0], w.rtol, w.atol, w.krylov_dim, h_cell=hc,
                               opts=rk.Opts(lanes_per_cell=args.lanes, cells_per_block=args.cells_per_block,
-                                           precision=PREC[args.precision]))
+                                           precision=PREC[args.precision], queue_order=args.queue_order, blocks_per_sm=args.blocks_per_sm))
     torch.cuda.synchronize()
     print(json.dumps({"plain_steps": args.plain_steps, "T_max": float(U[:, -1].max())}))
     return 0
@@ -250,7 +250,7 @@ def run_ours(args, rank, world, local_rank):
 
     def step(stats=None, events=None):
         rk.simpler_split_step(m, U, w.dt, D_DIFF, dx, w.rtol, w.atol, M, h_cell=hc, stats=stats,
-                              opts=rk.Opts(events=events, lanes_per_cell=args.lanes, cells_per_block=args.cells_per_block, precision=PREC[args.precision]), workspace=ws,
+                              opts=rk.Opts(events=events, lanes_per_cell=args.lanes, cells_per_block=args.cells_per_block, precision=PREC[args.precision], queue_order=args.queue_order, blocks_per_sm=args.blocks_per_sm), workspace=ws,
                               stream=stream)
 
     for _ in range(args.warmup):
@@ -270,7 +270,7 @@ def run_ours(args, rank, world, local_rank):
     with torch.cuda.stream(cap_stream):
         with torch.cuda.graph(graph, stream=cap_stream, capture_error_mode="relaxed"):
             rk.simpler_split_step(m, U, w.dt, D_DIFF, dx, w.rtol, w.atol, M, h_cell=hc, stats=stats_step,
-                                  opts=rk.Opts(lanes_per_cell=args.lanes, cells_per_block=args.cells_per_block, precision=PREC[args.precision]), workspace=ws, stream=cap_stream)
+                                  opts=rk.Opts(lanes_per_cell=args.lanes, cells_per_block=args.cells_per_block, precision=PREC[args.precision], queue_order=args.queue_order, blocks_per_sm=args.blocks_per_sm), workspace=ws, stream=cap_stream)
     torch.cuda.current_stream().wait_stream(cap_stream)
     torch.cuda.synchronize()
     restore()
@@ -356,7 +356,8 @@ def run_ours(args, rank, world, local_rank):
                                "(4 third-body, 2 Troe), Simpler split steps of 1e-7 s, ROK4E M=4, rtol 1e-6, "
                                "atol 1e-10", "precision": args.precision, "points": npts,
                    "l2": "flushed (256 MB write) between steps", "parallelism": f"replicas x{world}",
-                   "lanes_per_cell": args.lanes or 32, "cells_per_block": args.cells_per_block},
+                   "lanes_per_cell": args.lanes or 32, "cells_per_block": args.cells_per_block,
+                   "queue_order": args.queue_order, "blocks_per_sm": args.blocks_per_sm},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_nominal, "unit": "TFLOP/s",
                      "frac": achieved / peak_nominal, "traffic": None,
                      "kernel": "rok4e_integrate_kernel<32>", "kernel_ms_per_step": 1e3 * kern_total / args.steps,
@@ -393,6 +394,8 @@ def main():
     ap.add_argument("--lanes", type=int, default=0, help="lanes per cell (0: library default)")
     ap.add_argument("--cells-per-block", type=int, default=4, help="cells per block (0: library default)")
     ap.add_argument("--precision", default="fp64", choices=list(PREC))
+    ap.add_argument("--queue-order", type=int, default=1, help="0 auto, 1 interleaved, 2 longest first")
+    ap.add_argument("--blocks-per-sm", type=int, default=0, help="resident blocks per SM (0: all that fit)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

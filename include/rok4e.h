@@ -162,6 +162,10 @@ typedef struct rk_opts {
   double* trace;          /* device [ncell x trace_cap]: +h accepted, -h rejected, 0 unused */
   void* ev_begin;         /* optional cudaEvent_t recorded on the stream right before the */
   void* ev_end;           /* integration kernel and right after it (timing hook), or NULL */
+  int32_t queue_order;    /* 0 auto (1 without h_cell, 2 with it), 1 interleaved cell
+                             index, 2 longest expected first (dt / h_cell) */
+  int32_t blocks_per_sm;  /* resident blocks per SM for the persistent launch; 0: all
+                             that fit */
 } rk_opts;
 
 /* Bytes of workspace rk_rok4e_integrate needs: a work-queue counter, a
@@ -260,6 +264,30 @@ int rk_split_step(const rk_mech* mech, double* U, double* h_cell, int64_t npts, 
 /* Transport operator alone: TU = D d^2U/dx^2 (same discretisation). */
 int rk_diffusion_1d(const double* U, double* TU, int64_t npts, int32_t nvar, double D, double dx,
                     void* stream);
+
+/* ---- fixed-step integration with checkpoints and its adjoint ----------------
+ * nsteps fixed ROK4E steps of size h (Algorithm 1 with h held fixed: no error
+ * control), state in place; checkpoints (device [(nsteps + 1) x ncell x N],
+ * or NULL) receives the state at the start of every step and the final state.
+ * Analytic Jacobian-vector products, FP64.  Workspace: rk_rok4e_workspace_size. */
+int rk_rok4e_fixed_steps(const rk_mech* mech, double* Y, int64_t ncell, double p, double h,
+                         int32_t nsteps, int32_t krylov_dim, double* checkpoints, void* workspace,
+                         size_t workspace_bytes, void* stream);
+
+/* Discrete adjoint of rk_rok4e_fixed_steps: given the checkpoints of a forward
+ * run and ubar = dL/du(t_end) (device [ncell x N]), returns
+ *   grad_lnA[j] = sum_cells dL/d ln A_j   (device [Nr], input reaction order;
+ *                 for a Troe reaction A is the high-pressure factor)
+ *   grad_u0     = dL/du(0) per cell       (device [ncell x N], or NULL).
+ * Each step is recomputed from its checkpoint and differentiated exactly,
+ * including the dependence of the Arnoldi basis on the state and on ln A
+ * (second derivatives of the source term).  The paper has no adjoint; this is
+ * the library's sensitivity extension of its integrator.  Workspace:
+ * rk_rok4e_adjoint_workspace_size (about (60 N + 8 Nr) doubles per cell). */
+size_t rk_rok4e_adjoint_workspace_size(const rk_mech* mech, int64_t ncell, int32_t krylov_dim);
+int rk_rok4e_adjoint(const rk_mech* mech, const double* checkpoints, const double* ubar, int64_t ncell,
+                     double p, double h, int32_t nsteps, int32_t krylov_dim, double* grad_lnA,
+                     double* grad_u0, void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---- diagnostics ---------------------------------------------------------------
  * Throughput probes of the arithmetic units used by the roofline:

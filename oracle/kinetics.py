@@ -63,6 +63,7 @@ class Kinetics:
         order_f = nu_f.sum(axis=1)
         # concentration order of the rate expression: +1 for a (+M) third body
         conc_order = order_f + (self.kind == 1)
+        self.lnA_input = np.log(A)  # ln A as given (cm-mol-s)
         self.lnA = np.log(A) + (conc_order - 1) * np.log(1e-6)
         self.b = b
         self.Ea_R = Ea / R_GAS
@@ -73,6 +74,14 @@ class Kinetics:
         self.b0 = fo[:, 1]
         self.Ea0_R = fo[:, 2] / R_GAS
         self.troe_a, self.T3, self.T1, self.T2 = fo[:, 3], fo[:, 4], fo[:, 5], fo[:, 6]
+
+    def with_lnA(self, lnA):
+        """A copy whose ln A (SI) is replaced, e.g. by a complex-perturbed one.
+        ``lnA`` is in the input reaction order; the SI conversion offset is kept."""
+        import copy
+        other = copy.copy(self)
+        other.lnA = self.lnA + (np.asarray(lnA) - self.lnA_input)
+        return other
 
     # ------------------------------------------------------------------ thermo
     def coeffs(self, T):

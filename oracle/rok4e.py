@@ -65,29 +65,37 @@ T_END_TOL = 1e-12
 STATUS_OK, STATUS_MAX_ATTEMPTS, STATUS_NONFINITE, STATUS_STEP_UNDERFLOW = 0, 1, 2, 3
 
 
+def _norm(v):
+    """2-norm; for complex input the analytic continuation sqrt(sum v_i^2), so
+    that complex-step differentiation passes through the Arnoldi process."""
+    if np.iscomplexobj(v):
+        return np.sqrt(np.sum(v * v))
+    return np.linalg.norm(v)
+
+
 def arnoldi(jv, f, M):
     """Orthonormal Q (N x m) and Hessenberg H (m x m) with H = Q^T J Q on K_M(J, f)."""
     N = f.shape[0]
     M = min(M, N)
-    beta = np.linalg.norm(f)
-    if M == 0 or beta == 0.0 or not np.isfinite(beta):
-        return np.zeros((N, 0)), np.zeros((0, 0))
-    Q = np.zeros((N, M))
-    H = np.zeros((M, M))
+    beta = _norm(f)
+    if M == 0 or np.real(beta) == 0.0 or not np.isfinite(beta):
+        return np.zeros((N, 0), dtype=f.dtype), np.zeros((0, 0), dtype=f.dtype)
+    Q = np.zeros((N, M), dtype=f.dtype)
+    H = np.zeros((M, M), dtype=f.dtype)
     Q[:, 0] = f / beta
     m = M
     for j in range(M):
         w = jv(Q[:, j])
-        w0 = np.linalg.norm(w)
+        w0 = _norm(w)
         for _pass in range(2):
             for i in range(j + 1):
                 hij = Q[:, i] @ w
                 H[i, j] += hij
                 w = w - hij * Q[:, i]
-        hn = np.linalg.norm(w)
+        hn = _norm(w)
         if j + 1 == M:
             break
-        if hn <= BREAKDOWN_TOL * w0 or hn == 0.0:
+        if np.real(hn) <= BREAKDOWN_TOL * np.real(w0) or hn == 0.0:
             m = j + 1
             break
         H[j + 1, j] = hn
@@ -151,7 +159,7 @@ def integrate(f, jv_at, u0, t_end, rtol, atol, M, *, h0=None, max_attempts=10000
     Returns (u, info) with info: h_last, n_accept, n_reject, n_f, n_jv, status,
     errs (per attempt) and trace [(h, accepted)] when record or replay.
     """
-    u = np.array(u0, dtype=float)
+    u = np.array(u0, dtype=np.result_type(u0, float))
     t = 0.0
     h = t_end if h0 is None or h0 <= 0 else float(h0)
     if fixed_h is not None:
@@ -184,7 +192,7 @@ def integrate(f, jv_at, u0, t_end, rtol, atol, M, *, h0=None, max_attempts=10000
         u_star, u_hat, nf = attempt(f, u, fn, Q, H, h)
         info["n_f"] += nf
         n_att += 1
-        err = error_norm(u_star, u_hat, rtol, atol)
+        err = error_norm(u_star, u_hat, rtol, atol) if n_fixed is None else 0.0
         info["errs"].append(err)
         if n_fixed is not None:
             accept = True
@@ -197,7 +205,7 @@ def integrate(f, jv_at, u0, t_end, rtol, atol, M, *, h0=None, max_attempts=10000
         if record or replay is not None:
             info["trace"].append((h, accept))
         if accept:
-            if not np.all(np.isfinite(u_star)):
+            if not np.all(np.isfinite(u_star)):  # (complex: both parts)
                 info["status"] = STATUS_NONFINITE
                 break
             u = u_star

@@ -29,7 +29,8 @@ def _L():
 
 __all__ = ["Mechanism", "mech_load", "mech_validate", "chem_rhs", "chem_rhs_mixed", "chem_jvp", "rok4e_integrate",
            "rok4e_workspace_size", "simpler_split_step", "simpler_split_step_workspace_size",
-           "diffusion_1d", "probe_throughput", "eval_exp", "split_step", "SCHEMES", "Opts", "RokError", "STATS_FIELDS"]
+           "diffusion_1d", "probe_throughput", "eval_exp", "split_step", "SCHEMES", "rok4e_fixed_steps",
+           "rok4e_adjoint", "FixedStepROK4E", "Opts", "RokError", "STATS_FIELDS"]
 
 STATS_FIELDS = ("n_accept", "n_reject", "n_rhs", "status")
 
@@ -127,13 +128,14 @@ class Opts:
     """Integration options (rk_opts); None fields keep the library defaults."""
 
     def __init__(self, jv_mode=0, max_attempts=0, lanes_per_cell=0, cells_per_block=0, h0=0.0, fixed_h=0.0,
-                 trace=None, events=None, precision=0):
+                 trace=None, events=None, precision=0, queue_order=0, blocks_per_sm=0):
         self.jv_mode, self.max_attempts = jv_mode, max_attempts
         self.lanes_per_cell, self.cells_per_block = lanes_per_cell, cells_per_block
         self.h0, self.fixed_h = h0, fixed_h
         self.trace = trace  # CUDA float64 tensor [ncell, cap] or None
         self.events = events  # (begin, end) torch.cuda.Event pair around the integration kernel
-        self.precision = precision  # 0 FP64, 1 mixed (FP32 rates/contraction/J v/inner products)
+        self.precision = precision  # 0 FP64, 1 mixed (FP32 nu^T q and inner products), 2 + FP32 J v
+        self.queue_order, self.blocks_per_sm = queue_order, blocks_per_sm
 
     def c(self):
         cap = 0 if self.trace is None else int(self.trace.shape[-1])
@@ -142,7 +144,7 @@ class Opts:
         if self.events is not None:
             eb, ee = (ctypes.c_void_p(e.cuda_event) for e in self.events)
         return RkOpts(self.jv_mode, self.max_attempts, self.lanes_per_cell, self.cells_per_block, self.h0,
-                      self.fixed_h, cap, self.precision, tp, eb, ee)
+                      self.fixed_h, cap, self.precision, tp, eb, ee, self.queue_order, self.blocks_per_sm)
 
 
 def _ncell(Y, m):
@@ -251,6 +253,65 @@ def eval_exp(x, which=0, out=None, stream=None):
     _check(_L().rk_eval_exp(_dptr(x, "x"), _dptr(out, "out", x.numel()), x.numel(), int(which),
                             _stream_ptr(stream)), "rk_eval_exp")
     return out
+
+
+def rok4e_fixed_steps(m: Mechanism, Y, h, nsteps, krylov_dim=4, *, p=101325.0, checkpoints=None, workspace=None,
+                      stream=None):
+    """nsteps fixed ROK4E steps of size h in place; optionally records the state at
+    the start of every step and the final state in ``checkpoints`` [nsteps+1, ncell, N]."""
+    n = _ncell(Y, m)
+    if workspace is None:
+        workspace = torch.empty(rok4e_workspace_size(m, n, krylov_dim), dtype=torch.uint8, device=Y.device)
+    _check(_L().rk_rok4e_fixed_steps(m.handle, _dptr(Y, "Y"), n, float(p), float(h), int(nsteps), int(krylov_dim),
+                                     _dptr(checkpoints, "checkpoints", (int(nsteps) + 1) * Y.numel()),
+                                     _dptr(workspace, "workspace", dtype=torch.uint8), workspace.numel(),
+                                     _stream_ptr(stream)), "rk_rok4e_fixed_steps")
+    return Y
+
+
+def rok4e_adjoint(m: Mechanism, checkpoints, ubar, h, nsteps, krylov_dim=4, *, p=101325.0, grad_u0=None,
+                  workspace=None, stream=None):
+    """Discrete adjoint of rok4e_fixed_steps: returns (grad_lnA [Nr], grad_u0 [ncell, N] or None)."""
+    n = _ncell(ubar, m)
+    if workspace is None:
+        nb = int(_L().rk_rok4e_adjoint_workspace_size(m.handle, n, int(krylov_dim)))
+        workspace = torch.empty(nb, dtype=torch.uint8, device=ubar.device)
+    grad = torch.empty(m.n_reactions, dtype=torch.float64, device=ubar.device)
+    _check(_L().rk_rok4e_adjoint(m.handle, _dptr(checkpoints, "checkpoints", (int(nsteps) + 1) * ubar.numel()),
+                                 _dptr(ubar, "ubar"), n, float(p), float(h), int(nsteps), int(krylov_dim),
+                                 _dptr(grad, "grad"), _dptr(grad_u0, "grad_u0", ubar.numel()),
+                                 _dptr(workspace, "workspace", dtype=torch.uint8), workspace.numel(),
+                                 _stream_ptr(stream)), "rk_rok4e_adjoint")
+    return grad, grad_u0
+
+
+class FixedStepROK4E(torch.autograd.Function):
+    """u(t_end) of fixed-step ROK4E as a differentiable function of (ln A, u0).
+
+    forward(lnA, Y0, mech, h, nsteps, M, p): lnA is a CPU float64 tensor [Nr] of
+    natural logs of the pre-exponential factors (cm-mol-s, input reaction
+    order; for Troe reactions the high-pressure factor), Y0 a CUDA float64
+    tensor [ncell, N]; ``mech`` a synth.Mechanism supplying everything else.
+    The forward pass keeps one checkpoint per step; backward runs the
+    hand-written adjoint kernel (rk_rok4e_adjoint)."""
+
+    @staticmethod
+    def forward(ctx, lnA, Y0, mech, h, nsteps, M=4, p=101325.0):
+        mk = mech.copy()
+        mk.arrh[:, 0] = np.exp(lnA.detach().cpu().numpy())
+        m = Mechanism(mk)
+        Y = Y0.detach().clone().contiguous()
+        ckpt = torch.empty((int(nsteps) + 1,) + tuple(Y.shape), dtype=torch.float64, device=Y.device)
+        rok4e_fixed_steps(m, Y, h, nsteps, M, p=p, checkpoints=ckpt)
+        ctx.m, ctx.ckpt, ctx.h, ctx.nsteps, ctx.M, ctx.p = m, ckpt, h, nsteps, M, p
+        ctx.lnA_device = lnA.device
+        return Y
+
+    @staticmethod
+    def backward(ctx, gY):
+        g0 = torch.empty_like(gY)
+        grad, g0 = rok4e_adjoint(ctx.m, ctx.ckpt, gY.contiguous(), ctx.h, ctx.nsteps, ctx.M, p=ctx.p, grad_u0=g0)
+        return grad.to(ctx.lnA_device), g0, None, None, None, None, None
 
 
 def probe_throughput(kind: int) -> float:

@@ -41,6 +41,8 @@ class RkOpts(ctypes.Structure):
         ("trace", ctypes.c_void_p),
         ("ev_begin", ctypes.c_void_p),
         ("ev_end", ctypes.c_void_p),
+        ("queue_order", ctypes.c_int32),
+        ("blocks_per_sm", ctypes.c_int32),
     ]
 
 
@@ -81,6 +83,14 @@ SIGNATURES = {
                                      ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                      ctypes.POINTER(RkOpts), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                      ctypes.c_void_p]),
+    "rk_rok4e_fixed_steps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "rk_rok4e_adjoint_workspace_size": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]),
+    "rk_rok4e_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                        ctypes.c_void_p]),
     "rk_diffusion_1d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_void_p]),
     "rk_probe_throughput": (ctypes.c_int, [ctypes.c_int32, c_double_p]),

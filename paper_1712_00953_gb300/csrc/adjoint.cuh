@@ -1,0 +1,581 @@
+// Discrete adjoint of fixed-step ROK4E (Algorithm 1 with h held fixed) with
+// respect to the initial state and the log pre-exponential factors ln A_j.
+//
+// One thread integrates one cell backwards through the recorded steps.  For
+// each step n (last first) it reloads u_n from the checkpoints, recomputes the
+// step's internals -- f_n, the Arnoldi basis Q and Hessenberg H (CGS2), the
+// inverse of L = I - h gamma H, the stage vectors -- and then propagates the
+// adjoint u_bar back through, in reverse order:
+//   u_{n+1} = u_n + h sum_j b_j k_j
+//   k_i = F_i - Q (z_i - y_i) - G_i,  y_i = L^-1 z_i,  z_i = Q^T F_i,
+//   F_i = f(u_n + h sum_j alpha_ij k_j) + G_i,  G_i = sum_j (gamma_ij/gamma) k_j,
+//   L = I - h gamma H,
+//   Arnoldi: w = J q_j, two Gram-Schmidt passes, h_{j+1,j} = |w2|, q_{j+1} = w2 / h_{j+1,j},
+//   q_1 = f_n / |f_n|.
+// The Jacobian-vector products of the Arnoldi process depend on u_n and on
+// ln A through J, so their adjoint needs second derivatives of f: the
+// right-hand side is written once for dual numbers (value, tangent), whose
+// forward pass with tangent v gives J v and whose reverse pass with cotangent
+// w_bar gives J^T w_bar in the values and grad_u (w_bar^T J v) (equal to the
+// directional derivative of J^T w_bar along v) in the tangents.
+//
+// Per-cell arrays live in a structure-of-arrays workspace (element e of cell c
+// at row e * ncell + c), so that the threads of a warp access consecutive
+// addresses.
+#pragma once
+
+namespace rk {
+
+// ------------------------------------------------------------- dual numbers
+struct Dual {
+  double v, t;
+};
+__device__ __forceinline__ Dual dd(double v, double t = 0.0) { return Dual{v, t}; }
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return Dual{a.v + b.v, a.t + b.t}; }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return Dual{a.v - b.v, a.t - b.t}; }
+__device__ __forceinline__ Dual operator-(Dual a) { return Dual{-a.v, -a.t}; }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return Dual{a.v * b.v, fma(a.v, b.t, a.t * b.v)}; }
+__device__ __forceinline__ Dual operator*(double a, Dual b) { return Dual{a * b.v, a * b.t}; }
+__device__ __forceinline__ Dual operator*(Dual a, double b) { return Dual{a.v * b, a.t * b}; }
+__device__ __forceinline__ Dual operator+(Dual a, double b) { return Dual{a.v + b, a.t}; }
+__device__ __forceinline__ Dual operator+(double a, Dual b) { return Dual{a + b.v, b.t}; }
+__device__ __forceinline__ Dual operator-(Dual a, double b) { return Dual{a.v - b, a.t}; }
+__device__ __forceinline__ Dual operator-(double a, Dual b) { return Dual{a - b.v, -b.t}; }
+__device__ __forceinline__ Dual operator/(Dual a, Dual b) {
+  const double iv = 1.0 / b.v;
+  const double q = a.v * iv;
+  return Dual{q, (a.t - q * b.t) * iv};
+}
+__device__ __forceinline__ Dual operator/(double a, Dual b) { return dd(a) / b; }
+__device__ __forceinline__ Dual operator/(Dual a, double b) { return Dual{a.v / b, a.t / b}; }
+__device__ __forceinline__ Dual& operator+=(Dual& a, Dual b) {
+  a = a + b;
+  return a;
+}
+__device__ __forceinline__ Dual& operator-=(Dual& a, Dual b) {
+  a = a - b;
+  return a;
+}
+__device__ __forceinline__ Dual dexp(Dual a, const double* tab) {
+  const double e = exp_fast(a.v, tab);
+  return Dual{e, e * a.t};
+}
+__device__ __forceinline__ Dual dlog(Dual a) { return Dual{log(a.v), a.t / a.v}; }
+__device__ __forceinline__ Dual dlog10(Dual a) { return Dual{log10(a.v), a.t / (a.v * 2.302585092994046)}; }
+
+// element e of the current cell in a structure-of-arrays workspace
+template <typename T>
+struct Col {
+  T* p;
+  int64_t s;
+  __device__ __forceinline__ T& operator[](int64_t e) const { return p[e * s]; }
+};
+
+// Rows of the adjoint workspace (computed on the host).
+struct AdjLayout {
+  int N, ns, nr, ntb, M;
+  // double rows
+  int u, fn, Q, K, F, arg1, arg2, ubar, Kbar, Qbar, fb2, fbn, wbar, w, w1, w2, tmp, H, p1, p2, hn, Linv, zs, ys,
+      Lbar, Hbar, scal, theta;
+  int rows_d;
+  // dual rows
+  int ud, fd, C, cp, h, g, dcp, om, k, rfac, q, Ms, dlnk, dkdM, omg, sc, Cbar, gbar, ombar, Mbar, ubd, fbd;
+  int rows_D;
+};
+
+struct AdjFrame {
+  // doubles
+  Col<double> u, fn, Q, K, F, arg1, arg2, ubar, Kbar, Qbar, fb2, fbn, wbar, w, w1, w2, tmp, H, p1, p2, hn, Linv,
+      zs, ys, Lbar, Hbar, scal, theta;
+  // duals
+  Col<Dual> ud, fd, C, cp, h, g, dcp, om, k, rfac, q, Ms, dlnk, dkdM, omg, sc, Cbar, gbar, ombar, Mbar, ubd, fbd;
+};
+
+__device__ inline AdjFrame adj_frame(double* wsd, Dual* wsD, const AdjLayout& L, int64_t ncell, int64_t c) {
+  AdjFrame f;
+  auto D = [&](int row) { return Col<double>{wsd + (int64_t)row * ncell + c, ncell}; };
+  auto X = [&](int row) { return Col<Dual>{wsD + (int64_t)row * ncell + c, ncell}; };
+  f.u = D(L.u); f.fn = D(L.fn); f.Q = D(L.Q); f.K = D(L.K); f.F = D(L.F); f.arg1 = D(L.arg1); f.arg2 = D(L.arg2);
+  f.ubar = D(L.ubar); f.Kbar = D(L.Kbar); f.Qbar = D(L.Qbar); f.fb2 = D(L.fb2); f.fbn = D(L.fbn);
+  f.wbar = D(L.wbar); f.w = D(L.w); f.w1 = D(L.w1); f.w2 = D(L.w2); f.tmp = D(L.tmp); f.H = D(L.H);
+  f.p1 = D(L.p1); f.p2 = D(L.p2); f.hn = D(L.hn); f.Linv = D(L.Linv); f.zs = D(L.zs); f.ys = D(L.ys);
+  f.Lbar = D(L.Lbar); f.Hbar = D(L.Hbar); f.scal = D(L.scal); f.theta = D(L.theta);
+  f.ud = X(L.ud); f.fd = X(L.fd); f.C = X(L.C); f.cp = X(L.cp); f.h = X(L.h); f.g = X(L.g); f.dcp = X(L.dcp);
+  f.om = X(L.om); f.k = X(L.k); f.rfac = X(L.rfac); f.q = X(L.q); f.Ms = X(L.Ms); f.dlnk = X(L.dlnk);
+  f.dkdM = X(L.dkdM); f.omg = X(L.omg); f.sc = X(L.sc); f.Cbar = X(L.Cbar); f.gbar = X(L.gbar);
+  f.ombar = X(L.ombar); f.Mbar = X(L.Mbar); f.ubd = X(L.ubd); f.fbd = X(L.fbd);
+  return f;
+}
+
+enum { SC_T = 0, SC_INVT, SC_S, SC_RHO, SC_CB, SC_SH, SC_LNRTP, SC_N };
+
+// Forward pass of f on the dual state ud -> fd, keeping the tape.
+__device__ void adj_rhs_fwd(const MechView& m, const AdjFrame& F, double p) {
+  const int ns = m.ns;
+  const Dual T = F.ud[ns];
+  const Dual invT = 1.0 / T;
+  const Dual lnT = dlog(T);
+  Dual S = dd(0.0);
+  for (int k = 0; k < ns; ++k) {
+    const double* c = (T.v < m.Tmid[k]) ? m.lo : m.hi;
+    const double a1 = c[k], a2 = c[ns + k], a3 = c[2 * ns + k], a4 = c[3 * ns + k], a5 = c[4 * ns + k];
+    const Dual cp = (((a5 * T + a4) * T + a3) * T + a2) * T + a1;
+    const Dual hp = ((c[8 * ns + k] * T + c[7 * ns + k]) * T + c[6 * ns + k]) * T + c[5 * ns + k];
+    const Dual hrt = hp * T + a1 + c[9 * ns + k] * invT;
+    const Dual sp = ((c[12 * ns + k] * T + c[11 * ns + k]) * T + c[10 * ns + k]) * T + a2;
+    const Dual sr = a1 * lnT + sp * T + c[13 * ns + k];
+    F.cp[k] = cp;
+    F.h[k] = hrt;
+    F.g[k] = hrt - sr;
+    F.dcp[k] = ((c[16 * ns + k] * T + c[15 * ns + k]) * T + c[14 * ns + k]) * T + a2;
+    S += F.ud[k] * m.invW[k];
+  }
+  F.h[ns] = dd(0.0);
+  F.g[ns] = dd(0.0);
+  const Dual rho = p / (R_GAS * T * S);
+  for (int k = 0; k < ns; ++k) F.C[k] = rho * F.ud[k] * m.invW[k];
+  F.C[ns] = dd(1.0);
+  for (int t = 0; t < m.ntb; ++t) {
+    Dual Mc = dd(0.0);
+    for (int k = 0; k < ns; ++k) Mc += m.eff[(size_t)t * ns + k] * F.C[k];
+    F.Ms[t] = Mc;
+  }
+  const Dual lnRTp = dlog(R_GAS * T / P_REF);
+  for (int j = 0; j < m.nr; ++j) {
+    const uint32_t sl = m.slots[j];
+    const int ra = sl & 255, rb = (sl >> 8) & 255, pa = (sl >> 16) & 255, pb = sl >> 24;
+    const int meta = m.meta[j];
+    const int kind = meta & 3;
+    const bool rev = (meta >> 2) & 1;
+    const int dnu = ((meta >> 4) & 15) - 4;
+    const int slot = meta >> 8;
+    Dual k = dexp(m.lnA[j] + m.bexp[j] * lnT - m.EaR[j] * invT, m.etab);
+    const Dual rfac = rev ? dexp(F.g[pa] + F.g[pb] - F.g[ra] - F.g[rb] + (double)dnu * lnRTp, m.etab) : dd(0.0);
+    Dual mfac = dd(1.0);
+    if (kind == 1) mfac = F.Ms[slot];
+    if (kind == 2) {
+      const double* fo = m.fo + (size_t)slot * FO_STRIDE;
+      const Dual Mc = F.Ms[slot];
+      const Dual dlnkinf = (m.bexp[j] + m.EaR[j] * invT) * invT;
+      const Dual k0 = dexp(fo[0] + fo[1] * lnT - fo[2] * invT, m.etab);
+      const Dual dlnk0 = (fo[1] + fo[2] * invT) * invT;
+      Dual Pr = k0 * Mc / k;
+      if (!(Pr.v > 1e-300)) Pr = dd(1e-300);
+      const double a = fo[3];
+      const Dual e3 = dexp(-1.0 * T * fo[4], m.etab), e1 = dexp(-1.0 * T * fo[5], m.etab);
+      const Dual e2 = fo[6] > 0.0 ? dexp(-fo[6] * invT, m.etab) : dd(0.0);
+      const Dual Fc = (1.0 - a) * e3 + a * e1 + e2;
+      const Dual lFc = dlog10(Fc);
+      const Dual cc = -0.4 - 0.67 * lFc;
+      const Dual nn = 0.75 - 1.27 * lFc;
+      const Dual x = dlog10(Pr) + cc;
+      const Dual D = nn - 0.14 * x;
+      const Dual f1 = x / D;
+      const Dual den = 1.0 + f1 * f1;
+      const Dual lF = lFc / den;
+      const Dual Fb = dexp(lF * 2.302585092994046, m.etab);
+      const Dual onePr = 1.0 + Pr;
+      const Dual dlF_dL = -1.0 * lFc * 2.0 * f1 / (den * den) * nn / (D * D);
+      const Dual df1 = (-0.67 * D + 1.1762 * x) / (D * D);
+      const Dual dlF_dlFc = 1.0 / den - lFc * 2.0 * f1 / (den * den) * df1;
+      const Dual dFc = -(1.0 - a) * fo[4] * e3 - a * fo[5] * e1 + (fo[6] > 0.0 ? fo[6] * invT * invT * e2 : dd(0.0));
+      const Dual gg = 1.0 / onePr + dlF_dL;
+      F.dlnk[slot] = dlnkinf + gg * (dlnk0 - dlnkinf) + dlF_dlFc * dFc / Fc;
+      F.dkdM[slot] = k0 * Fb / onePr * gg;
+      F.omg[slot] = 1.0 - gg;
+      k = k * Pr / onePr * Fb;
+    }
+    const Dual Pf = F.C[ra] * F.C[rb];
+    const Dual Pb = F.C[pa] * F.C[pb];
+    F.k[j] = k;
+    F.rfac[j] = rfac;
+    F.q[j] = mfac * (k * Pf - k * rfac * Pb);
+  }
+  Dual Sh = dd(0.0), cb = dd(0.0);
+  for (int k = 0; k < ns; ++k) {
+    Dual om = dd(0.0);
+    for (int e = m.csr_ptr[k]; e < m.csr_ptr[k + 1]; ++e) om += m.csr_nu[e] * F.q[m.csr_j[e]];
+    F.om[k] = om;
+    F.fd[k] = m.W[k] * om / rho;
+    Sh += F.h[k] * om;
+    cb += F.ud[k] * F.cp[k] * m.invW[k];
+  }
+  F.fd[ns] = -1.0 * T * Sh / (rho * cb);
+  F.sc[SC_T] = T;
+  F.sc[SC_INVT] = invT;
+  F.sc[SC_S] = S;
+  F.sc[SC_RHO] = rho;
+  F.sc[SC_CB] = cb;
+  F.sc[SC_SH] = Sh;
+  F.sc[SC_LNRTP] = lnRTp;
+}
+
+// Reverse pass: ubd = J^T fbd on the tape of the last adj_rhs_fwd; the ln A
+// gradient is added to F.theta from the values (tangent = false) or from the
+// tangents (tangent = true) of the dual adjoint.
+__device__ void adj_rhs_rev(const MechView& m, const AdjFrame& F, bool tangent) {
+  const int ns = m.ns;
+  const Dual T = F.sc[SC_T], invT = F.sc[SC_INVT], S = F.sc[SC_S], rho = F.sc[SC_RHO];
+  const Dual cb = F.sc[SC_CB], Sh = F.sc[SC_SH];
+  const Dual fTb = F.fbd[ns];
+  const Dual rcb = rho * cb;
+  Dual Tbar = -1.0 * Sh / rcb * fTb;
+  const Dual Shbar = -1.0 * T / rcb * fTb;
+  Dual rhobar = T * Sh / (rho * rcb) * fTb;
+  const Dual cbbar = T * Sh / (rcb * cb) * fTb;
+  for (int k = 0; k < ns; ++k) {
+    F.ombar[k] = m.W[k] / rho * F.fbd[k] + F.h[k] * Shbar;
+    rhobar -= m.W[k] * F.om[k] / (rho * rho) * F.fbd[k];
+    F.Cbar[k] = dd(0.0);
+    F.gbar[k] = dd(0.0);
+  }
+  F.ombar[ns] = dd(0.0);
+  F.Cbar[ns] = dd(0.0);
+  F.gbar[ns] = dd(0.0);
+  for (int t = 0; t < m.ntb; ++t) F.Mbar[t] = dd(0.0);
+  const Dual lnRTp_unused = F.sc[SC_LNRTP];
+  (void)lnRTp_unused;
+  for (int j = 0; j < m.nr; ++j) {
+    const uint32_t sl = m.slots[j];
+    const int ra = sl & 255, rb = (sl >> 8) & 255, pa = (sl >> 16) & 255, pb = sl >> 24;
+    const int meta = m.meta[j];
+    const int kind = meta & 3;
+    const bool rev = (meta >> 2) & 1;
+    const int dnu = ((meta >> 4) & 15) - 4;
+    const int slot = meta >> 8;
+    const Dual qbar = F.ombar[pa] + F.ombar[pb] - F.ombar[ra] - F.ombar[rb];
+    const Dual k = F.k[j], rfac = F.rfac[j];
+    const Dual Pf = F.C[ra] * F.C[rb];
+    const Dual Pb = F.C[pa] * F.C[pb];
+    const Dual mfac = kind == 1 ? F.Ms[slot] : dd(1.0);
+    const Dual kr = k * rfac;
+    const Dual qm = qbar * mfac;
+    const Dual kbar = qm * (Pf - rfac * Pb);
+    const Dual Pfbar = qm * k;
+    const Dual Pbbar = -1.0 * qm * kr;
+    if (kind == 1) F.Mbar[slot] += qbar * (k * Pf - kr * Pb);
+    F.Cbar[ra] += Pfbar * F.C[rb];
+    F.Cbar[rb] += Pfbar * F.C[ra];
+    F.Cbar[pa] += Pbbar * F.C[pb];
+    F.Cbar[pb] += Pbbar * F.C[pa];
+    if (rev) {
+      const Dual drf = rfac * (-1.0 * qm * k * Pb);  // rfac * rfac_bar
+      F.gbar[pa] += drf;
+      F.gbar[pb] += drf;
+      F.gbar[ra] -= drf;
+      F.gbar[rb] -= drf;
+      Tbar += (double)dnu * drf * invT;
+    }
+    const Dual kk = k * kbar;
+    Dual th;
+    if (kind == 2) {
+      Tbar += kk * F.dlnk[slot];
+      F.Mbar[slot] += kbar * F.dkdM[slot];
+      th = kk * F.omg[slot];
+    } else {
+      Tbar += kk * ((m.bexp[j] + m.EaR[j] * invT) * invT);
+      th = kk;
+    }
+    F.theta[j] += tangent ? th.t : th.v;
+  }
+  for (int t = 0; t < m.ntb; ++t)
+    for (int k = 0; k < ns; ++k) F.Cbar[k] += m.eff[(size_t)t * ns + k] * F.Mbar[t];
+  for (int k = 0; k < ns; ++k) rhobar += F.ud[k] * m.invW[k] * F.Cbar[k];
+  Tbar -= rho * invT * rhobar;
+  const Dual Sbar = -1.0 * rho / S * rhobar;
+  for (int k = 0; k < ns; ++k) {
+    const Dual Yb = F.cp[k] * m.invW[k] * cbbar + rho * m.invW[k] * F.Cbar[k] + Sbar * m.invW[k];
+    F.ubd[k] = Yb;
+    const Dual cpbar = F.ud[k] * m.invW[k] * cbbar;
+    const Dual hbar = F.om[k] * Shbar;
+    Tbar += cpbar * F.dcp[k] + hbar * (F.cp[k] - F.h[k]) * invT - F.gbar[k] * F.h[k] * invT;
+  }
+  F.ubd[ns] = Tbar;
+}
+
+}  // namespace rk
+
+namespace rk {
+
+// Explicit inverse of I - h gamma H (m x m) by Gauss-Jordan with partial pivoting.
+__device__ inline void adj_small_inverse(const AdjFrame& F, int md, double h) {
+  double A[MAXM][MAXM], B[MAXM][MAXM];
+  for (int r = 0; r < md; ++r)
+    for (int c = 0; c < md; ++c) {
+      A[r][c] = (r == c ? 1.0 : 0.0) - h * GAM * F.H[r * MAXM + c];
+      B[r][c] = (r == c ? 1.0 : 0.0);
+    }
+  for (int c = 0; c < md; ++c) {
+    int pr = c;
+    for (int r = c + 1; r < md; ++r)
+      if (fabs(A[r][c]) > fabs(A[pr][c])) pr = r;
+    if (pr != c)
+      for (int j = 0; j < md; ++j) {
+        double t = A[c][j]; A[c][j] = A[pr][j]; A[pr][j] = t;
+        t = B[c][j]; B[c][j] = B[pr][j]; B[pr][j] = t;
+      }
+    const double inv = 1.0 / A[c][c];
+    for (int j = 0; j < md; ++j) {
+      A[c][j] *= inv;
+      B[c][j] *= inv;
+    }
+    for (int r = 0; r < md; ++r) {
+      if (r == c) continue;
+      const double f = A[r][c];
+      for (int j = 0; j < md; ++j) {
+        A[r][j] = fma(-f, A[c][j], A[r][j]);
+        B[r][j] = fma(-f, B[c][j], B[r][j]);
+      }
+    }
+  }
+  for (int r = 0; r < md; ++r)
+    for (int c = 0; c < md; ++c) F.Linv[r * MAXM + c] = B[r][c];
+}
+
+__device__ inline void adj_load_ud(const AdjFrame& F, int N, const Col<double>& x, const Col<double>* tan,
+                                   int64_t toff) {
+  for (int e = 0; e < N; ++e) F.ud[e] = Dual{x[e], tan ? (*tan)[toff + e] : 0.0};
+}
+
+// Forward recomputation and reverse sweep of one fixed ROK4E step of size h
+// from F.u; on entry F.ubar holds the adjoint of the step's result, on exit
+// that of F.u; the ln A gradient accumulates in F.theta.
+__device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double h, int M) {
+  const int ns = m.ns, N = ns + 1;
+  constexpr double g21 = G21 / GAM, g31 = G31 / GAM, g32 = G32 / GAM;
+  constexpr double g41 = G41 / GAM, g42 = G42 / GAM, g43 = G43 / GAM;
+  const double gij[4][3] = {{0, 0, 0}, {g21, 0, 0}, {g31, g32, 0}, {g41, g42, g43}};
+  const double bj[4] = {B1, B2, B3, B4};
+  if (M > N) M = N;
+  // ---------------------------------------------------------------- forward
+  adj_load_ud(F, N, F.u, nullptr, 0);
+  adj_rhs_fwd(m, F, p);
+  double beta2 = 0.0;
+  for (int e = 0; e < N; ++e) {
+    F.fn[e] = F.fd[e].v;
+    beta2 = fma(F.fn[e], F.fn[e], beta2);
+  }
+  const double beta = sqrt(beta2);
+  for (int i = 0; i < MAXM * MAXM; ++i) F.H[i] = 0.0;
+  int md = 0;
+  if (M > 0 && beta > 0.0 && isfinite(beta)) {
+    md = M;
+    for (int e = 0; e < N; ++e) F.Q[e] = F.fn[e] / beta;
+    for (int j = 0; j < M; ++j) {
+      adj_load_ud(F, N, F.u, &F.Q, (int64_t)j * N);
+      adj_rhs_fwd(m, F, p);
+      double w0 = 0.0;
+      for (int e = 0; e < N; ++e) {
+        F.w[e] = F.fd[e].t;
+        w0 = fma(F.w[e], F.w[e], w0);
+      }
+      w0 = sqrt(w0);
+      for (int pass = 0; pass < 2; ++pass) {
+        double pc[MAXM];
+        for (int i = 0; i <= j; ++i) {
+          double d = 0.0;
+          for (int e = 0; e < N; ++e) d = fma(F.Q[(int64_t)i * N + e], F.w[e], d);
+          pc[i] = d;
+        }
+        for (int e = 0; e < N; ++e) {
+          double we = F.w[e];
+          for (int i = 0; i <= j; ++i) we = fma(-pc[i], F.Q[(int64_t)i * N + e], we);
+          F.w[e] = we;
+        }
+        for (int i = 0; i <= j; ++i) {
+          F.H[i * MAXM + j] += pc[i];
+          (pass == 0 ? F.p1 : F.p2)[j * MAXM + i] = pc[i];
+        }
+      }
+      double hn = 0.0;
+      for (int e = 0; e < N; ++e) hn = fma(F.w[e], F.w[e], hn);
+      hn = sqrt(hn);
+      if (j + 1 == M) break;
+      if (hn <= BREAKDOWN_TOL * w0 || hn == 0.0) {
+        md = j + 1;
+        break;
+      }
+      F.H[(j + 1) * MAXM + j] = hn;
+      F.hn[j] = hn;
+      for (int e = 0; e < N; ++e) F.Q[(int64_t)(j + 1) * N + e] = F.w[e] / hn;
+    }
+  }
+  if (md > 0) adj_small_inverse(F, md, h);
+  // stages
+  for (int i = 0; i < 4; ++i) {
+    const Col<double> Ki{F.K.p + (int64_t)i * N * F.K.s, F.K.s};
+    const Col<double> Fi{F.F.p + (int64_t)i * N * F.F.s, F.F.s};
+    if (i == 1 || i == 2) {
+      const Col<double>& arg = (i == 1) ? F.arg1 : F.arg2;
+      for (int e = 0; e < N; ++e) {
+        const double acc = (i == 1) ? A21 * F.K[e] : fma(A32, F.K[(int64_t)N + e], A31 * F.K[e]);
+        arg[e] = F.u[e] + h * acc;
+      }
+      adj_load_ud(F, N, arg, nullptr, 0);
+      adj_rhs_fwd(m, F, p);
+      for (int e = 0; e < N; ++e) F.tmp[e] = F.fd[e].v;  // f_i (kept for stage 4)
+    }
+    double z[MAXM];
+    for (int l = 0; l < MAXM; ++l) z[l] = 0.0;
+    for (int e = 0; e < N; ++e) {
+      double Ge = 0.0;
+      for (int j = 0; j < i; ++j) Ge = fma(gij[i][j], F.K[(int64_t)j * N + e], Ge);
+      const double fe = (i == 0) ? F.fn[e] : F.tmp[e];
+      Fi[e] = fe + Ge;
+      F.w2[e] = Ge;
+      for (int l = 0; l < md; ++l) z[l] = fma(F.Q[(int64_t)l * N + e], Fi[e], z[l]);
+    }
+    double y[MAXM];
+    for (int r = 0; r < md; ++r) {
+      double acc = 0.0;
+      for (int c = 0; c < md; ++c) acc = fma(F.Linv[r * MAXM + c], z[c], acc);
+      y[r] = acc;
+    }
+    for (int l = 0; l < md; ++l) {
+      F.zs[i * MAXM + l] = z[l];
+      F.ys[i * MAXM + l] = y[l];
+    }
+    for (int e = 0; e < N; ++e) {
+      double acc = 0.0;
+      for (int l = 0; l < md; ++l) acc = fma(F.Q[(int64_t)l * N + e], z[l] - y[l], acc);
+      Ki[e] = (Fi[e] - acc) - F.w2[e];
+    }
+  }
+  // ---------------------------------------------------------------- reverse
+  for (int i = 0; i < 4; ++i)
+    for (int e = 0; e < N; ++e) F.Kbar[(int64_t)i * N + e] = h * bj[i] * F.ubar[e];
+  for (int64_t e = 0; e < (int64_t)md * N; ++e) F.Qbar[e] = 0.0;
+  for (int i = 0; i < MAXM * MAXM; ++i) F.Lbar[i] = 0.0;
+  for (int e = 0; e < N; ++e) {
+    F.fb2[e] = 0.0;
+    F.fbn[e] = 0.0;
+  }
+  for (int i = 3; i >= 0; --i) {
+    const Col<double> Kb{F.Kbar.p + (int64_t)i * N * F.Kbar.s, F.Kbar.s};
+    const Col<double> Fi{F.F.p + (int64_t)i * N * F.F.s, F.F.s};
+    double dbar[MAXM], zbar[MAXM];
+    for (int l = 0; l < md; ++l) {
+      double d = 0.0;
+      for (int e = 0; e < N; ++e) d = fma(F.Q[(int64_t)l * N + e], Kb[e], d);
+      dbar[l] = -d;
+    }
+    for (int r = 0; r < md; ++r) {
+      double a = 0.0;  // a = L^-T ybar with ybar = -dbar
+      for (int c = 0; c < md; ++c) a = fma(F.Linv[c * MAXM + r], -dbar[c], a);
+      zbar[r] = dbar[r] + a;
+      for (int c = 0; c < md; ++c) F.Lbar[r * MAXM + c] -= a * F.ys[i * MAXM + c];
+    }
+    for (int l = 0; l < md; ++l) {
+      const double dl = F.zs[i * MAXM + l] - F.ys[i * MAXM + l];
+      for (int e = 0; e < N; ++e) {
+        double qb = F.Qbar[(int64_t)l * N + e];
+        qb = fma(-dl, Kb[e], qb);
+        qb = fma(zbar[l], Fi[e], qb);
+        F.Qbar[(int64_t)l * N + e] = qb;
+      }
+    }
+    for (int e = 0; e < N; ++e) {
+      double Fb = Kb[e];
+      for (int l = 0; l < md; ++l) Fb = fma(F.Q[(int64_t)l * N + e], zbar[l], Fb);
+      const double Gb = Fb - Kb[e];
+      for (int j = 0; j < i; ++j) F.Kbar[(int64_t)j * N + e] += gij[i][j] * Gb;
+      F.w[e] = Fb;  // f_bar of this stage
+    }
+    if (i == 3) {
+      for (int e = 0; e < N; ++e) F.fb2[e] += F.w[e];
+    } else if (i == 2 || i == 1) {
+      const Col<double>& arg = (i == 1) ? F.arg1 : F.arg2;
+      if (i == 2)
+        for (int e = 0; e < N; ++e) F.fb2[e] += F.w[e];
+      adj_load_ud(F, N, arg, nullptr, 0);
+      adj_rhs_fwd(m, F, p);
+      for (int e = 0; e < N; ++e) F.fbd[e] = Dual{i == 2 ? F.fb2[e] : F.w[e], 0.0};
+      adj_rhs_rev(m, F, false);
+      for (int e = 0; e < N; ++e) {
+        const double ab = F.ubd[e].v;
+        F.ubar[e] += ab;
+        if (i == 2) {
+          F.Kbar[e] += h * A31 * ab;
+          F.Kbar[(int64_t)N + e] += h * A32 * ab;
+        } else {
+          F.Kbar[e] += h * A21 * ab;
+        }
+      }
+    } else {
+      for (int e = 0; e < N; ++e) F.fbn[e] += F.w[e];
+    }
+  }
+  for (int i = 0; i < MAXM * MAXM; ++i) F.Hbar[i] = -h * GAM * F.Lbar[i];
+  // Arnoldi, last column first
+  for (int j = md - 1; j >= 0; --j) {
+    adj_load_ud(F, N, F.u, &F.Q, (int64_t)j * N);
+    adj_rhs_fwd(m, F, p);
+    for (int e = 0; e < N; ++e) F.w[e] = F.fd[e].t;
+    for (int e = 0; e < N; ++e) {
+      double a = F.w[e];
+      for (int i = 0; i <= j; ++i) a = fma(-F.p1[j * MAXM + i], F.Q[(int64_t)i * N + e], a);
+      F.w1[e] = a;
+      double b = a;
+      for (int i = 0; i <= j; ++i) b = fma(-F.p2[j * MAXM + i], F.Q[(int64_t)i * N + e], b);
+      F.w2[e] = b;
+    }
+    // w2 -> (h_{j+1,j}, q_{j+1})
+    if (j + 1 < md) {
+      const double eta = F.hn[j];
+      double qw = 0.0;
+      for (int e = 0; e < N; ++e) qw = fma(F.Qbar[(int64_t)(j + 1) * N + e], F.w2[e], qw);
+      const double c = F.Hbar[(j + 1) * MAXM + j] - qw / (eta * eta);
+      for (int e = 0; e < N; ++e) F.wbar[e] = (F.Qbar[(int64_t)(j + 1) * N + e] + c * F.w2[e]) / eta;
+    } else {
+      for (int e = 0; e < N; ++e) F.wbar[e] = 0.0;
+    }
+    double pb2[MAXM], pb1[MAXM];
+    for (int i = 0; i <= j; ++i) {  // second pass
+      double d = 0.0;
+      for (int e = 0; e < N; ++e) d = fma(F.Q[(int64_t)i * N + e], F.wbar[e], d);
+      pb2[i] = F.Hbar[i * MAXM + j] - d;
+    }
+    for (int e = 0; e < N; ++e) {
+      double wb = F.wbar[e];
+      for (int i = 0; i <= j; ++i) {
+        F.Qbar[(int64_t)i * N + e] += -F.p2[j * MAXM + i] * F.wbar[e] + pb2[i] * F.w1[e];
+        wb = fma(pb2[i], F.Q[(int64_t)i * N + e], wb);
+      }
+      F.tmp[e] = wb;  // w1_bar
+    }
+    for (int i = 0; i <= j; ++i) {  // first pass
+      double d = 0.0;
+      for (int e = 0; e < N; ++e) d = fma(F.Q[(int64_t)i * N + e], F.tmp[e], d);
+      pb1[i] = F.Hbar[i * MAXM + j] - d;
+    }
+    for (int e = 0; e < N; ++e) {
+      double wb = F.tmp[e];
+      for (int i = 0; i <= j; ++i) {
+        F.Qbar[(int64_t)i * N + e] += -F.p1[j * MAXM + i] * F.tmp[e] + pb1[i] * F.w[e];
+        wb = fma(pb1[i], F.Q[(int64_t)i * N + e], wb);
+      }
+      F.wbar[e] = wb;
+    }
+    // w = J(u) q_j: J^T w_bar into q_bar_j, second-order terms into u_bar and theta
+    for (int e = 0; e < N; ++e) F.fbd[e] = Dual{F.wbar[e], 0.0};
+    adj_rhs_rev(m, F, true);
+    for (int e = 0; e < N; ++e) {
+      F.Qbar[(int64_t)j * N + e] += F.ubd[e].v;
+      F.ubar[e] += F.ubd[e].t;
+    }
+  }
+  // q_1 = f_n / |f_n|
+  if (md > 0) {
+    double qf = 0.0;
+    for (int e = 0; e < N; ++e) qf = fma(F.Qbar[e], F.fn[e], qf);
+    for (int e = 0; e < N; ++e) F.fbn[e] += F.Qbar[e] / beta - qf * F.fn[e] / (beta * beta * beta);
+  }
+  // f_n = f(u)
+  adj_load_ud(F, N, F.u, nullptr, 0);
+  adj_rhs_fwd(m, F, p);
+  for (int e = 0; e < N; ++e) F.fbd[e] = Dual{F.fbn[e], 0.0};
+  adj_rhs_rev(m, F, false);
+  for (int e = 0; e < N; ++e) F.ubar[e] += F.ubd[e].v;
+}
+
+}  // namespace rk

@@ -42,6 +42,7 @@ struct MechLayout {
   int64_t off_csr_ptr = 0, off_csr_j = 0;
   // FP32 copies read by the reduced-precision Jacobian-vector product
   int64_t off_Wf = 0, off_invWf = 0, off_bf = 0, off_EaRf = 0, off_efff = 0, off_csr_nuf = 0;
+  int64_t off_perm = 0;  // int32 per packed reaction: its index in the input description
   int64_t bytes = 0;
 };
 

@@ -187,6 +187,7 @@ bool pack_mechanism(const void* vdesc, HostMech* out, std::string* err) {
   L.off_EaRf = take(4 * (int64_t)nr);
   L.off_efff = take(4 * (int64_t)L.ntb * ns);
   L.off_csr_nuf = take(4 * (int64_t)nnz);
+  L.off_perm = take(4 * (int64_t)nr);
   L.bytes = align16(off);
 
   std::vector<unsigned char> buf((size_t)L.bytes, 0);
@@ -276,6 +277,7 @@ bool pack_mechanism(const void* vdesc, HostMech* out, std::string* err) {
   }
   for (int i = 0; i < L.ntb * ns; ++i) F(L.off_efff)[i] = (float)D(L.off_eff)[i];
   for (int i = 0; i < nnz; ++i) F(L.off_csr_nuf)[i] = (float)D(L.off_csr_nu)[i];
+  for (int r = 0; r < nr; ++r) I(L.off_perm)[r] = perm[r];
 
   out->L = L;
   out->packed.swap(buf);

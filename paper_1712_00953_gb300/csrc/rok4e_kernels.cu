@@ -137,6 +137,7 @@ struct MechView {
   const uint32_t* slots;
   const int32_t *meta, *csr_ptr, *csr_j;
   const float *Wf, *invWf, *bf, *EaRf, *efff, *csr_nuf;  // FP32 copies
+  const int32_t* perm;  // input index of each packed reaction
 };
 
 __host__ __device__ inline MechView make_view(const unsigned char* base, const MechLayout& L) {
@@ -166,6 +167,7 @@ __host__ __device__ inline MechView make_view(const unsigned char* base, const M
   m.EaRf = reinterpret_cast<const float*>(base + L.off_EaRf);
   m.efff = reinterpret_cast<const float*>(base + L.off_efff);
   m.csr_nuf = reinterpret_cast<const float*>(base + L.off_csr_nuf);
+  m.perm = reinterpret_cast<const int32_t*>(base + L.off_perm);
   return m;
 }
 
@@ -1281,6 +1283,66 @@ __global__ void __launch_bounds__(512) rok4e_integrate_kernel(IntegrateParams P)
   }
 }
 
+}  // namespace rk
+
+#include "adjoint.cuh"
+
+namespace rk {
+
+// ------------------------------------------------------------ adjoint kernels
+struct AdjointParams {
+  const unsigned char* mech;
+  MechLayout L;
+  AdjLayout A;
+  const double* ckpt;        // [(nsteps + 1) x ncell x N] states at the start of every step
+  const double* ubar_final;  // [ncell x N] dL/du(t_end)
+  double* grad_u0;           // [ncell x N] dL/du(0), or null
+  double* wsd;
+  Dual* wsD;
+  int64_t ncell;
+  double p, h;
+  int nsteps, M;
+};
+
+__global__ void __launch_bounds__(128) rok4e_adjoint_kernel(AdjointParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  load_exp_table(reinterpret_cast<double*>(smem));
+  load_mech(smem + EXP_TAB_BYTES, P.mech, P.L.bytes);
+  __syncthreads();
+  MechView m = make_view(smem + EXP_TAB_BYTES, P.L);
+  m.etab = reinterpret_cast<const double*>(smem);
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= P.ncell) return;
+  const AdjFrame F = adj_frame(P.wsd, P.wsD, P.A, P.ncell, c);
+  const int N = m.ns + 1;
+  for (int e = 0; e < N; ++e) F.ubar[e] = P.ubar_final[c * N + e];
+  for (int j = 0; j < m.nr; ++j) F.theta[j] = 0.0;
+  for (int n = P.nsteps - 1; n >= 0; --n) {
+    const double* un = P.ckpt + ((int64_t)n * P.ncell + c) * N;
+    for (int e = 0; e < N; ++e) F.u[e] = un[e];
+    adj_step(m, F, P.p, P.h, P.M);
+  }
+  if (P.grad_u0)
+    for (int e = 0; e < N; ++e) P.grad_u0[c * N + e] = F.ubar[e];
+}
+
+// grad[perm[r]] = sum over cells of theta[r][cell]; one block per reaction
+// with a fixed-order tree, so the sum does not depend on scheduling.
+__global__ void __launch_bounds__(256) adjoint_reduce_kernel(const double* __restrict__ theta, int64_t ncell,
+                                                             const int32_t* __restrict__ perm, double* grad) {
+  __shared__ double sh[256];
+  const int r = blockIdx.x;
+  double acc = 0.0;
+  for (int64_t c = threadIdx.x; c < ncell; c += blockDim.x) acc += theta[(int64_t)r * ncell + c];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) grad[perm[r]] = sh[0];
+}
+
 // One group per cell: f(u) + src, or J(u) v.
 struct PointParams {
   const unsigned char* mech;
@@ -1480,7 +1542,7 @@ int device_props(int* n_sm, size_t* smem_optin) {
 
 template <int G, typename K>
 int plan_for(K kernel, const rk_mech* mech, const SlotLayout& S, int want_cells, int64_t ncell, bool persistent,
-             LaunchPlan* plan) {
+             LaunchPlan* plan, int want_blocks_per_sm = 0) {
   int n_sm = 0;
   size_t smem_max = 0;
   int rc = device_props(&n_sm, &smem_max);
@@ -1506,6 +1568,7 @@ int plan_for(K kernel, const rk_mech* mech, const SlotLayout& S, int want_cells,
     if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   }
   if (per_sm == 0) return set_error(RK_E_UNSUPPORTED, "integration kernel cannot be resident on an SM");
+  if (want_blocks_per_sm > 0 && want_blocks_per_sm < per_sm) per_sm = want_blocks_per_sm;
   plan->G = G;
   plan->cells_per_block = cells;
   plan->smem = smem;
@@ -1593,7 +1656,10 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   P.order = nullptr;
   cudaError_t e = cudaMemsetAsync(wsb, 0, 768, stream);  // counter, histogram, cursors
   if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
-  if (h_cell && ncell > 1 && !(o.fixed_h > 0.0) && ncell < (int64_t)INT32_MAX) {
+  if (o.queue_order < 0 || o.queue_order > 2) return set_error(RK_E_INVALID_ARGUMENT, "queue_order must be 0..2");
+  const int order = o.queue_order == 0 ? (h_cell ? 2 : 1) : o.queue_order;
+  if (order == 2 && !h_cell) return set_error(RK_E_INVALID_ARGUMENT, "queue_order 2 needs h_cell");
+  if (order == 2 && ncell > 1 && !(o.fixed_h > 0.0) && ncell < (int64_t)INT32_MAX) {
     unsigned* hist = reinterpret_cast<unsigned*>(wsb + 256);
     unsigned* cursor = reinterpret_cast<unsigned*>(wsb + 512);
     int32_t* perm = reinterpret_cast<int32_t*>(wsb + 768);
@@ -1614,7 +1680,8 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   }
 #define RK_LAUNCH(GG, MX)                                                                          \
   do {                                                                                             \
-    rc = plan_for<GG>(rok4e_integrate_kernel<GG, MX>, mech, P.S, o.cells_per_block, ncell, true, &plan); \
+    rc = plan_for<GG>(rok4e_integrate_kernel<GG, MX>, mech, P.S, o.cells_per_block, ncell, true, &plan, \
+                      o.blocks_per_sm);                                                            \
     if (rc) return rc;                                                                             \
     rok4e_integrate_kernel<GG, MX><<<plan.blocks, plan.cells_per_block * GG, plan.smem, stream>>>(P); \
   } while (0)
@@ -1938,6 +2005,122 @@ int rk_simpler_split_step_noalloc(const rk_mech* mech, double* U, double* h_cell
   if (rc) return rc;
   return rk_simpler_split_step(mech, U, h_cell, npts, p, dt, D, dx, rtol, atol, krylov_dim, opts, stats, scratch,
                                (size_t)RK_NOALLOC_SCRATCH_BYTES, stream);
+}
+
+// ---- fixed-step forward with checkpoints and its discrete adjoint ----------
+static AdjLayout make_adj_layout(const MechLayout& L, int M) {
+  AdjLayout A;
+  A.N = L.ns + 1;
+  A.ns = L.ns;
+  A.nr = L.nr;
+  A.ntb = L.ntb;
+  A.M = M;
+  const int N = A.N, ns1 = L.ns + 1, nr = L.nr > 0 ? L.nr : 1, ntb = L.ntb > 0 ? L.ntb : 1;
+  int r = 0;
+  auto take = [&](int n) {
+    const int o = r;
+    r += n;
+    return o;
+  };
+  A.u = take(N); A.fn = take(N); A.Q = take(M * N); A.K = take(4 * N); A.F = take(4 * N);
+  A.arg1 = take(N); A.arg2 = take(N); A.ubar = take(N); A.Kbar = take(4 * N); A.Qbar = take(M * N);
+  A.fb2 = take(N); A.fbn = take(N); A.wbar = take(N); A.w = take(N); A.w1 = take(N); A.w2 = take(N);
+  A.tmp = take(N); A.H = take(MAXM * MAXM); A.p1 = take(MAXM * MAXM); A.p2 = take(MAXM * MAXM);
+  A.hn = take(MAXM); A.Linv = take(MAXM * MAXM); A.zs = take(4 * MAXM); A.ys = take(4 * MAXM);
+  A.Lbar = take(MAXM * MAXM); A.Hbar = take(MAXM * MAXM); A.scal = take(8); A.theta = take(nr);
+  A.rows_d = r;
+  r = 0;
+  A.ud = take(N); A.fd = take(N); A.C = take(ns1); A.cp = take(ns1); A.h = take(ns1); A.g = take(ns1);
+  A.dcp = take(ns1); A.om = take(ns1); A.k = take(nr); A.rfac = take(nr); A.q = take(nr); A.Ms = take(ntb);
+  A.dlnk = take(ntb); A.dkdM = take(ntb); A.omg = take(ntb); A.sc = take(SC_N); A.Cbar = take(ns1);
+  A.gbar = take(ns1); A.ombar = take(ns1); A.Mbar = take(ntb); A.ubd = take(N); A.fbd = take(N);
+  A.rows_D = r;
+  return A;
+}
+
+size_t rk_rok4e_adjoint_workspace_size(const rk_mech* mech, int64_t ncell, int32_t krylov_dim) {
+  if (!mech || ncell < 0 || krylov_dim < 1 || krylov_dim > RK_MAX_KRYLOV) return 0;
+  const int N = mech->host.L.ns + 1;
+  const AdjLayout A = make_adj_layout(mech->host.L, krylov_dim > N ? N : krylov_dim);
+  const size_t nd = (size_t)A.rows_d * (size_t)ncell * sizeof(double);
+  return ((nd + 255) & ~(size_t)255) + (size_t)A.rows_D * (size_t)ncell * sizeof(Dual) + 256;
+}
+
+int rk_rok4e_fixed_steps(const rk_mech* mech, double* Y, int64_t ncell, double p, double h, int32_t nsteps,
+                         int32_t krylov_dim, double* checkpoints, void* workspace, size_t workspace_bytes,
+                         void* stream) {
+  int rc = check_mech(mech);
+  if (rc) return rc;
+  if (ncell < 0 || nsteps < 0) return set_error(RK_E_INVALID_ARGUMENT, "ncell and nsteps must be >= 0");
+  if (ncell == 0 || nsteps == 0) return RK_OK;
+  if (!Y) return set_error(RK_E_INVALID_ARGUMENT, "null state array");
+  if (!(h > 0.0)) return set_error(RK_E_INVALID_ARGUMENT, "h must be > 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)ncell * (size_t)(mech->host.L.ns + 1) * sizeof(double);
+  rk_opts o;
+  memset(&o, 0, sizeof(o));
+  o.fixed_h = h;
+  for (int n = 0; n < nsteps; ++n) {
+    if (checkpoints) {
+      cudaError_t e = cudaMemcpyAsync((char*)checkpoints + (size_t)n * bytes, Y, bytes, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync");
+    }
+    rc = integrate_impl(mech, Y, nullptr, nullptr, ncell, p, h, 1.0, 1.0, krylov_dim, &o, nullptr, workspace,
+                        workspace_bytes, st);
+    if (rc) return rc;
+  }
+  if (checkpoints) {
+    cudaError_t e = cudaMemcpyAsync((char*)checkpoints + (size_t)nsteps * bytes, Y, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync");
+  }
+  return RK_OK;
+}
+
+int rk_rok4e_adjoint(const rk_mech* mech, const double* checkpoints, const double* ubar, int64_t ncell, double p,
+                     double h, int32_t nsteps, int32_t krylov_dim, double* grad_lnA, double* grad_u0,
+                     void* workspace, size_t workspace_bytes, void* stream) {
+  int rc = check_mech(mech);
+  if (rc) return rc;
+  if (ncell < 0 || nsteps < 0) return set_error(RK_E_INVALID_ARGUMENT, "ncell and nsteps must be >= 0");
+  if (krylov_dim < 1 || krylov_dim > RK_MAX_KRYLOV) return set_error(RK_E_INVALID_ARGUMENT, "krylov_dim outside 1..8");
+  if (!checkpoints || !ubar || !grad_lnA) return set_error(RK_E_INVALID_ARGUMENT, "null array");
+  if (!(h > 0.0) || !(p > 0.0)) return set_error(RK_E_INVALID_ARGUMENT, "need h > 0 and p > 0");
+  const size_t need = rk_rok4e_adjoint_workspace_size(mech, ncell, krylov_dim);
+  if (!workspace || workspace_bytes < need) return set_error(RK_E_WORKSPACE, "adjoint workspace too small");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = mech->host.L.ns + 1;
+  AdjointParams P;
+  P.mech = mech->dev;
+  P.L = mech->host.L;
+  P.A = make_adj_layout(mech->host.L, krylov_dim > N ? N : krylov_dim);
+  P.ckpt = checkpoints;
+  P.ubar_final = ubar;
+  P.grad_u0 = grad_u0;
+  P.wsd = static_cast<double*>(workspace);
+  const size_t nd = ((size_t)P.A.rows_d * (size_t)ncell * sizeof(double) + 255) & ~(size_t)255;
+  P.wsD = reinterpret_cast<Dual*>(static_cast<unsigned char*>(workspace) + nd);
+  P.ncell = ncell;
+  P.p = p;
+  P.h = h;
+  P.nsteps = nsteps;
+  P.M = krylov_dim > N ? N : krylov_dim;
+  const int nr = mech->host.L.nr;
+  if (ncell == 0 || nsteps == 0 || nr == 0) {
+    cudaError_t e = cudaMemsetAsync(grad_lnA, 0, (size_t)(nr > 0 ? nr : 0) * sizeof(double), st);
+    if (e == cudaSuccess && grad_u0 && ncell > 0)
+      e = cudaMemcpyAsync(grad_u0, ubar, (size_t)ncell * N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? RK_OK : cuda_error(e, "adjoint trivial case");
+  }
+  const size_t smem = (size_t)mech->host.L.bytes + EXP_TAB_BYTES;
+  cudaError_t e = cudaFuncSetAttribute(rok4e_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
+  rok4e_adjoint_kernel<<<(unsigned)((ncell + 127) / 128), 128, smem, st>>>(P);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "rok4e_adjoint_kernel launch");
+  adjoint_reduce_kernel<<<nr, 256, 0, st>>>(P.wsd + (int64_t)P.A.theta * ncell, ncell,
+                                           reinterpret_cast<const int32_t*>(mech->dev + mech->host.L.off_perm),
+                                           grad_lnA);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "adjoint_reduce_kernel launch");
+  return RK_OK;
 }
 
 int rk_probe_throughput(int32_t kind, double* ops_per_s) {

@@ -1,0 +1,125 @@
+"""GPU checks of the fixed-step integration and its discrete adjoint.
+
+* rk_rok4e_fixed_steps against the oracle's fixed-step integration.
+* The adjoint's d T_final / d ln A_j and d T_final / d u0 against the oracle's
+  complex-step derivatives of the same fixed-step computation (exact to
+  rounding), on a sample of parameters, and against GPU central differences.
+* The torch.autograd.Function wrapper returns the adjoint's gradient.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+P = 101325.0
+
+
+@pytest.fixture(scope="module")
+def rk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1712_00953_gb300 as rk
+
+    return rk
+
+
+def _setup(name, ncell):
+    from synth.fields import WORKLOADS, field_uniform, mechanism_for
+
+    w = WORKLOADS[name]
+    mech = mechanism_for(w)
+    U = field_uniform(ncell, mech.n_species, w.field_seed, 1000.0, 1500.0)
+    return w, mech, U
+
+
+def _adjoint_T(rk, mech, U, h, nsteps, M=4):
+    m = rk.mech_load(mech)
+    Y = torch.tensor(U, device="cuda")
+    n = U.shape[0]
+    ck = torch.empty(nsteps + 1, n, U.shape[1], dtype=torch.float64, device="cuda")
+    rk.rok4e_fixed_steps(m, Y, h, nsteps, M, checkpoints=ck)
+    ubar = torch.zeros_like(Y)
+    ubar[:, -1] = 1.0
+    g0 = torch.empty_like(Y)
+    grad, g0 = rk.rok4e_adjoint(m, ck, ubar, h, nsteps, M, grad_u0=g0)
+    torch.cuda.synchronize()
+    return Y.cpu().numpy(), ck.cpu().numpy(), grad.cpu().numpy(), g0.cpu().numpy()
+
+
+def test_fixed_steps_match_oracle(rk):
+    from oracle import rok4e as orok
+    from oracle.kinetics import Kinetics
+
+    w, mech, U = _setup("small", 6)
+    h, nsteps = 2e-8, 10
+    Y, ck, _, _ = _adjoint_T(rk, mech, U, h, nsteps)
+    ref, _ = orok.integrate_cells(Kinetics(mech), U, P, h * nsteps, 1.0, 1.0, 4, fixed_h=h)
+    ns = mech.n_species
+    assert np.all(np.abs(Y[:, :ns] - ref[:, :ns]) <= 1e-8 + 1e-6 * np.abs(ref[:, :ns]))
+    assert np.max(np.abs(Y[:, ns] - ref[:, ns])) <= 1e-6
+    np.testing.assert_array_equal(ck[0], U)
+    np.testing.assert_array_equal(ck[-1], Y)
+
+
+@pytest.mark.parametrize("name,nsteps,h", [("small", 10, 2e-8), ("mixed", 8, 1e-8)])
+def test_adjoint_matches_oracle_complex_step(rk, name, nsteps, h):
+    from oracle import adjoint as oad
+    from oracle.kinetics import Kinetics
+
+    w, mech, U = _setup(name, 3)
+    Y, ck, grad, g0 = _adjoint_T(rk, mech, U, h, nsteps)
+    kin = Kinetics(mech)
+    js = np.argsort(-np.abs(grad))[:6]  # the largest sensitivities plus two random ones
+    js = np.concatenate([js, np.random.default_rng(0).choice(mech.n_reactions, 2, replace=False)])
+    ref = sum(oad.grad_complex_step(kin, U[c], P, h, nsteps, 4, js) for c in range(U.shape[0]))
+    scale = np.max(np.abs(grad))
+    print(f"{name}: adjoint vs complex step, max |diff| / max |grad| = {np.max(np.abs(grad[js] - ref)) / scale:.3e}")
+    assert np.max(np.abs(grad[js] - ref)) <= 1e-7 * scale
+    # d T_final / d u0 for one cell, all components, by complex step on the state
+    c = 0
+    N = U.shape[1]
+    cs = np.empty(N)
+    for e in range(N):
+        u = U[c].astype(complex)
+        u[e] += 1e-30j
+        cs[e] = np.imag(oad.final_state(kin, u, P, h, nsteps, 4)[-1]) / 1e-30
+    assert np.max(np.abs(g0[c] - cs)) <= 1e-7 * np.max(np.abs(cs))
+
+
+def test_adjoint_matches_gpu_central_differences(rk):
+    w, mech, U = _setup("mixed", 64)
+    h, nsteps = 1e-8, 8
+    Y, ck, grad, _ = _adjoint_T(rk, mech, U, h, nsteps)
+    order = np.argsort(-np.abs(grad))[:12]
+    d = 1e-4
+    fd = []
+    for j in order:
+        vals = []
+        for sgn in (1.0, -1.0):
+            mk = mech.copy()
+            mk.arrh[j, 0] *= np.exp(sgn * d)
+            m = rk.mech_load(mk)
+            Yj = torch.tensor(U, device="cuda")
+            rk.rok4e_fixed_steps(m, Yj, h, nsteps, 4)
+            vals.append(Yj[:, -1].sum().item())
+        fd.append((vals[0] - vals[1]) / (2 * d))
+    fd = np.array(fd)
+    rel = np.abs(grad[order] - fd) / np.abs(grad[order])
+    print(f"adjoint vs central differences (d = {d}): max relative difference {rel.max():.2e}")
+    assert rel.max() < 1e-5
+
+
+def test_autograd_function(rk):
+    from paper_1712_00953_gb300 import FixedStepROK4E
+
+    w, mech, U = _setup("small", 16)
+    lnA = torch.tensor(np.log(mech.arrh[:, 0]), dtype=torch.float64, requires_grad=True)
+    Y0 = torch.tensor(U, device="cuda", requires_grad=True)
+    Y = FixedStepROK4E.apply(lnA, Y0, mech, 2e-8, 10, 4)
+    loss = Y[:, -1].sum()
+    loss.backward()
+    _, _, grad, g0 = _adjoint_T(rk, mech, U, 2e-8, 10)
+    np.testing.assert_allclose(lnA.grad.numpy(), grad, rtol=0, atol=1e-12 * np.abs(grad).max())
+    np.testing.assert_allclose(Y0.grad.cpu().numpy(), g0, rtol=0, atol=1e-12 * np.abs(g0).max())
