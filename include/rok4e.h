@@ -135,6 +135,18 @@ int rk_chem_rhs(const rk_mech* mech, const double* Y, const double* src, double 
 int rk_chem_jvp(const rk_mech* mech, const double* Y, const double* V, double p, double* JV,
                 int64_t ncell, int32_t mode, void* stream);
 
+/* Constant-volume source term and Jacobian-vector products (Eq. cv_reactor):
+ * cell c has the fixed density rho_cell[c] (device [ncell], kg/m^3);
+ * dY_k/dt = W_k w_k / rho, dT/dt = -sum_k u_k w_k / (rho c_v) with the molar
+ * internal energies u_k = h_k - R T and c_v = sum_k Y_k (c_p,k - R) / W_k.
+ * (The printed equation pairs h_k with c_v; a closed rigid adiabatic cell
+ * conserves internal energy, which is what the u_k form expresses.)  mode as
+ * in rk_chem_jvp (0 analytic, 1 finite difference). */
+int rk_chem_rhs_cv(const rk_mech* mech, const double* Y, const double* src, const double* rho_cell,
+                   double* dYdt, int64_t ncell, void* stream);
+int rk_chem_jvp_cv(const rk_mech* mech, const double* Y, const double* V, const double* rho_cell,
+                   double* JV, int64_t ncell, int32_t mode, void* stream);
+
 /* Mixed-precision source term: as rk_chem_rhs, with w = nu^T q in FP32 while
  * the rate coefficients, Gibbs factors, 1/Kc, the rates of progress
  * q = m (k prod C - k/Kc prod C), the heat release sum_j q_j Delta H_j and the
@@ -166,6 +178,12 @@ typedef struct rk_opts {
                              index, 2 longest expected first (dt / h_cell) */
   int32_t blocks_per_sm;  /* resident blocks per SM for the persistent launch; 0: all
                              that fit */
+  int32_t reactor;        /* 0 constant pressure (p, default); 1 constant volume: each
+                             cell keeps the density rho_cell[c] (kg/m^3) and the
+                             temperature equation uses internal energies and c_v
+                             (Eq. cv_reactor); p is then unused */
+  int32_t reserved1;
+  const double* rho_cell; /* device [ncell], read when reactor == 1 */
 } rk_opts;
 
 /* Bytes of workspace rk_rok4e_integrate needs: a work-queue counter, a

@@ -35,9 +35,19 @@ LN10 = np.log(10.0)
 
 
 class Kinetics:
-    """Dense-matrix restatement of a synth.Mechanism for the oracle."""
+    """Dense-matrix restatement of a synth.Mechanism for the oracle.
 
-    def __init__(self, mech):
+    reactor "cp": constant pressure -- the second argument of rhs/jacobian is p.
+    reactor "cv": constant volume (Eq. cv_reactor) -- the second argument is the
+    cell's density rho, held fixed; the temperature equation uses the species
+    internal energies u_k = h_k - R T and c_v = sum_k Y_k (cp_k - R) / W_k (the
+    printed equation pairs h_k with c_v; internal energies are what a closed,
+    rigid, adiabatic cell conserves)."""
+
+    def __init__(self, mech, reactor="cp"):
+        if reactor not in ("cp", "cv"):
+            raise ValueError(reactor)
+        self.reactor = reactor
         ns, nr = mech.n_species, mech.n_reactions
         self.ns, self.nr = ns, nr
         self.W = np.asarray(mech.W, dtype=float)
@@ -136,7 +146,7 @@ class Kinetics:
         Y, T = u[:ns], u[ns]
         cp_R, h_RT, s_R, dcp_R = self.thermo(T)
         S = np.sum(Y / self.W)
-        rho = p / (R_GAS * T * S)
+        rho = p / (R_GAS * T * S) if self.reactor == "cp" else p
         C = rho * Y / self.W
         lnT = np.log(T)
         kf = np.exp(self.lnA + self.b * lnT - self.Ea_R / T)
@@ -182,8 +192,9 @@ class Kinetics:
         ns = self.ns
         f = np.empty_like(u)
         f[:ns] = self.W * st["omega"] / st["rho"]
-        cbar = np.sum(st["Y"] * st["cp_R"] / self.W)
-        f[ns] = -st["T"] * np.sum(st["h_RT"] * st["omega"]) / (st["rho"] * cbar)
+        e = 0.0 if self.reactor == "cp" else 1.0  # u/RT = h/RT - 1, cv/R = cp/R - 1
+        cbar = np.sum(st["Y"] * (st["cp_R"] - e) / self.W)
+        f[ns] = -st["T"] * np.sum((st["h_RT"] - e) * st["omega"]) / (st["rho"] * cbar)
         if src is not None:
             f = f + src
         return f
@@ -197,11 +208,14 @@ class Kinetics:
         Wbar = 1.0 / S
         # dC/du and drho/du
         dC = np.zeros((ns, N), dtype=u.dtype)
-        dC[:, :ns] = np.diag(rho / W) - np.outer(C, Wbar / W)
-        dC[:, ns] = -C / T
         drho = np.zeros(N, dtype=u.dtype)
-        drho[:ns] = -rho * Wbar / W
-        drho[ns] = -rho / T
+        if self.reactor == "cp":
+            dC[:, :ns] = np.diag(rho / W) - np.outer(C, Wbar / W)
+            dC[:, ns] = -C / T
+            drho[:ns] = -rho * Wbar / W
+            drho[ns] = -rho / T
+        else:  # density fixed
+            dC[:, :ns] = np.diag(rho / W)
         # d(prod C^nu)/dC
         def dprod(nu):
             out = np.zeros((self.nr, ns), dtype=u.dtype)
@@ -234,7 +248,8 @@ class Kinetics:
         omega = st["omega"]
         J = np.zeros((N, N), dtype=u.dtype)
         J[:ns] = (W / rho)[:, None] * domega - (W * omega / rho**2)[:, None] * drho[None, :]
-        h_RT, cp_R, dcp_R = st["h_RT"], st["cp_R"], st["dcp_R"]
+        e = 0.0 if self.reactor == "cp" else 1.0
+        h_RT, cp_R, dcp_R = st["h_RT"] - e, st["cp_R"] - e, st["dcp_R"]
         cbar = np.sum(Y * cp_R / W)
         Sh = np.sum(h_RT * omega)
         dSh = h_RT @ domega

@@ -27,7 +27,8 @@ def _L():
         _LIB = _native.load()
     return _LIB
 
-__all__ = ["Mechanism", "mech_load", "mech_validate", "chem_rhs", "chem_rhs_mixed", "chem_jvp", "rok4e_integrate",
+__all__ = ["Mechanism", "mech_load", "mech_validate", "chem_rhs", "chem_rhs_mixed", "chem_rhs_cv", "chem_jvp_cv",
+           "chem_jvp", "rok4e_integrate",
            "rok4e_workspace_size", "simpler_split_step", "simpler_split_step_workspace_size",
            "diffusion_1d", "probe_throughput", "eval_exp", "split_step", "SCHEMES", "rok4e_fixed_steps",
            "rok4e_adjoint", "FixedStepROK4E", "Opts", "RokError", "STATS_FIELDS"]
@@ -128,7 +129,7 @@ class Opts:
     """Integration options (rk_opts); None fields keep the library defaults."""
 
     def __init__(self, jv_mode=0, max_attempts=0, lanes_per_cell=0, cells_per_block=0, h0=0.0, fixed_h=0.0,
-                 trace=None, events=None, precision=0, queue_order=0, blocks_per_sm=0):
+                 trace=None, events=None, precision=0, queue_order=0, blocks_per_sm=0, rho_cell=None):
         self.jv_mode, self.max_attempts = jv_mode, max_attempts
         self.lanes_per_cell, self.cells_per_block = lanes_per_cell, cells_per_block
         self.h0, self.fixed_h = h0, fixed_h
@@ -136,6 +137,7 @@ class Opts:
         self.events = events  # (begin, end) torch.cuda.Event pair around the integration kernel
         self.precision = precision  # 0 FP64, 1 mixed (FP32 nu^T q and inner products), 2 + FP32 J v
         self.queue_order, self.blocks_per_sm = queue_order, blocks_per_sm
+        self.rho_cell = rho_cell  # CUDA float64 [ncell]: constant-volume cells of these densities
 
     def c(self):
         cap = 0 if self.trace is None else int(self.trace.shape[-1])
@@ -143,8 +145,10 @@ class Opts:
         eb = ee = None
         if self.events is not None:
             eb, ee = (ctypes.c_void_p(e.cuda_event) for e in self.events)
+        rc = None if self.rho_cell is None else _dptr(self.rho_cell, "rho_cell")
         return RkOpts(self.jv_mode, self.max_attempts, self.lanes_per_cell, self.cells_per_block, self.h0,
-                      self.fixed_h, cap, self.precision, tp, eb, ee, self.queue_order, self.blocks_per_sm)
+                      self.fixed_h, cap, self.precision, tp, eb, ee, self.queue_order, self.blocks_per_sm,
+                      0 if rc is None else 1, 0, rc)
 
 
 def _ncell(Y, m):
@@ -166,6 +170,23 @@ def chem_rhs_mixed(m: Mechanism, Y, p, src=None, out=None, stream=None):
     out = torch.empty_like(Y) if out is None else out
     _check(_L().rk_chem_rhs_mixed(m.handle, _dptr(Y, "Y"), _dptr(src, "src", Y.numel()), float(p),
                                   _dptr(out, "out", Y.numel()), n, _stream_ptr(stream)), "rk_chem_rhs_mixed")
+    return out
+
+
+def chem_rhs_cv(m: Mechanism, Y, rho, src=None, out=None, stream=None):
+    """Constant-volume source term (cell c at the fixed density rho[c])."""
+    n = _ncell(Y, m)
+    out = torch.empty_like(Y) if out is None else out
+    _check(_L().rk_chem_rhs_cv(m.handle, _dptr(Y, "Y"), _dptr(src, "src", Y.numel()), _dptr(rho, "rho", n),
+                               _dptr(out, "out", Y.numel()), n, _stream_ptr(stream)), "rk_chem_rhs_cv")
+    return out
+
+
+def chem_jvp_cv(m: Mechanism, Y, V, rho, mode=0, out=None, stream=None):
+    n = _ncell(Y, m)
+    out = torch.empty_like(Y) if out is None else out
+    _check(_L().rk_chem_jvp_cv(m.handle, _dptr(Y, "Y"), _dptr(V, "V", Y.numel()), _dptr(rho, "rho", n),
+                               _dptr(out, "out", Y.numel()), n, int(mode), _stream_ptr(stream)), "rk_chem_jvp_cv")
     return out
 
 

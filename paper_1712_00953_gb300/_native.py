@@ -43,6 +43,9 @@ class RkOpts(ctypes.Structure):
         ("ev_end", ctypes.c_void_p),
         ("queue_order", ctypes.c_int32),
         ("blocks_per_sm", ctypes.c_int32),
+        ("reactor", ctypes.c_int32),
+        ("reserved1", ctypes.c_int32),
+        ("rho_cell", ctypes.c_void_p),
     ]
 
 
@@ -58,6 +61,10 @@ SIGNATURES = {
                                    ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p]),
     "rk_chem_rhs_mixed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "rk_chem_rhs_cv": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "rk_chem_jvp_cv": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p]),
     "rk_rok4e_workspace_size": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                                   ctypes.POINTER(RkOpts)]),
     "rk_rok4e_integrate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,

@@ -343,6 +343,7 @@ __device__ __forceinline__ void sum_first(const Grp<G>& g, T (&v)[MAXM], int n) 
 // Jacobian-vector product needs (uniform across the group).
 struct CellScalars {
   double T, invT, lnT, S, invS, rho, invrho, cb, invcb, Sh;
+  bool cv;
 };
 
 struct SlotPtrs {
@@ -399,7 +400,9 @@ __device__ inline SlotPtrs slot_ptrs(double* b, const SlotLayout& s) {
 }
 
 // ------------------------------------------------------------ chemistry RHS
-// out = f(uu) + src (src may be null).  uu, out: N-vectors in shared memory
+// out = f(uu) + src (src may be null).  p > 0: constant-pressure reactor at
+// pressure p; p < 0: constant-volume reactor of density -p (Eq. cv_reactor with
+// internal energies u_k/RT = h_k/RT - 1 and c_v/R = c_p/R - 1 per species).  uu, out: N-vectors in shared memory
 // (out must not alias uu).  When `cache` is set, the values the analytic
 // Jacobian-vector product reuses are kept (rate coefficients, w, d(cp/R)/dT
 // and the cell scalars).  Not inlined: chem_rhs and the integrator execute the
@@ -443,7 +446,9 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
   S = g.sum(S);
   ghi = g.imax(ghi);
   const bool direct_kc = ghi >= G_OVERFLOW_HI;  // |g/RT| >= 170, also NaN
-  const double rho = p / (R_GAS * T * S);
+  const bool cv = p < 0.0;
+  const double esh = cv ? 1.0 : 0.0;  // h/RT -> u/RT and cp/R -> cv/R shift
+  const double rho = cv ? -p : p / (R_GAS * T * S);
   const double invrho = 1.0 / rho;
   // concentrations, Gibbs factors, and (for up to MAXM pressure-dependent
   // reactions) the third-body concentrations [M]_t = sum_k eff_tk C_k
@@ -564,7 +569,8 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     s.q[j] = qj;
     if (MIXED) {
       s.fq[j] = __double2float_rn(qj);
-      shq = fma(qj, s.hRT[pa] + s.hRT[pb] - s.hRT[ra] - s.hRT[rb], shq);
+      const double dnud = dnu > 0 ? 1.0 : (dnu < 0 ? -1.0 : 0.0);
+      shq = fma(qj, s.hRT[pa] + s.hRT[pb] - s.hRT[ra] - s.hRT[rb] - esh * dnud, shq);
     }
     if (cache) {
       s.kc[j] = k;
@@ -592,8 +598,8 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     if (cache) s.om[k] = om;
     const double r = __dmul_rn(__dmul_rn(m.W[k], om), invrho);
     out[k] = src ? __dadd_rn(r, src[k]) : r;
-    if (!MIXED) Sh = fma(s.hRT[k], om, Sh);
-    cb = fma(uu[k] * s.cp[k], m.invW[k], cb);
+    if (!MIXED) Sh = fma(s.hRT[k] - esh, om, Sh);
+    cb = fma(uu[k] * (s.cp[k] - esh), m.invW[k], cb);
   }
   {
     double t2[2] = {Sh, cb};
@@ -616,6 +622,7 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     cs->cb = cb;
     cs->invcb = 1.0 / cb;
     cs->Sh = Sh;
+    cs->cv = cv;
   }
   g.sync();
 }
@@ -632,7 +639,8 @@ __device__ __noinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, cons
   double a = 0.0;
   for (int k = g.lane; k < ns; k += G) a = fma(v[k], m.invW[k], a);
   a = g.sum(a);
-  const double drr = -fma(a, cs.invS, vT * invT);  // d rho / rho
+  const double drr = cs.cv ? 0.0 : -fma(a, cs.invS, vT * invT);  // d rho / rho (0 at fixed volume)
+  const double esh = cs.cv ? 1.0 : 0.0;
   const bool coop_tb = m.ntb > 0 && m.ntb <= MAXM;
   double mp[MAXM];
 #pragma unroll
@@ -689,8 +697,8 @@ __device__ __noinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, cons
     for (int e = e0; e < e1; ++e) dom = fma(m.csr_nu[e], s.q[m.csr_j[e]], dom);
     const double om = s.om[k];
     out[k] = m.W[k] * (dom - om * drr) * cs.invrho;
-    dSh = fma(s.hRT[k], dom, fma((s.cp[k] - s.hRT[k]) * invT * vT, om, dSh));
-    dcb = fma(fma(uu[k] * s.dcp[k], vT, v[k] * s.cp[k]), m.invW[k], dcb);
+    dSh = fma(s.hRT[k] - esh, dom, fma((s.cp[k] - s.hRT[k]) * invT * vT, om, dSh));
+    dcb = fma(fma(uu[k] * s.dcp[k], vT, v[k] * (s.cp[k] - esh)), m.invW[k], dcb);
   }
   {
     double t2[2] = {dSh, dcb};
@@ -720,7 +728,8 @@ __device__ __noinline__ void jvp_eval_f32(const MechView& m, const SlotPtrs& s, 
   float a = 0.f;
   for (int k = g.lane; k < ns; k += G) a = fmaf(__double2float_rn(v[k]), m.invWf[k], a);
   a = g.sum(a);
-  const float drr = -fmaf(a, invS, vT * invT);
+  const float drr = cs.cv ? 0.f : -fmaf(a, invS, vT * invT);
+  const float esh = cs.cv ? 1.f : 0.f;
   const bool coop_tb = m.ntb > 0 && m.ntb <= MAXM;
   float mp[MAXM];
 #pragma unroll
@@ -778,8 +787,8 @@ __device__ __noinline__ void jvp_eval_f32(const MechView& m, const SlotPtrs& s, 
     const float om = s.fom[k];
     const float vk = __double2float_rn(v[k]);
     out[k] = (double)(m.Wf[k] * (dom - om * drr) * invrho);
-    dSh = fmaf(s.fh[k], dom, fmaf((s.fcp[k] - s.fh[k]) * invT * vT, om, dSh));
-    dcb = fmaf(fmaf(__double2float_rn(uu[k]) * s.fdcp[k], vT, vk * s.fcp[k]), m.invWf[k], dcb);
+    dSh = fmaf(s.fh[k] - esh, dom, fmaf((s.fcp[k] - s.fh[k]) * invT * vT, om, dSh));
+    dcb = fmaf(fmaf(__double2float_rn(uu[k]) * s.fdcp[k], vT, vk * (s.fcp[k] - esh)), m.invWf[k], dcb);
   }
   {
     float t2[2] = {dSh, dcb};
@@ -1059,6 +1068,7 @@ struct IntegrateParams {
   unsigned long long* counter;
   unsigned long long qstride;  // queue position q takes cell (q * qstride) mod ncell
   const int32_t* order;        // or, when set, cell order[q] (longest expected first)
+  const double* rho_cell;      // constant-volume densities, or null (constant pressure)
 };
 
 template <int G, bool MIXED>
@@ -1072,6 +1082,7 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
   g.sync();
   const double* srcp = P.src ? s.src : nullptr;
   const bool fixed = P.fixed_h > 0.0;
+  const double pr = P.rho_cell ? -P.rho_cell[cell] : P.p;  // negative: constant-volume density
   const bool fp32_jv = P.precision == 2;
   const double dt = P.dt;
   double h = P.h0 > 0.0 ? P.h0 : dt;
@@ -1084,9 +1095,9 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
   double t = 0.0, ln_err_prev = 0.0, h_last = h;  // err_n = 1 before the first step
   int n_acc = 0, n_rej = 0, n_rhs = 0, status = RK_CELL_OK, n_att = 0;
   CellScalars cs;
-  rhs_eval<G, MIXED>(m, s, s.u, srcp, P.p, s.fn, true, &cs);
+  rhs_eval<G, MIXED>(m, s, s.u, srcp, pr, s.fn, true, &cs);
   n_rhs += 1;
-  int mdim = arnoldi<G, MIXED>(m, s, cs, P.M, P.jv_mode, P.p, &n_rhs, fp32_jv);
+  int mdim = arnoldi<G, MIXED>(m, s, cs, P.M, P.jv_mode, pr, &n_rhs, fp32_jv);
   double* K0 = s.K;
   double* K1 = s.K + Nq;
   double* K2 = s.K + 2 * Nq;
@@ -1116,7 +1127,7 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
           s.arg[e] = s.u[e] + h * acc;
         }
         g.sync();
-        rhs_eval<G, MIXED>(m, s, s.arg, srcp, P.p, s.fr, false, &cs);
+        rhs_eval<G, MIXED>(m, s, s.arg, srcp, pr, s.fr, false, &cs);
         n_rhs += 1;
         fi = s.fr;
       } else {
@@ -1205,9 +1216,9 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
       h = hnew;
       const bool done = fixed ? (n_acc >= n_fixed) : (dt - t <= T_END_TOL * dt);
       if (!done) {
-        rhs_eval<G, MIXED>(m, s, s.u, srcp, P.p, s.fn, true, &cs);
+        rhs_eval<G, MIXED>(m, s, s.u, srcp, pr, s.fn, true, &cs);
         n_rhs += 1;
-        mdim = arnoldi<G, MIXED>(m, s, cs, P.M, P.jv_mode, P.p, &n_rhs, fp32_jv);
+        mdim = arnoldi<G, MIXED>(m, s, cs, P.M, P.jv_mode, pr, &n_rhs, fp32_jv);
       }
     } else {
       n_rej += 1;
@@ -1355,6 +1366,7 @@ struct PointParams {
   int64_t ncell;
   double p;
   int mode;  // 0 rhs, 1 analytic jvp, 2 finite-difference jvp, 3 mixed rhs, 4 FP32 analytic jvp
+  const double* rho_cell;  // constant-volume densities, or null
 };
 
 template <int G>
@@ -1381,25 +1393,26 @@ __global__ void __launch_bounds__(512) chem_point_kernel(PointParams P) {
     if (P.V) s.F[e] = P.V[cell * N + e];
   }
   g.sync();
+  const double pr = P.rho_cell ? -P.rho_cell[cell] : P.p;
   CellScalars cs;
   if (P.mode == 0 || P.mode == 3) {
-    if (P.mode == 3) rhs_eval<G, true>(m, s, s.u, P.src ? s.src : nullptr, P.p, s.fr, false, &cs);
-    else rhs_eval<G>(m, s, s.u, P.src ? s.src : nullptr, P.p, s.fr, false, &cs);
+    if (P.mode == 3) rhs_eval<G, true>(m, s, s.u, P.src ? s.src : nullptr, pr, s.fr, false, &cs);
+    else rhs_eval<G>(m, s, s.u, P.src ? s.src : nullptr, pr, s.fr, false, &cs);
     for (int e = g.lane; e < N; e += G) P.out[cell * N + e] = s.fr[e];
     return;
   }
   if (P.mode == 4) {
-    rhs_eval<G, true>(m, s, s.u, nullptr, P.p, s.fn, true, &cs);
+    rhs_eval<G, true>(m, s, s.u, nullptr, pr, s.fn, true, &cs);
     jvp_eval_f32<G>(m, s, s.u, cs, s.F, s.w);
     for (int e = g.lane; e < N; e += G) P.out[cell * N + e] = s.w[e];
     return;
   }
-  rhs_eval<G>(m, s, s.u, nullptr, P.p, s.fn, true, &cs);
+  rhs_eval<G>(m, s, s.u, nullptr, pr, s.fn, true, &cs);
   int n_rhs = 0;
   double unorm = 0.0;
   if (P.mode == 2) unorm = sqrt(group_dot<G>(g, s.u, s.u, N));
   // s.src is zero here, so the finite difference sees the bare source term
-  apply_jv<G>(m, s, cs, P.mode == 1 ? 0 : 1, P.p, unorm, s.F, s.w, &n_rhs);
+  apply_jv<G>(m, s, cs, P.mode == 1 ? 0 : 1, pr, unorm, s.F, s.w, &n_rhs);
   for (int e = g.lane; e < N; e += G) P.out[cell * N + e] = s.w[e];
 }
 
@@ -1652,6 +1665,9 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   P.stats = stats;
   unsigned char* wsb = static_cast<unsigned char*>(workspace);
   P.counter = reinterpret_cast<unsigned long long*>(wsb);
+  if (o.reactor < 0 || o.reactor > 1) return set_error(RK_E_INVALID_ARGUMENT, "reactor must be 0 or 1");
+  if (o.reactor == 1 && !o.rho_cell) return set_error(RK_E_INVALID_ARGUMENT, "constant volume needs rho_cell");
+  P.rho_cell = o.reactor == 1 ? o.rho_cell : nullptr;
   P.qstride = queue_stride(ncell);
   P.order = nullptr;
   cudaError_t e = cudaMemsetAsync(wsb, 0, 768, stream);  // counter, histogram, cursors
@@ -1760,7 +1776,7 @@ int rk_mech_info(const rk_mech* mech, int32_t* n_species, int32_t* n_reactions, 
 }
 
 static int point_call(const rk_mech* mech, const double* Y, const double* src, const double* V, double p,
-                      double* out, int64_t ncell, int mode, void* stream) {
+                      double* out, int64_t ncell, int mode, void* stream, const double* rho_cell = nullptr) {
   int rc = check_mech(mech);
   if (rc) return rc;
   if (ncell < 0) return set_error(RK_E_INVALID_ARGUMENT, "ncell < 0");
@@ -1768,8 +1784,9 @@ static int point_call(const rk_mech* mech, const double* Y, const double* src, c
   const bool needs_v = mode == 1 || mode == 2 || mode == 4;
   if (!Y || !out || (needs_v && !V)) return set_error(RK_E_INVALID_ARGUMENT, "null array");
   if (out == Y) return set_error(RK_E_INVALID_ARGUMENT, "output must not alias the state");
-  if (!(p > 0.0)) return set_error(RK_E_INVALID_ARGUMENT, "pressure must be > 0");
+  if (!rho_cell && !(p > 0.0)) return set_error(RK_E_INVALID_ARGUMENT, "pressure must be > 0");
   PointParams P;
+  P.rho_cell = rho_cell;
   P.mech = mech->dev;
   P.L = mech->host.L;
   P.S = make_slot(mech->host.L, 1, mode >= 3);
@@ -1802,6 +1819,19 @@ int rk_chem_jvp(const rk_mech* mech, const double* Y, const double* V, double p,
 int rk_chem_rhs_mixed(const rk_mech* mech, const double* Y, const double* src, double p, double* dYdt,
                       int64_t ncell, void* stream) {
   return point_call(mech, Y, src, nullptr, p, dYdt, ncell, 3, stream);
+}
+
+int rk_chem_rhs_cv(const rk_mech* mech, const double* Y, const double* src, const double* rho_cell, double* dYdt,
+                   int64_t ncell, void* stream) {
+  if (!rho_cell && ncell > 0) return set_error(RK_E_INVALID_ARGUMENT, "null density array");
+  return point_call(mech, Y, src, nullptr, 1.0, dYdt, ncell, 0, stream, rho_cell);
+}
+
+int rk_chem_jvp_cv(const rk_mech* mech, const double* Y, const double* V, const double* rho_cell, double* JV,
+                   int64_t ncell, int32_t mode, void* stream) {
+  if (mode != 0 && mode != 1) return set_error(RK_E_INVALID_ARGUMENT, "mode must be 0 or 1");
+  if (!rho_cell && ncell > 0) return set_error(RK_E_INVALID_ARGUMENT, "null density array");
+  return point_call(mech, Y, nullptr, V, 1.0, JV, ncell, mode == 0 ? 1 : 2, stream, rho_cell);
 }
 
 size_t rk_rok4e_workspace_size(const rk_mech* mech, int64_t ncell, int32_t krylov_dim, const rk_opts* opts) {

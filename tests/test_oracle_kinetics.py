@@ -233,3 +233,48 @@ def test_fd_jvp_converges_to_analytic(case):
     jv = kin.jvp(u, P, v)
     jfd = kin.jvp_fd(u, P, v)
     assert np.max(np.abs(jv - jfd)) < 1e-4 * np.max(np.abs(jv))
+
+
+def test_constant_volume_conserves_internal_energy_and_mass():
+    w = WORKLOADS["flame1d"]
+    mech = mechanism_for(w)
+    kin = Kinetics(mech, reactor="cv")
+    ns = mech.n_species
+    for u in _sample(initial_state(w)):
+        rho = 0.3
+        f = kin.rhs(u, rho)
+        T = u[ns]
+        cp_R, h_RT, _, _ = kin.thermo(T)
+        e_mass = (h_RT - 1.0) * R_GAS * T / mech.W  # internal energy per unit mass of species k
+        cv_mass = np.sum(u[:ns] * (cp_R - 1.0) * R_GAS / mech.W)
+        dE = np.sum(e_mass * f[:ns]) + cv_mass * f[ns]
+        assert abs(dE) < 1e-10 * np.sum(np.abs(e_mass * f[:ns]))
+        assert abs(f[:ns].sum()) < 1e-13 * np.max(np.abs(f[:ns]))
+
+
+def test_constant_volume_jacobian_matches_complex_step():
+    w = WORKLOADS["flame1d"]
+    kin = Kinetics(mechanism_for(w), reactor="cv")
+    for u in _sample(initial_state(w), 3):
+        rho = 0.25
+        J = kin.jacobian(u, rho)
+        N = len(u)
+        Jcs = np.empty_like(J)
+        for i in range(N):
+            s = max(1.0, abs(u[i]))
+            du = np.zeros(N, complex)
+            du[i] = 1e-30j * s
+            Jcs[:, i] = np.imag(kin.rhs(u + du, rho)) / (1e-30 * s)
+        scale = np.max(np.abs(Jcs), axis=1, keepdims=True) + 1e-300
+        assert np.max(np.abs(J - Jcs) / scale) < 1e-10
+
+
+def test_constant_volume_and_pressure_agree_on_species_rates_at_equal_density():
+    w = WORKLOADS["small"]
+    mech = mechanism_for(w)
+    cp, cv = Kinetics(mech), Kinetics(mech, reactor="cv")
+    u = initial_state(w)[3]
+    st = cp.state(u, P)
+    a, b = cp.rhs(u, P), cv.rhs(u, st["rho"])
+    ns = mech.n_species
+    np.testing.assert_allclose(b[:ns], a[:ns], rtol=1e-12, atol=1e-12 * np.abs(a[:ns]).max())
