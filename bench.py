@@ -450,9 +450,9 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=0,
                     help="run this many untimed split steps and exit (profiling case)")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per cell (0: library default)")
-    ap.add_argument("--cells-per-block", type=int, default=4, help="cells per block (0: library default)")
+    ap.add_argument("--cells-per-block", type=int, default=8, help="cells per block (0: library default)")
     ap.add_argument("--precision", default="fp64", choices=list(PREC))
-    ap.add_argument("--queue-order", type=int, default=1, help="0 auto, 1 interleaved, 2 longest first")
+    ap.add_argument("--queue-order", type=int, default=3, help="0 auto, 1 interleaved, 2 longest first, 3 static balanced bins")
     ap.add_argument("--workload", default="flame1d", choices=["flame1d", "batched"],
                     help="flame1d: the benchmark line; batched: the 2^20-cell throughput measurement")
     ap.add_argument("--blocks-per-sm", type=int, default=0, help="resident blocks per SM (0: all that fit)")

@@ -174,8 +174,12 @@ typedef struct rk_opts {
   double* trace;          /* device [ncell x trace_cap]: +h accepted, -h rejected, 0 unused */
   void* ev_begin;         /* optional cudaEvent_t recorded on the stream right before the */
   void* ev_end;           /* integration kernel and right after it (timing hook), or NULL */
-  int32_t queue_order;    /* 0 auto (1 without h_cell, 2 with it), 1 interleaved cell
-                             index, 2 longest expected first (dt / h_cell) */
+  int32_t queue_order;    /* 0 auto (1 without h_cell, 3 with it), 1 interleaved cell
+                             index, 2 longest expected first (dt / h_cell), 3 static
+                             balanced bins: the longest-first queue dealt in snake
+                             order over (block, warp group) bins, one block per
+                             resident slot on every SM (interleaved order without
+                             h_cell) */
   int32_t blocks_per_sm;  /* resident blocks per SM for the persistent launch; 0: all
                              that fit */
   int32_t reactor;        /* 0 constant pressure (p, default); 1 constant volume: each

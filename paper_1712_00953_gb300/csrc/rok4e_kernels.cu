@@ -39,6 +39,8 @@ namespace rk {
 // ---------------------------------------------------------------- constants
 constexpr double R_GAS = 8.314462618;
 constexpr double P_REF = 101325.0;
+constexpr double R_OVER_PREF = R_GAS / P_REF, PREF_OVER_R = P_REF / R_GAS, INV_R = 1.0 / R_GAS;
+constexpr double LN_R_OVER_PREF = -9.408091968961747;  // ln(R / P_ref)
 constexpr double GAM = 0.572816062482135;
 // Table coeff_rok4e (Sec. 4.2); b3 = 0, bhat4 = 0.
 constexpr double G21 = -0.602765307997356;
@@ -176,7 +178,7 @@ struct SlotLayout {
   int N, ns, nr, ntb, M;
   int u, src, fn, arg, fr, F, w, Q, K;        // N-vectors (Q: M of them, K: 4)
   int C, dC, cp, hRT, dcp, gRT, E, Einv, om;  // species (+1 sentinel entry)
-  int q, kc, krc;                             // reactions
+  int q, kc, krc, qT;                         // reactions (qT: d q_j / dT at u_n, for J v)
   int tb;                                     // [ntb][4]: [M], dk/d[M], dlnk/dT, 1/Kc
   int H, LU, piv, red;                        // small
   int fbase;  // FP32 region (mixed precision only), offset in doubles
@@ -220,6 +222,7 @@ static SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false) {
   s.q = take(L.nr > 0 ? L.nr : 1);
   s.kc = take(L.nr > 0 ? L.nr : 1);
   s.krc = take(L.nr > 0 ? L.nr : 1);
+  s.qT = take(L.nr > 0 ? L.nr : 1);
   s.tb = take(4 * (L.ntb > 0 ? L.ntb : 1));
   s.H = take(MAXM * MAXM);
   s.LU = take(MAXM * MAXM);
@@ -343,12 +346,13 @@ __device__ __forceinline__ void sum_first(const Grp<G>& g, T (&v)[MAXM], int n) 
 // Jacobian-vector product needs (uniform across the group).
 struct CellScalars {
   double T, invT, lnT, S, invS, rho, invrho, cb, invcb, Sh;
+  double pinv;  // 1 / p (constant pressure) or 1 / rho (constant volume): set by the caller
   bool cv;
 };
 
 struct SlotPtrs {
   double *u, *src, *fn, *arg, *fr, *F, *w, *Q, *K;
-  double *C, *dC, *cp, *hRT, *dcp, *gRT, *E, *Einv, *om, *q, *kc, *krc, *tb;
+  double *C, *dC, *cp, *hRT, *dcp, *gRT, *E, *Einv, *om, *q, *kc, *krc, *qT, *tb;
   double *H, *LU, *piv, *red;
   float *fC, *fdC, *fh, *fcp, *fdcp, *fom, *fq, *fkc, *fkr, *ftb, *fQ, *fw;  // mixed precision
   int Nq;  // stride between Krylov / stage vectors
@@ -377,6 +381,7 @@ __device__ inline SlotPtrs slot_ptrs(double* b, const SlotLayout& s) {
   p.q = b + s.q;
   p.kc = b + s.kc;
   p.krc = b + s.krc;
+  p.qT = b + s.qT;
   p.tb = b + s.tb;
   p.H = b + s.H;
   p.LU = b + s.LU;
@@ -448,8 +453,10 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
   const bool direct_kc = ghi >= G_OVERFLOW_HI;  // |g/RT| >= 170, also NaN
   const bool cv = p < 0.0;
   const double esh = cv ? 1.0 : 0.0;  // h/RT -> u/RT and cp/R -> cv/R shift
-  const double rho = cv ? -p : p / (R_GAS * T * S);
-  const double invrho = 1.0 / rho;
+  const double invS = 1.0 / S;
+  // rho = p / (R T S), 1/rho = R T S / p, with 1/p (or 1/rho) from the caller
+  const double rho = cv ? -p : p * invT * invS * INV_R;
+  const double invrho = cv ? cs->pinv : R_GAS * T * S * cs->pinv;
   // concentrations, Gibbs factors, and (for up to MAXM pressure-dependent
   // reactions) the third-body concentrations [M]_t = sum_k eff_tk C_k
   const bool coop_tb = m.ntb > 0 && m.ntb <= MAXM;
@@ -477,9 +484,9 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
   }
   g.sync();
   // reactions: rate coefficients and rates of progress
-  const double RTp = R_GAS * T / P_REF;
-  const double invRTp = P_REF / (R_GAS * T);
-  const double lnRTp = log(RTp);
+  const double RTp = R_OVER_PREF * T;
+  const double invRTp = PREF_OVER_R * invT;
+  const double lnRTp = LN_R_OVER_PREF + lnT;
   const double m_lnRTp = -lnRTp;
   double shq = 0.0;  // mixed mode: heat release sum_j q_j Delta H_j / RT in FP64
   for (int j = g.lane; j < m.nr; j += G) {
@@ -504,6 +511,8 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
       }
     }
     double mfac = 1.0;
+    double dlnk = 0.0;  // d ln k / dT (cache only)
+    if (cache) dlnk = (m.bexp[j] + m.EaR[j] * invT) * invT;
     if (kind != 0) {
       const int slot = meta >> 8;
       double Mc;
@@ -514,13 +523,14 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
         Mc = 0.0;
         for (int q = 0; q < ns; ++q) Mc = fma(e[q], s.C[q], Mc);
       }
-      double dkdM = 0.0, dlnk = (m.bexp[j] + m.EaR[j] * invT) * invT;
+      double dkdM = 0.0;
       if (kind == 1) {
         mfac = Mc;
       } else {
         const double* fo = m.fo + (size_t)slot * FO_STRIDE;
-        const double k0 = exp_fast(fo[0] + fo[1] * lnT - fo[2] * invT, m.etab);
-        double Pr = k0 * Mc * (1.0 / k);
+        // Pr = k0 [M] / k_inf = [M] exp(ln k0 - ln k_inf): no division
+        const double er = exp_fast(fo[0] + fo[1] * lnT - fo[2] * invT - lnk, m.etab);
+        double Pr = er * Mc;
         if (!(Pr > 1e-300)) Pr = 1e-300;
         const double a = fo[3];
         const double e3 = exp_fast(-T * fo[4], m.etab), e1 = exp_fast(-T * fo[5], m.etab);
@@ -531,17 +541,24 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
         const double nn = 0.75 - 1.27 * lFc;
         const double x = log10(Pr) + cc;
         const double D = nn - 0.14 * x;
-        const double iD = 1.0 / D;
-        const double f1 = x * iD;
-        const double iden = 1.0 / (1.0 + f1 * f1);
+        // one division for 1/(1 + Pr) and 1/(D^2 + x^2):
+        //   1/(1 + f1^2) = D^2/(D^2 + x^2) with f1 = x / D
+        const double s2 = fma(D, D, x * x);
+        const double onePr = 1.0 + Pr;
+        const double qd = 1.0 / (onePr * s2);
+        const double iOnePr = s2 * qd;
+        const double rr = onePr * qd;  // 1 / (D^2 + x^2)
+        const double iden = D * D * rr;
         const double F = exp_fast(lFc * iden * 2.302585092994046, m.etab);  // 10^(lFc / (1 + f1^2))
-        const double iOnePr = 1.0 / (1.0 + Pr);
         if (cache) {  // d ln k / dT and d k / d[M] for the analytic J v
+          const double k0 = k * er;
           const double dlnk0 = (fo[1] + fo[2] * invT) * invT;
-          const double w2 = lFc * 2.0 * f1 * iden * iden;
-          const double dlF_dL = -w2 * nn * iD * iD;
-          const double df1 = (-0.67 * D + 1.1762 * x) * iD * iD;
-          const double dlF_dlFc = iden - w2 * df1;
+          // d ln F / d log10 Pr = -2 lFc f1 n / (D^2 (1 + f1^2)^2) and
+          // d log10 F / d lFc = 1/(1 + f1^2) - 2 lFc f1 (df1/dlFc) / (1 + f1^2)^2,
+          // df1/dlFc = (-0.67 D + 1.1762 x) / D^2, written with rr = 1/(D^2 + x^2)
+          const double w = 2.0 * lFc * x * D * rr * rr;
+          const double dlF_dL = -w * nn;
+          const double dlF_dlFc = iden - w * (-0.67 * D + 1.1762 * x);
           const double dFc = -(1.0 - a) * fo[4] * e3 - a * fo[5] * e1 + (fo[6] > 0.0 ? fo[6] * invT * invT * e2 : 0.0);
           const double gg = iOnePr + dlF_dL;
           dlnk = dlnk + gg * (dlnk0 - dlnk) + dlF_dlFc * dFc * (1.0 / Fc);
@@ -573,6 +590,12 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
       shq = fma(qj, s.hRT[pa] + s.hRT[pb] - s.hRT[ra] - s.hRT[rb] - esh * dnud, shq);
     }
     if (cache) {
+      // d q_j / dT at fixed concentrations (without the third-body factor):
+      // k Pf d ln k/dT - kr Pb (d ln k/dT - d ln Kc/dT), with
+      // d ln Kc/dT = (sum_products h/RT - sum_reactants h/RT - dnu) / T.
+      const double dnud = dnu > 0 ? 1.0 : (dnu < 0 ? -1.0 : 0.0);
+      const double dlnKc = (s.hRT[pa] + s.hRT[pb] - s.hRT[ra] - s.hRT[rb] - dnud) * invT;
+      s.qT[j] = fma(k * dlnk, Pf, -kr * (dlnk - dlnKc) * Pb);
       s.kc[j] = k;
       s.krc[j] = kr;
       if (MIXED) {
@@ -600,6 +623,18 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     out[k] = src ? __dadd_rn(r, src[k]) : r;
     if (!MIXED) Sh = fma(s.hRT[k] - esh, om, Sh);
     cb = fma(uu[k] * (s.cp[k] - esh), m.invW[k], cb);
+    if (cache) {
+      // per-species factors of the analytic J v, written over arrays the
+      // remaining RHS no longer reads (lane-private entries k):
+      //   E: rho/W_k   Einv: W_k/rho   gRT: h_k/RT - esh
+      //   hRT: (cp_k/R - h_k/RT) w_k / T   dcp: Y_k (dcp_k/dT) / W_k   cp: (cp_k/R - esh) / W_k
+      s.E[k] = rho * m.invW[k];
+      s.Einv[k] = m.W[k] * invrho;
+      s.gRT[k] = s.hRT[k] - esh;
+      s.hRT[k] = (s.cp[k] - s.hRT[k]) * invT * om;
+      s.dcp[k] = uu[k] * s.dcp[k] * m.invW[k];
+      s.cp[k] = (s.cp[k] - esh) * m.invW[k];
+    }
   }
   {
     double t2[2] = {Sh, cb};
@@ -607,8 +642,9 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     Sh = t2[0];
     cb = t2[1];
   }
+  const double invcb = 1.0 / cb;
   if (g.lane == 0) {
-    const double r = -T * Sh / (rho * cb);
+    const double r = -T * Sh * invrho * invcb;
     out[ns] = src ? __dadd_rn(r, src[ns]) : r;
   }
   if (cache) {
@@ -616,11 +652,11 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     cs->invT = invT;
     cs->lnT = lnT;
     cs->S = S;
-    cs->invS = 1.0 / S;
+    cs->invS = invS;
     cs->rho = rho;
     cs->invrho = invrho;
     cs->cb = cb;
-    cs->invcb = 1.0 / cb;
+    cs->invcb = invcb;
     cs->Sh = Sh;
     cs->cv = cv;
   }
@@ -646,7 +682,7 @@ __device__ __noinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, cons
 #pragma unroll
   for (int t = 0; t < MAXM; ++t) mp[t] = 0.0;
   for (int k = g.lane; k < ns; k += G) {
-    const double dCk = fma(s.C[k], drr, cs.rho * v[k] * m.invW[k]);
+    const double dCk = fma(s.C[k], drr, s.E[k] * v[k]);  // E: rho / W_k
     s.dC[k] = dCk;
     if (coop_tb) {
 #pragma unroll
@@ -661,20 +697,15 @@ __device__ __noinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, cons
     const int ra = sl & 255, rb = (sl >> 8) & 255, pa = (sl >> 16) & 255, pb = sl >> 24;
     const int meta = m.meta[j];
     const int kind = meta & 3;
-    const int dnu = ((meta >> 4) & 15) - 4;
-    const double Pf = s.C[ra] * s.C[rb];
-    const double Pb = s.C[pa] * s.C[pb];
     const double dPf = fma(s.dC[ra], s.C[rb], s.C[ra] * s.dC[rb]);
     const double dPb = fma(s.dC[pa], s.C[pb], s.C[pa] * s.dC[pb]);
     const double k = s.kc[j], kr = s.krc[j];
-    double dlnk = (m.bexp[j] + m.EaR[j] * invT) * invT;
-    const double dnud = dnu > 0 ? 1.0 : (dnu < 0 ? -1.0 : 0.0);
-    const double dlnKc = (s.hRT[pa] + s.hRT[pb] - s.hRT[ra] - s.hRT[rb] - dnud) * invT;
-    if (kind == 2) dlnk = s.tb[4 * (meta >> 8) + 2];
-    double dq = k * fma(dlnk * vT, Pf, dPf) - kr * fma((dlnk - dlnKc) * vT, Pb, dPb);
+    double dq = fma(s.qT[j], vT, fma(k, dPf, -kr * dPb));
     if (kind != 0) {
       const int slot = meta >> 8;
       const double* t = s.tb + 4 * slot;
+      const double Pf = s.C[ra] * s.C[rb];
+      const double Pb = s.C[pa] * s.C[pb];
       double dM = 0.0;
       if (coop_tb) {
 #pragma unroll
@@ -695,10 +726,9 @@ __device__ __noinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, cons
     double dom = 0.0;
     const int e0 = m.csr_ptr[k], e1 = m.csr_ptr[k + 1];
     for (int e = e0; e < e1; ++e) dom = fma(m.csr_nu[e], s.q[m.csr_j[e]], dom);
-    const double om = s.om[k];
-    out[k] = m.W[k] * (dom - om * drr) * cs.invrho;
-    dSh = fma(s.hRT[k] - esh, dom, fma((s.cp[k] - s.hRT[k]) * invT * vT, om, dSh));
-    dcb = fma(fma(uu[k] * s.dcp[k], vT, v[k] * (s.cp[k] - esh)), m.invW[k], dcb);
+    out[k] = s.Einv[k] * fma(-s.om[k], drr, dom);  // Einv: W_k / rho
+    dSh = fma(s.gRT[k], dom, fma(s.hRT[k], vT, dSh));
+    dcb = fma(s.dcp[k], vT, fma(s.cp[k], v[k], dcb));
   }
   {
     double t2[2] = {dSh, dcb};
@@ -830,6 +860,7 @@ __device__ inline void apply_jv(const MechView& m, const SlotPtrs& s, const Cell
   for (int e = g.lane; e < N; e += G) s.arg[e] = s.u[e] + d * v[e];
   g.sync();
   CellScalars dummy;
+  dummy.pinv = cs.pinv;
   rhs_eval<G, MIXED>(m, s, s.arg, s.src, p, out, false, &dummy);
   *n_rhs += 1;
   for (int e = g.lane; e < N; e += G) out[e] = (out[e] - s.fn[e]) / d;
@@ -856,14 +887,15 @@ __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& 
   const int Nq = s.Nq;
   if (M > N) M = N;
   for (int i = g.lane; i < MAXM * MAXM; i += G) s.H[i] = 0.0;
-  const double beta = MIXED ? (double)sqrtf(group_dot_f<G>(g, s.fn, s.fn, N)) : sqrt(group_dot<G>(g, s.fn, s.fn, N));
-  if (M <= 0 || !(beta > 0.0) || !isfinite(beta)) {
+  // squared norms; 1/||.|| from one reciprocal square root
+  const double beta2 = MIXED ? (double)group_dot_f<G>(g, s.fn, s.fn, N) : group_dot<G>(g, s.fn, s.fn, N);
+  if (M <= 0 || !(beta2 > 0.0) || !isfinite(beta2)) {
     g.sync();
     return 0;
   }
   double unorm = 0.0;
   if (jv_mode != 0) unorm = sqrt(group_dot<G>(g, s.u, s.u, N));
-  const double ibeta = 1.0 / beta;
+  const double ibeta = rsqrt(beta2);
   for (int e = g.lane; e < N; e += G) {
     const double qe = s.fn[e] * ibeta;
     s.Q[e] = qe;
@@ -871,10 +903,11 @@ __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& 
   }
   g.sync();
   constexpr double brk = MIXED ? 1e-5 : BREAKDOWN_TOL;
+  constexpr double brk2 = brk * brk;  // breakdown ||w_after|| <= brk ||w_before||, on squares
   int mdim = M;
   for (int j = 0; j < M; ++j) {
     apply_jv<G, MIXED>(m, s, cs, jv_mode, p, unorm, s.Q + j * Nq, s.w, n_rhs, fp32_jv);
-    const double w0 = MIXED ? (double)sqrtf(group_dot_f<G>(g, s.w, s.w, N)) : sqrt(group_dot<G>(g, s.w, s.w, N));
+    const double w02 = MIXED ? (double)group_dot_f<G>(g, s.w, s.w, N) : group_dot<G>(g, s.w, s.w, N);
     double hcol[MAXM];
 #pragma unroll
     for (int i = 0; i < MAXM; ++i) hcol[i] = 0.0;
@@ -914,19 +947,20 @@ __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& 
 #pragma unroll
       for (int i = 0; i < MAXM; ++i) hcol[i] += hp[i];
     }
-    const double hn = MIXED ? (double)sqrtf(group_dot_f<G>(g, s.w, s.w, N)) : sqrt(group_dot<G>(g, s.w, s.w, N));
+    const double hn2 = MIXED ? (double)group_dot_f<G>(g, s.w, s.w, N) : group_dot<G>(g, s.w, s.w, N);
     if (g.lane == 0) {
 #pragma unroll
       for (int i = 0; i < MAXM; ++i)
         if (i <= j) s.H[i * MAXM + j] = hcol[i];
     }
     if (j + 1 == M) break;
-    if (hn <= brk * w0 || hn == 0.0) {
+    if (hn2 <= brk2 * w02 || hn2 == 0.0) {
       mdim = j + 1;
       break;
     }
+    const double ihn = rsqrt(hn2);
+    const double hn = hn2 * ihn;
     if (g.lane == 0) s.H[(j + 1) * MAXM + j] = hn;
-    const double ihn = 1.0 / hn;
     for (int e = g.lane; e < N; e += G) {
       const double qe = s.w[e] * ihn;
       s.Q[(j + 1) * Nq + e] = qe;
@@ -944,16 +978,21 @@ __device__ inline void factor_small(const SlotPtrs& s, int mdim, double h) {
   const Grp<G> g;
   if (g.lane == 0) {
     double* A = s.LU;
+    const double hg = h * GAM;
     for (int i = 0; i < mdim; ++i)
-      for (int j = 0; j < mdim; ++j) A[i * MAXM + j] = (i == j ? 1.0 : 0.0) - h * GAM * s.H[i * MAXM + j];
+      for (int j = 0; j < mdim; ++j) A[i * MAXM + j] = fma(-hg, s.H[i * MAXM + j], i == j ? 1.0 : 0.0);
     for (int c = 0; c < mdim; ++c) {
+      // partial pivoting; |a| compared through its bit pattern (the order of
+      // non-negative doubles is the order of their bits), an integer compare
       int pr = c;
-      double best = fabs(A[c * MAXM + c]);
-      for (int r = c + 1; r < mdim; ++r)
-        if (fabs(A[r * MAXM + c]) > best) {
-          best = fabs(A[r * MAXM + c]);
+      long long best = __double_as_longlong(fabs(A[c * MAXM + c]));
+      for (int r = c + 1; r < mdim; ++r) {
+        const long long cand = __double_as_longlong(fabs(A[r * MAXM + c]));
+        if (cand > best) {
+          best = cand;
           pr = r;
         }
+      }
       s.piv[c] = (double)pr;
       if (pr != c)
         for (int j = 0; j < mdim; ++j) {
@@ -1068,6 +1107,7 @@ struct IntegrateParams {
   unsigned long long* counter;
   unsigned long long qstride;  // queue position q takes cell (q * qstride) mod ncell
   const int32_t* order;        // or, when set, cell order[q] (longest expected first)
+  int subq;                    // > 0: static bins, subq sub-queues per block (queue order 3)
   const double* rho_cell;      // constant-volume densities, or null (constant pressure)
 };
 
@@ -1095,6 +1135,7 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
   double t = 0.0, ln_err_prev = 0.0, h_last = h;  // err_n = 1 before the first step
   int n_acc = 0, n_rej = 0, n_rhs = 0, status = RK_CELL_OK, n_att = 0;
   CellScalars cs;
+  cs.pinv = 1.0 / fabs(pr);
   rhs_eval<G, MIXED>(m, s, s.u, srcp, pr, s.fn, true, &cs);
   n_rhs += 1;
   int mdim = arnoldi<G, MIXED>(m, s, cs, P.M, P.jv_mode, pr, &n_rhs, fp32_jv);
@@ -1281,6 +1322,30 @@ __global__ void __launch_bounds__(512) rok4e_integrate_kernel(IntegrateParams P)
   const SlotPtrs s = slot_ptrs(base, P.S);
   init_sentinels<MIXED>(s, m.ns, g.lane);
   g.sync();
+  if (P.subq > 0) {
+    // Static bins: the queue (longest expected first) is dealt out in snake
+    // order over nb = gridDim.x * subq bins, bin k = sub * gridDim.x + block,
+    // so every block -- and within a block every group of warps sharing a
+    // sub-queue -- receives a near-equal share of the expensive cells.  Round
+    // r of bin k holds queue position r * nb + (r even ? k : nb - 1 - k).
+    __shared__ unsigned sub_ctr[4];
+    if (threadIdx.x < 4) sub_ctr[threadIdx.x] = 0u;
+    __syncthreads();
+    const int sub = gid % P.subq;
+    const unsigned long long nb = (unsigned long long)gridDim.x * (unsigned long long)P.subq;
+    const unsigned long long k = (unsigned long long)sub * gridDim.x + blockIdx.x;
+    while (true) {
+      unsigned r = 0u;
+      if (g.lane == 0) r = atomicAdd(&sub_ctr[sub], 1u);
+      r = __shfl_sync(g.mask, r, 0, G);
+      const unsigned long long q = (unsigned long long)r * nb + ((r & 1u) ? nb - 1ull - k : k);
+      if (q >= (unsigned long long)P.ncell) break;
+      const unsigned long long cell =
+          P.order ? (unsigned long long)P.order[q] : (q * P.qstride) % (unsigned long long)P.ncell;
+      integrate_cell<G, MIXED>(m, s, P, (int64_t)cell);
+    }
+    return;
+  }
   while (true) {
     unsigned long long q = 0;
     if (g.lane == 0) q = atomicAdd(P.counter, 1ull);
@@ -1395,6 +1460,7 @@ __global__ void __launch_bounds__(512) chem_point_kernel(PointParams P) {
   g.sync();
   const double pr = P.rho_cell ? -P.rho_cell[cell] : P.p;
   CellScalars cs;
+  cs.pinv = 1.0 / fabs(pr);
   if (P.mode == 0 || P.mode == 3) {
     if (P.mode == 3) rhs_eval<G, true>(m, s, s.u, P.src ? s.src : nullptr, pr, s.fr, false, &cs);
     else rhs_eval<G>(m, s, s.u, P.src ? s.src : nullptr, pr, s.fr, false, &cs);
@@ -1555,13 +1621,14 @@ int device_props(int* n_sm, size_t* smem_optin) {
 
 template <int G, typename K>
 int plan_for(K kernel, const rk_mech* mech, const SlotLayout& S, int want_cells, int64_t ncell, bool persistent,
-             LaunchPlan* plan, int want_blocks_per_sm = 0) {
+             LaunchPlan* plan, int want_blocks_per_sm = 0, bool fill_device = false) {
   int n_sm = 0;
   size_t smem_max = 0;
   int rc = device_props(&n_sm, &smem_max);
   if (rc) return rc;
   const size_t mech_bytes = (size_t)mech->host.L.bytes + EXP_TAB_BYTES;
   const size_t slot_bytes = (size_t)S.stride * sizeof(double);
+  smem_max -= 64;  // the kernels' static shared memory (queue counters)
   if (mech_bytes + slot_bytes > smem_max)
     return set_error(RK_E_UNSUPPORTED, "mechanism plus one cell's work arrays exceed shared memory");
   int cells = (int)((smem_max - mech_bytes) / slot_bytes);
@@ -1587,7 +1654,7 @@ int plan_for(K kernel, const rk_mech* mech, const SlotLayout& S, int want_cells,
   plan->smem = smem;
   const int64_t need = (ncell + cells - 1) / cells;
   int64_t blocks = persistent ? (int64_t)per_sm * n_sm : need;
-  if (persistent && blocks > need) blocks = need;
+  if (persistent && blocks > need && !fill_device) blocks = need;
   plan->blocks = (int)(blocks > 0 ? blocks : 1);
   return RK_OK;
 }
@@ -1672,10 +1739,11 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   P.order = nullptr;
   cudaError_t e = cudaMemsetAsync(wsb, 0, 768, stream);  // counter, histogram, cursors
   if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
-  if (o.queue_order < 0 || o.queue_order > 2) return set_error(RK_E_INVALID_ARGUMENT, "queue_order must be 0..2");
-  const int order = o.queue_order == 0 ? (h_cell ? 2 : 1) : o.queue_order;
+  if (o.queue_order < 0 || o.queue_order > 3) return set_error(RK_E_INVALID_ARGUMENT, "queue_order must be 0..3");
+  const int order = o.queue_order == 0 ? (h_cell ? 3 : 1) : o.queue_order;
   if (order == 2 && !h_cell) return set_error(RK_E_INVALID_ARGUMENT, "queue_order 2 needs h_cell");
-  if (order == 2 && ncell > 1 && !(o.fixed_h > 0.0) && ncell < (int64_t)INT32_MAX) {
+  P.subq = 0;
+  if ((order == 2 || order == 3) && h_cell && ncell > 1 && !(o.fixed_h > 0.0) && ncell < (int64_t)INT32_MAX) {
     unsigned* hist = reinterpret_cast<unsigned*>(wsb + 256);
     unsigned* cursor = reinterpret_cast<unsigned*>(wsb + 512);
     int32_t* perm = reinterpret_cast<int32_t*>(wsb + 768);
@@ -1697,8 +1765,9 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
 #define RK_LAUNCH(GG, MX)                                                                          \
   do {                                                                                             \
     rc = plan_for<GG>(rok4e_integrate_kernel<GG, MX>, mech, P.S, o.cells_per_block, ncell, true, &plan, \
-                      o.blocks_per_sm);                                                            \
+                      o.blocks_per_sm, order == 3);                                                \
     if (rc) return rc;                                                                             \
+    if (order == 3) P.subq = plan.cells_per_block % 4 == 0 ? 4 : (plan.cells_per_block % 2 == 0 ? 2 : 1); \
     rok4e_integrate_kernel<GG, MX><<<plan.blocks, plan.cells_per_block * GG, plan.smem, stream>>>(P); \
   } while (0)
   if (G == 32) {

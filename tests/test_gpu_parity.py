@@ -178,6 +178,31 @@ def test_lanes_per_cell_variants_agree(rk, lanes):
     _assert_state_close(b, a, mech.n_species, f"G={lanes}")
 
 
+def test_queue_orders_are_bitwise_identical(rk):
+    """Every cell's arithmetic is independent of which warp, block or SM runs
+    it: the interleaved, longest-first and static-bin queues (with several
+    block shapes) give bitwise identical states and carried steps."""
+    from synth.fields import initial_state
+
+    w, mech = _mech("flame1d")
+    U = initial_state(w)[::2]
+    m = rk.mech_load(mech)
+    n = U.shape[0]
+    h0 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    Y0 = torch.tensor(U, device="cuda")
+    rk.rok4e_integrate(m, Y0, w.dt, w.rtol, w.atol, 4, h_cell=h0)  # carried steps for the cost order
+    outs = []
+    for order, cpb, bps in [(1, 4, 0), (2, 4, 0), (3, 4, 0), (3, 16, 1), (3, 6, 0), (3, 8, 2)]:
+        Y = Y0.clone()
+        hc = h0.clone()
+        rk.rok4e_integrate(m, Y, w.dt, w.rtol, w.atol, 4, h_cell=hc,
+                           opts=rk.Opts(queue_order=order, cells_per_block=cpb, blocks_per_sm=bps))
+        torch.cuda.synchronize()
+        outs.append((Y.cpu(), hc.cpu()))
+    for Y, hc in outs[1:]:
+        assert torch.equal(Y, outs[0][0]) and torch.equal(hc, outs[0][1])
+
+
 def test_steady_state_is_bit_exact(rk):
     from synth.fields import initial_state
 
