@@ -173,9 +173,10 @@ def cpu_oracle_sample(w, mech, U, cells):
     dx = LENGTH / npts
     n_cells = len(cells)
     t0 = time.perf_counter()
-    osp.simpler_split_step_1d(kin, U, P_ATM, w.dt, D_DIFF, dx, w.rtol, w.atol, w.krylov_dim, cells=cells)
+    _, _, _, U_react = osp.simpler_split_step_1d(kin, U, P_ATM, w.dt, D_DIFF, dx, w.rtol, w.atol, w.krylov_dim,
+                                                 cells=cells)
     dt = time.perf_counter() - t0
-    return n_cells / dt, dt
+    return n_cells / dt, dt, U_react
 
 
 def run_reference(args, rank, world):
@@ -189,7 +190,7 @@ def run_reference(args, rank, world):
     t_total = 0.0
     cells_total = 0
     for k in range(args.steps):
-        _, dt = cpu_oracle_sample(w, mech, U, stratified_cells(npts, per_step, k))
+        _, dt, _ = cpu_oracle_sample(w, mech, U, stratified_cells(npts, per_step, k))
         t_total += dt
         cells_total += per_step
     value = cells_total / t_total
@@ -402,7 +403,26 @@ def run_ours(args, rank, world, local_rank):
     bad = int((st[:, :, 3] != 0).sum())
 
     # ---- CPU baseline: the oracle on a bounded sample of the initial field
-    cpu_v, cpu_t = cpu_oracle_sample(w, mech, U0, stratified_cells(npts, args.cpu_cells))
+    cells = stratified_cells(npts, args.cpu_cells)
+    cpu_v, cpu_t, U_react_ref = cpu_oracle_sample(w, mech, U0, cells)
+    # accuracy on the same sample: the GPU's reaction sub-step of the first
+    # split step (constant source T(U_n)) against the oracle's, both running
+    # their own adaptive step sequences from h = dt
+    Ug = torch.tensor(U0, device=dev)
+    Yr = Ug.clone()
+    rk.rok4e_integrate(m, Yr, w.dt, w.rtol, w.atol, M, src=rk.diffusion_1d(Ug, D_DIFF, dx),
+                       opts=rk.Opts(precision=PREC[args.precision]))
+    Yr = Yr.cpu().numpy()[cells]
+    Rr = U_react_ref[cells]
+    ns = mech.n_species
+    dY = np.abs(Yr[:, :ns] - Rr[:, :ns])
+    dT = np.abs(Yr[:, ns] - Rr[:, ns])
+    accuracy = {"vs": "FP64 oracle, reaction sub-step of the first split step, free-running step sequences",
+                "cells": len(cells), "max_abs_dY": float(dY.max()),
+                "max_rel_dY_where_Y_gt_1e-8": float((dY / np.maximum(np.abs(Rr[:, :ns]), 1e-8)).max()),
+                "max_abs_dT_K": float(dT.max()),
+                "within_1e-8_plus_1e-6Y_and_1e-6K": bool(np.all(dY <= 1e-8 + 1e-6 * np.abs(Rr[:, :ns]))
+                                                         and np.all(dT <= 1e-6))}
 
     clocks = clk.summary()
     line = {
@@ -422,6 +442,7 @@ def run_ours(args, rank, world, local_rank):
                      "peak_probe_fp64": peak_meas, "frac_of_probe": achieved / peak_meas,
                      "exp_flops_counted": EXP_FLOPS, "cuda_exp_cost_fma_measured": exp_fma,
                      "algorithmic_tflop_per_step": flops / args.steps / 1e12},
+        "accuracy": accuracy,
         "cpu_baseline": {"value": cpu_v, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
                          "sample": f"{args.cpu_cells} cells spread over the grid (golden-ratio sequence), one "
                                    f"split step of the initial field ({cpu_t:.1f} s)"},
