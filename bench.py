@@ -281,6 +281,77 @@ def run_batched(args, rank, world, local_rank):
     return 0
 
 
+def run_study(args, local_rank):
+    """Efficiency study (Sec. 4.4's comparison on GPU): integrate 1024 cells of
+    the batched workload's field (53 species / 325 reactions) over 1e-5 s in
+    splitting intervals h_CFL in {1e-9 .. 1e-5} s, carrying each cell's step
+    across intervals, with ROK4E M = 4, 6, 8 (analytic J v), ROK4E M = 4 with
+    finite-difference J v, and the explicit Dormand-Prince 5(4) pair, all at
+    rtol 1e-4, atol 1e-8.  Error: relative temperature error at 1e-5 s against
+    a tight-tolerance reference (ROK4E M = 8, rtol 1e-10, atol 1e-14, checked
+    against Dormand-Prince at the same tolerances).  One JSON line per case."""
+    import torch
+
+    import paper_1712_00953_gb300 as rk
+    from synth.fields import WORKLOADS, initial_state, mechanism_for
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = WORKLOADS["batched"]
+    mech = mechanism_for(w)
+    m = rk.mech_load(mech)
+    n = 1024
+    U_all = initial_state(w, n_cells=1 << 16)
+    U0 = torch.tensor(U_all[np.linspace(0, U_all.shape[0] - 1, n).astype(np.int64)], device=dev)
+    ns = mech.n_species
+    T_END = 1e-5
+    rtol, atol = 1e-4, 1e-8
+    st = torch.zeros(n, 4, dtype=torch.int32, device=dev)
+
+    def run(method, M, h_cfl, rt, at, jv_mode=0):
+        Y = U0.clone()
+        hc = torch.zeros(n, dtype=torch.float64, device=dev)
+        tot = np.zeros(4, dtype=np.int64)
+        ws = torch.empty(rk.rok4e_workspace_size(m, n, M), dtype=torch.uint8, device=dev)
+        o = rk.Opts(jv_mode=jv_mode)
+        n_int = int(round(T_END / h_cfl))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(n_int):
+            if method == "rkdp":
+                rk.rkdp_integrate(m, Y, h_cfl, rt, at, h_cell=hc, opts=o, stats=st, workspace=ws)
+            else:
+                rk.rok4e_integrate(m, Y, h_cfl, rt, at, M, h_cell=hc, opts=o, stats=st, workspace=ws)
+            if n_int <= 100:
+                tot += st.sum(dim=0).cpu().numpy()
+        e1.record()
+        torch.cuda.synchronize()
+        return Y, e0.elapsed_time(e1) * 1e-3, tot, n_int
+
+    ref, t_ref, _, _ = run("rok4e", 8, 1e-6, 1e-10, 1e-14)
+    ref_dp, _, _, _ = run("rkdp", 1, 1e-6, 1e-10, 1e-14)
+    Tref = ref[:, ns]
+    ref_check = float(((ref_dp[:, ns] - Tref).abs() / Tref).max())
+    cases = [("rok4e", 4, 0), ("rok4e", 6, 0), ("rok4e", 8, 0), ("rok4e", 4, 1), ("rkdp", 1, 0)]
+    for h_cfl in (1e-9, 1e-8, 1e-7, 1e-6, 1e-5):
+        for method, M, jv in cases:
+            Y, t, tot, n_int = run(method, M, h_cfl, rtol, atol, jv)
+            rel = ((Y[:, ns] - Tref).abs() / Tref).cpu().numpy()
+            name = "RKDP" if method == "rkdp" else f"ROK4E M={M}" + (" FD J v" if jv else "")
+            line = {"study": "efficiency", "method": name, "h_cfl_s": h_cfl, "intervals": n_int,
+                    "cells": n, "horizon_s": T_END, "rtol": rtol, "atol": atol,
+                    "gpu_s": t, "gpu_us_per_cell": t / n * 1e6,
+                    "T_rel_err_max": float(rel.max()), "T_rel_err_mean": float(rel.mean()),
+                    "reference": "ROK4E M=8 rtol 1e-10 atol 1e-14",
+                    "reference_vs_rkdp_T_rel": ref_check}
+            if n_int <= 100:
+                line.update({"attempts_per_cell": float((tot[0] + tot[1]) / n), "rhs_per_cell": float(tot[2] / n),
+                             "failed": int(tot[3] != 0)})
+            print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -474,6 +545,8 @@ def main():
     ap.add_argument("--cells-per-block", type=int, default=8, help="cells per block (0: library default)")
     ap.add_argument("--precision", default="fp64", choices=list(PREC))
     ap.add_argument("--queue-order", type=int, default=3, help="0 auto, 1 interleaved, 2 longest first, 3 static balanced bins")
+    ap.add_argument("--study", default="", choices=["", "efficiency"],
+                    help="efficiency: the ROK4E M / J v mode / explicit RK comparison over h_CFL")
     ap.add_argument("--workload", default="flame1d", choices=["flame1d", "batched"],
                     help="flame1d: the benchmark line; batched: the 2^20-cell throughput measurement")
     ap.add_argument("--blocks-per-sm", type=int, default=0, help="resident blocks per SM (0: all that fit)")
@@ -487,6 +560,8 @@ def main():
         return run_reference(args, rank, world)
     if args.plain_steps > 0:
         return run_plain(args)
+    if args.study == "efficiency":
+        return run_study(args, local_rank)
     if args.workload == "batched":
         return run_batched(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)

@@ -213,15 +213,29 @@ size_t rk_rok4e_workspace_size(const rk_mech* mech, int64_t ncell, int32_t krylo
  *            evaluations, status (RK_CELL_*); or NULL
  *  workspace device memory of rk_rok4e_workspace_size bytes
  * Cells are independent; one persistent launch processes them from a shared
- * work queue.  When h_cell is given (and steps are adaptive) the queue hands
- * out cells longest-expected-first, the expected substep count being dt/h_cell
- * binned on a quarter-octave log scale; otherwise it interleaves the cell
- * index so that neighbouring cells spread over the SMs.  The order changes
- * only the schedule: each cell's result is the same bits either way. */
+ * work queue (opts->queue_order).  By default, when h_cell is given and steps
+ * are adaptive, cells are sorted longest-expected-first (expected substeps
+ * dt/h_cell, binned on a quarter-octave log scale) and dealt to fixed
+ * per-block bins; otherwise the queue interleaves the cell index so that
+ * neighbouring cells spread over the SMs.  The order changes only the
+ * schedule: each cell's result is the same bits either way. */
 int rk_rok4e_integrate(const rk_mech* mech, double* Y, const double* src, double* h_cell,
                        int64_t ncell, double p, double dt, double rtol, double atol,
                        int32_t krylov_dim, const rk_opts* opts, int32_t* stats, void* workspace,
                        size_t workspace_bytes, void* stream);
+
+/* Integrate every cell over [0, dt] with the explicit Dormand-Prince 5(4) pair,
+ * the explicit reference method of the efficiency comparison (Sec. 4.4; the
+ * paper's RKDP of order 5): seven stages, the 5th-order solution propagated,
+ * the embedded 4th-order one for the error, first-same-as-last (6 RHS per
+ * attempt).  Error norm as in rk_rok4e_integrate; step control
+ * h* = h min(5, max(0.2, 0.9 err^(-1/5))).  Arguments, opts, stats, the work
+ * queue and the workspace (rk_rok4e_workspace_size with krylov_dim 1) are
+ * those of rk_rok4e_integrate; opts->precision must be 0 and jv_mode is
+ * ignored.  Returns RK_E_INVALID_ARGUMENT on bad arguments. */
+int rk_rkdp_integrate(const rk_mech* mech, double* Y, const double* src, double* h_cell, int64_t ncell,
+                      double p, double dt, double rtol, double atol, const rk_opts* opts,
+                      int32_t* stats, void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---- Simpler balanced splitting of a 1-D reaction-diffusion system -----------
  * One step of Eq. simpler_balanced on a uniform 1-D grid of npts cells with

@@ -28,7 +28,7 @@ def _L():
     return _LIB
 
 __all__ = ["Mechanism", "mech_load", "mech_validate", "chem_rhs", "chem_rhs_mixed", "chem_rhs_cv", "chem_jvp_cv",
-           "chem_jvp", "rok4e_integrate",
+           "chem_jvp", "rok4e_integrate", "rkdp_integrate",
            "rok4e_workspace_size", "simpler_split_step", "simpler_split_step_workspace_size",
            "diffusion_1d", "probe_throughput", "eval_exp", "split_step", "SCHEMES", "rok4e_fixed_steps",
            "rok4e_adjoint", "FixedStepROK4E", "Opts", "RokError", "STATS_FIELDS"]
@@ -217,6 +217,22 @@ def rok4e_integrate(m: Mechanism, Y, dt, rtol, atol, krylov_dim=4, *, p=101325.0
                                    _dptr(stats, "stats", 4 * n, torch.int32),
                                    _dptr(workspace, "workspace", dtype=torch.uint8), workspace.numel(),
                                    _stream_ptr(stream)), "rk_rok4e_integrate")
+    return Y
+
+
+def rkdp_integrate(m: Mechanism, Y, dt, rtol, atol, *, p=101325.0, src=None, h_cell=None,
+                   opts: Opts | None = None, stats=None, workspace=None, stream=None):
+    """Integrate every row of Y over dt in place with the explicit Dormand-Prince
+    5(4) pair (rk_rkdp_integrate)."""
+    n = _ncell(Y, m)
+    oc = (opts or Opts()).c()
+    if workspace is None:
+        workspace = torch.empty(rok4e_workspace_size(m, n, 1, opts), dtype=torch.uint8, device=Y.device)
+    _check(_L().rk_rkdp_integrate(m.handle, _dptr(Y, "Y"), _dptr(src, "src", Y.numel()),
+                                  _dptr(h_cell, "h_cell", n), n, float(p), float(dt), float(rtol), float(atol),
+                                  ctypes.byref(oc), _dptr(stats, "stats", 4 * n, torch.int32),
+                                  _dptr(workspace, "workspace", dtype=torch.uint8), workspace.numel(),
+                                  _stream_ptr(stream)), "rk_rkdp_integrate")
     return Y
 
 

@@ -1308,20 +1308,10 @@ __device__ inline void init_sentinels(const SlotPtrs& s, int ns, int lane) {
   }
 }
 
-template <int G, bool MIXED>
-__global__ void __launch_bounds__(512) rok4e_integrate_kernel(IntegrateParams P) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  load_exp_table(reinterpret_cast<double*>(smem));
-  load_mech(smem + EXP_TAB_BYTES, P.mech, P.L.bytes);
-  __syncthreads();
-  MechView m = make_view(smem + EXP_TAB_BYTES, P.L);
-  m.etab = reinterpret_cast<const double*>(smem);
-  const Grp<G> g;
-  const int gid = threadIdx.x / G;
-  double* base = reinterpret_cast<double*>(smem + EXP_TAB_BYTES + P.L.bytes) + (size_t)gid * P.S.stride;
-  const SlotPtrs s = slot_ptrs(base, P.S);
-  init_sentinels<MIXED>(s, m.ns, g.lane);
-  g.sync();
+// Hand cells to the warp groups of a persistent launch until the queue is
+// empty, calling body(cell) for each.
+template <int G, class Body>
+__device__ __forceinline__ void drain_queue(const IntegrateParams& P, const Grp<G>& g, int gid, Body&& body) {
   if (P.subq > 0) {
     // Static bins: the queue (longest expected first) is dealt out in snake
     // order over nb = gridDim.x * subq bins, bin k = sub * gridDim.x + block,
@@ -1342,7 +1332,7 @@ __global__ void __launch_bounds__(512) rok4e_integrate_kernel(IntegrateParams P)
       if (q >= (unsigned long long)P.ncell) break;
       const unsigned long long cell =
           P.order ? (unsigned long long)P.order[q] : (q * P.qstride) % (unsigned long long)P.ncell;
-      integrate_cell<G, MIXED>(m, s, P, (int64_t)cell);
+      body((int64_t)cell);
     }
     return;
   }
@@ -1355,8 +1345,190 @@ __global__ void __launch_bounds__(512) rok4e_integrate_kernel(IntegrateParams P)
     // hot side of a flame) spread over all SMs instead of filling a few.
     const unsigned long long cell =
         P.order ? (unsigned long long)P.order[q] : (q * P.qstride) % (unsigned long long)P.ncell;
-    integrate_cell<G, MIXED>(m, s, P, (int64_t)cell);
+    body((int64_t)cell);
   }
+}
+
+template <int G, bool MIXED>
+__global__ void __launch_bounds__(512) rok4e_integrate_kernel(IntegrateParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  load_exp_table(reinterpret_cast<double*>(smem));
+  load_mech(smem + EXP_TAB_BYTES, P.mech, P.L.bytes);
+  __syncthreads();
+  MechView m = make_view(smem + EXP_TAB_BYTES, P.L);
+  m.etab = reinterpret_cast<const double*>(smem);
+  const Grp<G> g;
+  const int gid = threadIdx.x / G;
+  double* base = reinterpret_cast<double*>(smem + EXP_TAB_BYTES + P.L.bytes) + (size_t)gid * P.S.stride;
+  const SlotPtrs s = slot_ptrs(base, P.S);
+  init_sentinels<MIXED>(s, m.ns, g.lane);
+  g.sync();
+  drain_queue<G>(P, g, gid, [&](int64_t cell) { integrate_cell<G, MIXED>(m, s, P, cell); });
+}
+
+// ------------------------------------------- explicit Dormand-Prince 5(4)
+// The explicit reference integrator of the efficiency study (Sec. 4.4):
+// seven stages, the 5th-order solution propagated, the embedded 4th-order
+// one for the error (J. R. Dormand and P. J. Prince, J. Comput. Appl. Math.
+// 6 (1980) 19-26), first-same-as-last; the same RMS error norm as ROK4E and
+// the elementary controller h* = h min(5, max(0.2, 0.9 err^-1/5)).
+namespace dp {
+constexpr double A21 = 1.0 / 5.0;
+constexpr double A31 = 3.0 / 40.0, A32 = 9.0 / 40.0;
+constexpr double A41 = 44.0 / 45.0, A42 = -56.0 / 15.0, A43 = 32.0 / 9.0;
+constexpr double A51 = 19372.0 / 6561.0, A52 = -25360.0 / 2187.0, A53 = 64448.0 / 6561.0, A54 = -212.0 / 729.0;
+constexpr double A61 = 9017.0 / 3168.0, A62 = -355.0 / 33.0, A63 = 46732.0 / 5247.0, A64 = 49.0 / 176.0,
+                 A65 = -5103.0 / 18656.0;
+constexpr double B1 = 35.0 / 384.0, B3 = 500.0 / 1113.0, B4 = 125.0 / 192.0, B5 = -2187.0 / 6784.0,
+                 B6 = 11.0 / 84.0;
+// b - bhat (b2 = bhat2 = 0, b7 = 0)
+constexpr double E1 = 35.0 / 384.0 - 5179.0 / 57600.0, E3 = 500.0 / 1113.0 - 7571.0 / 16695.0,
+                 E4 = 125.0 / 192.0 - 393.0 / 640.0, E5 = -2187.0 / 6784.0 + 92097.0 / 339200.0,
+                 E6 = 11.0 / 84.0 - 187.0 / 2100.0, E7 = -1.0 / 40.0;
+constexpr double SAFETY = 0.9;
+}  // namespace dp
+
+template <int G>
+__device__ void integrate_cell_rkdp(const MechView& m, const SlotPtrs& s, const IntegrateParams& P, int64_t cell) {
+  const Grp<G> g;
+  const int ns = m.ns, N = ns + 1, Nq = s.Nq;
+  for (int e = g.lane; e < N; e += G) {
+    s.u[e] = P.Y[cell * N + e];
+    s.src[e] = P.src ? P.src[cell * N + e] : 0.0;
+  }
+  g.sync();
+  const double* srcp = P.src ? s.src : nullptr;
+  const bool fixed = P.fixed_h > 0.0;
+  const double pr = P.rho_cell ? -P.rho_cell[cell] : P.p;
+  const double dt = P.dt;
+  double h = P.h0 > 0.0 ? P.h0 : dt;
+  if (P.h_cell) {
+    const double hc = P.h_cell[cell];
+    if (hc > 0.0) h = hc;
+  }
+  if (fixed) h = P.fixed_h;
+  const long long n_fixed = fixed ? llround(dt / P.fixed_h) : 0;
+  double t = 0.0, h_last = h;
+  int n_acc = 0, n_rej = 0, n_rhs = 0, status = RK_CELL_OK, n_att = 0;
+  CellScalars cs;
+  cs.pinv = 1.0 / fabs(pr);
+  // stage vectors k1..k7; k1 and k7 swap roles after an accepted step
+  double* k1 = s.fn;
+  double* k2 = s.K;
+  double* k3 = s.K + Nq;
+  double* k4 = s.K + 2 * Nq;
+  double* k5 = s.K + 3 * Nq;
+  double* k6 = s.F;
+  double* k7 = s.w;
+  rhs_eval<G>(m, s, s.u, srcp, pr, k1, false, &cs);
+  n_rhs += 1;
+  while (true) {
+    if (fixed) {
+      if (n_acc >= n_fixed) break;
+    } else if (dt - t <= T_END_TOL * dt) {
+      break;
+    }
+    if (n_att >= P.max_attempts) {
+      status = RK_CELL_MAX_ATTEMPTS;
+      break;
+    }
+    if (!fixed) h = fmin(h, dt - t);
+    for (int i = 1; i < 7; ++i) {
+      for (int e = g.lane; e < N; e += G) {
+        double acc;
+        if (i == 1) acc = dp::A21 * k1[e];
+        else if (i == 2) acc = fma(dp::A32, k2[e], dp::A31 * k1[e]);
+        else if (i == 3) acc = fma(dp::A43, k3[e], fma(dp::A42, k2[e], dp::A41 * k1[e]));
+        else if (i == 4) acc = fma(dp::A54, k4[e], fma(dp::A53, k3[e], fma(dp::A52, k2[e], dp::A51 * k1[e])));
+        else if (i == 5)
+          acc = fma(dp::A65, k5[e], fma(dp::A64, k4[e], fma(dp::A63, k3[e], fma(dp::A62, k2[e], dp::A61 * k1[e]))));
+        else  // a_7j = b_j: the last argument is the 5th-order solution
+          acc = fma(dp::B6, k6[e], fma(dp::B5, k5[e], fma(dp::B4, k4[e], fma(dp::B3, k3[e], dp::B1 * k1[e]))));
+        s.arg[e] = fma(h, acc, s.u[e]);
+      }
+      g.sync();
+      double* out = i == 1 ? k2 : i == 2 ? k3 : i == 3 ? k4 : i == 4 ? k5 : i == 5 ? k6 : k7;
+      rhs_eval<G>(m, s, s.arg, srcp, pr, out, false, &cs);
+      n_rhs += 1;
+    }
+    double part = 0.0;
+    int bad = 0;
+    for (int e = g.lane; e < N; e += G) {
+      const double us = s.arg[e];
+      const double d = h * fma(dp::E7, k7[e], fma(dp::E6, k6[e], fma(dp::E5, k5[e], fma(dp::E4, k4[e],
+                                                                                   fma(dp::E3, k3[e], dp::E1 * k1[e])))));
+      const double r = d / fma(P.rtol, fabs(us), P.atol);
+      part = fma(r, r, part);
+      bad |= (__double2hiint(us) & 0x7ff00000) == 0x7ff00000;
+    }
+    const double err = sqrt(g.sum(part) * (1.0 / N));
+    bad = g.any(bad);
+    const int att = n_att;
+    n_att += 1;
+    bool accept;
+    double hnew;
+    if (fixed) {
+      accept = true;
+      hnew = h;
+    } else {
+      const bool fin = (__double2hiint(err) & 0x7ff00000) != 0x7ff00000;
+      double fac = FAC_MIN;
+      if (fin) fac = fmin(FAC_MAX, fmax(FAC_MIN, dp::SAFETY * exp_fast(-0.2 * log(fmax(err, ERR_FLOOR)), m.etab)));
+      hnew = h * fac;
+      accept = fin && err <= 1.0;
+    }
+    if (P.trace && att < P.trace_cap && g.lane == 0) P.trace[cell * P.trace_cap + att] = accept ? h : -h;
+    if (accept) {
+      if (bad) {
+        status = RK_CELL_NONFINITE;
+        break;
+      }
+      for (int e = g.lane; e < N; e += G) s.u[e] = s.arg[e];
+      g.sync();
+      double* tk = k1;  // first same as last: f(u_{n+1}) is k7
+      k1 = k7;
+      k7 = tk;
+      t += h;
+      n_acc += 1;
+      h_last = hnew;
+      h = hnew;
+    } else {
+      n_rej += 1;
+      h = hnew;
+      if (h < H_MIN_FRAC * dt) {
+        status = RK_CELL_STEP_UNDERFLOW;
+        break;
+      }
+    }
+  }
+  for (int e = g.lane; e < N; e += G) P.Y[cell * N + e] = s.u[e];
+  if (g.lane == 0) {
+    if (P.h_cell) P.h_cell[cell] = h_last;
+    if (P.stats) {
+      P.stats[4 * cell + 0] = n_acc;
+      P.stats[4 * cell + 1] = n_rej;
+      P.stats[4 * cell + 2] = n_rhs;
+      P.stats[4 * cell + 3] = status;
+    }
+  }
+  g.sync();
+}
+
+template <int G>
+__global__ void __launch_bounds__(512) rkdp_integrate_kernel(IntegrateParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  load_exp_table(reinterpret_cast<double*>(smem));
+  load_mech(smem + EXP_TAB_BYTES, P.mech, P.L.bytes);
+  __syncthreads();
+  MechView m = make_view(smem + EXP_TAB_BYTES, P.L);
+  m.etab = reinterpret_cast<const double*>(smem);
+  const Grp<G> g;
+  const int gid = threadIdx.x / G;
+  double* base = reinterpret_cast<double*>(smem + EXP_TAB_BYTES + P.L.bytes) + (size_t)gid * P.S.stride;
+  const SlotPtrs s = slot_ptrs(base, P.S);
+  init_sentinels<false>(s, m.ns, g.lane);
+  g.sync();
+  drain_queue<G>(P, g, gid, [&](int64_t cell) { integrate_cell_rkdp<G>(m, s, P, cell); });
 }
 
 }  // namespace rk
@@ -1681,9 +1853,10 @@ int check_mech(const rk_mech* mech) {
   return RK_OK;
 }
 
+// method 0: ROK4E; 1: explicit Dormand-Prince 5(4) (M unused)
 int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_cell, int64_t ncell, double p,
                    double dt, double rtol, double atol, int32_t M, const rk_opts* opts, int32_t* stats,
-                   void* workspace, size_t workspace_bytes, cudaStream_t stream) {
+                   void* workspace, size_t workspace_bytes, cudaStream_t stream, int method = 0) {
   int rc = check_mech(mech);
   if (rc) return rc;
   if (ncell < 0) return set_error(RK_E_INVALID_ARGUMENT, "ncell < 0");
@@ -1702,13 +1875,14 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
     return set_error(RK_E_INVALID_ARGUMENT, "trace_cap > 0 needs a trace array");
   if (o.fixed_h < 0.0 || !isfinite(o.fixed_h)) return set_error(RK_E_INVALID_ARGUMENT, "fixed_h must be >= 0");
   if (o.precision < 0 || o.precision > 2) return set_error(RK_E_INVALID_ARGUMENT, "precision must be 0, 1 or 2");
+  if (method == 1 && o.precision != 0) return set_error(RK_E_INVALID_ARGUMENT, "the explicit integrator is FP64 only");
   const bool mixed = o.precision >= 1;
   const int G = o.lanes_per_cell == 0 ? 32 : o.lanes_per_cell;
   if (G != 8 && G != 16 && G != 32) return set_error(RK_E_INVALID_ARGUMENT, "lanes_per_cell must be 0, 8, 16 or 32");
   if (!workspace || workspace_bytes < rk_rok4e_workspace_size(mech, ncell, M, opts))
     return set_error(RK_E_WORKSPACE, "workspace missing or smaller than rk_rok4e_workspace_size");
   const int N = mech->host.L.ns + 1;
-  const int Meff = M > N ? N : M;
+  const int Meff = method == 1 ? 1 : (M > N ? N : M);
   IntegrateParams P;
   P.mech = mech->dev;
   P.L = mech->host.L;
@@ -1770,7 +1944,19 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
     if (order == 3) P.subq = plan.cells_per_block % 4 == 0 ? 4 : (plan.cells_per_block % 2 == 0 ? 2 : 1); \
     rok4e_integrate_kernel<GG, MX><<<plan.blocks, plan.cells_per_block * GG, plan.smem, stream>>>(P); \
   } while (0)
-  if (G == 32) {
+#define RK_LAUNCH_DP(GG)                                                                              \
+  do {                                                                                                \
+    rc = plan_for<GG>(rkdp_integrate_kernel<GG>, mech, P.S, o.cells_per_block, ncell, true, &plan,    \
+                      o.blocks_per_sm, order == 3);                                                   \
+    if (rc) return rc;                                                                                \
+    if (order == 3) P.subq = plan.cells_per_block % 4 == 0 ? 4 : (plan.cells_per_block % 2 == 0 ? 2 : 1); \
+    rkdp_integrate_kernel<GG><<<plan.blocks, plan.cells_per_block * GG, plan.smem, stream>>>(P);      \
+  } while (0)
+  if (method == 1) {
+    if (G == 32) RK_LAUNCH_DP(32);
+    else if (G == 16) RK_LAUNCH_DP(16);
+    else RK_LAUNCH_DP(8);
+  } else if (G == 32) {
     if (mixed) RK_LAUNCH(32, true);
     else RK_LAUNCH(32, false);
   } else if (G == 16) {
@@ -1781,6 +1967,7 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
     else RK_LAUNCH(8, false);
   }
 #undef RK_LAUNCH
+#undef RK_LAUNCH_DP
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "rok4e_integrate_kernel launch");
   if (o.ev_end) {
@@ -1917,6 +2104,13 @@ int rk_rok4e_integrate(const rk_mech* mech, double* Y, const double* src, double
                        int32_t* stats, void* workspace, size_t workspace_bytes, void* stream) {
   return integrate_impl(mech, Y, src, h_cell, ncell, p, dt, rtol, atol, krylov_dim, opts, stats, workspace,
                         workspace_bytes, (cudaStream_t)stream);
+}
+
+int rk_rkdp_integrate(const rk_mech* mech, double* Y, const double* src, double* h_cell, int64_t ncell, double p,
+                      double dt, double rtol, double atol, const rk_opts* opts, int32_t* stats, void* workspace,
+                      size_t workspace_bytes, void* stream) {
+  return integrate_impl(mech, Y, src, h_cell, ncell, p, dt, rtol, atol, 1, opts, stats, workspace, workspace_bytes,
+                        (cudaStream_t)stream, 1);
 }
 
 size_t rk_simpler_split_step_workspace_size(const rk_mech* mech, int64_t npts, int32_t krylov_dim,
