@@ -185,10 +185,39 @@ typedef struct rk_opts {
   int32_t reactor;        /* 0 constant pressure (p, default); 1 constant volume: each
                              cell keeps the density rho_cell[c] (kg/m^3) and the
                              temperature equation uses internal energies and c_v
-                             (Eq. cv_reactor); p is then unused */
+                             (Eq. cv_reactor); p is then unused.  2 conservative
+                             variables with an auxiliary temperature (Eq.
+                             chemical_source_balanced, see rk_chem_rhs_aux): rows of
+                             N = n_species + 1 + RK_AUX_EXTRA values; FP64 only, and
+                             only for rk_rok4e_integrate / rk_rkdp_integrate */
   int32_t reserved1;
   const double* rho_cell; /* device [ncell], read when reactor == 1 */
 } rk_opts;
+
+/* ---- Auxiliary-temperature reaction system (compressible coupling) ----------
+ * Eq. chemical_source_balanced: the reaction sub-step of a compressible solver
+ * integrates the conservative variables with a constant balancing term T_n and
+ * an auxiliary temperature used only for thermochemistry,
+ *   d/dt [U; T] = [R(U, T) + T_n; w_T],
+ *   w_T = (-sum_k e_k d(rho Y_k)/dt + |v|^2/2 d(rho)/dt - v . d(rho v)/dt
+ *          + d(rho E)/dt) / (rho c_v)                     (Eq. aux_t_equation)
+ * with the specific internal energies e_k = h_k - R T / W_k (the printed
+ * equation writes h_k; the energy identity rho E = sum_k rho Y_k e_k +
+ * rho |v|^2 / 2 that the equation differentiates needs e_k).  The chemical
+ * source R is W_k w_k in the species components and zero in mass, momentum
+ * and total energy.  Row layout (SI): [rho Y_1 .. rho Y_Ns, T, rho,
+ * rho v_x, rho v_y, rho v_z, rho E], N = Ns + 1 + RK_AUX_EXTRA; concentrations
+ * are (rho Y_k) / W_k. */
+#define RK_AUX_EXTRA 5
+
+/* dU/dt of the auxiliary-temperature system for ncell rows (device arrays
+ * [ncell x N], src = the balancing constants T_n or NULL; out must not alias
+ * U).  rk_chem_jvp_aux: J V at U with the same src (mode 0 analytic, 1 forward
+ * difference as in rk_chem_jvp). */
+int rk_chem_rhs_aux(const rk_mech* mech, const double* U, const double* src, double* dUdt, int64_t ncell,
+                    void* stream);
+int rk_chem_jvp_aux(const rk_mech* mech, const double* U, const double* src, const double* V, double* JV,
+                    int64_t ncell, int32_t mode, void* stream);
 
 /* Bytes of workspace rk_rok4e_integrate needs: a work-queue counter, a
  * histogram and the queue order (768 bytes + 4 bytes per cell, rounded). */

@@ -28,7 +28,7 @@ def _L():
     return _LIB
 
 __all__ = ["Mechanism", "mech_load", "mech_validate", "chem_rhs", "chem_rhs_mixed", "chem_rhs_cv", "chem_jvp_cv",
-           "chem_jvp", "rok4e_integrate", "rkdp_integrate",
+           "chem_jvp", "rok4e_integrate", "rkdp_integrate", "chem_rhs_aux", "chem_jvp_aux", "AUX_EXTRA",
            "rok4e_workspace_size", "simpler_split_step", "simpler_split_step_workspace_size",
            "diffusion_1d", "probe_throughput", "eval_exp", "split_step", "SCHEMES", "rok4e_fixed_steps",
            "rok4e_adjoint", "FixedStepROK4E", "Opts", "RokError", "STATS_FIELDS"]
@@ -129,7 +129,8 @@ class Opts:
     """Integration options (rk_opts); None fields keep the library defaults."""
 
     def __init__(self, jv_mode=0, max_attempts=0, lanes_per_cell=0, cells_per_block=0, h0=0.0, fixed_h=0.0,
-                 trace=None, events=None, precision=0, queue_order=0, blocks_per_sm=0, rho_cell=None):
+                 trace=None, events=None, precision=0, queue_order=0, blocks_per_sm=0, rho_cell=None,
+                 reactor=None):
         self.jv_mode, self.max_attempts = jv_mode, max_attempts
         self.lanes_per_cell, self.cells_per_block = lanes_per_cell, cells_per_block
         self.h0, self.fixed_h = h0, fixed_h
@@ -138,6 +139,9 @@ class Opts:
         self.precision = precision  # 0 FP64, 1 mixed (FP32 nu^T q and inner products), 2 + FP32 J v
         self.queue_order, self.blocks_per_sm = queue_order, blocks_per_sm
         self.rho_cell = rho_cell  # CUDA float64 [ncell]: constant-volume cells of these densities
+        # 0 constant pressure, 1 constant volume (implied by rho_cell), 2 conservative
+        # variables with the auxiliary temperature (rows of n_species + 1 + AUX_EXTRA)
+        self.reactor = reactor if reactor is not None else (0 if rho_cell is None else 1)
 
     def c(self):
         cap = 0 if self.trace is None else int(self.trace.shape[-1])
@@ -148,13 +152,38 @@ class Opts:
         rc = None if self.rho_cell is None else _dptr(self.rho_cell, "rho_cell")
         return RkOpts(self.jv_mode, self.max_attempts, self.lanes_per_cell, self.cells_per_block, self.h0,
                       self.fixed_h, cap, self.precision, tp, eb, ee, self.queue_order, self.blocks_per_sm,
-                      0 if rc is None else 1, 0, rc)
+                      int(self.reactor), 0, rc)
 
 
-def _ncell(Y, m):
-    if Y.dim() != 2 or Y.shape[1] != m.n_state:
-        raise ValueError(f"state must be [ncell, {m.n_state}]")
+AUX_EXTRA = 5  # rho, rho v (3), rho E after T in the auxiliary-temperature rows
+
+
+def _ncell(Y, m, extra=0):
+    if Y.dim() != 2 or Y.shape[1] != m.n_state + extra:
+        raise ValueError(f"state must be [ncell, {m.n_state + extra}]")
     return int(Y.shape[0])
+
+
+def _extra(opts):
+    return AUX_EXTRA if opts is not None and opts.reactor == 2 else 0
+
+
+def chem_rhs_aux(m: Mechanism, U, src=None, out=None, stream=None):
+    """dU/dt of the auxiliary-temperature system (rk_chem_rhs_aux); rows
+    [rho Y (Ns), T, rho, rho v (3), rho E]."""
+    n = _ncell(U, m, AUX_EXTRA)
+    out = torch.empty_like(U) if out is None else out
+    _check(_L().rk_chem_rhs_aux(m.handle, _dptr(U, "U"), _dptr(src, "src", U.numel()),
+                                _dptr(out, "out", U.numel()), n, _stream_ptr(stream)), "rk_chem_rhs_aux")
+    return out
+
+
+def chem_jvp_aux(m: Mechanism, U, V, src=None, mode=0, out=None, stream=None):
+    n = _ncell(U, m, AUX_EXTRA)
+    out = torch.empty_like(U) if out is None else out
+    _check(_L().rk_chem_jvp_aux(m.handle, _dptr(U, "U"), _dptr(src, "src", U.numel()), _dptr(V, "V", U.numel()),
+                                _dptr(out, "out", U.numel()), n, int(mode), _stream_ptr(stream)), "rk_chem_jvp_aux")
+    return out
 
 
 def chem_rhs(m: Mechanism, Y, p, src=None, out=None, stream=None):
@@ -206,7 +235,7 @@ def rok4e_workspace_size(m: Mechanism, ncell: int, krylov_dim: int, opts: Opts |
 def rok4e_integrate(m: Mechanism, Y, dt, rtol, atol, krylov_dim=4, *, p=101325.0, src=None, h_cell=None,
                     opts: Opts | None = None, stats=None, workspace=None, stream=None):
     """Integrate every row of Y over dt in place (rk_rok4e_integrate)."""
-    n = _ncell(Y, m)
+    n = _ncell(Y, m, _extra(opts))
     oc = (opts or Opts()).c()
     if workspace is None:
         nb = rok4e_workspace_size(m, n, krylov_dim, opts)
@@ -224,7 +253,7 @@ def rkdp_integrate(m: Mechanism, Y, dt, rtol, atol, *, p=101325.0, src=None, h_c
                    opts: Opts | None = None, stats=None, workspace=None, stream=None):
     """Integrate every row of Y over dt in place with the explicit Dormand-Prince
     5(4) pair (rk_rkdp_integrate)."""
-    n = _ncell(Y, m)
+    n = _ncell(Y, m, _extra(opts))
     oc = (opts or Opts()).c()
     if workspace is None:
         workspace = torch.empty(rok4e_workspace_size(m, n, 1, opts), dtype=torch.uint8, device=Y.device)

@@ -134,6 +134,7 @@ static int cuda_error(cudaError_t e, const char* where) {
 // ------------------------------------------------------------------- views
 struct MechView {
   int ns, nr, ntb;
+  int nx;  // state components after T: 0, or 5 (rho, rho u, rho E) for the auxiliary-temperature system
   const double* etab;  // 2^(j/128) table in shared memory
   const double *W, *invW, *Tmid, *lo, *hi, *lnA, *bexp, *EaR, *eff, *fo, *csr_nu;
   const uint32_t* slots;
@@ -147,6 +148,7 @@ __host__ __device__ inline MechView make_view(const unsigned char* base, const M
   m.ns = L.ns;
   m.nr = L.nr;
   m.ntb = L.ntb;
+  m.nx = 0;
   m.etab = nullptr;
   m.W = reinterpret_cast<const double*>(base + L.off_W);
   m.invW = reinterpret_cast<const double*>(base + L.off_invW);
@@ -186,9 +188,9 @@ struct SlotLayout {
   int stride;
 };
 
-static SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false) {
+static SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false, int nx = 0) {
   SlotLayout s;
-  s.N = L.ns + 1;
+  s.N = L.ns + 1 + nx;
   s.ns = L.ns;
   s.nr = L.nr;
   s.ntb = L.ntb;
@@ -347,6 +349,9 @@ __device__ __forceinline__ void sum_first(const Grp<G>& g, T (&v)[MAXM], int n) 
 struct CellScalars {
   double T, invT, lnT, S, invS, rho, invrho, cb, invcb, Sh;
   double pinv;  // 1 / p (constant pressure) or 1 / rho (constant volume): set by the caller
+  // auxiliary-temperature system: sum_k (cp_k/R - 1) F_k / W_k, the T row
+  // without its own source, 1 / rho and the velocity
+  double B, fT, irho_c, vel[3];
   bool cv;
 };
 
@@ -451,12 +456,16 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
   S = g.sum(S);
   ghi = g.imax(ghi);
   const bool direct_kc = ghi >= G_OVERFLOW_HI;  // |g/RT| >= 170, also NaN
-  const bool cv = p < 0.0;
+  // auxiliary-temperature system (Eq. chemical_source_balanced): the species
+  // components are rho Y_k, so C_k = u_k / W_k and d(rho Y_k)/dt = W_k w_k:
+  // the constant-volume arithmetic with unit density
+  const bool aux = m.nx > 0;
+  const bool cv = p < 0.0 || aux;
   const double esh = cv ? 1.0 : 0.0;  // h/RT -> u/RT and cp/R -> cv/R shift
   const double invS = 1.0 / S;
   // rho = p / (R T S), 1/rho = R T S / p, with 1/p (or 1/rho) from the caller
-  const double rho = cv ? -p : p * invT * invS * INV_R;
-  const double invrho = cv ? cs->pinv : R_GAS * T * S * cs->pinv;
+  const double rho = aux ? 1.0 : (cv ? -p : p * invT * invS * INV_R);
+  const double invrho = aux ? 1.0 : (cv ? cs->pinv : R_GAS * T * S * cs->pinv);
   // concentrations, Gibbs factors, and (for up to MAXM pressure-dependent
   // reactions) the third-body concentrations [M]_t = sum_k eff_tk C_k
   const bool coop_tb = m.ntb > 0 && m.ntb <= MAXM;
@@ -607,6 +616,7 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
   g.sync();
   // species pass 2: w = nu^T q, dY/dt and the sums of the temperature equation
   double Sh = MIXED ? shq : 0.0, cb = 0.0;
+  double Ax = 0.0, Bx = 0.0;  // auxiliary T: sum (u_k/RT) F_k / W_k and sum (cv_k/R) F_k / W_k
   for (int k = g.lane; k < ns; k += G) {
     double om = 0.0;
     const int e0 = m.csr_ptr[k], e1 = m.csr_ptr[k + 1];
@@ -620,9 +630,14 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     }
     if (cache) s.om[k] = om;
     const double r = __dmul_rn(__dmul_rn(m.W[k], om), invrho);
-    out[k] = src ? __dadd_rn(r, src[k]) : r;
+    const double Fk = src ? __dadd_rn(r, src[k]) : r;
+    out[k] = Fk;
     if (!MIXED) Sh = fma(s.hRT[k] - esh, om, Sh);
     cb = fma(uu[k] * (s.cp[k] - esh), m.invW[k], cb);
+    if (aux) {
+      Ax = fma((s.hRT[k] - 1.0) * Fk, m.invW[k], Ax);
+      Bx = fma((s.cp[k] - 1.0) * Fk, m.invW[k], Bx);
+    }
     if (cache) {
       // per-species factors of the analytic J v, written over arrays the
       // remaining RHS no longer reads (lane-private entries k):
@@ -636,15 +651,46 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
       s.cp[k] = (s.cp[k] - esh) * m.invW[k];
     }
   }
-  {
+  if (aux) {
+    double t4[4] = {Sh, cb, Ax, Bx};
+    sum_many<G, 4>(g, t4);
+    Sh = t4[0];
+    cb = t4[1];
+    Ax = t4[2];
+    Bx = t4[3];
+  } else {
     double t2[2] = {Sh, cb};
     sum_many<G, 2>(g, t2);
     Sh = t2[0];
     cb = t2[1];
   }
   const double invcb = 1.0 / cb;
+  double fT = 0.0;
+  if (aux) {
+    // Eq. aux_t_equation with specific internal energies e_k = (u_k/RT) R T / W_k
+    // and rho c_v = R cb:  w_T = (-R T Ax + |v|^2/2 d(rho)/dt - v . d(rho v)/dt
+    //                              + d(rho E)/dt) / (R cb)
+    const double irc = 1.0 / uu[ns + 1];
+    const double v0 = uu[ns + 2] * irc, v1 = uu[ns + 3] * irc, v2 = uu[ns + 4] * irc;
+    double X = 0.0;
+    if (src) {
+      const double kin = 0.5 * fma(v0, v0, fma(v1, v1, v2 * v2));
+      X = fma(kin, src[ns + 1], src[ns + 5]) - fma(v0, src[ns + 2], fma(v1, src[ns + 3], v2 * src[ns + 4]));
+    }
+    fT = fma(-T, Ax, X * INV_R) * invcb;
+    if (cache) {
+      cs->B = Bx;
+      cs->fT = fT;
+      cs->irho_c = irc;
+      cs->vel[0] = v0;
+      cs->vel[1] = v1;
+      cs->vel[2] = v2;
+    }
+    // d(rho)/dt, d(rho v)/dt, d(rho E)/dt: the balancing constants alone
+    for (int e = ns + 1 + g.lane; e < ns + 1 + m.nx; e += G) out[e] = src ? src[e] : 0.0;
+  }
   if (g.lane == 0) {
-    const double r = -T * Sh * invrho * invcb;
+    const double r = aux ? fT : -T * Sh * invrho * invcb;
     out[ns] = src ? __dadd_rn(r, src[ns]) : r;
   }
   if (cache) {
@@ -729,6 +775,29 @@ __device__ __noinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, cons
     out[k] = s.Einv[k] * fma(-s.om[k], drr, dom);  // Einv: W_k / rho
     dSh = fma(s.gRT[k], dom, fma(s.hRT[k], vT, dSh));
     dcb = fma(s.dcp[k], vT, fma(s.cp[k], v[k], dcb));
+  }
+  if (m.nx > 0) {
+    // auxiliary temperature: d w_T = (-vT B - T sum_k (u_k/RT) dF_k/W_k + dX/R - w_T dcb) / cb,
+    // dF_k = W_k dw_k, X = |v|^2/2 S_rho - v . S_m + S_E, dv = (d(rho v) - v d rho) / rho
+    double D1 = 0.0;
+    for (int k = g.lane; k < ns; k += G) D1 = fma(s.gRT[k], out[k] * m.invW[k], D1);  // gRT: h/RT - 1
+    double t2[2] = {D1, dcb};
+    sum_many<G, 2>(g, t2);
+    D1 = t2[0];
+    dcb = t2[1];
+    if (g.lane == 0) {
+      const double irc = cs.irho_c;
+      const double dv0 = (v[ns + 2] - cs.vel[0] * v[ns + 1]) * irc;
+      const double dv1 = (v[ns + 3] - cs.vel[1] * v[ns + 1]) * irc;
+      const double dv2 = (v[ns + 4] - cs.vel[2] * v[ns + 1]) * irc;
+      const double* S = s.src;  // the cell's balancing constants
+      const double dX = fma(dv0, fma(cs.vel[0], S[ns + 1], -S[ns + 2]),
+                            fma(dv1, fma(cs.vel[1], S[ns + 1], -S[ns + 3]), dv2 * fma(cs.vel[2], S[ns + 1], -S[ns + 4])));
+      out[ns] = (fma(-vT, cs.B, fma(-T, D1, dX * INV_R)) - cs.fT * dcb) * cs.invcb;
+    }
+    for (int e = ns + 1 + g.lane; e < ns + 1 + m.nx; e += G) out[e] = 0.0;
+    g.sync();
+    return;
   }
   {
     double t2[2] = {dSh, dcb};
@@ -844,7 +913,7 @@ __device__ inline void apply_jv(const MechView& m, const SlotPtrs& s, const Cell
                                 double p, double unorm, const double* v, double* out, int* n_rhs,
                                 bool fp32_jv = false) {
   const Grp<G> g;
-  const int N = m.ns + 1;
+  const int N = m.ns + 1 + m.nx;
   if (jv_mode == 0) {
     if (MIXED && fp32_jv) jvp_eval_f32<G>(m, s, s.u, cs, v, out);
     else jvp_eval<G>(m, s, s.u, cs, v, out);
@@ -883,7 +952,7 @@ template <int G, bool MIXED = false>
 __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& cs, int M, int jv_mode,
                        double p, int* n_rhs, bool fp32_jv = false) {
   const Grp<G> g;
-  const int N = m.ns + 1;
+  const int N = m.ns + 1 + m.nx;
   const int Nq = s.Nq;
   if (M > N) M = N;
   for (int i = g.lane; i < MAXM * MAXM; i += G) s.H[i] = 0.0;
@@ -1109,12 +1178,13 @@ struct IntegrateParams {
   const int32_t* order;        // or, when set, cell order[q] (longest expected first)
   int subq;                    // > 0: static bins, subq sub-queues per block (queue order 3)
   const double* rho_cell;      // constant-volume densities, or null (constant pressure)
+  int nx;                      // state components after T (5: auxiliary-temperature system)
 };
 
 template <int G, bool MIXED>
 __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const IntegrateParams& P, int64_t cell) {
   const Grp<G> g;
-  const int ns = m.ns, N = ns + 1, Nq = s.Nq;
+  const int ns = m.ns, N = ns + 1 + m.nx, Nq = s.Nq;
   for (int e = g.lane; e < N; e += G) {
     s.u[e] = P.Y[cell * N + e];
     s.src[e] = P.src ? P.src[cell * N + e] : 0.0;
@@ -1357,6 +1427,7 @@ __global__ void __launch_bounds__(512) rok4e_integrate_kernel(IntegrateParams P)
   __syncthreads();
   MechView m = make_view(smem + EXP_TAB_BYTES, P.L);
   m.etab = reinterpret_cast<const double*>(smem);
+  m.nx = P.nx;
   const Grp<G> g;
   const int gid = threadIdx.x / G;
   double* base = reinterpret_cast<double*>(smem + EXP_TAB_BYTES + P.L.bytes) + (size_t)gid * P.S.stride;
@@ -1391,7 +1462,7 @@ constexpr double SAFETY = 0.9;
 template <int G>
 __device__ void integrate_cell_rkdp(const MechView& m, const SlotPtrs& s, const IntegrateParams& P, int64_t cell) {
   const Grp<G> g;
-  const int ns = m.ns, N = ns + 1, Nq = s.Nq;
+  const int ns = m.ns, N = ns + 1 + m.nx, Nq = s.Nq;
   for (int e = g.lane; e < N; e += G) {
     s.u[e] = P.Y[cell * N + e];
     s.src[e] = P.src ? P.src[cell * N + e] : 0.0;
@@ -1522,6 +1593,7 @@ __global__ void __launch_bounds__(512) rkdp_integrate_kernel(IntegrateParams P) 
   __syncthreads();
   MechView m = make_view(smem + EXP_TAB_BYTES, P.L);
   m.etab = reinterpret_cast<const double*>(smem);
+  m.nx = P.nx;
   const Grp<G> g;
   const int gid = threadIdx.x / G;
   double* base = reinterpret_cast<double*>(smem + EXP_TAB_BYTES + P.L.bytes) + (size_t)gid * P.S.stride;
@@ -1604,6 +1676,7 @@ struct PointParams {
   double p;
   int mode;  // 0 rhs, 1 analytic jvp, 2 finite-difference jvp, 3 mixed rhs, 4 FP32 analytic jvp
   const double* rho_cell;  // constant-volume densities, or null
+  int nx;                  // state components after T (5: auxiliary-temperature system)
 };
 
 template <int G>
@@ -1614,6 +1687,7 @@ __global__ void __launch_bounds__(512) chem_point_kernel(PointParams P) {
   __syncthreads();
   MechView m = make_view(smem + EXP_TAB_BYTES, P.L);
   m.etab = reinterpret_cast<const double*>(smem);
+  m.nx = P.nx;
   const Grp<G> g;
   const int gid = threadIdx.x / G;
   const int gpb = blockDim.x / G;
@@ -1623,7 +1697,7 @@ __global__ void __launch_bounds__(512) chem_point_kernel(PointParams P) {
   const SlotPtrs s = slot_ptrs(base, P.S);
   if (P.mode >= 3) init_sentinels<true>(s, m.ns, g.lane);
   else init_sentinels<false>(s, m.ns, g.lane);
-  const int N = m.ns + 1;
+  const int N = m.ns + 1 + m.nx;
   for (int e = g.lane; e < N; e += G) {
     s.u[e] = P.Y[cell * N + e];
     s.src[e] = P.src ? P.src[cell * N + e] : 0.0;
@@ -1645,11 +1719,12 @@ __global__ void __launch_bounds__(512) chem_point_kernel(PointParams P) {
     for (int e = g.lane; e < N; e += G) P.out[cell * N + e] = s.w[e];
     return;
   }
-  rhs_eval<G>(m, s, s.u, nullptr, pr, s.fn, true, &cs);
+  // the auxiliary-temperature T row depends on the source; elsewhere s.src is
+  // zero here, so the finite difference sees the bare source term
+  rhs_eval<G>(m, s, s.u, m.nx > 0 ? s.src : nullptr, pr, s.fn, true, &cs);
   int n_rhs = 0;
   double unorm = 0.0;
   if (P.mode == 2) unorm = sqrt(group_dot<G>(g, s.u, s.u, N));
-  // s.src is zero here, so the finite difference sees the bare source term
   apply_jv<G>(m, s, cs, P.mode == 1 ? 0 : 1, pr, unorm, s.F, s.w, &n_rhs);
   for (int e = g.lane; e < N; e += G) P.out[cell * N + e] = s.w[e];
 }
@@ -1881,12 +1956,17 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   if (G != 8 && G != 16 && G != 32) return set_error(RK_E_INVALID_ARGUMENT, "lanes_per_cell must be 0, 8, 16 or 32");
   if (!workspace || workspace_bytes < rk_rok4e_workspace_size(mech, ncell, M, opts))
     return set_error(RK_E_WORKSPACE, "workspace missing or smaller than rk_rok4e_workspace_size");
-  const int N = mech->host.L.ns + 1;
+  if (o.reactor < 0 || o.reactor > 2) return set_error(RK_E_INVALID_ARGUMENT, "reactor must be 0, 1 or 2");
+  if (o.reactor == 2 && o.precision != 0)
+    return set_error(RK_E_INVALID_ARGUMENT, "the auxiliary-temperature system is FP64 only");
+  const int nx = o.reactor == 2 ? RK_AUX_EXTRA : 0;
+  const int N = mech->host.L.ns + 1 + nx;
   const int Meff = method == 1 ? 1 : (M > N ? N : M);
   IntegrateParams P;
   P.mech = mech->dev;
   P.L = mech->host.L;
-  P.S = make_slot(mech->host.L, Meff, mixed);
+  P.nx = nx;
+  P.S = make_slot(mech->host.L, Meff, mixed, nx);
   P.precision = o.precision;
   P.Y = Y;
   P.src = src;
@@ -1906,7 +1986,6 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   P.stats = stats;
   unsigned char* wsb = static_cast<unsigned char*>(workspace);
   P.counter = reinterpret_cast<unsigned long long*>(wsb);
-  if (o.reactor < 0 || o.reactor > 1) return set_error(RK_E_INVALID_ARGUMENT, "reactor must be 0 or 1");
   if (o.reactor == 1 && !o.rho_cell) return set_error(RK_E_INVALID_ARGUMENT, "constant volume needs rho_cell");
   P.rho_cell = o.reactor == 1 ? o.rho_cell : nullptr;
   P.qstride = queue_stride(ncell);
@@ -2032,7 +2111,8 @@ int rk_mech_info(const rk_mech* mech, int32_t* n_species, int32_t* n_reactions, 
 }
 
 static int point_call(const rk_mech* mech, const double* Y, const double* src, const double* V, double p,
-                      double* out, int64_t ncell, int mode, void* stream, const double* rho_cell = nullptr) {
+                      double* out, int64_t ncell, int mode, void* stream, const double* rho_cell = nullptr,
+                      int nx = 0) {
   int rc = check_mech(mech);
   if (rc) return rc;
   if (ncell < 0) return set_error(RK_E_INVALID_ARGUMENT, "ncell < 0");
@@ -2043,9 +2123,10 @@ static int point_call(const rk_mech* mech, const double* Y, const double* src, c
   if (!rho_cell && !(p > 0.0)) return set_error(RK_E_INVALID_ARGUMENT, "pressure must be > 0");
   PointParams P;
   P.rho_cell = rho_cell;
+  P.nx = nx;
   P.mech = mech->dev;
   P.L = mech->host.L;
-  P.S = make_slot(mech->host.L, 1, mode >= 3);
+  P.S = make_slot(mech->host.L, 1, mode >= 3, nx);
   P.Y = Y;
   P.src = src;
   P.V = V;
@@ -2088,6 +2169,17 @@ int rk_chem_jvp_cv(const rk_mech* mech, const double* Y, const double* V, const 
   if (mode != 0 && mode != 1) return set_error(RK_E_INVALID_ARGUMENT, "mode must be 0 or 1");
   if (!rho_cell && ncell > 0) return set_error(RK_E_INVALID_ARGUMENT, "null density array");
   return point_call(mech, Y, nullptr, V, 1.0, JV, ncell, mode == 0 ? 1 : 2, stream, rho_cell);
+}
+
+int rk_chem_rhs_aux(const rk_mech* mech, const double* U, const double* src, double* dUdt, int64_t ncell,
+                    void* stream) {
+  return point_call(mech, U, src, nullptr, 1.0, dUdt, ncell, 0, stream, nullptr, RK_AUX_EXTRA);
+}
+
+int rk_chem_jvp_aux(const rk_mech* mech, const double* U, const double* src, const double* V, double* JV,
+                    int64_t ncell, int32_t mode, void* stream) {
+  if (mode != 0 && mode != 1) return set_error(RK_E_INVALID_ARGUMENT, "mode must be 0 or 1");
+  return point_call(mech, U, src, V, 1.0, JV, ncell, mode == 0 ? 1 : 2, stream, nullptr, RK_AUX_EXTRA);
 }
 
 size_t rk_rok4e_workspace_size(const rk_mech* mech, int64_t ncell, int32_t krylov_dim, const rk_opts* opts) {
@@ -2138,6 +2230,8 @@ int rk_simpler_split_step(const rk_mech* mech, double* U, double* h_cell, int64_
                           int32_t* stats, void* workspace, size_t workspace_bytes, void* stream) {
   int rc = check_mech(mech);
   if (rc) return rc;
+  if (opts && opts->reactor == 2)
+    return set_error(RK_E_INVALID_ARGUMENT, "the auxiliary-temperature system is for rk_rok4e_integrate and rk_rkdp_integrate");
   if (npts < 0) return set_error(RK_E_INVALID_ARGUMENT, "npts < 0");
   if (npts == 0) return RK_OK;
   if (!U) return set_error(RK_E_INVALID_ARGUMENT, "null state array");
@@ -2200,6 +2294,8 @@ int rk_split_step(const rk_mech* mech, double* U, double* h_cell, int64_t npts, 
                   int32_t* stats, void* workspace, size_t workspace_bytes, void* stream) {
   int rc = check_mech(mech);
   if (rc) return rc;
+  if (opts && opts->reactor == 2)
+    return set_error(RK_E_INVALID_ARGUMENT, "the auxiliary-temperature system is for rk_rok4e_integrate and rk_rkdp_integrate");
   if (scheme < 0 || scheme > 3) return set_error(RK_E_INVALID_ARGUMENT, "scheme must be 0..3");
   if (npts < 0) return set_error(RK_E_INVALID_ARGUMENT, "npts < 0");
   if (npts == 0) return RK_OK;
@@ -2282,6 +2378,8 @@ int rk_simpler_split_step_noalloc(const rk_mech* mech, double* U, double* h_cell
                                   const rk_opts* opts, int32_t* stats, void* stream) {
   int rc = check_mech(mech);
   if (rc) return rc;
+  if (opts && opts->reactor == 2)
+    return set_error(RK_E_INVALID_ARGUMENT, "the auxiliary-temperature system is for rk_rok4e_integrate and rk_rkdp_integrate");
   if (npts < 0) return set_error(RK_E_INVALID_ARGUMENT, "npts < 0");
   const size_t need = rk_simpler_split_step_workspace_size(mech, npts, krylov_dim, opts);
   if (need > (size_t)RK_NOALLOC_SCRATCH_BYTES) {
