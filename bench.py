@@ -230,6 +230,38 @@ def run_plain(args):
     return 0
 
 
+def run_unit_costs(args):
+    """Small launches for per-unit FP64 instruction accounting under ncu (one
+    RHS, one J v and one integration launch over 4096 cells for the flame1d and
+    batched mechanisms), then the arithmetic-unit probes."""
+    import torch
+
+    import paper_1712_00953_gb300 as rk
+    from synth.fields import WORKLOADS, field_uniform, mechanism_for
+
+    for name in ("flame1d", "batched"):
+        w = WORKLOADS[name]
+        mech = mechanism_for(w)
+        m = rk.mech_load(mech)
+        n = 4096
+        U = torch.tensor(field_uniform(n, mech.n_species, 5, 1500.0, 2300.0), device="cuda")
+        V = torch.randn_like(U)
+        rk.chem_rhs(m, U, P_ATM)
+        rk.chem_jvp(m, U, V, P_ATM, mode=0)
+        st = torch.zeros(n, 4, dtype=torch.int32, device="cuda")
+        Y = U.clone()
+        rk.rok4e_integrate(m, Y, 1e-7, w.rtol, w.atol, 4, stats=st, opts=rk.Opts(cells_per_block=8))
+        torch.cuda.synchronize()
+        s = st.cpu().numpy()
+        print(json.dumps({"unit_costs": name, "cells": n, "attempts": int((s[:, 0] + s[:, 1]).sum()),
+                          "rhs": int(s[:, 2].sum()), "failed": int((s[:, 3] != 0).sum())}))
+    if not args.skip_probes:
+        names = ["fp64_fma", "fp32_fma", "fp64_exp", "cvt", "fp64_fma_1warp_per_sm", "fp64_fma_4warps_per_sm",
+                 "fp64_warp_inst_1lane_4warps_per_sm", "df_fma"]
+        print(json.dumps({"probes_ops_per_s": {nm: rk.probe_throughput(k) for k, nm in enumerate(names)}}))
+    return 0
+
+
 def run_batched(args, rank, world, local_rank):
     """The batched workload: 2^20 independent constant-pressure cells from a
     Gaussian random temperature field, one ROK4E integration of dt = 1e-6 s
@@ -295,9 +327,13 @@ def run_study(args, local_rank):
     import paper_1712_00953_gb300 as rk
     from synth.fields import WORKLOADS, initial_state, mechanism_for
 
+    import dataclasses
+
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     w = WORKLOADS["batched"]
+    if args.study_kcap > 0:  # a stiffer variant of the mechanism (larger cap on k C)
+        w = dataclasses.replace(w, k_cap=args.study_kcap)
     mech = mechanism_for(w)
     m = rk.mech_load(mech)
     n = 1024
@@ -339,7 +375,7 @@ def run_study(args, local_rank):
             Y, t, tot, n_int = run(method, M, h_cfl, rtol, atol, jv)
             rel = ((Y[:, ns] - Tref).abs() / Tref).cpu().numpy()
             name = "RKDP" if method == "rkdp" else f"ROK4E M={M}" + (" FD J v" if jv else "")
-            line = {"study": "efficiency", "method": name, "h_cfl_s": h_cfl, "intervals": n_int,
+            line = {"study": "efficiency", "k_cap": w.k_cap, "method": name, "h_cfl_s": h_cfl, "intervals": n_int,
                     "cells": n, "horizon_s": T_END, "rtol": rtol, "atol": atol,
                     "gpu_s": t, "gpu_us_per_cell": t / n * 1e6,
                     "T_rel_err_max": float(rel.max()), "T_rel_err_mean": float(rel.mean()),
@@ -519,7 +555,9 @@ def run_ours(args, rank, world, local_rank):
                                    f"split step of the initial field ({cpu_t:.1f} s)"},
         "e2e": {"value": e2e_value, "unit": "cell-steps/s", "h2d_bytes_per_step": int(U.numel() * 8),
                 "d2h_bytes_per_step": int(U.numel() * 8), "steps": e2e_steps},
-        "gpu_launches": 5 * args.steps,
+        # per split step: diffusion, the three queue-ordering kernels (longest-first
+        # orders), the integration, three SSP-RK3 stages
+        "gpu_launches": (5 + (3 if args.queue_order in (0, 2, 3) else 0)) * args.steps,
         "cuda_graph": {"timed_region": "one captured split step replayed per step",
                        "matches_eager_bitwise": graph_matches_eager},
         "clocks": clocks,
@@ -545,6 +583,11 @@ def main():
     ap.add_argument("--cells-per-block", type=int, default=8, help="cells per block (0: library default)")
     ap.add_argument("--precision", default="fp64", choices=list(PREC))
     ap.add_argument("--queue-order", type=int, default=3, help="0 auto, 1 interleaved, 2 longest first, 3 static balanced bins")
+    ap.add_argument("--unit-costs", action="store_true",
+                    help="small RHS / J v / integration launches (for ncu instruction counts) and the probes")
+    ap.add_argument("--skip-probes", action="store_true")
+    ap.add_argument("--study-kcap", type=float, default=0.0,
+                    help="efficiency study on a variant of the batched mechanism with this cap on k C (1/s)")
     ap.add_argument("--study", default="", choices=["", "efficiency"],
                     help="efficiency: the ROK4E M / J v mode / explicit RK comparison over h_CFL")
     ap.add_argument("--workload", default="flame1d", choices=["flame1d", "batched"],
@@ -560,6 +603,8 @@ def main():
         return run_reference(args, rank, world)
     if args.plain_steps > 0:
         return run_plain(args)
+    if args.unit_costs:
+        return run_unit_costs(args)
     if args.study == "efficiency":
         return run_study(args, local_rank)
     if args.workload == "batched":

@@ -357,7 +357,10 @@ int rk_rok4e_adjoint(const rk_mech* mech, const double* checkpoints, const doubl
 /* ---- diagnostics ---------------------------------------------------------------
  * Throughput probes of the arithmetic units used by the roofline:
  *  kind 0: FP64 FMA, 1: FP32 FMA, 2: FP64 exp(), 3: double<->float
- *  conversions.  Launches a dependent-operation
+ *  conversions; how the FP64 pipe is shared: 4: FP64 FMA with one warp per
+ *  SM, 5: four warps per SM, 6: four warps per SM with one active lane each
+ *  (rate of warp instructions); 7: double-float (FP32 pair) multiply-adds.
+ *  Launches a dependent-operation
  *  grid sized to the device and returns the operation rate (ops/s) measured
  *  with CUDA events in *ops_per_s.  Synchronous. */
 int rk_probe_throughput(int32_t kind, double* ops_per_s);

@@ -30,6 +30,7 @@ constexpr int FO_STRIDE = 8;  // lnA0(SI), b0, Ea0/R, a, 1/T***, 1/T*, T**, unus
 struct MechLayout {
   int32_t ns = 0, nr = 0;
   int32_t ntb = 0;  // reactions with kind > 0 (they come first)
+  int32_t ntroe = 0;  // Troe falloff reactions: the first ntroe, third-body slots 0..ntroe-1
   int32_t nnz = 0;  // entries of the species-major stoichiometry list
   // byte offsets into the packed buffer (all multiples of 16)
   int64_t off_W = 0, off_invW = 0, off_Tmid = 0, off_lo = 0, off_hi = 0;

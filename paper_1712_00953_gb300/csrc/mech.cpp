@@ -159,6 +159,7 @@ bool pack_mechanism(const void* vdesc, HostMech* out, std::string* err) {
   L.ns = ns;
   L.nr = nr;
   L.ntb = n_troe + n_tb;
+  L.ntroe = n_troe;
   L.nnz = nnz;
   int64_t off = 0;
   auto take = [&](int64_t bytes) {

@@ -133,7 +133,7 @@ static int cuda_error(cudaError_t e, const char* where) {
 
 // ------------------------------------------------------------------- views
 struct MechView {
-  int ns, nr, ntb;
+  int ns, nr, ntb, ntroe;
   int nx;  // state components after T: 0, or 5 (rho, rho u, rho E) for the auxiliary-temperature system
   const double* etab;  // 2^(j/128) table in shared memory
   const double *W, *invW, *Tmid, *lo, *hi, *lnA, *bexp, *EaR, *eff, *fo, *csr_nu;
@@ -148,6 +148,7 @@ __host__ __device__ inline MechView make_view(const unsigned char* base, const M
   m.ns = L.ns;
   m.nr = L.nr;
   m.ntb = L.ntb;
+  m.ntroe = L.ntroe;
   m.nx = 0;
   m.etab = nullptr;
   m.W = reinterpret_cast<const double*>(base + L.off_W);
@@ -182,6 +183,7 @@ struct SlotLayout {
   int C, dC, cp, hRT, dcp, gRT, E, Einv, om;  // species (+1 sentinel entry)
   int q, kc, krc, qT;                         // reactions (qT: d q_j / dT at u_n, for J v)
   int tb;                                     // [ntb][4]: [M], dk/d[M], dlnk/dT, 1/Kc
+  int tro;                                    // [11][ntroe]: Troe falloff scratch
   int H, LU, piv, red;                        // small
   int fbase;  // FP32 region (mixed precision only), offset in doubles
   int fC, fdC, fh, fcp, fdcp, fom, fq, fkc, fkr, ftb, fQ, fw;  // offsets in floats from fbase
@@ -226,6 +228,7 @@ static SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false, int 
   s.krc = take(L.nr > 0 ? L.nr : 1);
   s.qT = take(L.nr > 0 ? L.nr : 1);
   s.tb = take(4 * (L.ntb > 0 ? L.ntb : 1));
+  s.tro = take(11 * (L.ntroe > 0 ? L.ntroe : 1));
   s.H = take(MAXM * MAXM);
   s.LU = take(MAXM * MAXM);
   s.piv = take(MAXM);
@@ -357,7 +360,7 @@ struct CellScalars {
 
 struct SlotPtrs {
   double *u, *src, *fn, *arg, *fr, *F, *w, *Q, *K;
-  double *C, *dC, *cp, *hRT, *dcp, *gRT, *E, *Einv, *om, *q, *kc, *krc, *qT, *tb;
+  double *C, *dC, *cp, *hRT, *dcp, *gRT, *E, *Einv, *om, *q, *kc, *krc, *qT, *tb, *tro;
   double *H, *LU, *piv, *red;
   float *fC, *fdC, *fh, *fcp, *fdcp, *fom, *fq, *fkc, *fkr, *ftb, *fQ, *fw;  // mixed precision
   int Nq;  // stride between Krylov / stage vectors
@@ -387,6 +390,7 @@ __device__ inline SlotPtrs slot_ptrs(double* b, const SlotLayout& s) {
   p.kc = b + s.kc;
   p.krc = b + s.krc;
   p.qT = b + s.qT;
+  p.tro = b + s.tro;
   p.tb = b + s.tb;
   p.H = b + s.H;
   p.LU = b + s.LU;
@@ -492,6 +496,95 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     }
   }
   g.sync();
+  // Troe falloff factors (Sec. 4.4 kinetics; F_cent, Pr, F), spread over the
+  // lanes in three passes instead of one lane per reaction running the whole
+  // chain: (A) the four exponentials of each reaction, k0/k_inf, e^{-T/T***},
+  // e^{-T/T*}, e^{-T**/T}; (B) log10 F_cent and log10 Pr; (C) F, the falloff
+  // multiplier Pr/(1+Pr) F and, when caching, d ln k/dT and dk/d[M] / k_inf.
+  // Scratch tro (nt = ntroe): [0,4nt) exponentials, [4nt,6nt) logs,
+  // [6nt,7nt) multiplier, [7nt,8nt) d ln k/dT, [8nt,9nt) dk/d[M] / k_inf,
+  // [9nt,11nt) F_cent and Pr.
+  const int nt = m.ntroe;
+  if (nt > 0) {
+    double* tro = s.tro;
+    for (int l = g.lane; l < 4 * nt; l += G) {
+      const int i = l >> 2, c = l & 3;
+      const double* fo = m.fo + (size_t)i * FO_STRIDE;
+      double x;
+      if (c == 0) {
+        const double lnk_inf = m.lnA[i] + m.bexp[i] * lnT - m.EaR[i] * invT;
+        x = fo[0] + fo[1] * lnT - fo[2] * invT - lnk_inf;  // ln(k0 / k_inf)
+      } else if (c == 1) {
+        x = -T * fo[4];
+      } else if (c == 2) {
+        x = -T * fo[5];
+      } else {
+        x = fo[6] > 0.0 ? -fo[6] * invT : 0.0;
+      }
+      const double ex = exp_fast(x, m.etab);
+      tro[l] = (c == 3 && !(fo[6] > 0.0)) ? 0.0 : ex;
+    }
+    g.sync();
+    for (int l = g.lane; l < 2 * nt; l += G) {
+      const int i = l >> 1;
+      const double* fo = m.fo + (size_t)i * FO_STRIDE;
+      double y;
+      if (l & 1) {
+        double Mc;
+        if (coop_tb) {
+          Mc = s.tb[4 * i];
+        } else {
+          const double* e = m.eff + (size_t)i * ns;
+          Mc = 0.0;
+          for (int q = 0; q < ns; ++q) Mc = fma(e[q], s.C[q], Mc);
+        }
+        y = tro[4 * i] * Mc;  // Pr = [M] k0 / k_inf
+        if (!(y > 1e-300)) y = 1e-300;
+      } else {
+        const double a = fo[3];
+        y = (1.0 - a) * tro[4 * i + 1] + a * tro[4 * i + 2] + tro[4 * i + 3];  // F_cent
+      }
+      tro[9 * nt + l] = y;
+      tro[4 * nt + l] = log10(y);
+    }
+    g.sync();
+    for (int i = g.lane; i < nt; i += G) {
+      const double lFc = tro[4 * nt + 2 * i], lPr = tro[4 * nt + 2 * i + 1];
+      const double Fc = tro[9 * nt + 2 * i], Pr = tro[9 * nt + 2 * i + 1];
+      const double cc = -0.4 - 0.67 * lFc;
+      const double nn = 0.75 - 1.27 * lFc;
+      const double x = lPr + cc;
+      const double D = nn - 0.14 * x;
+      // one division for 1/(1 + Pr) and 1/(D^2 + x^2):
+      //   1/(1 + f1^2) = D^2/(D^2 + x^2) with f1 = x / D
+      const double s2 = fma(D, D, x * x);
+      const double onePr = 1.0 + Pr;
+      const double qd = 1.0 / (onePr * s2);
+      const double iOnePr = s2 * qd;
+      const double rr = onePr * qd;  // 1 / (D^2 + x^2)
+      const double iden = D * D * rr;
+      const double F = exp_fast(lFc * iden * 2.302585092994046, m.etab);  // 10^(lFc / (1 + f1^2))
+      tro[6 * nt + i] = Pr * iOnePr * F;
+      if (cache) {  // d ln k / dT and d k / d[M] for the analytic J v
+        const double* fo = m.fo + (size_t)i * FO_STRIDE;
+        const double a = fo[3];
+        const double er = tro[4 * i], e3 = tro[4 * i + 1], e1 = tro[4 * i + 2], e2 = tro[4 * i + 3];
+        const double dlnk_inf = (m.bexp[i] + m.EaR[i] * invT) * invT;
+        const double dlnk0 = (fo[1] + fo[2] * invT) * invT;
+        // d ln F / d log10 Pr = -2 lFc f1 n / (D^2 (1 + f1^2)^2) and
+        // d log10 F / d lFc = 1/(1 + f1^2) - 2 lFc f1 (df1/dlFc) / (1 + f1^2)^2,
+        // df1/dlFc = (-0.67 D + 1.1762 x) / D^2, written with rr = 1/(D^2 + x^2)
+        const double w = 2.0 * lFc * x * D * rr * rr;
+        const double dlF_dL = -w * nn;
+        const double dlF_dlFc = iden - w * (-0.67 * D + 1.1762 * x);
+        const double dFc = -(1.0 - a) * fo[4] * e3 - a * fo[5] * e1 + (fo[6] > 0.0 ? fo[6] * invT * invT * e2 : 0.0);
+        const double gg = iOnePr + dlF_dL;
+        tro[7 * nt + i] = dlnk_inf + gg * (dlnk0 - dlnk_inf) + dlF_dlFc * dFc * (1.0 / Fc);
+        tro[8 * nt + i] = er * F * iOnePr * gg;  // (dk/d[M]) / k_inf
+      }
+    }
+    g.sync();
+  }
   // reactions: rate coefficients and rates of progress
   const double RTp = R_OVER_PREF * T;
   const double invRTp = PREF_OVER_R * invT;
@@ -536,44 +629,13 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
       if (kind == 1) {
         mfac = Mc;
       } else {
-        const double* fo = m.fo + (size_t)slot * FO_STRIDE;
-        // Pr = k0 [M] / k_inf = [M] exp(ln k0 - ln k_inf): no division
-        const double er = exp_fast(fo[0] + fo[1] * lnT - fo[2] * invT - lnk, m.etab);
-        double Pr = er * Mc;
-        if (!(Pr > 1e-300)) Pr = 1e-300;
-        const double a = fo[3];
-        const double e3 = exp_fast(-T * fo[4], m.etab), e1 = exp_fast(-T * fo[5], m.etab);
-        const double e2 = fo[6] > 0.0 ? exp_fast(-fo[6] * invT, m.etab) : 0.0;
-        const double Fc = (1.0 - a) * e3 + a * e1 + e2;
-        const double lFc = log10(Fc);
-        const double cc = -0.4 - 0.67 * lFc;
-        const double nn = 0.75 - 1.27 * lFc;
-        const double x = log10(Pr) + cc;
-        const double D = nn - 0.14 * x;
-        // one division for 1/(1 + Pr) and 1/(D^2 + x^2):
-        //   1/(1 + f1^2) = D^2/(D^2 + x^2) with f1 = x / D
-        const double s2 = fma(D, D, x * x);
-        const double onePr = 1.0 + Pr;
-        const double qd = 1.0 / (onePr * s2);
-        const double iOnePr = s2 * qd;
-        const double rr = onePr * qd;  // 1 / (D^2 + x^2)
-        const double iden = D * D * rr;
-        const double F = exp_fast(lFc * iden * 2.302585092994046, m.etab);  // 10^(lFc / (1 + f1^2))
-        if (cache) {  // d ln k / dT and d k / d[M] for the analytic J v
-          const double k0 = k * er;
-          const double dlnk0 = (fo[1] + fo[2] * invT) * invT;
-          // d ln F / d log10 Pr = -2 lFc f1 n / (D^2 (1 + f1^2)^2) and
-          // d log10 F / d lFc = 1/(1 + f1^2) - 2 lFc f1 (df1/dlFc) / (1 + f1^2)^2,
-          // df1/dlFc = (-0.67 D + 1.1762 x) / D^2, written with rr = 1/(D^2 + x^2)
-          const double w = 2.0 * lFc * x * D * rr * rr;
-          const double dlF_dL = -w * nn;
-          const double dlF_dlFc = iden - w * (-0.67 * D + 1.1762 * x);
-          const double dFc = -(1.0 - a) * fo[4] * e3 - a * fo[5] * e1 + (fo[6] > 0.0 ? fo[6] * invT * invT * e2 : 0.0);
-          const double gg = iOnePr + dlF_dL;
-          dlnk = dlnk + gg * (dlnk0 - dlnk) + dlF_dlFc * dFc * (1.0 / Fc);
-          dkdM = k0 * F * iOnePr * gg;
+        // Troe: the multiplier and derivatives from the falloff passes above
+        // (Troe reactions hold slots 0..ntroe-1)
+        if (cache) {
+          dlnk = s.tro[7 * nt + slot];
+          dkdM = k * s.tro[8 * nt + slot];
         }
-        k = k * Pr * iOnePr * F;
+        k = k * s.tro[6 * nt + slot];
       }
       if (cache) {
         double* t = s.tb + 4 * (meta >> 8);
@@ -1789,7 +1851,8 @@ __global__ void exp_eval_kernel(const double* __restrict__ x, double* __restrict
   }
 }
 
-__global__ void probe_fp64_kernel(double* out, int iters, double a) {
+__global__ void probe_fp64_kernel(double* out, int iters, double a, int active_lanes = 32) {
+  if ((int)(threadIdx.x & 31) >= active_lanes) return;
   double x0 = threadIdx.x * 1e-9, x1 = x0 + 1e-3, x2 = x0 + 2e-3, x3 = x0 + 3e-3;
   double x4 = x0 + 4e-3, x5 = x0 + 5e-3, x6 = x0 + 6e-3, x7 = x0 + 7e-3;
   for (int i = 0; i < iters; ++i) {
@@ -1810,6 +1873,37 @@ __global__ void probe_fp32_kernel(float* out, int iters, float a) {
   float r = 0.f;
 #pragma unroll
   for (int j = 0; j < 8; ++j) r += x[j];
+  if (r == 12345.678f) out[0] = r;
+}
+// Double-float (FP32 pair) multiply-add, a*b + c with a 48-bit significand:
+// exact product by fmaf, error-free sum (Knuth's two-sum) of the leading parts.
+struct f2 {
+  float h, l;
+};
+__device__ __forceinline__ f2 df_fma(f2 a, f2 b, f2 c) {
+  const float ph = a.h * b.h;
+  float pl = fmaf(a.h, b.h, -ph);
+  pl = fmaf(a.h, b.l, pl);
+  pl = fmaf(a.l, b.h, pl);
+  const float sh = ph + c.h;
+  const float bb = sh - ph;
+  const float sl = (ph - (sh - bb)) + (c.h - bb);
+  const float t = sl + pl + c.l;
+  const float h = sh + t;
+  return {h, t - (h - sh)};
+}
+__global__ void probe_df_kernel(float* out, int iters, float ah, float al) {
+  const f2 a{ah, al};
+  f2 x[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) x[j] = {threadIdx.x * 1e-9f + j * 1e-3f, 0.f};
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) x[j] = df_fma(x[j], a, a);
+  }
+  float r = 0.f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) r += x[j].h + x[j].l;
   if (r == 12345.678f) out[0] = r;
 }
 __global__ void probe_cvt_kernel(double* out, int iters) {
@@ -2515,7 +2609,7 @@ int rk_rok4e_adjoint(const rk_mech* mech, const double* checkpoints, const doubl
 }
 
 int rk_probe_throughput(int32_t kind, double* ops_per_s) {
-  if (!ops_per_s || kind < 0 || kind > 3) return set_error(RK_E_INVALID_ARGUMENT, "bad probe arguments");
+  if (!ops_per_s || kind < 0 || kind > 7) return set_error(RK_E_INVALID_ARGUMENT, "bad probe arguments");
   int n_sm = 0;
   size_t smem = 0;
   int rc = device_props(&n_sm, &smem);
@@ -2541,6 +2635,15 @@ int rk_probe_throughput(int32_t kind, double* ops_per_s) {
     } else if (kind == 2) {
       probe_exp_kernel<<<blocks, threads>>>((double*)buf, iters);
       ops = (double)blocks * threads * iters * 4.0;
+    } else if (kind == 4 || kind == 5 || kind == 6) {
+      // one block per SM: 1 warp (kind 4), 4 warps (5), 4 warps with one lane
+      // active each (6; counted per warp instruction)
+      const int t = kind == 4 ? 32 : 128;
+      probe_fp64_kernel<<<n_sm, t>>>((double*)buf, iters, 0.999999, kind == 6 ? 1 : 32);
+      ops = (double)n_sm * t * iters * 8.0 / (kind == 6 ? 32.0 : 1.0);
+    } else if (kind == 7) {
+      probe_df_kernel<<<2 * n_sm, 512>>>((float*)buf, iters, 0.9999f, 1e-9f);
+      ops = (double)2 * n_sm * 512 * iters * 4.0;
     } else {
       probe_cvt_kernel<<<blocks, threads>>>((double*)buf, iters);
       ops = (double)blocks * threads * iters * 8.0;  // conversions
