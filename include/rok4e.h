@@ -367,7 +367,9 @@ int rk_probe_throughput(int32_t kind, double* ops_per_s);
 
 /* The kernels' table-driven exponential on a device array (for testing it
  * against the CUDA math library): which 0: y = exp(x); 1: exp(x) and 2:
- * exp(-x) from the shared-reduction pair.  Method: Tang, ACM TOMS 15(2),
+ * exp(-x) from the shared-reduction pair; 3, 4, 5: the same three in the
+ * mixed-precision form (polynomial's small term in FP32, relative error
+ * ~1e-12) used by precision levels 1 and 2.  Method: Tang, ACM TOMS 15(2),
  * 1989, with a 128-entry table; the paper itself delegates kinetics to
  * Cantera and prints no exponential. */
 int rk_eval_exp(const double* x, double* y, int64_t n, int32_t which, void* stream);

@@ -32,6 +32,7 @@ struct MechLayout {
   int32_t ntb = 0;  // reactions with kind > 0 (they come first)
   int32_t ntroe = 0;  // Troe falloff reactions: the first ntroe, third-body slots 0..ntroe-1
   int32_t nnz = 0;  // entries of the species-major stoichiometry list
+  int32_t npiece = 0;  // pieces the list is split into for the gather (>= ns)
   // byte offsets into the packed buffer (all multiples of 16)
   int64_t off_W = 0, off_invW = 0, off_Tmid = 0, off_lo = 0, off_hi = 0;
   int64_t off_lnA = 0, off_b = 0, off_EaR = 0;
@@ -41,6 +42,8 @@ struct MechLayout {
   int64_t off_slots = 0;  // uint32 per reaction: ra | rb<<8 | pa<<16 | pb<<24 (ns = empty)
   int64_t off_meta = 0;   // int32 per reaction: kind | rev<<2 | (dnu+4)<<4 | slot<<8
   int64_t off_csr_ptr = 0, off_csr_j = 0;
+  int64_t off_piece_ptr = 0;   // int32 [npiece + 1]: list offset of each piece
+  int64_t off_spec_piece = 0;  // int32 [ns + 1]: first piece of each species
   // FP32 copies read by the reduced-precision Jacobian-vector product
   int64_t off_Wf = 0, off_invWf = 0, off_bf = 0, off_EaRf = 0, off_efff = 0, off_csr_nuf = 0;
   int64_t off_perm = 0;  // int32 per packed reaction: its index in the input description

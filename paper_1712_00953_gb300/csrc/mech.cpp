@@ -154,6 +154,44 @@ bool pack_mechanism(const void* vdesc, HostMech* out, std::string* err) {
   int nnz = 0;
   for (auto& row : rows) nnz += (int)row.size();
 
+  // ---- pieces of the list for the gather w = nu^T q: every species row is cut
+  // into near-equal pieces of at most Lp entries; one lane sums one piece, so
+  // a warp's loop runs ceil(npiece/32) x Lp times instead of the longest row.
+  // Lp minimises that count plus the adds that join a species' pieces.
+  int maxdeg = 1;
+  for (auto& row : rows) maxdeg = std::max(maxdeg, (int)row.size());
+  int Lp = maxdeg;
+  {
+    long best = -1;
+    for (int cand = 1; cand <= maxdeg; ++cand) {
+      int P = 0, maxp = 1;
+      for (auto& row : rows) {
+        const int pk = std::max(1, ((int)row.size() + cand - 1) / cand);
+        P += pk;
+        maxp = std::max(maxp, pk);
+      }
+      const long cost = (long)((P + 31) / 32) * cand + (maxp - 1);
+      if (best < 0 || cost < best) {
+        best = cost;
+        Lp = cand;
+      }
+    }
+  }
+  std::vector<int32_t> piece_ptr, spec_piece;
+  {
+    int pos = 0;
+    for (int k = 0; k < ns; ++k) {
+      spec_piece.push_back((int32_t)piece_ptr.size());
+      const int deg = (int)rows[k].size();
+      const int pk = std::max(1, (deg + Lp - 1) / Lp);
+      for (int i = 0; i < pk; ++i) piece_ptr.push_back(pos + (int)((long)deg * i / pk));
+      pos += deg;
+    }
+    spec_piece.push_back((int32_t)piece_ptr.size());
+    piece_ptr.push_back(pos);
+  }
+  const int npiece = (int)piece_ptr.size() - 1;
+
   // ---- layout
   MechLayout L;
   L.ns = ns;
@@ -161,6 +199,7 @@ bool pack_mechanism(const void* vdesc, HostMech* out, std::string* err) {
   L.ntb = n_troe + n_tb;
   L.ntroe = n_troe;
   L.nnz = nnz;
+  L.npiece = npiece;
   int64_t off = 0;
   auto take = [&](int64_t bytes) {
     const int64_t o = off;
@@ -182,6 +221,8 @@ bool pack_mechanism(const void* vdesc, HostMech* out, std::string* err) {
   L.off_meta = take(4 * (int64_t)nr);
   L.off_csr_ptr = take(4 * (int64_t)(ns + 1));
   L.off_csr_j = take(4 * (int64_t)nnz);
+  L.off_piece_ptr = take(4 * (int64_t)(npiece + 1));
+  L.off_spec_piece = take(4 * (int64_t)(ns + 1));
   L.off_Wf = take(4 * (int64_t)ns);
   L.off_invWf = take(4 * (int64_t)ns);
   L.off_bf = take(4 * (int64_t)nr);
@@ -267,6 +308,8 @@ bool pack_mechanism(const void* vdesc, HostMech* out, std::string* err) {
     }
   }
   I(L.off_csr_ptr)[ns] = pos;
+  for (int p = 0; p <= npiece; ++p) I(L.off_piece_ptr)[p] = piece_ptr[p];
+  for (int k = 0; k <= ns; ++k) I(L.off_spec_piece)[k] = spec_piece[k];
   auto F = [&](int64_t o) { return reinterpret_cast<float*>(buf.data() + o); };
   for (int k = 0; k < ns; ++k) {
     F(L.off_Wf)[k] = (float)D(L.off_W)[k];

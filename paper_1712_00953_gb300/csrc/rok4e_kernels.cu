@@ -89,6 +89,62 @@ __device__ __forceinline__ double exp_fast(double x, const double* __restrict__ 
   return exp_scale(fma(t, p, t), k >> 7);
 }
 
+// Mixed-precision exp: the same argument reduction and reconstruction in FP64,
+// e^r - 1 = r + r^2 q(r) with the small term r^2 q(r) (|r| <= ln2/256, so at
+// most 3.7e-6) in FP32.  Relative error ~1e-12 for 6 FP64 operations instead
+// of 10.
+__device__ __forceinline__ double exp_mixed(double x, const double* __restrict__ tab) {
+  if ((__double2hiint(x) & 0x7fffffff) >= 0x40862000) return exp(x);
+  const double kt = fma(x, RK_N_OVER_LN2, EXP_SHIFTER);
+  const int k = __double2loint(kt);
+  const double kd = kt - EXP_SHIFTER;
+  double r = fma(-kd, RK_LN2_OVER_N_HI, x);
+  r = fma(-kd, RK_LN2_OVER_N_LO, r);
+  const float rf = __double2float_rn(r);
+  const float q = fmaf(fmaf(fmaf(rf, 1.0f / 120.0f, 1.0f / 24.0f), rf, 1.0f / 6.0f), rf, 0.5f);
+  const double p = r + (double)(rf * rf * q);
+  const double t = tab[k & (RK_EXP2_TABLE_N - 1)];
+  return exp_scale(fma(t, p, t), k >> 7);
+}
+
+// (exp(x), exp(-x)) as exp_mixed, sharing the argument reduction.
+__device__ __forceinline__ void exp_pm_mixed(double x, const double* __restrict__ tab, double* ep, double* em) {
+  if ((__double2hiint(x) & 0x7fffffff) >= 0x40862000) {
+    *ep = exp(x);
+    *em = exp(-x);
+    return;
+  }
+  const double kt = fma(x, RK_N_OVER_LN2, EXP_SHIFTER);
+  const int k = __double2loint(kt);
+  const double kd = kt - EXP_SHIFTER;
+  double r = fma(-kd, RK_LN2_OVER_N_HI, x);
+  r = fma(-kd, RK_LN2_OVER_N_LO, r);
+  const float rf = __double2float_rn(r);
+  const float r2 = rf * rf;
+  const float qp = fmaf(fmaf(fmaf(rf, 1.0f / 120.0f, 1.0f / 24.0f), rf, 1.0f / 6.0f), rf, 0.5f);
+  const float qm = fmaf(fmaf(fmaf(-rf, 1.0f / 120.0f, 1.0f / 24.0f), -rf, 1.0f / 6.0f), -rf, 0.5f);
+  const double pp = r + (double)(r2 * qp);
+  const double pm = (double)(r2 * qm) - r;
+  const double tp = tab[k & (RK_EXP2_TABLE_N - 1)];
+  const int km = -k;
+  const double tm = tab[km & (RK_EXP2_TABLE_N - 1)];
+  *ep = exp_scale(fma(tp, pp, tp), k >> 7);
+  *em = exp_scale(fma(tm, pm, tm), km >> 7);
+}
+
+// 1/x by Newton's iteration for the reciprocal, r <- r + r (1 - x r), from
+// an FP32 estimate: two steps square the estimate's relative error twice
+// ((1e-7)^4), leaving the last rounding.  Four FP64 operations instead of a
+// full-precision division; for positive normal x inside the FP32 range (the
+// temperature and the mixture sums of a cell).
+__device__ __forceinline__ double rcp_newton(double x) {
+  double r = (double)__frcp_rn(__double2float_rn(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
 // (exp(x), exp(-x)) sharing one argument reduction.
 __device__ __forceinline__ void exp_pm(double x, const double* __restrict__ tab, double* ep, double* em) {
   if ((__double2hiint(x) & 0x7fffffff) >= 0x40862000) {
@@ -139,6 +195,8 @@ struct MechView {
   const double *W, *invW, *Tmid, *lo, *hi, *lnA, *bexp, *EaR, *eff, *fo, *csr_nu;
   const uint32_t* slots;
   const int32_t *meta, *csr_ptr, *csr_j;
+  const int32_t *piece_ptr, *spec_piece;  // gather pieces of the species-major list
+  int npiece;
   const float *Wf, *invWf, *bf, *EaRf, *efff, *csr_nuf;  // FP32 copies
   const int32_t* perm;  // input index of each packed reaction
 };
@@ -166,6 +224,9 @@ __host__ __device__ inline MechView make_view(const unsigned char* base, const M
   m.meta = reinterpret_cast<const int32_t*>(base + L.off_meta);
   m.csr_ptr = reinterpret_cast<const int32_t*>(base + L.off_csr_ptr);
   m.csr_j = reinterpret_cast<const int32_t*>(base + L.off_csr_j);
+  m.piece_ptr = reinterpret_cast<const int32_t*>(base + L.off_piece_ptr);
+  m.spec_piece = reinterpret_cast<const int32_t*>(base + L.off_spec_piece);
+  m.npiece = L.npiece;
   m.Wf = reinterpret_cast<const float*>(base + L.off_Wf);
   m.invWf = reinterpret_cast<const float*>(base + L.off_invWf);
   m.bf = reinterpret_cast<const float*>(base + L.off_bf);
@@ -184,9 +245,10 @@ struct SlotLayout {
   int q, kc, krc, qT;                         // reactions (qT: d q_j / dT at u_n, for J v)
   int tb;                                     // [ntb][4]: [M], dk/d[M], dlnk/dT, 1/Kc
   int tro;                                    // [11][ntroe]: Troe falloff scratch
+  int part;                                   // [npiece]: gather partial sums
   int H, LU, piv, red;                        // small
   int fbase;  // FP32 region (mixed precision only), offset in doubles
-  int fC, fdC, fh, fcp, fdcp, fom, fq, fkc, fkr, ftb, fQ, fw;  // offsets in floats from fbase
+  int fC, fdC, fh, fcp, fdcp, fom, fq, fkc, fkr, ftb, fQ, fw, fpart;  // offsets in floats from fbase
   int stride;
 };
 
@@ -229,6 +291,7 @@ static SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false, int 
   s.qT = take(L.nr > 0 ? L.nr : 1);
   s.tb = take(4 * (L.ntb > 0 ? L.ntb : 1));
   s.tro = take(11 * (L.ntroe > 0 ? L.ntroe : 1));
+  s.part = take(L.npiece > 0 ? L.npiece : 1);
   s.H = take(MAXM * MAXM);
   s.LU = take(MAXM * MAXM);
   s.piv = take(MAXM);
@@ -253,8 +316,9 @@ static SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false, int 
     s.ftb = ftake(4 * (L.ntb > 0 ? L.ntb : 1));
     s.fQ = ftake(Nq * M);
     s.fw = ftake(Nq);
+    s.fpart = ftake(L.npiece > 0 ? L.npiece : 1);
   } else {
-    s.fC = s.fdC = s.fh = s.fcp = s.fdcp = s.fom = s.fq = s.fkc = s.fkr = s.ftb = s.fQ = s.fw = 0;
+    s.fC = s.fdC = s.fh = s.fcp = s.fdcp = s.fom = s.fq = s.fkc = s.fkr = s.ftb = s.fQ = s.fw = s.fpart = 0;
   }
   o += (fo + 1) / 2;
   s.stride = (o + 3) & ~3;
@@ -360,9 +424,9 @@ struct CellScalars {
 
 struct SlotPtrs {
   double *u, *src, *fn, *arg, *fr, *F, *w, *Q, *K;
-  double *C, *dC, *cp, *hRT, *dcp, *gRT, *E, *Einv, *om, *q, *kc, *krc, *qT, *tb, *tro;
+  double *C, *dC, *cp, *hRT, *dcp, *gRT, *E, *Einv, *om, *q, *kc, *krc, *qT, *tb, *tro, *part;
   double *H, *LU, *piv, *red;
-  float *fC, *fdC, *fh, *fcp, *fdcp, *fom, *fq, *fkc, *fkr, *ftb, *fQ, *fw;  // mixed precision
+  float *fC, *fdC, *fh, *fcp, *fdcp, *fom, *fq, *fkc, *fkr, *ftb, *fQ, *fw, *fpart;  // mixed precision
   int Nq;  // stride between Krylov / stage vectors
 };
 
@@ -391,6 +455,7 @@ __device__ inline SlotPtrs slot_ptrs(double* b, const SlotLayout& s) {
   p.krc = b + s.krc;
   p.qT = b + s.qT;
   p.tro = b + s.tro;
+  p.part = b + s.part;
   p.tb = b + s.tb;
   p.H = b + s.H;
   p.LU = b + s.LU;
@@ -409,8 +474,33 @@ __device__ inline SlotPtrs slot_ptrs(double* b, const SlotLayout& s) {
   p.ftb = f + s.ftb;
   p.fQ = f + s.fQ;
   p.fw = f + s.fw;
+  p.fpart = f + s.fpart;
   p.Nq = (s.N + 1) & ~1;
   return p;
+}
+
+// w = nu^T q, pass 1: the species-major list is cut into pieces of near-equal
+// length (chosen when the mechanism is packed); each lane sums whole pieces
+// into part[], so the warp's loop runs over the longest piece rather than the
+// longest species row.  Pass 2 (piece_sum) adds a species' pieces in order:
+// the result does not depend on the launch shape.
+template <int G, typename T>
+__device__ __forceinline__ void gather_pieces(const MechView& m, int lane, const T* __restrict__ nu,
+                                              const T* __restrict__ q, T* part) {
+  for (int p = lane; p < m.npiece; p += G) {
+    T acc = T(0);
+    const int e1 = m.piece_ptr[p + 1];
+    for (int e = m.piece_ptr[p]; e < e1; ++e) acc = fma(nu[e], q[m.csr_j[e]], acc);
+    part[p] = acc;
+  }
+}
+template <typename T>
+__device__ __forceinline__ T piece_sum(const MechView& m, const T* part, int k) {
+  const int p1 = m.spec_piece[k + 1];
+  int p = m.spec_piece[k];
+  T acc = part[p];
+  for (++p; p < p1; ++p) acc += part[p];
+  return acc;
 }
 
 // ------------------------------------------------------------ chemistry RHS
@@ -428,7 +518,7 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
   const Grp<G> g;
   const int ns = m.ns;
   const double T = uu[ns];
-  const double invT = 1.0 / T;
+  const double invT = rcp_newton(T);
   const double lnT = log(T);
   // species pass 1: thermo, Gibbs factors, sum Y/W
   double S = 0.0;
@@ -466,7 +556,7 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
   const bool aux = m.nx > 0;
   const bool cv = p < 0.0 || aux;
   const double esh = cv ? 1.0 : 0.0;  // h/RT -> u/RT and cp/R -> cv/R shift
-  const double invS = 1.0 / S;
+  const double invS = rcp_newton(S);
   // rho = p / (R T S), 1/rho = R T S / p, with 1/p (or 1/rho) from the caller
   const double rho = aux ? 1.0 : (cv ? -p : p * invT * invS * INV_R);
   const double invrho = aux ? 1.0 : (cv ? cs->pinv : R_GAS * T * S * cs->pinv);
@@ -480,7 +570,10 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     const double Ck = rho * uu[k] * m.invW[k];
     s.C[k] = Ck;
     if (MIXED && cache) s.fC[k] = __double2float_rn(Ck);
-    if (!direct_kc) exp_pm(s.gRT[k], m.etab, &s.E[k], &s.Einv[k]);
+    if (!direct_kc) {
+      if (MIXED) exp_pm_mixed(s.gRT[k], m.etab, &s.E[k], &s.Einv[k]);
+      else exp_pm(s.gRT[k], m.etab, &s.E[k], &s.Einv[k]);
+    }
     if (coop_tb) {
 #pragma unroll
       for (int t = 0; t < MAXM; ++t)
@@ -599,7 +692,7 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     const bool rev = (meta >> 2) & 1;
     const int dnu = ((meta >> 4) & 15) - 4;
     const double lnk = m.lnA[j] + m.bexp[j] * lnT - m.EaR[j] * invT;
-    double k = exp_fast(lnk, m.etab);
+    double k = MIXED ? exp_mixed(lnk, m.etab) : exp_fast(lnk, m.etab);
     const double Pf = s.C[ra] * s.C[rb];
     const double Pb = s.C[pa] * s.C[pb];
     double rfac = 0.0;  // 1/Kc
@@ -679,16 +772,17 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
   // species pass 2: w = nu^T q, dY/dt and the sums of the temperature equation
   double Sh = MIXED ? shq : 0.0, cb = 0.0;
   double Ax = 0.0, Bx = 0.0;  // auxiliary T: sum (u_k/RT) F_k / W_k and sum (cv_k/R) F_k / W_k
+  if (MIXED) gather_pieces<G, float>(m, g.lane, m.csr_nuf, s.fq, s.fpart);  // FP32 (q formed in FP64)
+  else gather_pieces<G, double>(m, g.lane, m.csr_nu, s.q, s.part);
+  g.sync();
   for (int k = g.lane; k < ns; k += G) {
-    double om = 0.0;
-    const int e0 = m.csr_ptr[k], e1 = m.csr_ptr[k + 1];
-    if (MIXED) {  // w = nu^T q in FP32 (q itself was formed in FP64)
-      float omf = 0.f;
-      for (int e = e0; e < e1; ++e) omf = fmaf(m.csr_nuf[e], s.fq[m.csr_j[e]], omf);
+    double om;
+    if (MIXED) {
+      const float omf = piece_sum(m, s.fpart, k);
       om = (double)omf;
       if (cache) s.fom[k] = omf;
     } else {
-      for (int e = e0; e < e1; ++e) om = fma(m.csr_nu[e], s.q[m.csr_j[e]], om);
+      om = piece_sum(m, s.part, k);
     }
     if (cache) s.om[k] = om;
     const double r = __dmul_rn(__dmul_rn(m.W[k], om), invrho);
@@ -726,7 +820,7 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     Sh = t2[0];
     cb = t2[1];
   }
-  const double invcb = 1.0 / cb;
+  const double invcb = rcp_newton(cb);
   double fT = 0.0;
   if (aux) {
     // Eq. aux_t_equation with specific internal energies e_k = (u_k/RT) R T / W_k
@@ -829,11 +923,11 @@ __device__ __noinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, cons
     s.q[j] = dq;
   }
   g.sync();
+  gather_pieces<G, double>(m, g.lane, m.csr_nu, s.q, s.part);
+  g.sync();
   double dSh = 0.0, dcb = 0.0;
   for (int k = g.lane; k < ns; k += G) {
-    double dom = 0.0;
-    const int e0 = m.csr_ptr[k], e1 = m.csr_ptr[k + 1];
-    for (int e = e0; e < e1; ++e) dom = fma(m.csr_nu[e], s.q[m.csr_j[e]], dom);
+    const double dom = piece_sum(m, s.part, k);
     out[k] = s.Einv[k] * fma(-s.om[k], drr, dom);  // Einv: W_k / rho
     dSh = fma(s.gRT[k], dom, fma(s.hRT[k], vT, dSh));
     dcb = fma(s.dcp[k], vT, fma(s.cp[k], v[k], dcb));
@@ -940,11 +1034,11 @@ __device__ __noinline__ void jvp_eval_f32(const MechView& m, const SlotPtrs& s, 
     s.fq[j] = dq;
   }
   g.sync();
+  gather_pieces<G, float>(m, g.lane, m.csr_nuf, s.fq, s.fpart);
+  g.sync();
   float dSh = 0.f, dcb = 0.f;
   for (int k = g.lane; k < ns; k += G) {
-    float dom = 0.f;
-    const int e0 = m.csr_ptr[k], e1 = m.csr_ptr[k + 1];
-    for (int e = e0; e < e1; ++e) dom = fmaf(m.csr_nuf[e], s.fq[m.csr_j[e]], dom);
+    const float dom = piece_sum(m, s.fpart, k);
     const float om = s.fom[k];
     const float vk = __double2float_rn(v[k]);
     out[k] = (double)(m.Wf[k] * (dom - om * drr) * invrho);
@@ -1844,6 +1938,12 @@ __global__ void exp_eval_kernel(const double* __restrict__ x, double* __restrict
   if (i >= n) return;
   if (which == 0) {
     y[i] = exp_fast(x[i], tab);
+  } else if (which == 3) {
+    y[i] = exp_mixed(x[i], tab);
+  } else if (which == 4 || which == 5) {
+    double ep, em;
+    exp_pm_mixed(x[i], tab, &ep, &em);
+    y[i] = which == 4 ? ep : em;
   } else {
     double ep, em;
     exp_pm(x[i], tab, &ep, &em);
@@ -2662,7 +2762,7 @@ int rk_probe_throughput(int32_t kind, double* ops_per_s) {
 }
 
 int rk_eval_exp(const double* x, double* y, int64_t n, int32_t which, void* stream) {
-  if (n < 0 || which < 0 || which > 2) return set_error(RK_E_INVALID_ARGUMENT, "bad exp arguments");
+  if (n < 0 || which < 0 || which > 5) return set_error(RK_E_INVALID_ARGUMENT, "bad exp arguments");
   if (n == 0) return RK_OK;
   if (!x || !y) return set_error(RK_E_INVALID_ARGUMENT, "null array");
   exp_eval_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, y, n, which);

@@ -370,6 +370,18 @@ def test_table_exp_matches_cuda_exp(rk):
         assert np.array_equal(y[keep], r[keep])
 
 
+def test_mixed_exp_close_to_cuda_exp(rk):
+    """The mixed-precision exp (FP64 reduction and reconstruction, FP32 for the
+    polynomial's small term) within 2e-12 relative of CUDA's exp."""
+    rng = np.random.default_rng(1)
+    x = np.concatenate([rng.uniform(-707.9, 707.9, 400000), rng.uniform(-3, 3, 200000), [0.0, 1e-300]])
+    xt = torch.tensor(x, device="cuda")
+    for which, sign in ((3, 1.0), (4, 1.0), (5, -1.0)):
+        y = rk.eval_exp(xt, which).cpu().numpy()
+        r = torch.exp(sign * xt).cpu().numpy()
+        assert np.max(np.abs(y - r) / r) < 2e-12
+
+
 def test_cuda_graph_capture_matches_eager(rk):
     """The split step captured once in a CUDA graph and replayed gives the same
     bits as the eager calls."""
