@@ -246,7 +246,7 @@ struct SlotLayout {
   int tb;                                     // [ntb][4]: [M], dk/d[M], dlnk/dT, 1/Kc
   int tro;                                    // [11][ntroe]: Troe falloff scratch
   int part;                                   // [npiece]: gather partial sums
-  int H, LU, piv, red;                        // small
+  int H, LU, piv, red, Bm;                    // small (Bm: I - (I - h gamma H)^-1)
   int fbase;  // FP32 region (mixed precision only), offset in doubles
   int fC, fdC, fh, fcp, fdcp, fom, fq, fkc, fkr, ftb, fQ, fw, fpart;  // offsets in floats from fbase
   int stride;
@@ -296,6 +296,7 @@ static SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false, int 
   s.LU = take(MAXM * MAXM);
   s.piv = take(MAXM);
   s.red = take(4);
+  s.Bm = take(MAXM * MAXM);
   s.fbase = o;
   int fo = 0;
   auto ftake = [&](int n) {
@@ -425,7 +426,7 @@ struct CellScalars {
 struct SlotPtrs {
   double *u, *src, *fn, *arg, *fr, *F, *w, *Q, *K;
   double *C, *dC, *cp, *hRT, *dcp, *gRT, *E, *Einv, *om, *q, *kc, *krc, *qT, *tb, *tro, *part;
-  double *H, *LU, *piv, *red;
+  double *H, *LU, *piv, *red, *Bm;
   float *fC, *fdC, *fh, *fcp, *fdcp, *fom, *fq, *fkc, *fkr, *ftb, *fQ, *fw, *fpart;  // mixed precision
   int Nq;  // stride between Krylov / stage vectors
 };
@@ -460,6 +461,7 @@ __device__ inline SlotPtrs slot_ptrs(double* b, const SlotLayout& s) {
   p.H = b + s.H;
   p.LU = b + s.LU;
   p.piv = b + s.piv;
+  p.Bm = b + s.Bm;
   p.red = b + s.red;
   float* f = reinterpret_cast<float*>(b + s.fbase);
   p.fC = f + s.fC;
@@ -1197,6 +1199,25 @@ __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& 
   return mdim;
 }
 
+// Solve (I - h gamma H) y = z in place (every lane, redundantly; the factor
+// stores reciprocal pivots, so the solve has no divisions).
+__device__ inline void solve_small(const SlotPtrs& s, int mdim, double* z) {
+  for (int c = 0; c < mdim; ++c) {
+    const int pr = (int)s.piv[c];
+    if (pr != c) {
+      const double t = z[c];
+      z[c] = z[pr];
+      z[pr] = t;
+    }
+  }
+  for (int r = 1; r < mdim; ++r)
+    for (int c = 0; c < r; ++c) z[r] = fma(-s.LU[r * MAXM + c], z[c], z[r]);
+  for (int r = mdim - 1; r >= 0; --r) {
+    for (int c = r + 1; c < mdim; ++c) z[r] = fma(-s.LU[r * MAXM + c], z[c], z[r]);
+    z[r] = z[r] * s.LU[r * MAXM + r];
+  }
+}
+
 // LU factorisation with partial pivoting of I - h gamma H (m x m), by lane 0.
 template <int G>
 __device__ inline void factor_small(const SlotPtrs& s, int mdim, double h) {
@@ -1235,26 +1256,18 @@ __device__ inline void factor_small(const SlotPtrs& s, int mdim, double h) {
     }
   }
   g.sync();
+  // B = I - (I - h gamma H)^-1, one column per lane (a solve with e_l), so each
+  // stage applies the low-rank correction as one matrix-vector product
+  if (g.lane < mdim) {
+    double x[MAXM];
+#pragma unroll
+    for (int i = 0; i < MAXM; ++i) x[i] = i == g.lane ? 1.0 : 0.0;
+    solve_small(s, mdim, x);
+    for (int i = 0; i < mdim; ++i) s.Bm[i * MAXM + g.lane] = (i == g.lane ? 1.0 : 0.0) - x[i];
+  }
+  g.sync();
 }
 
-// Solve (I - h gamma H) y = z in place (every lane, redundantly; the factor
-// stores reciprocal pivots, so the solve has no divisions).
-__device__ inline void solve_small(const SlotPtrs& s, int mdim, double* z) {
-  for (int c = 0; c < mdim; ++c) {
-    const int pr = (int)s.piv[c];
-    if (pr != c) {
-      const double t = z[c];
-      z[c] = z[pr];
-      z[pr] = t;
-    }
-  }
-  for (int r = 1; r < mdim; ++r)
-    for (int c = 0; c < r; ++c) z[r] = fma(-s.LU[r * MAXM + c], z[c], z[r]);
-  for (int r = mdim - 1; r >= 0; --r) {
-    for (int c = r + 1; c < mdim; ++c) z[r] = fma(-s.LU[r * MAXM + c], z[c], z[r]);
-    z[r] = z[r] * s.LU[r * MAXM + r];
-  }
-}
 
 // ------------------------------------------------ cost-ordered work queue
 // Cells are handed out longest-expected-first: the expected substep count of
@@ -1358,7 +1371,8 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
   }
   if (fixed) h = P.fixed_h;
   const long long n_fixed = fixed ? llround(dt / P.fixed_h) : 0;
-  double t = 0.0, ln_err_prev = 0.0, h_last = h;  // err_n = 1 before the first step
+  double t = 0.0, h_last = h;
+  float lg_err_prev = 0.f;  // log2 err_n; err_n = 1 before the first step
   int n_acc = 0, n_rej = 0, n_rhs = 0, status = RK_CELL_OK, n_att = 0;
   CellScalars cs;
   cs.pinv = 1.0 / fabs(pr);
@@ -1417,18 +1431,21 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
           if (l < mdim) part[l] = fma(s.Q[l * Nq + e], Fe, part[l]);
       }
       if (mdim > 0) sum_first<G>(g, part, mdim);
-      double z[MAXM], y[MAXM];
+      // c = (I - (I - h gamma H)^-1) Q^T F_i: lane l < m forms c_l, every lane then reads all
+      double cl = 0.0;
+      if (g.lane < mdim) {
 #pragma unroll
-      for (int l = 0; l < MAXM; ++l) {
-        z[l] = (l < mdim) ? part[l] : 0.0;
-        y[l] = z[l];
+        for (int c = 0; c < MAXM; ++c)
+          if (c < mdim) cl = fma(s.Bm[g.lane * MAXM + c], part[c], cl);
       }
-      solve_small(s, mdim, y);
+      double cz[MAXM];
+#pragma unroll
+      for (int l = 0; l < MAXM; ++l) cz[l] = __shfl_sync(g.mask, cl, l, G);
       for (int e = g.lane; e < N; e += G) {
         double acc = 0.0;
 #pragma unroll
         for (int l = 0; l < MAXM; ++l)
-          if (l < mdim) acc = fma(s.Q[l * Nq + e], z[l] - y[l], acc);
+          if (l < mdim) acc = fma(s.Q[l * Nq + e], cz[l], acc);
         Ki[e] = (s.F[e] - acc) - s.w[e];
       }
       g.sync();
@@ -1451,21 +1468,23 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
     const int att = n_att;
     n_att += 1;
     bool accept;
-    double hnew, ln_err = 0.0;
+    double hnew;
+    float lg_err = 0.f;
     if (fixed) {
       accept = true;
       hnew = h;
     } else {
-      // h* = h min(5, max(0.2, 0.8 err_n^beta / err*^alpha)) with the powers
-      // as exp(beta ln err_n - alpha ln err*) (ln err_n kept from acceptance)
+      // h* = h min(5, max(0.2, 0.8 err_n^beta / err*^alpha)), the factor in
+      // FP32 as 2^(beta log2 err_n - alpha log2 err*) (log2 err_n kept from
+      // acceptance); the accept test err <= 1 stays FP64
       const bool fin = (__double2hiint(err) & 0x7ff00000) != 0x7ff00000;
-      double fac = FAC_MIN;
-      ln_err = 0.0;
+      float fac = (float)FAC_MIN;
       if (fin) {
-        ln_err = log(fmax(err, ERR_FLOOR));
-        fac = fmin(FAC_MAX, fmax(FAC_MIN, SAFETY * exp_fast(PI_BETA * ln_err_prev - PI_ALPHA * ln_err, m.etab)));
+        lg_err = __log2f(fmaxf(__double2float_rn(err), (float)ERR_FLOOR));
+        fac = fminf((float)FAC_MAX,
+                    fmaxf((float)FAC_MIN, (float)SAFETY * exp2f((float)PI_BETA * lg_err_prev - (float)PI_ALPHA * lg_err)));
       }
-      hnew = h * fac;
+      hnew = h * (double)fac;
       accept = fin && err <= 1.0;
     }
     if (P.trace && att < P.trace_cap && g.lane == 0) P.trace[cell * P.trace_cap + att] = accept ? h : -h;
@@ -1477,7 +1496,7 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
       for (int e = g.lane; e < N; e += G) s.u[e] = s.arg[e];
       g.sync();
       t += h;
-      if (!fixed) ln_err_prev = ln_err;
+      if (!fixed) lg_err_prev = lg_err;
       n_acc += 1;
       h_last = hnew;
       h = hnew;
@@ -1699,9 +1718,12 @@ __device__ void integrate_cell_rkdp(const MechView& m, const SlotPtrs& s, const 
       hnew = h;
     } else {
       const bool fin = (__double2hiint(err) & 0x7ff00000) != 0x7ff00000;
-      double fac = FAC_MIN;
-      if (fin) fac = fmin(FAC_MAX, fmax(FAC_MIN, dp::SAFETY * exp_fast(-0.2 * log(fmax(err, ERR_FLOOR)), m.etab)));
-      hnew = h * fac;
+      float fac = (float)FAC_MIN;  // FP32 factor, as in the ROK4E controller
+      if (fin)
+        fac = fminf((float)FAC_MAX, fmaxf((float)FAC_MIN, (float)dp::SAFETY *
+                                                              exp2f(-0.2f * __log2f(fmaxf(__double2float_rn(err),
+                                                                                          (float)ERR_FLOOR)))));
+      hnew = h * (double)fac;
       accept = fin && err <= 1.0;
     }
     if (P.trace && att < P.trace_cap && g.lane == 0) P.trace[cell * P.trace_cap + att] = accept ? h : -h;
