@@ -473,6 +473,42 @@ def run_ours(args, rank, world, local_rank):
     kern_ms = [a.elapsed_time(b) for a, b in kev]
     graph_matches_eager = bool(torch.equal(U, U_graph))
 
+    # ---- critical path: the reaction sub-step of the first timed step for all
+    # cells, then for its most expensive cell alone (one warp on an otherwise
+    # idle GPU): a launch cannot end before its hottest cell's serial
+    # instruction stream has run
+    restore()
+    Tn = rk.diffusion_1d(U, D_DIFF, dx)
+    cp_opts = rk.Opts(lanes_per_cell=args.lanes, cells_per_block=args.cells_per_block,
+                      precision=PREC[args.precision], queue_order=args.queue_order,
+                      blocks_per_sm=args.blocks_per_sm)
+    cp_st = torch.zeros(npts, 4, dtype=torch.int32, device=dev)
+    cp_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    cp_t = []
+    for cells in (None, "hottest"):
+        if cells is None:
+            Yc, hcc, srcc, stc = U.clone(), hc_start.clone(), Tn, cp_st
+        else:
+            c = int(torch.argmax(cp_st[:, 0] + cp_st[:, 1]).item())
+            hot_attempts = int((cp_st[c, 0] + cp_st[c, 1]).item())
+            Yc, hcc, srcc = U[c:c + 1].clone(), hc_start[c:c + 1].clone(), Tn[c:c + 1].contiguous()
+            stc = torch.zeros(1, 4, dtype=torch.int32, device=dev)
+        ts = []
+        for _ in range(3):
+            Y2, h2 = Yc.clone(), hcc.clone()
+            flush.fill_(0.0)
+            cp_ev[0].record(stream)
+            rk.rok4e_integrate(m, Y2, w.dt, w.rtol, w.atol, M, src=srcc, h_cell=h2, opts=cp_opts, stats=stc,
+                               stream=stream)
+            cp_ev[1].record(stream)
+            torch.cuda.synchronize()
+            ts.append(cp_ev[0].elapsed_time(cp_ev[1]))
+        cp_t.append(min(ts))
+    critical_path = {"all_cells_ms": cp_t[0], "hottest_cell_alone_ms": cp_t[1],
+                     "hottest_cell_attempts": hot_attempts, "ratio": cp_t[0] / cp_t[1],
+                     "what": "reaction sub-step of the first timed split step: whole grid vs its most expensive "
+                             "cell integrated alone"}
+
     # ---- end to end through the public API with host buffers: the same steps
     # from the same state, with the state copied in from pinned host memory and
     # the result copied back every step
@@ -550,6 +586,7 @@ def run_ours(args, rank, world, local_rank):
                      "exp_flops_counted": EXP_FLOPS, "cuda_exp_cost_fma_measured": exp_fma,
                      "algorithmic_tflop_per_step": flops / args.steps / 1e12},
         "accuracy": accuracy,
+        "critical_path": critical_path,
         "cpu_baseline": {"value": cpu_v, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
                          "sample": f"{args.cpu_cells} cells spread over the grid (golden-ratio sequence), one "
                                    f"split step of the initial field ({cpu_t:.1f} s)"},
