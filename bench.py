@@ -36,7 +36,7 @@ D_DIFF = 1.0e-4  # m^2/s
 LENGTH = 1.0e-2  # m
 P_ATM = 101325.0
 L2_FLUSH_BYTES = 256 << 20
-PREC = {"fp64": 0, "mixed": 1, "mixed-fp32jv": 2}
+PREC = {"fp64": 0, "mixed": 1, "mixed-fp32jv": 2, "mixed-df": 3}
 
 
 def _env_int(k, d):

@@ -130,8 +130,9 @@ int rk_chem_rhs(const rk_mech* mech, const double* Y, const double* src, double 
  * derivative of rk_chem_rhs); mode 1: forward difference
  * (f(u + d v) - f(u)) / d with d = sqrt(eps) (1 + ||u||_2) / ||v||_2, as in
  * the matrix-free products of Sec. 4.3; mode 2: the analytic product
- * evaluated in FP32 (the mixed-precision integrator's J v).  All arrays
- * device [ncell x N]. */
+ * evaluated in FP32 (the mixed-precision integrator's J v); mode 3: the
+ * analytic product with its reaction-level core in double-float (precision
+ * level 3).  All arrays device [ncell x N]. */
 int rk_chem_jvp(const rk_mech* mech, const double* Y, const double* V, double p, double* JV,
                 int64_t ncell, int32_t mode, void* stream);
 
@@ -170,7 +171,12 @@ typedef struct rk_opts {
                              Gibbs factors, 1/Kc, rates of progress, heat release,
                              Jacobian-vector products, stage solves, error norm and
                              state update in FP64.  2: as 1 with the
-                             Jacobian-vector products in FP32 as well */
+                             Jacobian-vector products in FP32 as well.  3: FP64
+                             Arnoldi, stages, norm and update; the exponentials'
+                             polynomial tails in FP32 (~1e-12 relative); the
+                             Jacobian-vector product's reaction-level core
+                             (d(C_a C_b), dq, nu^T dq) in double-float (FP32
+                             pairs, ~44-bit significands) on the FP32 pipe */
   double* trace;          /* device [ncell x trace_cap]: +h accepted, -h rejected, 0 unused */
   void* ev_begin;         /* optional cudaEvent_t recorded on the stream right before the */
   void* ev_end;           /* integration kernel and right after it (timing hook), or NULL */

@@ -136,7 +136,9 @@ class Opts:
         self.h0, self.fixed_h = h0, fixed_h
         self.trace = trace  # CUDA float64 tensor [ncell, cap] or None
         self.events = events  # (begin, end) torch.cuda.Event pair around the integration kernel
-        self.precision = precision  # 0 FP64, 1 mixed (FP32 nu^T q and inner products), 2 + FP32 J v
+        # 0 FP64, 1 mixed (FP32 nu^T q and inner products), 2 + FP32 J v,
+        # 3 FP64 Krylov path with a double-float J v core and FP32 exp tails
+        self.precision = precision
         self.queue_order, self.blocks_per_sm = queue_order, blocks_per_sm
         self.rho_cell = rho_cell  # CUDA float64 [ncell]: constant-volume cells of these densities
         # 0 constant pressure, 1 constant volume (implied by rho_cell), 2 conservative

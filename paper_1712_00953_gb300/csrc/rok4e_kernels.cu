@@ -145,6 +145,42 @@ __device__ __forceinline__ double rcp_newton(double x) {
   return fma(r, e, r);
 }
 
+// ---- double-float ("df") arithmetic: a value h + l held as two FP32 numbers
+// with |l| <= ulp(h)/2, ~44-bit significand, on the FP32 pipe.  Products by
+// the error-free FMA split (Dekker's two-product), sums by Knuth's two-sum,
+// each renormalised.  FP32 exponent range: callers keep magnitudes inside it.
+struct df2 {
+  float h, l;
+};
+__device__ __forceinline__ df2 df_from(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(df2 a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ df2 df_norm(float s, float e) {
+  const float h = s + e;
+  return {h, e - (h - s)};
+}
+__device__ __forceinline__ df2 df_mul(df2 a, df2 b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return df_norm(p, e);
+}
+__device__ __forceinline__ df2 df_add(df2 a, df2 b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  const float e = ((a.h - (s - bb)) + (b.h - bb)) + (a.l + b.l);
+  return df_norm(s, e);
+}
+__device__ __forceinline__ df2 df_neg(df2 a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ df2 df_scale(float c, df2 a) {  // c * a with the exact product of c and a.h
+  const float p = c * a.h;
+  const float e = fmaf(c, a.h, -p);
+  return df_norm(p, fmaf(c, a.l, e));
+}
+
 // (exp(x), exp(-x)) sharing one argument reduction.
 __device__ __forceinline__ void exp_pm(double x, const double* __restrict__ tab, double* ep, double* em) {
   if ((__double2hiint(x) & 0x7fffffff) >= 0x40862000) {
@@ -246,6 +282,7 @@ struct SlotLayout {
   int tb;                                     // [ntb][4]: [M], dk/d[M], dlnk/dT, 1/Kc
   int tro;                                    // [11][ntroe]: Troe falloff scratch
   int part;                                   // [npiece]: gather partial sums
+  int C2, dC2;                                // species: double-float C and dC (precision 3)
   int H, LU, piv, red, Bm;                    // small (Bm: I - (I - h gamma H)^-1)
   int fbase;  // FP32 region (mixed precision only), offset in doubles
   int fC, fdC, fh, fcp, fdcp, fom, fq, fkc, fkr, ftb, fQ, fw, fpart;  // offsets in floats from fbase
@@ -292,6 +329,8 @@ static SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false, int 
   s.tb = take(4 * (L.ntb > 0 ? L.ntb : 1));
   s.tro = take(11 * (L.ntroe > 0 ? L.ntroe : 1));
   s.part = take(L.npiece > 0 ? L.npiece : 1);
+  s.C2 = take(ns1);
+  s.dC2 = take(ns1);
   s.H = take(MAXM * MAXM);
   s.LU = take(MAXM * MAXM);
   s.piv = take(MAXM);
@@ -417,6 +456,7 @@ __device__ __forceinline__ void sum_first(const Grp<G>& g, T (&v)[MAXM], int n) 
 struct CellScalars {
   double T, invT, lnT, S, invS, rho, invrho, cb, invcb, Sh;
   double pinv;  // 1 / p (constant pressure) or 1 / rho (constant volume): set by the caller
+  int prec;     // precision level (3: mixed exp in the RHS, double-float J v core): set by the caller
   // auxiliary-temperature system: sum_k (cp_k/R - 1) F_k / W_k, the T row
   // without its own source, 1 / rho and the velocity
   double B, fT, irho_c, vel[3];
@@ -426,6 +466,7 @@ struct CellScalars {
 struct SlotPtrs {
   double *u, *src, *fn, *arg, *fr, *F, *w, *Q, *K;
   double *C, *dC, *cp, *hRT, *dcp, *gRT, *E, *Einv, *om, *q, *kc, *krc, *qT, *tb, *tro, *part;
+  df2 *C2, *dC2;
   double *H, *LU, *piv, *red, *Bm;
   float *fC, *fdC, *fh, *fcp, *fdcp, *fom, *fq, *fkc, *fkr, *ftb, *fQ, *fw, *fpart;  // mixed precision
   int Nq;  // stride between Krylov / stage vectors
@@ -457,6 +498,8 @@ __device__ inline SlotPtrs slot_ptrs(double* b, const SlotLayout& s) {
   p.qT = b + s.qT;
   p.tro = b + s.tro;
   p.part = b + s.part;
+  p.C2 = reinterpret_cast<df2*>(b + s.C2);
+  p.dC2 = reinterpret_cast<df2*>(b + s.dC2);
   p.tb = b + s.tb;
   p.H = b + s.H;
   p.LU = b + s.LU;
@@ -572,8 +615,9 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     const double Ck = rho * uu[k] * m.invW[k];
     s.C[k] = Ck;
     if (MIXED && cache) s.fC[k] = __double2float_rn(Ck);
+    if (cache && cs->prec == 3) s.C2[k] = df_from(Ck);
     if (!direct_kc) {
-      if (MIXED) exp_pm_mixed(s.gRT[k], m.etab, &s.E[k], &s.Einv[k]);
+      if (MIXED || cs->prec == 3) exp_pm_mixed(s.gRT[k], m.etab, &s.E[k], &s.Einv[k]);
       else exp_pm(s.gRT[k], m.etab, &s.E[k], &s.Einv[k]);
     }
     if (coop_tb) {
@@ -694,7 +738,7 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     const bool rev = (meta >> 2) & 1;
     const int dnu = ((meta >> 4) & 15) - 4;
     const double lnk = m.lnA[j] + m.bexp[j] * lnT - m.EaR[j] * invT;
-    double k = MIXED ? exp_mixed(lnk, m.etab) : exp_fast(lnk, m.etab);
+    double k = (MIXED || cs->prec == 3) ? exp_mixed(lnk, m.etab) : exp_fast(lnk, m.etab);
     const double Pf = s.C[ra] * s.C[rb];
     const double Pb = s.C[pa] * s.C[pb];
     double rfac = 0.0;  // 1/Kc
@@ -761,9 +805,16 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
       // d ln Kc/dT = (sum_products h/RT - sum_reactants h/RT - dnu) / T.
       const double dnud = dnu > 0 ? 1.0 : (dnu < 0 ? -1.0 : 0.0);
       const double dlnKc = (s.hRT[pa] + s.hRT[pb] - s.hRT[ra] - s.hRT[rb] - dnud) * invT;
-      s.qT[j] = fma(k * dlnk, Pf, -kr * (dlnk - dlnKc) * Pb);
-      s.kc[j] = k;
-      s.krc[j] = kr;
+      const double qT = fma(k * dlnk, Pf, -kr * (dlnk - dlnKc) * Pb);
+      if (cs->prec == 3) {  // double-float copies for the J v core, in the same storage
+        reinterpret_cast<df2*>(s.qT)[j] = df_from(qT);
+        reinterpret_cast<df2*>(s.kc)[j] = df_from(k);
+        reinterpret_cast<df2*>(s.krc)[j] = df_from(kr);
+      } else {
+        s.qT[j] = qT;
+        s.kc[j] = k;
+        s.krc[j] = kr;
+      }
       if (MIXED) {
         s.fkc[j] = __double2float_rn(k);
         s.fkr[j] = __double2float_rn(kr);
@@ -969,6 +1020,106 @@ __device__ __noinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, cons
   g.sync();
 }
 
+// Analytic J v with its reaction-level core in double-float (precision 3):
+// dP = d(C_a C_b), dq_j = qT_j vT + k_j dPf - kr_j dPb and the gather
+// dw = nu^T dq run on the FP32 pipe with ~44-bit significands from the
+// double-float copies rhs_eval wrote at u_n; the species and temperature rows
+// (and the third-body / falloff corrections) stay FP64.  Same derivative as
+// jvp_eval to ~1e-13 relative, so the Krylov basis is that of the FP64 path.
+template <int G>
+__device__ __noinline__ void jvp_eval_df(const MechView& m, const SlotPtrs& s, const double* uu,
+                                         const CellScalars& cs, const double* v, double* out) {
+  const Grp<G> g;
+  const int ns = m.ns;
+  const double vT = v[ns];
+  const double T = cs.T, invT = cs.invT;
+  double a = 0.0;
+  for (int k = g.lane; k < ns; k += G) a = fma(v[k], m.invW[k], a);
+  a = g.sum(a);
+  const double drr = cs.cv ? 0.0 : -fma(a, cs.invS, vT * invT);
+  const bool coop_tb = m.ntb > 0 && m.ntb <= MAXM;
+  double mp[MAXM];
+#pragma unroll
+  for (int t = 0; t < MAXM; ++t) mp[t] = 0.0;
+  for (int k = g.lane; k < ns; k += G) {
+    const double dCk = fma(s.C[k], drr, s.E[k] * v[k]);  // E: rho / W_k
+    s.dC[k] = dCk;
+    s.dC2[k] = df_from(dCk);
+    if (coop_tb) {
+#pragma unroll
+      for (int t = 0; t < MAXM; ++t)
+        if (t < m.ntb) mp[t] = fma(m.eff[t * ns + k], dCk, mp[t]);
+    }
+  }
+  if (coop_tb) sum_first<G>(g, mp, m.ntb);
+  g.sync();
+  const df2 vT2 = df_from(vT);
+  const df2* k2 = reinterpret_cast<const df2*>(s.kc);
+  const df2* kr2 = reinterpret_cast<const df2*>(s.krc);
+  const df2* qT2 = reinterpret_cast<const df2*>(s.qT);
+  df2* dq2 = reinterpret_cast<df2*>(s.q);
+  for (int j = g.lane; j < m.nr; j += G) {
+    const uint32_t sl = m.slots[j];
+    const int ra = sl & 255, rb = (sl >> 8) & 255, pa = (sl >> 16) & 255, pb = sl >> 24;
+    const int meta = m.meta[j];
+    const int kind = meta & 3;
+    const df2 dPf = df_add(df_mul(s.dC2[ra], s.C2[rb]), df_mul(s.C2[ra], s.dC2[rb]));
+    const df2 dPb = df_add(df_mul(s.dC2[pa], s.C2[pb]), df_mul(s.C2[pa], s.dC2[pb]));
+    df2 dq = df_add(df_mul(qT2[j], vT2), df_add(df_mul(k2[j], dPf), df_neg(df_mul(kr2[j], dPb))));
+    if (kind != 0) {  // third body / falloff: the [M] terms in FP64
+      const int slot = meta >> 8;
+      const double* t = s.tb + 4 * slot;
+      const double Pf = s.C[ra] * s.C[rb];
+      const double Pb = s.C[pa] * s.C[pb];
+      double dM = 0.0;
+      if (coop_tb) {
+#pragma unroll
+        for (int q = 0; q < MAXM; ++q)
+          if (q == slot) dM = mp[q];
+      } else {
+        const double* e = m.eff + (size_t)slot * ns;
+        for (int q = 0; q < ns; ++q) dM = fma(e[q], s.dC[q], dM);
+      }
+      const double dqd = df_to(dq);
+      double r;
+      if (kind == 1) r = t[0] * dqd + dM * (df_to(k2[j]) * Pf - df_to(kr2[j]) * Pb);
+      else r = dqd + t[1] * dM * (Pf - t[3] * Pb);
+      dq = df_from(r);
+    }
+    dq2[j] = dq;
+  }
+  g.sync();
+  df2* part2 = reinterpret_cast<df2*>(s.part);
+  for (int p = g.lane; p < m.npiece; p += G) {
+    df2 acc = {0.0f, 0.0f};
+    const int e1 = m.piece_ptr[p + 1];
+    for (int e = m.piece_ptr[p]; e < e1; ++e) acc = df_add(acc, df_scale(m.csr_nuf[e], dq2[m.csr_j[e]]));
+    part2[p] = acc;
+  }
+  g.sync();
+  double dSh = 0.0, dcb = 0.0;
+  for (int k = g.lane; k < ns; k += G) {
+    const int p1 = m.spec_piece[k + 1];
+    int p = m.spec_piece[k];
+    df2 acc = part2[p];
+    for (++p; p < p1; ++p) acc = df_add(acc, part2[p]);
+    const double dom = df_to(acc);
+    out[k] = s.Einv[k] * fma(-s.om[k], drr, dom);  // Einv: W_k / rho
+    dSh = fma(s.gRT[k], dom, fma(s.hRT[k], vT, dSh));
+    dcb = fma(s.dcp[k], vT, fma(s.cp[k], v[k], dcb));
+  }
+  {
+    double t2[2] = {dSh, dcb};
+    sum_many<G, 2>(g, t2);
+    dSh = t2[0];
+    dcb = t2[1];
+  }
+  if (g.lane == 0) {
+    out[ns] = (-(vT * cs.Sh + T * dSh) + T * cs.Sh * (drr + dcb * cs.invcb)) * (cs.invrho * cs.invcb);
+  }
+  g.sync();
+}
+
 // Reduced-precision analytic J v (mixed mode): the same derivative as
 // jvp_eval evaluated in FP32 from the FP32 copies cached by
 // rhs_eval<G, true>(..., cache = true).  v and out stay FP64 vectors.
@@ -1074,6 +1225,7 @@ __device__ inline void apply_jv(const MechView& m, const SlotPtrs& s, const Cell
   const int N = m.ns + 1 + m.nx;
   if (jv_mode == 0) {
     if (MIXED && fp32_jv) jvp_eval_f32<G>(m, s, s.u, cs, v, out);
+    else if (!MIXED && cs.prec == 3) jvp_eval_df<G>(m, s, s.u, cs, v, out);
     else jvp_eval<G>(m, s, s.u, cs, v, out);
     return;
   }
@@ -1088,6 +1240,7 @@ __device__ inline void apply_jv(const MechView& m, const SlotPtrs& s, const Cell
   g.sync();
   CellScalars dummy;
   dummy.pinv = cs.pinv;
+  dummy.prec = cs.prec;
   rhs_eval<G, MIXED>(m, s, s.arg, s.src, p, out, false, &dummy);
   *n_rhs += 1;
   for (int e = g.lane; e < N; e += G) out[e] = (out[e] - s.fn[e]) / d;
@@ -1376,6 +1529,7 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
   int n_acc = 0, n_rej = 0, n_rhs = 0, status = RK_CELL_OK, n_att = 0;
   CellScalars cs;
   cs.pinv = 1.0 / fabs(pr);
+  cs.prec = P.precision == 3 ? 3 : 0;
   rhs_eval<G, MIXED>(m, s, s.u, srcp, pr, s.fn, true, &cs);
   n_rhs += 1;
   int mdim = arnoldi<G, MIXED>(m, s, cs, P.M, P.jv_mode, pr, &n_rhs, fp32_jv);
@@ -1541,6 +1695,8 @@ __device__ inline void init_sentinels(const SlotPtrs& s, int ns, int lane) {
   if (lane == 0) {
     s.C[ns] = 1.0;
     s.dC[ns] = 0.0;
+    s.C2[ns] = {1.0f, 0.0f};
+    s.dC2[ns] = {0.0f, 0.0f};
     s.hRT[ns] = 0.0;
     s.gRT[ns] = 0.0;
     s.E[ns] = 1.0;
@@ -1658,6 +1814,7 @@ __device__ void integrate_cell_rkdp(const MechView& m, const SlotPtrs& s, const 
   int n_acc = 0, n_rej = 0, n_rhs = 0, status = RK_CELL_OK, n_att = 0;
   CellScalars cs;
   cs.pinv = 1.0 / fabs(pr);
+  cs.prec = 0;
   // stage vectors k1..k7; k1 and k7 swap roles after an accepted step
   double* k1 = s.fn;
   double* k2 = s.K;
@@ -1852,7 +2009,8 @@ struct PointParams {
   double* out;
   int64_t ncell;
   double p;
-  int mode;  // 0 rhs, 1 analytic jvp, 2 finite-difference jvp, 3 mixed rhs, 4 FP32 analytic jvp
+  int mode;  // 0 rhs, 1 analytic jvp, 2 finite-difference jvp, 3 mixed rhs, 4 FP32 analytic jvp,
+             // 5 analytic jvp with the double-float core
   const double* rho_cell;  // constant-volume densities, or null
   int nx;                  // state components after T (5: auxiliary-temperature system)
 };
@@ -1885,6 +2043,7 @@ __global__ void __launch_bounds__(512) chem_point_kernel(PointParams P) {
   const double pr = P.rho_cell ? -P.rho_cell[cell] : P.p;
   CellScalars cs;
   cs.pinv = 1.0 / fabs(pr);
+  cs.prec = 0;
   if (P.mode == 0 || P.mode == 3) {
     if (P.mode == 3) rhs_eval<G, true>(m, s, s.u, P.src ? s.src : nullptr, pr, s.fr, false, &cs);
     else rhs_eval<G>(m, s, s.u, P.src ? s.src : nullptr, pr, s.fr, false, &cs);
@@ -1894,6 +2053,13 @@ __global__ void __launch_bounds__(512) chem_point_kernel(PointParams P) {
   if (P.mode == 4) {
     rhs_eval<G, true>(m, s, s.u, nullptr, pr, s.fn, true, &cs);
     jvp_eval_f32<G>(m, s, s.u, cs, s.F, s.w);
+    for (int e = g.lane; e < N; e += G) P.out[cell * N + e] = s.w[e];
+    return;
+  }
+  if (P.mode == 5) {
+    cs.prec = 3;
+    rhs_eval<G>(m, s, s.u, nullptr, pr, s.fn, true, &cs);
+    jvp_eval_df<G>(m, s, s.u, cs, s.F, s.w);
     for (int e = g.lane; e < N; e += G) P.out[cell * N + e] = s.w[e];
     return;
   }
@@ -2165,9 +2331,9 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   if (o.trace_cap < 0 || (o.trace_cap > 0 && !o.trace))
     return set_error(RK_E_INVALID_ARGUMENT, "trace_cap > 0 needs a trace array");
   if (o.fixed_h < 0.0 || !isfinite(o.fixed_h)) return set_error(RK_E_INVALID_ARGUMENT, "fixed_h must be >= 0");
-  if (o.precision < 0 || o.precision > 2) return set_error(RK_E_INVALID_ARGUMENT, "precision must be 0, 1 or 2");
+  if (o.precision < 0 || o.precision > 3) return set_error(RK_E_INVALID_ARGUMENT, "precision must be 0..3");
   if (method == 1 && o.precision != 0) return set_error(RK_E_INVALID_ARGUMENT, "the explicit integrator is FP64 only");
-  const bool mixed = o.precision >= 1;
+  const bool mixed = o.precision == 1 || o.precision == 2;  // level 3 runs the FP64 kernel with cs.prec = 3
   const int G = o.lanes_per_cell == 0 ? 32 : o.lanes_per_cell;
   if (G != 8 && G != 16 && G != 32) return set_error(RK_E_INVALID_ARGUMENT, "lanes_per_cell must be 0, 8, 16 or 32");
   if (!workspace || workspace_bytes < rk_rok4e_workspace_size(mech, ncell, M, opts))
@@ -2365,8 +2531,9 @@ int rk_chem_rhs(const rk_mech* mech, const double* Y, const double* src, double 
 
 int rk_chem_jvp(const rk_mech* mech, const double* Y, const double* V, double p, double* JV, int64_t ncell,
                 int32_t mode, void* stream) {
-  if (mode < 0 || mode > 2) return set_error(RK_E_INVALID_ARGUMENT, "mode must be 0, 1 or 2");
-  return point_call(mech, Y, nullptr, V, p, JV, ncell, mode == 0 ? 1 : (mode == 1 ? 2 : 4), stream);
+  if (mode < 0 || mode > 3) return set_error(RK_E_INVALID_ARGUMENT, "mode must be 0..3");
+  return point_call(mech, Y, nullptr, V, p, JV, ncell, mode == 0 ? 1 : (mode == 1 ? 2 : (mode == 2 ? 4 : 5)),
+                    stream);
 }
 
 int rk_chem_rhs_mixed(const rk_mech* mech, const double* Y, const double* src, double p, double* dYdt,

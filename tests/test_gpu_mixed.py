@@ -68,6 +68,26 @@ def test_fp32_jvp_close_to_oracle(rk, name):
     assert np.max(np.abs(out - ref) / scale) < 1e-4
 
 
+@pytest.mark.parametrize("name", ["small", "flame1d", "batched"])
+def test_double_float_jvp_close_to_oracle(rk, name):
+    """The J v with its reaction-level core in double-float (precision 3)
+    against the oracle's analytic Jacobian: ~1e-12 of the row scale, far inside
+    what the Krylov basis needs (the FP32 J v is ~1e-5)."""
+    from oracle.kinetics import Kinetics
+    from synth.fields import field_uniform
+
+    w, mech = _mech(name)
+    kin = Kinetics(mech)
+    U = field_uniform(48, mech.n_species, 19, 600.0, 2500.0)
+    V = np.random.default_rng(4).normal(size=U.shape)
+    V /= np.linalg.norm(V, axis=1, keepdims=True)
+    m = rk.mech_load(mech)
+    out = rk.chem_jvp(m, torch.tensor(U, device="cuda"), torch.tensor(V, device="cuda"), P, mode=3).cpu().numpy()
+    ref = np.array([kin.jvp(u, P, v) for u, v in zip(U, V)])
+    scale = np.max(np.abs(ref), axis=1, keepdims=True)
+    assert np.max(np.abs(out - ref) / scale) < 1e-11
+
+
 def _run(rk, mech, U, w, precision, cap=8192, M=4):
     m = rk.mech_load(mech)
     Y = torch.tensor(U, device="cuda")
@@ -79,7 +99,7 @@ def _run(rk, mech, U, w, precision, cap=8192, M=4):
     return Y.cpu().numpy(), st.cpu().numpy(), tr.cpu().numpy()
 
 
-@pytest.mark.parametrize("precision,t_bar", [(1, 1e-6), (2, 1e-5)])
+@pytest.mark.parametrize("precision,t_bar", [(1, 1e-6), (2, 1e-5), (3, 1e-6)])
 def test_mixed_integration_error_vs_fp64_oracle(rk, precision, t_bar):
     """Mixed-precision ROK4E on the small workload, replayed through the FP64
     oracle.  Level 1 (FP64 J v) stays within the library's bar
@@ -115,7 +135,7 @@ def test_mixed_split_steps_vs_fp64_gpu(rk):
     _, U0 = field_tanh_front(512, mech.n_species, w.field_seed)
     dx = 1e-2 / 512
     res = {}
-    for prec in (0, 1, 2):
+    for prec in (0, 1, 2, 3):
         U = torch.tensor(U0, device="cuda")
         hc = torch.zeros(512, dtype=torch.float64, device="cuda")
         for _ in range(5):
@@ -124,7 +144,7 @@ def test_mixed_split_steps_vs_fp64_gpu(rk):
         torch.cuda.synchronize()
         res[prec] = U.cpu().numpy()
     ns = mech.n_species
-    for prec in (1, 2):
+    for prec in (1, 2, 3):
         dY = np.abs(res[prec][:, :ns] - res[0][:, :ns])
         dT = np.abs(res[prec][:, ns] - res[0][:, ns])
         print(f"mixed level {prec} vs FP64 GPU after 5 split steps: max |dY| {dY.max():.3e} (per species "
