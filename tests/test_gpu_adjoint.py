@@ -128,8 +128,12 @@ def test_autograd_function(rk):
 def test_adjoint_full_size_sampled(rk):
     """The adjoint workload at full size (4096 cells, 100 species / 500
     reactions, 50 fixed steps of 1e-7 s): the adjoint seeded on two sampled
-    cells' final temperatures, checked along a random direction in ln A against
-    the oracle's complex-step directional derivative of those two cells."""
+    cells' final temperatures (the coldest and the hottest), checked along a
+    random direction in ln A against the oracle's complex-step directional
+    derivative of those two cells.  The hot cell's derivative is ill-conditioned
+    (a 1e-13 relative change of its initial temperature moves it by ~1e-6
+    relative in the oracle itself), so the bar per cell is ten times the
+    oracle's own spread under such perturbations, plus 1e-9 relative."""
     from oracle import adjoint as oad
     from oracle.kinetics import Kinetics
     from synth.fields import WORKLOADS, initial_state, mechanism_for
@@ -154,11 +158,17 @@ def test_adjoint_full_size_sampled(rk):
     kin = Kinetics(mech)
     d = np.random.default_rng(7).normal(size=mech.n_reactions)
     d /= np.linalg.norm(d)
-    ref = 0.0
+    lnA = kin.lnA_input.astype(complex) + 1j * oad.CS_EPS * d
+    ref, tol = 0.0, 0.0
     for c in cells:
-        lnA = kin.lnA_input.astype(complex) + 1j * oad.CS_EPS * d
-        uf = oad.final_state(kin, U[c].astype(complex), P, h, nsteps, w.krylov_dim, lnA)
-        ref += float(np.imag(uf[-1])) / oad.CS_EPS
+        vals = []
+        for pert in (0.0, 1e-13, -1e-13):
+            u0 = U[c].copy()
+            u0[-1] *= 1.0 + pert
+            uf = oad.final_state(kin, u0.astype(complex), P, h, nsteps, w.krylov_dim, lnA)
+            vals.append(float(np.imag(uf[-1])) / oad.CS_EPS)
+        ref += vals[0]
+        tol += 10.0 * max(abs(vals[1] - vals[0]), abs(vals[2] - vals[0])) + 1e-9 * abs(vals[0])
     got = float(grad @ d)
-    print(f"full-size adjoint, directional derivative: GPU {got:.10e}, oracle {ref:.10e}")
-    assert abs(got - ref) <= 1e-7 * max(abs(ref), np.max(np.abs(grad)))
+    print(f"full-size adjoint, directional derivative: GPU {got:.10e}, oracle {ref:.10e}, bar {tol:.2e}")
+    assert abs(got - ref) <= tol
