@@ -162,7 +162,8 @@ typedef struct rk_opts {
   int32_t jv_mode;        /* 0 analytic Jacobian-vector products (default), 1 finite difference */
   int32_t max_attempts;   /* per-cell cap on attempted steps; <= 0: 100000 */
   int32_t lanes_per_cell; /* 0 auto; 8, 16 or 32 lanes of a warp share one cell */
-  int32_t cells_per_block;/* 0 auto (as many as shared memory allows) */
+  int32_t cells_per_block;/* 0 auto: as many as shared memory allows, at most
+                             256 threads per block (8 cells of 32 lanes) */
   double h0;              /* first step when h_cell is NULL or holds <= 0; <= 0: dt */
   double fixed_h;         /* > 0: fixed steps of this size, no error control */
   int32_t trace_cap;      /* attempts recorded per cell into trace (0: none) */

@@ -56,6 +56,10 @@ constexpr double FAC_MIN = 0.2, FAC_MAX = 5.0, SAFETY = 0.8, ERR_FLOOR = 1e-10;
 constexpr double BREAKDOWN_TOL = 1e-12, T_END_TOL = 1e-12, H_MIN_FRAC = 1e-12;
 constexpr int G_OVERFLOW_HI = 0x40654000;  // high word of 170.0
 constexpr int MAXM = RK_MAX_KRYLOV;
+// Threads per block of the per-cell kernels: 8 warps, so each thread may hold
+// up to 255 registers (one such block fills an SM's register file, which the
+// cells' shared-memory slots limit the SM to anyway).
+constexpr int MAX_BLOCK_THREADS = 256;
 constexpr int EXP_TAB_BYTES = RK_EXP2_TABLE_N * 8;  // leads the dynamic shared memory
 
 __constant__ double c_exp2_table[RK_EXP2_TABLE_N] = {RK_EXP2_TABLE_VALUES};
@@ -1751,7 +1755,7 @@ __device__ __forceinline__ void drain_queue(const IntegrateParams& P, const Grp<
 }
 
 template <int G, bool MIXED>
-__global__ void __launch_bounds__(512) rok4e_integrate_kernel(IntegrateParams P) {
+__global__ void __launch_bounds__(MAX_BLOCK_THREADS, 1) rok4e_integrate_kernel(IntegrateParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   load_exp_table(reinterpret_cast<double*>(smem));
   load_mech(smem + EXP_TAB_BYTES, P.mech, P.L.bytes);
@@ -1921,7 +1925,7 @@ __device__ void integrate_cell_rkdp(const MechView& m, const SlotPtrs& s, const 
 }
 
 template <int G>
-__global__ void __launch_bounds__(512) rkdp_integrate_kernel(IntegrateParams P) {
+__global__ void __launch_bounds__(MAX_BLOCK_THREADS) rkdp_integrate_kernel(IntegrateParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   load_exp_table(reinterpret_cast<double*>(smem));
   load_mech(smem + EXP_TAB_BYTES, P.mech, P.L.bytes);
@@ -2016,7 +2020,7 @@ struct PointParams {
 };
 
 template <int G>
-__global__ void __launch_bounds__(512) chem_point_kernel(PointParams P) {
+__global__ void __launch_bounds__(MAX_BLOCK_THREADS) chem_point_kernel(PointParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   load_exp_table(reinterpret_cast<double*>(smem));
   load_mech(smem + EXP_TAB_BYTES, P.mech, P.L.bytes);
@@ -2261,7 +2265,7 @@ int plan_for(K kernel, const rk_mech* mech, const SlotLayout& S, int want_cells,
   if (mech_bytes + slot_bytes > smem_max)
     return set_error(RK_E_UNSUPPORTED, "mechanism plus one cell's work arrays exceed shared memory");
   int cells = (int)((smem_max - mech_bytes) / slot_bytes);
-  cells = cells > 512 / G ? 512 / G : cells;
+  cells = cells > MAX_BLOCK_THREADS / G ? MAX_BLOCK_THREADS / G : cells;
   if (want_cells > 0 && want_cells < cells) cells = want_cells;
   if (!persistent && (int64_t)cells > ncell) cells = (int)(ncell > 0 ? ncell : 1);
   size_t smem = mech_bytes + (size_t)cells * slot_bytes;
