@@ -142,6 +142,38 @@ def _psr_flows(Da):
     return flow_T, flow_R
 
 
+@pytest.mark.parametrize("case", ["extinction", "ignition"])
+def test_near_limit_psr_strang_early_onset(case):
+    """Sec. 3.5's near-limit cases of the scalar PSR: with a fixed splitting
+    step, Strang splitting extinguishes (ignites) far too early, while simple
+    and Simpler balanced splitting, which keep the steady states, follow the
+    unsplit solution's slow passage to within a step or two."""
+    Da = _paper(f"psr_Da_near_{case}")
+    T0 = _paper(f"psr_T0_near_{case}")
+    thr, t_end, h = (0.4, 2000.0, Da / 10) if case == "extinction" else (0.6, 4e5, Da / 2)
+    hit = (lambda T: T < thr) if case == "extinction" else (lambda T: T > thr)
+    ref = solve_ivp(lambda t, y: sum(sp.psr_rhs_parts(y, Da)), (0, t_end), [T0], rtol=1e-12, atol=1e-14,
+                    method="LSODA", dense_output=True)
+    ts = np.linspace(0, t_end, 200001)
+    t_ref = ts[np.argmax(hit(ref.sol(ts)[0]))]
+    flow_T, flow_R = _psr_flows(Da)
+    Top = lambda T: sp.psr_rhs_parts(T, Da)[1]
+    Rop = lambda T: sp.psr_rhs_parts(T, Da)[0]
+    steps = {"strang": lambda T: sp.strang_step(T, h, flow_T, flow_R),
+             "simpler": lambda T: sp.simpler_step(T, h, Top, flow_T, flow_R),
+             "simple_balanced": lambda T: sp.simple_balanced_step(T, h, Top, Rop, flow_T, flow_R)}
+    onset = {}
+    for name, step in steps.items():
+        T, t = T0, 0.0
+        while t < t_end and not hit(T):
+            T, t = step(T), t + h
+        onset[name] = t
+    print(f"{case}: unsplit {t_ref:.1f}, " + ", ".join(f"{k} {v:.1f}" for k, v in onset.items()))
+    assert onset["strang"] < 0.7 * t_ref
+    for name in ("simpler", "simple_balanced"):
+        assert abs(onset[name] - t_ref) < 0.02 * t_ref
+
+
 def test_simpler_second_order_on_scalar_psr():
     Da = 100.0
     T0, t_end = 0.6, 2.0
