@@ -923,9 +923,11 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
 }
 
 // Analytic Jacobian-vector product out = J(u_n) v, using the values cached by
-// the last rhs_eval(..., cache = true) at u_n.  v, out: N-vectors.
+// the last rhs_eval(..., cache = true) at u_n.  v, out: N-vectors.  Inlined
+// (unlike rhs_eval, nothing requires two call sites to produce the same bits),
+// which saves the call's register save and restore four times per attempt.
 template <int G>
-__device__ __noinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, const double* uu,
+__device__ __forceinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, const double* uu,
                                       const CellScalars& cs, const double* v, double* out) {
   const Grp<G> g;
   const int ns = m.ns;
@@ -1031,7 +1033,7 @@ __device__ __noinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, cons
 // (and the third-body / falloff corrections) stay FP64.  Same derivative as
 // jvp_eval to ~1e-13 relative, so the Krylov basis is that of the FP64 path.
 template <int G>
-__device__ __noinline__ void jvp_eval_df(const MechView& m, const SlotPtrs& s, const double* uu,
+__device__ __forceinline__ void jvp_eval_df(const MechView& m, const SlotPtrs& s, const double* uu,
                                          const CellScalars& cs, const double* v, double* out) {
   const Grp<G> g;
   const int ns = m.ns;
