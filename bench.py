@@ -612,8 +612,15 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "flushed (256 MB write) between steps", "parallelism": f"replicas x{world}",
                    "lanes_per_cell": args.lanes or 32, "cells_per_block": args.cells_per_block,
                    "queue_order": args.queue_order, "blocks_per_sm": args.blocks_per_sm},
+        # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one fp64
+        # integration launch of this workload, from the ncu capture summarised in
+        # profiles/rok4e_integrate_flame1d.md (bytes per launch; it describes the
+        # kernel as profiled there and goes stale when the kernel changes)
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_nominal, "unit": "TFLOP/s",
-                     "frac": achieved / peak_nominal, "traffic": None,
+                     "frac": achieved / peak_nominal,
+                     "traffic": 2284288 if args.precision == "fp64" else None,
+                     "traffic_unit": "bytes per launch (ncu capture)",
+                     "algorithmic_bytes_per_launch": int(npts * N * 8 * 3 + npts * (16 + 16)),
                      "kernel": "rok4e_integrate_kernel<32>", "kernel_ms_per_step": 1e3 * kern_total / args.steps,
                      "peak_probe_fp64": peak_meas, "frac_of_probe": achieved / peak_meas,
                      "exp_flops_counted": EXP_FLOPS, "cuda_exp_cost_fma_measured": exp_fma,
