@@ -85,6 +85,31 @@ def algorithmic_flops(model, stats, M, exp_flops=EXP_FLOPS):
     return float(rhs_total + n_arn * (M * model["jvp"] + model["arnoldi"]) + (n_acc + n_rej) * model["attempt"])
 
 
+def shard_range(n, rank, world):
+    """Contiguous, near-equal slice [lo, hi) of n independent cells for one rank."""
+    return n * rank // world, n * (rank + 1) // world
+
+
+def reduce_stats(st, dist, device):
+    """Totals over every rank's cells from per-cell statistics [n_local, 4]
+    (accepted, rejected, RHS evaluations, status): summed accepted steps,
+    attempts and RHS evaluations, the largest substep count, the number of
+    failed cells and of cells (a sum and a max all-reduce); without ``dist``
+    the local totals."""
+    import torch
+
+    st = np.asarray(st, dtype=np.int64).reshape(-1, 4)
+    sums = torch.tensor([float(st[:, 0].sum()), float((st[:, 0] + st[:, 1]).sum()), float(st[:, 2].sum()),
+                         float((st[:, 3] != 0).sum()), float(st.shape[0])], dtype=torch.float64, device=device)
+    mx = torch.tensor([float(st[:, 0].max()) if st.shape[0] else 0.0], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(sums, op=dist.ReduceOp.SUM)
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    acc, a, r, f, c = (float(x) for x in sums.cpu())
+    return {"accepted": acc, "attempts": a, "rhs": r, "failed_cells": int(f), "cells": int(c),
+            "substeps_max": int(mx.item())}
+
+
 def max_over_ranks(t, dist, device):
     """The slowest rank's time (every rank gets it); ``dist`` is None for one process."""
     if dist is None:
@@ -296,7 +321,10 @@ def run_unit_costs(args):
 def run_batched(args, rank, world, local_rank):
     """The batched workload: 2^20 independent constant-pressure cells from a
     Gaussian random temperature field, one ROK4E integration of dt = 1e-6 s
-    (M = 4) per step from the same initial field; cell-steps/s."""
+    (M = 4) per step from the same initial field; cell-steps/s.  On N GPUs the
+    2^20 cells are sharded contiguously over the ranks (strong scaling: the
+    cells are independent, so no data moves between GPUs); the statistics are
+    all-reduced and the time is the slowest rank's."""
     import torch
 
     import paper_1712_00953_gb300 as rk
@@ -304,9 +332,19 @@ def run_batched(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist = dist_mod
+        dist.init_process_group("nccl", device_id=dev)
     w = WORKLOADS["batched"]
     mech = mechanism_for(w)
-    U0 = torch.tensor(initial_state(w), device=dev)
+    U_all = initial_state(w)
+    n_total = U_all.shape[0]
+    lo, hi = shard_range(n_total, rank, world)
+    U0 = torch.tensor(U_all[lo:hi], device=dev)
+    del U_all
     n = U0.shape[0]
     m = rk.mech_load(mech)
     M = w.krylov_dim
@@ -322,6 +360,8 @@ def run_batched(args, rank, world, local_rank):
         Y.copy_(U0)
         rk.rok4e_integrate(m, Y, w.dt, w.rtol, w.atol, M, opts=o, workspace=ws)
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     kern = 0.0
     flops = 0.0
     model = flop_model(mech, M)
@@ -331,15 +371,25 @@ def run_batched(args, rank, world, local_rank):
         torch.cuda.synchronize()
         kern += ev[0].elapsed_time(ev[1]) * 1e-3
         flops += algorithmic_flops(model, st.cpu().numpy(), M)
-    s = st.cpu().numpy()
+    kern_max = max_over_ranks(kern, dist, dev)
+    flops_all = flops
+    tot = reduce_stats(st.cpu().numpy(), dist, dev)
+    if dist:
+        fl = torch.tensor([flops], dtype=torch.float64, device=dev)
+        dist.all_reduce(fl, op=dist.ReduceOp.SUM)
+        flops_all = float(fl.item())
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
     line = {"workload": "batched: 2^20 cells, 53 species / 325 reactions, one 1e-6 s ROK4E step, M=4",
-            "precision": args.precision, "cell_steps_per_s": n * args.steps / kern,
-            "kernel_s_per_step": kern / args.steps,
-            "roofline": {"bound": "alu", "achieved": flops / kern / 1e12, "peak": 1.25, "unit": "TFLOP/s",
-                         "frac": flops / kern / 1e12 / 1.25},
-            "substeps_mean": float(s[:, 0].mean()), "substeps_max": int(s[:, 0].max()),
-            "attempts_per_s": float((s[:, 0] + s[:, 1]).sum() * args.steps / kern),
-            "failed_cells": int((s[:, 3] != 0).sum())}
+            "precision": args.precision, "n_gpus": world, "scaling": "strong" if world > 1 else "weak",
+            "cells_per_gpu": n, "cell_steps_per_s": n_total * args.steps / kern_max,
+            "kernel_s_per_step": kern_max / args.steps,
+            "roofline": {"bound": "alu", "achieved": flops_all / kern_max / 1e12 / world, "peak": 1.25,
+                         "unit": "TFLOP/s per GPU", "frac": flops_all / kern_max / 1e12 / 1.25 / world},
+            "substeps_mean": tot["accepted"] / tot["cells"], "substeps_max": tot["substeps_max"],
+            "attempts_per_s": tot["attempts"] * args.steps / kern_max,
+            "failed_cells": tot["failed_cells"]}
     print(json.dumps(line))
     return 0
 
