@@ -1457,13 +1457,23 @@ __global__ void __launch_bounds__(ORDER_THREADS) order_count_kernel(const double
     if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
-__global__ void order_scan_kernel(const unsigned* hist, unsigned* cursor) {
+// Also counts the "hot" cells, those within a factor 2 of the most expensive
+// expected cost (the top four quarter-octave bins below the highest occupied
+// one), when that cost is at least 2 substeps; the static-bin queue gives each
+// of them a group of warps of its own.
+__global__ void order_scan_kernel(const unsigned* hist, unsigned* cursor, unsigned* nhot) {
   if (threadIdx.x == 0) {
     unsigned acc = 0u;
+    int top = -1;
     for (int b = ORDER_BINS - 1; b >= 0; --b) {  // most expensive bin first
       cursor[b] = acc;
       acc += hist[b];
+      if (top < 0 && hist[b] > 0u) top = b;
     }
+    unsigned hot = 0u;
+    if (top >= 4)
+      for (int b = top; b > top - 4; --b) hot += hist[b];
+    *nhot = hot;
   }
 }
 
@@ -1505,6 +1515,7 @@ struct IntegrateParams {
   unsigned long long qstride;  // queue position q takes cell (q * qstride) mod ncell
   const int32_t* order;        // or, when set, cell order[q] (longest expected first)
   int subq;                    // > 0: static bins, subq sub-queues per block (queue order 3)
+  const unsigned* nhot;        // with static bins: number of hot cells leading the order, or null
   const double* rho_cell;      // constant-volume densities, or null (constant pressure)
   int nx;                      // state components after T (5: auxiliary-temperature system)
 };
@@ -1728,14 +1739,26 @@ __device__ __forceinline__ void drain_queue(const IntegrateParams& P, const Grp<
     __shared__ unsigned sub_ctr[4];
     if (threadIdx.x < 4) sub_ctr[threadIdx.x] = 0u;
     __syncthreads();
+    // The H hot cells that lead the order (a small set: at most nb/8) each
+    // get bin k = q of their own, so no other cell shares their group's FP64
+    // unit; the rest are dealt in snake order over the other nb - H bins.
     const int sub = gid % P.subq;
     const unsigned long long nb = (unsigned long long)gridDim.x * (unsigned long long)P.subq;
     const unsigned long long k = (unsigned long long)sub * gridDim.x + blockIdx.x;
+    unsigned long long H = P.nhot ? (unsigned long long)*P.nhot : 0ull;
+    if (H * 8ull > nb) H = 0ull;
+    const unsigned long long nb2 = nb - H;
     while (true) {
       unsigned r = 0u;
       if (g.lane == 0) r = atomicAdd(&sub_ctr[sub], 1u);
       r = __shfl_sync(g.mask, r, 0, G);
-      const unsigned long long q = (unsigned long long)r * nb + ((r & 1u) ? nb - 1ull - k : k);
+      unsigned long long q;
+      if (k < H) {
+        q = r == 0u ? k : (unsigned long long)P.ncell;
+      } else {
+        const unsigned long long k2 = k - H;
+        q = H + (unsigned long long)r * nb2 + ((r & 1u) ? nb2 - 1ull - k2 : k2);
+      }
       if (q >= (unsigned long long)P.ncell) break;
       const unsigned long long cell =
           P.order ? (unsigned long long)P.order[q] : (q * P.qstride) % (unsigned long long)P.ncell;
@@ -2384,19 +2407,22 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   const int order = o.queue_order == 0 ? (h_cell ? 3 : 1) : o.queue_order;
   if (order == 2 && !h_cell) return set_error(RK_E_INVALID_ARGUMENT, "queue_order 2 needs h_cell");
   P.subq = 0;
+  P.nhot = nullptr;
   if ((order == 2 || order == 3) && h_cell && ncell > 1 && !(o.fixed_h > 0.0) && ncell < (int64_t)INT32_MAX) {
     unsigned* hist = reinterpret_cast<unsigned*>(wsb + 256);
+    unsigned* nhot = reinterpret_cast<unsigned*>(wsb + 64);
     unsigned* cursor = reinterpret_cast<unsigned*>(wsb + 512);
     int32_t* perm = reinterpret_cast<int32_t*>(wsb + 768);
     int64_t nblk = (ncell + 4095) / 4096;
     if (nblk > 1024) nblk = 1024;
     const int64_t chunk = (ncell + nblk - 1) / nblk;
     order_count_kernel<<<(unsigned)nblk, ORDER_THREADS, 0, stream>>>(h_cell, ncell, chunk, dt, hist);
-    order_scan_kernel<<<1, 32, 0, stream>>>(hist, cursor);
+    order_scan_kernel<<<1, 32, 0, stream>>>(hist, cursor, nhot);
     order_scatter_kernel<<<(unsigned)nblk, ORDER_THREADS, 0, stream>>>(h_cell, ncell, chunk, dt, cursor, perm);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "work-queue ordering launch");
     P.order = perm;
+    P.nhot = nhot;
   }
   LaunchPlan plan;
   if (o.ev_begin) {
