@@ -185,8 +185,9 @@ typedef struct rk_opts {
                              index, 2 longest expected first (dt / h_cell), 3 static
                              balanced bins: the longest-first queue dealt in snake
                              order over (block, warp group) bins, one block per
-                             resident slot on every SM (interleaved order without
-                             h_cell) */
+                             resident slot on every SM, the few cells within a
+                             factor 4 of the most expensive each alone on a block
+                             (interleaved order without h_cell) */
   int32_t blocks_per_sm;  /* resident blocks per SM for the persistent launch; 0: all
                              that fit */
   int32_t reactor;        /* 0 constant pressure (p, default); 1 constant volume: each

@@ -1457,10 +1457,10 @@ __global__ void __launch_bounds__(ORDER_THREADS) order_count_kernel(const double
     if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
-// Also counts the "hot" cells, those within a factor 2 of the most expensive
-// expected cost (the top four quarter-octave bins below the highest occupied
-// one), when that cost is at least 2 substeps; the static-bin queue gives each
-// of them a group of warps of its own.
+// Also counts the "hot" cells, those within a factor 4 of the most expensive
+// expected cost (the eight quarter-octave bins from the highest occupied one
+// down), when that cost is at least 2 substeps; the static-bin queue gives
+// each of them a group of warps of its own.
 __global__ void order_scan_kernel(const unsigned* hist, unsigned* cursor, unsigned* nhot) {
   if (threadIdx.x == 0) {
     unsigned acc = 0u;
@@ -1472,7 +1472,7 @@ __global__ void order_scan_kernel(const unsigned* hist, unsigned* cursor, unsign
     }
     unsigned hot = 0u;
     if (top >= 4)
-      for (int b = top; b > top - 4; --b) hot += hist[b];
+      for (int b = top; b > top - 8 && b >= 0; --b) hot += hist[b];
     *nhot = hot;
   }
 }
@@ -1739,25 +1739,28 @@ __device__ __forceinline__ void drain_queue(const IntegrateParams& P, const Grp<
     __shared__ unsigned sub_ctr[4];
     if (threadIdx.x < 4) sub_ctr[threadIdx.x] = 0u;
     __syncthreads();
-    // The H hot cells that lead the order (a small set: at most nb/8) each
-    // get bin k = q of their own, so no other cell shares their group's FP64
-    // unit; the rest are dealt in snake order over the other nb - H bins.
+    // The H hot cells that lead the order (when they are few: at most half the
+    // blocks and an eighth of the cells) each get a block -- an SM -- of their
+    // own: hot cell b runs on sub-queue 0 of block b and that block takes
+    // nothing else, so no other cell shares its SM's FP64 units, shared-memory
+    // pipe or instruction cache.  The rest are dealt in snake order over the
+    // bins of the other blocks.
     const int sub = gid % P.subq;
-    const unsigned long long nb = (unsigned long long)gridDim.x * (unsigned long long)P.subq;
-    const unsigned long long k = (unsigned long long)sub * gridDim.x + blockIdx.x;
+    const unsigned long long nblk = gridDim.x;
     unsigned long long H = P.nhot ? (unsigned long long)*P.nhot : 0ull;
-    if (H * 8ull > nb) H = 0ull;
-    const unsigned long long nb2 = nb - H;
+    if (H * 2ull > nblk || H * 8ull > (unsigned long long)P.ncell) H = 0ull;
+    const unsigned long long nb = (nblk - H) * (unsigned long long)P.subq;
+    const bool hot_block = blockIdx.x < H;
+    const unsigned long long k = hot_block ? 0ull : (unsigned long long)sub * (nblk - H) + (blockIdx.x - H);
     while (true) {
       unsigned r = 0u;
       if (g.lane == 0) r = atomicAdd(&sub_ctr[sub], 1u);
       r = __shfl_sync(g.mask, r, 0, G);
       unsigned long long q;
-      if (k < H) {
-        q = r == 0u ? k : (unsigned long long)P.ncell;
+      if (hot_block) {
+        q = (sub == 0 && r == 0u) ? (unsigned long long)blockIdx.x : (unsigned long long)P.ncell;
       } else {
-        const unsigned long long k2 = k - H;
-        q = H + (unsigned long long)r * nb2 + ((r & 1u) ? nb2 - 1ull - k2 : k2);
+        q = H + (unsigned long long)r * nb + ((r & 1u) ? nb - 1ull - k : k);
       }
       if (q >= (unsigned long long)P.ncell) break;
       const unsigned long long cell =
