@@ -49,9 +49,6 @@ extern "C" {
 #define RK_CELL_MAX_ATTEMPTS 1      /* attempt cap reached before t_end          */
 #define RK_CELL_NONFINITE 2         /* an accepted state was not finite          */
 #define RK_CELL_STEP_UNDERFLOW 3    /* h fell below 1e-12 dt after rejections    */
-#define RK_CELL_GROUP_SYNC 4        /* the warps sharing an expensive cell lost
-                                       step (a bounded wait ran out); its result
-                                       is not valid                              */
 
 /* Limits of this build. */
 #define RK_MAX_SPECIES 254          /* species indices are packed in 8 bits     */

@@ -465,52 +465,7 @@ struct CellScalars {
   // without its own source, 1 / rho and the velocity
   double B, fT, irho_c, vel[3];
   bool cv;
-  // Warp group (an expensive cell given a whole SM): nw warps each run the
-  // whole integration on their own slot; the loops over reactions and over the
-  // gather's pieces are split between them and their results written into
-  // every member's slot, with a group barrier on each side.  nw = 1: one warp.
-  int nw = 1, wid = 0;
-  int slot_stride = 0;     // doubles between consecutive members' slots
-  unsigned* bar = nullptr; // barrier state in shared memory: arrivals, generation
-  int* fail = nullptr;     // set when a barrier wait ran out
 };
-
-// Bounded group barrier for a warp group (no-op for one warp).  Every member's
-// shared-memory writes before it are visible to every member after it.  A wait
-// that runs out sets *fail; later barriers are then skipped, the members run
-// on unsynchronised and the cell reports RK_CELL_GROUP_SYNC, so nothing waits
-// for ever.
-constexpr long long GROUP_SPIN_LIMIT = 1ll << 26;
-__device__ __forceinline__ void group_barrier(const CellScalars& cs, int lane) {
-  if (cs.nw <= 1) return;
-  __threadfence_block();
-  __syncwarp();
-  if (lane == 0 && *reinterpret_cast<volatile int*>(cs.fail) == 0) {
-    volatile unsigned* gen = cs.bar + 1;
-    const unsigned g0 = *gen;
-    if (atomicAdd(cs.bar, 1u) == (unsigned)cs.nw - 1u) {
-      *reinterpret_cast<volatile unsigned*>(cs.bar) = 0u;
-      __threadfence_block();
-      atomicAdd(cs.bar + 1, 1u);
-    } else {
-      long long it = 0;
-      while (*gen == g0) {
-        if (++it > GROUP_SPIN_LIMIT) {
-          atomicExch(cs.fail, 1);
-          break;
-        }
-      }
-    }
-    __threadfence_block();
-  }
-  __syncwarp();
-}
-
-// Store v at arr[i] of every group member's slot (arr is this member's array).
-template <typename T>
-__device__ __forceinline__ void group_store(const CellScalars& cs, T* arr, int i, T v) {
-  for (int w = 0; w < cs.nw; ++w) arr[i + (ptrdiff_t)(w - cs.wid) * (ptrdiff_t)cs.slot_stride * (8 / (ptrdiff_t)sizeof(T))] = v;
-}
 
 struct SlotPtrs {
   double *u, *src, *fn, *arg, *fr, *F, *w, *Q, *K;
@@ -580,12 +535,12 @@ __device__ inline SlotPtrs slot_ptrs(double* b, const SlotLayout& s) {
 // the result does not depend on the launch shape.
 template <int G, typename T>
 __device__ __forceinline__ void gather_pieces(const MechView& m, int lane, const T* __restrict__ nu,
-                                              const T* __restrict__ q, T* part, const CellScalars& cs) {
-  for (int p = lane + cs.wid * G; p < m.npiece; p += G * cs.nw) {  // pieces split over a warp group
+                                              const T* __restrict__ q, T* part) {
+  for (int p = lane; p < m.npiece; p += G) {
     T acc = T(0);
     const int e1 = m.piece_ptr[p + 1];
     for (int e = m.piece_ptr[p]; e < e1; ++e) acc = fma(nu[e], q[m.csr_j[e]], acc);
-    group_store(cs, part, p, acc);
+    part[p] = acc;
   }
 }
 template <typename T>
@@ -779,8 +734,7 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
   const double lnRTp = LN_R_OVER_PREF + lnT;
   const double m_lnRTp = -lnRTp;
   double shq = 0.0;  // mixed mode: heat release sum_j q_j Delta H_j / RT in FP64
-  group_barrier(*cs, g.lane);  // the reactions are split over a warp group
-  for (int j = g.lane + cs->wid * G; j < m.nr; j += G * cs->nw) {
+  for (int j = g.lane; j < m.nr; j += G) {
     const uint32_t sl = m.slots[j];
     const int ra = sl & 255, rb = (sl >> 8) & 255, pa = (sl >> 16) & 255, pb = sl >> 24;
     const int meta = m.meta[j];
@@ -828,10 +782,10 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
       }
       if (cache) {
         double* t = s.tb + 4 * (meta >> 8);
-        group_store(*cs, t, 0, Mc);
-        group_store(*cs, t, 1, dkdM);
-        group_store(*cs, t, 2, dlnk);
-        group_store(*cs, t, 3, rfac);
+        t[0] = Mc;
+        t[1] = dkdM;
+        t[2] = dlnk;
+        t[3] = rfac;
         if (MIXED) {
           float* tf = s.ftb + 4 * (meta >> 8);
           tf[0] = __double2float_rn(Mc);
@@ -843,7 +797,7 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     }
     const double kr = k * rfac;
     const double qj = mfac * (k * Pf - kr * Pb);
-    group_store(*cs, s.q, j, qj);
+    s.q[j] = qj;
     if (MIXED) {
       s.fq[j] = __double2float_rn(qj);
       const double dnud = dnu > 0 ? 1.0 : (dnu < 0 ? -1.0 : 0.0);
@@ -857,13 +811,13 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
       const double dlnKc = (s.hRT[pa] + s.hRT[pb] - s.hRT[ra] - s.hRT[rb] - dnud) * invT;
       const double qT = fma(k * dlnk, Pf, -kr * (dlnk - dlnKc) * Pb);
       if (cs->prec == 3) {  // double-float copies for the J v core, in the same storage
-        group_store(*cs, reinterpret_cast<df2*>(s.qT), j, df_from(qT));
-        group_store(*cs, reinterpret_cast<df2*>(s.kc), j, df_from(k));
-        group_store(*cs, reinterpret_cast<df2*>(s.krc), j, df_from(kr));
+        reinterpret_cast<df2*>(s.qT)[j] = df_from(qT);
+        reinterpret_cast<df2*>(s.kc)[j] = df_from(k);
+        reinterpret_cast<df2*>(s.krc)[j] = df_from(kr);
       } else {
-        group_store(*cs, s.qT, j, qT);
-        group_store(*cs, s.kc, j, k);
-        group_store(*cs, s.krc, j, kr);
+        s.qT[j] = qT;
+        s.kc[j] = k;
+        s.krc[j] = kr;
       }
       if (MIXED) {
         s.fkc[j] = __double2float_rn(k);
@@ -875,12 +829,9 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
   // species pass 2: w = nu^T q, dY/dt and the sums of the temperature equation
   double Sh = MIXED ? shq : 0.0, cb = 0.0;
   double Ax = 0.0, Bx = 0.0;  // auxiliary T: sum (u_k/RT) F_k / W_k and sum (cv_k/R) F_k / W_k
+  if (MIXED) gather_pieces<G, float>(m, g.lane, m.csr_nuf, s.fq, s.fpart);  // FP32 (q formed in FP64)
+  else gather_pieces<G, double>(m, g.lane, m.csr_nu, s.q, s.part);
   g.sync();
-  group_barrier(*cs, g.lane);
-  if (MIXED) gather_pieces<G, float>(m, g.lane, m.csr_nuf, s.fq, s.fpart, *cs);  // FP32 (q formed in FP64)
-  else gather_pieces<G, double>(m, g.lane, m.csr_nu, s.q, s.part, *cs);
-  g.sync();
-  group_barrier(*cs, g.lane);
   for (int k = g.lane; k < ns; k += G) {
     double om;
     if (MIXED) {
@@ -1002,8 +953,7 @@ __device__ __forceinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, c
   }
   if (coop_tb) sum_first<G>(g, mp, m.ntb);  // d[M]_t, identical on every lane
   g.sync();
-  group_barrier(cs, g.lane);  // the reactions are split over a warp group
-  for (int j = g.lane + cs.wid * G; j < m.nr; j += G * cs.nw) {
+  for (int j = g.lane; j < m.nr; j += G) {
     const uint32_t sl = m.slots[j];
     const int ra = sl & 255, rb = (sl >> 8) & 255, pa = (sl >> 16) & 255, pb = sl >> 24;
     const int meta = m.meta[j];
@@ -1029,13 +979,11 @@ __device__ __forceinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, c
       if (kind == 1) dq = t[0] * dq + dM * (k * Pf - kr * Pb);
       else dq = dq + t[1] * dM * (Pf - t[3] * Pb);
     }
-    group_store(cs, s.q, j, dq);
+    s.q[j] = dq;
   }
   g.sync();
-  group_barrier(cs, g.lane);
-  gather_pieces<G, double>(m, g.lane, m.csr_nu, s.q, s.part, cs);
+  gather_pieces<G, double>(m, g.lane, m.csr_nu, s.q, s.part);
   g.sync();
-  group_barrier(cs, g.lane);
   double dSh = 0.0, dcb = 0.0;
   for (int k = g.lane; k < ns; k += G) {
     const double dom = piece_sum(m, s.part, k);
@@ -1111,13 +1059,12 @@ __device__ __forceinline__ void jvp_eval_df(const MechView& m, const SlotPtrs& s
   }
   if (coop_tb) sum_first<G>(g, mp, m.ntb);
   g.sync();
-  group_barrier(cs, g.lane);  // the reactions and pieces are split over a warp group
   const df2 vT2 = df_from(vT);
   const df2* k2 = reinterpret_cast<const df2*>(s.kc);
   const df2* kr2 = reinterpret_cast<const df2*>(s.krc);
   const df2* qT2 = reinterpret_cast<const df2*>(s.qT);
   df2* dq2 = reinterpret_cast<df2*>(s.q);
-  for (int j = g.lane + cs.wid * G; j < m.nr; j += G * cs.nw) {
+  for (int j = g.lane; j < m.nr; j += G) {
     const uint32_t sl = m.slots[j];
     const int ra = sl & 255, rb = (sl >> 8) & 255, pa = (sl >> 16) & 255, pb = sl >> 24;
     const int meta = m.meta[j];
@@ -1145,19 +1092,17 @@ __device__ __forceinline__ void jvp_eval_df(const MechView& m, const SlotPtrs& s
       else r = dqd + t[1] * dM * (Pf - t[3] * Pb);
       dq = df_from(r);
     }
-    group_store(cs, dq2, j, dq);
+    dq2[j] = dq;
   }
   g.sync();
-  group_barrier(cs, g.lane);
   df2* part2 = reinterpret_cast<df2*>(s.part);
-  for (int p = g.lane + cs.wid * G; p < m.npiece; p += G * cs.nw) {
+  for (int p = g.lane; p < m.npiece; p += G) {
     df2 acc = {0.0f, 0.0f};
     const int e1 = m.piece_ptr[p + 1];
     for (int e = m.piece_ptr[p]; e < e1; ++e) acc = df_add(acc, df_scale(m.csr_nuf[e], dq2[m.csr_j[e]]));
-    group_store(cs, part2, p, acc);
+    part2[p] = acc;
   }
   g.sync();
-  group_barrier(cs, g.lane);
   double dSh = 0.0, dcb = 0.0;
   for (int k = g.lane; k < ns; k += G) {
     const int p1 = m.spec_piece[k + 1];
@@ -1248,7 +1193,7 @@ __device__ __noinline__ void jvp_eval_f32(const MechView& m, const SlotPtrs& s, 
     s.fq[j] = dq;
   }
   g.sync();
-  gather_pieces<G, float>(m, g.lane, m.csr_nuf, s.fq, s.fpart, cs);
+  gather_pieces<G, float>(m, g.lane, m.csr_nuf, s.fq, s.fpart);
   g.sync();
   float dSh = 0.f, dcb = 0.f;
   for (int k = g.lane; k < ns; k += G) {
@@ -1302,11 +1247,6 @@ __device__ inline void apply_jv(const MechView& m, const SlotPtrs& s, const Cell
   CellScalars dummy;
   dummy.pinv = cs.pinv;
   dummy.prec = cs.prec;
-  dummy.nw = cs.nw;
-  dummy.wid = cs.wid;
-  dummy.slot_stride = cs.slot_stride;
-  dummy.bar = cs.bar;
-  dummy.fail = cs.fail;
   rhs_eval<G, MIXED>(m, s, s.arg, s.src, p, out, false, &dummy);
   *n_rhs += 1;
   for (int e = g.lane; e < N; e += G) out[e] = (out[e] - s.fn[e]) / d;
@@ -1580,12 +1520,8 @@ struct IntegrateParams {
   int nx;                      // state components after T (5: auxiliary-temperature system)
 };
 
-// nw > 1: this warp is member wid of a group of nw warps (consecutive slots)
-// sharing the cell; bar/fail: the group's barrier state.  Member 0 alone
-// writes the results.
 template <int G, bool MIXED>
-__device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const IntegrateParams& P, int64_t cell,
-                               int nw = 1, int wid = 0, unsigned* bar = nullptr, int* fail = nullptr) {
+__device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const IntegrateParams& P, int64_t cell) {
   const Grp<G> g;
   const int ns = m.ns, N = ns + 1 + m.nx, Nq = s.Nq;
   for (int e = g.lane; e < N; e += G) {
@@ -1611,11 +1547,6 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
   CellScalars cs;
   cs.pinv = 1.0 / fabs(pr);
   cs.prec = P.precision == 3 ? 3 : 0;
-  cs.nw = nw;
-  cs.wid = wid;
-  cs.slot_stride = P.S.stride;
-  cs.bar = bar;
-  cs.fail = fail;
   rhs_eval<G, MIXED>(m, s, s.u, srcp, pr, s.fn, true, &cs);
   n_rhs += 1;
   int mdim = arnoldi<G, MIXED>(m, s, cs, P.M, P.jv_mode, pr, &n_rhs, fp32_jv);
@@ -1727,7 +1658,7 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
       hnew = h * (double)fac;
       accept = fin && err <= 1.0;
     }
-    if (P.trace && att < P.trace_cap && g.lane == 0 && wid == 0) P.trace[cell * P.trace_cap + att] = accept ? h : -h;
+    if (P.trace && att < P.trace_cap && g.lane == 0) P.trace[cell * P.trace_cap + att] = accept ? h : -h;
     if (accept) {
       if (bad) {
         status = RK_CELL_NONFINITE;
@@ -1755,10 +1686,8 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
       }
     }
   }
-  if (nw > 1 && *reinterpret_cast<volatile int*>(fail) != 0) status = RK_CELL_GROUP_SYNC;
-  if (wid == 0)
-    for (int e = g.lane; e < N; e += G) P.Y[cell * N + e] = s.u[e];
-  if (g.lane == 0 && wid == 0) {
+  for (int e = g.lane; e < N; e += G) P.Y[cell * N + e] = s.u[e];
+  if (g.lane == 0) {
     if (P.h_cell) P.h_cell[cell] = h_last;
     if (P.stats) {
       P.stats[4 * cell + 0] = n_acc;
@@ -1799,9 +1728,7 @@ __device__ inline void init_sentinels(const SlotPtrs& s, int ns, int lane) {
 
 // Hand cells to the warp groups of a persistent launch until the queue is
 // empty, calling body(cell) for each.
-// GROUPS: the body takes (cell, nw, wid, bar, fail) and can share a cell
-// between warps; otherwise it takes the cell alone.
-template <int G, bool GROUPS, class Body>
+template <int G, class Body>
 __device__ __forceinline__ void drain_queue(const IntegrateParams& P, const Grp<G>& g, int gid, Body&& body) {
   if (P.subq > 0) {
     // Static bins: the queue (longest expected first) is dealt out in snake
@@ -1810,11 +1737,7 @@ __device__ __forceinline__ void drain_queue(const IntegrateParams& P, const Grp<
     // sub-queue -- receives a near-equal share of the expensive cells.  Round
     // r of bin k holds queue position r * nb + (r even ? k : nb - 1 - k).
     __shared__ unsigned sub_ctr[4];
-    __shared__ unsigned grp_bar[2];
-    __shared__ int grp_fail;
     if (threadIdx.x < 4) sub_ctr[threadIdx.x] = 0u;
-    if (threadIdx.x < 2) grp_bar[threadIdx.x] = 0u;
-    if (threadIdx.x == 0) grp_fail = 0;
     __syncthreads();
     // The H hot cells that lead the order (when they are few: at most half the
     // blocks and an eighth of the cells) each get a block -- an SM -- of their
@@ -1829,19 +1752,6 @@ __device__ __forceinline__ void drain_queue(const IntegrateParams& P, const Grp<
     const unsigned long long nb = (nblk - H) * (unsigned long long)P.subq;
     const bool hot_block = blockIdx.x < H;
     const unsigned long long k = hot_block ? 0ull : (unsigned long long)sub * (nblk - H) + (blockIdx.x - H);
-    if constexpr (GROUPS && G == 32) {
-      if (hot_block) {
-        // the hot cell shared by up to four warps, one per sub-partition
-        const int nwh = (int)(blockDim.x / 32u) < 4 ? (int)(blockDim.x / 32u) : 4;
-        if (gid < nwh) {
-          const unsigned long long q = blockIdx.x;
-          const unsigned long long cell =
-              P.order ? (unsigned long long)P.order[q] : (q * P.qstride) % (unsigned long long)P.ncell;
-          body((int64_t)cell, nwh, gid, grp_bar, &grp_fail);
-        }
-        return;
-      }
-    }
     while (true) {
       unsigned r = 0u;
       if (g.lane == 0) r = atomicAdd(&sub_ctr[sub], 1u);
@@ -1855,8 +1765,7 @@ __device__ __forceinline__ void drain_queue(const IntegrateParams& P, const Grp<
       if (q >= (unsigned long long)P.ncell) break;
       const unsigned long long cell =
           P.order ? (unsigned long long)P.order[q] : (q * P.qstride) % (unsigned long long)P.ncell;
-      if constexpr (GROUPS) body((int64_t)cell, 1, 0, grp_bar, &grp_fail);
-      else body((int64_t)cell);
+      body((int64_t)cell);
     }
     return;
   }
@@ -1869,8 +1778,7 @@ __device__ __forceinline__ void drain_queue(const IntegrateParams& P, const Grp<
     // hot side of a flame) spread over all SMs instead of filling a few.
     const unsigned long long cell =
         P.order ? (unsigned long long)P.order[q] : (q * P.qstride) % (unsigned long long)P.ncell;
-    if constexpr (GROUPS) body((int64_t)cell, 1, 0, (unsigned*)nullptr, (int*)nullptr);
-    else body((int64_t)cell);
+    body((int64_t)cell);
   }
 }
 
@@ -1889,13 +1797,7 @@ __global__ void __launch_bounds__(MAX_BLOCK_THREADS, 1) rok4e_integrate_kernel(I
   const SlotPtrs s = slot_ptrs(base, P.S);
   init_sentinels<MIXED>(s, m.ns, g.lane);
   g.sync();
-  if constexpr (!MIXED && G == 32) {
-    drain_queue<G, true>(P, g, gid, [&](int64_t cell, int nw, int wid, unsigned* bar, int* fail) {
-      integrate_cell<G, MIXED>(m, s, P, cell, nw, wid, bar, fail);
-    });
-  } else {
-    drain_queue<G, false>(P, g, gid, [&](int64_t cell) { integrate_cell<G, MIXED>(m, s, P, cell); });
-  }
+  drain_queue<G>(P, g, gid, [&](int64_t cell) { integrate_cell<G, MIXED>(m, s, P, cell); });
 }
 
 // ------------------------------------------- explicit Dormand-Prince 5(4)
@@ -2065,7 +1967,7 @@ __global__ void __launch_bounds__(MAX_BLOCK_THREADS) rkdp_integrate_kernel(Integ
   const SlotPtrs s = slot_ptrs(base, P.S);
   init_sentinels<false>(s, m.ns, g.lane);
   g.sync();
-  drain_queue<G, false>(P, g, gid, [&](int64_t cell) { integrate_cell_rkdp<G>(m, s, P, cell); });
+  drain_queue<G>(P, g, gid, [&](int64_t cell) { integrate_cell_rkdp<G>(m, s, P, cell); });
 }
 
 }  // namespace rk
