@@ -1473,7 +1473,13 @@ __global__ void order_scan_kernel(const unsigned* hist, unsigned* cursor, unsign
     unsigned hot = 0u;
     if (top >= 4)
       for (int b = top; b > top - 8 && b >= 0; --b) hot += hist[b];
-    *nhot = hot;
+    // expected substeps (2^(bin/4)) of the hottest cell and of all the others
+    float rest = 0.f;
+    for (int b = 0; b < ORDER_BINS; ++b)
+      if (!(top >= 4 && b > top - 8 && b <= top)) rest += (float)hist[b] * exp2f(0.25f * (float)b);
+    nhot[0] = hot;
+    nhot[1] = __float_as_uint(top >= 0 ? exp2f(0.25f * (float)top) : 0.f);
+    nhot[2] = __float_as_uint(rest);
   }
 }
 
@@ -1747,8 +1753,14 @@ __device__ __forceinline__ void drain_queue(const IntegrateParams& P, const Grp<
     // bins of the other blocks.
     const int sub = gid % P.subq;
     const unsigned long long nblk = gridDim.x;
-    unsigned long long H = P.nhot ? (unsigned long long)*P.nhot : 0ull;
+    unsigned long long H = P.nhot ? (unsigned long long)P.nhot[0] : 0ull;
     if (H * 2ull > nblk || H * 8ull > (unsigned long long)P.ncell) H = 0ull;
+    if (H > 0ull) {
+      // only while the other cells, spread over the other blocks' four
+      // sub-partitions, still finish within the hottest cell's expected time
+      const float top_cost = __uint_as_float(P.nhot[1]), rest_cost = __uint_as_float(P.nhot[2]);
+      if (rest_cost > top_cost * 4.0f * (float)(nblk - H)) H = 0ull;
+    }
     const unsigned long long nb = (nblk - H) * (unsigned long long)P.subq;
     const bool hot_block = blockIdx.x < H;
     const unsigned long long k = hot_block ? 0ull : (unsigned long long)sub * (nblk - H) + (blockIdx.x - H);
