@@ -663,9 +663,9 @@ def run_ours(args, rank, world, local_rank):
                    "lanes_per_cell": args.lanes or 32, "cells_per_block": args.cells_per_block,
                    "queue_order": args.queue_order, "blocks_per_sm": args.blocks_per_sm},
         # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one fp64
-        # integration launch of this workload, from the ncu capture summarised in
-        # profiles/rok4e_integrate_flame1d.md (bytes per launch; it describes the
-        # kernel as profiled there and goes stale when the kernel changes)
+        # integration launch of this workload from one ncu --set full capture
+        # of this kernel (bytes per launch; it describes the kernel as captured
+        # and goes stale when the kernel changes)
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_nominal, "unit": "TFLOP/s",
                      "frac": achieved / peak_nominal,
                      "traffic": 2274304 if args.precision == "fp64" else None,
