@@ -558,10 +558,12 @@ __device__ __forceinline__ T piece_sum(const MechView& m, const T* part, int k) 
 // internal energies u_k/RT = h_k/RT - 1 and c_v/R = c_p/R - 1 per species).  uu, out: N-vectors in shared memory
 // (out must not alias uu).  When `cache` is set, the values the analytic
 // Jacobian-vector product reuses are kept (rate coefficients, w, d(cp/R)/dT
-// and the cell scalars).  Not inlined: chem_rhs and the integrator execute the
-// same instructions, so R(u) - R(u) is exactly zero in a steady-state cell.
+// and the cell scalars).  Inlined into every caller: each product that meets
+// a sum is written as an explicit fma or __dmul_rn, so no context can contract
+// it differently, chem_rhs and the integrator compute the same bits and
+// R(u) - R(u) is exactly zero in a steady-state cell.
 template <int G, bool MIXED = false>
-__device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, const double* uu,
+__device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, const double* uu,
                                       const double* src, double p, double* out, bool cache,
                                       CellScalars* cs) {
   const Grp<G> g;
@@ -577,7 +579,7 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     const double a1 = c[k], a2 = c[ns + k], a3 = c[2 * ns + k], a4 = c[3 * ns + k], a5 = c[4 * ns + k];
     const double cp = fma(fma(fma(fma(a5, T, a4), T, a3), T, a2), T, a1);
     const double hp = fma(fma(fma(c[8 * ns + k], T, c[7 * ns + k]), T, c[6 * ns + k]), T, c[5 * ns + k]);
-    const double hrt = fma(hp, T, a1) + c[9 * ns + k] * invT;
+    const double hrt = fma(c[9 * ns + k], invT, fma(hp, T, a1));
     const double sp = fma(fma(fma(c[12 * ns + k], T, c[11 * ns + k]), T, c[10 * ns + k]), T, a2);
     const double sr = fma(a1, lnT, fma(sp, T, c[13 * ns + k]));
     const double grt = hrt - sr;
@@ -586,7 +588,7 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     s.gRT[k] = grt;
     ghi = max(ghi, __double2hiint(grt) & 0x7fffffff);
     if (cache) {
-      const double dcp = fma(fma(c[16 * ns + k], T, c[15 * ns + k]), T, c[14 * ns + k]) * T + a2;
+      const double dcp = fma(fma(fma(c[16 * ns + k], T, c[15 * ns + k]), T, c[14 * ns + k]), T, a2);
       s.dcp[k] = dcp;
       if (MIXED) {
         s.fh[k] = __double2float_rn(hrt);
@@ -655,8 +657,8 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
       const double* fo = m.fo + (size_t)i * FO_STRIDE;
       double x;
       if (c == 0) {
-        const double lnk_inf = m.lnA[i] + m.bexp[i] * lnT - m.EaR[i] * invT;
-        x = fo[0] + fo[1] * lnT - fo[2] * invT - lnk_inf;  // ln(k0 / k_inf)
+        const double lnk_inf = fma(-m.EaR[i], invT, fma(m.bexp[i], lnT, m.lnA[i]));
+        x = fma(-fo[2], invT, fma(fo[1], lnT, fo[0])) - lnk_inf;  // ln(k0 / k_inf)
       } else if (c == 1) {
         x = -T * fo[4];
       } else if (c == 2) {
@@ -685,7 +687,7 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
         if (!(y > 1e-300)) y = 1e-300;
       } else {
         const double a = fo[3];
-        y = (1.0 - a) * tro[4 * i + 1] + a * tro[4 * i + 2] + tro[4 * i + 3];  // F_cent
+        y = fma(1.0 - a, tro[4 * i + 1], fma(a, tro[4 * i + 2], tro[4 * i + 3]));  // F_cent
       }
       tro[9 * nt + l] = y;
       tro[4 * nt + l] = log10(y);
@@ -694,10 +696,10 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     for (int i = g.lane; i < nt; i += G) {
       const double lFc = tro[4 * nt + 2 * i], lPr = tro[4 * nt + 2 * i + 1];
       const double Fc = tro[9 * nt + 2 * i], Pr = tro[9 * nt + 2 * i + 1];
-      const double cc = -0.4 - 0.67 * lFc;
-      const double nn = 0.75 - 1.27 * lFc;
+      const double cc = fma(-0.67, lFc, -0.4);
+      const double nn = fma(-1.27, lFc, 0.75);
       const double x = lPr + cc;
-      const double D = nn - 0.14 * x;
+      const double D = fma(-0.14, x, nn);
       // one division for 1/(1 + Pr) and 1/(D^2 + x^2):
       //   1/(1 + f1^2) = D^2/(D^2 + x^2) with f1 = x / D
       const double s2 = fma(D, D, x * x);
@@ -712,17 +714,19 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
         const double* fo = m.fo + (size_t)i * FO_STRIDE;
         const double a = fo[3];
         const double er = tro[4 * i], e3 = tro[4 * i + 1], e1 = tro[4 * i + 2], e2 = tro[4 * i + 3];
-        const double dlnk_inf = (m.bexp[i] + m.EaR[i] * invT) * invT;
-        const double dlnk0 = (fo[1] + fo[2] * invT) * invT;
+        const double dlnk_inf = __dmul_rn(fma(m.EaR[i], invT, m.bexp[i]), invT);
+        const double dlnk0 = __dmul_rn(fma(fo[2], invT, fo[1]), invT);
         // d ln F / d log10 Pr = -2 lFc f1 n / (D^2 (1 + f1^2)^2) and
         // d log10 F / d lFc = 1/(1 + f1^2) - 2 lFc f1 (df1/dlFc) / (1 + f1^2)^2,
         // df1/dlFc = (-0.67 D + 1.1762 x) / D^2, written with rr = 1/(D^2 + x^2)
-        const double w = 2.0 * lFc * x * D * rr * rr;
-        const double dlF_dL = -w * nn;
-        const double dlF_dlFc = iden - w * (-0.67 * D + 1.1762 * x);
-        const double dFc = -(1.0 - a) * fo[4] * e3 - a * fo[5] * e1 + (fo[6] > 0.0 ? fo[6] * invT * invT * e2 : 0.0);
-        const double gg = iOnePr + dlF_dL;
-        tro[7 * nt + i] = dlnk_inf + gg * (dlnk0 - dlnk_inf) + dlF_dlFc * dFc * (1.0 / Fc);
+        // (every product that meets a sum is an explicit fma or __dmul_rn, so
+        // the compiler cannot contract it differently where this is inlined)
+        const double w = __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(2.0, lFc), x), D), rr), rr);
+        const double gg = fma(-w, nn, iOnePr);
+        const double dlF_dlFc = fma(-w, fma(-0.67, D, __dmul_rn(1.1762, x)), iden);
+        const double e2t = fo[6] > 0.0 ? __dmul_rn(__dmul_rn(__dmul_rn(fo[6], invT), invT), e2) : 0.0;
+        const double dFc = fma(-(1.0 - a), __dmul_rn(fo[4], e3), fma(-a, __dmul_rn(fo[5], e1), e2t));
+        tro[7 * nt + i] = fma(__dmul_rn(dlF_dlFc, dFc), 1.0 / Fc, fma(gg, dlnk0 - dlnk_inf, dlnk_inf));
         tro[8 * nt + i] = er * F * iOnePr * gg;  // (dk/d[M]) / k_inf
       }
     }
@@ -741,7 +745,7 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     const int kind = meta & 3;
     const bool rev = (meta >> 2) & 1;
     const int dnu = ((meta >> 4) & 15) - 4;
-    const double lnk = m.lnA[j] + m.bexp[j] * lnT - m.EaR[j] * invT;
+    const double lnk = fma(-m.EaR[j], invT, fma(m.bexp[j], lnT, m.lnA[j]));
     double k = (MIXED || cs->prec == 3) ? exp_mixed(lnk, m.etab) : exp_fast(lnk, m.etab);
     const double Pf = s.C[ra] * s.C[rb];
     const double Pb = s.C[pa] * s.C[pb];
@@ -757,7 +761,7 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     }
     double mfac = 1.0;
     double dlnk = 0.0;  // d ln k / dT (cache only)
-    if (cache) dlnk = (m.bexp[j] + m.EaR[j] * invT) * invT;
+    if (cache) dlnk = __dmul_rn(fma(m.EaR[j], invT, m.bexp[j]), invT);
     if (kind != 0) {
       const int slot = meta >> 8;
       double Mc;
@@ -796,20 +800,20 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
       }
     }
     const double kr = k * rfac;
-    const double qj = mfac * (k * Pf - kr * Pb);
+    const double qj = mfac * fma(k, Pf, -__dmul_rn(kr, Pb));
     s.q[j] = qj;
     if (MIXED) {
       s.fq[j] = __double2float_rn(qj);
       const double dnud = dnu > 0 ? 1.0 : (dnu < 0 ? -1.0 : 0.0);
-      shq = fma(qj, s.hRT[pa] + s.hRT[pb] - s.hRT[ra] - s.hRT[rb] - esh * dnud, shq);
+      shq = fma(qj, fma(-esh, dnud, s.hRT[pa] + s.hRT[pb] - s.hRT[ra] - s.hRT[rb]), shq);
     }
     if (cache) {
       // d q_j / dT at fixed concentrations (without the third-body factor):
       // k Pf d ln k/dT - kr Pb (d ln k/dT - d ln Kc/dT), with
       // d ln Kc/dT = (sum_products h/RT - sum_reactants h/RT - dnu) / T.
       const double dnud = dnu > 0 ? 1.0 : (dnu < 0 ? -1.0 : 0.0);
-      const double dlnKc = (s.hRT[pa] + s.hRT[pb] - s.hRT[ra] - s.hRT[rb] - dnud) * invT;
-      const double qT = fma(k * dlnk, Pf, -kr * (dlnk - dlnKc) * Pb);
+      const double dlnKc = __dmul_rn(s.hRT[pa] + s.hRT[pb] - s.hRT[ra] - s.hRT[rb] - dnud, invT);
+      const double qT = fma(__dmul_rn(k, dlnk), Pf, -__dmul_rn(__dmul_rn(kr, dlnk - dlnKc), Pb));
       if (cs->prec == 3) {  // double-float copies for the J v core, in the same storage
         reinterpret_cast<df2*>(s.qT)[j] = df_from(qT);
         reinterpret_cast<df2*>(s.kc)[j] = df_from(k);
@@ -920,6 +924,25 @@ __device__ __noinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, cons
     cs->cv = cv;
   }
   g.sync();
+}
+
+// rhs_eval behind a call, where its size matters more than the call: the
+// point kernels, the finite-difference J v, the explicit integrator's first
+// evaluation and the 8/16-lane and mixed variants of the integrator (one
+// inlined copy per call site would multiply the compile time).  Same bits as
+// the inlined copies.
+template <int G, bool MIXED = false>
+__device__ __noinline__ void rhs_eval_call(const MechView& m, const SlotPtrs& s, const double* uu,
+                                           const double* src, double p, double* out, bool cache,
+                                           CellScalars* cs) {
+  rhs_eval<G, MIXED>(m, s, uu, src, p, out, cache, cs);
+}
+template <int G, bool MIXED, bool INL>
+__device__ __forceinline__ void rhs_dispatch(const MechView& m, const SlotPtrs& s, const double* uu,
+                                             const double* src, double p, double* out, bool cache,
+                                             CellScalars* cs) {
+  if constexpr (INL) rhs_eval<G, MIXED>(m, s, uu, src, p, out, cache, cs);
+  else rhs_eval_call<G, MIXED>(m, s, uu, src, p, out, cache, cs);
 }
 
 // Analytic Jacobian-vector product out = J(u_n) v, using the values cached by
@@ -1247,7 +1270,7 @@ __device__ inline void apply_jv(const MechView& m, const SlotPtrs& s, const Cell
   CellScalars dummy;
   dummy.pinv = cs.pinv;
   dummy.prec = cs.prec;
-  rhs_eval<G, MIXED>(m, s, s.arg, s.src, p, out, false, &dummy);
+  rhs_eval_call<G, MIXED>(m, s, s.arg, s.src, p, out, false, &dummy);
   *n_rhs += 1;
   for (int e = g.lane; e < N; e += G) out[e] = (out[e] - s.fn[e]) / d;
   g.sync();
@@ -1553,9 +1576,9 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
   CellScalars cs;
   cs.pinv = 1.0 / fabs(pr);
   cs.prec = P.precision == 3 ? 3 : 0;
-  rhs_eval<G, MIXED>(m, s, s.u, srcp, pr, s.fn, true, &cs);
-  n_rhs += 1;
-  int mdim = arnoldi<G, MIXED>(m, s, cs, P.M, P.jv_mode, pr, &n_rhs, fp32_jv);
+  constexpr bool INL = G == 32 && !MIXED;  // the RHS inlined on the main path
+  int mdim = 0;
+  bool fresh = true;  // f_n and the Krylov basis are due at u (start, or after an accepted step)
   double* K0 = s.K;
   double* K1 = s.K + Nq;
   double* K2 = s.K + 2 * Nq;
@@ -1563,6 +1586,12 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
   constexpr double g21 = G21 / GAM, g31 = G31 / GAM, g32 = G32 / GAM;
   constexpr double g41 = G41 / GAM, g42 = G42 / GAM, g43 = G43 / GAM;
   while (true) {
+    if (fresh) {
+      rhs_dispatch<G, MIXED, INL>(m, s, s.u, srcp, pr, s.fn, true, &cs);
+      n_rhs += 1;
+      mdim = arnoldi<G, MIXED>(m, s, cs, P.M, P.jv_mode, pr, &n_rhs, fp32_jv);
+      fresh = false;
+    }
     if (fixed) {
       if (n_acc >= n_fixed) break;
     } else if (dt - t <= T_END_TOL * dt) {
@@ -1585,7 +1614,7 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
           s.arg[e] = s.u[e] + h * acc;
         }
         g.sync();
-        rhs_eval<G, MIXED>(m, s, s.arg, srcp, pr, s.fr, false, &cs);
+        rhs_dispatch<G, MIXED, INL>(m, s, s.arg, srcp, pr, s.fr, false, &cs);
         n_rhs += 1;
         fi = s.fr;
       } else {
@@ -1678,11 +1707,7 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
       h_last = hnew;
       h = hnew;
       const bool done = fixed ? (n_acc >= n_fixed) : (dt - t <= T_END_TOL * dt);
-      if (!done) {
-        rhs_eval<G, MIXED>(m, s, s.u, srcp, pr, s.fn, true, &cs);
-        n_rhs += 1;
-        mdim = arnoldi<G, MIXED>(m, s, cs, P.M, P.jv_mode, pr, &n_rhs, fp32_jv);
-      }
+      fresh = !done;
     } else {
       n_rej += 1;
       h = hnew;
@@ -1867,7 +1892,7 @@ __device__ void integrate_cell_rkdp(const MechView& m, const SlotPtrs& s, const 
   double* k5 = s.K + 3 * Nq;
   double* k6 = s.F;
   double* k7 = s.w;
-  rhs_eval<G>(m, s, s.u, srcp, pr, k1, false, &cs);
+  rhs_eval_call<G>(m, s, s.u, srcp, pr, k1, false, &cs);
   n_rhs += 1;
   while (true) {
     if (fixed) {
@@ -1895,7 +1920,7 @@ __device__ void integrate_cell_rkdp(const MechView& m, const SlotPtrs& s, const 
       }
       g.sync();
       double* out = i == 1 ? k2 : i == 2 ? k3 : i == 3 ? k4 : i == 4 ? k5 : i == 5 ? k6 : k7;
-      rhs_eval<G>(m, s, s.arg, srcp, pr, out, false, &cs);
+      rhs_dispatch<G, false, G == 32>(m, s, s.arg, srcp, pr, out, false, &cs);
       n_rhs += 1;
     }
     double part = 0.0;
@@ -2089,27 +2114,27 @@ __global__ void __launch_bounds__(MAX_BLOCK_THREADS) chem_point_kernel(PointPara
   cs.pinv = 1.0 / fabs(pr);
   cs.prec = 0;
   if (P.mode == 0 || P.mode == 3) {
-    if (P.mode == 3) rhs_eval<G, true>(m, s, s.u, P.src ? s.src : nullptr, pr, s.fr, false, &cs);
-    else rhs_eval<G>(m, s, s.u, P.src ? s.src : nullptr, pr, s.fr, false, &cs);
+    if (P.mode == 3) rhs_eval_call<G, true>(m, s, s.u, P.src ? s.src : nullptr, pr, s.fr, false, &cs);
+    else rhs_eval_call<G>(m, s, s.u, P.src ? s.src : nullptr, pr, s.fr, false, &cs);
     for (int e = g.lane; e < N; e += G) P.out[cell * N + e] = s.fr[e];
     return;
   }
   if (P.mode == 4) {
-    rhs_eval<G, true>(m, s, s.u, nullptr, pr, s.fn, true, &cs);
+    rhs_eval_call<G, true>(m, s, s.u, nullptr, pr, s.fn, true, &cs);
     jvp_eval_f32<G>(m, s, s.u, cs, s.F, s.w);
     for (int e = g.lane; e < N; e += G) P.out[cell * N + e] = s.w[e];
     return;
   }
   if (P.mode == 5) {
     cs.prec = 3;
-    rhs_eval<G>(m, s, s.u, nullptr, pr, s.fn, true, &cs);
+    rhs_eval_call<G>(m, s, s.u, nullptr, pr, s.fn, true, &cs);
     jvp_eval_df<G>(m, s, s.u, cs, s.F, s.w);
     for (int e = g.lane; e < N; e += G) P.out[cell * N + e] = s.w[e];
     return;
   }
   // the auxiliary-temperature T row depends on the source; elsewhere s.src is
   // zero here, so the finite difference sees the bare source term
-  rhs_eval<G>(m, s, s.u, m.nx > 0 ? s.src : nullptr, pr, s.fn, true, &cs);
+  rhs_eval_call<G>(m, s, s.u, m.nx > 0 ? s.src : nullptr, pr, s.fn, true, &cs);
   int n_rhs = 0;
   double unorm = 0.0;
   if (P.mode == 2) unorm = sqrt(group_dot<G>(g, s.u, s.u, N));
