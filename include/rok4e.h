@@ -373,13 +373,17 @@ int rk_rok4e_adjoint(const rk_mech* mech, const double* checkpoints, const doubl
  *  with CUDA events in *ops_per_s.  Synchronous. */
 int rk_probe_throughput(int32_t kind, double* ops_per_s);
 
-/* The kernels' table-driven exponential on a device array (for testing it
+/* The kernels' own elementary functions on a device array (for testing them
  * against the CUDA math library): which 0: y = exp(x); 1: exp(x) and 2:
  * exp(-x) from the shared-reduction pair; 3, 4, 5: the same three in the
  * mixed-precision form (polynomial's small term in FP32, relative error
- * ~1e-12) used by precision levels 1 and 2.  Method: Tang, ACM TOMS 15(2),
- * 1989, with a 128-entry table; the paper itself delegates kinetics to
- * Cantera and prints no exponential. */
+ * ~1e-12) used by precision levels 1 to 3; 6: y = ln x; 7: y = 1/x.
+ * Methods: Tang, ACM TOMS 15(2), 1989 (exp) and 16(4), 1990 (ln), each with
+ * a 128-entry table; 1/x by two Newton steps from an FP32 estimate where x
+ * and 1/x are FP32-normal, a division elsewhere.  The paper itself delegates
+ * kinetics to Cantera and prints none of these.  x, y: n doubles in device
+ * memory, distinct arrays; asynchronous on `stream`; RK_E_INVALID_ARGUMENT
+ * for n < 0 or which outside 0..7. */
 int rk_eval_exp(const double* x, double* y, int64_t n, int32_t which, void* stream);
 
 const char* rk_status_string(int32_t code);

@@ -316,8 +316,8 @@ def diffusion_1d(U, D, dx, out=None, stream=None):
 
 
 def eval_exp(x, which=0, out=None, stream=None):
-    """The kernels' table-driven exp on a CUDA float64 tensor (0: exp(x), 1/2: exp(+-x) pair;
-    3/4/5: the same in the mixed-precision form)."""
+    """The kernels' own elementary functions on a CUDA float64 tensor (0: exp(x), 1/2: exp(+-x)
+    pair; 3/4/5: the same in the mixed-precision form; 6: ln x; 7: 1/x)."""
     out = torch.empty_like(x) if out is None else out
     _check(_L().rk_eval_exp(_dptr(x, "x"), _dptr(out, "out", x.numel()), x.numel(), int(which),
                             _stream_ptr(stream)), "rk_eval_exp")

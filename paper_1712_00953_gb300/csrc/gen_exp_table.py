@@ -1,13 +1,19 @@
-"""Generate exp2_table.h: correctly rounded 2^(j/128), j = 0..127, as hex literals.
+"""Generate exp2_table.h: the tables of the kernels' exponential and logarithm.
 
-Used by the table-driven exponential of the kernels (Tang, "Table-driven
-implementation of the exponential function in IEEE floating-point arithmetic",
-ACM TOMS 15(2), 1989).  The values are computed with 50-digit decimal
+Exponential (Tang, "Table-driven implementation of the exponential function
+in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989): correctly rounded
+2^(j/128), j = 0..127, and ln2/128 split in two.  Logarithm (Tang,
+"Table-driven implementation of the logarithm function in IEEE
+floating-point arithmetic", ACM TOMS 16(4), 1990): for the 128 intervals
+[1 + j/128, 1 + (j+1)/128) of the significand, the reciprocal of the
+interval's centre rounded to binary64 (inv_c) and -ln(inv_c) of that rounded
+value, and ln2 split in two.  Values are computed with 60-digit decimal
 arithmetic and rounded once to binary64.
 
     python paper_1712_00953_gb300/csrc/gen_exp_table.py > paper_1712_00953_gb300/csrc/exp2_table.h
 """
 
+import struct
 from decimal import Decimal, getcontext
 
 N = 128
@@ -16,7 +22,8 @@ N = 128
 def main():
     getcontext().prec = 60
     ln2 = Decimal(2).ln()
-    lines = ["// Generated by gen_exp_table.py: RK_EXP2_TABLE_VALUES[j] = 2^(j/128) rounded to binary64.",
+    lines = ["// Generated by gen_exp_table.py: RK_EXP2_TABLE_VALUES[j] = 2^(j/128) rounded to binary64;",
+             "// RK_LOG_INV_C_VALUES[j] = 1/(1 + (j + 1/2)/128) rounded, RK_LOG_LN_C_VALUES[j] = -ln of it.",
              "#pragma once", f"#define RK_EXP2_TABLE_N {N}", "#define RK_EXP2_TABLE_VALUES \\"]
     for j in range(N):
         v = (ln2 * j / N).exp()
@@ -27,13 +34,22 @@ def main():
     ln2n = ln2 / N
     head = float(ln2n)
     # clear the low 32 bits of the head so that k * head is exact for |k| < 2^20
-    import struct
     bits = struct.unpack("<Q", struct.pack("<d", head))[0] & ~((1 << 32) - 1)
     head = struct.unpack("<d", struct.pack("<Q", bits))[0]
     tail = float(ln2n - Decimal(head))
     lines.append(f"constexpr double RK_LN2_OVER_N_HI = {head.hex()};")
     lines.append(f"constexpr double RK_LN2_OVER_N_LO = {tail.hex()};")
     lines.append(f"constexpr double RK_N_OVER_LN2 = {float(Decimal(N) / ln2).hex()};")
+    # logarithm: inv_c_j = 1 / (1 + (j + 1/2) / N) rounded, ln_c_j = -ln(inv_c_j) of the rounded value
+    inv_c = [float(1 / (1 + (Decimal(j) + Decimal(1) / 2) / N)) for j in range(N)]
+    ln_c = [float(-Decimal(v).ln()) for v in inv_c]  # Decimal(v) is the binary64 value exactly
+    lines.append(f"#define RK_LOG_INV_C_VALUES {', '.join(v.hex() for v in inv_c)}")
+    lines.append(f"#define RK_LOG_LN_C_VALUES {', '.join(v.hex() for v in ln_c)}")
+    bits = struct.unpack("<Q", struct.pack("<d", float(ln2)))[0] & ~((1 << 32) - 1)
+    ln2_hi = struct.unpack("<d", struct.pack("<Q", bits))[0]
+    lines.append(f"constexpr double RK_LN2_HI = {ln2_hi.hex()};")
+    lines.append(f"constexpr double RK_LN2_LO = {float(ln2 - Decimal(ln2_hi)).hex()};")
+    lines.append(f"constexpr double RK_INV_LN10 = {float(1 / Decimal(10).ln()).hex()};")
     print("\n".join(lines))
 
 

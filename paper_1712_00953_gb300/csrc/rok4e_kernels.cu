@@ -63,6 +63,8 @@ constexpr int MAX_BLOCK_THREADS = 256;
 constexpr int EXP_TAB_BYTES = RK_EXP2_TABLE_N * 8;  // leads the dynamic shared memory
 
 __constant__ double c_exp2_table[RK_EXP2_TABLE_N] = {RK_EXP2_TABLE_VALUES};
+__constant__ double c_log_inv_c[RK_EXP2_TABLE_N] = {RK_LOG_INV_C_VALUES};
+__constant__ double c_log_ln_c[RK_EXP2_TABLE_N] = {RK_LOG_LN_C_VALUES};
 
 // ------------------------------------------------- table-driven exponential
 // exp(x) by Tang's table-driven method (ACM TOMS 15(2), 1989) with a 128-entry
@@ -147,6 +149,41 @@ __device__ __forceinline__ double rcp_newton(double x) {
   r = fma(r, e, r);
   e = fma(-x, r, 1.0);
   return fma(r, e, r);
+}
+
+// 1/x: rcp_newton where x and its reciprocal are FP32-normal (|x| in
+// [2^-125, 2^125)), a full division elsewhere (zero, subnormal, huge,
+// infinite, NaN).  Within ~1 ulp of the division.
+__device__ __forceinline__ double rcp_any(double x) {
+  const unsigned ex = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
+  return ex - 898u < 250u ? rcp_newton(x) : 1.0 / x;
+}
+
+// ------------------------------------------------- table-driven logarithm
+// ln x by Tang's table-driven method (ACM TOMS 16(4), 1990): x = 2^e m with
+// m in [1, 2); the significand's top 7 bits pick the interval
+// [1 + j/128, 1 + (j+1)/128) and its tabulated centre reciprocal inv_c_j
+// (rounded) with ln_c_j = -ln(inv_c_j), so ln x = e ln2 + ln_c_j + ln(1 + r),
+// r = m inv_c_j - 1 by one fma (|r| <= 2^-8), ln(1 + r) by its Taylor
+// polynomial through r^7 (truncation below 1e-20).  11 FP64 operations;
+// absolute error ~1.5e-16 max(1, |ln x|) (a few ulp only where ln x is near
+// 0, which the intervals below 1 reach through cancellation against e ln2).
+// Zero, negative, subnormal, infinite and NaN arguments take the library log().
+__device__ __forceinline__ double log_fast(double x) {
+  const int hi = __double2hiint(x);
+  if ((unsigned)(hi - 0x00100000) >= 0x7fe00000u) return log(x);
+  const int j = (hi >> 13) & (RK_EXP2_TABLE_N - 1);
+  const double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, __double2loint(x));
+  // e as a double: 2^52 + biased exponent, less 2^52 + 1023 (exact)
+  const double e = __hiloint2double(0x43300000, hi >> 20) - 4503599627371519.0;
+  const double r = fma(m, c_log_inv_c[j], -1.0);
+  double q = fma(r, 1.0 / 7.0, -1.0 / 6.0);
+  q = fma(q, r, 0.2);
+  q = fma(q, r, -0.25);
+  q = fma(q, r, 1.0 / 3.0);
+  q = fma(q, r, -0.5);
+  const double p = fma(__dmul_rn(r, r), q, r);
+  return fma(e, RK_LN2_HI, c_log_ln_c[j]) + fma(e, RK_LN2_LO, p);
 }
 
 // ---- double-float ("df") arithmetic: a value h + l held as two FP32 numbers
@@ -570,7 +607,7 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
   const int ns = m.ns;
   const double T = uu[ns];
   const double invT = rcp_newton(T);
-  const double lnT = log(T);
+  const double lnT = log_fast(T);
   // species pass 1: thermo, Gibbs factors, sum Y/W
   double S = 0.0;
   int ghi = 0;  // max over species of the high word of |g/RT| (integer compare)
@@ -690,7 +727,7 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
         y = fma(1.0 - a, tro[4 * i + 1], fma(a, tro[4 * i + 2], tro[4 * i + 3]));  // F_cent
       }
       tro[9 * nt + l] = y;
-      tro[4 * nt + l] = log10(y);
+      tro[4 * nt + l] = __dmul_rn(log_fast(y), RK_INV_LN10);
     }
     g.sync();
     for (int i = g.lane; i < nt; i += G) {
@@ -704,7 +741,7 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
       //   1/(1 + f1^2) = D^2/(D^2 + x^2) with f1 = x / D
       const double s2 = fma(D, D, x * x);
       const double onePr = 1.0 + Pr;
-      const double qd = 1.0 / (onePr * s2);
+      const double qd = rcp_any(__dmul_rn(onePr, s2));
       const double iOnePr = s2 * qd;
       const double rr = onePr * qd;  // 1 / (D^2 + x^2)
       const double iden = D * D * rr;
@@ -726,7 +763,7 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
         const double dlF_dlFc = fma(-w, fma(-0.67, D, __dmul_rn(1.1762, x)), iden);
         const double e2t = fo[6] > 0.0 ? __dmul_rn(__dmul_rn(__dmul_rn(fo[6], invT), invT), e2) : 0.0;
         const double dFc = fma(-(1.0 - a), __dmul_rn(fo[4], e3), fma(-a, __dmul_rn(fo[5], e1), e2t));
-        tro[7 * nt + i] = fma(__dmul_rn(dlF_dlFc, dFc), 1.0 / Fc, fma(gg, dlnk0 - dlnk_inf, dlnk_inf));
+        tro[7 * nt + i] = fma(__dmul_rn(dlF_dlFc, dFc), rcp_any(Fc), fma(gg, dlnk0 - dlnk_inf, dlnk_inf));
         tro[8 * nt + i] = er * F * iOnePr * gg;  // (dk/d[M]) / k_inf
       }
     }
@@ -1428,7 +1465,7 @@ __device__ inline void factor_small(const SlotPtrs& s, int mdim, double h) {
           A[c * MAXM + j] = A[pr * MAXM + j];
           A[pr * MAXM + j] = t;
         }
-      const double inv = 1.0 / A[c * MAXM + c];
+      const double inv = rcp_any(A[c * MAXM + c]);
       for (int r = c + 1; r < mdim; ++r) {
         const double l = A[r * MAXM + c] * inv;
         A[r * MAXM + c] = l;
@@ -1664,7 +1701,7 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
       const double ue = s.u[e];
       const double us = ue + h * fma(B4, k3, fma(B3, k2, fma(B2, k1, B1 * k0)));
       const double uh = ue + h * fma(BH4, k3, fma(BH3, k2, fma(BH2, k1, BH1 * k0)));
-      const double d = (uh - us) / (P.atol + P.rtol * fabs(us));
+      const double d = (uh - us) * rcp_any(fma(P.rtol, fabs(us), P.atol));
       part = fma(d, d, part);
       bad |= (__double2hiint(us) & 0x7ff00000) == 0x7ff00000;
       s.arg[e] = us;
@@ -2195,6 +2232,10 @@ __global__ void exp_eval_kernel(const double* __restrict__ x, double* __restrict
   if (i >= n) return;
   if (which == 0) {
     y[i] = exp_fast(x[i], tab);
+  } else if (which == 6) {
+    y[i] = log_fast(x[i]);
+  } else if (which == 7) {
+    y[i] = rcp_any(x[i]);
   } else if (which == 3) {
     y[i] = exp_mixed(x[i], tab);
   } else if (which == 4 || which == 5) {
@@ -3023,7 +3064,7 @@ int rk_probe_throughput(int32_t kind, double* ops_per_s) {
 }
 
 int rk_eval_exp(const double* x, double* y, int64_t n, int32_t which, void* stream) {
-  if (n < 0 || which < 0 || which > 5) return set_error(RK_E_INVALID_ARGUMENT, "bad exp arguments");
+  if (n < 0 || which < 0 || which > 7) return set_error(RK_E_INVALID_ARGUMENT, "bad exp arguments");
   if (n == 0) return RK_OK;
   if (!x || !y) return set_error(RK_E_INVALID_ARGUMENT, "null array");
   exp_eval_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, y, n, which);

@@ -382,6 +382,43 @@ def test_mixed_exp_close_to_cuda_exp(rk):
         assert np.max(np.abs(y - r) / r) < 2e-12
 
 
+def test_table_log_and_newton_reciprocal_match_cuda(rk):
+    """The kernels' table-driven ln (Tang 1990) against CUDA's log: within
+    3 ulp or 2.5e-16 absolute (near x = 1, where the intervals below 1 cancel
+    against -ln 2); the Newton reciprocal within 1 ulp of the IEEE division;
+    both identical to the library on their fallback ranges (zero, negative,
+    subnormal, huge, infinite, NaN)."""
+    rng = np.random.default_rng(2)
+    tiny = np.finfo(float).tiny
+    special = [1.0, 2.0, 0.5, 1.0 - 2.0 ** -53, 1.0 + 2.0 ** -52, tiny, np.finfo(float).max, 5e-324, 0.0,
+               -0.0, -1.0, np.inf, -np.inf, np.nan, 2.0 ** -125, 2.0 ** 125, np.nextafter(2.0 ** 125, 0.0)]
+    x = np.concatenate([10.0 ** rng.uniform(-307, 308, 400000), rng.uniform(200.0, 6000.0, 200000),
+                        rng.uniform(0.25, 4.0, 200000), 1.0 + rng.uniform(-1e-2, 1e-2, 50000), special])
+    xt = torch.tensor(x, device="cuda")
+    y = rk.eval_exp(xt, 6).cpu().numpy()
+    ref = torch.log(xt).cpu().numpy()
+    fast = (x >= tiny) & np.isfinite(x)
+    bound = np.maximum(3.0 * np.spacing(np.abs(ref[fast])), 2.5e-16)
+    assert np.all(np.abs(y[fast] - ref[fast]) <= bound)
+    assert y[x == 1.0][0] == 0.0 or abs(y[x == 1.0][0]) < 1e-18
+    other = ~fast
+    assert np.array_equal(np.isnan(y[other]), np.isnan(ref[other]))
+    keep = other & ~np.isnan(ref)
+    assert np.array_equal(y[keep], ref[keep])
+
+    xr = np.concatenate([x, -x])
+    xrt = torch.tensor(xr, device="cuda")
+    yr = rk.eval_exp(xrt, 7).cpu().numpy()
+    rr = (1.0 / xrt).cpu().numpy()
+    ax = np.abs(xr)
+    newton = (ax >= 2.0 ** -125) & (ax < 2.0 ** 125)
+    assert np.max(_ulps(yr[newton], rr[newton])) <= 1
+    other = ~newton
+    assert np.array_equal(np.isnan(yr[other]), np.isnan(rr[other]))
+    keep = other & ~np.isnan(rr)
+    assert np.array_equal(yr[keep], rr[keep])
+
+
 def test_cuda_graph_capture_matches_eager(rk):
     """The split step captured once in a CUDA graph and replayed gives the same
     bits as the eager calls."""
