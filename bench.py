@@ -668,7 +668,7 @@ def run_ours(args, rank, world, local_rank):
         # and goes stale when the kernel changes)
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_nominal, "unit": "TFLOP/s",
                      "frac": achieved / peak_nominal,
-                     "traffic": 1551872 if args.precision == "fp64" else None,
+                     "traffic": 1531904 if args.precision == "fp64" else None,
                      "traffic_unit": "bytes per launch (ncu capture)",
                      "algorithmic_bytes_per_launch": int(npts * N * 8 * 3 + npts * (16 + 16)),
                      "kernel": "rok4e_integrate_kernel<32>", "kernel_ms_per_step": 1e3 * kern_total / args.steps,
