@@ -595,10 +595,11 @@ __device__ __forceinline__ T piece_sum(const MechView& m, const T* part, int k) 
 // internal energies u_k/RT = h_k/RT - 1 and c_v/R = c_p/R - 1 per species).  uu, out: N-vectors in shared memory
 // (out must not alias uu).  When `cache` is set, the values the analytic
 // Jacobian-vector product reuses are kept (rate coefficients, w, d(cp/R)/dT
-// and the cell scalars).  Inlined into every caller: each product that meets
-// a sum is written as an explicit fma or __dmul_rn, so no context can contract
-// it differently, chem_rhs and the integrator compute the same bits and
-// R(u) - R(u) is exactly zero in a steady-state cell.
+// and the cell scalars).  Inlined into the 32-lane FP64 integrator and called
+// through rhs_eval_call elsewhere; each product that meets a sum is written as
+// an explicit fma or __dmul_rn, so no copy can contract it differently,
+// chem_rhs and the integrator compute the same bits and R(u) - R(u) is
+// exactly zero in a steady-state cell.
 template <int G, bool MIXED = false>
 __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, const double* uu,
                                       const double* src, double p, double* out, bool cache,
