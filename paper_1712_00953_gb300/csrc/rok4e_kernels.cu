@@ -323,14 +323,17 @@ struct SlotLayout {
   int tb;                                     // [ntb][4]: [M], dk/d[M], dlnk/dT, 1/Kc
   int tro;                                    // [11][ntroe]: Troe falloff scratch
   int part;                                   // [npiece]: gather partial sums
-  int C2, dC2;                                // species: double-float C and dC (precision 3)
+  int C2, dC2;                                // species: double-float C and dC (precision 3, else -1)
   int H, LU, piv, red, Bm;                    // small (Bm: I - (I - h gamma H)^-1)
   int fbase;  // FP32 region (mixed precision only), offset in doubles
   int fC, fdC, fh, fcp, fdcp, fom, fq, fkc, fkr, ftb, fQ, fw, fpart;  // offsets in floats from fbase
   int stride;
 };
 
-static SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false, int nx = 0) {
+// mixed: the FP32 arrays of precision levels 1 and 2; df: the double-float
+// species arrays of precision level 3 (left out otherwise, which lets a 53-species
+// mechanism keep 7 cells per block instead of 6).
+static SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false, int nx = 0, bool df = false) {
   SlotLayout s;
   s.N = L.ns + 1 + nx;
   s.ns = L.ns;
@@ -370,8 +373,8 @@ static SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false, int 
   s.tb = take(4 * (L.ntb > 0 ? L.ntb : 1));
   s.tro = take(11 * (L.ntroe > 0 ? L.ntroe : 1));
   s.part = take(L.npiece > 0 ? L.npiece : 1);
-  s.C2 = take(ns1);
-  s.dC2 = take(ns1);
+  s.C2 = df ? take(ns1) : -1;
+  s.dC2 = df ? take(ns1) : -1;
   s.H = take(MAXM * MAXM);
   s.LU = take(MAXM * MAXM);
   s.piv = take(MAXM);
@@ -539,8 +542,8 @@ __device__ inline SlotPtrs slot_ptrs(double* b, const SlotLayout& s) {
   p.qT = b + s.qT;
   p.tro = b + s.tro;
   p.part = b + s.part;
-  p.C2 = reinterpret_cast<df2*>(b + s.C2);
-  p.dC2 = reinterpret_cast<df2*>(b + s.dC2);
+  p.C2 = s.C2 >= 0 ? reinterpret_cast<df2*>(b + s.C2) : nullptr;
+  p.dC2 = s.dC2 >= 0 ? reinterpret_cast<df2*>(b + s.dC2) : nullptr;
   p.tb = b + s.tb;
   p.H = b + s.H;
   p.LU = b + s.LU;
@@ -1781,8 +1784,10 @@ __device__ inline void init_sentinels(const SlotPtrs& s, int ns, int lane) {
   if (lane == 0) {
     s.C[ns] = 1.0;
     s.dC[ns] = 0.0;
-    s.C2[ns] = {1.0f, 0.0f};
-    s.dC2[ns] = {0.0f, 0.0f};
+    if (s.C2) {
+      s.C2[ns] = {1.0f, 0.0f};
+      s.dC2[ns] = {0.0f, 0.0f};
+    }
     s.hRT[ns] = 0.0;
     s.gRT[ns] = 0.0;
     s.E[ns] = 1.0;
@@ -2459,7 +2464,7 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   P.mech = mech->dev;
   P.L = mech->host.L;
   P.nx = nx;
-  P.S = make_slot(mech->host.L, Meff, mixed, nx);
+  P.S = make_slot(mech->host.L, Meff, mixed, nx, o.precision == 3);
   P.precision = o.precision;
   P.Y = Y;
   P.src = src;
@@ -2622,7 +2627,7 @@ static int point_call(const rk_mech* mech, const double* Y, const double* src, c
   P.nx = nx;
   P.mech = mech->dev;
   P.L = mech->host.L;
-  P.S = make_slot(mech->host.L, 1, mode >= 3, nx);
+  P.S = make_slot(mech->host.L, 1, mode >= 3, nx, mode == 5);
   P.Y = Y;
   P.src = src;
   P.V = V;
