@@ -342,6 +342,51 @@ def test_simpler_split_step_1d_parity(rk):
         _assert_state_close(Ug.cpu().numpy(), Uo, mech.n_species, f"split step {step}")
 
 
+def test_flame1d_full_size_split_steps_sampled(rk):
+    """The 2048-point flame1d Simpler split step at full size in the
+    benchmark's launch configuration (carried h_cell, default queue order and
+    block shape), two steps from the initial field.  Each step is checked at
+    sampled points -- the hottest cell, the steepest temperature gradient, the
+    middle and both ends -- against the oracle started from the GPU's own
+    input state: the reaction sub-step of the seven points around each sample
+    is replayed with the full field's T(U_n), and the one-step SSP-RK3
+    transport correction, whose stencil reaches three points, then gives the
+    sample exactly as over the whole field."""
+    from oracle import splitting as osp
+    from oracle.kinetics import Kinetics
+    from synth.fields import field_tanh_front
+
+    w, mech = _mech("flame1d")
+    kin = Kinetics(mech)
+    _, U0 = field_tanh_front(w.n_cells, mech.n_species, w.field_seed)
+    npts = U0.shape[0]
+    assert npts == 2048
+    dx, D = 1e-2 / npts, 1e-4
+    ns = mech.n_species
+    m = rk.mech_load(mech)
+    Ug = torch.tensor(U0, device="cuda")
+    hc = torch.zeros(npts, dtype=torch.float64, device="cuda")
+    trace = torch.zeros(npts, 1024, dtype=torch.float64, device="cuda")
+    stats = torch.zeros(npts, 4, dtype=torch.int32, device="cuda")
+    for step in range(2):
+        Un, hn = Ug.cpu().numpy(), hc.cpu().numpy()
+        trace.zero_()
+        rk.simpler_split_step(m, Ug, w.dt, D, dx, w.rtol, w.atol, w.krylov_dim, h_cell=hc, stats=stats,
+                              opts=rk.Opts(trace=trace))
+        torch.cuda.synchronize()
+        out, st, tr = Ug.cpu().numpy(), stats.cpu().numpy(), trace.cpu().numpy()
+        assert np.all(st[:, 3] == 0) and np.all(np.isfinite(out))
+        attempts = st[:, 0] + st[:, 1]
+        assert attempts.max() <= trace.shape[1]
+        picks = (int(np.argmax(attempts)), int(np.argmax(np.abs(np.diff(Un[:, ns])))), npts // 2, 0, npts - 1)
+        centres = sorted({min(max(c, 3), npts - 4) for c in picks})
+        cells = sorted({c + d for c in centres for d in range(-3, 4)})
+        replay = [_replay_of(tr[c]) if c in cells else None for c in range(npts)]
+        ref, _, _, _ = osp.simpler_split_step_1d(kin, Un, P, w.dt, D, dx, w.rtol, w.atol, w.krylov_dim,
+                                                 h_cell=hn, replay=replay, cells=cells)
+        _assert_state_close(out[centres], ref[centres], ns, f"full-size split step {step}")
+
+
 def _ulps(a, b):
     ia = a.view(np.int64)
     ib = b.view(np.int64)

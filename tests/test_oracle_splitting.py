@@ -279,3 +279,27 @@ def test_simpler_split_matches_dedicated_function():
     b, _, _, _ = sp.simpler_split_step_1d(kin, U, 101325.0, 1e-8, 1e-4, 1e-2 / 8, 1e-6, 1e-10, 4,
                                           h_cell=np.zeros(8))
     np.testing.assert_array_equal(a, b)
+
+
+def test_reaction_windows_give_the_full_field_step_at_their_centres():
+    """The one-step SSP-RK3 transport correction reaches three points, so a
+    sampled point's split step needs the reaction sub-step only on the seven
+    points around it (the full-size GPU parity test relies on this): with the
+    step sequences replayed, the windowed step equals the full-field step
+    exactly at the window centres, near the boundaries too, and not one point
+    further out."""
+    from synth.fields import WORKLOADS, field_tanh_front, mechanism_for
+
+    w = WORKLOADS["flame1d"]
+    mech = mechanism_for(w)
+    kin = Kinetics(mech)
+    npts = 40
+    _, U = field_tanh_front(npts, mech.n_species, w.field_seed)
+    dx, D, p = 1e-2 / npts, 1e-4, 101325.0
+    full, _, infos, _ = sp.simpler_split_step_1d(kin, U, p, w.dt, D, dx, w.rtol, w.atol, 4, record=True)
+    centres = [3, 17, 20, 36]
+    cells = sorted({c + d for c in centres for d in range(-3, 4)})
+    replay = [infos[c]["trace"] if c in cells else None for c in range(npts)]
+    win, _, _, _ = sp.simpler_split_step_1d(kin, U, p, w.dt, D, dx, w.rtol, w.atol, 4, replay=replay, cells=cells)
+    assert np.array_equal(win[centres], full[centres])
+    assert not np.array_equal(win[15], full[15])  # two points from an uncomputed one
