@@ -255,7 +255,11 @@ size_t rk_rok4e_workspace_size(const rk_mech* mech, int64_t ncell, int32_t krylo
  * dt/h_cell, binned on a quarter-octave log scale) and dealt to fixed
  * per-block bins; otherwise the queue interleaves the cell index so that
  * neighbouring cells spread over the SMs.  The order changes only the
- * schedule: each cell's result is the same bits either way. */
+ * schedule: each cell's result is the same bits either way.
+ * Returns RK_E_INVALID_ARGUMENT for null arrays, ncell < 0, dt <= 0, bad
+ * tolerances or options; RK_E_WORKSPACE for a missing or short workspace;
+ * RK_E_UNSUPPORTED when the mechanism and one cell's work arrays do not fit in
+ * an SM's shared memory; RK_E_CUDA when a launch fails.  ncell = 0 is a no-op. */
 int rk_rok4e_integrate(const rk_mech* mech, double* Y, const double* src, double* h_cell,
                        int64_t ncell, double p, double dt, double rtol, double atol,
                        int32_t krylov_dim, const rk_opts* opts, int32_t* stats, void* workspace,
@@ -283,7 +287,10 @@ int rk_rkdp_integrate(const rk_mech* mech, double* Y, const double* src, double*
  *   reaction:  dU/dt = R(U) - c_n over dt from U_n   (ROK4E, per cell);
  *   transport: dU/dt = T(U) + c_n over dt/2           (one SSP-RK3 step).
  *  U       device [npts x N] in/out;  h_cell as in rk_rok4e_integrate.
- *  stats   as in rk_rok4e_integrate (reaction sub-step), or NULL. */
+ *  stats   as in rk_rok4e_integrate (reaction sub-step), or NULL.
+ *  D, dx   diffusivity (m^2/s, >= 0) and grid spacing (m, > 0).
+ * Workspace from rk_simpler_split_step_workspace_size; error codes as for
+ * rk_rok4e_integrate. */
 size_t rk_simpler_split_step_workspace_size(const rk_mech* mech, int64_t npts,
                                             int32_t krylov_dim, const rk_opts* opts);
 int rk_simpler_split_step(const rk_mech* mech, double* U, double* h_cell, int64_t npts, double p,
@@ -386,7 +393,12 @@ int rk_probe_throughput(int32_t kind, double* ops_per_s);
  * for n < 0 or which outside 0..7. */
 int rk_eval_exp(const double* x, double* y, int64_t n, int32_t which, void* stream);
 
+/* Name of an RK_* return code (a static string; "unknown status" otherwise). */
 const char* rk_status_string(int32_t code);
+
+/* Copies the message of the most recent failed call on the calling thread
+ * (empty if none) into buf, truncated to len - 1 characters and terminated;
+ * buf may be NULL.  Always returns RK_OK. */
 int rk_last_error(char* buf, size_t len);
 
 #ifdef __cplusplus
