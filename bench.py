@@ -664,11 +664,15 @@ def run_ours(args, rank, world, local_rank):
                    "queue_order": args.queue_order, "blocks_per_sm": args.blocks_per_sm},
         # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one fp64
         # integration launch of this workload from one ncu --set full capture
-        # of this kernel (bytes per launch; it describes the kernel as captured
-        # and goes stale when the kernel changes)
+        # of the current kernel (bytes per launch), null while no capture of
+        # the current kernel exists; traffic_last_capture keeps the figure of
+        # the last captured build, labelled as such
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_nominal, "unit": "TFLOP/s",
                      "frac": achieved / peak_nominal,
-                     "traffic": 1531904 if args.precision == "fp64" else None,
+                     "traffic": None,
+                     "traffic_last_capture": {"bytes_per_launch": 1531904, "build": "before the cell slots "
+                                              "dropped the double-float arrays outside precision level 3 "
+                                              "(shared-memory offsets only)"} if args.precision == "fp64" else None,
                      "traffic_unit": "bytes per launch (ncu capture)",
                      "algorithmic_bytes_per_launch": int(npts * N * 8 * 3 + npts * (16 + 16)),
                      "kernel": "rok4e_integrate_kernel<32>", "kernel_ms_per_step": 1e3 * kern_total / args.steps,
