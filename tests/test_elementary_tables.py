@@ -3,7 +3,9 @@
 generator's output, every entry is the correctly rounded value of its
 definition (60-digit decimal arithmetic), and the logarithm's method with
 this table -- emulated on the host with exactly rounded fma -- stays within
-the bound the GPU test applies to the kernel (3 ulp or 2.5e-16 absolute)."""
+the bound the GPU test applies to the kernel (3 ulp or 2.5e-16 absolute).
+The kernels' Newton reciprocal, emulated the same way from a correctly
+rounded FP32 estimate, stays within 1 ulp of the IEEE quotient."""
 
 import importlib.util
 import io
@@ -110,3 +112,23 @@ def _check_log_method():
         bound = max(Decimal(3) * Decimal(float(np.spacing(abs(float(exact))))), Decimal("2.5e-16"))
         assert err <= bound, (x, y, float(exact))
     assert _log_method(1.0, inv_c, ln_c, c) == 0.0 or abs(_log_method(1.0, inv_c, ln_c, c)) < 1e-18
+
+
+def _rcp_method(x):
+    """Two Newton steps r <- r + r (1 - x r) from the correctly rounded FP32
+    reciprocal, each operation rounded once, as in the kernels."""
+    r = float(np.float32(1.0) / np.float32(x))
+    e = _fma(-x, r, 1.0)
+    r = _fma(r, e, r)
+    e = _fma(-x, r, 1.0)
+    return _fma(r, e, r)
+
+
+def test_newton_reciprocal_method_within_one_ulp():
+    rng = np.random.default_rng(6)
+    xs = np.concatenate([2.0 ** rng.uniform(-124.9, 124.9, 2000), 1.0 + rng.uniform(0.0, 1.0, 500),
+                         [1.0, 3.0, 0.1, 2.0 ** -125, np.nextafter(2.0 ** 125, 0.0), 1.0 - 2.0 ** -53]])
+    xs = np.concatenate([xs, -xs])
+    for x in xs:
+        y, ref = _rcp_method(float(x)), 1.0 / float(x)
+        assert abs(np.array(y).view(np.int64) - np.array(ref).view(np.int64)) <= 1, (x, y, ref)
