@@ -187,6 +187,25 @@ def test_troe_center_value():
         assert kin._troe_F(T, np.array([pr]))[0][0] <= 1.0 + 1e-15
 
 
+def test_troe_broadening_width():
+    """F = sqrt(Fcent) where the broadening ratio (log Pr + c) / (n - d (log Pr + c))
+    is +1 or -1, i.e. at log Pr + c = n / (1 + d) and -n / (1 - d), d = 0.14:
+    two points at different distances on either side of the centre, which fix
+    n and d (and the sign of d) where the centre value cannot."""
+    a, T3, T1, T2 = 0.6, 200.0, 1500.0, 5000.0
+    kin = Kinetics(_troe_mech(a, T3, T1, T2))
+    T = 1100.0
+    Fc = (1 - a) * np.exp(-T / T3) + a * np.exp(-T / T1) + np.exp(-T2 / T)
+    c = -0.4 - 0.67 * np.log10(Fc)
+    n = 0.75 - 1.27 * np.log10(Fc)
+    for x in (n / 1.14, -n / 0.86):
+        F = kin._troe_F(T, np.array([10.0 ** (x - c)]))[0][0]
+        assert F == pytest.approx(np.sqrt(Fc), rel=1e-12)
+    # the mirror image of the lower point is not a half-width point
+    F = kin._troe_F(T, np.array([10.0 ** (n / 0.86 - c)]))[0][0]
+    assert abs(F - np.sqrt(Fc)) > 1e-3 * np.sqrt(Fc)
+
+
 def test_third_body_linear_in_efficiencies():
     w = WORKLOADS["flame1d"]
     mech = mechanism_for(w)
