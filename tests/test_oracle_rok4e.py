@@ -222,3 +222,30 @@ def test_arnoldi_breakdown_on_invariant_subspace():
 def test_zero_rhs_gives_empty_basis():
     Q, H = rok4e.arnoldi(lambda v: v, np.zeros(4), 4)
     assert Q.shape == (4, 0)
+
+
+def test_error_norm_is_rms_over_all_components():
+    """Reading R5 (the paper leaves the norm open): the root mean square over
+    all N components.  A component with no error dilutes it by sqrt(N/(N+1)),
+    which a max norm would not; one error at the tolerance in every component
+    gives err = 1 whatever N."""
+    rng = np.random.default_rng(11)
+    u = rng.uniform(0.5, 2.0, 6)
+    d = rng.normal(size=6) * 1e-7
+    e6 = rok4e.error_norm(u, u + d, 1e-6, 1e-9)
+    e7 = rok4e.error_norm(np.append(u, 1.0), np.append(u + d, 1.0), 1e-6, 1e-9)
+    assert e7 == pytest.approx(e6 * np.sqrt(6 / 7), rel=1e-13)
+    sc = 1e-9 + 1e-6 * u
+    assert rok4e.error_norm(u, u + sc, 1e-6, 1e-9) == pytest.approx(1.0, rel=1e-9)  # (u + sc) - u rounds
+
+
+def test_error_weights_use_the_propagated_solution():
+    """Reading R5: the weights atol + rtol |u*| come from the propagated
+    (order-4) solution u*, not the embedded one: with atol = 0 and u^ - u* =
+    rtol u* in every component the error is exactly 1, while weights from u^
+    would give 1 / (1 + rtol)."""
+    rtol = 1e-3
+    u_star = np.array([1.0, 100.0, 0.25])
+    u_hat = u_star * (1 + rtol)
+    assert rok4e.error_norm(u_star, u_hat, rtol, 0.0) == pytest.approx(1.0, rel=1e-12)
+    assert abs(rok4e.error_norm(u_star, u_hat, rtol, 0.0) - 1 / (1 + rtol)) > 1e-4
