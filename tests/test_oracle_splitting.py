@@ -303,3 +303,66 @@ def test_reaction_windows_give_the_full_field_step_at_their_centres():
     win, _, _, _ = sp.simpler_split_step_1d(kin, U, p, w.dt, D, dx, w.rtol, w.atol, 4, replay=replay, cells=cells)
     assert np.array_equal(win[centres], full[centres])
     assert not np.array_equal(win[15], full[15])  # two points from an uncomputed one
+
+
+def test_laplacian_ends_are_zero_flux_walls():
+    """Reading R18, zero-gradient ends: the first point does not see the last
+    one (no wrap-around), and a linear profile U = a + b x on cell centres,
+    whose interior fluxes are all b, gains b / dx in the first cell and loses
+    it in the last, since nothing crosses the walls."""
+    n, dx, b = 12, 0.25, 3.0
+    x = (np.arange(n) + 0.5) * dx
+    U = (2.0 + b * x)[:, None]
+    L = sp.laplacian_neumann(U, dx)
+    assert np.allclose(L[1:-1, 0], 0.0, atol=1e-12)
+    assert L[0, 0] == pytest.approx(b / dx, rel=1e-12) and L[-1, 0] == pytest.approx(-b / dx, rel=1e-12)
+    V = np.random.default_rng(2).normal(size=(n, 2))
+    W = V.copy()
+    W[-1] += 5.0
+    assert np.array_equal(sp.laplacian_neumann(V, dx)[:-2], sp.laplacian_neumann(W, dx)[:-2])
+
+
+@pytest.mark.parametrize("scheme", sp.SCHEMES)
+def test_1d_schemes_are_the_generic_schemes(scheme):
+    """Each branch of split_step_1d is the scheme function pinned on the scalar
+    problems above (Strang, Eq. balanced, simple balanced reaction first,
+    Eq. simpler_balanced), driven by the 1-D flows: one SSP-RK3 step for
+    transport, ROK4E per cell for reaction with the first step carried over."""
+    from oracle import rok4e
+    from synth.fields import WORKLOADS, field_tanh_front, mechanism_for
+
+    w = WORKLOADS["flame1d"]
+    mech = mechanism_for(w)
+    kin = Kinetics(mech)
+    n, p, dt, D = 8, 101325.0, 1e-8, 1e-4
+    dx = 1e-2 / n
+    _, U = field_tanh_front(n, mech.n_species, w.field_seed)
+    hc = np.zeros(n)
+
+    def flow_T(V, t, c):
+        return sp.ssprk3(V, t, lambda X: sp.diffusion_op(X, D, dx) + c)
+
+    def flow_R(V, t, src):
+        out = V.copy()
+        for i in range(n):
+            s = None if np.isscalar(src) and src == 0.0 else src[i]
+            f, jv_at = rok4e.reactor(kin, p, s)
+            out[i], inf = rok4e.integrate(f, jv_at, V[i], t, w.rtol, w.atol, 4, h0=hc[i])
+            hc[i] = inf["h_last"]
+        return out
+
+    def T_op(V):
+        return sp.diffusion_op(V, D, dx)
+
+    def R_op(V):
+        return np.array([kin.rhs(u, p) for u in V])
+
+    generic = {
+        "simpler": lambda: sp.simpler_step(U, dt, T_op, flow_T, flow_R),
+        "strang": lambda: sp.strang_step(U, dt, flow_T, flow_R),
+        "simple_balanced": lambda: sp.simple_balanced_step(U, dt, T_op, R_op, flow_T, flow_R, True),
+        "simple_balanced_transport_first": lambda: sp.simple_balanced_step(U, dt, T_op, R_op, flow_T, flow_R,
+                                                                           False),
+    }[scheme]()
+    dedicated = sp.split_step_1d(kin, U, p, dt, D, dx, w.rtol, w.atol, 4, scheme)
+    np.testing.assert_array_equal(dedicated, generic)
