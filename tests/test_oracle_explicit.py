@@ -176,3 +176,41 @@ def test_agrees_with_rok4e_on_a_chemistry_cell():
     ns = mech.n_species
     assert ie["status"] == 0 and ir["status"] == 0
     assert np.max(np.abs(ue[:ns] - ur[:ns])) < 1e-8 and abs(ue[ns] - ur[ns]) < 1e-5
+
+
+def test_controller_exponent_matches_the_pair_order():
+    """The embedded difference of the 5(4) pair scales as h^5, so the
+    controller's h* = 0.9 err^(-1/5) h must bring the next error to 0.9^5
+    (unclipped factors): checked at err = 10 on the linear system with tight
+    tolerances, where the asymptotic law holds to ~1 %.  An exponent of -1/4
+    would land near 0.33."""
+    L, c, u0 = _linear_problem()
+    f = lambda u: L @ u + c
+
+    def err(h):
+        u5, u4, _, _ = explicit.attempt(f, u0, f(u0), h)
+        return explicit.error_norm(u5, u4, 1e-13, 1e-13)
+
+    lo, hi = 1e-4, 1.0
+    for _ in range(60):  # bisection for err(h) = 10
+        mid = np.sqrt(lo * hi)
+        lo, hi = (lo, mid) if err(mid) > 10 else (mid, hi)
+    e = err(lo)
+    assert 9.0 < e <= 10.0
+    assert err(lo * explicit.step_factor(e)) == pytest.approx(0.9**5, rel=0.05)
+
+
+def test_error_norm_is_rms_with_weights_from_the_propagated_solution():
+    """Reading R22: the RMS norm of ROK4E, weights atol + rtol |u5| from the
+    propagated 5th-order solution: an error-free component dilutes it by
+    sqrt(N/(N+1)) (a max norm would not), and u4 - u5 = rtol u5 with atol = 0
+    gives exactly 1 (weights from u4 would give 1 / (1 + rtol))."""
+    rng = np.random.default_rng(12)
+    u = rng.uniform(0.5, 2.0, 5)
+    d = rng.normal(size=5) * 1e-7
+    e5 = explicit.error_norm(u, u + d, 1e-6, 1e-9)
+    e6 = explicit.error_norm(np.append(u, 1.0), np.append(u + d, 1.0), 1e-6, 1e-9)
+    assert e6 == pytest.approx(e5 * np.sqrt(5 / 6), rel=1e-13)
+    rtol = 1e-3
+    u5 = np.array([1.0, 100.0, 0.25])
+    assert explicit.error_norm(u5, u5 * (1 + rtol), rtol, 0.0) == pytest.approx(1.0, rel=1e-12)

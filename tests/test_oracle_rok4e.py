@@ -249,3 +249,59 @@ def test_error_weights_use_the_propagated_solution():
     u_hat = u_star * (1 + rtol)
     assert rok4e.error_norm(u_star, u_hat, rtol, 0.0) == pytest.approx(1.0, rel=1e-12)
     assert abs(rok4e.error_norm(u_star, u_hat, rtol, 0.0) - 1 / (1 + rtol)) > 1e-4
+
+
+def test_pi_controller_uses_the_last_accepted_error():
+    """Sec. 4.3's PI controller, h* = h min(5, max(0.2, 0.8 err_n^(0.4/4) /
+    err*^(0.7/4))), with err_n the error of the last accepted step (1 before
+    the first, floored at 1e-10): every recorded attempt's step follows from
+    the previous attempt's error and the last accepted one, clipped to the
+    end of the interval, and the carried h_last is the last proposal."""
+    w = WORKLOADS["small"]
+    kin = Kinetics(mechanism_for(w))
+    f, jv_at = rok4e.reactor(kin, 101325.0)
+    u0 = initial_state(w)[5]
+    t_end = 1e-5
+    _, info = rok4e.integrate(f, jv_at, u0, t_end, 1e-8, 1e-12, 4, record=True)  # h0 = t_end
+    tr, errs = info["trace"], info["errs"]
+    assert len(tr) > 10 and any(not acc for _, acc in tr) and sum(acc for _, acc in tr) > 5
+    t, err_n = 0.0, 1.0
+    for i in range(len(tr)):
+        h, acc = tr[i]
+        e = max(errs[i], 1e-10)
+        proposal = h * min(5.0, max(0.2, 0.8 * err_n**0.1 / e**0.175))
+        if acc:
+            t += h
+            err_n = e
+        if i + 1 < len(tr):
+            assert tr[i + 1][0] == pytest.approx(min(proposal, t_end - t), rel=1e-12), i
+    assert tr[-1][1] and info["h_last"] == pytest.approx(proposal, rel=1e-12)
+
+
+def test_carried_step_is_the_controllers_proposal():
+    """h_last, the step a cell carries into its next split step, is the
+    controller's proposal after the last accepted step, not that step (which
+    the end of the interval clips): on a smooth problem it is larger (1.47 times here; exactly 1 if the accepted step were carried)."""
+    A = np.diag([-1.0, -2.0, -0.5])
+    f = lambda u: A @ u
+    _, info = rok4e.integrate(f, lambda u: (lambda v: A @ v), np.ones(3), 1.0, 1e-3, 1e-6, 3,
+                              h0=0.01, record=True)
+    last_accepted = [h for h, acc in info["trace"] if acc][-1]
+    assert info["h_last"] > 1.2 * last_accepted
+
+
+def test_fd_increment_stays_finite_at_the_zero_state():
+    """The finite-difference increment d = sqrt(eps) (1 + ||u||) / ||v|| of the
+    matrix-free product keeps its (1 + ...) so that u = 0 still has a step: on
+    an affine right-hand side the product is A v there too."""
+    rng = np.random.default_rng(13)
+    A = rng.normal(size=(5, 5))
+    c = rng.normal(size=5)
+
+    class Affine:
+        def rhs(self, u, p, src=None):
+            return A @ u + c
+
+    _, jv_at = rok4e.reactor(Affine(), 1.0, jv_mode="fd")
+    v = rng.normal(size=5)
+    assert np.allclose(jv_at(np.zeros(5))(v), A @ v, rtol=1e-6, atol=1e-6 * np.abs(A @ v).max())
