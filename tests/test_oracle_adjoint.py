@@ -1,7 +1,8 @@
 """Pins of the oracle's gradient of fixed-step ROK4E w.r.t. ln A and u0: the
 complex-step derivative agrees with central finite differences (whose
 truncation error is O(d^2)) on the sensitivities large enough for finite
-differences to resolve, and is linear in the objective weights."""
+differences to resolve, converges at that rate with a Richardson-extrapolated
+limit equal to it to 1e-8, and is linear in the objective weights."""
 
 import numpy as np
 import pytest
@@ -29,6 +30,25 @@ def test_complex_step_matches_central_differences(case):
     big = np.argsort(-np.abs(cs))[:5]
     fd = oad.grad_central_fd(kin, u0, P, h, n, 4, big, d=1e-4)
     assert np.max(np.abs(fd - cs[big]) / np.abs(cs[big])) < 1e-4
+
+
+def test_complex_step_is_the_limit_of_central_differences(case):
+    """Central differences at d and d/2 converge to the complex-step value at
+    the O(d^2) rate, and their Richardson extrapolation (O(d^4)) agrees with
+    it to 1e-8 relative -- tight enough to see a 1e-6 error in the
+    derivative itself."""
+    kin, u0 = case
+    h, n = 2e-8, 6
+    js = np.arange(kin.nr)
+    cs = oad.grad_complex_step(kin, u0, P, h, n, 4, js)
+    big = np.argsort(-np.abs(cs))[:5]
+    d = 1e-2
+    f1 = oad.grad_central_fd(kin, u0, P, h, n, 4, big, d=d)
+    f2 = oad.grad_central_fd(kin, u0, P, h, n, 4, big, d=d / 2)
+    e1, e2 = np.abs(f1 - cs[big]), np.abs(f2 - cs[big])
+    assert np.all((e1 / e2 > 3.5) & (e1 / e2 < 4.5))
+    rich = (4.0 * f2 - f1) / 3.0
+    assert np.max(np.abs(rich - cs[big]) / np.abs(cs[big])) < 1e-8
 
 
 def test_gradient_is_linear_in_the_objective(case):
