@@ -77,6 +77,28 @@ def test_thermo_continuous_at_midpoint(case):
         assert np.allclose(lo[:3], hi[:3], rtol=1e-8, atol=1e-8)
 
 
+def test_thermo_range_is_chosen_by_t_mid(case):
+    """NASA-7: below T_mid the low-temperature coefficients alone apply,
+    above it the high-temperature ones alone: scrambling the set that does
+    not apply leaves cp, h and s unchanged, scrambling the one that does
+    changes them."""
+    mech, kin, _ = case
+    tm = mech.nasa[:, 1]
+    rng = np.random.default_rng(14)
+    for lo_side in (True, False):
+        T = float(np.min(tm)) * 0.8 if lo_side else float(np.max(tm)) * 1.2
+        other = mech.copy()
+        same = mech.copy()
+        cols_other = slice(10, 17) if lo_side else slice(3, 10)
+        cols_same = slice(3, 10) if lo_side else slice(10, 17)
+        other.nasa[:, cols_other] *= 1.0 + 0.1 * rng.normal(size=other.nasa[:, cols_other].shape)
+        same.nasa[:, cols_same] *= 1.0 + 0.1 * rng.normal(size=same.nasa[:, cols_same].shape)
+        ref = kin.thermo(T)[:3]
+        for a, b in zip(Kinetics(other).thermo(T)[:3], ref):
+            np.testing.assert_array_equal(a, b)
+        assert not np.allclose(Kinetics(same).thermo(T)[0], ref[0], rtol=1e-6)
+
+
 def test_van_t_hoff(case):
     mech, kin, U = case
     u = _sample(U, 1)[0].copy()
