@@ -122,6 +122,18 @@ MISTAKES = [
     ("oracle/splitting.py", "    R = alpha * beta * alpha + (alpha * Bs - (alpha * beta + 1) * As) * A",
      "    R = alpha * beta * alpha + (alpha * Bs - (alpha * beta + 1) * As) * B", SPL, "caught"),
     ("oracle/splitting.py", "    alpha = np.exp(A * h / 2)", "    alpha = np.exp(A * h)", SPL, "caught"),
+    ("oracle/splitting.py", "    R = alpha * beta * alpha + 0.5 * (alpha * Bs - (alpha * beta + 1) * As) * (A - B)",
+     "    R = alpha * beta * alpha + 0.5 * (alpha * Bs - (alpha * beta + 1) * As) * (A + B)", SPL, "caught"),
+    ("oracle/splitting.py", "    Q = -0.5 * (alpha * Bs + (alpha * beta + 1) * As)",
+     "    Q = 0.5 * (alpha * Bs + (alpha * beta + 1) * As)", SPL, "caught"),
+    ("oracle/splitting.py", "    Q = -alpha * Bs", "    Q = -beta * Bs", SPL, "caught"),
+    ("oracle/splitting.py", "        return e * u + (e - 1) / k * (const + src)", "        return e * u + (e - 1) / k * (const - src)",
+     SPL, "caught"),
+    # scalar PSR model (Eq. scalar_psr)
+    ("oracle/splitting.py", "    react = (T_ad - T) * np.exp(-T_a / T)", "    react = (T_ad - T) * np.exp(-T_a * T)", SPL, "caught"),
+    ("oracle/splitting.py", "    mix = (T_in - T) / Da", "    mix = (T_in - T) * Da", SPL, "caught"),
+    ("oracle/splitting.py", "    return (T - T_in) / ((T_ad - T) * np.exp(-T_a / T))",
+     "    return (T - T_in) / ((T_ad - T) * np.exp(-T_a / (2 * T)))", SPL, "caught"),
     # auxiliary-temperature system
     ("oracle/conservative.py", '        e = (st["h_RT"] - 1.0) * R_GAS * T / self.W',
      '        e = (st["h_RT"]) * R_GAS * T / self.W', CON, "caught"),
