@@ -4,8 +4,9 @@ generator's output, every entry is the correctly rounded value of its
 definition (60-digit decimal arithmetic), and the logarithm's method with
 this table -- emulated on the host with exactly rounded fma -- stays within
 the bound the GPU test applies to the kernel (3 ulp or 2.5e-16 absolute).
-The kernels' Newton reciprocal, emulated the same way from a correctly
-rounded FP32 estimate, stays within 1 ulp of the IEEE quotient."""
+The exponential's method with its table stays within 2 ulp of the exact
+value, and the kernels' Newton reciprocal, emulated the same way from a
+correctly rounded FP32 estimate, within 1 ulp of the IEEE quotient."""
 
 import importlib.util
 import io
@@ -132,3 +133,36 @@ def test_newton_reciprocal_method_within_one_ulp():
     for x in xs:
         y, ref = _rcp_method(float(x)), 1.0 / float(x)
         assert abs(np.array(y).view(np.int64) - np.array(ref).view(np.int64)) <= 1, (x, y, ref)
+
+
+def _exp_method(x, tab, c):
+    """Tang's table-driven exp with the kernel's steps, each rounded once:
+    k = round(x 128 / ln2) by the 1.5 2^52 shifter, r = x - k ln2/128 in two
+    parts, e^r - 1 = r + r^2 (1/2 + r/6 + r^2/24 + r^3/120), 2^(k/128) from the
+    table and 2^(k >> 7) by exponent scaling."""
+    shifter = 6755399441055744.0
+    kt = _fma(x, c["RK_N_OVER_LN2"], shifter)
+    k = int(kt - shifter)
+    kd = kt - shifter
+    r = _fma(-kd, c["RK_LN2_OVER_N_HI"], x)
+    r = _fma(-kd, c["RK_LN2_OVER_N_LO"], r)
+    q = _fma(r, 1.0 / 120.0, 1.0 / 24.0)
+    q = _fma(q, r, 1.0 / 6.0)
+    q = _fma(q, r, 0.5)
+    p = _fma(r * r, q, r)
+    t = tab[k & 127]
+    return math.ldexp(_fma(t, p, t), k >> 7)
+
+
+def test_exp_method_within_two_ulp():
+    _, exp_vals, _, _, c = _header()
+    rng = np.random.default_rng(7)
+    xs = np.concatenate([rng.uniform(-700.0, 700.0, 1500), rng.uniform(-3.0, 3.0, 500),
+                         [0.0, 1.0, -1.0, 1e-300, np.log(2.0), 700.0, -700.0]])
+    with localcontext() as ctx:
+        ctx.prec = 40
+        for x in xs:
+            y = _exp_method(float(x), exp_vals, c)
+            exact = Decimal(float(x)).exp()
+            err_ulp = abs(Decimal(y) - exact) / Decimal(float(np.spacing(float(exact))))
+            assert err_ulp <= 2, (x, y, float(exact), float(err_ulp))
