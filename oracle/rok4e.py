@@ -2,20 +2,20 @@
 
 TEST INFRASTRUCTURE ONLY.  Nothing in the library imports this module.
 
-The integrator follows Algorithm 1 step by step:
+What it computes (Sec. 4.1-4.3):
 
 1. Arnoldi on K_M(J_n, f_n) gives Q_n (N x m) and H_n (m x m), m <= M
-   (Sec. 4.1).  Modified Gram-Schmidt with one full reorthogonalisation
-   pass; breakdown when the orthogonalised vector has lost all but 1e-12 of
-   the norm of J q_j, which leaves an invariant subspace of dimension m.
-2. For each stage i the transformed stage equation (Eq. s_stage_row_transformed)
-   is solved with the low-rank inverse of Eq. solve_kry_jac:
-     F_i = f(u_n + h sum_j alpha_ij k_j) + sum_j (gamma_ij/gamma) k_j
-     k_i = F_i - Q (I - (I - h gamma H)^-1) Q^T F_i - sum_j (gamma_ij/gamma) k_j
-   Stages 3 and 4 share the argument of f (alpha_4j = alpha_3j, alpha_43 = 0),
-   so f is evaluated 3 times per attempt, the first being f_n itself.
-3. u* = u_n + h sum b_j k_j, u^ = u_n + h sum bhat_j k_j, the normalised
-   error, the PI controller of Sec. 4.3 and accept/reject.
+   (Sec. 4.1, Eq. jac_proj).  Modified Gram-Schmidt with one full
+   reorthogonalisation pass; breakdown when the orthogonalised vector has lost
+   all but 1e-12 of the norm of J q_j, which leaves an invariant subspace of
+   dimension m.
+2. The four stages of the Rosenbrock form (Eq. s_stage_row) with A_n = Q H Q^T,
+   solved on the Krylov coordinates and the orthogonal complement separately
+   (``attempt``); the same stages as Eq. s_stage_row_transformed with the
+   inverse of Eq. solve_kry_jac.  f is evaluated 3 times per attempt.
+3. The solution and its embedded order-3 companion (coefficient table of
+   Sec. 4.2), the normalised error and the PI controller of Sec. 4.3, and
+   accept/reject, repeated until t_end.
 
 Readings of the text (where it is silent or garbled):
 * Table coeff_rok4e prints two rows labelled b_2 and bhat_2; the values are
@@ -104,34 +104,47 @@ def arnoldi(jv, f, M):
 
 
 def attempt(f, u, fn, Q, H, h):
-    """One ROK4E attempt of size h from u with f(u) = fn.  Returns (u*, u^, n_f)."""
+    """One ROK4E attempt of size h from u with f(u) = fn.  Returns (u*, u^, n_f).
+
+    The stages are those of the Rosenbrock form, Eq. s_stage_row (with the
+    factor h on its A_n term), for the projected Jacobian A_n = Q H Q^T of
+    Eq. jac_proj.  A_n vanishes on the orthogonal complement of the Krylov
+    space and acts as H on the Krylov coordinates, so every stage splits
+    exactly into an m x m Rosenbrock stage on the coordinates and an explicit
+    part on the complement:
+
+        (I - h gamma H) kappa_i = Q^T f_i + h H sum_{j<i} gamma_ij kappa_j
+        k_i = Q kappa_i + (f_i - Q Q^T f_i),   f_i = f(u + h sum_{j<i} alpha_ij k_j).
+
+    This is the stage vector of the transformed form (Eq. s_stage_row_transformed)
+    solved with the low-rank inverse of Eq. solve_kry_jac, reached without the
+    Woodbury identity.  A stage whose row of alpha_ij equals the previous
+    stage's has the same argument (ROK4E: alpha_4j = alpha_3j), so f is
+    evaluated at most 3 times per attempt, the first being fn itself.  Then
+    u* = u + h sum b_j k_j and u^ = u + h sum bhat_j k_j (Sec. 4.2, embedded
+    order-3 formula).
+    """
     m = Q.shape[1]
-    L = np.eye(m) - h * GAMMA * H
-    ks = []
+    N = u.shape[0]
+    dtype = np.result_type(u, fn, Q, H, float)
+    stage_matrix = np.eye(m) - h * GAMMA * H
+    K = np.zeros((4, N), dtype=dtype)  # stage vectors k_i
+    kappa = np.zeros((4, m), dtype=dtype)  # their Krylov coordinates Q^T k_i
     n_f = 0
-    f_prev_arg = None
-    f_prev_val = None
+    fi = fn
     for i in range(4):
-        arg = u + h * sum((ALPHA_IJ[i, j] * ks[j] for j in range(i)), np.zeros_like(u))
-        if i == 0:
-            fi = fn
-        elif f_prev_arg is not None and np.array_equal(arg, f_prev_arg):
-            fi = f_prev_val  # stage 4 shares stage 3's argument (alpha_4j = alpha_3j)
-        else:
-            fi = f(arg)
+        if i > 0 and not np.array_equal(ALPHA_IJ[i], ALPHA_IJ[i - 1]):
+            fi = f(u + h * (ALPHA_IJ[i, :i] @ K[:i]))
             n_f += 1
-        f_prev_arg, f_prev_val = arg, fi
-        G = sum((GAMMA_IJ[i, j] / GAMMA * ks[j] for j in range(i)), np.zeros_like(u))
-        F = fi + G
         if m > 0:
-            z = Q.T @ F
-            y = np.linalg.solve(L, z)
-            k = F - Q @ (z - y) - G
+            coupling = h * (H @ (GAMMA_IJ[i, :i] @ kappa[:i]))
+            proj = Q.T @ fi
+            kappa[i] = np.linalg.solve(stage_matrix, proj + coupling)
+            K[i] = Q @ kappa[i] + (fi - Q @ proj)
         else:
-            k = F - G
-        ks.append(k)
-    u_star = u + h * sum(B[j] * ks[j] for j in range(4))
-    u_hat = u + h * sum(BHAT[j] * ks[j] for j in range(4))
+            K[i] = fi
+    u_star = u + h * (B @ K)
+    u_hat = u + h * (BHAT @ K)
     return u_star, u_hat, n_f
 
 

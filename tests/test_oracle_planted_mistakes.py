@@ -1,17 +1,17 @@
 """Plant plausible mistakes in the oracle, one at a time, and check that the
-oracle's pins catch each one (CPU only; about ten minutes).
+oracle's pins catch each one (CPU only; about ten minutes in all).
 
-    python tests/plant_oracle_mistakes.py
+    python -m pytest tests/test_oracle_planted_mistakes.py --runslow -q
 
-Every entry replaces one line of an oracle module, runs the pin files that
-cover it with pytest, and restores the module (also on errors and Ctrl-C).
-A mistake is caught when some pin fails (or a pin exceeds its 60 s limit).
-The three entries marked ``equivalent`` change no result and are expected to
-survive.  The script exits non-zero if any other mistake survives or a
-pattern no longer matches the oracle's source.
+Each case copies the oracle, the input generators and the pin files into a
+fresh temporary directory, replaces one line of an oracle module there, and
+runs the pin files that cover it with pytest in a subprocess; the repository's
+own sources are never modified.  A mistake is caught when some pin fails (or a
+pin exceeds its 60 s limit).  The entries marked ``equivalent`` change no
+result and are expected to survive.  A pattern that no longer matches the
+oracle's source exactly once fails its case.
 
-Not collected by pytest (the name does not start with ``test_``): it runs the
-pin suite some sixty times.
+Marked ``slow``: skipped unless pytest runs with --runslow.
 """
 
 import os
@@ -19,6 +19,8 @@ import pathlib
 import shutil
 import subprocess
 import sys
+
+import pytest
 
 ROOT = pathlib.Path(__file__).resolve().parents[1]
 
@@ -65,20 +67,32 @@ MISTAKES = [
      KIN, "caught"),
     ("oracle/kinetics.py", "        dlnkf = (self.b + self.Ea_R / T) / T", "        dlnkf = (self.b - self.Ea_R / T) / T",
      KIN, "caught"),
-    # ROK4E: stages, projected solve, Arnoldi
-    ("oracle/rok4e.py", "    L = np.eye(m) - h * GAMMA * H", "    L = np.eye(m) + h * GAMMA * H", ROK, "caught"),
-    ("oracle/rok4e.py", "            k = F - Q @ (z - y) - G", "            k = F - Q @ (z - y) + G", ROK, "caught"),
-    ("oracle/rok4e.py", "        G = sum((GAMMA_IJ[i, j] / GAMMA * ks[j] for j in range(i)), np.zeros_like(u))",
-     "        G = sum((GAMMA_IJ[i, j] * ks[j] for j in range(i)), np.zeros_like(u))", ROK, "caught"),
-    ("oracle/rok4e.py", "            y = np.linalg.solve(L, z)", "            y = np.linalg.solve(L.T, z)", ROK, "caught"),
+    # ROK4E: stages (Krylov coordinates and complement), Arnoldi
+    ("oracle/rok4e.py", "    stage_matrix = np.eye(m) - h * GAMMA * H", "    stage_matrix = np.eye(m) + h * GAMMA * H",
+     ROK, "caught"),
+    ("oracle/rok4e.py", "            K[i] = Q @ kappa[i] + (fi - Q @ proj)", "            K[i] = Q @ kappa[i]", ROK,
+     "caught"),  # the orthogonal complement dropped
+    ("oracle/rok4e.py", "            coupling = h * (H @ (GAMMA_IJ[i, :i] @ kappa[:i]))",
+     "            coupling = (H @ (GAMMA_IJ[i, :i] @ kappa[:i]))", ROK, "caught"),  # no h on the A_n term
+    ("oracle/rok4e.py", "            coupling = h * (H @ (GAMMA_IJ[i, :i] @ kappa[:i]))",
+     "            coupling = h * (H @ (GAMMA_IJ[:i, i] @ kappa[:i]))", ROK, "caught"),  # transposed table
+    ("oracle/rok4e.py", "            coupling = h * (H @ (GAMMA_IJ[i, :i] @ kappa[:i]))",
+     "            coupling = h * (H.T @ (GAMMA_IJ[i, :i] @ kappa[:i]))", ROK, "caught"),
+    ("oracle/rok4e.py", "            kappa[i] = np.linalg.solve(stage_matrix, proj + coupling)",
+     "            kappa[i] = np.linalg.solve(stage_matrix.T, proj + coupling)", ROK, "caught"),
+    ("oracle/rok4e.py", "            fi = f(u + h * (ALPHA_IJ[i, :i] @ K[:i]))",
+     "            fi = f(u + h * (GAMMA_IJ[i, :i] @ K[:i]))", ROK, "caught"),
+    ("oracle/rok4e.py", "        if i > 0 and not np.array_equal(ALPHA_IJ[i], ALPHA_IJ[i - 1]):",
+     "        if i == 1:", ROK, "caught"),  # stage 3 reuses stage 2's f
+    ("oracle/rok4e.py", "        if i > 0 and not np.array_equal(ALPHA_IJ[i], ALPHA_IJ[i - 1]):",
+     "        if i > 0:", ROK, "caught"),  # a 4th f per attempt: the count pin (3 per attempt) fails
+    ("oracle/rok4e.py", "    u_star = u + h * (B @ K)", "    u_star = u + h * (B[:3] @ K[:3])", ROK, "caught"),
+    ("oracle/rok4e.py", "    u_hat = u + h * (BHAT @ K)", "    u_hat = u + h * (BHAT[:3] @ K[:3])", ROK,
+     "equivalent"),  # bhat_4 = 0
     ("oracle/rok4e.py", "                H[i, j] += hij", "                H[j, i] += hij", ROK, "caught"),
     ("oracle/rok4e.py", "        for _pass in range(2):", "        for _pass in range(1):", ROK, "caught"),
     ("oracle/rok4e.py", "        Q[:, j + 1] = w / hn", "        Q[:, j + 1] = w / w0", ROK, "caught"),
     ("oracle/rok4e.py", "        H[j + 1, j] = hn", "        H[j + 1, j] = 0.0", ROK, "caught"),
-    ("oracle/rok4e.py", "            fi = f_prev_val  # stage 4 shares stage 3's argument (alpha_4j = alpha_3j)",
-     "            fi = fn", ROK, "caught"),
-    ("oracle/rok4e.py", "    u_hat = u + h * sum(BHAT[j] * ks[j] for j in range(4))",
-     "    u_hat = u + h * sum(BHAT[j] * ks[j] for j in range(3))", ROK, "equivalent"),  # b^_4 = 0
     # ROK4E: error norm, controller, integration loop, finite-difference J v
     ("oracle/rok4e.py", "    return float(np.sqrt(np.mean(((u_hat - u_star) / sc) ** 2)))",
      "    return float(np.max(np.abs((u_hat - u_star) / sc)))", ROK, "caught"),
@@ -155,41 +169,30 @@ MISTAKES = [
 ]
 
 
-def run(tests):
-    # No bytecode: two mutants of equal length written within one second would
-    # otherwise share a cached .pyc (validated by mtime and size only).
-    shutil.rmtree(ROOT / "oracle" / "__pycache__", ignore_errors=True)
+COPY = ("oracle", "synth", "tests")
+
+
+def _run_in_copy(tmp, module, old, new, tests):
+    for d in COPY:
+        shutil.copytree(ROOT / d, tmp / d, ignore=shutil.ignore_patterns("__pycache__", "*.pyc"))
+    path = tmp / module
+    src = path.read_text()
+    assert src.count(old) == 1, f"pattern not found exactly once in {module}: {old.strip()[:70]}"
+    path.write_text(src.replace(old, new))
     env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1")
-    cmd = [sys.executable, "-B", "-m", "pytest", "-x", "-q", "-m", "not gpu", "-p", "no:cacheprovider", "--timeout=60"]
+    cmd = [sys.executable, "-B", "-m", "pytest", "-x", "-q", "-m", "not gpu and not slow", "-p", "no:cacheprovider",
+           "--timeout=60", *tests]
     try:
-        r = subprocess.run(cmd + tests, cwd=ROOT, capture_output=True, text=True, timeout=900, env=env)
+        r = subprocess.run(cmd, cwd=tmp, capture_output=True, text=True, timeout=900, env=env)
     except subprocess.TimeoutExpired:
         return "caught", "suite timeout"
     lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
     return ("caught" if r.returncode else "survived"), (lines[-1] if lines else "")
 
 
-def main():
-    bad = []
-    for module, old, new, tests, expected in MISTAKES:
-        path = ROOT / module
-        src = path.read_text()
-        if src.count(old) != 1:
-            bad.append((module, old, "pattern not found once"))
-            print(f"NO MATCH  {module}: {old.strip()[:70]}", flush=True)
-            continue
-        try:
-            path.write_text(src.replace(old, new))
-            outcome, last = run(tests)
-        finally:
-            path.write_text(src)
-        ok = (outcome == "caught") == (expected == "caught")
-        print(f"{'ok ' if ok else 'BAD'} {outcome:9s} {module}: {new.strip()[:70]} | {last[:60]}", flush=True)
-        if not ok:
-            bad.append((module, new, outcome))
-    print(f"{len(MISTAKES) - len(bad)} of {len(MISTAKES)} as expected")
-    return 1 if bad else 0
-
-
-if __name__ == "__main__":
-    sys.exit(main())
+@pytest.mark.slow
+@pytest.mark.parametrize("module,old,new,tests,expected", MISTAKES,
+                         ids=[f"{i:02d}-{m[0].split('/')[-1][:-3]}" for i, m in enumerate(MISTAKES)])
+def test_planted_mistake(tmp_path, module, old, new, tests, expected):
+    outcome, last = _run_in_copy(tmp_path, module, old, new, tests)
+    assert outcome == ("caught" if expected == "caught" else "survived"), (new.strip(), last)
