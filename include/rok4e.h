@@ -307,12 +307,18 @@ int rk_simpler_split_step(const rk_mech* mech, double* U, double* h_cell, int64_
  * library routine.  Its scratch (the transport term T(U_n), two SSP-RK3 stage
  * buffers and the work-queue counter) lives in one static device array of
  * RK_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until the
- * process exits; npts x (n_species + 1) must fit in it (about 174,000 values:
- * 2048 points of a 30-species mechanism use 63,488), else the call returns
- * RK_E_UNSUPPORTED with the limit in rk_last_error.
- *  - The first call on a device looks the array's device address up (once per
- *    device, with that device current); make that first call before any stream
- *    capture.
+ * process exits.  The call needs rk_simpler_split_step_workspace_size(mech,
+ * npts, ...) <= RK_NOALLOC_SCRATCH_BYTES, about 24 (n_species + 1) + 4 bytes
+ * per point: at most 5,605 points of a 30-species mechanism (2048 use 1.53 MB)
+ * or 3,225 of a 53-species one.  Beyond that it launches nothing and returns
+ * RK_E_UNSUPPORTED, with the largest npts that fits this mechanism in
+ * rk_last_error.
+ *  - The array's device address is looked up with the device current and
+ *    cached per device with the ID of its CUDA context.  The first call in a
+ *    context -- on each device, and again after cudaDeviceReset or after the
+ *    primary context was released and created anew -- does this lookup; make
+ *    it before any stream capture (inside a capture such a call returns
+ *    RK_E_UNSUPPORTED instead).
  *  - Every call on a device shares the one array and finds the previous call's
  *    contents there (the parts that must start from zero are cleared by the
  *    call).  Calls that overlap on the GPU -- on different streams, or from

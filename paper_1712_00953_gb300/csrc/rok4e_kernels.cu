@@ -21,6 +21,7 @@
 //    one per reaction), falling back to one exponential per reaction when a
 //    species has |g/RT| > 170 (where a product of four factors could overflow);
 //  * w = nu^T q is a gather over a species-major list (deterministic order).
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -2853,26 +2854,88 @@ int rk_split_step(const rk_mech* mech, double* U, double* h_cell, int64_t npts, 
 // Scratch for rk_simpler_split_step_noalloc: a fixed array in device memory that
 // every GPU loading this library reserves until the process exits.  Host code
 // may not pass the symbol itself to a kernel (on the host it names a host-side
-// placeholder), so its device address is looked up once per device with
-// cudaGetSymbolAddress, with that device current, and cached.
+// placeholder), so its device address is looked up with cudaGetSymbolAddress,
+// with the device current, and cached per device together with the ID of the
+// CUDA context it belongs to.  A later call in another context of that device
+// (after cudaDeviceReset, or once the primary context was released and made
+// again, when the module -- and the array -- can sit at another address) looks
+// the address up again; inside a stream capture it refuses instead, since the
+// lookup may have to load the module.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[RK_NOALLOC_SCRATCH_BYTES];
 static std::mutex g_noalloc_mu;
-static void* g_noalloc_ptr[256] = {nullptr};
+struct NoallocEntry {
+  unsigned long long ctx_id;
+  void* ptr;
+};
+static NoallocEntry g_noalloc[256] = {};
 
-static int noalloc_scratch(void** out) {
+typedef CUresult (*PFN_ctx_get_current)(CUcontext*);
+typedef CUresult (*PFN_ctx_get_id)(CUcontext, unsigned long long*);
+
+// ID of the calling thread's current CUDA context, through the driver entry
+// points the runtime hands out (no link against the driver library).
+static int current_ctx_id(unsigned long long* id) {
+  static PFN_ctx_get_current get_current = nullptr;
+  static PFN_ctx_get_id get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+    if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDriverEntryPointByVersion");
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return set_error(RK_E_CUDA, "the driver does not provide cuCtxGetCurrent / cuCtxGetId");
+    get_current = reinterpret_cast<PFN_ctx_get_current>(f1);
+    get_id = reinterpret_cast<PFN_ctx_get_id>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return set_error(RK_E_CUDA, "no current CUDA context");
+  if (get_id(ctx, id) != CUDA_SUCCESS) return set_error(RK_E_CUDA, "cuCtxGetId failed");
+  return RK_OK;
+}
+
+static int noalloc_scratch(cudaStream_t stream, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
   if (dev < 0 || dev >= 256) return set_error(RK_E_UNSUPPORTED, "device ordinal out of range");
+  // also makes the device's context current on this thread (runtime initialisation)
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(stream, &cap);
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamIsCapturing");
+  unsigned long long id = 0;
+  int rc = current_ctx_id(&id);
+  if (rc) return rc;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  NoallocEntry& ent = g_noalloc[dev];
+  if (!ent.ptr || ent.ctx_id != id) {
+    if (cap != cudaStreamCaptureStatusNone)
+      return set_error(RK_E_UNSUPPORTED,
+                       "rk_simpler_split_step_noalloc: the first call in a CUDA context must come before any "
+                       "stream capture (it looks up the static scratch's device address)");
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress");
-    g_noalloc_ptr[dev] = ptr;
+    ent.ptr = ptr;
+    ent.ctx_id = id;
   }
-  *out = g_noalloc_ptr[dev];
+  *out = ent.ptr;
   return RK_OK;
+}
+
+// Largest npts whose split-step scratch fits the static array (the workspace
+// size grows with npts, so bisection finds it exactly).
+static int64_t noalloc_max_points(const rk_mech* mech, int32_t krylov_dim, const rk_opts* opts) {
+  int64_t lo = 0, hi = (int64_t)RK_NOALLOC_SCRATCH_BYTES;  // need(hi) > the array: > 8 bytes per point
+  while (hi - lo > 1) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    if (rk_simpler_split_step_workspace_size(mech, mid, krylov_dim, opts) <= (size_t)RK_NOALLOC_SCRATCH_BYTES)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
 }
 
 int rk_simpler_split_step_noalloc(const rk_mech* mech, double* U, double* h_cell, int64_t npts, double p, double dt,
@@ -2885,16 +2948,16 @@ int rk_simpler_split_step_noalloc(const rk_mech* mech, double* U, double* h_cell
   if (npts < 0) return set_error(RK_E_INVALID_ARGUMENT, "npts < 0");
   const size_t need = rk_simpler_split_step_workspace_size(mech, npts, krylov_dim, opts);
   if (need > (size_t)RK_NOALLOC_SCRATCH_BYTES) {
-    char msg[256];
+    char msg[320];
     snprintf(msg, sizeof(msg),
-             "npts x (n_species + 1) = %lld values needs %zu bytes of scratch; the static scratch holds %zu "
-             "(at most %zu values): use rk_simpler_split_step with a workspace",
-             (long long)(npts * (mech->host.L.ns + 1)), need, (size_t)RK_NOALLOC_SCRATCH_BYTES,
-             (size_t)((RK_NOALLOC_SCRATCH_BYTES - 512 - 256 * 3) / (3 * sizeof(double))));
+             "npts = %lld (x %d values) needs %zu bytes of scratch; the static scratch holds %zu bytes, "
+             "at most %lld points of this mechanism: use rk_simpler_split_step with a workspace",
+             (long long)npts, mech->host.L.ns + 1, need, (size_t)RK_NOALLOC_SCRATCH_BYTES,
+             (long long)noalloc_max_points(mech, krylov_dim, opts));
     return set_error(RK_E_UNSUPPORTED, msg);
   }
   void* scratch = nullptr;
-  rc = noalloc_scratch(&scratch);
+  rc = noalloc_scratch((cudaStream_t)stream, &scratch);
   if (rc) return rc;
   return rk_simpler_split_step(mech, U, h_cell, npts, p, dt, D, dx, rtol, atol, krylov_dim, opts, stats, scratch,
                                (size_t)RK_NOALLOC_SCRATCH_BYTES, stream);
