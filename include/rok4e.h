@@ -148,11 +148,14 @@ int rk_chem_rhs_cv(const rk_mech* mech, const double* Y, const double* src, cons
 int rk_chem_jvp_cv(const rk_mech* mech, const double* Y, const double* V, const double* rho_cell,
                    double* JV, int64_t ncell, int32_t mode, void* stream);
 
-/* Mixed-precision source term: as rk_chem_rhs, with w = nu^T q in FP32 while
- * the rate coefficients, Gibbs factors, 1/Kc, the rates of progress
- * q = m (k prod C - k/Kc prod C), the heat release sum_j q_j Delta H_j and the
- * assembly of f stay FP64 (the right-hand side the mixed-precision integrator
- * uses). */
+/* Mixed-precision source term (the right-hand side of precision levels 1 and
+ * 2): as rk_chem_rhs, with w = nu^T q gathered on the FP32 pipe in
+ * double-float (FP32 pairs, ~44-bit significands; the small-integer net
+ * coefficients are exact in FP32) and the exponentials' polynomial tails in
+ * FP32 (~1e-12 relative), while the rate coefficients, Gibbs factors, 1/Kc, the
+ * rates of progress q = m (k prod C - k/Kc prod C) and the assembly of f stay
+ * FP64.  Needs |q_j| below the FP32 range (3.4e38 mol/m^3/s); rates below
+ * 1.2e-38 drop out of w. */
 int rk_chem_rhs_mixed(const rk_mech* mech, const double* Y, const double* src, double p,
                       double* dYdt, int64_t ncell, void* stream);
 
@@ -167,12 +170,17 @@ typedef struct rk_opts {
   double h0;              /* first step when h_cell is NULL or holds <= 0; <= 0: dt */
   double fixed_h;         /* > 0: fixed steps of this size, no error control */
   int32_t trace_cap;      /* attempts recorded per cell into trace (0: none) */
-  int32_t precision;      /* 0: FP64 throughout (default).  1: mixed -- w = nu^T q and
-                             the Arnoldi inner products in FP32; rate coefficients,
-                             Gibbs factors, 1/Kc, rates of progress, heat release,
-                             Jacobian-vector products, stage solves, error norm and
-                             state update in FP64.  2: as 1 with the
-                             Jacobian-vector products in FP32 as well.  3: FP64
+  int32_t precision;      /* 0: FP64 throughout (default).  1: mixed -- w = nu^T q (in
+                             the right-hand side and the Jacobian-vector product)
+                             gathered in double-float on the FP32 pipe, the first
+                             Gram-Schmidt pass of Arnoldi with FP32 inner products
+                             (the reorthogonalisation pass and the norms FP64),
+                             the exponentials' polynomial tails in FP32; rate
+                             coefficients, Gibbs factors, 1/Kc, rates of progress,
+                             stage solves, error norm and state update in FP64.
+                             2: as 1 with the Jacobian-vector products in FP32
+                             (~1e-5 relative: does not keep the 1e-6 K bar
+                             against the FP64 oracle).  3: FP64
                              Arnoldi, stages, norm and update; the exponentials'
                              polynomial tails in FP32 (~1e-12 relative); the
                              Jacobian-vector product's reaction-level core
@@ -180,7 +188,9 @@ typedef struct rk_opts {
                              pairs, ~44-bit significands) on the FP32 pipe */
   double* trace;          /* device [ncell x trace_cap]: +h accepted, -h rejected, 0 unused */
   void* ev_begin;         /* optional cudaEvent_t recorded on the stream right before the */
-  void* ev_end;           /* integration kernel and right after it (timing hook), or NULL */
+  void* ev_end;           /* integration kernel and right after it (timing hook), or NULL;
+                             inside a stream capture they are recorded as external
+                             event-record nodes, so each replay of the graph records them */
   int32_t queue_order;    /* 0 auto (1 without h_cell, 3 with it), 1 interleaved cell
                              index, 2 longest expected first (dt / h_cell), 3 static
                              balanced bins: the longest-first queue dealt in snake
@@ -350,6 +360,31 @@ int rk_split_step(const rk_mech* mech, double* U, double* h_cell, int64_t npts, 
 /* Transport operator alone: TU = D d^2U/dx^2 (same discretisation). */
 int rk_diffusion_1d(const double* U, double* TU, int64_t npts, int32_t nvar, double D, double dx,
                     void* stream);
+
+/* The transport of one slice of the 1-D domain, for a domain split over ranks
+ * (the paper's 3-D runs decompose the domain over processes, Sec. 5; the
+ * transport's three-point stencil needs one neighbour point per side).  The
+ * slice's npts points are held with one ghost row on each side: Uext / Xext
+ * are device [(npts + 2) x nvar], row r + 1 holding the slice's point r, row 0
+ * and row npts + 1 the neighbouring slices' end points -- or, at an end of
+ * the whole domain, a copy of the slice's own end point, which is the
+ * zero-gradient boundary.  With the ghost rows filled so, both calls give the
+ * same bits at every point as rk_diffusion_1d and the SSP-RK3 stages inside
+ * rk_simpler_split_step on the whole domain.
+ *  rk_diffusion_1d_ghost: TU [npts x nvar] = D d^2U/dx^2; TU must not overlap
+ *    Uext.
+ *  rk_ssprk3_stage_ghost: one stage of the SSP-RK3 step (Shu-Osher form) of
+ *    dU/dt = D d^2U/dx^2 + sigma S over k: stage 0 Out = X + k g(X); stage 1
+ *    Out = 3/4 U1 + 1/4 (X + k g(X)); stage 2 Out = 1/3 U1 + 2/3 (X + k g(X)),
+ *    g(X) = D d^2X/dx^2 + sigma S, X from Xext; U1, S (nullable) and Out are
+ *    [npts x nvar]; Out may be U1, not Xext.  The Simpler correction of
+ *    Eq. simpler_balanced is sigma = -1, S = T(U_n), k = dt / 2.
+ * Returns RK_E_INVALID_ARGUMENT for bad sizes, a null array, an overlap or
+ * dx <= 0 (nothing launched), RK_E_CUDA if the launch fails. */
+int rk_diffusion_1d_ghost(const double* Uext, double* TU, int64_t npts, int32_t nvar, double D, double dx,
+                          void* stream);
+int rk_ssprk3_stage_ghost(int32_t stage, const double* U1, const double* Xext, const double* S, double sigma,
+                          double* Out, int64_t npts, int32_t nvar, double D, double dx, double k, void* stream);
 
 /* ---- fixed-step integration with checkpoints and its adjoint ----------------
  * nsteps fixed ROK4E steps of size h (Algorithm 1 with h held fixed: no error

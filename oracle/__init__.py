@@ -10,6 +10,8 @@ Modules:
   kinetics   constant-pressure reactor RHS f(u) and its dense Jacobian
   rok4e      Arnoldi, one ROK4E attempt, Algorithm 1 with PI control
   splitting  Strang / balanced / Simpler steps, scalar recurrences, 1-D case
+  c_oracle   the same method compiled from C (oracle/c/), pinned against the
+             modules above; for long horizons and the timed CPU baseline
 """
 
 from . import kinetics, rok4e, splitting  # noqa: F401

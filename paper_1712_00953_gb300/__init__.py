@@ -30,8 +30,9 @@ def _L():
 __all__ = ["Mechanism", "mech_load", "mech_validate", "chem_rhs", "chem_rhs_mixed", "chem_rhs_cv", "chem_jvp_cv",
            "chem_jvp", "rok4e_integrate", "rkdp_integrate", "chem_rhs_aux", "chem_jvp_aux", "AUX_EXTRA",
            "rok4e_workspace_size", "simpler_split_step", "simpler_split_step_workspace_size",
-           "diffusion_1d", "probe_throughput", "eval_exp", "split_step", "SCHEMES", "rok4e_fixed_steps",
-           "rok4e_adjoint", "FixedStepROK4E", "Opts", "RokError", "STATS_FIELDS"]
+           "diffusion_1d", "diffusion_1d_ghost", "ssprk3_stage_ghost", "GhostTransport",
+           "simpler_split_step_phases", "halo_exchange", "simpler_split_step_sharded", "probe_throughput", "eval_exp", "split_step", "SCHEMES", "rok4e_fixed_steps",
+           "rok4e_adjoint", "rok4e_adjoint_workspace_size", "FixedStepROK4E", "Opts", "RokError", "STATS_FIELDS"]
 
 STATS_FIELDS = ("n_accept", "n_reject", "n_rhs", "status")
 
@@ -315,6 +316,122 @@ def diffusion_1d(U, D, dx, out=None, stream=None):
     return out
 
 
+def diffusion_1d_ghost(Uext, D, dx, out=None, stream=None):
+    """D d^2U/dx^2 on the n interior rows of Uext [n + 2, nvar] (rows 0 and
+    n + 1 are ghost rows): rk_diffusion_1d_ghost."""
+    n = int(Uext.shape[0]) - 2
+    out = torch.empty((n, Uext.shape[1]), dtype=torch.float64, device=Uext.device) if out is None else out
+    _check(_L().rk_diffusion_1d_ghost(_dptr(Uext, "Uext"), _dptr(out, "out", n * Uext.shape[1]), n,
+                                      int(Uext.shape[1]), float(D), float(dx), _stream_ptr(stream)),
+           "rk_diffusion_1d_ghost")
+    return out
+
+
+def ssprk3_stage_ghost(stage, U1, Xext, S, sigma, out, D, dx, k, stream=None):
+    """One SSP-RK3 stage on a slice held with ghost rows (rk_ssprk3_stage_ghost)."""
+    n = int(Xext.shape[0]) - 2
+    nv = int(Xext.shape[1])
+    _check(_L().rk_ssprk3_stage_ghost(int(stage), _dptr(U1, "U1", n * nv), _dptr(Xext, "Xext"),
+                                      _dptr(S, "S", n * nv), float(sigma), _dptr(out, "out", n * nv), n, nv,
+                                      float(D), float(dx), float(k), _stream_ptr(stream)), "rk_ssprk3_stage_ghost")
+    return out
+
+
+class GhostTransport:
+    """The library's ghost-row transport kernels: the backend of
+    simpler_split_step_phases on a CUDA device."""
+
+    def __init__(self, stream=None):
+        self.stream = stream
+
+    def diffusion(self, Xext, D, dx):
+        return diffusion_1d_ghost(Xext, D, dx, stream=self.stream)
+
+    def stage(self, stage, U1, Xext, S, sigma, out, D, dx, k):
+        ssprk3_stage_ghost(stage, U1, Xext, S, sigma, out, D, dx, k, stream=self.stream)
+
+    def empty_like(self, t):
+        return torch.empty_like(t)
+
+
+def simpler_split_step_phases(react, backend, Uext, dt, D, dx):
+    """One Simpler balanced split step (Eq. simpler_balanced) of a slice of the
+    1-D domain held with one ghost row per side (Uext [n + 2, nvar], the
+    slice's points in rows 1..n, updated in place), as a generator: before
+    each of the four transport evaluations it yields the array whose ghost
+    rows the caller must fill (halo_exchange) -- U_n for T(U_n), then the
+    state after the reaction sub-step and the two intermediate SSP-RK3 stages.
+    react(U, Tn) integrates the slice's points over dt with the constant
+    source Tn = T(U_n); backend supplies diffusion / stage / empty_like."""
+    n = int(Uext.shape[0]) - 2
+    U = Uext[1:n + 1]
+    yield Uext
+    Tn = backend.diffusion(Uext, D, dx)
+    react(U, Tn)
+    yield Uext
+    V1, V2 = backend.empty_like(Uext), backend.empty_like(Uext)
+    k = 0.5 * dt
+    backend.stage(0, U, Uext, Tn, -1.0, V1[1:n + 1], D, dx, k)
+    yield V1
+    backend.stage(1, U, V1, Tn, -1.0, V2[1:n + 1], D, dx, k)
+    yield V2
+    backend.stage(2, U, V2, Tn, -1.0, U, D, dx, k)
+
+
+def halo_exchange(ext, rank, world, group=None):
+    """Fill the ghost rows of ext [n + 2, nvar] for a domain split into
+    contiguous slices over ranks 0..world-1 in order: row 0 from rank - 1's
+    last point, row n + 1 from rank + 1's first point (torch.distributed
+    point-to-point sends and receives: NCCL for CUDA tensors, gloo on the
+    CPU); at an end of the whole domain, a copy of the slice's own end point
+    (zero-gradient boundary)."""
+    n = int(ext.shape[0]) - 2
+    ops = []
+    if world > 1:
+        import torch.distributed as dist
+
+        if rank > 0:
+            ops += [dist.P2POp(dist.isend, ext[1], rank - 1, group), dist.P2POp(dist.irecv, ext[0], rank - 1, group)]
+        if rank < world - 1:
+            ops += [dist.P2POp(dist.isend, ext[n], rank + 1, group),
+                    dist.P2POp(dist.irecv, ext[n + 1], rank + 1, group)]
+        if ops:
+            for req in dist.batch_isend_irecv(ops):
+                req.wait()
+    if rank == 0:
+        ext[0].copy_(ext[1])
+    if rank == world - 1:
+        ext[n + 1].copy_(ext[n])
+    return ext
+
+
+def simpler_split_step_sharded(m: Mechanism, Uext, dt, D, dx, rtol, atol, krylov_dim=4, *, rank=0, world=1,
+                               group=None, p=101325.0, h_cell=None, opts: Opts | None = None, stats=None,
+                               workspace=None, stream=None):
+    """One Simpler split step of this rank's slice of the 1-D domain (Uext [n +
+    2, nvar] with ghost rows, updated in place), exchanging one-point halos
+    with the neighbouring ranks before each of the four transport evaluations.
+    With every rank's slice the result is bitwise that of simpler_split_step
+    on the whole domain."""
+    import contextlib
+
+    n = int(Uext.shape[0]) - 2
+    if workspace is None:
+        workspace = torch.empty(rok4e_workspace_size(m, n, krylov_dim, opts), dtype=torch.uint8,
+                                device=Uext.device)
+
+    def react(U, Tn):
+        rok4e_integrate(m, U, dt, rtol, atol, krylov_dim, p=p, src=Tn, h_cell=h_cell, opts=opts, stats=stats,
+                        workspace=workspace)
+
+    # kernels, ghost copies and the communication all on one stream (the
+    # given one made current, else the current one)
+    with torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext():
+        for ext in simpler_split_step_phases(react, GhostTransport(), Uext, dt, D, dx):
+            halo_exchange(ext, rank, world, group)
+    return Uext
+
+
 def eval_exp(x, which=0, out=None, stream=None):
     """The kernels' own elementary functions on a CUDA float64 tensor (0: exp(x), 1/2: exp(+-x)
     pair; 3/4/5: the same in the mixed-precision form; 6: ln x; 7: 1/x)."""
@@ -338,13 +455,17 @@ def rok4e_fixed_steps(m: Mechanism, Y, h, nsteps, krylov_dim=4, *, p=101325.0, c
     return Y
 
 
+def rok4e_adjoint_workspace_size(m: Mechanism, ncell: int, krylov_dim: int) -> int:
+    return int(_L().rk_rok4e_adjoint_workspace_size(m.handle, int(ncell), int(krylov_dim)))
+
+
 def rok4e_adjoint(m: Mechanism, checkpoints, ubar, h, nsteps, krylov_dim=4, *, p=101325.0, grad_u0=None,
                   workspace=None, stream=None):
     """Discrete adjoint of rok4e_fixed_steps: returns (grad_lnA [Nr], grad_u0 [ncell, N] or None)."""
     n = _ncell(ubar, m)
     if workspace is None:
-        nb = int(_L().rk_rok4e_adjoint_workspace_size(m.handle, n, int(krylov_dim)))
-        workspace = torch.empty(nb, dtype=torch.uint8, device=ubar.device)
+        workspace = torch.empty(rok4e_adjoint_workspace_size(m, n, krylov_dim), dtype=torch.uint8,
+                                device=ubar.device)
     grad = torch.empty(m.n_reactions, dtype=torch.float64, device=ubar.device)
     _check(_L().rk_rok4e_adjoint(m.handle, _dptr(checkpoints, "checkpoints", (int(nsteps) + 1) * ubar.numel()),
                                  _dptr(ubar, "ubar"), n, float(p), float(h), int(nsteps), int(krylov_dim),

@@ -108,6 +108,11 @@ SIGNATURES = {
                                         ctypes.c_void_p]),
     "rk_diffusion_1d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_void_p]),
+    "rk_diffusion_1d_ghost": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_void_p]),
+    "rk_ssprk3_stage_ghost": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_double, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_void_p]),
     "rk_probe_throughput": (ctypes.c_int, [ctypes.c_int32, c_double_p]),
     "rk_eval_exp": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                    ctypes.c_void_p]),

@@ -593,6 +593,27 @@ __device__ __forceinline__ T piece_sum(const MechView& m, const T* part, int k) 
   return acc;
 }
 
+// The same gather in double-float (FP32 pairs, ~44-bit significands, on the
+// FP32 pipe): the net coefficients are small integers, exact in FP32, so each
+// product nu_e q_j is formed with the pair's precision and summed by two-sums.
+template <int G>
+__device__ __forceinline__ void gather_pieces_df(const MechView& m, int lane, const df2* __restrict__ q,
+                                                 df2* part) {
+  for (int p = lane; p < m.npiece; p += G) {
+    df2 acc = {0.0f, 0.0f};
+    const int e1 = m.piece_ptr[p + 1];
+    for (int e = m.piece_ptr[p]; e < e1; ++e) acc = df_add(acc, df_scale(m.csr_nuf[e], q[m.csr_j[e]]));
+    part[p] = acc;
+  }
+}
+__device__ __forceinline__ double piece_sum_df(const MechView& m, const df2* part, int k) {
+  const int p1 = m.spec_piece[k + 1];
+  int p = m.spec_piece[k];
+  df2 acc = part[p];
+  for (++p; p < p1; ++p) acc = df_add(acc, part[p]);
+  return df_to(acc);
+}
+
 // ------------------------------------------------------------ chemistry RHS
 // out = f(uu) + src (src may be null).  p > 0: constant-pressure reactor at
 // pressure p; p < 0: constant-volume reactor of density -p (Eq. cv_reactor with
@@ -779,7 +800,6 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
   const double invRTp = PREF_OVER_R * invT;
   const double lnRTp = LN_R_OVER_PREF + lnT;
   const double m_lnRTp = -lnRTp;
-  double shq = 0.0;  // mixed mode: heat release sum_j q_j Delta H_j / RT in FP64
   for (int j = g.lane; j < m.nr; j += G) {
     const uint32_t sl = m.slots[j];
     const int ra = sl & 255, rb = (sl >> 8) & 255, pa = (sl >> 16) & 255, pb = sl >> 24;
@@ -843,12 +863,8 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
     }
     const double kr = k * rfac;
     const double qj = mfac * fma(k, Pf, -__dmul_rn(kr, Pb));
-    s.q[j] = qj;
-    if (MIXED) {
-      s.fq[j] = __double2float_rn(qj);
-      const double dnud = dnu > 0 ? 1.0 : (dnu < 0 ? -1.0 : 0.0);
-      shq = fma(qj, fma(-esh, dnud, s.hRT[pa] + s.hRT[pb] - s.hRT[ra] - s.hRT[rb]), shq);
-    }
+    if (MIXED) reinterpret_cast<df2*>(s.q)[j] = df_from(qj);  // double-float copy for the gather
+    else s.q[j] = qj;
     if (cache) {
       // d q_j / dT at fixed concentrations (without the third-body factor):
       // k Pf d ln k/dT - kr Pb (d ln k/dT - d ln Kc/dT), with
@@ -873,17 +889,16 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
   }
   g.sync();
   // species pass 2: w = nu^T q, dY/dt and the sums of the temperature equation
-  double Sh = MIXED ? shq : 0.0, cb = 0.0;
+  double Sh = 0.0, cb = 0.0;
   double Ax = 0.0, Bx = 0.0;  // auxiliary T: sum (u_k/RT) F_k / W_k and sum (cv_k/R) F_k / W_k
-  if (MIXED) gather_pieces<G, float>(m, g.lane, m.csr_nuf, s.fq, s.fpart);  // FP32 (q formed in FP64)
+  if (MIXED) gather_pieces_df<G>(m, g.lane, reinterpret_cast<const df2*>(s.q), reinterpret_cast<df2*>(s.part));
   else gather_pieces<G, double>(m, g.lane, m.csr_nu, s.q, s.part);
   g.sync();
   for (int k = g.lane; k < ns; k += G) {
     double om;
     if (MIXED) {
-      const float omf = piece_sum(m, s.fpart, k);
-      om = (double)omf;
-      if (cache) s.fom[k] = omf;
+      om = piece_sum_df(m, reinterpret_cast<const df2*>(s.part), k);
+      if (cache) s.fom[k] = __double2float_rn(om);
     } else {
       om = piece_sum(m, s.part, k);
     }
@@ -891,7 +906,7 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
     const double r = __dmul_rn(__dmul_rn(m.W[k], om), invrho);
     const double Fk = src ? __dadd_rn(r, src[k]) : r;
     out[k] = Fk;
-    if (!MIXED) Sh = fma(s.hRT[k] - esh, om, Sh);
+    Sh = fma(s.hRT[k] - esh, om, Sh);
     cb = fma(uu[k] * (s.cp[k] - esh), m.invW[k], cb);
     if (aux) {
       Ax = fma((s.hRT[k] - 1.0) * Fk, m.invW[k], Ax);
@@ -991,7 +1006,7 @@ __device__ __forceinline__ void rhs_dispatch(const MechView& m, const SlotPtrs& 
 // the last rhs_eval(..., cache = true) at u_n.  v, out: N-vectors.  Inlined
 // (unlike rhs_eval, nothing requires two call sites to produce the same bits),
 // which saves the call's register save and restore four times per attempt.
-template <int G>
+template <int G, bool DFG = false>
 __device__ __forceinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, const double* uu,
                                       const CellScalars& cs, const double* v, double* out) {
   const Grp<G> g;
@@ -1044,14 +1059,16 @@ __device__ __forceinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, c
       if (kind == 1) dq = t[0] * dq + dM * (k * Pf - kr * Pb);
       else dq = dq + t[1] * dM * (Pf - t[3] * Pb);
     }
-    s.q[j] = dq;
+    if (DFG) reinterpret_cast<df2*>(s.q)[j] = df_from(dq);
+    else s.q[j] = dq;
   }
   g.sync();
-  gather_pieces<G, double>(m, g.lane, m.csr_nu, s.q, s.part);
+  if (DFG) gather_pieces_df<G>(m, g.lane, reinterpret_cast<const df2*>(s.q), reinterpret_cast<df2*>(s.part));
+  else gather_pieces<G, double>(m, g.lane, m.csr_nu, s.q, s.part);
   g.sync();
   double dSh = 0.0, dcb = 0.0;
   for (int k = g.lane; k < ns; k += G) {
-    const double dom = piece_sum(m, s.part, k);
+    const double dom = DFG ? piece_sum_df(m, reinterpret_cast<const df2*>(s.part), k) : piece_sum(m, s.part, k);
     out[k] = s.Einv[k] * fma(-s.om[k], drr, dom);  // Einv: W_k / rho
     dSh = fma(s.gRT[k], dom, fma(s.hRT[k], vT, dSh));
     dcb = fma(s.dcp[k], vT, fma(s.cp[k], v[k], dcb));
@@ -1160,21 +1177,11 @@ __device__ __forceinline__ void jvp_eval_df(const MechView& m, const SlotPtrs& s
     dq2[j] = dq;
   }
   g.sync();
-  df2* part2 = reinterpret_cast<df2*>(s.part);
-  for (int p = g.lane; p < m.npiece; p += G) {
-    df2 acc = {0.0f, 0.0f};
-    const int e1 = m.piece_ptr[p + 1];
-    for (int e = m.piece_ptr[p]; e < e1; ++e) acc = df_add(acc, df_scale(m.csr_nuf[e], dq2[m.csr_j[e]]));
-    part2[p] = acc;
-  }
+  gather_pieces_df<G>(m, g.lane, dq2, reinterpret_cast<df2*>(s.part));
   g.sync();
   double dSh = 0.0, dcb = 0.0;
   for (int k = g.lane; k < ns; k += G) {
-    const int p1 = m.spec_piece[k + 1];
-    int p = m.spec_piece[k];
-    df2 acc = part2[p];
-    for (++p; p < p1; ++p) acc = df_add(acc, part2[p]);
-    const double dom = df_to(acc);
+    const double dom = piece_sum_df(m, reinterpret_cast<const df2*>(s.part), k);
     out[k] = s.Einv[k] * fma(-s.om[k], drr, dom);  // Einv: W_k / rho
     dSh = fma(s.gRT[k], dom, fma(s.hRT[k], vT, dSh));
     dcb = fma(s.dcp[k], vT, fma(s.cp[k], v[k], dcb));
@@ -1297,7 +1304,7 @@ __device__ inline void apply_jv(const MechView& m, const SlotPtrs& s, const Cell
   if (jv_mode == 0) {
     if (MIXED && fp32_jv) jvp_eval_f32<G>(m, s, s.u, cs, v, out);
     else if (!MIXED && cs.prec == 3) jvp_eval_df<G>(m, s, s.u, cs, v, out);
-    else jvp_eval<G>(m, s, s.u, cs, v, out);
+    else jvp_eval<G, MIXED>(m, s, s.u, cs, v, out);
     return;
   }
   const double nv = sqrt(group_dot<G>(g, v, v, N));
@@ -1327,9 +1334,11 @@ __device__ inline float group_dot_f(const Grp<G>& g, const double* a, const doub
 
 // Arnoldi with classical Gram-Schmidt and one reorthogonalisation pass on
 // K_M(J_n, f_n) (Sec. 4.1).  Returns the dimension m <= M; Q and H in the slot.
-// MIXED: the inner products and norms run in FP32 (the vector updates stay
-// FP64); the breakdown test then uses 1e-5 instead of 1e-12, the level below
-// which an FP32 residual norm is rounding noise.
+// MIXED: the first Gram-Schmidt pass takes its inner products in FP32 (from
+// the FP32 copy of Q); the reorthogonalisation pass, which removes what the
+// first pass left behind -- its FP32 rounding included -- and the norms stay
+// FP64, so the basis and H keep FP64 quality (mixed-precision "twice is
+// enough").
 template <int G, bool MIXED = false>
 __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& cs, int M, int jv_mode,
                        double p, int* n_rhs, bool fp32_jv = false) {
@@ -1339,7 +1348,7 @@ __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& 
   if (M > N) M = N;
   for (int i = g.lane; i < MAXM * MAXM; i += G) s.H[i] = 0.0;
   // squared norms; 1/||.|| from one reciprocal square root
-  const double beta2 = MIXED ? (double)group_dot_f<G>(g, s.fn, s.fn, N) : group_dot<G>(g, s.fn, s.fn, N);
+  const double beta2 = group_dot<G>(g, s.fn, s.fn, N);
   if (M <= 0 || !(beta2 > 0.0) || !isfinite(beta2)) {
     g.sync();
     return 0;
@@ -1353,18 +1362,18 @@ __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& 
     if (MIXED) s.fQ[e] = __double2float_rn(qe);
   }
   g.sync();
-  constexpr double brk = MIXED ? 1e-5 : BREAKDOWN_TOL;
-  constexpr double brk2 = brk * brk;  // breakdown ||w_after|| <= brk ||w_before||, on squares
+  constexpr double brk2 = BREAKDOWN_TOL * BREAKDOWN_TOL;  // breakdown ||w_after|| <= tol ||w_before||, on squares
   int mdim = M;
   for (int j = 0; j < M; ++j) {
     apply_jv<G, MIXED>(m, s, cs, jv_mode, p, unorm, s.Q + j * Nq, s.w, n_rhs, fp32_jv);
+    // (only the breakdown threshold reads ||J q_j||^2: FP32 is enough there)
     const double w02 = MIXED ? (double)group_dot_f<G>(g, s.w, s.w, N) : group_dot<G>(g, s.w, s.w, N);
     double hcol[MAXM];
 #pragma unroll
     for (int i = 0; i < MAXM; ++i) hcol[i] = 0.0;
     for (int pass = 0; pass < 2; ++pass) {
       double hp[MAXM];
-      if (MIXED) {
+      if (MIXED && pass == 0) {
         float part[MAXM];
 #pragma unroll
         for (int i = 0; i < MAXM; ++i) part[i] = 0.f;
@@ -1398,7 +1407,7 @@ __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& 
 #pragma unroll
       for (int i = 0; i < MAXM; ++i) hcol[i] += hp[i];
     }
-    const double hn2 = MIXED ? (double)group_dot_f<G>(g, s.w, s.w, N) : group_dot<G>(g, s.w, s.w, N);
+    const double hn2 = group_dot<G>(g, s.w, s.w, N);
     if (g.lane == 0) {
 #pragma unroll
       for (int i = 0; i < MAXM; ++i)
@@ -2188,10 +2197,26 @@ __global__ void __launch_bounds__(MAX_BLOCK_THREADS) chem_point_kernel(PointPara
 
 // ---------------------------------------------------------- 1-D transport
 // TU = D (U[i-1] - 2 U[i] + U[i+1]) / dx^2 with zero-gradient ends, and the
-// three SSP-RK3 stages of dU/dt = T(U) - Tn over dt/2 (Shu-Osher form).
-__device__ inline double lap1d(const double* U, int64_t i, int v, int64_t n, int nv) {
-  const int64_t im = i > 0 ? i - 1 : 0, ip = i + 1 < n ? i + 1 : n - 1;
-  return U[im * nv + v] - 2.0 * U[i * nv + v] + U[ip * nv + v];
+// three SSP-RK3 stages of dU/dt = T(U) - Tn over dt/2 (Shu-Osher form).  The
+// per-entry arithmetic sits in the inline functions below with every rounding
+// explicit (fma, __dmul_rn, __dadd_rn), so the whole-domain kernels and the
+// kernels on a slice held with ghost rows give the same bits for the same
+// neighbours -- a domain split over ranks reproduces the unsplit step exactly.
+__device__ __forceinline__ double diffusion_value(double xm, double x0, double xp, double D, double inv_dx2) {
+  const double lap = __dadd_rn(fma(-2.0, x0, xm), xp);
+  return __dmul_rn(D, __dmul_rn(lap, inv_dx2));
+}
+
+// stage 0: X + k g(X); stage 1: 3/4 U1 + 1/4 (X + k g(X)); stage 2:
+// 1/3 U1 + 2/3 (X + k g(X)), with g(X) = D lap X + sigma s
+__device__ __forceinline__ double ssprk3_value(int stage, double u1, double xm, double x0, double xp, bool has_s,
+                                               double s, double sigma, double D, double inv_dx2, double k) {
+  const double dX = diffusion_value(xm, x0, xp, D, inv_dx2);
+  const double gX = has_s ? fma(sigma, s, dX) : dX;
+  const double xk = fma(k, gX, x0);
+  if (stage == 0) return xk;
+  if (stage == 1) return fma(0.75, u1, __dmul_rn(0.25, xk));
+  return fma(2.0 / 3.0, xk, __ddiv_rn(u1, 3.0));
 }
 
 // c = (a R + b T) elementwise (the balancing constants of the splittings)
@@ -2207,12 +2232,10 @@ __global__ void diffusion_kernel(const double* __restrict__ U, double* __restric
   if (idx >= n * nv) return;
   const int64_t i = idx / nv;
   const int v = (int)(idx - i * nv);
-  TU[idx] = D * (lap1d(U, i, v, n, nv) * inv_dx2);
+  const int64_t im = i > 0 ? i - 1 : 0, ip = i + 1 < n ? i + 1 : n - 1;
+  TU[idx] = diffusion_value(U[im * nv + v], U[idx], U[ip * nv + v], D, inv_dx2);
 }
 
-// stage 0: V1 = U1 + k g(U1); stage 1: V2 = 3/4 U1 + 1/4 (V1 + k g(V1));
-// stage 2: U = 1/3 U1 + 2/3 (V2 + k g(V2)), with g(V) = D lap V + sigma S
-// (S a constant source array, or null for pure transport).
 __global__ void ssprk3_stage_kernel(int stage, const double* __restrict__ U1, const double* __restrict__ X,
                                     const double* __restrict__ S, double sigma, double* Out, int64_t n, int nv,
                                     double D, double inv_dx2, double k) {
@@ -2220,14 +2243,29 @@ __global__ void ssprk3_stage_kernel(int stage, const double* __restrict__ U1, co
   if (idx >= n * nv) return;
   const int64_t i = idx / nv;
   const int v = (int)(idx - i * nv);
-  const double dX = D * (lap1d(X, i, v, n, nv) * inv_dx2);
-  const double gX = S ? fma(sigma, S[idx], dX) : dX;
-  const double xk = X[idx] + k * gX;
-  double r;
-  if (stage == 0) r = xk;
-  else if (stage == 1) r = 0.75 * U1[idx] + 0.25 * xk;
-  else r = U1[idx] / 3.0 + (2.0 / 3.0) * xk;
-  Out[idx] = r;
+  const int64_t im = i > 0 ? i - 1 : 0, ip = i + 1 < n ? i + 1 : n - 1;
+  Out[idx] = ssprk3_value(stage, U1[idx], X[im * nv + v], X[idx], X[ip * nv + v], S != nullptr,
+                          S ? S[idx] : 0.0, sigma, D, inv_dx2, k);
+}
+
+// The same two operations on a slice of n points held with one ghost row on
+// each side: Xext has n + 2 rows, row r + 1 is the slice's point r.
+__global__ void diffusion_ghost_kernel(const double* __restrict__ Xext, double* __restrict__ TU, int64_t n, int nv,
+                                       double D, double inv_dx2) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * nv) return;
+  const double* c = Xext + nv + idx;
+  TU[idx] = diffusion_value(c[-nv], c[0], c[nv], D, inv_dx2);
+}
+
+__global__ void ssprk3_stage_ghost_kernel(int stage, const double* __restrict__ U1, const double* __restrict__ Xext,
+                                          const double* __restrict__ S, double sigma, double* Out, int64_t n,
+                                          int nv, double D, double inv_dx2, double k) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * nv) return;
+  const double* c = Xext + nv + idx;
+  Out[idx] = ssprk3_value(stage, U1[idx], c[-nv], c[0], c[nv], S != nullptr, S ? S[idx] : 0.0, sigma, D,
+                          inv_dx2, k);
 }
 
 // ------------------------------------------------------------------ probes
@@ -2513,8 +2551,17 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
     P.nhot = nhot;
   }
   LaunchPlan plan;
+  // timing events: inside a stream capture they become event-record nodes of
+  // the graph (external records), so every replay times the kernel
+  unsigned ev_flags = 0u;
+  if (o.ev_begin || o.ev_end) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamIsCapturing");
+    if (cap == cudaStreamCaptureStatusActive) ev_flags = cudaEventRecordExternal;
+  }
   if (o.ev_begin) {
-    e = cudaEventRecord((cudaEvent_t)o.ev_begin, stream);
+    e = cudaEventRecordWithFlags((cudaEvent_t)o.ev_begin, stream, ev_flags);
     if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
   }
 #define RK_LAUNCH(GG, MX)                                                                          \
@@ -2552,7 +2599,7 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "rok4e_integrate_kernel launch");
   if (o.ev_end) {
-    e = cudaEventRecord((cudaEvent_t)o.ev_end, stream);
+    e = cudaEventRecordWithFlags((cudaEvent_t)o.ev_end, stream, ev_flags);
     if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
   }
   return RK_OK;
@@ -2726,6 +2773,37 @@ int rk_diffusion_1d(const double* U, double* TU, int64_t npts, int32_t nvar, dou
                                                                                   1.0 / (dx * dx));
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? RK_OK : cuda_error(e, "diffusion_kernel launch");
+}
+
+int rk_diffusion_1d_ghost(const double* Uext, double* TU, int64_t npts, int32_t nvar, double D, double dx,
+                          void* stream) {
+  if (npts < 0 || nvar < 1) return set_error(RK_E_INVALID_ARGUMENT, "bad sizes");
+  if (npts == 0) return RK_OK;
+  if (!Uext || !TU) return set_error(RK_E_INVALID_ARGUMENT, "null array");
+  if (TU + npts * nvar > Uext && Uext + (npts + 2) * nvar > TU)
+    return set_error(RK_E_INVALID_ARGUMENT, "TU must not overlap Uext");
+  if (!(dx > 0.0)) return set_error(RK_E_INVALID_ARGUMENT, "dx must be > 0");
+  const int64_t n = npts * nvar;
+  diffusion_ghost_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(Uext, TU, npts, nvar, D,
+                                                                                        1.0 / (dx * dx));
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RK_OK : cuda_error(e, "diffusion_ghost_kernel launch");
+}
+
+int rk_ssprk3_stage_ghost(int32_t stage, const double* U1, const double* Xext, const double* S, double sigma,
+                          double* Out, int64_t npts, int32_t nvar, double D, double dx, double k, void* stream) {
+  if (stage < 0 || stage > 2) return set_error(RK_E_INVALID_ARGUMENT, "stage must be 0, 1 or 2");
+  if (npts < 0 || nvar < 1) return set_error(RK_E_INVALID_ARGUMENT, "bad sizes");
+  if (npts == 0) return RK_OK;
+  if (!U1 || !Xext || !Out) return set_error(RK_E_INVALID_ARGUMENT, "null array");
+  if (Out + npts * nvar > Xext && Xext + (npts + 2) * nvar > Out)
+    return set_error(RK_E_INVALID_ARGUMENT, "Out must not overlap Xext");
+  if (!(dx > 0.0)) return set_error(RK_E_INVALID_ARGUMENT, "dx must be > 0");
+  const int64_t n = npts * nvar;
+  ssprk3_stage_ghost_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      stage, U1, Xext, S, sigma, Out, npts, nvar, D, 1.0 / (dx * dx), k);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RK_OK : cuda_error(e, "ssprk3_stage_ghost_kernel launch");
 }
 
 int rk_simpler_split_step(const rk_mech* mech, double* U, double* h_cell, int64_t npts, double p, double dt,

@@ -3,6 +3,9 @@
 * Each scheme against the oracle's split step on the same grid, both
   integrating the reaction sub-steps at tight tolerance (free running).
 * Scheme 0 of rk_split_step is bitwise rk_simpler_split_step.
+* The domain split into slices with one ghost row per side (the multi-GPU
+  layout), emulated by two slices on one GPU whose halos are copied between
+  the phases, is bitwise the whole-domain split step.
 * Second-order convergence in the split step size of the balanced schemes
   (the paper's 1-D flame shows 2nd order in T), measured on the GPU.
 """
@@ -134,3 +137,57 @@ def test_transport_first_simple_balancing_is_unstable_at_large_steps(rk, case):
     print(f"coarse step: transport-first simple balanced {e_tf:.3e} K vs Simpler {e_s:.3e} K; finer {e_tf_fine:.3e} K")
     assert e_tf > 100 * e_s
     assert e_tf_fine < 0.01 * e_tf
+
+
+def test_sharded_slices_equal_whole_domain_bitwise(rk, case):
+    """Two slices of a 301-point front (150 + 151 points) held with ghost
+    rows, their halos copied between them before each of the four transport
+    evaluations (host-ordered copies on one stream: no kernel waits on
+    another), three split steps: states, carried steps and statistics equal
+    rk_simpler_split_step on the whole domain bit for bit; so does the
+    one-rank rk.simpler_split_step_sharded."""
+    from synth.fields import field_tanh_front
+
+    w, mech = case
+    m = rk.mech_load(mech)
+    npts = 301
+    _, U0 = field_tanh_front(npts, mech.n_species, w.field_seed)
+    dx = 1e-2 / npts
+    U = torch.tensor(U0, device="cuda")
+    hc = torch.zeros(npts, dtype=torch.float64, device="cuda")
+    st = torch.zeros(npts, 4, dtype=torch.int32, device="cuda")
+    cuts = [(0, 150), (150, npts)]
+    ext = [torch.zeros(b - a + 2, U0.shape[1], dtype=torch.float64, device="cuda") for a, b in cuts]
+    hs = [torch.zeros(b - a, dtype=torch.float64, device="cuda") for a, b in cuts]
+    ss = [torch.zeros(b - a, 4, dtype=torch.int32, device="cuda") for a, b in cuts]
+    for e, (a, b) in zip(ext, cuts):
+        e[1:-1] = U[a:b]
+    one = torch.zeros(npts + 2, U0.shape[1], dtype=torch.float64, device="cuda")
+    one[1:-1] = U
+    h1 = torch.zeros(npts, dtype=torch.float64, device="cuda")
+    for step in range(3):
+        rk.simpler_split_step(m, U, w.dt, D, dx, w.rtol, w.atol, 4, h_cell=hc, stats=st)
+        rk.simpler_split_step_sharded(m, one, w.dt, D, dx, w.rtol, w.atol, 4, h_cell=h1)
+
+        def react(r):
+            return lambda Ur, Tn: rk.rok4e_integrate(m, Ur, w.dt, w.rtol, w.atol, 4, src=Tn, h_cell=hs[r],
+                                                     stats=ss[r])
+
+        gens = [rk.simpler_split_step_phases(react(r), rk.GhostTransport(), ext[r], w.dt, D, dx) for r in (0, 1)]
+        while True:
+            xs = [next(g, None) for g in gens]
+            if all(x is None for x in xs):
+                break
+            assert all(x is not None for x in xs)
+            n0, n1 = xs[0].shape[0] - 2, xs[1].shape[0] - 2
+            xs[0][0] = xs[0][1]  # the domain's ends: zero gradient
+            xs[1][n1 + 1] = xs[1][n1]
+            xs[0][n0 + 1] = xs[1][1]  # the halo between the slices
+            xs[1][0] = xs[0][n0]
+        torch.cuda.synchronize()
+        got = torch.cat([e[1:-1] for e in ext])
+        assert torch.equal(got, U), step
+        assert torch.equal(torch.cat(hs), hc), step
+        assert torch.equal(torch.cat(ss), st), step
+        assert torch.equal(one[1:-1], U), step
+        assert torch.equal(h1, hc), step
