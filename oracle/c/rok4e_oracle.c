@@ -320,7 +320,7 @@ static int attempt(const orc_mech* mech, const double* src, double p, const doub
 /* status: 0 ok, 1 attempt cap, 2 non-finite accepted state, 3 step underflow */
 static void integrate_cell(const orc_mech* mech, double* u, const double* src, double p, double dt, double rtol,
                            double atol, int M, int jv_mode, double* h_io, const double* replay, int cap,
-                           int32_t* stats) {
+                           int32_t* stats, double* rec) {
   const int N = mech->ns + 1;
   double Q[ORC_MAX_M][ORC_MAX_SP], H[ORC_MAX_M][ORC_MAX_M];
   double fn[ORC_MAX_SP], us[ORC_MAX_SP], uh[ORC_MAX_SP];
@@ -365,6 +365,7 @@ static void integrate_cell(const orc_mech* mech, double* u, const double* src, d
     }
     const double h_new = h * fac;
     const int accept = forced >= 0 ? forced : (isfinite(err) && err <= 1.0);
+    if (rec && n_att - 1 < cap) rec[n_att - 1] = accept ? h : -h;
     if (accept) {
       if (bad) {
         status = 2;
@@ -419,16 +420,19 @@ int orc_jvp(const orc_mech* m, const double* u, const double* v, double p, int j
 
 /* Every row of U [ncell x (ns+1)] over dt in place (OpenMP over cells).
  * src [ncell x N] or NULL; h [ncell]: in h0 (<= 0: dt), out the next step;
- * replay [ncell x cap] or NULL; stats [ncell x 4] or NULL. */
+ * replay [ncell x cap] or NULL; record [ncell x cap] or NULL (the attempts
+ * taken, +h accepted / -h rejected, first cap of them; zero the buffer first);
+ * stats [ncell x 4] or NULL. */
 int orc_integrate(const orc_mech* m, double* U, const double* src, double* h, int64_t ncell, double p, double dt,
-                  double rtol, double atol, int M, int jv_mode, const double* replay, int cap, int32_t* stats,
-                  int nthreads) {
+                  double rtol, double atol, int M, int jv_mode, const double* replay, double* record, int cap,
+                  int32_t* stats, int nthreads) {
   if (!m || !U || ncell < 0 || M < 0 || M > ORC_MAX_M || !(dt > 0.0)) return -1;
   const int N = m->ns + 1;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
   for (int64_t c = 0; c < ncell; ++c)
     integrate_cell(m, U + c * N, src ? src + c * N : NULL, p, dt, rtol, atol, M, jv_mode, h ? h + c : NULL,
-                   replay ? replay + c * cap : NULL, cap, stats ? stats + 4 * c : NULL);
+                   replay ? replay + c * cap : NULL, cap, stats ? stats + 4 * c : NULL,
+                   record ? record + c * cap : NULL);
   return 0;
 }
 
@@ -442,11 +446,11 @@ static void diffusion(const double* U, double* TU, int64_t npts, int nv, double 
 }
 
 /* nsteps Simpler balanced split steps (Eq. simpler_balanced) of the 1-D
- * system U [npts x N] in place, h [npts] carried; replay [nsteps x npts x cap]
- * or NULL; stats [nsteps x npts x 4] or NULL. */
+ * system U [npts x N] in place, h [npts] carried; replay and record
+ * [nsteps x npts x cap] or NULL; stats [nsteps x npts x 4] or NULL. */
 int orc_simpler_steps(const orc_mech* m, double* U, double* h, int64_t npts, double p, double dt, double D,
-                      double dx, double rtol, double atol, int M, int nsteps, const double* replay, int cap,
-                      int32_t* stats, int nthreads) {
+                      double dx, double rtol, double atol, int M, int nsteps, const double* replay, double* record,
+                      int cap, int32_t* stats, int nthreads) {
   if (!m || !U || !h || npts < 1 || nsteps < 0) return -1;
   const int nv = m->ns + 1;
   const size_t n = (size_t)npts * nv;
@@ -457,7 +461,8 @@ int orc_simpler_steps(const orc_mech* m, double* U, double* h, int64_t npts, dou
   for (int s = 0; s < nsteps; ++s) {
     diffusion(U, Tn, npts, nv, D, dx);
     orc_integrate(m, U, Tn, h, npts, p, dt, rtol, atol, M, 0, replay ? replay + (size_t)s * npts * cap : NULL,
-                  cap, stats ? stats + (size_t)s * npts * 4 : NULL, nthreads);
+                  record ? record + (size_t)s * npts * cap : NULL, cap,
+                  stats ? stats + (size_t)s * npts * 4 : NULL, nthreads);
     /* one SSP-RK3 step of dU/dt = T(U) - T(U_n) over dt/2 (Shu-Osher form) */
     const double k = 0.5 * dt;
     memcpy(U1, U, sizeof(double) * n);

@@ -55,10 +55,10 @@ def _lib():
         lib.orc_rhs.argtypes = [P, P, P, ctypes.c_double, P]
         lib.orc_jvp.argtypes = [P, P, P, ctypes.c_double, ctypes.c_int, P]
         lib.orc_integrate.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                      ctypes.c_double, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int]
+                                      ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, P, ctypes.c_int]
         lib.orc_simpler_steps.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                          ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int]
+                                          ctypes.c_int, P, P, ctypes.c_int, P, ctypes.c_int]
         _LIB = lib
     return _LIB
 
@@ -105,8 +105,9 @@ class COracle:
         return out
 
     def integrate(self, U, dt, rtol, atol, M, *, p=101325.0, src=None, h0=None, replay=None, jv_mode=0,
-                  threads=None):
-        """Every row of U over dt (copies; returns (U_out, h_last, stats [n, 4])).
+                  record_cap=0, threads=None):
+        """Every row of U over dt (copies; returns (U_out, h_last, stats [n, 4]),
+        plus the recorded attempts [n, record_cap] when record_cap > 0).
         replay: [n, cap] signed steps (+h accepted, -h rejected, 0 ends)."""
         U = np.array(U, dtype=np.float64, order="C")
         n = U.shape[0]
@@ -114,25 +115,40 @@ class COracle:
         h = np.zeros(n) if h0 is None else np.array(np.broadcast_to(h0, (n,)), dtype=np.float64)
         rp = None if replay is None else np.ascontiguousarray(replay, dtype=np.float64)
         cap = 0 if rp is None else rp.shape[1]
+        rec = None
+        if record_cap > 0:
+            if rp is not None and record_cap != cap:
+                raise ValueError("record_cap must equal the replay's cap")
+            cap = record_cap
+            rec = np.zeros((n, cap))
         st = np.zeros((n, 4), dtype=np.int32)
         rc = _lib().orc_integrate(self.h, _p(U), _p(s), _p(h), n, float(p), float(dt), float(rtol), float(atol),
-                                  int(M), int(jv_mode), _p(rp), cap, _p(st), threads or (os.cpu_count() or 1))
+                                  int(M), int(jv_mode), _p(rp), _p(rec), cap, _p(st),
+                                  threads or (os.cpu_count() or 1))
         if rc:
             raise ValueError("orc_integrate: bad arguments")
-        return U, h, st
+        return (U, h, st) if rec is None else (U, h, st, rec)
 
-    def simpler_steps(self, U, h, nsteps, dt, D, dx, rtol, atol, M, *, p=101325.0, replay=None, threads=None):
-        """nsteps Simpler split steps of the 1-D system (copies; returns (U, h, stats [nsteps, npts, 4])).
+    def simpler_steps(self, U, h, nsteps, dt, D, dx, rtol, atol, M, *, p=101325.0, replay=None, record_cap=0,
+                      threads=None):
+        """nsteps Simpler split steps of the 1-D system (copies; returns (U, h, stats [nsteps, npts, 4]),
+        plus the recorded attempts [nsteps, npts, record_cap] when record_cap > 0).
         replay: [nsteps, npts, cap] or None."""
         U = np.array(U, dtype=np.float64, order="C")
         h = np.array(h, dtype=np.float64)
         npts = U.shape[0]
         rp = None if replay is None else np.ascontiguousarray(replay, dtype=np.float64)
         cap = 0 if rp is None else rp.shape[2]
+        rec = None
+        if record_cap > 0:
+            if rp is not None and record_cap != cap:
+                raise ValueError("record_cap must equal the replay's cap")
+            cap = record_cap
+            rec = np.zeros((nsteps, npts, cap))
         st = np.zeros((nsteps, npts, 4), dtype=np.int32)
         rc = _lib().orc_simpler_steps(self.h, _p(U), _p(h), npts, float(p), float(dt), float(D), float(dx),
-                                      float(rtol), float(atol), int(M), int(nsteps), _p(rp), cap, _p(st),
+                                      float(rtol), float(atol), int(M), int(nsteps), _p(rp), _p(rec), cap, _p(st),
                                       threads or (os.cpu_count() or 1))
         if rc:
             raise ValueError("orc_simpler_steps: bad arguments")
-        return U, h, st
+        return (U, h, st) if rec is None else (U, h, st, rec)

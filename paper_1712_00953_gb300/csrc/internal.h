@@ -1,8 +1,9 @@
 // Internal layout shared by the host packing code (mech.cpp) and the kernels.
 //
 // A loaded mechanism is one contiguous device buffer.  Every block of the
-// integration kernels copies it verbatim into shared memory, so the offsets
-// below are valid relative to either copy.  Reactions are reordered so that
+// integration kernels copies a prefix of it verbatim into shared memory (as
+// much as its precision level reads), so the offsets below are valid relative
+// to either copy.  Reactions are reordered so that
 // Troe falloff reactions come first, then third-body reactions, then the
 // elementary ones: the lanes that take the longer pressure-dependent code path
 // then all sit in the first iteration of the per-lane reaction loop.
@@ -48,6 +49,9 @@ struct MechLayout {
   int64_t off_Wf = 0, off_invWf = 0, off_bf = 0, off_EaRf = 0, off_efff = 0, off_csr_nuf = 0;
   int64_t off_perm = 0;  // int32 per packed reaction: its index in the input description
   int64_t bytes = 0;
+  // prefixes of the buffer that kernels copy to shared memory: through the FP64
+  // arrays; also csr_nuf (double-float gathers); also the other FP32 copies
+  int64_t bytes_fp64 = 0, bytes_df = 0, bytes_f32 = 0;
 };
 
 struct HostMech {

@@ -223,12 +223,18 @@ bool pack_mechanism(const void* vdesc, HostMech* out, std::string* err) {
   L.off_csr_j = take(4 * (int64_t)nnz);
   L.off_piece_ptr = take(4 * (int64_t)(npiece + 1));
   L.off_spec_piece = take(4 * (int64_t)(ns + 1));
+  // what only some kernels read comes last, so a kernel copies a prefix:
+  // FP64 paths stop here, the double-float gathers also read csr_nuf, the FP32
+  // Jacobian-vector product the other FP32 copies; perm is read from global memory
+  L.bytes_fp64 = off;
+  L.off_csr_nuf = take(4 * (int64_t)nnz);
+  L.bytes_df = off;
   L.off_Wf = take(4 * (int64_t)ns);
   L.off_invWf = take(4 * (int64_t)ns);
   L.off_bf = take(4 * (int64_t)nr);
   L.off_EaRf = take(4 * (int64_t)nr);
   L.off_efff = take(4 * (int64_t)L.ntb * ns);
-  L.off_csr_nuf = take(4 * (int64_t)nnz);
+  L.bytes_f32 = off;
   L.off_perm = take(4 * (int64_t)nr);
   L.bytes = align16(off);
 

@@ -357,7 +357,6 @@ static SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false, int 
   s.w = take(N);
   const int Nq = (N + 1) & ~1;  // stride between Krylov / stage vectors
   s.Q = take(Nq * M);
-  s.K = take(4 * Nq);
   s.C = take(ns1);
   s.dC = take(ns1);
   s.cp = take(ns1);
@@ -371,16 +370,23 @@ static SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false, int 
   s.kc = take(L.nr > 0 ? L.nr : 1);
   s.krc = take(L.nr > 0 ? L.nr : 1);
   s.qT = take(L.nr > 0 ? L.nr : 1);
+  // The stage vectors K live only inside an attempt; the J v caches kc, krc,
+  // qT (contiguous) only from the caching right-hand side to the end of the
+  // Arnoldi process that precedes the attempts.  K shares their storage when
+  // it fits there.
+  const int nr_even = ((L.nr > 0 ? L.nr : 1) + 1) & ~1;
+  s.K = (4 * Nq <= 3 * nr_even) ? s.kc : take(4 * Nq);
   s.tb = take(4 * (L.ntb > 0 ? L.ntb : 1));
   s.tro = take(11 * (L.ntroe > 0 ? L.ntroe : 1));
   s.part = take(L.npiece > 0 ? L.npiece : 1);
   s.C2 = df ? take(ns1) : -1;
   s.dC2 = df ? take(ns1) : -1;
-  s.H = take(MAXM * MAXM);
-  s.LU = take(MAXM * MAXM);
+  // M x M matrices stored with row stride MAXM: M rows
+  s.H = take(M * MAXM);
+  s.LU = take(M * MAXM);
   s.piv = take(MAXM);
   s.red = take(4);
-  s.Bm = take(MAXM * MAXM);
+  s.Bm = take(M * MAXM);
   s.fbase = o;
   int fo = 0;
   auto ftake = [&](int n) {
@@ -1346,7 +1352,7 @@ __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& 
   const int N = m.ns + 1 + m.nx;
   const int Nq = s.Nq;
   if (M > N) M = N;
-  for (int i = g.lane; i < MAXM * MAXM; i += G) s.H[i] = 0.0;
+  for (int i = g.lane; i < M * MAXM; i += G) s.H[i] = 0.0;
   // squared norms; 1/||.|| from one reciprocal square root
   const double beta2 = group_dot<G>(g, s.fn, s.fn, N);
   if (M <= 0 || !(beta2 > 0.0) || !isfinite(beta2)) {
@@ -1598,6 +1604,7 @@ struct IntegrateParams {
   const unsigned* nhot;        // with static bins: number of hot cells leading the order, or null
   const double* rho_cell;      // constant-volume densities, or null (constant pressure)
   int nx;                      // state components after T (5: auxiliary-temperature system)
+  int64_t mech_copy;           // bytes of the mechanism each block copies (a prefix, by precision)
 };
 
 template <int G, bool MIXED>
@@ -1876,14 +1883,14 @@ template <int G, bool MIXED>
 __global__ void __launch_bounds__(MAX_BLOCK_THREADS, 1) rok4e_integrate_kernel(IntegrateParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   load_exp_table(reinterpret_cast<double*>(smem));
-  load_mech(smem + EXP_TAB_BYTES, P.mech, P.L.bytes);
+  load_mech(smem + EXP_TAB_BYTES, P.mech, P.mech_copy);
   __syncthreads();
   MechView m = make_view(smem + EXP_TAB_BYTES, P.L);
   m.etab = reinterpret_cast<const double*>(smem);
   m.nx = P.nx;
   const Grp<G> g;
   const int gid = threadIdx.x / G;
-  double* base = reinterpret_cast<double*>(smem + EXP_TAB_BYTES + P.L.bytes) + (size_t)gid * P.S.stride;
+  double* base = reinterpret_cast<double*>(smem + EXP_TAB_BYTES + P.mech_copy) + (size_t)gid * P.S.stride;
   const SlotPtrs s = slot_ptrs(base, P.S);
   init_sentinels<MIXED>(s, m.ns, g.lane);
   g.sync();
@@ -2046,14 +2053,14 @@ template <int G>
 __global__ void __launch_bounds__(MAX_BLOCK_THREADS) rkdp_integrate_kernel(IntegrateParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   load_exp_table(reinterpret_cast<double*>(smem));
-  load_mech(smem + EXP_TAB_BYTES, P.mech, P.L.bytes);
+  load_mech(smem + EXP_TAB_BYTES, P.mech, P.mech_copy);
   __syncthreads();
   MechView m = make_view(smem + EXP_TAB_BYTES, P.L);
   m.etab = reinterpret_cast<const double*>(smem);
   m.nx = P.nx;
   const Grp<G> g;
   const int gid = threadIdx.x / G;
-  double* base = reinterpret_cast<double*>(smem + EXP_TAB_BYTES + P.L.bytes) + (size_t)gid * P.S.stride;
+  double* base = reinterpret_cast<double*>(smem + EXP_TAB_BYTES + P.mech_copy) + (size_t)gid * P.S.stride;
   const SlotPtrs s = slot_ptrs(base, P.S);
   init_sentinels<false>(s, m.ns, g.lane);
   g.sync();
@@ -2405,12 +2412,12 @@ int device_props(int* n_sm, size_t* smem_optin) {
 
 template <int G, typename K>
 int plan_for(K kernel, const rk_mech* mech, const SlotLayout& S, int want_cells, int64_t ncell, bool persistent,
-             LaunchPlan* plan, int want_blocks_per_sm = 0, bool fill_device = false) {
+             LaunchPlan* plan, int want_blocks_per_sm = 0, bool fill_device = false, int64_t copy_bytes = -1) {
   int n_sm = 0;
   size_t smem_max = 0;
   int rc = device_props(&n_sm, &smem_max);
   if (rc) return rc;
-  const size_t mech_bytes = (size_t)mech->host.L.bytes + EXP_TAB_BYTES;
+  const size_t mech_bytes = (size_t)(copy_bytes >= 0 ? copy_bytes : mech->host.L.bytes) + EXP_TAB_BYTES;
   const size_t slot_bytes = (size_t)S.stride * sizeof(double);
   smem_max -= 64;  // the kernels' static shared memory (queue counters)
   if (mech_bytes + slot_bytes > smem_max)
@@ -2525,6 +2532,10 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   P.counter = reinterpret_cast<unsigned long long*>(wsb);
   if (o.reactor == 1 && !o.rho_cell) return set_error(RK_E_INVALID_ARGUMENT, "constant volume needs rho_cell");
   P.rho_cell = o.reactor == 1 ? o.rho_cell : nullptr;
+  {
+    const MechLayout& L = mech->host.L;
+    P.mech_copy = (method == 1 || o.precision == 0) ? L.bytes_fp64 : (o.precision == 2 ? L.bytes_f32 : L.bytes_df);
+  }
   P.qstride = queue_stride(ncell);
   P.order = nullptr;
   cudaError_t e = cudaMemsetAsync(wsb, 0, 768, stream);  // counter, histogram, cursors
@@ -2567,7 +2578,7 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
 #define RK_LAUNCH(GG, MX)                                                                          \
   do {                                                                                             \
     rc = plan_for<GG>(rok4e_integrate_kernel<GG, MX>, mech, P.S, o.cells_per_block, ncell, true, &plan, \
-                      o.blocks_per_sm, order == 3);                                                \
+                      o.blocks_per_sm, order == 3, P.mech_copy);                                   \
     if (rc) return rc;                                                                             \
     if (order == 3) P.subq = plan.cells_per_block % 4 == 0 ? 4 : (plan.cells_per_block % 2 == 0 ? 2 : 1); \
     rok4e_integrate_kernel<GG, MX><<<plan.blocks, plan.cells_per_block * GG, plan.smem, stream>>>(P); \
@@ -2575,7 +2586,7 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
 #define RK_LAUNCH_DP(GG)                                                                              \
   do {                                                                                                \
     rc = plan_for<GG>(rkdp_integrate_kernel<GG>, mech, P.S, o.cells_per_block, ncell, true, &plan,    \
-                      o.blocks_per_sm, order == 3);                                                   \
+                      o.blocks_per_sm, order == 3, P.mech_copy);                                      \
     if (rc) return rc;                                                                                \
     if (order == 3) P.subq = plan.cells_per_block % 4 == 0 ? 4 : (plan.cells_per_block % 2 == 0 ? 2 : 1); \
     rkdp_integrate_kernel<GG><<<plan.blocks, plan.cells_per_block * GG, plan.smem, stream>>>(P);      \
