@@ -54,8 +54,12 @@ GOLDEN = 0.6180339887498949
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one integration launch from
 # an ncu capture of the current kernel (bytes per launch), keyed by workload;
-# None while no capture of the current kernel exists.
-TRAFFIC = {"batched": None, "flame1d": None}
+# None while no capture of the current kernel exists.  batched: 2^18 cells
+# captured (267,186,432 B), scaled by cells to the 2^20-cell launch (the
+# traffic per cell does not depend on the launch size); flame1d: the 8th split
+# step's integration launch, whose 0.5 MB state stays in L2 (writes are not
+# all flushed by the kernel's end).
+TRAFFIC = {"batched": 267186432 * 4, "flame1d": 1397760 + 125440}
 
 
 def _env_int(k, d):
@@ -474,6 +478,8 @@ def run_headline(args, rank, world, dev, dist):
                      "frac": achieved / FP64_PEAK, "peak_kind": "nominal FP64 (MEASURED_PEAKS.json has no FP64 "
                                                                 "entry; the bench's own FMA probe agrees)",
                      "traffic": TRAFFIC["batched"],
+                     "traffic_note": "ncu dram bytes of a 2^18-cell launch scaled by cells to 2^20 "
+                                     "(profiles/rok4e_integrate_batched.md)",
                      "algorithmic_bytes_per_launch": int(n * (2 * N * 8 + 16 + 8 + 8 + 4)),
                      "kernel": "rok4e_integrate_kernel<32, 0>", "kernel_s_per_step": kern_s,
                      "kernel_timing": kernel_timing, "exp_flops_counted": EXP_FLOPS,
