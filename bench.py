@@ -1018,7 +1018,7 @@ def run_unit_costs(args):
                           "rhs": int(s[:, 2].sum()), "failed": int((s[:, 3] != 0).sum())}))
     if not args.skip_probes:
         names = ["fp64_fma", "fp32_fma", "fp64_exp", "cvt", "fp64_fma_1warp_per_sm", "fp64_fma_4warps_per_sm",
-                 "fp64_warp_inst_1lane_4warps_per_sm", "df_fma"]
+                 "fp64_warp_inst_1lane_4warps_per_sm", "df_fma", "i2f_f64"]
         print(json.dumps({"probes_ops_per_s": {nm: rk.probe_throughput(k) for k, nm in enumerate(names)}}))
     return 0
 

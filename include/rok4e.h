@@ -415,7 +415,8 @@ int rk_rok4e_adjoint(const rk_mech* mech, const double* checkpoints, const doubl
  *  kind 0: FP64 FMA, 1: FP32 FMA, 2: FP64 exp(), 3: double<->float
  *  conversions; how the FP64 pipe is shared: 4: FP64 FMA with one warp per
  *  SM, 5: four warps per SM, 6: four warps per SM with one active lane each
- *  (rate of warp instructions); 7: double-float (FP32 pair) multiply-adds.
+ *  (rate of warp instructions); 7: double-float (FP32 pair) multiply-adds;
+ *  8: int -> double conversions (with an integer op and a bit move each).
  *  Launches a dependent-operation
  *  grid sized to the device and returns the operation rate (ops/s) measured
  *  with CUDA events in *ops_per_s.  Synchronous. */

@@ -507,7 +507,7 @@ class FixedStepROK4E(torch.autograd.Function):
 def probe_throughput(kind: int) -> float:
     """Measured rate (ops/s) of 0: FP64 FMA, 1: FP32 FMA, 2: FP64 exp, 3: conversions,
     4/5: FP64 FMA with 1/4 warps per SM, 6: FP64 warp instructions with one active
-    lane, 7: double-float multiply-adds (rk_probe_throughput)."""
+    lane, 7: double-float multiply-adds, 8: int -> double conversions (rk_probe_throughput)."""
     v = ctypes.c_double()
     _check(_L().rk_probe_throughput(int(kind), ctypes.byref(v)), "rk_probe_throughput")
     return v.value

@@ -2,7 +2,9 @@
 
 Exponential (Tang, "Table-driven implementation of the exponential function
 in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989): correctly rounded
-2^(j/128), j = 0..127, and ln2/128 split in two.  Logarithm (Tang,
+2^(j/256), j = 0..255, and ln2/256 split in two (256 intervals keep the
+reduced argument within ln2/512, where a degree-4 polynomial of e^r - 1 is
+accurate below an ulp).  Logarithm (Tang,
 "Table-driven implementation of the logarithm function in IEEE
 floating-point arithmetic", ACM TOMS 16(4), 1990): for the 128 intervals
 [1 + j/128, 1 + (j+1)/128) of the significand, the reciprocal of the
@@ -16,15 +18,17 @@ arithmetic and rounded once to binary64.
 import struct
 from decimal import Decimal, getcontext
 
-N = 128
+N = 256  # exponential table
+NL = 128  # logarithm tables
 
 
 def main():
     getcontext().prec = 60
     ln2 = Decimal(2).ln()
-    lines = ["// Generated by gen_exp_table.py: RK_EXP2_TABLE_VALUES[j] = 2^(j/128) rounded to binary64;",
+    lines = ["// Generated by gen_exp_table.py: RK_EXP2_TABLE_VALUES[j] = 2^(j/256) rounded to binary64;",
              "// RK_LOG_INV_C_VALUES[j] = 1/(1 + (j + 1/2)/128) rounded, RK_LOG_LN_C_VALUES[j] = -ln of it.",
-             "#pragma once", f"#define RK_EXP2_TABLE_N {N}", "#define RK_EXP2_TABLE_VALUES \\"]
+             "#pragma once", f"#define RK_EXP2_TABLE_N {N}", f"#define RK_LOG_TABLE_N {NL}",
+             "#define RK_EXP2_TABLE_VALUES \\"]
     for j in range(N):
         v = (ln2 * j / N).exp()
         f = float(v)  # Decimal -> nearest binary64
@@ -40,8 +44,8 @@ def main():
     lines.append(f"constexpr double RK_LN2_OVER_N_HI = {head.hex()};")
     lines.append(f"constexpr double RK_LN2_OVER_N_LO = {tail.hex()};")
     lines.append(f"constexpr double RK_N_OVER_LN2 = {float(Decimal(N) / ln2).hex()};")
-    # logarithm: inv_c_j = 1 / (1 + (j + 1/2) / N) rounded, ln_c_j = -ln(inv_c_j) of the rounded value
-    inv_c = [float(1 / (1 + (Decimal(j) + Decimal(1) / 2) / N)) for j in range(N)]
+    # logarithm: inv_c_j = 1 / (1 + (j + 1/2) / NL) rounded, ln_c_j = -ln(inv_c_j) of the rounded value
+    inv_c = [float(1 / (1 + (Decimal(j) + Decimal(1) / 2) / NL)) for j in range(NL)]
     ln_c = [float(-Decimal(v).ln()) for v in inv_c]  # Decimal(v) is the binary64 value exactly
     lines.append(f"#define RK_LOG_INV_C_VALUES {', '.join(v.hex() for v in inv_c)}")
     lines.append(f"#define RK_LOG_LN_C_VALUES {', '.join(v.hex() for v in ln_c)}")

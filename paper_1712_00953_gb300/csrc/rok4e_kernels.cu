@@ -14,12 +14,16 @@
 // global atomic counter (work stealing), so cells needing 1 or 200 substeps
 // share one launch without a tail of idle blocks.
 //
-// Arithmetic.  FP64 throughout.  Two restatements differ from a literal
+// Arithmetic.  FP64 throughout.  Three restatements differ from a literal
 // transcription of the kinetics while computing the same quantities:
 //  * 1/Kc_j = exp(Delta G_j/RT) (RT/p_ref)^dnu_j is formed as a product of the
-//    per-species factors exp(+-g_k/RT) (2 exponentials per species instead of
-//    one per reaction), falling back to one exponential per reaction when a
-//    species has |g/RT| > 170 (where a product of four factors could overflow);
+//    per-species factors E_k = exp(g_k/RT) (RT/p_ref) over the products and
+//    1/E_k over the reactants (2 exponentials per species instead of one per
+//    reaction, the pressure factor folded in), falling back to one
+//    exponential per reaction when some |g/RT + ln(RT/p_ref)| > 170 (where a
+//    product of four factors could overflow);
+//  * q_j = m_j k_j (prod C^nu' - prod C^nu''/Kc_j), the second product formed
+//    from the per-species C_k E_k and the reactants' 1/E_k;
 //  * w = nu^T q is a gather over a species-major list (deterministic order).
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -64,18 +68,19 @@ constexpr int MAX_BLOCK_THREADS = 256;
 constexpr int EXP_TAB_BYTES = RK_EXP2_TABLE_N * 8;  // leads the dynamic shared memory
 
 __constant__ double c_exp2_table[RK_EXP2_TABLE_N] = {RK_EXP2_TABLE_VALUES};
-__constant__ double c_log_inv_c[RK_EXP2_TABLE_N] = {RK_LOG_INV_C_VALUES};
-__constant__ double c_log_ln_c[RK_EXP2_TABLE_N] = {RK_LOG_LN_C_VALUES};
+__constant__ double c_log_inv_c[RK_LOG_TABLE_N] = {RK_LOG_INV_C_VALUES};
+__constant__ double c_log_ln_c[RK_LOG_TABLE_N] = {RK_LOG_LN_C_VALUES};
 
 // ------------------------------------------------- table-driven exponential
-// exp(x) by Tang's table-driven method (ACM TOMS 15(2), 1989) with a 128-entry
-// table of 2^(j/128): x = (128 m + j) ln2/128 + r with |r| <= ln2/256,
-// exp(x) = 2^m 2^(j/128) (1 + p(r)), p the degree-5 Taylor polynomial of
-// e^r - 1 (truncation < 1e-18 relative).  k = 128 m + j comes from adding a
-// 1.5 2^52 shifter, r from a two-part ln2/128, and the final scaling by 2^m is
-// an integer add to the exponent field, so the fast path costs 10 FP64
+// exp(x) by Tang's table-driven method (ACM TOMS 15(2), 1989) with a 256-entry
+// table of 2^(j/256): x = (256 m + j) ln2/256 + r with |r| <= ln2/512,
+// exp(x) = 2^m 2^(j/256) (1 + p(r)), p the degree-4 Taylor polynomial of
+// e^r - 1 (truncation < 4e-17 relative).  k = 256 m + j comes from adding a
+// 1.5 2^52 shifter, r from a two-part ln2/256, and the final scaling by 2^m is
+// an integer add to the exponent field, so the fast path costs 9 FP64
 // operations.  |x| >= 708, infinities and NaN take the library exp().
 constexpr double EXP_SHIFTER = 6755399441055744.0;  // 1.5 * 2^52
+constexpr int EXP_LOG2N = 8;                        // log2 of the table size
 
 __device__ __forceinline__ double exp_scale(double y, int e) {
   return __hiloint2double(__double2hiint(y) + (e << 20), __double2loint(y));
@@ -88,18 +93,17 @@ __device__ __forceinline__ double exp_fast(double x, const double* __restrict__ 
   const double kd = kt - EXP_SHIFTER;
   double r = fma(-kd, RK_LN2_OVER_N_HI, x);
   r = fma(-kd, RK_LN2_OVER_N_LO, r);
-  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-  q = fma(q, r, 1.0 / 6.0);
+  double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
   q = fma(q, r, 0.5);
   const double p = fma(r * r, q, r);
   const double t = tab[k & (RK_EXP2_TABLE_N - 1)];
-  return exp_scale(fma(t, p, t), k >> 7);
+  return exp_scale(fma(t, p, t), k >> EXP_LOG2N);
 }
 
 // Mixed-precision exp: the same argument reduction and reconstruction in FP64,
-// e^r - 1 = r + r^2 q(r) with the small term r^2 q(r) (|r| <= ln2/256, so at
-// most 3.7e-6) in FP32.  Relative error ~1e-12 for 6 FP64 operations instead
-// of 10.
+// e^r - 1 = r + r^2 q(r) with the small term r^2 q(r) (|r| <= ln2/512, so at
+// most 9.2e-7) in FP32.  Relative error ~1e-13 for 6 FP64 operations instead
+// of 9.
 __device__ __forceinline__ double exp_mixed(double x, const double* __restrict__ tab) {
   if ((__double2hiint(x) & 0x7fffffff) >= 0x40862000) return exp(x);
   const double kt = fma(x, RK_N_OVER_LN2, EXP_SHIFTER);
@@ -108,10 +112,10 @@ __device__ __forceinline__ double exp_mixed(double x, const double* __restrict__
   double r = fma(-kd, RK_LN2_OVER_N_HI, x);
   r = fma(-kd, RK_LN2_OVER_N_LO, r);
   const float rf = __double2float_rn(r);
-  const float q = fmaf(fmaf(fmaf(rf, 1.0f / 120.0f, 1.0f / 24.0f), rf, 1.0f / 6.0f), rf, 0.5f);
+  const float q = fmaf(fmaf(rf, 1.0f / 24.0f, 1.0f / 6.0f), rf, 0.5f);
   const double p = r + (double)(rf * rf * q);
   const double t = tab[k & (RK_EXP2_TABLE_N - 1)];
-  return exp_scale(fma(t, p, t), k >> 7);
+  return exp_scale(fma(t, p, t), k >> EXP_LOG2N);
 }
 
 // (exp(x), exp(-x)) as exp_mixed, sharing the argument reduction.
@@ -128,15 +132,15 @@ __device__ __forceinline__ void exp_pm_mixed(double x, const double* __restrict_
   r = fma(-kd, RK_LN2_OVER_N_LO, r);
   const float rf = __double2float_rn(r);
   const float r2 = rf * rf;
-  const float qp = fmaf(fmaf(fmaf(rf, 1.0f / 120.0f, 1.0f / 24.0f), rf, 1.0f / 6.0f), rf, 0.5f);
-  const float qm = fmaf(fmaf(fmaf(-rf, 1.0f / 120.0f, 1.0f / 24.0f), -rf, 1.0f / 6.0f), -rf, 0.5f);
+  const float qp = fmaf(fmaf(rf, 1.0f / 24.0f, 1.0f / 6.0f), rf, 0.5f);
+  const float qm = fmaf(fmaf(-rf, 1.0f / 24.0f, 1.0f / 6.0f), -rf, 0.5f);
   const double pp = r + (double)(r2 * qp);
   const double pm = (double)(r2 * qm) - r;
   const double tp = tab[k & (RK_EXP2_TABLE_N - 1)];
   const int km = -k;
   const double tm = tab[km & (RK_EXP2_TABLE_N - 1)];
-  *ep = exp_scale(fma(tp, pp, tp), k >> 7);
-  *em = exp_scale(fma(tm, pm, tm), km >> 7);
+  *ep = exp_scale(fma(tp, pp, tp), k >> EXP_LOG2N);
+  *em = exp_scale(fma(tm, pm, tm), km >> EXP_LOG2N);
 }
 
 // 1/x by Newton's iteration for the reciprocal, r <- r + r (1 - x r), from
@@ -173,7 +177,7 @@ __device__ __forceinline__ double rcp_any(double x) {
 __device__ __forceinline__ double log_fast(double x) {
   const int hi = __double2hiint(x);
   if ((unsigned)(hi - 0x00100000) >= 0x7fe00000u) return log(x);
-  const int j = (hi >> 13) & (RK_EXP2_TABLE_N - 1);
+  const int j = (hi >> 13) & (RK_LOG_TABLE_N - 1);
   const double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, __double2loint(x));
   // e as a double: 2^52 + biased exponent, less 2^52 + 1023 (exact)
   const double e = __hiloint2double(0x43300000, hi >> 20) - 4503599627371519.0;
@@ -236,19 +240,17 @@ __device__ __forceinline__ void exp_pm(double x, const double* __restrict__ tab,
   double r = fma(-kd, RK_LN2_OVER_N_HI, x);
   r = fma(-kd, RK_LN2_OVER_N_LO, r);
   const double r2 = r * r;
-  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-  q = fma(q, r, 1.0 / 6.0);
+  double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
   q = fma(q, r, 0.5);
   const double pp = fma(r2, q, r);
-  double qm = fma(-r, 1.0 / 120.0, 1.0 / 24.0);
-  qm = fma(qm, -r, 1.0 / 6.0);
+  double qm = fma(-r, 1.0 / 24.0, 1.0 / 6.0);
   qm = fma(qm, -r, 0.5);
   const double pm = fma(r2, qm, -r);
   const double tp = tab[k & (RK_EXP2_TABLE_N - 1)];
   const int km = -k;
   const double tm = tab[km & (RK_EXP2_TABLE_N - 1)];
-  *ep = exp_scale(fma(tp, pp, tp), k >> 7);
-  *em = exp_scale(fma(tm, pm, tm), km >> 7);
+  *ep = exp_scale(fma(tp, pp, tp), k >> EXP_LOG2N);
+  *em = exp_scale(fma(tm, pm, tm), km >> EXP_LOG2N);
 }
 
 __device__ inline void load_exp_table(double* dst) {
@@ -319,7 +321,7 @@ __host__ __device__ inline MechView make_view(const unsigned char* base, const M
 struct SlotLayout {
   int N, ns, nr, ntb, M;
   int u, src, fn, arg, fr, F, w, Q, K;        // N-vectors (Q: M of them, K: 4)
-  int C, dC, cp, hRT, dcp, gRT, E, Einv, om;  // species (+1 sentinel entry)
+  int C, dC, cp, hRT, dcp, gRT, E, Einv, CE, om;  // species (+1 sentinel entry)
   int q, kc, krc, qT;                         // reactions (qT: d q_j / dT at u_n, for J v)
   int tb;                                     // [ntb][4]: [M], dk/d[M], dlnk/dT, 1/Kc
   int tro;                                    // [11][ntroe]: Troe falloff scratch
@@ -365,6 +367,7 @@ static SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false, int 
   s.gRT = take(ns1);
   s.E = take(ns1);
   s.Einv = take(ns1);
+  s.CE = take(ns1);
   s.om = take(ns1);
   s.q = take(L.nr > 0 ? L.nr : 1);
   s.kc = take(L.nr > 0 ? L.nr : 1);
@@ -516,7 +519,7 @@ struct CellScalars {
 
 struct SlotPtrs {
   double *u, *src, *fn, *arg, *fr, *F, *w, *Q, *K;
-  double *C, *dC, *cp, *hRT, *dcp, *gRT, *E, *Einv, *om, *q, *kc, *krc, *qT, *tb, *tro, *part;
+  double *C, *dC, *cp, *hRT, *dcp, *gRT, *E, *Einv, *CE, *om, *q, *kc, *krc, *qT, *tb, *tro, *part;
   df2 *C2, *dC2;
   double *H, *LU, *piv, *red, *Bm;
   float *fC, *fdC, *fh, *fcp, *fdcp, *fom, *fq, *fkc, *fkr, *ftb, *fQ, *fw, *fpart;  // mixed precision
@@ -542,6 +545,7 @@ __device__ inline SlotPtrs slot_ptrs(double* b, const SlotLayout& s) {
   p.gRT = b + s.gRT;
   p.E = b + s.E;
   p.Einv = b + s.Einv;
+  p.CE = b + s.CE;
   p.om = b + s.om;
   p.q = b + s.q;
   p.kc = b + s.kc;
@@ -640,9 +644,10 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
   const double T = uu[ns];
   const double invT = rcp_newton(T);
   const double lnT = log_fast(T);
+  const double lnRTp = LN_R_OVER_PREF + lnT;  // ln(R T / p_ref)
   // species pass 1: thermo, Gibbs factors, sum Y/W
   double S = 0.0;
-  int ghi = 0;  // max over species of the high word of |g/RT| (integer compare)
+  int ghi = 0;  // max over species of the high word of |g/RT + ln(RT/p_ref)| (integer compare)
   for (int k = g.lane; k < ns; k += G) {
     const double* c = (T < m.Tmid[k]) ? m.lo : m.hi;
     const double a1 = c[k], a2 = c[ns + k], a3 = c[2 * ns + k], a4 = c[3 * ns + k], a5 = c[4 * ns + k];
@@ -655,10 +660,13 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
     s.cp[k] = cp;
     s.hRT[k] = hrt;
     s.gRT[k] = grt;
-    ghi = max(ghi, __double2hiint(grt) & 0x7fffffff);
+    ghi = max(ghi, __double2hiint(grt + lnRTp) & 0x7fffffff);
     if (cache) {
       const double dcp = fma(fma(fma(c[16 * ns + k], T, c[15 * ns + k]), T, c[14 * ns + k]), T, a2);
       s.dcp[k] = dcp;
+      // (h/RT - 1)/T, whose sum over a reaction's products less its reactants is
+      // d ln Kc/dT; kept in dC, which the J v overwrites later (sentinel entry 0)
+      s.dC[k] = __dmul_rn(hrt - 1.0, invT);
       if (MIXED) {
         s.fh[k] = __double2float_rn(hrt);
         s.fcp[k] = __double2float_rn(cp);
@@ -669,7 +677,7 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
   }
   S = g.sum(S);
   ghi = g.imax(ghi);
-  const bool direct_kc = ghi >= G_OVERFLOW_HI;  // |g/RT| >= 170, also NaN
+  const bool direct_kc = ghi >= G_OVERFLOW_HI;  // some |g/RT + ln(RT/p_ref)| >= 170, also NaN
   // auxiliary-temperature system (Eq. chemical_source_balanced): the species
   // components are rho Y_k, so C_k = u_k / W_k and d(rho Y_k)/dt = W_k w_k:
   // the constant-volume arithmetic with unit density
@@ -692,8 +700,13 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
     if (MIXED && cache) s.fC[k] = __double2float_rn(Ck);
     if (cache && cs->prec == 3) s.C2[k] = df_from(Ck);
     if (!direct_kc) {
-      if (MIXED || cs->prec == 3) exp_pm_mixed(s.gRT[k], m.etab, &s.E[k], &s.Einv[k]);
-      else exp_pm(s.gRT[k], m.etab, &s.E[k], &s.Einv[k]);
+      // E = e^{g/RT} (RT/p_ref), Einv = 1/E: 1/Kc of a reaction is the product of
+      // E over its products and Einv over its reactants (the pressure factor
+      // (RT/p_ref)^dnu included); CE = C E, so k/Kc prod C^nu'' is three products
+      const double a = s.gRT[k] + lnRTp;
+      if (MIXED || cs->prec == 3) exp_pm_mixed(a, m.etab, &s.E[k], &s.Einv[k]);
+      else exp_pm(a, m.etab, &s.E[k], &s.Einv[k]);
+      s.CE[k] = __dmul_rn(Ck, s.E[k]);
     }
     if (coop_tb) {
 #pragma unroll
@@ -802,9 +815,6 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
     g.sync();
   }
   // reactions: rate coefficients and rates of progress
-  const double RTp = R_OVER_PREF * T;
-  const double invRTp = PREF_OVER_R * invT;
-  const double lnRTp = LN_R_OVER_PREF + lnT;
   const double m_lnRTp = -lnRTp;
   for (int j = g.lane; j < m.nr; j += G) {
     const uint32_t sl = m.slots[j];
@@ -815,16 +825,17 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
     const int dnu = ((meta >> 4) & 15) - 4;
     const double lnk = fma(-m.EaR[j], invT, fma(m.bexp[j], lnT, m.lnA[j]));
     double k = (MIXED || cs->prec == 3) ? exp_mixed(lnk, m.etab) : exp_fast(lnk, m.etab);
-    const double Pf = s.C[ra] * s.C[rb];
-    const double Pb = s.C[pa] * s.C[pb];
-    double rfac = 0.0;  // 1/Kc
+    const double Pf = __dmul_rn(s.C[ra], s.C[rb]);
+    // Rb = prod C^nu'' / Kc, rfac = 1/Kc (only the caching evaluation needs it)
+    double Rb = 0.0, rfac = 0.0;
     if (rev) {
       if (!direct_kc) {
-        const double pf = dnu > 0 ? RTp : (dnu < 0 ? invRTp : 1.0);
-        rfac = s.E[pa] * s.Einv[ra] * s.E[pb] * s.Einv[rb] * pf;
+        Rb = __dmul_rn(__dmul_rn(__dmul_rn(s.CE[pa], s.CE[pb]), s.Einv[ra]), s.Einv[rb]);
+        if (cache) rfac = __dmul_rn(__dmul_rn(__dmul_rn(s.E[pa], s.E[pb]), s.Einv[ra]), s.Einv[rb]);
       } else {
         const double dl = dnu > 0 ? lnRTp : (dnu < 0 ? m_lnRTp : 0.0);
         rfac = exp_fast(s.gRT[pa] + s.gRT[pb] - s.gRT[ra] - s.gRT[rb] + dl, m.etab);
+        Rb = __dmul_rn(rfac, __dmul_rn(s.C[pa], s.C[pb]));
       }
     }
     double mfac = 1.0;
@@ -867,17 +878,20 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
         }
       }
     }
-    const double kr = k * rfac;
-    const double qj = mfac * fma(k, Pf, -__dmul_rn(kr, Pb));
+    // q = m k (prod C^nu' - prod C^nu'' / Kc); the third-body factor only where there is one
+    const double q0 = __dmul_rn(k, __dsub_rn(Pf, Rb));
+    double qj = q0;
+    if (kind == 1) qj = __dmul_rn(mfac, qj);
     if (MIXED) reinterpret_cast<df2*>(s.q)[j] = df_from(qj);  // double-float copy for the gather
     else s.q[j] = qj;
     if (cache) {
+      const double kr = __dmul_rn(k, rfac);
       // d q_j / dT at fixed concentrations (without the third-body factor):
-      // k Pf d ln k/dT - kr Pb (d ln k/dT - d ln Kc/dT), with
-      // d ln Kc/dT = (sum_products h/RT - sum_reactants h/RT - dnu) / T.
-      const double dnud = dnu > 0 ? 1.0 : (dnu < 0 ? -1.0 : 0.0);
-      const double dlnKc = __dmul_rn(s.hRT[pa] + s.hRT[pb] - s.hRT[ra] - s.hRT[rb] - dnud, invT);
-      const double qT = fma(__dmul_rn(k, dlnk), Pf, -__dmul_rn(__dmul_rn(kr, dlnk - dlnKc), Pb));
+      // d ln k/dT q0 + d ln Kc/dT k prod C^nu''/Kc, q0 = k (prod C^nu' - prod C^nu''/Kc),
+      // with d ln Kc/dT = (sum_products h/RT - sum_reactants h/RT - dnu) / T
+      // summed from the per-species (h/RT - 1)/T
+      const double dlnKc = __dsub_rn(__dadd_rn(s.dC[pa], s.dC[pb]), __dadd_rn(s.dC[ra], s.dC[rb]));
+      const double qT = fma(dlnk, q0, __dmul_rn(dlnKc, __dmul_rn(k, Rb)));
       if (cs->prec == 3) {  // double-float copies for the J v core, in the same storage
         reinterpret_cast<df2*>(s.qT)[j] = df_from(qT);
         reinterpret_cast<df2*>(s.kc)[j] = df_from(k);
@@ -1809,6 +1823,7 @@ __device__ inline void init_sentinels(const SlotPtrs& s, int ns, int lane) {
     s.gRT[ns] = 0.0;
     s.E[ns] = 1.0;
     s.Einv[ns] = 1.0;
+    s.CE[ns] = 1.0;
     if (MIXED) {
       s.fC[ns] = 1.f;
       s.fdC[ns] = 0.f;
@@ -2364,6 +2379,21 @@ __global__ void probe_cvt_kernel(double* out, int iters) {
   }
   const double r = x0 + x1 + x2 + x3;
   if (r == 12345.678) out[0] = r;
+}
+// int -> double conversions (I2F.F64): eight chains of a conversion, a bit
+// move and an integer xor, with no FP64 arithmetic
+__global__ void probe_i2f_kernel(double* out, int iters) {
+  int k[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) k[j] = (int)threadIdx.x + 1000 * j;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) k[j] = __double2hiint((double)k[j]) ^ (k[j] + i);
+  }
+  int r = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) r ^= k[j];
+  if (r == 123456789) out[0] = (double)r;
 }
 __global__ void probe_exp_kernel(double* out, int iters) {
   double x0 = -threadIdx.x * 1e-6, x1 = x0 - 0.25, x2 = x0 - 0.5, x3 = x0 - 0.75;
@@ -3169,7 +3199,7 @@ int rk_rok4e_adjoint(const rk_mech* mech, const double* checkpoints, const doubl
 }
 
 int rk_probe_throughput(int32_t kind, double* ops_per_s) {
-  if (!ops_per_s || kind < 0 || kind > 7) return set_error(RK_E_INVALID_ARGUMENT, "bad probe arguments");
+  if (!ops_per_s || kind < 0 || kind > 8) return set_error(RK_E_INVALID_ARGUMENT, "bad probe arguments");
   int n_sm = 0;
   size_t smem = 0;
   int rc = device_props(&n_sm, &smem);
@@ -3181,7 +3211,7 @@ int rk_probe_throughput(int32_t kind, double* ops_per_s) {
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   const int threads = 512, blocks = n_sm * 4;
-  const int iters = kind == 2 ? 2000 : (kind == 0 ? 20000 : (kind == 3 ? 20000 : 200000));
+  const int iters = kind == 2 ? 2000 : (kind == 0 ? 20000 : (kind == 3 || kind == 8 ? 20000 : 200000));
   double ops = 0.0;
   float ms = 0.f;
   for (int rep = 0; rep < 2; ++rep) {  // first launch warms up
@@ -3204,6 +3234,9 @@ int rk_probe_throughput(int32_t kind, double* ops_per_s) {
     } else if (kind == 7) {
       probe_df_kernel<<<2 * n_sm, 512>>>((float*)buf, iters, 0.9999f, 1e-9f);
       ops = (double)2 * n_sm * 512 * iters * 4.0;
+    } else if (kind == 8) {
+      probe_i2f_kernel<<<blocks, threads>>>((double*)buf, iters);
+      ops = (double)blocks * threads * iters * 8.0;
     } else {
       probe_cvt_kernel<<<blocks, threads>>>((double*)buf, iters);
       ops = (double)blocks * threads * iters * 8.0;  // conversions

@@ -4,8 +4,8 @@ generator's output, every entry is the correctly rounded value of its
 definition (60-digit decimal arithmetic), and the logarithm's method with
 this table -- emulated on the host with exactly rounded fma -- stays within
 the bound the GPU test applies to the kernel (3 ulp or 2.5e-16 absolute).
-The exponential's method with its table stays within 2 ulp of the exact
-value, and the kernels' Newton reciprocal, emulated the same way from a
+The exponential's method (256-entry table, degree-4 polynomial) with its
+table stays within 2 ulp of the exact value, and the kernels' Newton reciprocal, emulated the same way from a
 correctly rounded FP32 estimate, within 1 ulp of the IEEE quotient."""
 
 import importlib.util
@@ -62,16 +62,17 @@ def test_table_entries_are_correctly_rounded():
 def _check_entries():
     _, exp_vals, inv_c, ln_c, c = _header()
     ln2 = Decimal(2).ln()
-    assert len(exp_vals) == len(inv_c) == len(ln_c) == 128
+    assert len(exp_vals) == 256 and len(inv_c) == len(ln_c) == 128
+    for j in range(256):
+        assert _is_correctly_rounded(exp_vals[j], (ln2 * j / 256).exp())
     for j in range(128):
-        assert _is_correctly_rounded(exp_vals[j], (ln2 * j / 128).exp())
         assert _is_correctly_rounded(inv_c[j], 1 / (1 + (Decimal(j) + Decimal("0.5")) / 128))
         assert _is_correctly_rounded(ln_c[j], -Decimal(inv_c[j]).ln())
     # ln 2 split: the head has 32 trailing zero bits (e * head exact for |e| < 2^20)
     assert Fraction(c["RK_LN2_HI"]).denominator <= 2 ** 21
     assert abs(Decimal(c["RK_LN2_HI"]) + Decimal(c["RK_LN2_LO"]) - ln2) < Decimal(2) ** -75
-    assert Fraction(c["RK_LN2_OVER_N_HI"]).denominator <= 2 ** 28
-    assert abs(Decimal(c["RK_LN2_OVER_N_HI"]) + Decimal(c["RK_LN2_OVER_N_LO"]) - ln2 / 128) < Decimal(2) ** -82
+    assert Fraction(c["RK_LN2_OVER_N_HI"]).denominator <= 2 ** 29
+    assert abs(Decimal(c["RK_LN2_OVER_N_HI"]) + Decimal(c["RK_LN2_OVER_N_LO"]) - ln2 / 256) < Decimal(2) ** -83
     assert _is_correctly_rounded(c["RK_INV_LN10"], 1 / Decimal(10).ln())
 
 
@@ -137,21 +138,20 @@ def test_newton_reciprocal_method_within_one_ulp():
 
 def _exp_method(x, tab, c):
     """Tang's table-driven exp with the kernel's steps, each rounded once:
-    k = round(x 128 / ln2) by the 1.5 2^52 shifter, r = x - k ln2/128 in two
-    parts, e^r - 1 = r + r^2 (1/2 + r/6 + r^2/24 + r^3/120), 2^(k/128) from the
-    table and 2^(k >> 7) by exponent scaling."""
+    k = round(x 256 / ln2) by the 1.5 2^52 shifter, r = x - k ln2/256 in two
+    parts, e^r - 1 = r + r^2 (1/2 + r/6 + r^2/24), 2^(k/256) from the table and
+    2^(k >> 8) by exponent scaling."""
     shifter = 6755399441055744.0
     kt = _fma(x, c["RK_N_OVER_LN2"], shifter)
     k = int(kt - shifter)
     kd = kt - shifter
     r = _fma(-kd, c["RK_LN2_OVER_N_HI"], x)
     r = _fma(-kd, c["RK_LN2_OVER_N_LO"], r)
-    q = _fma(r, 1.0 / 120.0, 1.0 / 24.0)
-    q = _fma(q, r, 1.0 / 6.0)
+    q = _fma(r, 1.0 / 24.0, 1.0 / 6.0)
     q = _fma(q, r, 0.5)
     p = _fma(r * r, q, r)
-    t = tab[k & 127]
-    return math.ldexp(_fma(t, p, t), k >> 7)
+    t = tab[k & 255]
+    return math.ldexp(_fma(t, p, t), k >> 8)
 
 
 def test_exp_method_within_two_ulp():
