@@ -48,7 +48,7 @@ D_DIFF = 1.0e-4  # m^2/s
 LENGTH = 1.0e-2  # m
 P_ATM = 101325.0
 L2_FLUSH_BYTES = 256 << 20
-PREC = {"fp64": 0, "mixed": 1, "mixed-fp32jv": 2, "mixed-df": 3}
+PREC = {"fp64": 0, "mixed": 1, "mixed-fp32jv": 2, "mixed-df": 3, "tensor": 4}
 FP64_PEAK = 1.25  # TFLOP/s: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal)
 GOLDEN = 0.6180339887498949
 
@@ -586,7 +586,7 @@ def run_flame(args, dev, precision, extras=True):
     attempts = float((st[:, :, 0] + st[:, :, 1]).sum())
     out = {"workload": "flame1d: 1-D reaction-diffusion, 2048 points on 1 cm, 30 species / 150 reactions "
                        "(4 third-body, 2 Troe), Simpler split steps of 1e-7 s, ROK4E M=4, rtol 1e-6, atol 1e-10",
-           "precision": {0: "fp64", 1: "mixed", 2: "mixed-fp32jv", 3: "mixed-df"}[precision],
+           "precision": {v: k for k, v in PREC.items()}[precision],
            "value": value, "unit": "cell-steps/s", "steps": K, "warmup": args.warmup,
            "steps_window": f"split steps {args.warmup + 1}..{args.warmup + K} from the initial tanh field",
            "ms_per_step": 1e3 * t_total / K, "attempts_per_s": attempts / t_total,
@@ -597,8 +597,9 @@ def run_flame(args, dev, precision, extras=True):
            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK, "unit": "TFLOP/s",
                         "frac": achieved / FP64_PEAK, "traffic": TRAFFIC["flame1d"] if precision == 0 else None,
                         "algorithmic_bytes_per_launch": int(npts * N * 8 * 3 + npts * (16 + 16)),
-                        "kernel": "rok4e_integrate_kernel<32, 0>" if precision in (0, 3) else
-                                  "rok4e_integrate_kernel<32, 1>",
+                        "kernel": {0: "rok4e_integrate_kernel<32, 0, 0>", 3: "rok4e_integrate_kernel<32, 0, 0>",
+                                   4: "rok4e_integrate_kernel<32, 0, 1>"}.get(precision,
+                                                                              "rok4e_integrate_kernel<32, 1, 0>"),
                         "kernel_ms_per_step": 1e3 * kern_total / K},
            "cuda_graph": {"timed_region": "one captured split step replayed per step",
                           "matches_eager_bitwise": graph_matches_eager},
@@ -707,9 +708,11 @@ def run_batched_levels(args, dev, M, lanes, cpb):
     U0 = torch.tensor(U_host, device=dev)
     ws = torch.empty(rk.rok4e_workspace_size(m, n, M), dtype=torch.uint8, device=dev)
     out = {"cells": n, "krylov_dim": M, "steps": args.level_steps}
-    for name in ("fp64", "mixed", "mixed-fp32jv", "mixed-df"):
+    for name in ("fp64", "mixed", "mixed-fp32jv", "mixed-df", "tensor"):
         prec = PREC[name]
         kw = dict(lanes_per_cell=lanes, cells_per_block=cpb, precision=prec, queue_order=args.queue_order)
+        if name == "tensor":  # one cell per warp; the nu^T tiles take shared memory: as many cells as fit
+            kw.update(lanes_per_cell=32, cells_per_block=0)
         Y = U0.clone()
         hc = torch.zeros(n, dtype=torch.float64, device=dev)
         st = torch.zeros(n, 4, dtype=torch.int32, device=dev)
@@ -741,7 +744,7 @@ def run_batched_levels(args, dev, M, lanes, cpb):
         out[name] = {"value": n * args.level_steps / t, "unit": "cell-steps/s",
                      "attempts_per_cell_step": float(att.mean()), "cells_failed": int((s_np[:, 3] != 0).sum()),
                      "accuracy": acc}
-    for name in ("mixed", "mixed-fp32jv", "mixed-df"):
+    for name in ("mixed", "mixed-fp32jv", "mixed-df", "tensor"):
         out[name]["vs_fp64"] = out[name]["value"] / out["fp64"]["value"]
     return out
 
@@ -847,6 +850,19 @@ def run_adjoint(args, dev):
             tf.append(ev[0].elapsed_time(ev[1]) * 1e-3)
             tb.append(ev[1].elapsed_time(ev[2]) * 1e-3)
     t_f, t_b = statistics.mean(tf), statistics.mean(tb)
+    # the adjoint alone at each lane count (one cell per 8, 16 or 32 lanes)
+    sweep = {}
+    for G in (8, 16, 32):
+        ts = []
+        for rep in range(2):
+            ev[1].record(stream)
+            g_G, _ = rk.rok4e_adjoint(m, ck, ubar, h, nsteps, M, workspace=wsb, lanes_per_cell=G)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            if rep > 0:
+                ts.append(ev[1].elapsed_time(ev[2]) * 1e-3)
+        sweep[str(G)] = {"adjoint_s": min(ts),
+                         "max_rel_diff_vs_auto": float((g_G - grad).abs().max() / grad.abs().max())}
     d = np.random.default_rng(7).normal(size=mech.n_reactions)
     d /= np.linalg.norm(d)
     # central differences along d on the GPU, per cell, at h = 1e-6 and 1e-7
@@ -893,7 +909,7 @@ def run_adjoint(args, dev):
     return {"workload": "adjoint: 4096 cells, 100 species / 500 reactions, 50 fixed ROK4E steps of 1e-7 s, "
                         "M=4; gradient of sum_c T_c(final) w.r.t. all 500 ln A_j",
             "value": n * nsteps / (t_f + t_b), "unit": "cell-steps/s (forward with checkpoints + adjoint)",
-            "forward_s": t_f, "adjoint_s": t_b, "reps": len(tf),
+            "forward_s": t_f, "adjoint_s": t_b, "reps": len(tf), "adjoint_lanes_per_cell": sweep,
             "kernels": "rok4e_integrate_kernel (fixed steps), rok4e_adjoint_kernel, adjoint_reduce_kernel",
             "gradient_check": {
                 "direction": "random unit vector in ln A (seed 7)",
@@ -964,6 +980,22 @@ def run_plain(args):
     import paper_1712_00953_gb300 as rk
     from synth.fields import WORKLOADS, field_tanh_front, mechanism_for
 
+    if args.workload == "adjoint":
+        from synth.fields import initial_state
+
+        w = WORKLOADS["adjoint"]
+        m = rk.mech_load(mechanism_for(w))
+        U = torch.tensor(initial_state(w)[: args.plain_cells], device="cuda")
+        n, N = U.shape
+        ck = torch.empty(w.n_steps + 1, n, N, dtype=torch.float64, device="cuda")
+        rk.rok4e_fixed_steps(m, U, w.dt, w.n_steps, w.krylov_dim, checkpoints=ck)
+        ubar = torch.zeros_like(U)
+        ubar[:, -1] = 1.0
+        for _ in range(max(1, args.plain_steps)):
+            grad, _ = rk.rok4e_adjoint(m, ck, ubar, w.dt, w.n_steps, w.krylov_dim, lanes_per_cell=args.lanes)
+        torch.cuda.synchronize()
+        print(json.dumps({"plain_steps": args.plain_steps, "cells": n, "grad_max": float(grad.abs().max())}))
+        return 0
     if args.workload == "batched":
         w = WORKLOADS["batched"]
         m = rk.mech_load(mechanism_for(w))
@@ -1119,7 +1151,7 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and not args.headline_only:
         configs = {"small": run_small(args, dev), "flame1d": run_flame(args, dev, 0)}
         mixed = {}
-        for name in ("mixed", "mixed-fp32jv", "mixed-df"):
+        for name in ("mixed", "mixed-fp32jv", "mixed-df", "tensor"):
             mixed[name] = run_flame(args, dev, PREC[name], extras=False)
         mixed["note"] = ("the flame1d workload at each precision level against its FP64 value "
                          f"{configs['flame1d']['value']:.0f} cell-steps/s; accuracy against the FP64 oracle")
@@ -1166,7 +1198,7 @@ def main():
                     help="efficiency study on a variant of the batched mechanism with this cap on k C (1/s)")
     ap.add_argument("--study", default="", choices=["", "efficiency"],
                     help="efficiency: the ROK4E M / J v mode / explicit RK comparison over h_CFL")
-    ap.add_argument("--workload", default="batched", choices=["batched", "flame1d"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "flame1d", "adjoint"],
                     help="profiling case of --plain-steps")
     ap.add_argument("--blocks-per-sm", type=int, default=0, help="resident blocks per SM (0: all that fit)")
     args = ap.parse_args()

@@ -132,7 +132,9 @@ int rk_chem_rhs(const rk_mech* mech, const double* Y, const double* src, double 
  * the matrix-free products of Sec. 4.3; mode 2: the analytic product
  * evaluated in FP32 (the mixed-precision integrator's J v); mode 3: the
  * analytic product with its reaction-level core in double-float (precision
- * level 3).  All arrays device [ncell x N]. */
+ * level 3); mode 4: the analytic product with nu^T dq formed on the tensor
+ * cores as in rk_chem_rhs_tc (precision level 4).  All arrays device
+ * [ncell x N]. */
 int rk_chem_jvp(const rk_mech* mech, const double* Y, const double* V, double p, double* JV,
                 int64_t ncell, int32_t mode, void* stream);
 
@@ -158,6 +160,19 @@ int rk_chem_jvp_cv(const rk_mech* mech, const double* Y, const double* V, const 
  * 1.2e-38 drop out of w. */
 int rk_chem_rhs_mixed(const rk_mech* mech, const double* Y, const double* src, double p,
                       double* dYdt, int64_t ncell, void* stream);
+
+/* Tensor-core source term (the right-hand side of precision level 4): as
+ * rk_chem_rhs, with w = nu^T q formed by BF16 mma.  Each cell's rates q_j are
+ * cut, relative to a power of two 2^Es above the cell's largest |q_j|, into
+ * seven signed 8-bit digits (all of q_j above 2^(Es - 56)); the net
+ * coefficients (small integers) and the digits are exact in BF16, every
+ * product and every FP32 accumulation of the mma is exact, and FP64 adds the
+ * seven scaled digit sums of each species.  So w_k carries no error beyond
+ * the dropped tails, at most 2^-55 of the cell's largest rate per reaction,
+ * and the six FP64 additions.  A cell whose rates are all below 2^-920
+ * gathers in FP64 instead.  Every other step as in rk_chem_rhs. */
+int rk_chem_rhs_tc(const rk_mech* mech, const double* Y, const double* src, double p,
+                   double* dYdt, int64_t ncell, void* stream);
 
 /* ---- ROK4E integration (Sec. 4, Algorithm 1) ---------------------------------
  * Options; pass NULL for defaults (all zero fields mean "default"). */
@@ -185,7 +200,11 @@ typedef struct rk_opts {
                              polynomial tails in FP32 (~1e-12 relative); the
                              Jacobian-vector product's reaction-level core
                              (d(C_a C_b), dq, nu^T dq) in double-float (FP32
-                             pairs, ~44-bit significands) on the FP32 pipe */
+                             pairs, ~44-bit significands) on the FP32 pipe.
+                             4: FP64 throughout except w = nu^T q (in the
+                             right-hand side and the Jacobian-vector product),
+                             which is formed on the tensor cores as in
+                             rk_chem_rhs_tc; needs lanes_per_cell 0 or 32 */
   double* trace;          /* device [ncell x trace_cap]: +h accepted, -h rejected, 0 unused */
   void* ev_begin;         /* optional cudaEvent_t recorded on the stream right before the */
   void* ev_end;           /* integration kernel and right after it (timing hook), or NULL;
@@ -404,11 +423,21 @@ int rk_rok4e_fixed_steps(const rk_mech* mech, double* Y, int64_t ncell, double p
  * including the dependence of the Arnoldi basis on the state and on ln A
  * (second derivatives of the source term).  The paper has no adjoint; this is
  * the library's sensitivity extension of its integrator.  Workspace:
- * rk_rok4e_adjoint_workspace_size (about (60 N + 8 Nr) doubles per cell). */
+ * rk_rok4e_adjoint_workspace_size (about (60 N + 12 Nr) doubles per cell, one
+ * contiguous record per cell).  The sums over cells and within a cell have a
+ * fixed order: repeated calls give the same bits. */
 size_t rk_rok4e_adjoint_workspace_size(const rk_mech* mech, int64_t ncell, int32_t krylov_dim);
 int rk_rok4e_adjoint(const rk_mech* mech, const double* checkpoints, const double* ubar, int64_t ncell,
                      double p, double h, int32_t nsteps, int32_t krylov_dim, double* grad_lnA,
                      double* grad_u0, void* workspace, size_t workspace_bytes, void* stream);
+/* As rk_rok4e_adjoint, with lanes_per_cell lanes of a warp (8, 16 or 32)
+ * sharing each cell's species, reaction and state loops; 0 chooses from ncell
+ * (fewer lanes per cell when there are cells enough to fill the GPU).  The
+ * result does not depend on the lane count beyond rounding. */
+int rk_rok4e_adjoint_ex(const rk_mech* mech, const double* checkpoints, const double* ubar, int64_t ncell,
+                        double p, double h, int32_t nsteps, int32_t krylov_dim, int32_t lanes_per_cell,
+                        double* grad_lnA, double* grad_u0, void* workspace, size_t workspace_bytes,
+                        void* stream);
 
 /* ---- diagnostics ---------------------------------------------------------------
  * Throughput probes of the arithmetic units used by the roofline:

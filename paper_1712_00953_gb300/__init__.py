@@ -27,7 +27,7 @@ def _L():
         _LIB = _native.load()
     return _LIB
 
-__all__ = ["Mechanism", "mech_load", "mech_validate", "chem_rhs", "chem_rhs_mixed", "chem_rhs_cv", "chem_jvp_cv",
+__all__ = ["Mechanism", "mech_load", "mech_validate", "chem_rhs", "chem_rhs_mixed", "chem_rhs_tc", "chem_rhs_cv", "chem_jvp_cv",
            "chem_jvp", "rok4e_integrate", "rkdp_integrate", "chem_rhs_aux", "chem_jvp_aux", "AUX_EXTRA",
            "rok4e_workspace_size", "simpler_split_step", "simpler_split_step_workspace_size",
            "diffusion_1d", "diffusion_1d_ghost", "ssprk3_stage_ghost", "GhostTransport",
@@ -202,6 +202,15 @@ def chem_rhs_mixed(m: Mechanism, Y, p, src=None, out=None, stream=None):
     out = torch.empty_like(Y) if out is None else out
     _check(_L().rk_chem_rhs_mixed(m.handle, _dptr(Y, "Y"), _dptr(src, "src", Y.numel()), float(p),
                                   _dptr(out, "out", Y.numel()), n, _stream_ptr(stream)), "rk_chem_rhs_mixed")
+    return out
+
+
+def chem_rhs_tc(m: Mechanism, Y, p, src=None, out=None, stream=None):
+    """Source term with w = nu^T q formed on the tensor cores (rk_chem_rhs_tc)."""
+    n = _ncell(Y, m)
+    out = torch.empty_like(Y) if out is None else out
+    _check(_L().rk_chem_rhs_tc(m.handle, _dptr(Y, "Y"), _dptr(src, "src", Y.numel()), float(p),
+                               _dptr(out, "out", Y.numel()), n, _stream_ptr(stream)), "rk_chem_rhs_tc")
     return out
 
 
@@ -460,18 +469,19 @@ def rok4e_adjoint_workspace_size(m: Mechanism, ncell: int, krylov_dim: int) -> i
 
 
 def rok4e_adjoint(m: Mechanism, checkpoints, ubar, h, nsteps, krylov_dim=4, *, p=101325.0, grad_u0=None,
-                  workspace=None, stream=None):
-    """Discrete adjoint of rok4e_fixed_steps: returns (grad_lnA [Nr], grad_u0 [ncell, N] or None)."""
+                  workspace=None, stream=None, lanes_per_cell=0):
+    """Discrete adjoint of rok4e_fixed_steps: returns (grad_lnA [Nr], grad_u0 [ncell, N] or None).
+    lanes_per_cell: 8, 16 or 32 lanes per cell, 0 chosen from the cell count (rk_rok4e_adjoint_ex)."""
     n = _ncell(ubar, m)
     if workspace is None:
         workspace = torch.empty(rok4e_adjoint_workspace_size(m, n, krylov_dim), dtype=torch.uint8,
                                 device=ubar.device)
     grad = torch.empty(m.n_reactions, dtype=torch.float64, device=ubar.device)
-    _check(_L().rk_rok4e_adjoint(m.handle, _dptr(checkpoints, "checkpoints", (int(nsteps) + 1) * ubar.numel()),
-                                 _dptr(ubar, "ubar"), n, float(p), float(h), int(nsteps), int(krylov_dim),
-                                 _dptr(grad, "grad"), _dptr(grad_u0, "grad_u0", ubar.numel()),
-                                 _dptr(workspace, "workspace", dtype=torch.uint8), workspace.numel(),
-                                 _stream_ptr(stream)), "rk_rok4e_adjoint")
+    _check(_L().rk_rok4e_adjoint_ex(m.handle, _dptr(checkpoints, "checkpoints", (int(nsteps) + 1) * ubar.numel()),
+                                    _dptr(ubar, "ubar"), n, float(p), float(h), int(nsteps), int(krylov_dim),
+                                    int(lanes_per_cell), _dptr(grad, "grad"), _dptr(grad_u0, "grad_u0", ubar.numel()),
+                                    _dptr(workspace, "workspace", dtype=torch.uint8), workspace.numel(),
+                                    _stream_ptr(stream)), "rk_rok4e_adjoint_ex")
     return grad, grad_u0
 
 

@@ -1,7 +1,8 @@
 // Discrete adjoint of fixed-step ROK4E (Algorithm 1 with h held fixed) with
 // respect to the initial state and the log pre-exponential factors ln A_j.
 //
-// One thread integrates one cell backwards through the recorded steps.  For
+// A group of G lanes of one warp (G = 8, 16 or 32) integrates one cell
+// backwards through the recorded steps.  For
 // each step n (last first) it reloads u_n from the checkpoints, recomputes the
 // step's internals -- f_n, the Arnoldi basis Q and Hessenberg H (CGS2), the
 // inverse of L = I - h gamma H, the stage vectors -- and then propagates the
@@ -19,9 +20,19 @@
 // w_bar gives J^T w_bar in the values and grad_u (w_bar^T J v) (equal to the
 // directional derivative of J^T w_bar along v) in the tangents.
 //
-// Per-cell arrays live in a structure-of-arrays workspace (element e of cell c
-// at row e * ncell + c), so that the threads of a warp access consecutive
-// addresses.
+// The lanes of a group split every loop over the state, the species and the
+// reactions (element e belongs to lane e mod G in every per-element array, so
+// those arrays need no synchronisation between loops); sums are butterfly
+// reductions, which leave bit-identical values in all lanes, so every lane
+// holds the same scalars and small matrices, and lane 0 alone writes the
+// small matrices the group keeps in memory.  The reverse pass scatters the
+// cotangents of C and g/RT to species through a species-major list of the
+// reaction slots each species fills, so every sum has a fixed order and the
+// result does not depend on scheduling.
+//
+// Per-cell arrays live in a workspace record per cell (element e of array a
+// at offset a + e of the cell's record), so that a group's lanes access
+// consecutive addresses.
 #pragma once
 
 namespace rk {
@@ -67,8 +78,7 @@ __device__ __forceinline__ Dual dlog10(Dual a) { return Dual{log10(a.v), a.t / (
 template <typename T>
 struct Col {
   T* p;
-  int64_t s;
-  __device__ __forceinline__ T& operator[](int64_t e) const { return p[e * s]; }
+  __device__ __forceinline__ T& operator[](int64_t e) const { return p[e]; }
 };
 
 // Rows of the adjoint workspace (computed on the host).
@@ -79,7 +89,7 @@ struct AdjLayout {
       Lbar, Hbar, scal, theta;
   int rows_d;
   // dual rows
-  int ud, fd, C, cp, h, g, dcp, om, k, rfac, q, Ms, dlnk, dkdM, omg, sc, Cbar, gbar, ombar, Mbar, ubd, fbd;
+  int ud, fd, C, cp, h, g, dcp, om, k, rfac, q, Ms, dlnk, dkdM, omg, sc, Cbar, gbar, ombar, Mbar, ubd, fbd, Pbb, drf;
   int rows_D;
 };
 
@@ -88,13 +98,18 @@ struct AdjFrame {
   Col<double> u, fn, Q, K, F, arg1, arg2, ubar, Kbar, Qbar, fb2, fbn, wbar, w, w1, w2, tmp, H, p1, p2, hn, Linv,
       zs, ys, Lbar, Hbar, scal, theta;
   // duals
-  Col<Dual> ud, fd, C, cp, h, g, dcp, om, k, rfac, q, Ms, dlnk, dkdM, omg, sc, Cbar, gbar, ombar, Mbar, ubd, fbd;
+  // (in the reverse pass q holds d/d(prod C^nu') per reaction, Pbb d/d(prod C^nu''), drf the
+  // cotangent of ln(k_r/k_f) times k_r/k_f)
+  Col<Dual> ud, fd, C, cp, h, g, dcp, om, k, rfac, q, Ms, dlnk, dkdM, omg, sc, Cbar, gbar, ombar, Mbar, ubd, fbd,
+      Pbb, drf;
 };
 
-__device__ inline AdjFrame adj_frame(double* wsd, Dual* wsD, const AdjLayout& L, int64_t ncell, int64_t c) {
+__device__ inline AdjFrame adj_frame(double* wsd, Dual* wsD, const AdjLayout& L, int64_t c) {
   AdjFrame f;
-  auto D = [&](int row) { return Col<double>{wsd + (int64_t)row * ncell + c, ncell}; };
-  auto X = [&](int row) { return Col<Dual>{wsD + (int64_t)row * ncell + c, ncell}; };
+  double* bd = wsd + c * L.rows_d;
+  Dual* bD = wsD + c * L.rows_D;
+  auto D = [&](int row) { return Col<double>{bd + row}; };
+  auto X = [&](int row) { return Col<Dual>{bD + row}; };
   f.u = D(L.u); f.fn = D(L.fn); f.Q = D(L.Q); f.K = D(L.K); f.F = D(L.F); f.arg1 = D(L.arg1); f.arg2 = D(L.arg2);
   f.ubar = D(L.ubar); f.Kbar = D(L.Kbar); f.Qbar = D(L.Qbar); f.fb2 = D(L.fb2); f.fbn = D(L.fbn);
   f.wbar = D(L.wbar); f.w = D(L.w); f.w1 = D(L.w1); f.w2 = D(L.w2); f.tmp = D(L.tmp); f.H = D(L.H);
@@ -103,20 +118,29 @@ __device__ inline AdjFrame adj_frame(double* wsd, Dual* wsD, const AdjLayout& L,
   f.ud = X(L.ud); f.fd = X(L.fd); f.C = X(L.C); f.cp = X(L.cp); f.h = X(L.h); f.g = X(L.g); f.dcp = X(L.dcp);
   f.om = X(L.om); f.k = X(L.k); f.rfac = X(L.rfac); f.q = X(L.q); f.Ms = X(L.Ms); f.dlnk = X(L.dlnk);
   f.dkdM = X(L.dkdM); f.omg = X(L.omg); f.sc = X(L.sc); f.Cbar = X(L.Cbar); f.gbar = X(L.gbar);
-  f.ombar = X(L.ombar); f.Mbar = X(L.Mbar); f.ubd = X(L.ubd); f.fbd = X(L.fbd);
+  f.ombar = X(L.ombar); f.Mbar = X(L.Mbar); f.ubd = X(L.ubd); f.fbd = X(L.fbd); f.Pbb = X(L.Pbb); f.drf = X(L.drf);
   return f;
+}
+
+// sum of a dual over the group (all lanes receive the same bits)
+template <int G>
+__device__ __forceinline__ Dual gsum(const Grp<G>& g, Dual a) {
+  return Dual{g.sum(a.v), g.sum(a.t)};
 }
 
 enum { SC_T = 0, SC_INVT, SC_S, SC_RHO, SC_CB, SC_SH, SC_LNRTP, SC_N };
 
 // Forward pass of f on the dual state ud -> fd, keeping the tape.
+template <int G>
 __device__ void adj_rhs_fwd(const MechView& m, const AdjFrame& F, double p) {
-  const int ns = m.ns;
+  const Grp<G> g;
+  const int ns = m.ns, L = g.lane;
+  g.sync();  // ud complete
   const Dual T = F.ud[ns];
   const Dual invT = 1.0 / T;
   const Dual lnT = dlog(T);
   Dual S = dd(0.0);
-  for (int k = 0; k < ns; ++k) {
+  for (int k = L; k < ns; k += G) {
     const double* c = (T.v < m.Tmid[k]) ? m.lo : m.hi;
     const double a1 = c[k], a2 = c[ns + k], a3 = c[2 * ns + k], a4 = c[3 * ns + k], a5 = c[4 * ns + k];
     const Dual cp = (((a5 * T + a4) * T + a3) * T + a2) * T + a1;
@@ -130,18 +154,23 @@ __device__ void adj_rhs_fwd(const MechView& m, const AdjFrame& F, double p) {
     F.dcp[k] = ((c[16 * ns + k] * T + c[15 * ns + k]) * T + c[14 * ns + k]) * T + a2;
     S += F.ud[k] * m.invW[k];
   }
-  F.h[ns] = dd(0.0);
-  F.g[ns] = dd(0.0);
+  S = gsum(g, S);
   const Dual rho = p / (R_GAS * T * S);
-  for (int k = 0; k < ns; ++k) F.C[k] = rho * F.ud[k] * m.invW[k];
-  F.C[ns] = dd(1.0);
-  for (int t = 0; t < m.ntb; ++t) {
+  for (int k = L; k < ns; k += G) F.C[k] = rho * F.ud[k] * m.invW[k];
+  if (L == ns % G) {  // the empty reaction slot: C = 1, h = g = 0
+    F.h[ns] = dd(0.0);
+    F.g[ns] = dd(0.0);
+    F.C[ns] = dd(1.0);
+  }
+  g.sync();
+  for (int t = L; t < m.ntb; t += G) {
     Dual Mc = dd(0.0);
     for (int k = 0; k < ns; ++k) Mc += m.eff[(size_t)t * ns + k] * F.C[k];
     F.Ms[t] = Mc;
   }
+  g.sync();
   const Dual lnRTp = dlog(R_GAS * T / P_REF);
-  for (int j = 0; j < m.nr; ++j) {
+  for (int j = L; j < m.nr; j += G) {
     const uint32_t sl = m.slots[j];
     const int ra = sl & 255, rb = (sl >> 8) & 255, pa = (sl >> 16) & 255, pb = sl >> 24;
     const int meta = m.meta[j];
@@ -191,8 +220,9 @@ __device__ void adj_rhs_fwd(const MechView& m, const AdjFrame& F, double p) {
     F.rfac[j] = rfac;
     F.q[j] = mfac * (k * Pf - k * rfac * Pb);
   }
+  g.sync();
   Dual Sh = dd(0.0), cb = dd(0.0);
-  for (int k = 0; k < ns; ++k) {
+  for (int k = L; k < ns; k += G) {
     Dual om = dd(0.0);
     for (int e = m.csr_ptr[k]; e < m.csr_ptr[k + 1]; ++e) om += m.csr_nu[e] * F.q[m.csr_j[e]];
     F.om[k] = om;
@@ -200,42 +230,49 @@ __device__ void adj_rhs_fwd(const MechView& m, const AdjFrame& F, double p) {
     Sh += F.h[k] * om;
     cb += F.ud[k] * F.cp[k] * m.invW[k];
   }
-  F.fd[ns] = -1.0 * T * Sh / (rho * cb);
-  F.sc[SC_T] = T;
-  F.sc[SC_INVT] = invT;
-  F.sc[SC_S] = S;
-  F.sc[SC_RHO] = rho;
-  F.sc[SC_CB] = cb;
-  F.sc[SC_SH] = Sh;
-  F.sc[SC_LNRTP] = lnRTp;
+  Sh = gsum(g, Sh);
+  cb = gsum(g, cb);
+  if (L == ns % G) F.fd[ns] = -1.0 * T * Sh / (rho * cb);
+  if (L == 0) {
+    F.sc[SC_T] = T;
+    F.sc[SC_INVT] = invT;
+    F.sc[SC_S] = S;
+    F.sc[SC_RHO] = rho;
+    F.sc[SC_CB] = cb;
+    F.sc[SC_SH] = Sh;
+    F.sc[SC_LNRTP] = lnRTp;
+  }
+  g.sync();
 }
 
 // Reverse pass: ubd = J^T fbd on the tape of the last adj_rhs_fwd; the ln A
 // gradient is added to F.theta from the values (tangent = false) or from the
-// tangents (tangent = true) of the dual adjoint.
+// tangents (tangent = true) of the dual adjoint.  Each lane takes its
+// reactions' cotangents (stored per reaction), then its species gather them
+// through the species-major slot list.
+template <int G>
 __device__ void adj_rhs_rev(const MechView& m, const AdjFrame& F, bool tangent) {
-  const int ns = m.ns;
+  const Grp<G> g;
+  const int ns = m.ns, L = g.lane;
+  g.sync();  // fbd and the tape complete
   const Dual T = F.sc[SC_T], invT = F.sc[SC_INVT], S = F.sc[SC_S], rho = F.sc[SC_RHO];
   const Dual cb = F.sc[SC_CB], Sh = F.sc[SC_SH];
   const Dual fTb = F.fbd[ns];
   const Dual rcb = rho * cb;
-  Dual Tbar = -1.0 * Sh / rcb * fTb;
+  const Dual Tbar0 = -1.0 * Sh / rcb * fTb;
   const Dual Shbar = -1.0 * T / rcb * fTb;
-  Dual rhobar = T * Sh / (rho * rcb) * fTb;
+  const Dual rhobar0 = T * Sh / (rho * rcb) * fTb;
   const Dual cbbar = T * Sh / (rcb * cb) * fTb;
-  for (int k = 0; k < ns; ++k) {
+  Dual rhobar_l = dd(0.0);  // this lane's share of rho_bar
+  for (int k = L; k < ns; k += G) {
     F.ombar[k] = m.W[k] / rho * F.fbd[k] + F.h[k] * Shbar;
-    rhobar -= m.W[k] * F.om[k] / (rho * rho) * F.fbd[k];
-    F.Cbar[k] = dd(0.0);
-    F.gbar[k] = dd(0.0);
+    rhobar_l -= m.W[k] * F.om[k] / (rho * rho) * F.fbd[k];
   }
-  F.ombar[ns] = dd(0.0);
-  F.Cbar[ns] = dd(0.0);
-  F.gbar[ns] = dd(0.0);
-  for (int t = 0; t < m.ntb; ++t) F.Mbar[t] = dd(0.0);
-  const Dual lnRTp_unused = F.sc[SC_LNRTP];
-  (void)lnRTp_unused;
-  for (int j = 0; j < m.nr; ++j) {
+  if (L == ns % G) F.ombar[ns] = dd(0.0);
+  for (int t = L; t < m.ntb; t += G) F.Mbar[t] = dd(0.0);
+  g.sync();
+  Dual Tbar_l = dd(0.0);  // this lane's share of T_bar
+  for (int j = L; j < m.nr; j += G) {
     const uint32_t sl = m.slots[j];
     const int ra = sl & 255, rb = (sl >> 8) & 255, pa = (sl >> 16) & 255, pb = sl >> 24;
     const int meta = m.meta[j];
@@ -251,54 +288,67 @@ __device__ void adj_rhs_rev(const MechView& m, const AdjFrame& F, bool tangent) 
     const Dual kr = k * rfac;
     const Dual qm = qbar * mfac;
     const Dual kbar = qm * (Pf - rfac * Pb);
-    const Dual Pfbar = qm * k;
-    const Dual Pbbar = -1.0 * qm * kr;
-    if (kind == 1) F.Mbar[slot] += qbar * (k * Pf - kr * Pb);
-    F.Cbar[ra] += Pfbar * F.C[rb];
-    F.Cbar[rb] += Pfbar * F.C[ra];
-    F.Cbar[pa] += Pbbar * F.C[pb];
-    F.Cbar[pb] += Pbbar * F.C[pa];
+    if (kind == 1) F.Mbar[slot] += qbar * (k * Pf - kr * Pb);  // slots are one per reaction
+    F.q[j] = qm * k;          // d/d(prod C^nu')
+    F.Pbb[j] = -1.0 * qm * kr;  // d/d(prod C^nu'')
+    Dual drf = dd(0.0);
     if (rev) {
-      const Dual drf = rfac * (-1.0 * qm * k * Pb);  // rfac * rfac_bar
-      F.gbar[pa] += drf;
-      F.gbar[pb] += drf;
-      F.gbar[ra] -= drf;
-      F.gbar[rb] -= drf;
-      Tbar += (double)dnu * drf * invT;
+      drf = rfac * (-1.0 * qm * k * Pb);  // rfac * rfac_bar
+      Tbar_l += (double)dnu * drf * invT;
     }
+    F.drf[j] = drf;
     const Dual kk = k * kbar;
     Dual th;
     if (kind == 2) {
-      Tbar += kk * F.dlnk[slot];
+      Tbar_l += kk * F.dlnk[slot];
       F.Mbar[slot] += kbar * F.dkdM[slot];
       th = kk * F.omg[slot];
     } else {
-      Tbar += kk * ((m.bexp[j] + m.EaR[j] * invT) * invT);
+      Tbar_l += kk * ((m.bexp[j] + m.EaR[j] * invT) * invT);
       th = kk;
     }
     F.theta[j] += tangent ? th.t : th.v;
   }
-  for (int t = 0; t < m.ntb; ++t)
-    for (int k = 0; k < ns; ++k) F.Cbar[k] += m.eff[(size_t)t * ns + k] * F.Mbar[t];
-  for (int k = 0; k < ns; ++k) rhobar += F.ud[k] * m.invW[k] * F.Cbar[k];
-  Tbar -= rho * invT * rhobar;
+  g.sync();
+  for (int k = L; k < ns; k += G) {
+    Dual cbar = dd(0.0), gbar = dd(0.0);
+    for (int i = m.role_ptr[k]; i < m.role_ptr[k + 1]; ++i) {
+      const int e = m.role[i], j = e >> 2, role = e & 3;
+      // the other factor of the same product: ra <-> rb, pa <-> pb
+      const int other = (m.slots[j] >> (8 * (role ^ 1))) & 255;
+      cbar += (role < 2 ? F.q[j] : F.Pbb[j]) * F.C[other];
+      gbar = role < 2 ? gbar - F.drf[j] : gbar + F.drf[j];
+    }
+    for (int t = 0; t < m.ntb; ++t) cbar += m.eff[(size_t)t * ns + k] * F.Mbar[t];
+    F.Cbar[k] = cbar;
+    F.gbar[k] = gbar;
+    rhobar_l += F.ud[k] * m.invW[k] * cbar;
+  }
+  const Dual rhobar = rhobar0 + gsum(g, rhobar_l);
+  Dual Tbar = Tbar0 + gsum(g, Tbar_l) - rho * invT * rhobar;
   const Dual Sbar = -1.0 * rho / S * rhobar;
-  for (int k = 0; k < ns; ++k) {
+  Dual T2_l = dd(0.0);
+  for (int k = L; k < ns; k += G) {
     const Dual Yb = F.cp[k] * m.invW[k] * cbbar + rho * m.invW[k] * F.Cbar[k] + Sbar * m.invW[k];
     F.ubd[k] = Yb;
     const Dual cpbar = F.ud[k] * m.invW[k] * cbbar;
     const Dual hbar = F.om[k] * Shbar;
-    Tbar += cpbar * F.dcp[k] + hbar * (F.cp[k] - F.h[k]) * invT - F.gbar[k] * F.h[k] * invT;
+    T2_l += cpbar * F.dcp[k] + hbar * (F.cp[k] - F.h[k]) * invT - F.gbar[k] * F.h[k] * invT;
   }
-  F.ubd[ns] = Tbar;
+  Tbar += gsum(g, T2_l);
+  if (L == ns % G) F.ubd[ns] = Tbar;
+  g.sync();
 }
 
 }  // namespace rk
 
 namespace rk {
 
-// Explicit inverse of I - h gamma H (m x m) by Gauss-Jordan with partial pivoting.
+// Explicit inverse of I - h gamma H (m x m) by Gauss-Jordan with partial
+// pivoting; every lane of the group computes it (same bits), lane 0 stores it.
+template <int G>
 __device__ inline void adj_small_inverse(const AdjFrame& F, int md, double h) {
+  const Grp<G> g;
   double A[MAXM][MAXM], B[MAXM][MAXM];
   for (int r = 0; r < md; ++r)
     for (int c = 0; c < md; ++c) {
@@ -328,170 +378,187 @@ __device__ inline void adj_small_inverse(const AdjFrame& F, int md, double h) {
       }
     }
   }
-  for (int r = 0; r < md; ++r)
-    for (int c = 0; c < md; ++c) F.Linv[r * MAXM + c] = B[r][c];
+  if (g.lane == 0)
+    for (int r = 0; r < md; ++r)
+      for (int c = 0; c < md; ++c) F.Linv[r * MAXM + c] = B[r][c];
+  g.sync();
 }
 
-__device__ inline void adj_load_ud(const AdjFrame& F, int N, const Col<double>& x, const Col<double>* tan,
-                                   int64_t toff) {
-  for (int e = 0; e < N; ++e) F.ud[e] = Dual{x[e], tan ? (*tan)[toff + e] : 0.0};
+template <int G>
+__device__ inline void adj_load_ud(const AdjFrame& F, int N, const Col<double>& x, const double* tan) {
+  const Grp<G> g;
+  for (int e = g.lane; e < N; e += G) F.ud[e] = Dual{x[e], tan ? tan[e] : 0.0};
 }
 
 // Forward recomputation and reverse sweep of one fixed ROK4E step of size h
 // from F.u; on entry F.ubar holds the adjoint of the step's result, on exit
 // that of F.u; the ln A gradient accumulates in F.theta.
+template <int G>
 __device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double h, int M) {
-  const int ns = m.ns, N = ns + 1;
+  const Grp<G> g;
+  const int ns = m.ns, N = ns + 1, L = g.lane;
   constexpr double g21 = G21 / GAM, g31 = G31 / GAM, g32 = G32 / GAM;
   constexpr double g41 = G41 / GAM, g42 = G42 / GAM, g43 = G43 / GAM;
   const double gij[4][3] = {{0, 0, 0}, {g21, 0, 0}, {g31, g32, 0}, {g41, g42, g43}};
   const double bj[4] = {B1, B2, B3, B4};
   if (M > N) M = N;
+  double* Q = &F.Q[0];
   // ---------------------------------------------------------------- forward
-  adj_load_ud(F, N, F.u, nullptr, 0);
-  adj_rhs_fwd(m, F, p);
+  adj_load_ud<G>(F, N, F.u, nullptr);
+  adj_rhs_fwd<G>(m, F, p);
   double beta2 = 0.0;
-  for (int e = 0; e < N; ++e) {
+  for (int e = L; e < N; e += G) {
     F.fn[e] = F.fd[e].v;
     beta2 = fma(F.fn[e], F.fn[e], beta2);
   }
-  const double beta = sqrt(beta2);
-  for (int i = 0; i < MAXM * MAXM; ++i) F.H[i] = 0.0;
+  const double beta = sqrt(g.sum(beta2));
+  if (L == 0)
+    for (int i = 0; i < MAXM * MAXM; ++i) F.H[i] = 0.0;
   int md = 0;
   if (M > 0 && beta > 0.0 && isfinite(beta)) {
     md = M;
-    for (int e = 0; e < N; ++e) F.Q[e] = F.fn[e] / beta;
+    for (int e = L; e < N; e += G) Q[e] = F.fn[e] / beta;
     for (int j = 0; j < M; ++j) {
-      adj_load_ud(F, N, F.u, &F.Q, (int64_t)j * N);
-      adj_rhs_fwd(m, F, p);
+      adj_load_ud<G>(F, N, F.u, Q + (int64_t)j * N);
+      adj_rhs_fwd<G>(m, F, p);
       double w0 = 0.0;
-      for (int e = 0; e < N; ++e) {
+      for (int e = L; e < N; e += G) {
         F.w[e] = F.fd[e].t;
         w0 = fma(F.w[e], F.w[e], w0);
       }
-      w0 = sqrt(w0);
+      w0 = sqrt(g.sum(w0));
       for (int pass = 0; pass < 2; ++pass) {
         double pc[MAXM];
         for (int i = 0; i <= j; ++i) {
           double d = 0.0;
-          for (int e = 0; e < N; ++e) d = fma(F.Q[(int64_t)i * N + e], F.w[e], d);
-          pc[i] = d;
+          for (int e = L; e < N; e += G) d = fma(Q[(int64_t)i * N + e], F.w[e], d);
+          pc[i] = g.sum(d);
         }
-        for (int e = 0; e < N; ++e) {
+        for (int e = L; e < N; e += G) {
           double we = F.w[e];
-          for (int i = 0; i <= j; ++i) we = fma(-pc[i], F.Q[(int64_t)i * N + e], we);
+          for (int i = 0; i <= j; ++i) we = fma(-pc[i], Q[(int64_t)i * N + e], we);
           F.w[e] = we;
         }
-        for (int i = 0; i <= j; ++i) {
-          F.H[i * MAXM + j] += pc[i];
-          (pass == 0 ? F.p1 : F.p2)[j * MAXM + i] = pc[i];
-        }
+        if (L == 0)
+          for (int i = 0; i <= j; ++i) {
+            F.H[i * MAXM + j] += pc[i];
+            (pass == 0 ? F.p1 : F.p2)[j * MAXM + i] = pc[i];
+          }
       }
       double hn = 0.0;
-      for (int e = 0; e < N; ++e) hn = fma(F.w[e], F.w[e], hn);
-      hn = sqrt(hn);
+      for (int e = L; e < N; e += G) hn = fma(F.w[e], F.w[e], hn);
+      hn = sqrt(g.sum(hn));
       if (j + 1 == M) break;
       if (hn <= BREAKDOWN_TOL * w0 || hn == 0.0) {
         md = j + 1;
         break;
       }
-      F.H[(j + 1) * MAXM + j] = hn;
-      F.hn[j] = hn;
-      for (int e = 0; e < N; ++e) F.Q[(int64_t)(j + 1) * N + e] = F.w[e] / hn;
+      if (L == 0) {
+        F.H[(j + 1) * MAXM + j] = hn;
+        F.hn[j] = hn;
+      }
+      for (int e = L; e < N; e += G) Q[(int64_t)(j + 1) * N + e] = F.w[e] / hn;
     }
   }
-  if (md > 0) adj_small_inverse(F, md, h);
+  g.sync();  // H, p1, p2, hn from lane 0
+  if (md > 0) adj_small_inverse<G>(F, md, h);
   // stages
   for (int i = 0; i < 4; ++i) {
-    const Col<double> Ki{F.K.p + (int64_t)i * N * F.K.s, F.K.s};
-    const Col<double> Fi{F.F.p + (int64_t)i * N * F.F.s, F.F.s};
+    double* Ki = &F.K[(int64_t)i * N];
+    double* Fi = &F.F[(int64_t)i * N];
     if (i == 1 || i == 2) {
       const Col<double>& arg = (i == 1) ? F.arg1 : F.arg2;
-      for (int e = 0; e < N; ++e) {
+      for (int e = L; e < N; e += G) {
         const double acc = (i == 1) ? A21 * F.K[e] : fma(A32, F.K[(int64_t)N + e], A31 * F.K[e]);
         arg[e] = F.u[e] + h * acc;
       }
-      adj_load_ud(F, N, arg, nullptr, 0);
-      adj_rhs_fwd(m, F, p);
-      for (int e = 0; e < N; ++e) F.tmp[e] = F.fd[e].v;  // f_i (kept for stage 4)
+      adj_load_ud<G>(F, N, arg, nullptr);
+      adj_rhs_fwd<G>(m, F, p);
+      for (int e = L; e < N; e += G) F.tmp[e] = F.fd[e].v;  // f_i (kept for stage 4)
     }
     double z[MAXM];
     for (int l = 0; l < MAXM; ++l) z[l] = 0.0;
-    for (int e = 0; e < N; ++e) {
+    for (int e = L; e < N; e += G) {
       double Ge = 0.0;
       for (int j = 0; j < i; ++j) Ge = fma(gij[i][j], F.K[(int64_t)j * N + e], Ge);
       const double fe = (i == 0) ? F.fn[e] : F.tmp[e];
       Fi[e] = fe + Ge;
       F.w2[e] = Ge;
-      for (int l = 0; l < md; ++l) z[l] = fma(F.Q[(int64_t)l * N + e], Fi[e], z[l]);
+      for (int l = 0; l < md; ++l) z[l] = fma(Q[(int64_t)l * N + e], Fi[e], z[l]);
     }
+    for (int l = 0; l < md; ++l) z[l] = g.sum(z[l]);
     double y[MAXM];
     for (int r = 0; r < md; ++r) {
       double acc = 0.0;
       for (int c = 0; c < md; ++c) acc = fma(F.Linv[r * MAXM + c], z[c], acc);
       y[r] = acc;
     }
-    for (int l = 0; l < md; ++l) {
-      F.zs[i * MAXM + l] = z[l];
-      F.ys[i * MAXM + l] = y[l];
-    }
-    for (int e = 0; e < N; ++e) {
+    if (L == 0)
+      for (int l = 0; l < md; ++l) {
+        F.zs[i * MAXM + l] = z[l];
+        F.ys[i * MAXM + l] = y[l];
+      }
+    for (int e = L; e < N; e += G) {
       double acc = 0.0;
-      for (int l = 0; l < md; ++l) acc = fma(F.Q[(int64_t)l * N + e], z[l] - y[l], acc);
+      for (int l = 0; l < md; ++l) acc = fma(Q[(int64_t)l * N + e], z[l] - y[l], acc);
       Ki[e] = (Fi[e] - acc) - F.w2[e];
     }
   }
   // ---------------------------------------------------------------- reverse
+  g.sync();  // zs, ys from lane 0
   for (int i = 0; i < 4; ++i)
-    for (int e = 0; e < N; ++e) F.Kbar[(int64_t)i * N + e] = h * bj[i] * F.ubar[e];
-  for (int64_t e = 0; e < (int64_t)md * N; ++e) F.Qbar[e] = 0.0;
-  for (int i = 0; i < MAXM * MAXM; ++i) F.Lbar[i] = 0.0;
-  for (int e = 0; e < N; ++e) {
+    for (int e = L; e < N; e += G) F.Kbar[(int64_t)i * N + e] = h * bj[i] * F.ubar[e];
+  for (int l = 0; l < md; ++l)
+    for (int e = L; e < N; e += G) F.Qbar[(int64_t)l * N + e] = 0.0;
+  if (L == 0)
+    for (int i = 0; i < MAXM * MAXM; ++i) F.Lbar[i] = 0.0;
+  for (int e = L; e < N; e += G) {
     F.fb2[e] = 0.0;
     F.fbn[e] = 0.0;
   }
   for (int i = 3; i >= 0; --i) {
-    const Col<double> Kb{F.Kbar.p + (int64_t)i * N * F.Kbar.s, F.Kbar.s};
-    const Col<double> Fi{F.F.p + (int64_t)i * N * F.F.s, F.F.s};
+    const double* Kb = &F.Kbar[(int64_t)i * N];
+    const double* Fi = &F.F[(int64_t)i * N];
     double dbar[MAXM], zbar[MAXM];
     for (int l = 0; l < md; ++l) {
       double d = 0.0;
-      for (int e = 0; e < N; ++e) d = fma(F.Q[(int64_t)l * N + e], Kb[e], d);
-      dbar[l] = -d;
+      for (int e = L; e < N; e += G) d = fma(Q[(int64_t)l * N + e], Kb[e], d);
+      dbar[l] = -g.sum(d);
     }
     for (int r = 0; r < md; ++r) {
       double a = 0.0;  // a = L^-T ybar with ybar = -dbar
       for (int c = 0; c < md; ++c) a = fma(F.Linv[c * MAXM + r], -dbar[c], a);
       zbar[r] = dbar[r] + a;
-      for (int c = 0; c < md; ++c) F.Lbar[r * MAXM + c] -= a * F.ys[i * MAXM + c];
+      if (L == 0)
+        for (int c = 0; c < md; ++c) F.Lbar[r * MAXM + c] -= a * F.ys[i * MAXM + c];
     }
     for (int l = 0; l < md; ++l) {
       const double dl = F.zs[i * MAXM + l] - F.ys[i * MAXM + l];
-      for (int e = 0; e < N; ++e) {
+      for (int e = L; e < N; e += G) {
         double qb = F.Qbar[(int64_t)l * N + e];
         qb = fma(-dl, Kb[e], qb);
         qb = fma(zbar[l], Fi[e], qb);
         F.Qbar[(int64_t)l * N + e] = qb;
       }
     }
-    for (int e = 0; e < N; ++e) {
+    for (int e = L; e < N; e += G) {
       double Fb = Kb[e];
-      for (int l = 0; l < md; ++l) Fb = fma(F.Q[(int64_t)l * N + e], zbar[l], Fb);
+      for (int l = 0; l < md; ++l) Fb = fma(Q[(int64_t)l * N + e], zbar[l], Fb);
       const double Gb = Fb - Kb[e];
       for (int j = 0; j < i; ++j) F.Kbar[(int64_t)j * N + e] += gij[i][j] * Gb;
       F.w[e] = Fb;  // f_bar of this stage
     }
     if (i == 3) {
-      for (int e = 0; e < N; ++e) F.fb2[e] += F.w[e];
+      for (int e = L; e < N; e += G) F.fb2[e] += F.w[e];
     } else if (i == 2 || i == 1) {
       const Col<double>& arg = (i == 1) ? F.arg1 : F.arg2;
       if (i == 2)
-        for (int e = 0; e < N; ++e) F.fb2[e] += F.w[e];
-      adj_load_ud(F, N, arg, nullptr, 0);
-      adj_rhs_fwd(m, F, p);
-      for (int e = 0; e < N; ++e) F.fbd[e] = Dual{i == 2 ? F.fb2[e] : F.w[e], 0.0};
-      adj_rhs_rev(m, F, false);
-      for (int e = 0; e < N; ++e) {
+        for (int e = L; e < N; e += G) F.fb2[e] += F.w[e];
+      adj_load_ud<G>(F, N, arg, nullptr);
+      adj_rhs_fwd<G>(m, F, p);
+      for (int e = L; e < N; e += G) F.fbd[e] = Dual{i == 2 ? F.fb2[e] : F.w[e], 0.0};
+      adj_rhs_rev<G>(m, F, false);
+      for (int e = L; e < N; e += G) {
         const double ab = F.ubd[e].v;
         F.ubar[e] += ab;
         if (i == 2) {
@@ -502,64 +569,67 @@ __device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double 
         }
       }
     } else {
-      for (int e = 0; e < N; ++e) F.fbn[e] += F.w[e];
+      for (int e = L; e < N; e += G) F.fbn[e] += F.w[e];
     }
   }
-  for (int i = 0; i < MAXM * MAXM; ++i) F.Hbar[i] = -h * GAM * F.Lbar[i];
+  if (L == 0)
+    for (int i = 0; i < MAXM * MAXM; ++i) F.Hbar[i] = -h * GAM * F.Lbar[i];
+  g.sync();  // Hbar from lane 0
   // Arnoldi, last column first
   for (int j = md - 1; j >= 0; --j) {
-    adj_load_ud(F, N, F.u, &F.Q, (int64_t)j * N);
-    adj_rhs_fwd(m, F, p);
-    for (int e = 0; e < N; ++e) F.w[e] = F.fd[e].t;
-    for (int e = 0; e < N; ++e) {
+    adj_load_ud<G>(F, N, F.u, Q + (int64_t)j * N);
+    adj_rhs_fwd<G>(m, F, p);
+    for (int e = L; e < N; e += G) F.w[e] = F.fd[e].t;
+    for (int e = L; e < N; e += G) {
       double a = F.w[e];
-      for (int i = 0; i <= j; ++i) a = fma(-F.p1[j * MAXM + i], F.Q[(int64_t)i * N + e], a);
+      for (int i = 0; i <= j; ++i) a = fma(-F.p1[j * MAXM + i], Q[(int64_t)i * N + e], a);
       F.w1[e] = a;
       double b = a;
-      for (int i = 0; i <= j; ++i) b = fma(-F.p2[j * MAXM + i], F.Q[(int64_t)i * N + e], b);
+      for (int i = 0; i <= j; ++i) b = fma(-F.p2[j * MAXM + i], Q[(int64_t)i * N + e], b);
       F.w2[e] = b;
     }
     // w2 -> (h_{j+1,j}, q_{j+1})
     if (j + 1 < md) {
       const double eta = F.hn[j];
       double qw = 0.0;
-      for (int e = 0; e < N; ++e) qw = fma(F.Qbar[(int64_t)(j + 1) * N + e], F.w2[e], qw);
+      for (int e = L; e < N; e += G) qw = fma(F.Qbar[(int64_t)(j + 1) * N + e], F.w2[e], qw);
+      qw = g.sum(qw);
       const double c = F.Hbar[(j + 1) * MAXM + j] - qw / (eta * eta);
-      for (int e = 0; e < N; ++e) F.wbar[e] = (F.Qbar[(int64_t)(j + 1) * N + e] + c * F.w2[e]) / eta;
+      for (int e = L; e < N; e += G) F.wbar[e] = (F.Qbar[(int64_t)(j + 1) * N + e] + c * F.w2[e]) / eta;
     } else {
-      for (int e = 0; e < N; ++e) F.wbar[e] = 0.0;
+      for (int e = L; e < N; e += G) F.wbar[e] = 0.0;
     }
     double pb2[MAXM], pb1[MAXM];
     for (int i = 0; i <= j; ++i) {  // second pass
       double d = 0.0;
-      for (int e = 0; e < N; ++e) d = fma(F.Q[(int64_t)i * N + e], F.wbar[e], d);
-      pb2[i] = F.Hbar[i * MAXM + j] - d;
+      for (int e = L; e < N; e += G) d = fma(Q[(int64_t)i * N + e], F.wbar[e], d);
+      pb2[i] = F.Hbar[i * MAXM + j] - g.sum(d);
     }
-    for (int e = 0; e < N; ++e) {
+    for (int e = L; e < N; e += G) {
       double wb = F.wbar[e];
       for (int i = 0; i <= j; ++i) {
         F.Qbar[(int64_t)i * N + e] += -F.p2[j * MAXM + i] * F.wbar[e] + pb2[i] * F.w1[e];
-        wb = fma(pb2[i], F.Q[(int64_t)i * N + e], wb);
+        wb = fma(pb2[i], Q[(int64_t)i * N + e], wb);
       }
       F.tmp[e] = wb;  // w1_bar
     }
     for (int i = 0; i <= j; ++i) {  // first pass
       double d = 0.0;
-      for (int e = 0; e < N; ++e) d = fma(F.Q[(int64_t)i * N + e], F.tmp[e], d);
-      pb1[i] = F.Hbar[i * MAXM + j] - d;
+      for (int e = L; e < N; e += G) d = fma(Q[(int64_t)i * N + e], F.tmp[e], d);
+      pb1[i] = F.Hbar[i * MAXM + j] - g.sum(d);
     }
-    for (int e = 0; e < N; ++e) {
+    for (int e = L; e < N; e += G) {
       double wb = F.tmp[e];
       for (int i = 0; i <= j; ++i) {
         F.Qbar[(int64_t)i * N + e] += -F.p1[j * MAXM + i] * F.tmp[e] + pb1[i] * F.w[e];
-        wb = fma(pb1[i], F.Q[(int64_t)i * N + e], wb);
+        wb = fma(pb1[i], Q[(int64_t)i * N + e], wb);
       }
       F.wbar[e] = wb;
     }
     // w = J(u) q_j: J^T w_bar into q_bar_j, second-order terms into u_bar and theta
-    for (int e = 0; e < N; ++e) F.fbd[e] = Dual{F.wbar[e], 0.0};
-    adj_rhs_rev(m, F, true);
-    for (int e = 0; e < N; ++e) {
+    for (int e = L; e < N; e += G) F.fbd[e] = Dual{F.wbar[e], 0.0};
+    adj_rhs_rev<G>(m, F, true);
+    for (int e = L; e < N; e += G) {
       F.Qbar[(int64_t)j * N + e] += F.ubd[e].v;
       F.ubar[e] += F.ubd[e].t;
     }
@@ -567,15 +637,17 @@ __device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double 
   // q_1 = f_n / |f_n|
   if (md > 0) {
     double qf = 0.0;
-    for (int e = 0; e < N; ++e) qf = fma(F.Qbar[e], F.fn[e], qf);
-    for (int e = 0; e < N; ++e) F.fbn[e] += F.Qbar[e] / beta - qf * F.fn[e] / (beta * beta * beta);
+    for (int e = L; e < N; e += G) qf = fma(F.Qbar[e], F.fn[e], qf);
+    qf = g.sum(qf);
+    for (int e = L; e < N; e += G) F.fbn[e] += F.Qbar[e] / beta - qf * F.fn[e] / (beta * beta * beta);
   }
   // f_n = f(u)
-  adj_load_ud(F, N, F.u, nullptr, 0);
-  adj_rhs_fwd(m, F, p);
-  for (int e = 0; e < N; ++e) F.fbd[e] = Dual{F.fbn[e], 0.0};
-  adj_rhs_rev(m, F, false);
-  for (int e = 0; e < N; ++e) F.ubar[e] += F.ubd[e].v;
+  adj_load_ud<G>(F, N, F.u, nullptr);
+  adj_rhs_fwd<G>(m, F, p);
+  for (int e = L; e < N; e += G) F.fbd[e] = Dual{F.fbn[e], 0.0};
+  adj_rhs_rev<G>(m, F, false);
+  for (int e = L; e < N; e += G) F.ubar[e] += F.ubd[e].v;
+  g.sync();
 }
 
 }  // namespace rk

@@ -48,6 +48,16 @@ struct MechLayout {
   // FP32 copies read by the reduced-precision Jacobian-vector product
   int64_t off_Wf = 0, off_invWf = 0, off_bf = 0, off_EaRf = 0, off_efff = 0, off_csr_nuf = 0;
   int64_t off_perm = 0;  // int32 per packed reaction: its index in the input description
+  // species-major list of the reaction slots each species fills (the adjoint's
+  // deterministic gathers of d/dC and d/dg): entry r << 2 | role, role 0..3 =
+  // the slot ra, rb, pa, pb of packed reaction r; species k's entries are
+  // role[role_ptr[k] .. role_ptr[k + 1])
+  int32_t nrole = 0;
+  int64_t off_role_ptr = 0, off_role = 0;
+  // nu^T (species x packed reactions) as the A operands of 16 x 16 BF16 mma tiles:
+  // tile (st, rt) holds, for each lane, its four 32-bit registers (8 BF16) together
+  int32_t nst = 0, nrt = 0;  // species tiles, reaction tiles
+  int64_t off_nuT = 0;       // [nst][nrt][32 lanes] x 16 bytes
   int64_t bytes = 0;
   // prefixes of the buffer that kernels copy to shared memory: through the FP64
   // arrays; also csr_nuf (double-float gathers); also the other FP32 copies

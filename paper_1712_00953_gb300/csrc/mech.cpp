@@ -236,6 +236,29 @@ bool pack_mechanism(const void* vdesc, HostMech* out, std::string* err) {
   L.off_efff = take(4 * (int64_t)L.ntb * ns);
   L.bytes_f32 = off;
   L.off_perm = take(4 * (int64_t)nr);
+  // reaction slots per species (filled below from the packed slots)
+  std::vector<std::vector<int32_t>> roles(ns);
+  for (int r = 0; r < nr; ++r) {
+    const int j = perm[r];
+    // the same expansion as the packed slots below: entries 0, 1 reactants, 2, 3 products
+    int sl[4] = {ns, ns, ns, ns}, a = 0, b = 2;
+    for (int s = 0; s < 4; ++s) {
+      const int k = d->rxn_sp[4 * (size_t)j + s], nu = d->rxn_nu[4 * (size_t)j + s];
+      if (k < 0) continue;
+      for (int t = 0; t < (nu < 0 ? -nu : nu); ++t) {
+        if (s < 2 && a < 2) sl[a++] = k;
+        else if (s >= 2 && b < 4) sl[b++] = k;
+      }
+    }
+    for (int role = 0; role < 4; ++role)
+      if (sl[role] < ns) roles[sl[role]].push_back(r << 2 | role);
+  }
+  for (auto& v : roles) L.nrole += (int32_t)v.size();
+  L.off_role_ptr = take(4 * (int64_t)(ns + 1));
+  L.off_role = take(4 * (int64_t)(L.nrole > 0 ? L.nrole : 1));
+  L.nst = (ns + 15) / 16;
+  L.nrt = (nr + 15) / 16;
+  L.off_nuT = take(16 * 32 * (int64_t)L.nst * L.nrt);
   L.bytes = align16(off);
 
   std::vector<unsigned char> buf((size_t)L.bytes, 0);
@@ -328,6 +351,43 @@ bool pack_mechanism(const void* vdesc, HostMech* out, std::string* err) {
   for (int i = 0; i < L.ntb * ns; ++i) F(L.off_efff)[i] = (float)D(L.off_eff)[i];
   for (int i = 0; i < nnz; ++i) F(L.off_csr_nuf)[i] = (float)D(L.off_csr_nu)[i];
   for (int r = 0; r < nr; ++r) I(L.off_perm)[r] = perm[r];
+  {
+    int pos = 0;
+    for (int k = 0; k < ns; ++k) {
+      I(L.off_role_ptr)[k] = pos;
+      for (int32_t e : roles[k]) I(L.off_role)[pos++] = e;
+    }
+    I(L.off_role_ptr)[ns] = pos;
+  }
+  // nu^T tiles for the tensor-core gather: net coefficients (small integers,
+  // exact in BF16) placed in each lane's A-operand registers of mma.m16n8k16
+  // (register 0: row g, columns 2t, 2t+1; 1: row g+8; 2: row g, columns
+  // 2t+8, 2t+9; 3: row g+8; g = lane / 4, t = lane % 4; the lower column in
+  // the lower 16 bits)
+  {
+    std::vector<double> A((size_t)ns * nr, 0.0);
+    for (int k = 0; k < ns; ++k)
+      for (auto& e : rows[k]) A[(size_t)k * nr + e.first] = e.second;
+    auto a = [&](int k, int r) { return (k < ns && r < nr) ? A[(size_t)k * nr + r] : 0.0; };
+    auto bf16 = [](double x) {
+      const float f = (float)x;  // a small integer: its BF16 is the float's upper half, exactly
+      uint32_t u;
+      memcpy(&u, &f, 4);
+      return u >> 16;
+    };
+    auto pack = [&](int k, int r) { return bf16(a(k, r)) | (bf16(a(k, r + 1)) << 16); };
+    uint32_t* T = U(L.off_nuT);
+    for (int st = 0; st < L.nst; ++st)
+      for (int rt = 0; rt < L.nrt; ++rt)
+        for (int l = 0; l < 32; ++l) {
+          const int g = l >> 2, t = l & 3, k0 = 16 * st + g, r0 = 16 * rt + 2 * t;
+          uint32_t* R = T + 4 * ((size_t)(st * L.nrt + rt) * 32 + l);
+          R[0] = pack(k0, r0);
+          R[1] = pack(k0 + 8, r0);
+          R[2] = pack(k0, r0 + 8);
+          R[3] = pack(k0 + 8, r0 + 8);
+        }
+  }
 
   out->L = L;
   out->packed.swap(buf);

@@ -44,7 +44,7 @@ namespace rk {
 // ---------------------------------------------------------------- constants
 constexpr double R_GAS = 8.314462618;
 constexpr double P_REF = 101325.0;
-constexpr double R_OVER_PREF = R_GAS / P_REF, PREF_OVER_R = P_REF / R_GAS, INV_R = 1.0 / R_GAS;
+constexpr double PREF_OVER_R = P_REF / R_GAS, INV_R = 1.0 / R_GAS;
 constexpr double LN_R_OVER_PREF = -9.408091968961747;  // ln(R / P_ref)
 constexpr double GAM = 0.572816062482135;
 // Table coeff_rok4e (Sec. 4.2); b3 = 0, bhat4 = 0.
@@ -279,6 +279,9 @@ struct MechView {
   int npiece;
   const float *Wf, *invWf, *bf, *EaRf, *efff, *csr_nuf;  // FP32 copies
   const int32_t* perm;  // input index of each packed reaction
+  int nst, nrt;         // nu^T tiles (species, reactions) of the tensor-core gather
+  const uint4* nuT;     // their A operands, per tile and lane
+  const int32_t *role_ptr, *role;  // species-major reaction slots (r << 2 | role)
 };
 
 __host__ __device__ inline MechView make_view(const unsigned char* base, const MechLayout& L) {
@@ -314,6 +317,11 @@ __host__ __device__ inline MechView make_view(const unsigned char* base, const M
   m.efff = reinterpret_cast<const float*>(base + L.off_efff);
   m.csr_nuf = reinterpret_cast<const float*>(base + L.off_csr_nuf);
   m.perm = reinterpret_cast<const int32_t*>(base + L.off_perm);
+  m.nst = L.nst;
+  m.nrt = L.nrt;
+  m.nuT = reinterpret_cast<const uint4*>(base + L.off_nuT);
+  m.role_ptr = reinterpret_cast<const int32_t*>(base + L.off_role_ptr);
+  m.role = reinterpret_cast<const int32_t*>(base + L.off_role);
   return m;
 }
 
@@ -327,6 +335,7 @@ struct SlotLayout {
   int tro;                                    // [11][ntroe]: Troe falloff scratch
   int part;                                   // [npiece]: gather partial sums
   int C2, dC2;                                // species: double-float C and dC (precision 3, else -1)
+  int dig;                                    // BF16 digits of q, [8][16 nrt] (precision 4, else -1)
   int H, LU, piv, red, Bm;                    // small (Bm: I - (I - h gamma H)^-1)
   int fbase;  // FP32 region (mixed precision only), offset in doubles
   int fC, fdC, fh, fcp, fdcp, fom, fq, fkc, fkr, ftb, fQ, fw, fpart;  // offsets in floats from fbase
@@ -336,7 +345,8 @@ struct SlotLayout {
 // mixed: the FP32 arrays of precision levels 1 and 2; df: the double-float
 // species arrays of precision level 3 (left out otherwise, which lets a 53-species
 // mechanism keep 7 cells per block instead of 6).
-static SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false, int nx = 0, bool df = false) {
+static SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false, int nx = 0, bool df = false,
+                            bool tc = false) {
   SlotLayout s;
   s.N = L.ns + 1 + nx;
   s.ns = L.ns;
@@ -384,6 +394,7 @@ static SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false, int 
   s.part = take(L.npiece > 0 ? L.npiece : 1);
   s.C2 = df ? take(ns1) : -1;
   s.dC2 = df ? take(ns1) : -1;
+  s.dig = tc ? take(2 * 16 * L.nrt) : -1;  // 8 x 16 nrt BF16 = 2 x 16 nrt doubles
   // M x M matrices stored with row stride MAXM: M rows
   s.H = take(M * MAXM);
   s.LU = take(M * MAXM);
@@ -521,6 +532,7 @@ struct SlotPtrs {
   double *u, *src, *fn, *arg, *fr, *F, *w, *Q, *K;
   double *C, *dC, *cp, *hRT, *dcp, *gRT, *E, *Einv, *CE, *om, *q, *kc, *krc, *qT, *tb, *tro, *part;
   df2 *C2, *dC2;
+  uint16_t* dig;
   double *H, *LU, *piv, *red, *Bm;
   float *fC, *fdC, *fh, *fcp, *fdcp, *fom, *fq, *fkc, *fkr, *ftb, *fQ, *fw, *fpart;  // mixed precision
   int Nq;  // stride between Krylov / stage vectors
@@ -555,6 +567,7 @@ __device__ inline SlotPtrs slot_ptrs(double* b, const SlotLayout& s) {
   p.part = b + s.part;
   p.C2 = s.C2 >= 0 ? reinterpret_cast<df2*>(b + s.C2) : nullptr;
   p.dC2 = s.dC2 >= 0 ? reinterpret_cast<df2*>(b + s.dC2) : nullptr;
+  p.dig = s.dig >= 0 ? reinterpret_cast<uint16_t*>(b + s.dig) : nullptr;
   p.tb = b + s.tb;
   p.H = b + s.H;
   p.LU = b + s.LU;
@@ -624,6 +637,97 @@ __device__ __forceinline__ double piece_sum_df(const MechView& m, const df2* par
   return df_to(acc);
 }
 
+// ---- w = nu^T q on the tensor cores (precision level 4), exact to FP64 level.
+// Each q_j is cut, relative to 2^Es with Es above the cell's largest |q_j|,
+// into seven signed 8-bit digits (56 bits below 2^Es; what lies below
+// 2^(Es - 56) is dropped, at most 2^-55 of the largest rate); the digits and
+// the small-integer net coefficients are exact in BF16, each product is exact
+// in FP32 and so is every sum the mma accumulates (|sum| <= 2 x 255 x Nr <
+// 2^24), so the FP32 accumulators hold the digit columns of nu^T q exactly.
+// mma.m16n8k16: A = a 16 x 16 tile of nu^T (species x reactions, prepacked
+// per lane), B = the 16 x 8 tile of digits (reactions x digit 0..6, column 7
+// zero), D = 16 species x 8 digit sums; FP64 then adds the seven scaled digit
+// sums of each species (rounding once per addition, like a sum of terms).
+__device__ __forceinline__ void mma_bf16_m16n8k16(float (&d)[4], const uint4& a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+}
+
+// A signed integer |v| <= 256 as BF16 (exact: its float's upper half).
+__device__ __forceinline__ uint16_t bf16_of_small_int(int v) {
+  return (uint16_t)(__float_as_uint((float)v) >> 16);
+}
+
+// x * 2^e for a double x holding an integer of magnitude below 2^53 and an
+// exponent that keeps the result normal: an integer add to the exponent field.
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+  return x == 0.0 ? 0.0 : exp_scale(x, e);
+}
+
+// out[k] = sum_j nu_jk q_j for the cell (q: Nr doubles in shared memory).
+// Returns false, writing nothing, when every |q_j| < 2^-920 (the digit
+// weights would leave the normal range): the caller then gathers in FP64.
+template <int G>
+__device__ bool gather_tc(const MechView& m, const SlotPtrs& s, const double* __restrict__ q,
+                          double* __restrict__ out) {
+  static_assert(G == 32, "the tensor-core gather runs one cell per warp");
+  const Grp<G> g;
+  const int lane = g.lane;
+  const int nrp = 16 * m.nrt;
+  // the scale: 2^(Eb - 1023) above every |q_j| (Eb one above the largest biased exponent)
+  int emax = 0;
+  for (int j = lane; j < m.nr; j += G) emax = max(emax, (__double2hiint(q[j]) >> 20) & 0x7ff);
+  const int Eb = g.imax(emax) + 1;
+  if (Eb < 104) return false;
+  // digits of |q_j| 2^(56 - Es), most significant first, with q_j's sign
+  for (int j = lane; j < m.nr; j += G) {
+    const long long bits = __double_as_longlong(q[j]);
+    const int e = (int)((bits >> 52) & 0x7ff);
+    unsigned long long V = 0ull;
+    if (e != 0) {  // zero and subnormal rates (below 2^-1022) drop out
+      const unsigned long long mant = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+      const int sh = e + 4 - Eb;  // V = mant 2^sh < 2^56
+      V = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> (-sh)) : 0ull);
+    }
+    const bool neg = bits < 0;
+#pragma unroll
+    for (int n = 0; n < 7; ++n) {
+      const int dn = (int)((V >> (48 - 8 * n)) & 255ull);
+      s.dig[n * nrp + j] = bf16_of_small_int(neg ? -dn : dn);
+    }
+  }
+  g.sync();
+  const int grp = lane >> 2, tq = lane & 3;
+  const uint32_t* drow = reinterpret_cast<const uint32_t*>(s.dig + grp * nrp);
+  // digit n weighs 2^(Es - 8 (n + 1)), Es = Eb - 1023
+  const int w0 = Eb - 1023 - 8 * (2 * tq + 1), w1 = w0 - 8;
+  for (int st = 0; st < m.nst; ++st) {
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int rt = 0; rt < m.nrt; ++rt) {
+      const uint4 a = m.nuT[(st * m.nrt + rt) * 32 + lane];
+      mma_bf16_m16n8k16(d, a, drow[8 * rt + tq], drow[8 * rt + tq + 4]);
+    }
+    // this lane: digits 2tq and 2tq+1 of species rows grp (d0, d1) and grp + 8 (d2, d3)
+    double r0 = scale_pow2((double)d[1], w1) + scale_pow2((double)d[0], w0);
+    double r1 = scale_pow2((double)d[3], w1) + scale_pow2((double)d[2], w0);
+    // add the four lanes of the group, least significant digits first
+    r0 = __shfl_xor_sync(g.mask, r0, 1) + r0;
+    r1 = __shfl_xor_sync(g.mask, r1, 1) + r1;
+    r0 = __shfl_xor_sync(g.mask, r0, 2) + r0;
+    r1 = __shfl_xor_sync(g.mask, r1, 2) + r1;
+    if (tq == 0) {
+      const int k0 = 16 * st + grp, k1 = k0 + 8;
+      if (k0 < m.ns) out[k0] = r0;
+      if (k1 < m.ns) out[k1] = r1;
+    }
+  }
+  g.sync();
+  return true;
+}
+
 // ------------------------------------------------------------ chemistry RHS
 // out = f(uu) + src (src may be null).  p > 0: constant-pressure reactor at
 // pressure p; p < 0: constant-volume reactor of density -p (Eq. cv_reactor with
@@ -635,7 +739,7 @@ __device__ __forceinline__ double piece_sum_df(const MechView& m, const df2* par
 // an explicit fma or __dmul_rn, so no copy can contract it differently,
 // chem_rhs and the integrator compute the same bits and R(u) - R(u) is
 // exactly zero in a steady-state cell.
-template <int G, bool MIXED = false>
+template <int G, bool MIXED = false, bool TC = false>
 __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, const double* uu,
                                       const double* src, double p, double* out, bool cache,
                                       CellScalars* cs) {
@@ -911,8 +1015,10 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
   // species pass 2: w = nu^T q, dY/dt and the sums of the temperature equation
   double Sh = 0.0, cb = 0.0;
   double Ax = 0.0, Bx = 0.0;  // auxiliary T: sum (u_k/RT) F_k / W_k and sum (cv_k/R) F_k / W_k
+  bool tc_om = false;  // w already in part[0..ns) from the tensor cores
+  if constexpr (TC) tc_om = gather_tc<G>(m, s, s.q, s.part);
   if (MIXED) gather_pieces_df<G>(m, g.lane, reinterpret_cast<const df2*>(s.q), reinterpret_cast<df2*>(s.part));
-  else gather_pieces<G, double>(m, g.lane, m.csr_nu, s.q, s.part);
+  else if (!tc_om) gather_pieces<G, double>(m, g.lane, m.csr_nu, s.q, s.part);
   g.sync();
   for (int k = g.lane; k < ns; k += G) {
     double om;
@@ -920,7 +1026,7 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
       om = piece_sum_df(m, reinterpret_cast<const df2*>(s.part), k);
       if (cache) s.fom[k] = __double2float_rn(om);
     } else {
-      om = piece_sum(m, s.part, k);
+      om = tc_om ? s.part[k] : piece_sum(m, s.part, k);
     }
     if (cache) s.om[k] = om;
     const double r = __dmul_rn(__dmul_rn(m.W[k], om), invrho);
@@ -1008,25 +1114,25 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
 // evaluation and the 8/16-lane and mixed variants of the integrator (one
 // inlined copy per call site would multiply the compile time).  Same bits as
 // the inlined copies.
-template <int G, bool MIXED = false>
+template <int G, bool MIXED = false, bool TC = false>
 __device__ __noinline__ void rhs_eval_call(const MechView& m, const SlotPtrs& s, const double* uu,
                                            const double* src, double p, double* out, bool cache,
                                            CellScalars* cs) {
-  rhs_eval<G, MIXED>(m, s, uu, src, p, out, cache, cs);
+  rhs_eval<G, MIXED, TC>(m, s, uu, src, p, out, cache, cs);
 }
-template <int G, bool MIXED, bool INL>
+template <int G, bool MIXED, bool INL, bool TC = false>
 __device__ __forceinline__ void rhs_dispatch(const MechView& m, const SlotPtrs& s, const double* uu,
                                              const double* src, double p, double* out, bool cache,
                                              CellScalars* cs) {
-  if constexpr (INL) rhs_eval<G, MIXED>(m, s, uu, src, p, out, cache, cs);
-  else rhs_eval_call<G, MIXED>(m, s, uu, src, p, out, cache, cs);
+  if constexpr (INL) rhs_eval<G, MIXED, TC>(m, s, uu, src, p, out, cache, cs);
+  else rhs_eval_call<G, MIXED, TC>(m, s, uu, src, p, out, cache, cs);
 }
 
 // Analytic Jacobian-vector product out = J(u_n) v, using the values cached by
 // the last rhs_eval(..., cache = true) at u_n.  v, out: N-vectors.  Inlined
 // (unlike rhs_eval, nothing requires two call sites to produce the same bits),
 // which saves the call's register save and restore four times per attempt.
-template <int G, bool DFG = false>
+template <int G, bool DFG = false, bool TC = false>
 __device__ __forceinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, const double* uu,
                                       const CellScalars& cs, const double* v, double* out) {
   const Grp<G> g;
@@ -1037,7 +1143,6 @@ __device__ __forceinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, c
   for (int k = g.lane; k < ns; k += G) a = fma(v[k], m.invW[k], a);
   a = g.sum(a);
   const double drr = cs.cv ? 0.0 : -fma(a, cs.invS, vT * invT);  // d rho / rho (0 at fixed volume)
-  const double esh = cs.cv ? 1.0 : 0.0;
   const bool coop_tb = m.ntb > 0 && m.ntb <= MAXM;
   double mp[MAXM];
 #pragma unroll
@@ -1083,12 +1188,15 @@ __device__ __forceinline__ void jvp_eval(const MechView& m, const SlotPtrs& s, c
     else s.q[j] = dq;
   }
   g.sync();
+  bool tc_om = false;  // d w already in part[0..ns) from the tensor cores
+  if constexpr (TC) tc_om = gather_tc<G>(m, s, s.q, s.part);
   if (DFG) gather_pieces_df<G>(m, g.lane, reinterpret_cast<const df2*>(s.q), reinterpret_cast<df2*>(s.part));
-  else gather_pieces<G, double>(m, g.lane, m.csr_nu, s.q, s.part);
+  else if (!tc_om) gather_pieces<G, double>(m, g.lane, m.csr_nu, s.q, s.part);
   g.sync();
   double dSh = 0.0, dcb = 0.0;
   for (int k = g.lane; k < ns; k += G) {
-    const double dom = DFG ? piece_sum_df(m, reinterpret_cast<const df2*>(s.part), k) : piece_sum(m, s.part, k);
+    const double dom = DFG ? piece_sum_df(m, reinterpret_cast<const df2*>(s.part), k)
+                           : (tc_om ? s.part[k] : piece_sum(m, s.part, k));
     out[k] = s.Einv[k] * fma(-s.om[k], drr, dom);  // Einv: W_k / rho
     dSh = fma(s.gRT[k], dom, fma(s.hRT[k], vT, dSh));
     dcb = fma(s.dcp[k], vT, fma(s.cp[k], v[k], dcb));
@@ -1315,7 +1423,7 @@ __device__ inline double group_dot(const Grp<G>& g, const double* a, const doubl
 }
 
 // J v into out: analytic, or forward difference with the oracle's increment.
-template <int G, bool MIXED = false>
+template <int G, bool MIXED = false, bool TC = false>
 __device__ inline void apply_jv(const MechView& m, const SlotPtrs& s, const CellScalars& cs, int jv_mode,
                                 double p, double unorm, const double* v, double* out, int* n_rhs,
                                 bool fp32_jv = false) {
@@ -1324,7 +1432,7 @@ __device__ inline void apply_jv(const MechView& m, const SlotPtrs& s, const Cell
   if (jv_mode == 0) {
     if (MIXED && fp32_jv) jvp_eval_f32<G>(m, s, s.u, cs, v, out);
     else if (!MIXED && cs.prec == 3) jvp_eval_df<G>(m, s, s.u, cs, v, out);
-    else jvp_eval<G, MIXED>(m, s, s.u, cs, v, out);
+    else jvp_eval<G, MIXED, TC>(m, s, s.u, cs, v, out);
     return;
   }
   const double nv = sqrt(group_dot<G>(g, v, v, N));
@@ -1339,7 +1447,7 @@ __device__ inline void apply_jv(const MechView& m, const SlotPtrs& s, const Cell
   CellScalars dummy;
   dummy.pinv = cs.pinv;
   dummy.prec = cs.prec;
-  rhs_eval_call<G, MIXED>(m, s, s.arg, s.src, p, out, false, &dummy);
+  rhs_eval_call<G, MIXED, TC>(m, s, s.arg, s.src, p, out, false, &dummy);
   *n_rhs += 1;
   for (int e = g.lane; e < N; e += G) out[e] = (out[e] - s.fn[e]) / d;
   g.sync();
@@ -1359,7 +1467,7 @@ __device__ inline float group_dot_f(const Grp<G>& g, const double* a, const doub
 // first pass left behind -- its FP32 rounding included -- and the norms stay
 // FP64, so the basis and H keep FP64 quality (mixed-precision "twice is
 // enough").
-template <int G, bool MIXED = false>
+template <int G, bool MIXED = false, bool TC = false>
 __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& cs, int M, int jv_mode,
                        double p, int* n_rhs, bool fp32_jv = false) {
   const Grp<G> g;
@@ -1385,7 +1493,7 @@ __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& 
   constexpr double brk2 = BREAKDOWN_TOL * BREAKDOWN_TOL;  // breakdown ||w_after|| <= tol ||w_before||, on squares
   int mdim = M;
   for (int j = 0; j < M; ++j) {
-    apply_jv<G, MIXED>(m, s, cs, jv_mode, p, unorm, s.Q + j * Nq, s.w, n_rhs, fp32_jv);
+    apply_jv<G, MIXED, TC>(m, s, cs, jv_mode, p, unorm, s.Q + j * Nq, s.w, n_rhs, fp32_jv);
     // (only the breakdown threshold reads ||J q_j||^2: FP32 is enough there)
     const double w02 = MIXED ? (double)group_dot_f<G>(g, s.w, s.w, N) : group_dot<G>(g, s.w, s.w, N);
     double hcol[MAXM];
@@ -1619,9 +1727,10 @@ struct IntegrateParams {
   const double* rho_cell;      // constant-volume densities, or null (constant pressure)
   int nx;                      // state components after T (5: auxiliary-temperature system)
   int64_t mech_copy;           // bytes of the mechanism each block copies (a prefix, by precision)
+  int64_t tc_bytes;            // precision 4: bytes of nu^T tiles copied after that prefix (else 0)
 };
 
-template <int G, bool MIXED>
+template <int G, bool MIXED, bool TC = false>
 __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const IntegrateParams& P, int64_t cell) {
   const Grp<G> g;
   const int ns = m.ns, N = ns + 1 + m.nx, Nq = s.Nq;
@@ -1647,7 +1756,7 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
   int n_acc = 0, n_rej = 0, n_rhs = 0, status = RK_CELL_OK, n_att = 0;
   CellScalars cs;
   cs.pinv = 1.0 / fabs(pr);
-  cs.prec = P.precision == 3 ? 3 : 0;
+  cs.prec = P.precision == 3 ? 3 : (TC ? 4 : 0);
   constexpr bool INL = G == 32 && !MIXED;  // the RHS inlined on the main path
   int mdim = 0;
   bool fresh = true;  // f_n and the Krylov basis are due at u (start, or after an accepted step)
@@ -1659,9 +1768,9 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
   constexpr double g41 = G41 / GAM, g42 = G42 / GAM, g43 = G43 / GAM;
   while (true) {
     if (fresh) {
-      rhs_dispatch<G, MIXED, INL>(m, s, s.u, srcp, pr, s.fn, true, &cs);
+      rhs_dispatch<G, MIXED, INL, TC>(m, s, s.u, srcp, pr, s.fn, true, &cs);
       n_rhs += 1;
-      mdim = arnoldi<G, MIXED>(m, s, cs, P.M, P.jv_mode, pr, &n_rhs, fp32_jv);
+      mdim = arnoldi<G, MIXED, TC>(m, s, cs, P.M, P.jv_mode, pr, &n_rhs, fp32_jv);
       fresh = false;
     }
     if (fixed) {
@@ -1686,7 +1795,7 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
           s.arg[e] = s.u[e] + h * acc;
         }
         g.sync();
-        rhs_dispatch<G, MIXED, INL>(m, s, s.arg, srcp, pr, s.fr, false, &cs);
+        rhs_dispatch<G, MIXED, INL, TC>(m, s, s.arg, srcp, pr, s.fr, false, &cs);
         n_rhs += 1;
         fi = s.fr;
       } else {
@@ -1894,22 +2003,27 @@ __device__ __forceinline__ void drain_queue(const IntegrateParams& P, const Grp<
   }
 }
 
-template <int G, bool MIXED>
+template <int G, bool MIXED, bool TC = false>
 __global__ void __launch_bounds__(MAX_BLOCK_THREADS, 1) rok4e_integrate_kernel(IntegrateParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   load_exp_table(reinterpret_cast<double*>(smem));
   load_mech(smem + EXP_TAB_BYTES, P.mech, P.mech_copy);
+  if (TC) load_mech(smem + EXP_TAB_BYTES + P.mech_copy, P.mech + P.L.off_nuT, P.tc_bytes);
   __syncthreads();
   MechView m = make_view(smem + EXP_TAB_BYTES, P.L);
   m.etab = reinterpret_cast<const double*>(smem);
   m.nx = P.nx;
+  if (TC) m.nuT = reinterpret_cast<const uint4*>(smem + EXP_TAB_BYTES + P.mech_copy);
   const Grp<G> g;
   const int gid = threadIdx.x / G;
-  double* base = reinterpret_cast<double*>(smem + EXP_TAB_BYTES + P.mech_copy) + (size_t)gid * P.S.stride;
+  double* base = reinterpret_cast<double*>(smem + EXP_TAB_BYTES + P.mech_copy + (TC ? P.tc_bytes : 0)) +
+                 (size_t)gid * P.S.stride;
   const SlotPtrs s = slot_ptrs(base, P.S);
   init_sentinels<MIXED>(s, m.ns, g.lane);
+  if (TC)  // digit rows: row 7 and the reaction padding stay zero
+    for (int i = g.lane; i < 8 * 16 * m.nrt; i += G) s.dig[i] = 0;
   g.sync();
-  drain_queue<G>(P, g, gid, [&](int64_t cell) { integrate_cell<G, MIXED>(m, s, P, cell); });
+  drain_queue<G>(P, g, gid, [&](int64_t cell) { integrate_cell<G, MIXED, TC>(m, s, P, cell); });
 }
 
 // ------------------------------------------- explicit Dormand-Prince 5(4)
@@ -2103,36 +2217,41 @@ struct AdjointParams {
   int nsteps, M;
 };
 
+// One group of G lanes per cell (see adjoint.cuh); 128-thread blocks.
+template <int G>
 __global__ void __launch_bounds__(128) rok4e_adjoint_kernel(AdjointParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   load_exp_table(reinterpret_cast<double*>(smem));
-  load_mech(smem + EXP_TAB_BYTES, P.mech, P.L.bytes);
+  load_mech(smem + EXP_TAB_BYTES, P.mech, P.L.off_nuT);
   __syncthreads();
   MechView m = make_view(smem + EXP_TAB_BYTES, P.L);
   m.etab = reinterpret_cast<const double*>(smem);
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= P.ncell) return;
-  const AdjFrame F = adj_frame(P.wsd, P.wsD, P.A, P.ncell, c);
+  const Grp<G> g;
+  const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  if (c >= P.ncell) return;  // whole groups: a group never straddles the end
+  const AdjFrame F = adj_frame(P.wsd, P.wsD, P.A, c);
   const int N = m.ns + 1;
-  for (int e = 0; e < N; ++e) F.ubar[e] = P.ubar_final[c * N + e];
-  for (int j = 0; j < m.nr; ++j) F.theta[j] = 0.0;
+  for (int e = g.lane; e < N; e += G) F.ubar[e] = P.ubar_final[c * N + e];
+  for (int j = g.lane; j < m.nr; j += G) F.theta[j] = 0.0;
   for (int n = P.nsteps - 1; n >= 0; --n) {
     const double* un = P.ckpt + ((int64_t)n * P.ncell + c) * N;
-    for (int e = 0; e < N; ++e) F.u[e] = un[e];
-    adj_step(m, F, P.p, P.h, P.M);
+    for (int e = g.lane; e < N; e += G) F.u[e] = un[e];
+    adj_step<G>(m, F, P.p, P.h, P.M);
   }
   if (P.grad_u0)
-    for (int e = 0; e < N; ++e) P.grad_u0[c * N + e] = F.ubar[e];
+    for (int e = g.lane; e < N; e += G) P.grad_u0[c * N + e] = F.ubar[e];
 }
 
-// grad[perm[r]] = sum over cells of theta[r][cell]; one block per reaction
+// grad[perm[r]] = sum over cells of theta[cell][r] (cell records stride doubles
+// apart); one block per reaction
 // with a fixed-order tree, so the sum does not depend on scheduling.
 __global__ void __launch_bounds__(256) adjoint_reduce_kernel(const double* __restrict__ theta, int64_t ncell,
-                                                             const int32_t* __restrict__ perm, double* grad) {
+                                                             int64_t stride, const int32_t* __restrict__ perm,
+                                                             double* grad) {
   __shared__ double sh[256];
   const int r = blockIdx.x;
   double acc = 0.0;
-  for (int64_t c = threadIdx.x; c < ncell; c += blockDim.x) acc += theta[(int64_t)r * ncell + c];
+  for (int64_t c = threadIdx.x; c < ncell; c += blockDim.x) acc += theta[c * stride + r];
   sh[threadIdx.x] = acc;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
@@ -2154,29 +2273,36 @@ struct PointParams {
   int64_t ncell;
   double p;
   int mode;  // 0 rhs, 1 analytic jvp, 2 finite-difference jvp, 3 mixed rhs, 4 FP32 analytic jvp,
-             // 5 analytic jvp with the double-float core
+             // 5 analytic jvp with the double-float core, 6 rhs with the tensor-core gather,
+             // 7 analytic jvp with the tensor-core gather
   const double* rho_cell;  // constant-volume densities, or null
   int nx;                  // state components after T (5: auxiliary-temperature system)
+  int64_t mech_copy;       // bytes of the mechanism copied to shared memory (a prefix)
+  int64_t tc_bytes;        // modes 6 and 7: bytes of nu^T tiles copied after that prefix (else 0)
 };
 
 template <int G>
 __global__ void __launch_bounds__(MAX_BLOCK_THREADS) chem_point_kernel(PointParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   load_exp_table(reinterpret_cast<double*>(smem));
-  load_mech(smem + EXP_TAB_BYTES, P.mech, P.L.bytes);
+  load_mech(smem + EXP_TAB_BYTES, P.mech, P.mech_copy);
+  if (P.tc_bytes) load_mech(smem + EXP_TAB_BYTES + P.mech_copy, P.mech + P.L.off_nuT, P.tc_bytes);
   __syncthreads();
   MechView m = make_view(smem + EXP_TAB_BYTES, P.L);
   m.etab = reinterpret_cast<const double*>(smem);
   m.nx = P.nx;
+  if (P.tc_bytes) m.nuT = reinterpret_cast<const uint4*>(smem + EXP_TAB_BYTES + P.mech_copy);
   const Grp<G> g;
   const int gid = threadIdx.x / G;
   const int gpb = blockDim.x / G;
   const int64_t cell = (int64_t)blockIdx.x * gpb + gid;
   if (cell >= P.ncell) return;
-  double* base = reinterpret_cast<double*>(smem + EXP_TAB_BYTES + P.L.bytes) + (size_t)gid * P.S.stride;
+  double* base = reinterpret_cast<double*>(smem + EXP_TAB_BYTES + P.mech_copy + P.tc_bytes) + (size_t)gid * P.S.stride;
   const SlotPtrs s = slot_ptrs(base, P.S);
-  if (P.mode >= 3) init_sentinels<true>(s, m.ns, g.lane);
+  if (P.mode >= 3 && P.mode <= 5) init_sentinels<true>(s, m.ns, g.lane);
   else init_sentinels<false>(s, m.ns, g.lane);
+  if (P.mode >= 6)
+    for (int i = g.lane; i < 8 * 16 * m.nrt; i += G) s.dig[i] = 0;
   const int N = m.ns + 1 + m.nx;
   for (int e = g.lane; e < N; e += G) {
     s.u[e] = P.Y[cell * N + e];
@@ -2188,8 +2314,16 @@ __global__ void __launch_bounds__(MAX_BLOCK_THREADS) chem_point_kernel(PointPara
   CellScalars cs;
   cs.pinv = 1.0 / fabs(pr);
   cs.prec = 0;
-  if (P.mode == 0 || P.mode == 3) {
+  if (P.mode == 7) {
+    cs.prec = 4;
+    rhs_eval_call<G, false, true>(m, s, s.u, nullptr, pr, s.fn, true, &cs);
+    jvp_eval<G, false, true>(m, s, s.u, cs, s.F, s.w);
+    for (int e = g.lane; e < N; e += G) P.out[cell * N + e] = s.w[e];
+    return;
+  }
+  if (P.mode == 0 || P.mode == 3 || P.mode == 6) {
     if (P.mode == 3) rhs_eval_call<G, true>(m, s, s.u, P.src ? s.src : nullptr, pr, s.fr, false, &cs);
+    else if (P.mode == 6) rhs_eval_call<G, false, true>(m, s, s.u, P.src ? s.src : nullptr, pr, s.fr, false, &cs);
     else rhs_eval_call<G>(m, s, s.u, P.src ? s.src : nullptr, pr, s.fr, false, &cs);
     for (int e = g.lane; e < N; e += G) P.out[cell * N + e] = s.fr[e];
     return;
@@ -2523,11 +2657,13 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   if (o.trace_cap < 0 || (o.trace_cap > 0 && !o.trace))
     return set_error(RK_E_INVALID_ARGUMENT, "trace_cap > 0 needs a trace array");
   if (o.fixed_h < 0.0 || !isfinite(o.fixed_h)) return set_error(RK_E_INVALID_ARGUMENT, "fixed_h must be >= 0");
-  if (o.precision < 0 || o.precision > 3) return set_error(RK_E_INVALID_ARGUMENT, "precision must be 0..3");
+  if (o.precision < 0 || o.precision > 4) return set_error(RK_E_INVALID_ARGUMENT, "precision must be 0..4");
   if (method == 1 && o.precision != 0) return set_error(RK_E_INVALID_ARGUMENT, "the explicit integrator is FP64 only");
   const bool mixed = o.precision == 1 || o.precision == 2;  // level 3 runs the FP64 kernel with cs.prec = 3
   const int G = o.lanes_per_cell == 0 ? 32 : o.lanes_per_cell;
   if (G != 8 && G != 16 && G != 32) return set_error(RK_E_INVALID_ARGUMENT, "lanes_per_cell must be 0, 8, 16 or 32");
+  const bool tc = o.precision == 4;
+  if (tc && G != 32) return set_error(RK_E_INVALID_ARGUMENT, "precision 4 (tensor-core gather) needs 32 lanes per cell");
   if (!workspace || workspace_bytes < rk_rok4e_workspace_size(mech, ncell, M, opts))
     return set_error(RK_E_WORKSPACE, "workspace missing or smaller than rk_rok4e_workspace_size");
   if (o.reactor < 0 || o.reactor > 2) return set_error(RK_E_INVALID_ARGUMENT, "reactor must be 0, 1 or 2");
@@ -2540,7 +2676,7 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   P.mech = mech->dev;
   P.L = mech->host.L;
   P.nx = nx;
-  P.S = make_slot(mech->host.L, Meff, mixed, nx, o.precision == 3);
+  P.S = make_slot(mech->host.L, Meff, mixed, nx, o.precision == 3, tc);
   P.precision = o.precision;
   P.Y = Y;
   P.src = src;
@@ -2564,7 +2700,9 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   P.rho_cell = o.reactor == 1 ? o.rho_cell : nullptr;
   {
     const MechLayout& L = mech->host.L;
-    P.mech_copy = (method == 1 || o.precision == 0) ? L.bytes_fp64 : (o.precision == 2 ? L.bytes_f32 : L.bytes_df);
+    P.mech_copy = (method == 1 || o.precision == 0 || tc) ? L.bytes_fp64
+                                                          : (o.precision == 2 ? L.bytes_f32 : L.bytes_df);
+    P.tc_bytes = tc ? (int64_t)16 * 32 * L.nst * L.nrt : 0;
   }
   P.qstride = queue_stride(ncell);
   P.order = nullptr;
@@ -2613,6 +2751,14 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
     if (order == 3) P.subq = plan.cells_per_block % 4 == 0 ? 4 : (plan.cells_per_block % 2 == 0 ? 2 : 1); \
     rok4e_integrate_kernel<GG, MX><<<plan.blocks, plan.cells_per_block * GG, plan.smem, stream>>>(P); \
   } while (0)
+#define RK_LAUNCH_TC()                                                                             \
+  do {                                                                                             \
+    rc = plan_for<32>(rok4e_integrate_kernel<32, false, true>, mech, P.S, o.cells_per_block, ncell, true, \
+                      &plan, o.blocks_per_sm, order == 3, P.mech_copy + P.tc_bytes);                 \
+    if (rc) return rc;                                                                             \
+    if (order == 3) P.subq = plan.cells_per_block % 4 == 0 ? 4 : (plan.cells_per_block % 2 == 0 ? 2 : 1); \
+    rok4e_integrate_kernel<32, false, true><<<plan.blocks, plan.cells_per_block * 32, plan.smem, stream>>>(P); \
+  } while (0)
 #define RK_LAUNCH_DP(GG)                                                                              \
   do {                                                                                                \
     rc = plan_for<GG>(rkdp_integrate_kernel<GG>, mech, P.S, o.cells_per_block, ncell, true, &plan,    \
@@ -2626,7 +2772,8 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
     else if (G == 16) RK_LAUNCH_DP(16);
     else RK_LAUNCH_DP(8);
   } else if (G == 32) {
-    if (mixed) RK_LAUNCH(32, true);
+    if (tc) RK_LAUNCH_TC();
+    else if (mixed) RK_LAUNCH(32, true);
     else RK_LAUNCH(32, false);
   } else if (G == 16) {
     if (mixed) RK_LAUNCH(16, true);
@@ -2636,6 +2783,7 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
     else RK_LAUNCH(8, false);
   }
 #undef RK_LAUNCH
+#undef RK_LAUNCH_TC
 #undef RK_LAUNCH_DP
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "rok4e_integrate_kernel launch");
@@ -2707,7 +2855,7 @@ static int point_call(const rk_mech* mech, const double* Y, const double* src, c
   if (rc) return rc;
   if (ncell < 0) return set_error(RK_E_INVALID_ARGUMENT, "ncell < 0");
   if (ncell == 0) return RK_OK;
-  const bool needs_v = mode == 1 || mode == 2 || mode == 4;
+  const bool needs_v = mode == 1 || mode == 2 || mode == 4 || mode == 5 || mode == 7;
   if (!Y || !out || (needs_v && !V)) return set_error(RK_E_INVALID_ARGUMENT, "null array");
   if (out == Y) return set_error(RK_E_INVALID_ARGUMENT, "output must not alias the state");
   if (!rho_cell && !(p > 0.0)) return set_error(RK_E_INVALID_ARGUMENT, "pressure must be > 0");
@@ -2716,7 +2864,7 @@ static int point_call(const rk_mech* mech, const double* Y, const double* src, c
   P.nx = nx;
   P.mech = mech->dev;
   P.L = mech->host.L;
-  P.S = make_slot(mech->host.L, 1, mode >= 3, nx, mode == 5);
+  P.S = make_slot(mech->host.L, 1, mode >= 3 && mode <= 5, nx, mode == 5, mode >= 6);
   P.Y = Y;
   P.src = src;
   P.V = V;
@@ -2724,8 +2872,13 @@ static int point_call(const rk_mech* mech, const double* Y, const double* src, c
   P.ncell = ncell;
   P.p = p;
   P.mode = mode;
+  {
+    const MechLayout& L = mech->host.L;  // everything but the nu^T tiles; the tiles only with the FP64 arrays
+    P.mech_copy = mode >= 6 ? L.bytes_fp64 : L.off_nuT;
+    P.tc_bytes = mode >= 6 ? (int64_t)16 * 32 * L.nst * L.nrt : 0;
+  }
   LaunchPlan plan;
-  rc = plan_for<32>(chem_point_kernel<32>, mech, P.S, 8, ncell, false, &plan);
+  rc = plan_for<32>(chem_point_kernel<32>, mech, P.S, 8, ncell, false, &plan, 0, false, P.mech_copy + P.tc_bytes);
   if (rc) return rc;
   chem_point_kernel<32><<<plan.blocks, plan.cells_per_block * 32, plan.smem, (cudaStream_t)stream>>>(P);
   cudaError_t e = cudaGetLastError();
@@ -2739,9 +2892,14 @@ int rk_chem_rhs(const rk_mech* mech, const double* Y, const double* src, double 
 
 int rk_chem_jvp(const rk_mech* mech, const double* Y, const double* V, double p, double* JV, int64_t ncell,
                 int32_t mode, void* stream) {
-  if (mode < 0 || mode > 3) return set_error(RK_E_INVALID_ARGUMENT, "mode must be 0..3");
-  return point_call(mech, Y, nullptr, V, p, JV, ncell, mode == 0 ? 1 : (mode == 1 ? 2 : (mode == 2 ? 4 : 5)),
-                    stream);
+  if (mode < 0 || mode > 4) return set_error(RK_E_INVALID_ARGUMENT, "mode must be 0..4");
+  static const int point_mode[5] = {1, 2, 4, 5, 7};
+  return point_call(mech, Y, nullptr, V, p, JV, ncell, point_mode[mode], stream);
+}
+
+int rk_chem_rhs_tc(const rk_mech* mech, const double* Y, const double* src, double p, double* dYdt,
+                   int64_t ncell, void* stream) {
+  return point_call(mech, Y, src, nullptr, p, dYdt, ncell, 6, stream);
 }
 
 int rk_chem_rhs_mixed(const rk_mech* mech, const double* Y, const double* src, double p, double* dYdt,
@@ -3109,6 +3267,7 @@ static AdjLayout make_adj_layout(const MechLayout& L, int M) {
   A.dcp = take(ns1); A.om = take(ns1); A.k = take(nr); A.rfac = take(nr); A.q = take(nr); A.Ms = take(ntb);
   A.dlnk = take(ntb); A.dkdM = take(ntb); A.omg = take(ntb); A.sc = take(SC_N); A.Cbar = take(ns1);
   A.gbar = take(ns1); A.ombar = take(ns1); A.Mbar = take(ntb); A.ubd = take(N); A.fbd = take(N);
+  A.Pbb = take(nr); A.drf = take(nr);
   A.rows_D = r;
   return A;
 }
@@ -3154,6 +3313,13 @@ int rk_rok4e_fixed_steps(const rk_mech* mech, double* Y, int64_t ncell, double p
 int rk_rok4e_adjoint(const rk_mech* mech, const double* checkpoints, const double* ubar, int64_t ncell, double p,
                      double h, int32_t nsteps, int32_t krylov_dim, double* grad_lnA, double* grad_u0,
                      void* workspace, size_t workspace_bytes, void* stream) {
+  return rk_rok4e_adjoint_ex(mech, checkpoints, ubar, ncell, p, h, nsteps, krylov_dim, 0, grad_lnA, grad_u0,
+                             workspace, workspace_bytes, stream);
+}
+
+int rk_rok4e_adjoint_ex(const rk_mech* mech, const double* checkpoints, const double* ubar, int64_t ncell, double p,
+                        double h, int32_t nsteps, int32_t krylov_dim, int32_t lanes_per_cell, double* grad_lnA,
+                        double* grad_u0, void* workspace, size_t workspace_bytes, void* stream) {
   int rc = check_mech(mech);
   if (rc) return rc;
   if (ncell < 0 || nsteps < 0) return set_error(RK_E_INVALID_ARGUMENT, "ncell and nsteps must be >= 0");
@@ -3186,12 +3352,31 @@ int rk_rok4e_adjoint(const rk_mech* mech, const double* checkpoints, const doubl
       e = cudaMemcpyAsync(grad_u0, ubar, (size_t)ncell * N * sizeof(double), cudaMemcpyDeviceToDevice, st);
     return e == cudaSuccess ? RK_OK : cuda_error(e, "adjoint trivial case");
   }
-  const size_t smem = (size_t)mech->host.L.bytes + EXP_TAB_BYTES;
-  cudaError_t e = cudaFuncSetAttribute(rok4e_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
-  rok4e_adjoint_kernel<<<(unsigned)((ncell + 127) / 128), 128, smem, st>>>(P);
+  int G = lanes_per_cell;
+  if (G == 0) {  // auto: the fewest lanes that still give every SM sub-partition ~4 warps
+    int n_sm = 0;
+    size_t smem_max = 0;
+    rc = device_props(&n_sm, &smem_max);
+    if (rc) return rc;
+    const int64_t want_threads = (int64_t)n_sm * 4 * 4 * 32;
+    G = ncell * 8 >= want_threads ? 8 : (ncell * 16 >= want_threads ? 16 : 32);
+  }
+  if (G != 8 && G != 16 && G != 32) return set_error(RK_E_INVALID_ARGUMENT, "lanes_per_cell must be 0, 8, 16 or 32");
+  const size_t smem = (size_t)mech->host.L.off_nuT + EXP_TAB_BYTES;
+  const unsigned blocks = (unsigned)((ncell * G + 127) / 128);
+  cudaError_t e = cudaSuccess;
+#define RK_LAUNCH_ADJ(GG)                                                                                        \
+  do {                                                                                                           \
+    e = cudaFuncSetAttribute(rok4e_adjoint_kernel<GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");                                          \
+    rok4e_adjoint_kernel<GG><<<blocks, 128, smem, st>>>(P);                                                      \
+  } while (0)
+  if (G == 8) RK_LAUNCH_ADJ(8);
+  else if (G == 16) RK_LAUNCH_ADJ(16);
+  else RK_LAUNCH_ADJ(32);
+#undef RK_LAUNCH_ADJ
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "rok4e_adjoint_kernel launch");
-  adjoint_reduce_kernel<<<nr, 256, 0, st>>>(P.wsd + (int64_t)P.A.theta * ncell, ncell,
+  adjoint_reduce_kernel<<<nr, 256, 0, st>>>(P.wsd + P.A.theta, ncell, P.A.rows_d,
                                            reinterpret_cast<const int32_t*>(mech->dev + mech->host.L.off_perm),
                                            grad_lnA);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "adjoint_reduce_kernel launch");

@@ -4,7 +4,9 @@ Precision level 1 gathers w = nu^T q (in the right-hand side and the
 Jacobian-vector product) in double-float on the FP32 pipe, takes the first
 Gram-Schmidt pass of Arnoldi with FP32 inner products and the exponentials'
 polynomial tails in FP32; level 2 also runs the Jacobian-vector products in
-FP32; level 3 keeps the Krylov path in FP64 with a double-float J v core.
+FP32; level 3 keeps the Krylov path in FP64 with a double-float J v core;
+level 4 keeps everything FP64 but forms w = nu^T q on the tensor cores from
+exact 8-bit digit slices of q.
 The bar is the library's, for every level: |dY| <= 1e-8 + 1e-6 |Y| and
 |dT| <= 1e-6 K against the FP64 oracle replaying the GPU run's own step
 sequence.
@@ -90,6 +92,102 @@ def test_double_float_jvp_close_to_oracle(rk, name):
     assert np.max(np.abs(out - ref) / scale) < 1e-10
 
 
+@pytest.mark.parametrize("name", ["small", "flame1d", "batched", "adjoint"])
+def test_tensor_core_rhs_close_to_oracle(rk, name):
+    """w = nu^T q on the tensor cores (precision 4): every q_j is kept down
+    to 2^-55 of the cell's largest rate and the rest is exact, so the source
+    term meets the FP64 path's own bar against the oracle, with and without
+    a source."""
+    from oracle.kinetics import Kinetics
+    from synth.fields import field_uniform
+
+    w, mech = _mech(name)
+    kin = Kinetics(mech)
+    U = field_uniform(67, mech.n_species, 23, 300.0, 3000.0)
+    src = np.random.default_rng(8).normal(size=U.shape) * 10.0
+    m = rk.mech_load(mech)
+    Ug = torch.tensor(U, device="cuda")
+    for s in (None, src):
+        sg = None if s is None else torch.tensor(s, device="cuda")
+        out = rk.chem_rhs_tc(m, Ug, P, src=sg).cpu().numpy()
+        ref = np.array([kin.rhs(u, P, None if s is None else s[i]) for i, u in enumerate(U)])
+        scale = np.max(np.abs(ref), axis=1, keepdims=True)
+        err = np.max(np.abs(out - ref) / scale)
+        fp64 = rk.chem_rhs(m, Ug, P, src=sg).cpu().numpy()
+        print(f"{name}: tensor-core RHS vs oracle {err:.2e} of the row scale; FP64 path "
+              f"{np.max(np.abs(fp64 - ref) / scale):.2e}")
+        assert err < 1e-11
+
+
+def test_tensor_core_tiles_that_do_not_fit_are_refused(rk):
+    """The 100-species / 500-reaction mechanism's nu^T tiles (7 x 32 of
+    them, 112 KiB) fit beside one cell of the point kernel but leave no room
+    for a cell of the integrator with M = 4: precision 4 is refused on the
+    host with an error, nothing is launched, and the FP64 integration of the
+    same cells still runs."""
+    w, mech = _mech("adjoint")
+    from synth.fields import field_uniform
+
+    U = torch.tensor(field_uniform(4, mech.n_species, 3, 900.0, 1500.0), device="cuda")
+    m = rk.mech_load(mech)
+    with pytest.raises(rk.RokError, match="shared memory"):
+        rk.rok4e_integrate(m, U.clone(), w.dt, w.rtol, w.atol, 4, opts=rk.Opts(precision=4))
+    st = torch.zeros(4, 4, dtype=torch.int32, device="cuda")
+    rk.rok4e_integrate(m, U, w.dt, w.rtol, w.atol, 4, stats=st)
+    torch.cuda.synchronize()
+    assert torch.isfinite(U).all() and int(st[:, 3].abs().sum()) == 0
+
+
+def test_tensor_core_rhs_extreme_cells(rk):
+    """Cells whose rates span the widest ranges: 300 K (rates over hundreds
+    of orders of magnitude), 3000 K, and cells of one species with every other
+    at 1e-30 (nearly every rate tiny beside the few of that species).  The
+    digits keep each rate down to 2^-55 of the largest, so the bar against the
+    oracle is the FP64 path's."""
+    from oracle.kinetics import Kinetics
+
+    w, mech = _mech("batched")
+    kin = Kinetics(mech)
+    ns = mech.n_species
+    rows = []
+    for T in (300.0, 3000.0):
+        u = np.full(ns + 1, 1.0 / ns)
+        u[ns] = T
+        rows.append(u)
+    for k in range(0, ns, 5):
+        u = np.full(ns + 1, 1e-30)
+        u[k] = 1.0 - (ns - 1) * 1e-30
+        u[ns] = 1400.0
+        rows.append(u)
+    U = np.array(rows)
+    m = rk.mech_load(mech)
+    Ug = torch.tensor(U, device="cuda")
+    out = rk.chem_rhs_tc(m, Ug, P).cpu().numpy()
+    ref = np.array([kin.rhs(u, P) for u in U])
+    scale = np.max(np.abs(ref), axis=1, keepdims=True)
+    assert np.all(np.isfinite(out))
+    assert np.max(np.abs(out - ref) / scale) < 1e-11
+
+
+@pytest.mark.parametrize("name", ["small", "flame1d", "batched"])
+def test_tensor_core_jvp_close_to_oracle(rk, name):
+    """The analytic J v with nu^T dq on the tensor cores (rk_chem_jvp mode
+    4) against the oracle's analytic Jacobian, at the FP64 product's bar."""
+    from oracle.kinetics import Kinetics
+    from synth.fields import field_uniform
+
+    w, mech = _mech(name)
+    kin = Kinetics(mech)
+    U = field_uniform(40, mech.n_species, 29, 500.0, 2800.0)
+    V = np.random.default_rng(6).normal(size=U.shape)
+    V /= np.linalg.norm(V, axis=1, keepdims=True)
+    m = rk.mech_load(mech)
+    out = rk.chem_jvp(m, torch.tensor(U, device="cuda"), torch.tensor(V, device="cuda"), P, mode=4).cpu().numpy()
+    ref = np.array([kin.jvp(u, P, v) for u, v in zip(U, V)])
+    scale = np.max(np.abs(ref), axis=1, keepdims=True)
+    assert np.max(np.abs(out - ref) / scale) < 1e-10
+
+
 def _run(rk, mech, U, w, precision, cap=8192, M=4):
     m = rk.mech_load(mech)
     Y = torch.tensor(U, device="cuda")
@@ -101,7 +199,7 @@ def _run(rk, mech, U, w, precision, cap=8192, M=4):
     return Y.cpu().numpy(), st.cpu().numpy(), tr.cpu().numpy()
 
 
-@pytest.mark.parametrize("precision", [1, 2, 3])
+@pytest.mark.parametrize("precision", [1, 2, 3, 4])
 def test_mixed_integration_error_vs_fp64_oracle(rk, precision):
     """Mixed-precision ROK4E on the small workload (10 species / 24
     reactions, one 1e-6 s step), replayed through the FP64 oracle, at the
@@ -125,7 +223,7 @@ def test_mixed_integration_error_vs_fp64_oracle(rk, precision):
     assert dT.max() <= 1e-6, dT.max()
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2, 3])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3, 4])
 def test_flame_mechanism_levels_vs_fp64_oracle(rk, precision):
     """The precision levels on the 1-D flame's mechanism (30 species / 150
     reactions, 4 third-body, 2 Troe) and tanh field: the reaction sub-step of
@@ -181,7 +279,7 @@ def test_mixed_split_steps_vs_fp64_gpu(rk):
     _, U0 = field_tanh_front(512, mech.n_species, w.field_seed)
     dx = 1e-2 / 512
     res = {}
-    for prec in (0, 1, 2, 3):
+    for prec in (0, 1, 2, 3, 4):
         U = torch.tensor(U0, device="cuda")
         hc = torch.zeros(512, dtype=torch.float64, device="cuda")
         for _ in range(5):
@@ -190,7 +288,7 @@ def test_mixed_split_steps_vs_fp64_gpu(rk):
         torch.cuda.synchronize()
         res[prec] = U.cpu().numpy()
     ns = mech.n_species
-    for prec in (1, 2, 3):
+    for prec in (1, 2, 3, 4):
         dY = np.abs(res[prec][:, :ns] - res[0][:, :ns])
         dT = np.abs(res[prec][:, ns] - res[0][:, ns])
         print(f"mixed level {prec} vs FP64 GPU after 5 split steps: max |dY| {dY.max():.3e} (per species "
