@@ -852,7 +852,7 @@ def run_adjoint(args, dev):
     t_f, t_b = statistics.mean(tf), statistics.mean(tb)
     # the adjoint alone at each lane count (one cell per 8, 16 or 32 lanes)
     sweep = {}
-    for G in (8, 16, 32):
+    for G in (4, 8, 16, 32):
         ts = []
         for rep in range(2):
             ev[1].record(stream)

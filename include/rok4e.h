@@ -430,10 +430,10 @@ size_t rk_rok4e_adjoint_workspace_size(const rk_mech* mech, int64_t ncell, int32
 int rk_rok4e_adjoint(const rk_mech* mech, const double* checkpoints, const double* ubar, int64_t ncell,
                      double p, double h, int32_t nsteps, int32_t krylov_dim, double* grad_lnA,
                      double* grad_u0, void* workspace, size_t workspace_bytes, void* stream);
-/* As rk_rok4e_adjoint, with lanes_per_cell lanes of a warp (8, 16 or 32)
+/* As rk_rok4e_adjoint, with lanes_per_cell lanes of a warp (4, 8, 16 or 32)
  * sharing each cell's species, reaction and state loops; 0 chooses from ncell
- * (fewer lanes per cell when there are cells enough to fill the GPU).  The
- * result does not depend on the lane count beyond rounding. */
+ * (8, or more when there are too few cells to give every SM sub-partition a
+ * warp).  The result does not depend on the lane count beyond rounding. */
 int rk_rok4e_adjoint_ex(const rk_mech* mech, const double* checkpoints, const double* ubar, int64_t ncell,
                         double p, double h, int32_t nsteps, int32_t krylov_dim, int32_t lanes_per_cell,
                         double* grad_lnA, double* grad_u0, void* workspace, size_t workspace_bytes,

@@ -471,7 +471,7 @@ def rok4e_adjoint_workspace_size(m: Mechanism, ncell: int, krylov_dim: int) -> i
 def rok4e_adjoint(m: Mechanism, checkpoints, ubar, h, nsteps, krylov_dim=4, *, p=101325.0, grad_u0=None,
                   workspace=None, stream=None, lanes_per_cell=0):
     """Discrete adjoint of rok4e_fixed_steps: returns (grad_lnA [Nr], grad_u0 [ncell, N] or None).
-    lanes_per_cell: 8, 16 or 32 lanes per cell, 0 chosen from the cell count (rk_rok4e_adjoint_ex)."""
+    lanes_per_cell: 4, 8, 16 or 32 lanes per cell, 0 chosen from the cell count (rk_rok4e_adjoint_ex)."""
     n = _ncell(ubar, m)
     if workspace is None:
         workspace = torch.empty(rok4e_adjoint_workspace_size(m, n, krylov_dim), dtype=torch.uint8,

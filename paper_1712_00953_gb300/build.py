@@ -2,9 +2,11 @@
 
     python -m paper_1712_00953_gb300.build
 
-Two translation units compile in parallel: the host-only mechanism packing
-(g++) and the kernels plus C ABI (nvcc, -gencode arch=compute_103a,code=sm_103a).
-The CUDA runtime is linked statically so the library only needs the driver.
+The translation units compile in parallel: the host-only mechanism packing
+(g++), the C ABI with the small kernels (rok4e_kernels.cu) and one file per
+group of heavy kernel instantiations (k_*.cu), all with nvcc -gencode
+arch=compute_103a,code=sm_103a.  The CUDA runtime is linked statically so the
+library only needs the driver.
 """
 
 from __future__ import annotations
@@ -39,22 +41,34 @@ def build(verbose: bool = False, extra_nvcc=()) -> str:
     bdir = os.path.join(OUT_DIR, "obj")
     os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
-    cu = os.path.join(CSRC, "rok4e_kernels.cu")
-    cpp = os.path.join(CSRC, "mech.cpp")
-    o_cu = os.path.join(bdir, "rok4e_kernels.o")
+    cus = sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
+    cmds, objs = [], []
+    for f in cus:
+        o = os.path.join(bdir, f[:-3] + ".o")
+        cmds.append([nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
+                     "--expt-relaxed-constexpr", "-c", os.path.join(CSRC, f), "-o", o, *extra_nvcc])
+        objs.append(o)
     o_cpp = os.path.join(bdir, "mech.o")
-    cmd_cu = [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-              "--expt-relaxed-constexpr", "-c", cu, "-o", o_cu, *extra_nvcc]
-    cmd_cpp = ["g++", "-O2", "-std=c++17", "-fPIC", "-I", INCLUDE, "-I", CSRC, "-c", cpp, "-o", o_cpp]
-    procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT) for c in (cmd_cu, cmd_cpp)]
-    outs = [p.communicate()[0].decode(errors="replace") for p in procs]
-    for c, p, o in zip((cmd_cu, cmd_cpp), procs, outs):
+    cmds.append(["g++", "-O2", "-std=c++17", "-fPIC", "-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, "mech.cpp"),
+                 "-o", o_cpp])
+    objs.append(o_cpp)
+    # at most one compile per core
+    jobs = max(1, min(len(cmds), os.cpu_count() or 1))
+    pending, running = list(cmds), []
+    while pending or running:
+        while pending and len(running) < jobs:
+            c = pending.pop(0)
+            running.append((c, subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        c, p = running.pop(0)
+        o = p.communicate()[0].decode(errors="replace")
         if verbose and o.strip():
             print(o)
         if p.returncode != 0:
+            for _, q in running:
+                q.wait()
             raise RuntimeError(f"compile failed: {' '.join(c)}\n{o}")
     tmp = lib_path() + ".tmp"
-    cmd_ld = [nvcc, ARCH, "-shared", "-cudart", "static", o_cu, o_cpp, "-o", tmp]
+    cmd_ld = [nvcc, ARCH, "-shared", "-cudart", "static", *objs, "-o", tmp]
     r = subprocess.run(cmd_ld, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd_ld)}\n{r.stdout.decode(errors='replace')}")

@@ -1,7 +1,7 @@
 // Discrete adjoint of fixed-step ROK4E (Algorithm 1 with h held fixed) with
 // respect to the initial state and the log pre-exponential factors ln A_j.
 //
-// A group of G lanes of one warp (G = 8, 16 or 32) integrates one cell
+// A group of G lanes of one warp (G = 4, 8, 16 or 32) integrates one cell
 // backwards through the recorded steps.  For
 // each step n (last first) it reloads u_n from the checkpoints, recomputes the
 // step's internals -- f_n, the Arnoldi basis Q and Hessenberg H (CGS2), the

@@ -1,0 +1,46 @@
+// Definitions of the per-cell kernel launches declared in device.cuh.  Only
+// the k_*.cu translation units include this header, each explicitly
+// instantiating its share, so every heavy kernel is compiled exactly once.
+#pragma once
+#include "device.cuh"
+
+namespace rk {
+
+// Persistent ROK4E launch: as many cells per block as shared memory allows
+// (or a.cells_per_block), one wave of blocks sized to the device.
+template <int G, bool MIXED, bool TC>
+int launch_rok4e(const IntegrateLaunch& a) {
+  IntegrateParams& P = *a.P;
+  LaunchPlan plan;
+  const int rc = plan_for<G>(rok4e_integrate_kernel<G, MIXED, TC>, a.mech, P.S, a.cells_per_block, a.ncell, true,
+                             &plan, a.blocks_per_sm, a.static_bins, P.mech_copy + P.tc_bytes);
+  if (rc) return rc;
+  if (a.static_bins) P.subq = plan.cells_per_block % 4 == 0 ? 4 : (plan.cells_per_block % 2 == 0 ? 2 : 1);
+  rok4e_integrate_kernel<G, MIXED, TC><<<plan.blocks, plan.cells_per_block * G, plan.smem, a.stream>>>(P);
+  return RK_OK;
+}
+
+// Persistent explicit Dormand-Prince launch, planned like ROK4E's.
+template <int G>
+int launch_rkdp(const IntegrateLaunch& a) {
+  IntegrateParams& P = *a.P;
+  LaunchPlan plan;
+  const int rc = plan_for<G>(rkdp_integrate_kernel<G>, a.mech, P.S, a.cells_per_block, a.ncell, true, &plan,
+                             a.blocks_per_sm, a.static_bins, P.mech_copy);
+  if (rc) return rc;
+  if (a.static_bins) P.subq = plan.cells_per_block % 4 == 0 ? 4 : (plan.cells_per_block % 2 == 0 ? 2 : 1);
+  rkdp_integrate_kernel<G><<<plan.blocks, plan.cells_per_block * G, plan.smem, a.stream>>>(P);
+  return RK_OK;
+}
+
+// The adjoint: 128-thread blocks of 128 / G cells, the mechanism in shared memory.
+template <int G>
+int launch_adjoint(const AdjointParams& P, size_t smem, unsigned blocks, cudaStream_t st) {
+  const cudaError_t e =
+      cudaFuncSetAttribute(rok4e_adjoint_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
+  rok4e_adjoint_kernel<G><<<blocks, 128, smem, st>>>(P);
+  return RK_OK;
+}
+
+}  // namespace rk

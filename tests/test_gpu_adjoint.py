@@ -113,7 +113,7 @@ def test_adjoint_matches_gpu_central_differences(rk):
 
 @pytest.mark.parametrize("name", ["small", "mixed", "adjoint"])
 def test_adjoint_lane_counts_agree(rk, name):
-    """8, 16 and 32 lanes per cell split the same loops differently, so the
+    """4, 8, 16 and 32 lanes per cell split the same loops differently, so the
     gradients agree to rounding; a repeated call with the same lane count
     gives the same bits (every sum has a fixed order)."""
     w, mech, U = _setup(name, 40)
@@ -125,14 +125,14 @@ def test_adjoint_lane_counts_agree(rk, name):
     ubar = torch.zeros_like(Y)
     ubar[:, -1] = 1.0
     res = {}
-    for G in (8, 16, 32, 8):
+    for G in (4, 8, 16, 32, 8):
         g0 = torch.empty_like(Y)
         grad, g0 = rk.rok4e_adjoint(m, ck, ubar, h, nsteps, 4, grad_u0=g0, lanes_per_cell=G)
         torch.cuda.synchronize()
         if G in res:
             assert torch.equal(grad, res[G][0]) and torch.equal(g0, res[G][1])
         res[G] = (grad.clone(), g0.clone())
-    for G in (16, 32):
+    for G in (4, 16, 32):
         for a, b in zip(res[G], res[8]):
             assert torch.max(torch.abs(a - b)) <= 1e-12 * torch.max(torch.abs(b)), (G, float(torch.max(torch.abs(a - b))))
     with pytest.raises(rk.RokError, match="lanes_per_cell"):
