@@ -55,11 +55,11 @@ GOLDEN = 0.6180339887498949
 # dram__bytes_read.sum + dram__bytes_write.sum of one integration launch from
 # an ncu capture of the current kernel (bytes per launch), keyed by workload;
 # None while no capture of the current kernel exists.  batched: 2^18 cells
-# captured (267,186,432 B), scaled by cells to the 2^20-cell launch (the
+# captured (264,804,096 B), scaled by cells to the 2^20-cell launch (the
 # traffic per cell does not depend on the launch size); flame1d: the 8th split
 # step's integration launch, whose 0.5 MB state stays in L2 (writes are not
 # all flushed by the kernel's end).
-TRAFFIC = {"batched": 267186432 * 4, "flame1d": 1397760 + 125440}
+TRAFFIC = {"batched": (136091904 + 128712192) * 4, "flame1d": 1395456 + 125952}
 
 
 def _env_int(k, d):
@@ -96,6 +96,38 @@ def flop_model(mech, M):
 
 
 EXP_FLOPS = 20  # one FP64 exp counted as 10 operations (the table-driven method's count)
+
+
+def adjoint_flop_model(mech, M):
+    """Algorithmic FP64 flops of the adjoint of one fixed ROK4E step of one
+    cell (rk_rok4e_adjoint), FMA = 2, one exp or log = EXP_FLOPS, a division 1.
+
+    Value passes of the right-hand side: per species 46 (thermo polynomials,
+    C, the sums of the temperature equation, f), per net coefficient 2 (the
+    gather), per reaction 16 plus 6 for a reversible one, two exponentials per
+    reversible reaction and one per other, 2 per species and third-body
+    reaction.  Their reverse: per species 34 plus 3 per reaction slot the
+    species fills, per reaction 26.  A dual (value, tangent) pass costs 2.5x
+    its value pass's arithmetic plus one multiply per exponential.  Per step:
+    6 value and 8 dual forward passes (f at u_n twice, at the two stage
+    arguments twice, and M = 4 J q_j twice), 3 value and 4 dual reverse
+    passes; the Krylov and stage algebra forward and reverse three times the
+    forward step's (the integrator's Arnoldi and attempt counts)."""
+    ns, nr = mech.n_species, mech.n_reactions
+    kind = np.asarray(mech.kind)
+    rev = np.asarray(mech.reversible).astype(bool)
+    n_tb = int((kind > 0).sum())
+    n_rev = int(rev.sum())
+    slots = int(sum(sum(abs(int(n)) for s_, n in zip(mech.rxn_sp[j], mech.rxn_nu[j]) if s_ >= 0) for j in range(nr)))
+    fm = flop_model(mech, M)
+    nnz_term = fm["rhs"] - (ns * 40 + nr * 16 + n_tb * 2 * ns + 10)  # 2 per net coefficient (+ Troe)
+    fwd_v = ns * 46 + nnz_term + nr * 16 + n_rev * 6 + n_tb * 2 * ns
+    exps = nr + n_rev
+    rev_v = ns * 34 + 3 * slots + nr * 26
+    fwd_d = 2.5 * fwd_v + exps
+    rev_d = 2.5 * rev_v
+    krylov = 3 * (fm["arnoldi"] + fm["attempt"])
+    return float(6 * (fwd_v + EXP_FLOPS * exps) + 8 * (fwd_d + EXP_FLOPS * exps) + 3 * rev_v + 4 * rev_d + krylov)
 
 
 def algorithmic_flops(model, stats, M, exp_flops=EXP_FLOPS):
@@ -906,9 +938,17 @@ def run_adjoint(args, dev):
         cs_cells.append({"cell": c, "T0_K": float(U_host[c, -1]), "adjoint": got1, "oracle_complex_step": ref1,
                          "rel_diff": abs(got1 - ref1) / max(abs(ref1), 1e-300),
                          "oracle_s": time.perf_counter() - t0})
+    aflops = adjoint_flop_model(mech, M) * n * nsteps
+    achieved = aflops / t_b / 1e12
     return {"workload": "adjoint: 4096 cells, 100 species / 500 reactions, 50 fixed ROK4E steps of 1e-7 s, "
                         "M=4; gradient of sum_c T_c(final) w.r.t. all 500 ln A_j",
             "value": n * nsteps / (t_f + t_b), "unit": "cell-steps/s (forward with checkpoints + adjoint)",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK, "traffic": None,
+                         "kernel": "rok4e_adjoint_kernel<8>",
+                         "algorithmic_tflop": aflops / 1e12,
+                         "model": "bench.py adjoint_flop_model: value and dual right-hand-side passes and their "
+                                  "reverse per step, Krylov and stage algebra"},
             "forward_s": t_f, "adjoint_s": t_b, "reps": len(tf), "adjoint_lanes_per_cell": sweep,
             "kernels": "rok4e_integrate_kernel (fixed steps), rok4e_adjoint_kernel, adjoint_reduce_kernel",
             "gradient_check": {
@@ -1194,6 +1234,8 @@ def main():
     ap.add_argument("--unit-costs", action="store_true",
                     help="small RHS / J v / integration launches (for ncu instruction counts) and the probes")
     ap.add_argument("--skip-probes", action="store_true")
+    ap.add_argument("--only", default="", choices=["", "adjoint", "flame1d", "small"],
+                    help="run one workload's block alone and print it (no headline line)")
     ap.add_argument("--study-kcap", type=float, default=0.0,
                     help="efficiency study on a variant of the batched mechanism with this cap on k C (1/s)")
     ap.add_argument("--study", default="", choices=["", "efficiency"],
@@ -1215,6 +1257,15 @@ def main():
         return run_unit_costs(args)
     if args.study == "efficiency":
         return run_study(args, local_rank)
+    if args.only:
+        import torch
+
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        block = {"adjoint": lambda: run_adjoint(args, dev), "flame1d": lambda: run_flame(args, dev, 0),
+                 "small": lambda: run_small(args, dev)}[args.only]()
+        print(json.dumps({"only": args.only, args.only: block}))
+        return 0
     return run_ours(args, rank, world, local_rank)
 
 

@@ -122,54 +122,95 @@ __device__ inline AdjFrame adj_frame(double* wsd, Dual* wsD, const AdjLayout& L,
   return f;
 }
 
-// sum of a dual over the group (all lanes receive the same bits)
+// sum over the group (all lanes receive the same bits)
 template <int G>
 __device__ __forceinline__ Dual gsum(const Grp<G>& g, Dual a) {
   return Dual{g.sum(a.v), g.sum(a.t)};
 }
+template <int G>
+__device__ __forceinline__ double gsum(const Grp<G>& g, double a) {
+  return g.sum(a);
+}
+
+// The right-hand side passes come in two scalar types: Dual where the
+// tangents are needed (the Jacobian-vector products of the Arnoldi process and
+// their reverse), double where only values are (f at u_n and at the stage
+// arguments, and their reverse), which halves the arithmetic of those passes.
+// The tape keeps Duals either way (tangent 0 after a value pass).
+template <class Sc>
+__device__ __forceinline__ Sc sv(double v);
+template <>
+__device__ __forceinline__ double sv<double>(double v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ Dual sv<Dual>(double v) {
+  return Dual{v, 0.0};
+}
+template <class Sc>
+__device__ __forceinline__ Sc rd(const Dual& x);
+template <>
+__device__ __forceinline__ double rd<double>(const Dual& x) {
+  return x.v;
+}
+template <>
+__device__ __forceinline__ Dual rd<Dual>(const Dual& x) {
+  return x;
+}
+__device__ __forceinline__ Dual wr(double a) { return Dual{a, 0.0}; }
+__device__ __forceinline__ Dual wr(Dual a) { return a; }
+__device__ __forceinline__ double val(double a) { return a; }
+__device__ __forceinline__ double val(Dual a) { return a.v; }
+__device__ __forceinline__ double dexp(double a, const double* tab) { return exp_fast(a, tab); }
+__device__ __forceinline__ double dlog(double a) { return log(a); }
+__device__ __forceinline__ double dlog10(double a) { return log10(a); }
+// the ln A gradient contribution: the value, or (tangent passes) the tangent
+__device__ __forceinline__ double theta_part(double th, bool) { return th; }
+__device__ __forceinline__ double theta_part(Dual th, bool tangent) { return tangent ? th.t : th.v; }
 
 enum { SC_T = 0, SC_INVT, SC_S, SC_RHO, SC_CB, SC_SH, SC_LNRTP, SC_N };
 
-// Forward pass of f on the dual state ud -> fd, keeping the tape.
-template <int G>
+// Forward pass of f on the state ud -> fd, keeping the tape.
+template <int G, class Sc>
 __device__ void adj_rhs_fwd(const MechView& m, const AdjFrame& F, double p) {
   const Grp<G> g;
   const int ns = m.ns, L = g.lane;
   g.sync();  // ud complete
-  const Dual T = F.ud[ns];
-  const Dual invT = 1.0 / T;
-  const Dual lnT = dlog(T);
-  Dual S = dd(0.0);
+  const Sc T = rd<Sc>(F.ud[ns]);
+  const Sc invT = 1.0 / T;
+  const Sc lnT = dlog(T);
+  Sc S = sv<Sc>(0.0);
   for (int k = L; k < ns; k += G) {
-    const double* c = (T.v < m.Tmid[k]) ? m.lo : m.hi;
+    const double* c = (val(T) < m.Tmid[k]) ? m.lo : m.hi;
     const double a1 = c[k], a2 = c[ns + k], a3 = c[2 * ns + k], a4 = c[3 * ns + k], a5 = c[4 * ns + k];
-    const Dual cp = (((a5 * T + a4) * T + a3) * T + a2) * T + a1;
-    const Dual hp = ((c[8 * ns + k] * T + c[7 * ns + k]) * T + c[6 * ns + k]) * T + c[5 * ns + k];
-    const Dual hrt = hp * T + a1 + c[9 * ns + k] * invT;
-    const Dual sp = ((c[12 * ns + k] * T + c[11 * ns + k]) * T + c[10 * ns + k]) * T + a2;
-    const Dual sr = a1 * lnT + sp * T + c[13 * ns + k];
-    F.cp[k] = cp;
-    F.h[k] = hrt;
-    F.g[k] = hrt - sr;
-    F.dcp[k] = ((c[16 * ns + k] * T + c[15 * ns + k]) * T + c[14 * ns + k]) * T + a2;
-    S += F.ud[k] * m.invW[k];
+    const Sc cp = (((a5 * T + a4) * T + a3) * T + a2) * T + a1;
+    const Sc hp = ((c[8 * ns + k] * T + c[7 * ns + k]) * T + c[6 * ns + k]) * T + c[5 * ns + k];
+    const Sc hrt = hp * T + a1 + c[9 * ns + k] * invT;
+    const Sc sp = ((c[12 * ns + k] * T + c[11 * ns + k]) * T + c[10 * ns + k]) * T + a2;
+    const Sc sr = a1 * lnT + sp * T + c[13 * ns + k];
+    F.cp[k] = wr(cp);
+    F.h[k] = wr(hrt);
+    F.g[k] = wr(hrt - sr);
+    F.dcp[k] = wr(((c[16 * ns + k] * T + c[15 * ns + k]) * T + c[14 * ns + k]) * T + a2);
+    S += rd<Sc>(F.ud[k]) * m.invW[k];
   }
   S = gsum(g, S);
-  const Dual rho = p / (R_GAS * T * S);
-  for (int k = L; k < ns; k += G) F.C[k] = rho * F.ud[k] * m.invW[k];
+  const Sc rho = p / (R_GAS * T * S);
+  const Sc irho = 1.0 / rho;
+  for (int k = L; k < ns; k += G) F.C[k] = wr(rho * rd<Sc>(F.ud[k]) * m.invW[k]);
   if (L == ns % G) {  // the empty reaction slot: C = 1, h = g = 0
-    F.h[ns] = dd(0.0);
-    F.g[ns] = dd(0.0);
-    F.C[ns] = dd(1.0);
+    F.h[ns] = Dual{0.0, 0.0};
+    F.g[ns] = Dual{0.0, 0.0};
+    F.C[ns] = Dual{1.0, 0.0};
   }
   g.sync();
   for (int t = L; t < m.ntb; t += G) {
-    Dual Mc = dd(0.0);
-    for (int k = 0; k < ns; ++k) Mc += m.eff[(size_t)t * ns + k] * F.C[k];
-    F.Ms[t] = Mc;
+    Sc Mc = sv<Sc>(0.0);
+    for (int k = 0; k < ns; ++k) Mc += m.eff[(size_t)t * ns + k] * rd<Sc>(F.C[k]);
+    F.Ms[t] = wr(Mc);
   }
   g.sync();
-  const Dual lnRTp = dlog(R_GAS * T / P_REF);
+  const Sc lnRTp = dlog(R_GAS * T / P_REF);
   for (int j = L; j < m.nr; j += G) {
     const uint32_t sl = m.slots[j];
     const int ra = sl & 255, rb = (sl >> 8) & 255, pa = (sl >> 16) & 255, pb = sl >> 24;
@@ -178,100 +219,107 @@ __device__ void adj_rhs_fwd(const MechView& m, const AdjFrame& F, double p) {
     const bool rev = (meta >> 2) & 1;
     const int dnu = ((meta >> 4) & 15) - 4;
     const int slot = meta >> 8;
-    Dual k = dexp(m.lnA[j] + m.bexp[j] * lnT - m.EaR[j] * invT, m.etab);
-    const Dual rfac = rev ? dexp(F.g[pa] + F.g[pb] - F.g[ra] - F.g[rb] + (double)dnu * lnRTp, m.etab) : dd(0.0);
-    Dual mfac = dd(1.0);
-    if (kind == 1) mfac = F.Ms[slot];
+    Sc k = dexp(m.lnA[j] + m.bexp[j] * lnT - m.EaR[j] * invT, m.etab);
+    const Sc rfac = rev ? dexp(rd<Sc>(F.g[pa]) + rd<Sc>(F.g[pb]) - rd<Sc>(F.g[ra]) - rd<Sc>(F.g[rb]) +
+                                   (double)dnu * lnRTp,
+                               m.etab)
+                        : sv<Sc>(0.0);
+    Sc mfac = sv<Sc>(1.0);
+    if (kind == 1) mfac = rd<Sc>(F.Ms[slot]);
     if (kind == 2) {
       const double* fo = m.fo + (size_t)slot * FO_STRIDE;
-      const Dual Mc = F.Ms[slot];
-      const Dual dlnkinf = (m.bexp[j] + m.EaR[j] * invT) * invT;
-      const Dual k0 = dexp(fo[0] + fo[1] * lnT - fo[2] * invT, m.etab);
-      const Dual dlnk0 = (fo[1] + fo[2] * invT) * invT;
-      Dual Pr = k0 * Mc / k;
-      if (!(Pr.v > 1e-300)) Pr = dd(1e-300);
+      const Sc Mc = rd<Sc>(F.Ms[slot]);
+      const Sc dlnkinf = (m.bexp[j] + m.EaR[j] * invT) * invT;
+      const Sc k0 = dexp(fo[0] + fo[1] * lnT - fo[2] * invT, m.etab);
+      const Sc dlnk0 = (fo[1] + fo[2] * invT) * invT;
+      Sc Pr = k0 * Mc / k;
+      if (!(val(Pr) > 1e-300)) Pr = sv<Sc>(1e-300);
       const double a = fo[3];
-      const Dual e3 = dexp(-1.0 * T * fo[4], m.etab), e1 = dexp(-1.0 * T * fo[5], m.etab);
-      const Dual e2 = fo[6] > 0.0 ? dexp(-fo[6] * invT, m.etab) : dd(0.0);
-      const Dual Fc = (1.0 - a) * e3 + a * e1 + e2;
-      const Dual lFc = dlog10(Fc);
-      const Dual cc = -0.4 - 0.67 * lFc;
-      const Dual nn = 0.75 - 1.27 * lFc;
-      const Dual x = dlog10(Pr) + cc;
-      const Dual D = nn - 0.14 * x;
-      const Dual f1 = x / D;
-      const Dual den = 1.0 + f1 * f1;
-      const Dual lF = lFc / den;
-      const Dual Fb = dexp(lF * 2.302585092994046, m.etab);
-      const Dual onePr = 1.0 + Pr;
-      const Dual dlF_dL = -1.0 * lFc * 2.0 * f1 / (den * den) * nn / (D * D);
-      const Dual df1 = (-0.67 * D + 1.1762 * x) / (D * D);
-      const Dual dlF_dlFc = 1.0 / den - lFc * 2.0 * f1 / (den * den) * df1;
-      const Dual dFc = -(1.0 - a) * fo[4] * e3 - a * fo[5] * e1 + (fo[6] > 0.0 ? fo[6] * invT * invT * e2 : dd(0.0));
-      const Dual gg = 1.0 / onePr + dlF_dL;
-      F.dlnk[slot] = dlnkinf + gg * (dlnk0 - dlnkinf) + dlF_dlFc * dFc / Fc;
-      F.dkdM[slot] = k0 * Fb / onePr * gg;
-      F.omg[slot] = 1.0 - gg;
+      const Sc e3 = dexp(-1.0 * T * fo[4], m.etab), e1 = dexp(-1.0 * T * fo[5], m.etab);
+      const Sc e2 = fo[6] > 0.0 ? dexp(-fo[6] * invT, m.etab) : sv<Sc>(0.0);
+      const Sc Fc = (1.0 - a) * e3 + a * e1 + e2;
+      const Sc lFc = dlog10(Fc);
+      const Sc cc = -0.4 - 0.67 * lFc;
+      const Sc nn = 0.75 - 1.27 * lFc;
+      const Sc x = dlog10(Pr) + cc;
+      const Sc D = nn - 0.14 * x;
+      const Sc f1 = x / D;
+      const Sc den = 1.0 + f1 * f1;
+      const Sc lF = lFc / den;
+      const Sc Fb = dexp(lF * 2.302585092994046, m.etab);
+      const Sc onePr = 1.0 + Pr;
+      const Sc dlF_dL = -1.0 * lFc * 2.0 * f1 / (den * den) * nn / (D * D);
+      const Sc df1 = (-0.67 * D + 1.1762 * x) / (D * D);
+      const Sc dlF_dlFc = 1.0 / den - lFc * 2.0 * f1 / (den * den) * df1;
+      const Sc dFc =
+          -(1.0 - a) * fo[4] * e3 - a * fo[5] * e1 + (fo[6] > 0.0 ? fo[6] * invT * invT * e2 : sv<Sc>(0.0));
+      const Sc gg = 1.0 / onePr + dlF_dL;
+      F.dlnk[slot] = wr(dlnkinf + gg * (dlnk0 - dlnkinf) + dlF_dlFc * dFc / Fc);
+      F.dkdM[slot] = wr(k0 * Fb / onePr * gg);
+      F.omg[slot] = wr(1.0 - gg);
       k = k * Pr / onePr * Fb;
     }
-    const Dual Pf = F.C[ra] * F.C[rb];
-    const Dual Pb = F.C[pa] * F.C[pb];
-    F.k[j] = k;
-    F.rfac[j] = rfac;
-    F.q[j] = mfac * (k * Pf - k * rfac * Pb);
+    const Sc Pf = rd<Sc>(F.C[ra]) * rd<Sc>(F.C[rb]);
+    const Sc Pb = rd<Sc>(F.C[pa]) * rd<Sc>(F.C[pb]);
+    F.k[j] = wr(k);
+    F.rfac[j] = wr(rfac);
+    F.q[j] = wr(mfac * (k * Pf - k * rfac * Pb));
   }
   g.sync();
-  Dual Sh = dd(0.0), cb = dd(0.0);
+  Sc Sh = sv<Sc>(0.0), cb = sv<Sc>(0.0);
   for (int k = L; k < ns; k += G) {
-    Dual om = dd(0.0);
-    for (int e = m.csr_ptr[k]; e < m.csr_ptr[k + 1]; ++e) om += m.csr_nu[e] * F.q[m.csr_j[e]];
-    F.om[k] = om;
-    F.fd[k] = m.W[k] * om / rho;
-    Sh += F.h[k] * om;
-    cb += F.ud[k] * F.cp[k] * m.invW[k];
+    Sc om = sv<Sc>(0.0);
+    for (int e = m.csr_ptr[k]; e < m.csr_ptr[k + 1]; ++e) om += m.csr_nu[e] * rd<Sc>(F.q[m.csr_j[e]]);
+    F.om[k] = wr(om);
+    F.fd[k] = wr(m.W[k] * om * irho);
+    Sh += rd<Sc>(F.h[k]) * om;
+    cb += rd<Sc>(F.ud[k]) * rd<Sc>(F.cp[k]) * m.invW[k];
   }
   Sh = gsum(g, Sh);
   cb = gsum(g, cb);
-  if (L == ns % G) F.fd[ns] = -1.0 * T * Sh / (rho * cb);
+  if (L == ns % G) F.fd[ns] = wr(-1.0 * T * Sh / (rho * cb));
   if (L == 0) {
-    F.sc[SC_T] = T;
-    F.sc[SC_INVT] = invT;
-    F.sc[SC_S] = S;
-    F.sc[SC_RHO] = rho;
-    F.sc[SC_CB] = cb;
-    F.sc[SC_SH] = Sh;
-    F.sc[SC_LNRTP] = lnRTp;
+    F.sc[SC_T] = wr(T);
+    F.sc[SC_INVT] = wr(invT);
+    F.sc[SC_S] = wr(S);
+    F.sc[SC_RHO] = wr(rho);
+    F.sc[SC_CB] = wr(cb);
+    F.sc[SC_SH] = wr(Sh);
+    F.sc[SC_LNRTP] = wr(lnRTp);
   }
   g.sync();
 }
 
 // Reverse pass: ubd = J^T fbd on the tape of the last adj_rhs_fwd; the ln A
 // gradient is added to F.theta from the values (tangent = false) or from the
-// tangents (tangent = true) of the dual adjoint.  Each lane takes its
-// reactions' cotangents (stored per reaction), then its species gather them
-// through the species-major slot list.
-template <int G>
+// tangents (tangent = true, Dual passes only) of the adjoint.  Each lane takes
+// its reactions' cotangents (stored per reaction), then its species gather
+// them through the species-major slot list.
+template <int G, class Sc>
 __device__ void adj_rhs_rev(const MechView& m, const AdjFrame& F, bool tangent) {
   const Grp<G> g;
   const int ns = m.ns, L = g.lane;
   g.sync();  // fbd and the tape complete
-  const Dual T = F.sc[SC_T], invT = F.sc[SC_INVT], S = F.sc[SC_S], rho = F.sc[SC_RHO];
-  const Dual cb = F.sc[SC_CB], Sh = F.sc[SC_SH];
-  const Dual fTb = F.fbd[ns];
-  const Dual rcb = rho * cb;
-  const Dual Tbar0 = -1.0 * Sh / rcb * fTb;
-  const Dual Shbar = -1.0 * T / rcb * fTb;
-  const Dual rhobar0 = T * Sh / (rho * rcb) * fTb;
-  const Dual cbbar = T * Sh / (rcb * cb) * fTb;
-  Dual rhobar_l = dd(0.0);  // this lane's share of rho_bar
+  const Sc T = rd<Sc>(F.sc[SC_T]), invT = rd<Sc>(F.sc[SC_INVT]), S = rd<Sc>(F.sc[SC_S]);
+  const Sc rho = rd<Sc>(F.sc[SC_RHO]), cb = rd<Sc>(F.sc[SC_CB]), Sh = rd<Sc>(F.sc[SC_SH]);
+  const Sc irho = 1.0 / rho;
+  const Sc fTb = rd<Sc>(F.fbd[ns]);
+  const Sc rcb = rho * cb;
+  const Sc Tbar0 = -1.0 * Sh / rcb * fTb;
+  const Sc Shbar = -1.0 * T / rcb * fTb;
+  const Sc rhobar0 = T * Sh / (rho * rcb) * fTb;
+  const Sc cbbar = T * Sh / (rcb * cb) * fTb;
+  Sc rhobar_l = sv<Sc>(0.0);  // this lane's share of rho_bar
   for (int k = L; k < ns; k += G) {
-    F.ombar[k] = m.W[k] / rho * F.fbd[k] + F.h[k] * Shbar;
-    rhobar_l -= m.W[k] * F.om[k] / (rho * rho) * F.fbd[k];
+    const Sc fb = rd<Sc>(F.fbd[k]);
+    const Sc wfb = m.W[k] * irho * fb;
+    F.ombar[k] = wr(wfb + rd<Sc>(F.h[k]) * Shbar);
+    rhobar_l -= wfb * rd<Sc>(F.om[k]) * irho;
   }
-  if (L == ns % G) F.ombar[ns] = dd(0.0);
-  for (int t = L; t < m.ntb; t += G) F.Mbar[t] = dd(0.0);
+  if (L == ns % G) F.ombar[ns] = Dual{0.0, 0.0};
+  for (int t = L; t < m.ntb; t += G) F.Mbar[t] = Dual{0.0, 0.0};
   g.sync();
-  Dual Tbar_l = dd(0.0);  // this lane's share of T_bar
+  Sc Tbar_l = sv<Sc>(0.0);  // this lane's share of T_bar
   for (int j = L; j < m.nr; j += G) {
     const uint32_t sl = m.slots[j];
     const int ra = sl & 255, rb = (sl >> 8) & 255, pa = (sl >> 16) & 255, pb = sl >> 24;
@@ -280,63 +328,64 @@ __device__ void adj_rhs_rev(const MechView& m, const AdjFrame& F, bool tangent) 
     const bool rev = (meta >> 2) & 1;
     const int dnu = ((meta >> 4) & 15) - 4;
     const int slot = meta >> 8;
-    const Dual qbar = F.ombar[pa] + F.ombar[pb] - F.ombar[ra] - F.ombar[rb];
-    const Dual k = F.k[j], rfac = F.rfac[j];
-    const Dual Pf = F.C[ra] * F.C[rb];
-    const Dual Pb = F.C[pa] * F.C[pb];
-    const Dual mfac = kind == 1 ? F.Ms[slot] : dd(1.0);
-    const Dual kr = k * rfac;
-    const Dual qm = qbar * mfac;
-    const Dual kbar = qm * (Pf - rfac * Pb);
-    if (kind == 1) F.Mbar[slot] += qbar * (k * Pf - kr * Pb);  // slots are one per reaction
-    F.q[j] = qm * k;          // d/d(prod C^nu')
-    F.Pbb[j] = -1.0 * qm * kr;  // d/d(prod C^nu'')
-    Dual drf = dd(0.0);
+    const Sc qbar = rd<Sc>(F.ombar[pa]) + rd<Sc>(F.ombar[pb]) - rd<Sc>(F.ombar[ra]) - rd<Sc>(F.ombar[rb]);
+    const Sc k = rd<Sc>(F.k[j]), rfac = rd<Sc>(F.rfac[j]);
+    const Sc Pf = rd<Sc>(F.C[ra]) * rd<Sc>(F.C[rb]);
+    const Sc Pb = rd<Sc>(F.C[pa]) * rd<Sc>(F.C[pb]);
+    const Sc mfac = kind == 1 ? rd<Sc>(F.Ms[slot]) : sv<Sc>(1.0);
+    const Sc kr = k * rfac;
+    const Sc qm = qbar * mfac;
+    const Sc kbar = qm * (Pf - rfac * Pb);
+    if (kind == 1) F.Mbar[slot] = wr(qbar * (k * Pf - kr * Pb));  // slots are one per reaction
+    F.q[j] = wr(qm * k);           // d/d(prod C^nu')
+    F.Pbb[j] = wr(-1.0 * qm * kr);  // d/d(prod C^nu'')
+    Sc drf = sv<Sc>(0.0);
     if (rev) {
       drf = rfac * (-1.0 * qm * k * Pb);  // rfac * rfac_bar
       Tbar_l += (double)dnu * drf * invT;
     }
-    F.drf[j] = drf;
-    const Dual kk = k * kbar;
-    Dual th;
+    F.drf[j] = wr(drf);
+    const Sc kk = k * kbar;
+    Sc th;
     if (kind == 2) {
-      Tbar_l += kk * F.dlnk[slot];
-      F.Mbar[slot] += kbar * F.dkdM[slot];
-      th = kk * F.omg[slot];
+      Tbar_l += kk * rd<Sc>(F.dlnk[slot]);
+      F.Mbar[slot] = wr(kbar * rd<Sc>(F.dkdM[slot]));
+      th = kk * rd<Sc>(F.omg[slot]);
     } else {
       Tbar_l += kk * ((m.bexp[j] + m.EaR[j] * invT) * invT);
       th = kk;
     }
-    F.theta[j] += tangent ? th.t : th.v;
+    F.theta[j] += theta_part(th, tangent);
   }
   g.sync();
   for (int k = L; k < ns; k += G) {
-    Dual cbar = dd(0.0), gbar = dd(0.0);
+    Sc cbar = sv<Sc>(0.0), gbar = sv<Sc>(0.0);
     for (int i = m.role_ptr[k]; i < m.role_ptr[k + 1]; ++i) {
       const int e = m.role[i], j = e >> 2, role = e & 3;
       // the other factor of the same product: ra <-> rb, pa <-> pb
       const int other = (m.slots[j] >> (8 * (role ^ 1))) & 255;
-      cbar += (role < 2 ? F.q[j] : F.Pbb[j]) * F.C[other];
-      gbar = role < 2 ? gbar - F.drf[j] : gbar + F.drf[j];
+      cbar += rd<Sc>(role < 2 ? F.q[j] : F.Pbb[j]) * rd<Sc>(F.C[other]);
+      gbar = role < 2 ? gbar - rd<Sc>(F.drf[j]) : gbar + rd<Sc>(F.drf[j]);
     }
-    for (int t = 0; t < m.ntb; ++t) cbar += m.eff[(size_t)t * ns + k] * F.Mbar[t];
-    F.Cbar[k] = cbar;
-    F.gbar[k] = gbar;
-    rhobar_l += F.ud[k] * m.invW[k] * cbar;
+    for (int t = 0; t < m.ntb; ++t) cbar += m.eff[(size_t)t * ns + k] * rd<Sc>(F.Mbar[t]);
+    F.Cbar[k] = wr(cbar);
+    F.gbar[k] = wr(gbar);
+    rhobar_l += rd<Sc>(F.ud[k]) * m.invW[k] * cbar;
   }
-  const Dual rhobar = rhobar0 + gsum(g, rhobar_l);
-  Dual Tbar = Tbar0 + gsum(g, Tbar_l) - rho * invT * rhobar;
-  const Dual Sbar = -1.0 * rho / S * rhobar;
-  Dual T2_l = dd(0.0);
+  const Sc rhobar = rhobar0 + gsum(g, rhobar_l);
+  Sc Tbar = Tbar0 + gsum(g, Tbar_l) - rho * invT * rhobar;
+  const Sc Sbar = -1.0 * rho / S * rhobar;
+  Sc T2_l = sv<Sc>(0.0);
   for (int k = L; k < ns; k += G) {
-    const Dual Yb = F.cp[k] * m.invW[k] * cbbar + rho * m.invW[k] * F.Cbar[k] + Sbar * m.invW[k];
-    F.ubd[k] = Yb;
-    const Dual cpbar = F.ud[k] * m.invW[k] * cbbar;
-    const Dual hbar = F.om[k] * Shbar;
-    T2_l += cpbar * F.dcp[k] + hbar * (F.cp[k] - F.h[k]) * invT - F.gbar[k] * F.h[k] * invT;
+    const Sc cpk = rd<Sc>(F.cp[k]), hk = rd<Sc>(F.h[k]);
+    const Sc Yb = cpk * m.invW[k] * cbbar + rho * m.invW[k] * rd<Sc>(F.Cbar[k]) + Sbar * m.invW[k];
+    F.ubd[k] = wr(Yb);
+    const Sc cpbar = rd<Sc>(F.ud[k]) * m.invW[k] * cbbar;
+    const Sc hbar = rd<Sc>(F.om[k]) * Shbar;
+    T2_l += cpbar * rd<Sc>(F.dcp[k]) + hbar * (cpk - hk) * invT - rd<Sc>(F.gbar[k]) * hk * invT;
   }
   Tbar += gsum(g, T2_l);
-  if (L == ns % G) F.ubd[ns] = Tbar;
+  if (L == ns % G) F.ubd[ns] = wr(Tbar);
   g.sync();
 }
 
@@ -405,7 +454,7 @@ __device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double 
   double* Q = &F.Q[0];
   // ---------------------------------------------------------------- forward
   adj_load_ud<G>(F, N, F.u, nullptr);
-  adj_rhs_fwd<G>(m, F, p);
+  adj_rhs_fwd<G, double>(m, F, p);
   double beta2 = 0.0;
   for (int e = L; e < N; e += G) {
     F.fn[e] = F.fd[e].v;
@@ -420,7 +469,7 @@ __device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double 
     for (int e = L; e < N; e += G) Q[e] = F.fn[e] / beta;
     for (int j = 0; j < M; ++j) {
       adj_load_ud<G>(F, N, F.u, Q + (int64_t)j * N);
-      adj_rhs_fwd<G>(m, F, p);
+      adj_rhs_fwd<G, Dual>(m, F, p);
       double w0 = 0.0;
       for (int e = L; e < N; e += G) {
         F.w[e] = F.fd[e].t;
@@ -473,7 +522,7 @@ __device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double 
         arg[e] = F.u[e] + h * acc;
       }
       adj_load_ud<G>(F, N, arg, nullptr);
-      adj_rhs_fwd<G>(m, F, p);
+      adj_rhs_fwd<G, double>(m, F, p);
       for (int e = L; e < N; e += G) F.tmp[e] = F.fd[e].v;  // f_i (kept for stage 4)
     }
     double z[MAXM];
@@ -555,9 +604,9 @@ __device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double 
       if (i == 2)
         for (int e = L; e < N; e += G) F.fb2[e] += F.w[e];
       adj_load_ud<G>(F, N, arg, nullptr);
-      adj_rhs_fwd<G>(m, F, p);
+      adj_rhs_fwd<G, double>(m, F, p);
       for (int e = L; e < N; e += G) F.fbd[e] = Dual{i == 2 ? F.fb2[e] : F.w[e], 0.0};
-      adj_rhs_rev<G>(m, F, false);
+      adj_rhs_rev<G, double>(m, F, false);
       for (int e = L; e < N; e += G) {
         const double ab = F.ubd[e].v;
         F.ubar[e] += ab;
@@ -578,7 +627,7 @@ __device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double 
   // Arnoldi, last column first
   for (int j = md - 1; j >= 0; --j) {
     adj_load_ud<G>(F, N, F.u, Q + (int64_t)j * N);
-    adj_rhs_fwd<G>(m, F, p);
+    adj_rhs_fwd<G, Dual>(m, F, p);
     for (int e = L; e < N; e += G) F.w[e] = F.fd[e].t;
     for (int e = L; e < N; e += G) {
       double a = F.w[e];
@@ -628,7 +677,7 @@ __device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double 
     }
     // w = J(u) q_j: J^T w_bar into q_bar_j, second-order terms into u_bar and theta
     for (int e = L; e < N; e += G) F.fbd[e] = Dual{F.wbar[e], 0.0};
-    adj_rhs_rev<G>(m, F, true);
+    adj_rhs_rev<G, Dual>(m, F, true);
     for (int e = L; e < N; e += G) {
       F.Qbar[(int64_t)j * N + e] += F.ubd[e].v;
       F.ubar[e] += F.ubd[e].t;
@@ -643,9 +692,9 @@ __device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double 
   }
   // f_n = f(u)
   adj_load_ud<G>(F, N, F.u, nullptr);
-  adj_rhs_fwd<G>(m, F, p);
+  adj_rhs_fwd<G, double>(m, F, p);
   for (int e = L; e < N; e += G) F.fbd[e] = Dual{F.fbn[e], 0.0};
-  adj_rhs_rev<G>(m, F, false);
+  adj_rhs_rev<G, double>(m, F, false);
   for (int e = L; e < N; e += G) F.ubar[e] += F.ubd[e].v;
   g.sync();
 }

@@ -14,9 +14,12 @@
 // shared memory next to a per-block copy of the mechanism.
 //
 // Batching.  The integration kernel is persistent: one wave of blocks sized
-// to the device, each group repeatedly takes the next cell index from a
-// global atomic counter (work stealing), so cells needing 1 or 200 substeps
-// share one launch without a tail of idle blocks.
+// to the device.  With carried step sizes the cells are sorted by expected
+// cost and dealt to static per-block bins (the most expensive alone on an
+// SM), each drained from a shared-memory counter; otherwise each group takes
+// the next cell index from a global atomic counter (work stealing).  Either
+// way cells needing 1 or 200 substeps share one launch without a tail of
+// idle blocks.
 //
 // Arithmetic.  FP64 throughout.  Three restatements differ from a literal
 // transcription of the kinetics while computing the same quantities:
@@ -271,7 +274,7 @@ int cuda_error(cudaError_t e, const char* where);
 struct MechView {
   int ns, nr, ntb, ntroe;
   int nx;  // state components after T: 0, or 5 (rho, rho u, rho E) for the auxiliary-temperature system
-  const double* etab;  // 2^(j/128) table in shared memory
+  const double* etab;  // 2^(j/256) table in shared memory
   const double *W, *invW, *Tmid, *lo, *hi, *lnA, *bexp, *EaR, *eff, *fo, *csr_nu;
   const uint32_t* slots;
   const int32_t *meta, *csr_ptr, *csr_j;
@@ -2157,7 +2160,10 @@ struct AdjointParams {
   int nsteps, M;
 };
 
-// One group of G lanes per cell (see adjoint.cuh); 128-thread blocks.
+// One group of G lanes per cell (see adjoint.cuh); 128-thread blocks.  The
+// grid holds as many blocks as are resident at once and the cells are dealt
+// to them in turn (cell c to block c mod gridDim.x), so every SM receives the
+// same number of cells and none idles while others finish.
 template <int G>
 __global__ void __launch_bounds__(128) rok4e_adjoint_kernel(AdjointParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -2167,19 +2173,23 @@ __global__ void __launch_bounds__(128) rok4e_adjoint_kernel(AdjointParams P) {
   MechView m = make_view(smem + EXP_TAB_BYTES, P.L);
   m.etab = reinterpret_cast<const double*>(smem);
   const Grp<G> g;
-  const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-  if (c >= P.ncell) return;  // whole groups: a group never straddles the end
-  const AdjFrame F = adj_frame(P.wsd, P.wsD, P.A, c);
+  const int gpb = blockDim.x / G;
+  const int64_t stride = (int64_t)gridDim.x * gpb;
   const int N = m.ns + 1;
-  for (int e = g.lane; e < N; e += G) F.ubar[e] = P.ubar_final[c * N + e];
-  for (int j = g.lane; j < m.nr; j += G) F.theta[j] = 0.0;
-  for (int n = P.nsteps - 1; n >= 0; --n) {
-    const double* un = P.ckpt + ((int64_t)n * P.ncell + c) * N;
-    for (int e = g.lane; e < N; e += G) F.u[e] = un[e];
-    adj_step<G>(m, F, P.p, P.h, P.M);
+  // whole groups take each cell, so a group's lanes agree on every branch
+  for (int64_t c = blockIdx.x + (int64_t)gridDim.x * (threadIdx.x / G); c < P.ncell; c += stride) {
+    const AdjFrame F = adj_frame(P.wsd, P.wsD, P.A, c);
+    for (int e = g.lane; e < N; e += G) F.ubar[e] = P.ubar_final[c * N + e];
+    for (int j = g.lane; j < m.nr; j += G) F.theta[j] = 0.0;
+    for (int n = P.nsteps - 1; n >= 0; --n) {
+      const double* un = P.ckpt + ((int64_t)n * P.ncell + c) * N;
+      for (int e = g.lane; e < N; e += G) F.u[e] = un[e];
+      adj_step<G>(m, F, P.p, P.h, P.M);
+    }
+    if (P.grad_u0)
+      for (int e = g.lane; e < N; e += G) P.grad_u0[c * N + e] = F.ubar[e];
+    g.sync();
   }
-  if (P.grad_u0)
-    for (int e = g.lane; e < N; e += G) P.grad_u0[c * N + e] = F.ubar[e];
 }
 
 // One group per cell: f(u) + src, or J(u) v.
@@ -2359,6 +2369,6 @@ int launch_rok4e(const IntegrateLaunch& a);
 template <int G>
 int launch_rkdp(const IntegrateLaunch& a);
 template <int G>
-int launch_adjoint(const AdjointParams& P, size_t smem, unsigned blocks, cudaStream_t st);
+int launch_adjoint(const AdjointParams& P, size_t smem, cudaStream_t st);
 
 }  // namespace rk

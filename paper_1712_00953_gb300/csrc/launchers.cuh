@@ -33,13 +33,25 @@ int launch_rkdp(const IntegrateLaunch& a) {
   return RK_OK;
 }
 
-// The adjoint: 128-thread blocks of 128 / G cells, the mechanism in shared memory.
+// The adjoint: 128-thread blocks of 128 / G cell slots, the mechanism in
+// shared memory, as many blocks as the device holds at once (no more than
+// the cells fill).
 template <int G>
-int launch_adjoint(const AdjointParams& P, size_t smem, unsigned blocks, cudaStream_t st) {
-  const cudaError_t e =
+int launch_adjoint(const AdjointParams& P, size_t smem, cudaStream_t st) {
+  cudaError_t e =
       cudaFuncSetAttribute(rok4e_adjoint_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
-  rok4e_adjoint_kernel<G><<<blocks, 128, smem, st>>>(P);
+  int n_sm = 0;
+  size_t smem_max = 0;
+  const int rc = device_props(&n_sm, &smem_max);
+  if (rc) return rc;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rok4e_adjoint_kernel<G>, 128, smem);
+  if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (per_sm < 1) return set_error(RK_E_UNSUPPORTED, "adjoint kernel cannot be resident on an SM");
+  const int64_t need = (P.ncell * G + 127) / 128;
+  const int64_t blocks = need < (int64_t)per_sm * n_sm ? need : (int64_t)per_sm * n_sm;
+  rok4e_adjoint_kernel<G><<<(unsigned)blocks, 128, smem, st>>>(P);
   return RK_OK;
 }
 

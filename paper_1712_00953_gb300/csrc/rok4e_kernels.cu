@@ -1014,11 +1014,10 @@ int rk_rok4e_adjoint_ex(const rk_mech* mech, const double* checkpoints, const do
   if (G != 4 && G != 8 && G != 16 && G != 32)
     return set_error(RK_E_INVALID_ARGUMENT, "lanes_per_cell must be 0, 4, 8, 16 or 32");
   const size_t smem = (size_t)mech->host.L.off_nuT + EXP_TAB_BYTES;
-  const unsigned blocks = (unsigned)((ncell * G + 127) / 128);
   cudaError_t e = cudaSuccess;
-  rc = G == 4 ? launch_adjoint<4>(P, smem, blocks, st)
-              : (G == 8 ? launch_adjoint<8>(P, smem, blocks, st)
-                        : (G == 16 ? launch_adjoint<16>(P, smem, blocks, st) : launch_adjoint<32>(P, smem, blocks, st)));
+  rc = G == 4 ? launch_adjoint<4>(P, smem, st)
+              : (G == 8 ? launch_adjoint<8>(P, smem, st)
+                        : (G == 16 ? launch_adjoint<16>(P, smem, st) : launch_adjoint<32>(P, smem, st)));
   if (rc) return rc;
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "rok4e_adjoint_kernel launch");
   adjoint_reduce_kernel<<<nr, 256, 0, st>>>(P.wsd + P.A.theta, ncell, P.A.rows_d,
