@@ -43,6 +43,7 @@ extern "C" {
 #define RK_E_CUDA (-3)              /* a CUDA runtime call failed               */
 #define RK_E_UNSUPPORTED (-4)       /* size beyond what the kernels support     */
 #define RK_E_WORKSPACE (-5)         /* workspace missing or too small           */
+#define RK_E_CALLBACK (-6)          /* a caller-supplied callback returned nonzero */
 
 /* ---- per-cell status codes (stats[4*cell + 3]) ---------------------------- */
 #define RK_CELL_OK 0
@@ -326,6 +327,36 @@ int rk_simpler_split_step(const rk_mech* mech, double* U, double* h_cell, int64_
                           double dt, double D, double dx, double rtol, double atol,
                           int32_t krylov_dim, const rk_opts* opts, int32_t* stats,
                           void* workspace, size_t workspace_bytes, void* stream);
+
+/* A caller-supplied transport operator for rk_simpler_split_step_ext: writes
+ * TU = T(U) for one field (both device [npts x nvar], row-major; TU never
+ * aliases U), enqueuing its work on `stream` (the cudaStream_t the split step
+ * was given) and returning 0, or nonzero to stop the step.  It is called on
+ * the calling host thread, in stream order with the library's own launches;
+ * `user` is passed through unchanged. */
+typedef int (*rk_transport_fn)(const double* U, double* TU, int64_t npts, int32_t nvar, void* user,
+                               void* stream);
+
+/* Simpler balanced split step (Eq. simpler_balanced) with the caller's own
+ * transport operator T, for a grid or a transport model the built-in 1-D
+ * diffusion does not cover:
+ *   Tn = T(U_n) (one call);
+ *   reaction:  dU/dt = R(U) + Tn over dt from U_n   (ROK4E per cell, as
+ *              rk_rok4e_integrate with src = Tn);
+ *   transport: dU/dt = T(U) - Tn over dt/2          (one SSP-RK3 step: three
+ *              calls, on the post-reaction state and the two stage values).
+ * transport NULL: the reaction step alone over dt (the 0-D case, src = 0).
+ * The npts cells of U are the grid's points in whatever order the operator
+ * uses.  U, h_cell, stats, opts as in rk_simpler_split_step; workspace from
+ * rk_split_step_workspace_size (any scheme).  With an operator that computes
+ * the built-in diffusion the result is bitwise that of rk_simpler_split_step.
+ * Returns RK_E_CALLBACK (the step stops where the callback failed, U then
+ * partly updated) when the operator returns nonzero, else as
+ * rk_simpler_split_step. */
+int rk_simpler_split_step_ext(const rk_mech* mech, double* U, double* h_cell, int64_t npts, double p,
+                              double dt, double rtol, double atol, int32_t krylov_dim,
+                              rk_transport_fn transport, void* user, const rk_opts* opts, int32_t* stats,
+                              void* workspace, size_t workspace_bytes, void* stream);
 
 /* Allocation-free variant of rk_simpler_split_step (the paper has no
  * counterpart: this is a library convenience).  Some callers cannot allocate

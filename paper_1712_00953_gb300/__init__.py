@@ -27,7 +27,7 @@ def _L():
         _LIB = _native.load()
     return _LIB
 
-__all__ = ["Mechanism", "mech_load", "mech_validate", "chem_rhs", "chem_rhs_mixed", "chem_rhs_tc", "chem_rhs_cv", "chem_jvp_cv",
+__all__ = ["Mechanism", "mech_load", "mech_validate", "chem_rhs", "chem_rhs_mixed", "chem_rhs_tc", "simpler_split_step_ext", "chem_rhs_cv", "chem_jvp_cv",
            "chem_jvp", "rok4e_integrate", "rkdp_integrate", "chem_rhs_aux", "chem_jvp_aux", "AUX_EXTRA",
            "rok4e_workspace_size", "simpler_split_step", "simpler_split_step_workspace_size",
            "diffusion_1d", "diffusion_1d_ghost", "ssprk3_stage_ghost", "GhostTransport",
@@ -295,6 +295,51 @@ def simpler_split_step(m: Mechanism, U, dt, D, dx, rtol, atol, krylov_dim=4, *, 
                                       ctypes.byref(oc), _dptr(stats, "stats", 4 * n, torch.int32),
                                       _dptr(workspace, "workspace", dtype=torch.uint8), workspace.numel(),
                                       _stream_ptr(stream)), "rk_simpler_split_step")
+    return U
+
+
+def simpler_split_step_ext(m: Mechanism, U, dt, rtol, atol, krylov_dim=4, *, transport=None, p=101325.0,
+                           h_cell=None, opts: Opts | None = None, stats=None, workspace=None, stream=None):
+    """One Simpler balanced split step with the caller's transport operator
+    (rk_simpler_split_step_ext), in place.  ``transport(X, TX)`` receives two
+    float64 CUDA tensors [npts, N] and writes T(X) into TX on the current
+    stream; None runs the reaction step alone."""
+    n = _ncell(U, m)
+    N = U.shape[-1]
+    oc = (opts or Opts()).c()
+    if workspace is None:
+        nb = int(_L().rk_split_step_workspace_size(m.handle, n, int(krylov_dim), 0, ctypes.byref(oc)))
+        workspace = torch.empty(nb, dtype=torch.uint8, device=U.device)
+    cb, err = ctypes.cast(None, _native.TRANSPORT_FN), []  # NULL: the reaction step alone
+    if transport is not None:
+        ws_lo, ws_hi = workspace.data_ptr(), workspace.data_ptr() + workspace.numel()
+        nbytes = n * N * 8
+
+        def view(ptr):  # the field at a device address the library passed: U or a workspace vector
+            if ptr == U.data_ptr():
+                return U.view(n, N)
+            if ws_lo <= ptr and ptr + nbytes <= ws_hi:
+                off = ptr - ws_lo
+                return workspace[off:off + nbytes].view(torch.float64).view(n, N)
+            raise RokError(f"transport callback: unknown device address {ptr:#x}")
+
+        def trampoline(x, tx, npts, nvar, user, strm):
+            try:
+                transport(view(x), view(tx))
+                return 0
+            except Exception as e:  # re-raised after the call returns
+                err.append(e)
+                return 1
+
+        cb = _native.TRANSPORT_FN(trampoline)
+    rc = _L().rk_simpler_split_step_ext(m.handle, _dptr(U, "U"), _dptr(h_cell, "h_cell", n), n, float(p), float(dt),
+                                        float(rtol), float(atol), int(krylov_dim), cb, None, ctypes.byref(oc),
+                                        _dptr(stats, "stats", 4 * n, torch.int32),
+                                        _dptr(workspace, "workspace", dtype=torch.uint8), workspace.numel(),
+                                        _stream_ptr(stream))
+    if err:
+        raise err[0]
+    _check(rc, "rk_simpler_split_step_ext")
     return U
 
 

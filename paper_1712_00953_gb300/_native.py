@@ -7,6 +7,10 @@ import os
 
 from .build import lib_path
 
+# rk_transport_fn: int (*)(const double* U, double* TU, int64_t npts, int32_t nvar, void* user, void* stream)
+TRANSPORT_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                ctypes.c_void_p, ctypes.c_void_p)
+
 c_double_p = ctypes.POINTER(ctypes.c_double)
 c_int32_p = ctypes.POINTER(ctypes.c_int32)
 
@@ -83,6 +87,11 @@ SIGNATURES = {
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "rk_simpler_split_step_workspace_size": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                                                ctypes.POINTER(RkOpts)]),
+    "rk_simpler_split_step_ext": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                                 ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                 ctypes.c_int32, TRANSPORT_FN, ctypes.c_void_p,
+                                                 ctypes.POINTER(RkOpts), ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_size_t, ctypes.c_void_p]),
     "rk_simpler_split_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                              ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_double, ctypes.c_int32,

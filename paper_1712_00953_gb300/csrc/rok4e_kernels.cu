@@ -109,15 +109,30 @@ __device__ __forceinline__ double diffusion_value(double xm, double x0, double x
 }
 
 // stage 0: X + k g(X); stage 1: 3/4 U1 + 1/4 (X + k g(X)); stage 2:
-// 1/3 U1 + 2/3 (X + k g(X)), with g(X) = D lap X + sigma s
-__device__ __forceinline__ double ssprk3_value(int stage, double u1, double xm, double x0, double xp, bool has_s,
-                                               double s, double sigma, double D, double inv_dx2, double k) {
-  const double dX = diffusion_value(xm, x0, xp, D, inv_dx2);
-  const double gX = has_s ? fma(sigma, s, dX) : dX;
+// 1/3 U1 + 2/3 (X + k g(X)), with g(X) = T(X) + sigma s and tx = T(X)
+__device__ __forceinline__ double ssprk3_combine(int stage, double u1, double x0, double tx, bool has_s, double s,
+                                                 double sigma, double k) {
+  const double gX = has_s ? fma(sigma, s, tx) : tx;
   const double xk = fma(k, gX, x0);
   if (stage == 0) return xk;
   if (stage == 1) return fma(0.75, u1, __dmul_rn(0.25, xk));
   return fma(2.0 / 3.0, xk, __ddiv_rn(u1, 3.0));
+}
+
+// the same with T(X) = D lap X from the neighbours
+__device__ __forceinline__ double ssprk3_value(int stage, double u1, double xm, double x0, double xp, bool has_s,
+                                               double s, double sigma, double D, double inv_dx2, double k) {
+  return ssprk3_combine(stage, u1, x0, diffusion_value(xm, x0, xp, D, inv_dx2), has_s, s, sigma, k);
+}
+
+// A stage with T(X) given (the caller's transport operator): Out = the stage of
+// U1, X and TX elementwise over n entries.
+__global__ void ssprk3_combine_kernel(int stage, const double* __restrict__ U1, const double* __restrict__ X,
+                                      const double* __restrict__ TX, const double* __restrict__ S, double sigma,
+                                      double* Out, int64_t n, double k) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  Out[idx] = ssprk3_combine(stage, U1[idx], X[idx], TX[idx], S != nullptr, S ? S[idx] : 0.0, sigma, k);
 }
 
 // c = (a R + b T) elementwise (the balancing constants of the splittings)
@@ -694,6 +709,56 @@ int rk_simpler_split_step(const rk_mech* mech, double* U, double* h_cell, int64_
   return e == cudaSuccess ? RK_OK : cuda_error(e, "ssprk3_stage_kernel launch");
 }
 
+int rk_simpler_split_step_ext(const rk_mech* mech, double* U, double* h_cell, int64_t npts, double p, double dt,
+                              double rtol, double atol, int32_t krylov_dim, rk_transport_fn transport, void* user,
+                              const rk_opts* opts, int32_t* stats, void* workspace, size_t workspace_bytes,
+                              void* stream) {
+  int rc = check_mech(mech);
+  if (rc) return rc;
+  if (opts && opts->reactor == 2)
+    return set_error(RK_E_INVALID_ARGUMENT, "the auxiliary-temperature system is for rk_rok4e_integrate and rk_rkdp_integrate");
+  if (npts < 0) return set_error(RK_E_INVALID_ARGUMENT, "npts < 0");
+  if (npts == 0) return RK_OK;
+  if (!U) return set_error(RK_E_INVALID_ARGUMENT, "null state array");
+  const size_t need = rk_split_step_workspace_size(mech, npts, krylov_dim, 0, opts);
+  if (!workspace || workspace_bytes < need) return set_error(RK_E_WORKSPACE, "workspace too small");
+  const int nv = mech->host.L.ns + 1;
+  const int64_t n = npts * nv;
+  const size_t vec = ((size_t)n * sizeof(double) + 255) & ~(size_t)255;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  double* Tn = reinterpret_cast<double*>(ws + 256);
+  double* V1 = reinterpret_cast<double*>(ws + 256 + vec);
+  double* V2 = reinterpret_cast<double*>(ws + 256 + 2 * vec);
+  double* TX = reinterpret_cast<double*>(ws + 256 + 3 * vec);
+  void* ws_int = ws + 256 + 4 * vec;
+  const size_t ws_int_bytes = workspace_bytes - (256 + 4 * vec);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!transport)  // no transport: the reaction step alone (the 0-D case)
+    return integrate_impl(mech, U, nullptr, h_cell, npts, p, dt, rtol, atol, krylov_dim, opts, stats, ws_int,
+                          ws_int_bytes, st);
+  auto call = [&](const double* X, double* out) {
+    const int r = transport(X, out, npts, nv, user, stream);
+    return r == 0 ? RK_OK : set_error(RK_E_CALLBACK, "the transport callback returned " + std::to_string(r));
+  };
+  // T(U_n), the constant source of the reaction sub-step
+  if ((rc = call(U, Tn))) return rc;
+  rc = integrate_impl(mech, U, Tn, h_cell, npts, p, dt, rtol, atol, krylov_dim, opts, stats, ws_int, ws_int_bytes,
+                      st);
+  if (rc) return rc;
+  // transport correction over dt/2: one SSP-RK3 step of dU/dt = T(U) - T(U_n)
+  const double k = 0.5 * dt;
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  const double* X[3] = {U, V1, V2};
+  double* Out[3] = {V1, V2, U};
+  for (int stage = 0; stage < 3; ++stage) {
+    if ((rc = call(X[stage], TX))) return rc;
+    ssprk3_combine_kernel<<<nb, 256, 0, st>>>(stage, U, X[stage], TX, Tn, -1.0, Out[stage], n, k);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "ssprk3_combine_kernel launch");
+  }
+  return RK_OK;
+}
+
 // One SSP-RK3 step of dU/dt = D d^2U/dx^2 + sigma S over t, in place (V1, V2 scratch).
 static int transport_step(double* U, const double* S, double sigma, double t, double D, double dx, int64_t npts,
                           int nv, double* V1, double* V2, cudaStream_t st) {
@@ -1100,6 +1165,7 @@ const char* rk_status_string(int32_t code) {
     case RK_E_CUDA: return "CUDA error";
     case RK_E_UNSUPPORTED: return "unsupported size";
     case RK_E_WORKSPACE: return "workspace missing or too small";
+    case RK_E_CALLBACK: return "a caller's callback failed";
     default: return "unknown status";
   }
 }

@@ -8,6 +8,12 @@
   the phases, is bitwise the whole-domain split step.
 * Second-order convergence in the split step size of the balanced schemes
   (the paper's 1-D flame shows 2nd order in T), measured on the GPU.
+* The split step with the caller's own transport operator
+  (rk_simpler_split_step_ext): bitwise the built-in step when the operator is
+  the library's diffusion; with an upwind advection operator, against the
+  oracle's Simpler step (Eq. simpler_balanced) with the same operator,
+  replaying the GPU's reaction step sequences; without an operator, the
+  reaction step alone; a failing operator stops the step with an error.
 """
 
 import numpy as np
@@ -191,3 +197,118 @@ def test_sharded_slices_equal_whole_domain_bitwise(rk, case):
         assert torch.equal(torch.cat(ss), st), step
         assert torch.equal(one[1:-1], U), step
         assert torch.equal(h1, hc), step
+
+
+def _upwind_torch(a, dx):
+    def T(X, TX):  # first-order upwind advection at speed a > 0; the inflow point keeps its state
+        TX[0].zero_()
+        torch.mul(X[1:] - X[:-1], -a / dx, out=TX[1:])
+    return T
+
+
+def _upwind_numpy(U, a, dx):
+    TU = np.zeros_like(U)
+    TU[1:] = (U[1:] - U[:-1]) * (-a / dx)
+    return TU
+
+
+def test_split_step_ext_with_builtin_diffusion_is_bitwise(rk, case):
+    from synth.fields import field_tanh_front
+
+    w, mech = case
+    npts = 256
+    _, U0 = field_tanh_front(npts, mech.n_species, w.field_seed)
+    dx = 1e-2 / npts
+    m = rk.mech_load(mech)
+    res = []
+    for ext in (False, True):
+        U = torch.tensor(U0, device="cuda")
+        hc = torch.zeros(npts, dtype=torch.float64, device="cuda")
+        st = torch.zeros(npts, 4, dtype=torch.int32, device="cuda")
+        for _ in range(3):
+            if ext:
+                rk.simpler_split_step_ext(m, U, w.dt, w.rtol, w.atol, 4, h_cell=hc, stats=st,
+                                          transport=lambda X, TX: rk.diffusion_1d(X, D, dx, out=TX))
+            else:
+                rk.simpler_split_step(m, U, w.dt, D, dx, w.rtol, w.atol, 4, h_cell=hc, stats=st)
+        torch.cuda.synchronize()
+        res.append((U.cpu(), hc.cpu(), st.cpu()))
+    for a, b in zip(res[0], res[1]):
+        assert torch.equal(a, b)
+
+
+def test_split_step_ext_upwind_advection_vs_oracle(rk, case):
+    from oracle import rok4e as orok
+    from oracle import splitting as osp
+    from oracle.kinetics import Kinetics
+    from synth.fields import field_tanh_front
+
+    w, mech = case
+    kin = Kinetics(mech)
+    npts, a = 48, 10.0
+    _, U0 = field_tanh_front(npts, mech.n_species, w.field_seed)
+    dx = 1e-2 / npts
+    m = rk.mech_load(mech)
+    U = torch.tensor(U0, device="cuda")
+    hc = torch.zeros(npts, dtype=torch.float64, device="cuda")
+    trace = torch.zeros(npts, 4096, dtype=torch.float64, device="cuda")
+    Uo, h_or = U0.copy(), np.zeros(npts)
+    ns = mech.n_species
+    for step in range(2):
+        trace.zero_()
+        rk.simpler_split_step_ext(m, U, w.dt, w.rtol, w.atol, 4, h_cell=hc, opts=rk.Opts(trace=trace),
+                                  transport=_upwind_torch(a, dx))
+        torch.cuda.synchronize()
+        tr = trace.cpu().numpy()
+        # the oracle's Simpler step with the same operator, reaction sub-steps replayed
+        Tn = _upwind_numpy(Uo, a, dx)
+        U1 = Uo.copy()
+        for c in range(npts):
+            f, jv_at = orok.reactor(kin, P, Tn[c], "analytic")
+            U1[c], inf = orok.integrate(f, jv_at, Uo[c], w.dt, w.rtol, w.atol, 4, h0=h_or[c] if step else None,
+                                        replay=[(abs(h), h > 0) for h in tr[c] if h != 0.0])
+            h_or[c] = inf["h_last"]
+        Uo = osp.ssprk3(U1, w.dt / 2, lambda V: _upwind_numpy(V, a, dx) - Tn)
+        got = U.cpu().numpy()
+        dY = np.abs(got[:, :ns] - Uo[:, :ns])
+        dT = np.abs(got[:, ns] - Uo[:, ns])
+        print(f"upwind transport, split step {step}: max |dY| {dY.max():.3e}, max |dT| {dT.max():.3e} K")
+        assert np.all(dY <= 1e-8 + 1e-6 * np.abs(Uo[:, :ns]))
+        assert dT.max() <= 1e-6
+    # the transport moved the front: the state differs from a pure reaction step
+    Ur = torch.tensor(U0, device="cuda")
+    for _ in range(2):
+        rk.simpler_split_step_ext(m, Ur, w.dt, w.rtol, w.atol, 4)
+    torch.cuda.synchronize()
+    assert float((Ur - U).abs()[:, ns].max()) > 1e-3
+
+
+def test_split_step_ext_without_transport_is_the_reaction_step(rk, case):
+    from synth.fields import field_tanh_front
+
+    w, mech = case
+    npts = 128
+    _, U0 = field_tanh_front(npts, mech.n_species, w.field_seed)
+    m = rk.mech_load(mech)
+    U1, U2 = torch.tensor(U0, device="cuda"), torch.tensor(U0, device="cuda")
+    rk.simpler_split_step_ext(m, U1, w.dt, w.rtol, w.atol, 4)
+    rk.rok4e_integrate(m, U2, w.dt, w.rtol, w.atol, 4)
+    torch.cuda.synchronize()
+    assert torch.equal(U1, U2)
+
+
+def test_split_step_ext_failing_transport_stops_the_step(rk, case):
+    from synth.fields import field_tanh_front
+
+    w, mech = case
+    _, U0 = field_tanh_front(32, mech.n_species, w.field_seed)
+    m = rk.mech_load(mech)
+    U = torch.tensor(U0, device="cuda")
+
+    def bad(X, TX):
+        raise ValueError("transport not available")
+
+    with pytest.raises(ValueError, match="transport not available"):
+        rk.simpler_split_step_ext(m, U, w.dt, w.rtol, w.atol, 4, transport=bad)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(U.cpu().numpy(), U0)  # it failed before the reaction sub-step
