@@ -933,16 +933,24 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
     const double lnk = fma(-m.EaR[j], invT, fma(m.bexp[j], lnT, m.lnA[j]));
     double k = (MIXED || cs->prec == 3) ? exp_mixed(lnk, m.etab) : exp_fast(lnk, m.etab);
     const double Pf = __dmul_rn(s.C[ra], s.C[rb]);
-    // Rb = prod C^nu'' / Kc, rfac = 1/Kc (only the caching evaluation needs it)
-    double Rb = 0.0, rfac = 0.0;
+    // Rb = prod C^nu'' / Kc (the caching evaluation keeps it), rfac = 1/Kc
+    // (caching only), PfRb = Pf - Rb: from the per-species factors as
+    // (C_pa E_pa C_pb E_pb) (1/E_ra 1/E_rb) subtracted from Pf in one fma
+    double Rb = 0.0, rfac = 0.0, PfRb = Pf;
     if (rev) {
       if (!direct_kc) {
-        Rb = __dmul_rn(__dmul_rn(__dmul_rn(s.CE[pa], s.CE[pb]), s.Einv[ra]), s.Einv[rb]);
-        if (cache) rfac = __dmul_rn(__dmul_rn(__dmul_rn(s.E[pa], s.E[pb]), s.Einv[ra]), s.Einv[rb]);
+        const double X = __dmul_rn(s.CE[pa], s.CE[pb]);
+        const double Y = __dmul_rn(s.Einv[ra], s.Einv[rb]);
+        PfRb = fma(-X, Y, Pf);
+        if (cache) {
+          Rb = __dmul_rn(X, Y);
+          rfac = __dmul_rn(__dmul_rn(s.E[pa], s.E[pb]), Y);
+        }
       } else {
         const double dl = dnu > 0 ? lnRTp : (dnu < 0 ? m_lnRTp : 0.0);
         rfac = exp_fast(s.gRT[pa] + s.gRT[pb] - s.gRT[ra] - s.gRT[rb] + dl, m.etab);
         Rb = __dmul_rn(rfac, __dmul_rn(s.C[pa], s.C[pb]));
+        PfRb = __dsub_rn(Pf, Rb);
       }
     }
     double mfac = 1.0;
@@ -986,7 +994,7 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
       }
     }
     // q = m k (prod C^nu' - prod C^nu'' / Kc); the third-body factor only where there is one
-    const double q0 = __dmul_rn(k, __dsub_rn(Pf, Rb));
+    const double q0 = __dmul_rn(k, PfRb);
     double qj = q0;
     if (kind == 1) qj = __dmul_rn(mfac, qj);
     if (MIXED) reinterpret_cast<df2*>(s.q)[j] = df_from(qj);  // double-float copy for the gather
