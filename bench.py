@@ -109,10 +109,11 @@ def adjoint_flop_model(mech, M):
     reaction.  Their reverse: per species 34 plus 3 per reaction slot the
     species fills, per reaction 26.  A dual (value, tangent) pass costs 2.5x
     its value pass's arithmetic plus one multiply per exponential.  Per step:
-    6 value and 8 dual forward passes (f at u_n twice, at the two stage
-    arguments twice, and M = 4 J q_j twice), 3 value and 4 dual reverse
-    passes; the Krylov and stage algebra forward and reverse three times the
-    forward step's (the integrator's Arnoldi and attempt counts)."""
+    6 value and M dual forward passes (f at u_n twice, at the two stage
+    arguments twice, the M J q_j once: their tapes are kept for the reverse
+    sweep), 3 value and M dual reverse passes; the Krylov and stage algebra
+    forward and reverse three times the forward step's (the integrator's
+    Arnoldi and attempt counts)."""
     ns, nr = mech.n_species, mech.n_reactions
     kind = np.asarray(mech.kind)
     rev = np.asarray(mech.reversible).astype(bool)
@@ -127,7 +128,7 @@ def adjoint_flop_model(mech, M):
     fwd_d = 2.5 * fwd_v + exps
     rev_d = 2.5 * rev_v
     krylov = 3 * (fm["arnoldi"] + fm["attempt"])
-    return float(6 * (fwd_v + EXP_FLOPS * exps) + 8 * (fwd_d + EXP_FLOPS * exps) + 3 * rev_v + 4 * rev_d + krylov)
+    return float(6 * (fwd_v + EXP_FLOPS * exps) + M * (fwd_d + EXP_FLOPS * exps) + 3 * rev_v + M * rev_d + krylov)
 
 
 def algorithmic_flops(model, stats, M, exp_flops=EXP_FLOPS):

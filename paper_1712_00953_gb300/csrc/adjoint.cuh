@@ -88,8 +88,11 @@ struct AdjLayout {
   int u, fn, Q, K, F, arg1, arg2, ubar, Kbar, Qbar, fb2, fbn, wbar, w, w1, w2, tmp, H, p1, p2, hn, Linv, zs, ys,
       Lbar, Hbar, scal, theta;
   int rows_d;
-  // dual rows
+  // dual rows: the tape of a right-hand-side pass (rows [0, tape_len): ud .. sc),
+  // the reverse pass's work arrays, then M more tapes (the Arnoldi columns'
+  // J q_j passes, kept for the reverse sweep) from row tape0
   int ud, fd, C, cp, h, g, dcp, om, k, rfac, q, Ms, dlnk, dkdM, omg, sc, Cbar, gbar, ombar, Mbar, ubd, fbd, Pbb, drf;
+  int tape_len, tape0;
   int rows_D;
 };
 
@@ -120,6 +123,16 @@ __device__ inline AdjFrame adj_frame(double* wsd, Dual* wsD, const AdjLayout& L,
   f.dkdM = X(L.dkdM); f.omg = X(L.omg); f.sc = X(L.sc); f.Cbar = X(L.Cbar); f.gbar = X(L.gbar);
   f.ombar = X(L.ombar); f.Mbar = X(L.Mbar); f.ubd = X(L.ubd); f.fbd = X(L.fbd); f.Pbb = X(L.Pbb); f.drf = X(L.drf);
   return f;
+}
+
+// The frame with its tape rows moved by `delta` duals (the stored tape of an
+// Arnoldi column); the work arrays stay shared.
+__device__ inline AdjFrame adj_tape(const AdjFrame& F, int64_t delta) {
+  AdjFrame t = F;
+  Col<Dual>* cols[] = {&t.ud, &t.fd, &t.C, &t.cp, &t.h, &t.g, &t.dcp, &t.om, &t.k, &t.rfac, &t.q, &t.Ms,
+                       &t.dlnk, &t.dkdM, &t.omg, &t.sc};
+  for (Col<Dual>* c : cols) c->p += delta;
+  return t;
 }
 
 // sum over the group (all lanes receive the same bits)
@@ -443,7 +456,8 @@ __device__ inline void adj_load_ud(const AdjFrame& F, int N, const Col<double>& 
 // from F.u; on entry F.ubar holds the adjoint of the step's result, on exit
 // that of F.u; the ln A gradient accumulates in F.theta.
 template <int G>
-__device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double h, int M) {
+__device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double h, int M, int64_t tape0,
+                         int64_t tape_len) {
   const Grp<G> g;
   const int ns = m.ns, N = ns + 1, L = g.lane;
   constexpr double g21 = G21 / GAM, g31 = G31 / GAM, g32 = G32 / GAM;
@@ -468,11 +482,12 @@ __device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double 
     md = M;
     for (int e = L; e < N; e += G) Q[e] = F.fn[e] / beta;
     for (int j = 0; j < M; ++j) {
-      adj_load_ud<G>(F, N, F.u, Q + (int64_t)j * N);
-      adj_rhs_fwd<G, Dual>(m, F, p);
+      const AdjFrame Fj = adj_tape(F, tape0 + j * tape_len);  // this column's tape, kept for the reverse sweep
+      adj_load_ud<G>(Fj, N, F.u, Q + (int64_t)j * N);
+      adj_rhs_fwd<G, Dual>(m, Fj, p);
       double w0 = 0.0;
       for (int e = L; e < N; e += G) {
-        F.w[e] = F.fd[e].t;
+        F.w[e] = Fj.fd[e].t;
         w0 = fma(F.w[e], F.w[e], w0);
       }
       w0 = sqrt(g.sum(w0));
@@ -626,9 +641,8 @@ __device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double 
   g.sync();  // Hbar from lane 0
   // Arnoldi, last column first
   for (int j = md - 1; j >= 0; --j) {
-    adj_load_ud<G>(F, N, F.u, Q + (int64_t)j * N);
-    adj_rhs_fwd<G, Dual>(m, F, p);
-    for (int e = L; e < N; e += G) F.w[e] = F.fd[e].t;
+    const AdjFrame Fj = adj_tape(F, tape0 + j * tape_len);  // the tape of J(u) q_j from the forward sweep
+    for (int e = L; e < N; e += G) F.w[e] = Fj.fd[e].t;
     for (int e = L; e < N; e += G) {
       double a = F.w[e];
       for (int i = 0; i <= j; ++i) a = fma(-F.p1[j * MAXM + i], Q[(int64_t)i * N + e], a);
@@ -677,7 +691,7 @@ __device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double 
     }
     // w = J(u) q_j: J^T w_bar into q_bar_j, second-order terms into u_bar and theta
     for (int e = L; e < N; e += G) F.fbd[e] = Dual{F.wbar[e], 0.0};
-    adj_rhs_rev<G, Dual>(m, F, true);
+    adj_rhs_rev<G, Dual>(m, Fj, true);
     for (int e = L; e < N; e += G) {
       F.Qbar[(int64_t)j * N + e] += F.ubd[e].v;
       F.ubar[e] += F.ubd[e].t;

@@ -2192,7 +2192,7 @@ __global__ void __launch_bounds__(128) rok4e_adjoint_kernel(AdjointParams P) {
     for (int n = P.nsteps - 1; n >= 0; --n) {
       const double* un = P.ckpt + ((int64_t)n * P.ncell + c) * N;
       for (int e = g.lane; e < N; e += G) F.u[e] = un[e];
-      adj_step<G>(m, F, P.p, P.h, P.M);
+      adj_step<G>(m, F, P.p, P.h, P.M, P.A.tape0, P.A.tape_len);
     }
     if (P.grad_u0)
       for (int e = g.lane; e < N; e += G) P.grad_u0[c * N + e] = F.ubar[e];
