@@ -55,11 +55,11 @@ GOLDEN = 0.6180339887498949
 # dram__bytes_read.sum + dram__bytes_write.sum of one integration launch from
 # an ncu capture of the current kernel (bytes per launch), keyed by workload;
 # None while no capture of the current kernel exists.  batched: 2^18 cells
-# captured (264,804,096 B), scaled by cells to the 2^20-cell launch (the
+# captured (268,743,424 B), scaled by cells to the 2^20-cell launch (the
 # traffic per cell does not depend on the launch size); flame1d: the 8th split
 # step's integration launch, whose 0.5 MB state stays in L2 (writes are not
 # all flushed by the kernel's end).
-TRAFFIC = {"batched": (136091904 + 128712192) * 4, "flame1d": 1395456 + 125952}
+TRAFFIC = {"batched": (138423296 + 130320128) * 4, "flame1d": 1398528 + 125696}
 
 
 def _env_int(k, d):
@@ -109,11 +109,11 @@ def adjoint_flop_model(mech, M):
     reaction.  Their reverse: per species 34 plus 3 per reaction slot the
     species fills, per reaction 26.  A dual (value, tangent) pass costs 2.5x
     its value pass's arithmetic plus one multiply per exponential.  Per step:
-    6 value and M dual forward passes (f at u_n twice, at the two stage
-    arguments twice, the M J q_j once: their tapes are kept for the reverse
-    sweep), 3 value and M dual reverse passes; the Krylov and stage algebra
-    forward and reverse three times the forward step's (the integrator's
-    Arnoldi and attempt counts)."""
+    3 value and M dual forward passes (f at u_n and at the two stage
+    arguments, and the M J q_j; every tape is kept for the reverse sweep), 3
+    value and M dual reverse passes; the Krylov and stage algebra forward and
+    reverse three times the forward step's (the integrator's Arnoldi and
+    attempt counts)."""
     ns, nr = mech.n_species, mech.n_reactions
     kind = np.asarray(mech.kind)
     rev = np.asarray(mech.reversible).astype(bool)
@@ -128,7 +128,7 @@ def adjoint_flop_model(mech, M):
     fwd_d = 2.5 * fwd_v + exps
     rev_d = 2.5 * rev_v
     krylov = 3 * (fm["arnoldi"] + fm["attempt"])
-    return float(6 * (fwd_v + EXP_FLOPS * exps) + M * (fwd_d + EXP_FLOPS * exps) + 3 * rev_v + M * rev_d + krylov)
+    return float(3 * (fwd_v + EXP_FLOPS * exps) + M * (fwd_d + EXP_FLOPS * exps) + 3 * rev_v + M * rev_d + krylov)
 
 
 def algorithmic_flops(model, stats, M, exp_flops=EXP_FLOPS):

@@ -454,9 +454,9 @@ int rk_rok4e_fixed_steps(const rk_mech* mech, double* Y, int64_t ncell, double p
  * including the dependence of the Arnoldi basis on the state and on ln A
  * (second derivatives of the source term).  The paper has no adjoint; this is
  * the library's sensitivity extension of its integrator.  Workspace:
- * rk_rok4e_adjoint_workspace_size (about (40 + 20 M) N + (12 + 6 M) Nr
+ * rk_rok4e_adjoint_workspace_size (about (100 + 20 M) N + (30 + 6 M) Nr
  * doubles per cell for Krylov dimension M, one contiguous record per cell: the
- * Arnoldi columns' right-hand-side tapes are kept for the reverse sweep).  The sums over cells and within a cell have a
+ * tapes of every right-hand-side pass of a step are kept for its reverse sweep).  The sums over cells and within a cell have a
  * fixed order: repeated calls give the same bits. */
 size_t rk_rok4e_adjoint_workspace_size(const rk_mech* mech, int64_t ncell, int32_t krylov_dim);
 int rk_rok4e_adjoint(const rk_mech* mech, const double* checkpoints, const double* ubar, int64_t ncell,

@@ -88,9 +88,10 @@ struct AdjLayout {
   int u, fn, Q, K, F, arg1, arg2, ubar, Kbar, Qbar, fb2, fbn, wbar, w, w1, w2, tmp, H, p1, p2, hn, Linv, zs, ys,
       Lbar, Hbar, scal, theta;
   int rows_d;
-  // dual rows: the tape of a right-hand-side pass (rows [0, tape_len): ud .. sc),
-  // the reverse pass's work arrays, then M more tapes (the Arnoldi columns'
-  // J q_j passes, kept for the reverse sweep) from row tape0
+  // dual rows: one right-hand-side pass's tape (rows [0, tape_len): ud .. sc;
+  // that of f(u_n)), the reverse pass's work arrays, then M + 2 more tapes
+  // from row tape0: the Arnoldi columns' J q_j passes, f(arg1), f(arg2); all
+  // kept for the step's reverse sweep
   int ud, fd, C, cp, h, g, dcp, om, k, rfac, q, Ms, dlnk, dkdM, omg, sc, Cbar, gbar, ombar, Mbar, ubd, fbd, Pbb, drf;
   int tape_len, tape0;
   int rows_D;
@@ -467,11 +468,15 @@ __device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double 
   if (M > N) M = N;
   double* Q = &F.Q[0];
   // ---------------------------------------------------------------- forward
-  adj_load_ud<G>(F, N, F.u, nullptr);
-  adj_rhs_fwd<G, double>(m, F, p);
+  // the tapes of f(u_n) (in the frame's own tape rows), f(arg1) and f(arg2)
+  // (after the M Arnoldi columns') are kept as well, so the reverse sweep
+  // recomputes no forward pass
+  const AdjFrame& Fu = F;
+  adj_load_ud<G>(Fu, N, F.u, nullptr);
+  adj_rhs_fwd<G, double>(m, Fu, p);
   double beta2 = 0.0;
   for (int e = L; e < N; e += G) {
-    F.fn[e] = F.fd[e].v;
+    F.fn[e] = Fu.fd[e].v;
     beta2 = fma(F.fn[e], F.fn[e], beta2);
   }
   const double beta = sqrt(g.sum(beta2));
@@ -536,9 +541,10 @@ __device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double 
         const double acc = (i == 1) ? A21 * F.K[e] : fma(A32, F.K[(int64_t)N + e], A31 * F.K[e]);
         arg[e] = F.u[e] + h * acc;
       }
-      adj_load_ud<G>(F, N, arg, nullptr);
-      adj_rhs_fwd<G, double>(m, F, p);
-      for (int e = L; e < N; e += G) F.tmp[e] = F.fd[e].v;  // f_i (kept for stage 4)
+      const AdjFrame Fa = adj_tape(F, tape0 + (int64_t)(M + i - 1) * tape_len);
+      adj_load_ud<G>(Fa, N, arg, nullptr);
+      adj_rhs_fwd<G, double>(m, Fa, p);
+      for (int e = L; e < N; e += G) F.tmp[e] = Fa.fd[e].v;  // f_i (kept for stage 4)
     }
     double z[MAXM];
     for (int l = 0; l < MAXM; ++l) z[l] = 0.0;
@@ -618,10 +624,8 @@ __device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double 
       const Col<double>& arg = (i == 1) ? F.arg1 : F.arg2;
       if (i == 2)
         for (int e = L; e < N; e += G) F.fb2[e] += F.w[e];
-      adj_load_ud<G>(F, N, arg, nullptr);
-      adj_rhs_fwd<G, double>(m, F, p);
       for (int e = L; e < N; e += G) F.fbd[e] = Dual{i == 2 ? F.fb2[e] : F.w[e], 0.0};
-      adj_rhs_rev<G, double>(m, F, false);
+      adj_rhs_rev<G, double>(m, adj_tape(F, tape0 + (int64_t)(M + i - 1) * tape_len), false);
       for (int e = L; e < N; e += G) {
         const double ab = F.ubd[e].v;
         F.ubar[e] += ab;
@@ -705,10 +709,8 @@ __device__ void adj_step(const MechView& m, const AdjFrame& F, double p, double 
     for (int e = L; e < N; e += G) F.fbn[e] += F.Qbar[e] / beta - qf * F.fn[e] / (beta * beta * beta);
   }
   // f_n = f(u)
-  adj_load_ud<G>(F, N, F.u, nullptr);
-  adj_rhs_fwd<G, double>(m, F, p);
   for (int e = L; e < N; e += G) F.fbd[e] = Dual{F.fbn[e], 0.0};
-  adj_rhs_rev<G, double>(m, F, false);
+  adj_rhs_rev<G, double>(m, Fu, false);
   for (int e = L; e < N; e += G) F.ubar[e] += F.ubd[e].v;
   g.sync();
 }

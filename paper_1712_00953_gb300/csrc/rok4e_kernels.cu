@@ -981,7 +981,7 @@ static AdjLayout make_adj_layout(const MechLayout& L, int M) {
   A.gbar = take(ns1); A.ombar = take(ns1); A.Mbar = take(ntb); A.ubd = take(N); A.fbd = take(N);
   A.Pbb = take(nr); A.drf = take(nr);
   A.tape_len = A.Cbar;  // ud .. sc: what a forward pass writes and its reverse reads
-  A.tape0 = take(M * A.tape_len);
+  A.tape0 = take((M + 2) * A.tape_len);
   A.rows_D = r;
   return A;
 }
