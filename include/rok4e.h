@@ -205,7 +205,11 @@ typedef struct rk_opts {
                              4: FP64 throughout except w = nu^T q (in the
                              right-hand side and the Jacobian-vector product),
                              which is formed on the tensor cores as in
-                             rk_chem_rhs_tc; needs lanes_per_cell 0 or 32 */
+                             rk_chem_rhs_tc; needs lanes_per_cell 0 or 32.
+                             5: FP64 throughout except the exponentials'
+                             polynomial tails (FP32, ~1e-13 relative): the
+                             FP64 kernel's layout and occupancy, three FP64
+                             instructions fewer per exponential */
   double* trace;          /* device [ncell x trace_cap]: +h accepted, -h rejected, 0 unused */
   void* ev_begin;         /* optional cudaEvent_t recorded on the stream right before the */
   void* ev_end;           /* integration kernel and right after it (timing hook), or NULL;
@@ -454,7 +458,7 @@ int rk_rok4e_fixed_steps(const rk_mech* mech, double* Y, int64_t ncell, double p
  * including the dependence of the Arnoldi basis on the state and on ln A
  * (second derivatives of the source term).  The paper has no adjoint; this is
  * the library's sensitivity extension of its integrator.  Workspace:
- * rk_rok4e_adjoint_workspace_size (about (100 + 20 M) N + (30 + 6 M) Nr
+ * rk_rok4e_adjoint_workspace_size (about (86 + 14 M) N + (19 + 4 M) Nr
  * doubles per cell for Krylov dimension M, one contiguous record per cell: the
  * tapes of every right-hand-side pass of a step are kept for its reverse sweep).  The sums over cells and within a cell have a
  * fixed order: repeated calls give the same bits. */

@@ -88,10 +88,11 @@ struct AdjLayout {
   int u, fn, Q, K, F, arg1, arg2, ubar, Kbar, Qbar, fb2, fbn, wbar, w, w1, w2, tmp, H, p1, p2, hn, Linv, zs, ys,
       Lbar, Hbar, scal, theta;
   int rows_d;
-  // dual rows: one right-hand-side pass's tape (rows [0, tape_len): ud .. sc;
-  // that of f(u_n)), the reverse pass's work arrays, then M + 2 more tapes
-  // from row tape0: the Arnoldi columns' J q_j passes, f(arg1), f(arg2); all
-  // kept for the step's reverse sweep
+  // dual rows: one right-hand-side pass's tape (rows [0, tape_len): ud .. sc,
+  // what a forward pass writes and its reverse reads; that of f(u_n)), the
+  // arrays a pass uses only within itself (g, q) and the reverse pass's work
+  // arrays, then M + 2 more tapes from row tape0: the Arnoldi columns' J q_j
+  // passes, f(arg1), f(arg2); all kept for the step's reverse sweep
   int ud, fd, C, cp, h, g, dcp, om, k, rfac, q, Ms, dlnk, dkdM, omg, sc, Cbar, gbar, ombar, Mbar, ubd, fbd, Pbb, drf;
   int tape_len, tape0;
   int rows_D;
@@ -130,7 +131,7 @@ __device__ inline AdjFrame adj_frame(double* wsd, Dual* wsD, const AdjLayout& L,
 // Arnoldi column); the work arrays stay shared.
 __device__ inline AdjFrame adj_tape(const AdjFrame& F, int64_t delta) {
   AdjFrame t = F;
-  Col<Dual>* cols[] = {&t.ud, &t.fd, &t.C, &t.cp, &t.h, &t.g, &t.dcp, &t.om, &t.k, &t.rfac, &t.q, &t.Ms,
+  Col<Dual>* cols[] = {&t.ud, &t.fd, &t.C, &t.cp, &t.h, &t.dcp, &t.om, &t.k, &t.rfac, &t.Ms,
                        &t.dlnk, &t.dkdM, &t.omg, &t.sc};
   for (Col<Dual>* c : cols) c->p += delta;
   return t;

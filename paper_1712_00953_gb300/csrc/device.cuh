@@ -811,7 +811,7 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
       // E over its products and Einv over its reactants (the pressure factor
       // (RT/p_ref)^dnu included); CE = C E, so k/Kc prod C^nu'' is three products
       const double a = s.gRT[k] + lnRTp;
-      if (MIXED || cs->prec == 3) exp_pm_mixed(a, m.etab, &s.E[k], &s.Einv[k]);
+      if (MIXED || cs->prec == 3 || cs->prec == 5) exp_pm_mixed(a, m.etab, &s.E[k], &s.Einv[k]);
       else exp_pm(a, m.etab, &s.E[k], &s.Einv[k]);
       s.CE[k] = __dmul_rn(Ck, s.E[k]);
     }
@@ -931,7 +931,7 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
     const bool rev = (meta >> 2) & 1;
     const int dnu = ((meta >> 4) & 15) - 4;
     const double lnk = fma(-m.EaR[j], invT, fma(m.bexp[j], lnT, m.lnA[j]));
-    double k = (MIXED || cs->prec == 3) ? exp_mixed(lnk, m.etab) : exp_fast(lnk, m.etab);
+    double k = (MIXED || cs->prec == 3 || cs->prec == 5) ? exp_mixed(lnk, m.etab) : exp_fast(lnk, m.etab);
     const double Pf = __dmul_rn(s.C[ra], s.C[rb]);
     // Rb = prod C^nu'' / Kc (the caching evaluation keeps it), rfac = 1/Kc
     // (caching only), PfRb = Pf - Rb: from the per-species factors as
@@ -1707,7 +1707,7 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
   int n_acc = 0, n_rej = 0, n_rhs = 0, status = RK_CELL_OK, n_att = 0;
   CellScalars cs;
   cs.pinv = 1.0 / fabs(pr);
-  cs.prec = P.precision == 3 ? 3 : (TC ? 4 : 0);
+  cs.prec = (P.precision == 3 || P.precision == 5) ? P.precision : (TC ? 4 : 0);
   constexpr bool INL = G == 32 && !MIXED;  // the RHS inlined on the main path
   int mdim = 0;
   bool fresh = true;  // f_n and the Krylov basis are due at u (start, or after an accepted step)
@@ -2168,10 +2168,9 @@ struct AdjointParams {
   int nsteps, M;
 };
 
-// One group of G lanes per cell (see adjoint.cuh); 128-thread blocks.  The
-// grid holds as many blocks as are resident at once and the cells are dealt
-// to them in turn (cell c to block c mod gridDim.x), so every SM receives the
-// same number of cells and none idles while others finish.
+// One group of G lanes per cell (see adjoint.cuh); 128-thread blocks, at most
+// as many as are resident at once, the cells dealt to them in turn (cell c to
+// block c mod gridDim.x) when there are more cells than slots.
 template <int G>
 __global__ void __launch_bounds__(128) rok4e_adjoint_kernel(AdjointParams P) {
   extern __shared__ __align__(16) unsigned char smem[];

@@ -34,8 +34,10 @@ int launch_rkdp(const IntegrateLaunch& a) {
 }
 
 // The adjoint: 128-thread blocks of 128 / G cell slots, the mechanism in
-// shared memory, as many blocks as the device holds at once (at most one per
-// cell), so the cells dealt over them leave every SM the same share.
+// shared memory; enough blocks for one slot per cell, at most as many as the
+// device holds at once (the cells are then dealt over them in turn).  Filling
+// every resident slot instead, with some warps holding one or two cells,
+// measured 28 % slower on 4096 cells at 8 lanes.
 template <int G>
 int launch_adjoint(const AdjointParams& P, size_t smem, cudaStream_t st) {
   cudaError_t e =
@@ -50,7 +52,8 @@ int launch_adjoint(const AdjointParams& P, size_t smem, cudaStream_t st) {
   if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (per_sm < 1) return set_error(RK_E_UNSUPPORTED, "adjoint kernel cannot be resident on an SM");
   const int64_t resident = (int64_t)per_sm * n_sm;
-  const int64_t blocks = P.ncell < resident ? P.ncell : resident;
+  const int64_t need = (P.ncell * G + 127) / 128;
+  const int64_t blocks = need < resident ? need : resident;
   rok4e_adjoint_kernel<G><<<(unsigned)blocks, 128, smem, st>>>(P);
   return RK_OK;
 }

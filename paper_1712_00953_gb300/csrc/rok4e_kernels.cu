@@ -350,7 +350,7 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   if (o.trace_cap < 0 || (o.trace_cap > 0 && !o.trace))
     return set_error(RK_E_INVALID_ARGUMENT, "trace_cap > 0 needs a trace array");
   if (o.fixed_h < 0.0 || !isfinite(o.fixed_h)) return set_error(RK_E_INVALID_ARGUMENT, "fixed_h must be >= 0");
-  if (o.precision < 0 || o.precision > 4) return set_error(RK_E_INVALID_ARGUMENT, "precision must be 0..4");
+  if (o.precision < 0 || o.precision > 5) return set_error(RK_E_INVALID_ARGUMENT, "precision must be 0..5");
   if (method == 1 && o.precision != 0) return set_error(RK_E_INVALID_ARGUMENT, "the explicit integrator is FP64 only");
   const bool mixed = o.precision == 1 || o.precision == 2;  // level 3 runs the FP64 kernel with cs.prec = 3
   const int G = o.lanes_per_cell == 0 ? 32 : o.lanes_per_cell;
@@ -393,7 +393,7 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   P.rho_cell = o.reactor == 1 ? o.rho_cell : nullptr;
   {
     const MechLayout& L = mech->host.L;
-    P.mech_copy = (method == 1 || o.precision == 0 || tc) ? L.bytes_fp64
+    P.mech_copy = (method == 1 || o.precision == 0 || tc || o.precision == 5) ? L.bytes_fp64
                                                           : (o.precision == 2 ? L.bytes_f32 : L.bytes_df);
     P.tc_bytes = tc ? (int64_t)16 * 32 * L.nst * L.nrt : 0;
   }
@@ -975,12 +975,15 @@ static AdjLayout make_adj_layout(const MechLayout& L, int M) {
   A.Lbar = take(MAXM * MAXM); A.Hbar = take(MAXM * MAXM); A.scal = take(8); A.theta = take(nr);
   A.rows_d = r;
   r = 0;
-  A.ud = take(N); A.fd = take(N); A.C = take(ns1); A.cp = take(ns1); A.h = take(ns1); A.g = take(ns1);
-  A.dcp = take(ns1); A.om = take(ns1); A.k = take(nr); A.rfac = take(nr); A.q = take(nr); A.Ms = take(ntb);
-  A.dlnk = take(ntb); A.dkdM = take(ntb); A.omg = take(ntb); A.sc = take(SC_N); A.Cbar = take(ns1);
+  // the tape (what a forward pass writes and its reverse reads), then the
+  // arrays a pass only uses within itself
+  A.ud = take(N); A.fd = take(N); A.C = take(ns1); A.cp = take(ns1); A.h = take(ns1); A.dcp = take(ns1);
+  A.om = take(ns1); A.k = take(nr); A.rfac = take(nr); A.Ms = take(ntb); A.dlnk = take(ntb); A.dkdM = take(ntb);
+  A.omg = take(ntb); A.sc = take(SC_N);
+  A.tape_len = r;
+  A.g = take(ns1); A.q = take(nr); A.Cbar = take(ns1);
   A.gbar = take(ns1); A.ombar = take(ns1); A.Mbar = take(ntb); A.ubd = take(N); A.fbd = take(N);
   A.Pbb = take(nr); A.drf = take(nr);
-  A.tape_len = A.Cbar;  // ud .. sc: what a forward pass writes and its reverse reads
   A.tape0 = take((M + 2) * A.tape_len);
   A.rows_D = r;
   return A;

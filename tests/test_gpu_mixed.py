@@ -6,7 +6,8 @@ Gram-Schmidt pass of Arnoldi with FP32 inner products and the exponentials'
 polynomial tails in FP32; level 2 also runs the Jacobian-vector products in
 FP32; level 3 keeps the Krylov path in FP64 with a double-float J v core;
 level 4 keeps everything FP64 but forms w = nu^T q on the tensor cores from
-exact 8-bit digit slices of q.
+exact 8-bit digit slices of q; level 5 keeps everything FP64 but the
+exponentials' polynomial tails.
 The bar is the library's, for every level: |dY| <= 1e-8 + 1e-6 |Y| and
 |dT| <= 1e-6 K against the FP64 oracle replaying the GPU run's own step
 sequence.
@@ -199,7 +200,7 @@ def _run(rk, mech, U, w, precision, cap=8192, M=4):
     return Y.cpu().numpy(), st.cpu().numpy(), tr.cpu().numpy()
 
 
-@pytest.mark.parametrize("precision", [1, 2, 3, 4])
+@pytest.mark.parametrize("precision", [1, 2, 3, 4, 5])
 def test_mixed_integration_error_vs_fp64_oracle(rk, precision):
     """Mixed-precision ROK4E on the small workload (10 species / 24
     reactions, one 1e-6 s step), replayed through the FP64 oracle, at the
@@ -223,7 +224,7 @@ def test_mixed_integration_error_vs_fp64_oracle(rk, precision):
     assert dT.max() <= 1e-6, dT.max()
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3, 4, 5])
 def test_flame_mechanism_levels_vs_fp64_oracle(rk, precision):
     """The precision levels on the 1-D flame's mechanism (30 species / 150
     reactions, 4 third-body, 2 Troe) and tanh field: the reaction sub-step of
@@ -279,7 +280,7 @@ def test_mixed_split_steps_vs_fp64_gpu(rk):
     _, U0 = field_tanh_front(512, mech.n_species, w.field_seed)
     dx = 1e-2 / 512
     res = {}
-    for prec in (0, 1, 2, 3, 4):
+    for prec in (0, 1, 2, 3, 4, 5):
         U = torch.tensor(U0, device="cuda")
         hc = torch.zeros(512, dtype=torch.float64, device="cuda")
         for _ in range(5):
@@ -288,10 +289,34 @@ def test_mixed_split_steps_vs_fp64_gpu(rk):
         torch.cuda.synchronize()
         res[prec] = U.cpu().numpy()
     ns = mech.n_species
-    for prec in (1, 2, 3, 4):
+    for prec in (1, 2, 3, 4, 5):
         dY = np.abs(res[prec][:, :ns] - res[0][:, :ns])
         dT = np.abs(res[prec][:, ns] - res[0][:, ns])
         print(f"mixed level {prec} vs FP64 GPU after 5 split steps: max |dY| {dY.max():.3e} (per species "
               f"{np.array2string(dY.max(axis=0), precision=1)}), max |dT| {dT.max():.3e} K")
         assert np.all(np.isfinite(res[prec]))
         assert dY.max() < 1e-6 and dT.max() < 1e-3
+
+
+def test_batched_mechanism_fp32_exp_tails_vs_fp64_oracle(rk):
+    """Precision 5 (FP32 exponential tails only) on the batched workload's
+    mechanism and field (53 species / 325 reactions, one 1e-6 s step of 64
+    cells spread over the 2^20-cell field), replayed through the FP64 oracle
+    at the library's bar."""
+    from oracle import rok4e as orok
+    from oracle.kinetics import Kinetics
+    from synth.fields import initial_state
+
+    w, mech = _mech("batched")
+    U_all = initial_state(w, n_cells=1 << 14)
+    U = U_all[np.linspace(0, U_all.shape[0] - 1, 24).astype(np.int64)]
+    out, st, tr = _run(rk, mech, U, w, 5)
+    assert np.all(st[:, 3] == 0)
+    ref, _ = orok.integrate_cells(Kinetics(mech), U, P, w.dt, w.rtol, w.atol, 4,
+                                  replay=[[(abs(h), h > 0) for h in r if h != 0.0] for r in tr])
+    ns = mech.n_species
+    dY = np.abs(out[:, :ns] - ref[:, :ns])
+    dT = np.abs(out[:, ns] - ref[:, ns])
+    print(f"batched mechanism, precision 5 vs FP64 oracle (replay): max |dY| {dY.max():.3e}, max |dT| {dT.max():.3e} K")
+    assert np.all(dY <= 1e-8 + 1e-6 * np.abs(ref[:, :ns]))
+    assert dT.max() <= 1e-6
