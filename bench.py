@@ -48,7 +48,7 @@ D_DIFF = 1.0e-4  # m^2/s
 LENGTH = 1.0e-2  # m
 P_ATM = 101325.0
 L2_FLUSH_BYTES = 256 << 20
-PREC = {"fp64": 0, "mixed": 1, "mixed-fp32jv": 2, "mixed-df": 3, "tensor": 4, "exp32": 5}
+PREC = {"fp64": 0, "mixed": 1, "mixed-fp32jv": 2, "mixed-df": 3, "tensor": 4, "exp32": 5, "fp32jv": 6}
 FP64_PEAK = 1.25  # TFLOP/s: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal)
 GOLDEN = 0.6180339887498949
 
@@ -631,8 +631,8 @@ def run_flame(args, dev, precision, extras=True):
                         "frac": achieved / FP64_PEAK, "traffic": TRAFFIC["flame1d"] if precision == 0 else None,
                         "algorithmic_bytes_per_launch": int(npts * N * 8 * 3 + npts * (16 + 16)),
                         "kernel": {0: "rok4e_integrate_kernel<32, 0, 0>", 3: "rok4e_integrate_kernel<32, 0, 0>",
-                                   4: "rok4e_integrate_kernel<32, 0, 1>",
-                                   5: "rok4e_integrate_kernel<32, 0, 0>"}.get(precision,
+                                   4: "rok4e_integrate_kernel<32, 0, 1>", 5: "rok4e_integrate_kernel<32, 0, 0>",
+                                   6: "rok4e_integrate_kernel<32, 0, 0>"}.get(precision,
                                                                               "rok4e_integrate_kernel<32, 1, 0>"),
                         "kernel_ms_per_step": 1e3 * kern_total / K},
            "cuda_graph": {"timed_region": "one captured split step replayed per step",
@@ -742,7 +742,7 @@ def run_batched_levels(args, dev, M, lanes, cpb):
     U0 = torch.tensor(U_host, device=dev)
     ws = torch.empty(rk.rok4e_workspace_size(m, n, M), dtype=torch.uint8, device=dev)
     out = {"cells": n, "krylov_dim": M, "steps": args.level_steps}
-    for name in ("fp64", "mixed", "mixed-fp32jv", "mixed-df", "tensor", "exp32"):
+    for name in ("fp64", "mixed", "mixed-fp32jv", "mixed-df", "tensor", "exp32", "fp32jv"):
         prec = PREC[name]
         kw = dict(lanes_per_cell=lanes, cells_per_block=cpb, precision=prec, queue_order=args.queue_order)
         if name == "tensor":  # one cell per warp; the nu^T tiles take shared memory: as many cells as fit
@@ -778,7 +778,7 @@ def run_batched_levels(args, dev, M, lanes, cpb):
         out[name] = {"value": n * args.level_steps / t, "unit": "cell-steps/s",
                      "attempts_per_cell_step": float(att.mean()), "cells_failed": int((s_np[:, 3] != 0).sum()),
                      "accuracy": acc}
-    for name in ("mixed", "mixed-fp32jv", "mixed-df", "tensor", "exp32"):
+    for name in ("mixed", "mixed-fp32jv", "mixed-df", "tensor", "exp32", "fp32jv"):
         out[name]["vs_fp64"] = out[name]["value"] / out["fp64"]["value"]
     return out
 
@@ -1193,7 +1193,7 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and not args.headline_only:
         configs = {"small": run_small(args, dev), "flame1d": run_flame(args, dev, 0)}
         mixed = {}
-        for name in ("mixed", "mixed-fp32jv", "mixed-df", "tensor", "exp32"):
+        for name in ("mixed", "mixed-fp32jv", "mixed-df", "tensor", "exp32", "fp32jv"):
             mixed[name] = run_flame(args, dev, PREC[name], extras=False)
         mixed["note"] = ("the flame1d workload at each precision level against its FP64 value "
                          f"{configs['flame1d']['value']:.0f} cell-steps/s; accuracy against the FP64 oracle")

@@ -134,8 +134,9 @@ int rk_chem_rhs(const rk_mech* mech, const double* Y, const double* src, double 
  * evaluated in FP32 (the mixed-precision integrator's J v); mode 3: the
  * analytic product with its reaction-level core in double-float (precision
  * level 3); mode 4: the analytic product with nu^T dq formed on the tensor
- * cores as in rk_chem_rhs_tc (precision level 4).  All arrays device
- * [ncell x N]. */
+ * cores as in rk_chem_rhs_tc (precision level 4); mode 5: the analytic
+ * product in FP32 arithmetic on the FP64 caches (precision level 6).  All
+ * arrays device [ncell x N]. */
 int rk_chem_jvp(const rk_mech* mech, const double* Y, const double* V, double p, double* JV,
                 int64_t ncell, int32_t mode, void* stream);
 
@@ -209,7 +210,11 @@ typedef struct rk_opts {
                              5: FP64 throughout except the exponentials'
                              polynomial tails (FP32, ~1e-13 relative): the
                              FP64 kernel's layout and occupancy, three FP64
-                             instructions fewer per exponential */
+                             instructions fewer per exponential.
+                             6: as 5 with the Jacobian-vector products in FP32
+                             arithmetic on the FP64 caches (no FP32 copies,
+                             so the FP64 kernel's occupancy; ~1e-6 relative
+                             J v, which the Krylov basis tolerates) */
   double* trace;          /* device [ncell x trace_cap]: +h accepted, -h rejected, 0 unused */
   void* ev_begin;         /* optional cudaEvent_t recorded on the stream right before the */
   void* ev_end;           /* integration kernel and right after it (timing hook), or NULL;

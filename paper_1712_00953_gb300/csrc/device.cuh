@@ -339,6 +339,8 @@ struct SlotLayout {
   int part;                                   // [npiece]: gather partial sums
   int C2, dC2;                                // species: double-float C and dC (precision 3, else -1)
   int dig;                                    // BF16 digits of q, [8][16 nrt] (precision 4, else -1)
+  int fj;   // precision 6: FP32 species factors of the J v, when they do not fit beside the
+            // FP32 reaction caches in the kc/krc/qT storage (else -1)
   int H, LU, piv, red, Bm;                    // small (Bm: I - (I - h gamma H)^-1)
   int fbase;  // FP32 region (mixed precision only), offset in doubles
   int fC, fdC, fh, fcp, fdcp, fom, fq, fkc, fkr, ftb, fQ, fw, fpart;  // offsets in floats from fbase
@@ -349,7 +351,7 @@ struct SlotLayout {
 // species arrays of precision level 3 (left out otherwise, which lets a 53-species
 // mechanism keep 7 cells per block instead of 6).
 inline SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false, int nx = 0, bool df = false,
-                            bool tc = false) {
+                            bool tc = false, bool f32jv = false) {
   SlotLayout s;
   s.N = L.ns + 1 + nx;
   s.ns = L.ns;
@@ -398,6 +400,9 @@ inline SlotLayout make_slot(const MechLayout& L, int M, bool mixed = false, int 
   s.C2 = df ? take(ns1) : -1;
   s.dC2 = df ? take(ns1) : -1;
   s.dig = tc ? take(2 * 16 * L.nrt) : -1;  // 8 x 16 nrt BF16 = 2 x 16 nrt doubles
+  // precision 6 keeps its FP32 reaction caches in the first half of the kc/krc/qT
+  // storage and its 8 FP32 species arrays in the second half when they fit there
+  s.fj = (f32jv && 8 * ns1 > 3 * nr_even) ? take((8 * ns1 + 1) / 2) : -1;
   // M x M matrices stored with row stride MAXM: M rows
   s.H = take(M * MAXM);
   s.LU = take(M * MAXM);
@@ -536,6 +541,9 @@ struct SlotPtrs {
   double *C, *dC, *cp, *hRT, *dcp, *gRT, *E, *Einv, *CE, *om, *q, *kc, *krc, *qT, *tb, *tro, *part;
   df2 *C2, *dC2;
   uint16_t* dig;
+  // precision 6: FP32 J v caches in the kc/krc/qT storage -- per reaction k, k/Kc, dq/dT;
+  // per species C, rho/W, W/rho, w, h/RT - esh, (cp - h)/T w / RT, Y dcp/dT / W, cp / W
+  float *xk, *xkr, *xqT, *xC, *xE, *xEinv, *xom, *xg, *xh, *xdcp, *xcp;
   double *H, *LU, *piv, *red, *Bm;
   float *fC, *fdC, *fh, *fcp, *fdcp, *fom, *fq, *fkc, *fkr, *ftb, *fQ, *fw, *fpart;  // mixed precision
   int Nq;  // stride between Krylov / stage vectors
@@ -571,6 +579,22 @@ __device__ inline SlotPtrs slot_ptrs(double* b, const SlotLayout& s) {
   p.C2 = s.C2 >= 0 ? reinterpret_cast<df2*>(b + s.C2) : nullptr;
   p.dC2 = s.dC2 >= 0 ? reinterpret_cast<df2*>(b + s.dC2) : nullptr;
   p.dig = s.dig >= 0 ? reinterpret_cast<uint16_t*>(b + s.dig) : nullptr;
+  {
+    const int nr_even = ((s.nr > 0 ? s.nr : 1) + 1) & ~1, ns1 = s.ns + 1;
+    float* R = reinterpret_cast<float*>(b + s.kc);  // 3 nr_even doubles = 6 nr_even floats
+    p.xk = R;
+    p.xkr = R + nr_even;
+    p.xqT = R + 2 * nr_even;
+    float* X = s.fj >= 0 ? reinterpret_cast<float*>(b + s.fj) : R + 3 * nr_even;
+    p.xC = X;
+    p.xE = X + ns1;
+    p.xEinv = X + 2 * ns1;
+    p.xom = X + 3 * ns1;
+    p.xg = X + 4 * ns1;
+    p.xh = X + 5 * ns1;
+    p.xdcp = X + 6 * ns1;
+    p.xcp = X + 7 * ns1;
+  }
   p.tb = b + s.tb;
   p.H = b + s.H;
   p.LU = b + s.LU;
@@ -811,7 +835,7 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
       // E over its products and Einv over its reactants (the pressure factor
       // (RT/p_ref)^dnu included); CE = C E, so k/Kc prod C^nu'' is three products
       const double a = s.gRT[k] + lnRTp;
-      if (MIXED || cs->prec == 3 || cs->prec == 5) exp_pm_mixed(a, m.etab, &s.E[k], &s.Einv[k]);
+      if (MIXED || cs->prec == 3 || cs->prec >= 5) exp_pm_mixed(a, m.etab, &s.E[k], &s.Einv[k]);
       else exp_pm(a, m.etab, &s.E[k], &s.Einv[k]);
       s.CE[k] = __dmul_rn(Ck, s.E[k]);
     }
@@ -931,7 +955,7 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
     const bool rev = (meta >> 2) & 1;
     const int dnu = ((meta >> 4) & 15) - 4;
     const double lnk = fma(-m.EaR[j], invT, fma(m.bexp[j], lnT, m.lnA[j]));
-    double k = (MIXED || cs->prec == 3 || cs->prec == 5) ? exp_mixed(lnk, m.etab) : exp_fast(lnk, m.etab);
+    double k = (MIXED || cs->prec == 3 || cs->prec >= 5) ? exp_mixed(lnk, m.etab) : exp_fast(lnk, m.etab);
     const double Pf = __dmul_rn(s.C[ra], s.C[rb]);
     // Rb = prod C^nu'' / Kc (the caching evaluation keeps it), rfac = 1/Kc
     // (caching only), PfRb = Pf - Rb: from the per-species factors as
@@ -1011,6 +1035,10 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
         reinterpret_cast<df2*>(s.qT)[j] = df_from(qT);
         reinterpret_cast<df2*>(s.kc)[j] = df_from(k);
         reinterpret_cast<df2*>(s.krc)[j] = df_from(kr);
+      } else if (cs->prec == 6) {  // FP32 copies for the FP32 J v, in the same storage
+        s.xk[j] = __double2float_rn(k);
+        s.xkr[j] = __double2float_rn(kr);
+        s.xqT[j] = __double2float_rn(qT);
       } else {
         s.qT[j] = qT;
         s.kc[j] = k;
@@ -1060,6 +1088,16 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
       s.hRT[k] = (s.cp[k] - s.hRT[k]) * invT * om;
       s.dcp[k] = uu[k] * s.dcp[k] * m.invW[k];
       s.cp[k] = (s.cp[k] - esh) * m.invW[k];
+      if (cs->prec == 6) {  // FP32 copies for the FP32 J v
+        s.xC[k] = __double2float_rn(s.C[k]);
+        s.xE[k] = __double2float_rn(s.E[k]);
+        s.xEinv[k] = __double2float_rn(s.Einv[k]);
+        s.xom[k] = __double2float_rn(om);
+        s.xg[k] = __double2float_rn(s.gRT[k]);
+        s.xh[k] = __double2float_rn(s.hRT[k]);
+        s.xdcp[k] = __double2float_rn(s.dcp[k]);
+        s.xcp[k] = __double2float_rn(s.cp[k]);
+      }
     }
   }
   if (aux) {
@@ -1103,6 +1141,7 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
   if (g.lane == 0) {
     const double r = aux ? fT : -T * Sh * invrho * invcb;
     out[ns] = src ? __dadd_rn(r, src[ns]) : r;
+    if (cache && cs->prec == 6) s.xC[ns] = 1.f;  // the empty reaction slot
   }
   if (cache) {
     cs->T = T;
@@ -1425,6 +1464,110 @@ __device__ __noinline__ void jvp_eval_f32(const MechView& m, const SlotPtrs& s, 
   g.sync();
 }
 
+// A small nonzero integer held as a double, as a float, with integer
+// operations only (sign, exponent rebased from 1023 to 127, the top 20
+// significand bits of the high word): exact for |n| < 2^21.
+__device__ __forceinline__ float small_int_to_float(double x) {
+  const int hi = __double2hiint(x);
+  return __int_as_float((hi & (int)0x80000000) | ((((hi >> 20) & 0x7ff) - 896) << 23) | ((hi & 0xfffff) << 3));
+}
+
+// The analytic J v of jvp_eval in FP32 arithmetic (precision level 6): the
+// caching right-hand side at u_n left FP32 copies of the per-reaction k, k/Kc,
+// dq/dT and of the per-species factors in the spare storage of the FP64 J v
+// caches, and the intermediates -- dC, dq and the gather's partial sums -- are
+// kept as FP32 in the first half of the FP64 arrays' own storage, so the slot
+// layout, the mechanism copy and the occupancy are the FP64 kernel's and the
+// product issues almost no FP64 instruction.  FP32's ~1e-7 rounding (amplified
+// where k Pf and k/Kc Pb nearly cancel) is what the Krylov basis sees; the
+// stages, the error estimate and the state update stay FP64.
+template <int G>
+__device__ __noinline__ void jvp_eval_f32x(const MechView& m, const SlotPtrs& s, const double* uu,
+                                           const CellScalars& cs, const double* v, double* out) {
+  const Grp<G> g;
+  const int ns = m.ns;
+  float* fdC = reinterpret_cast<float*>(s.dC);
+  float* fq = reinterpret_cast<float*>(s.q);
+  float* fpart = reinterpret_cast<float*>(s.part);
+  auto f = [](double x) { return __double2float_rn(x); };
+  const float vT = f(v[ns]);
+  const float T = f(cs.T), invT = f(cs.invT);
+  float a = 0.f;
+  for (int k = g.lane; k < ns; k += G) a = fmaf(f(v[k]), f(m.invW[k]), a);
+  a = g.sum(a);
+  const float drr = cs.cv ? 0.f : -fmaf(a, f(cs.invS), vT * invT);
+  const bool coop_tb = m.ntb > 0 && m.ntb <= MAXM;
+  float mp[MAXM];
+#pragma unroll
+  for (int t = 0; t < MAXM; ++t) mp[t] = 0.f;
+  for (int k = g.lane; k < ns; k += G) {
+    const float dCk = fmaf(s.xC[k], drr, s.xE[k] * f(v[k]));  // xE: rho / W_k
+    fdC[k] = dCk;
+    if (coop_tb) {
+#pragma unroll
+      for (int t = 0; t < MAXM; ++t)
+        if (t < m.ntb) mp[t] = fmaf(f(m.eff[t * ns + k]), dCk, mp[t]);
+    }
+  }
+  if (g.lane == 0) fdC[ns] = 0.f;  // the empty reaction slot (its C = 1 is in xC)
+  if (coop_tb) sum_first<G>(g, mp, m.ntb);
+  g.sync();
+  for (int j = g.lane; j < m.nr; j += G) {
+    const uint32_t sl = m.slots[j];
+    const int ra = sl & 255, rb = (sl >> 8) & 255, pa = (sl >> 16) & 255, pb = sl >> 24;
+    const int meta = m.meta[j];
+    const int kind = meta & 3;
+    const float Cra = s.xC[ra], Crb = s.xC[rb], Cpa = s.xC[pa], Cpb = s.xC[pb];
+    const float dPf = fmaf(fdC[ra], Crb, Cra * fdC[rb]);
+    const float dPb = fmaf(fdC[pa], Cpb, Cpa * fdC[pb]);
+    const float k = s.xk[j], kr = s.xkr[j];
+    float dq = fmaf(s.xqT[j], vT, fmaf(k, dPf, -kr * dPb));
+    if (kind != 0) {
+      const int slot = meta >> 8;
+      const double* t = s.tb + 4 * slot;
+      const float Pf = Cra * Crb, Pb = Cpa * Cpb;
+      float dM = 0.f;
+      if (coop_tb) {
+#pragma unroll
+        for (int q = 0; q < MAXM; ++q)
+          if (q == slot) dM = mp[q];
+      } else {
+        const double* e = m.eff + (size_t)slot * ns;
+        for (int q = 0; q < ns; ++q) dM = fmaf(f(e[q]), fdC[q], dM);
+      }
+      if (kind == 1) dq = f(t[0]) * dq + dM * (k * Pf - kr * Pb);
+      else dq = dq + f(t[1]) * dM * (Pf - f(t[3]) * Pb);
+    }
+    fq[j] = dq;
+  }
+  g.sync();
+  for (int p = g.lane; p < m.npiece; p += G) {  // d w = nu^T dq
+    float acc = 0.f;
+    const int e1 = m.piece_ptr[p + 1];
+    for (int e = m.piece_ptr[p]; e < e1; ++e) acc = fmaf(small_int_to_float(m.csr_nu[e]), fq[m.csr_j[e]], acc);
+    fpart[p] = acc;
+  }
+  g.sync();
+  float dSh = 0.f, dcb = 0.f;
+  for (int k = g.lane; k < ns; k += G) {
+    const float dom = piece_sum(m, static_cast<const float*>(fpart), k);
+    out[k] = (double)(s.xEinv[k] * fmaf(-s.xom[k], drr, dom));  // xEinv: W_k / rho
+    dSh = fmaf(s.xg[k], dom, fmaf(s.xh[k], vT, dSh));
+    dcb = fmaf(s.xdcp[k], vT, fmaf(s.xcp[k], f(v[k]), dcb));
+  }
+  {
+    float t2[2] = {dSh, dcb};
+    sum_many<G, 2>(g, t2);
+    dSh = t2[0];
+    dcb = t2[1];
+  }
+  if (g.lane == 0) {
+    const float Sh = f(cs.Sh);
+    out[ns] = (double)((-(vT * Sh + T * dSh) + T * Sh * (drr + dcb * f(cs.invcb))) * (f(cs.invrho) * f(cs.invcb)));
+  }
+  g.sync();
+}
+
 // ----------------------------------------------------------------- helpers
 template <int G>
 __device__ inline double group_dot(const Grp<G>& g, const double* a, const double* b, int N) {
@@ -1443,6 +1586,7 @@ __device__ inline void apply_jv(const MechView& m, const SlotPtrs& s, const Cell
   if (jv_mode == 0) {
     if (MIXED && fp32_jv) jvp_eval_f32<G>(m, s, s.u, cs, v, out);
     else if (!MIXED && cs.prec == 3) jvp_eval_df<G>(m, s, s.u, cs, v, out);
+    else if (!MIXED && cs.prec == 6) jvp_eval_f32x<G>(m, s, s.u, cs, v, out);
     else jvp_eval<G, MIXED, TC>(m, s, s.u, cs, v, out);
     return;
   }
@@ -1707,7 +1851,7 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
   int n_acc = 0, n_rej = 0, n_rhs = 0, status = RK_CELL_OK, n_att = 0;
   CellScalars cs;
   cs.pinv = 1.0 / fabs(pr);
-  cs.prec = (P.precision == 3 || P.precision == 5) ? P.precision : (TC ? 4 : 0);
+  cs.prec = (P.precision == 3 || P.precision >= 5) ? P.precision : (TC ? 4 : 0);
   constexpr bool INL = G == 32 && !MIXED;  // the RHS inlined on the main path
   int mdim = 0;
   bool fresh = true;  // f_n and the Krylov basis are due at u (start, or after an accepted step)
@@ -2212,7 +2356,7 @@ struct PointParams {
   double p;
   int mode;  // 0 rhs, 1 analytic jvp, 2 finite-difference jvp, 3 mixed rhs, 4 FP32 analytic jvp,
              // 5 analytic jvp with the double-float core, 6 rhs with the tensor-core gather,
-             // 7 analytic jvp with the tensor-core gather
+             // 7 analytic jvp with the tensor-core gather, 8 FP32 analytic jvp on the FP64 caches
   const double* rho_cell;  // constant-volume densities, or null
   int nx;                  // state components after T (5: auxiliary-temperature system)
   int64_t mech_copy;       // bytes of the mechanism copied to shared memory (a prefix)
@@ -2239,7 +2383,7 @@ __global__ void __launch_bounds__(MAX_BLOCK_THREADS) chem_point_kernel(PointPara
   const SlotPtrs s = slot_ptrs(base, P.S);
   if (P.mode >= 3 && P.mode <= 5) init_sentinels<true>(s, m.ns, g.lane);
   else init_sentinels<false>(s, m.ns, g.lane);
-  if (P.mode >= 6)
+  if (P.mode == 6 || P.mode == 7)
     for (int i = g.lane; i < 8 * 16 * m.nrt; i += G) s.dig[i] = 0;
   const int N = m.ns + 1 + m.nx;
   for (int e = g.lane; e < N; e += G) {
@@ -2252,6 +2396,13 @@ __global__ void __launch_bounds__(MAX_BLOCK_THREADS) chem_point_kernel(PointPara
   CellScalars cs;
   cs.pinv = 1.0 / fabs(pr);
   cs.prec = 0;
+  if (P.mode == 8) {
+    cs.prec = 6;
+    rhs_eval_call<G>(m, s, s.u, nullptr, pr, s.fn, true, &cs);
+    jvp_eval_f32x<G>(m, s, s.u, cs, s.F, s.w);
+    for (int e = g.lane; e < N; e += G) P.out[cell * N + e] = s.w[e];
+    return;
+  }
   if (P.mode == 7) {
     cs.prec = 4;
     rhs_eval_call<G, false, true>(m, s, s.u, nullptr, pr, s.fn, true, &cs);

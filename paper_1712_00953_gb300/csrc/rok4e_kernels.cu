@@ -350,7 +350,7 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   if (o.trace_cap < 0 || (o.trace_cap > 0 && !o.trace))
     return set_error(RK_E_INVALID_ARGUMENT, "trace_cap > 0 needs a trace array");
   if (o.fixed_h < 0.0 || !isfinite(o.fixed_h)) return set_error(RK_E_INVALID_ARGUMENT, "fixed_h must be >= 0");
-  if (o.precision < 0 || o.precision > 5) return set_error(RK_E_INVALID_ARGUMENT, "precision must be 0..5");
+  if (o.precision < 0 || o.precision > 6) return set_error(RK_E_INVALID_ARGUMENT, "precision must be 0..6");
   if (method == 1 && o.precision != 0) return set_error(RK_E_INVALID_ARGUMENT, "the explicit integrator is FP64 only");
   const bool mixed = o.precision == 1 || o.precision == 2;  // level 3 runs the FP64 kernel with cs.prec = 3
   const int G = o.lanes_per_cell == 0 ? 32 : o.lanes_per_cell;
@@ -369,7 +369,7 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   P.mech = mech->dev;
   P.L = mech->host.L;
   P.nx = nx;
-  P.S = make_slot(mech->host.L, Meff, mixed, nx, o.precision == 3, tc);
+  P.S = make_slot(mech->host.L, Meff, mixed, nx, o.precision == 3, tc, o.precision == 6);
   P.precision = o.precision;
   P.Y = Y;
   P.src = src;
@@ -393,7 +393,7 @@ int integrate_impl(const rk_mech* mech, double* Y, const double* src, double* h_
   P.rho_cell = o.reactor == 1 ? o.rho_cell : nullptr;
   {
     const MechLayout& L = mech->host.L;
-    P.mech_copy = (method == 1 || o.precision == 0 || tc || o.precision == 5) ? L.bytes_fp64
+    P.mech_copy = (method == 1 || o.precision == 0 || tc || o.precision >= 5) ? L.bytes_fp64
                                                           : (o.precision == 2 ? L.bytes_f32 : L.bytes_df);
     P.tc_bytes = tc ? (int64_t)16 * 32 * L.nst * L.nrt : 0;
   }
@@ -517,7 +517,8 @@ static int point_call(const rk_mech* mech, const double* Y, const double* src, c
   if (rc) return rc;
   if (ncell < 0) return set_error(RK_E_INVALID_ARGUMENT, "ncell < 0");
   if (ncell == 0) return RK_OK;
-  const bool needs_v = mode == 1 || mode == 2 || mode == 4 || mode == 5 || mode == 7;
+  const bool needs_v = mode == 1 || mode == 2 || mode == 4 || mode == 5 || mode == 7 || mode == 8;
+  const bool tc = mode == 6 || mode == 7;
   if (!Y || !out || (needs_v && !V)) return set_error(RK_E_INVALID_ARGUMENT, "null array");
   if (out == Y) return set_error(RK_E_INVALID_ARGUMENT, "output must not alias the state");
   if (!rho_cell && !(p > 0.0)) return set_error(RK_E_INVALID_ARGUMENT, "pressure must be > 0");
@@ -526,7 +527,7 @@ static int point_call(const rk_mech* mech, const double* Y, const double* src, c
   P.nx = nx;
   P.mech = mech->dev;
   P.L = mech->host.L;
-  P.S = make_slot(mech->host.L, 1, mode >= 3 && mode <= 5, nx, mode == 5, mode >= 6);
+  P.S = make_slot(mech->host.L, 1, mode >= 3 && mode <= 5, nx, mode == 5, tc, mode == 8);
   P.Y = Y;
   P.src = src;
   P.V = V;
@@ -536,8 +537,8 @@ static int point_call(const rk_mech* mech, const double* Y, const double* src, c
   P.mode = mode;
   {
     const MechLayout& L = mech->host.L;  // everything but the nu^T tiles; the tiles only with the FP64 arrays
-    P.mech_copy = mode >= 6 ? L.bytes_fp64 : L.off_nuT;
-    P.tc_bytes = mode >= 6 ? (int64_t)16 * 32 * L.nst * L.nrt : 0;
+    P.mech_copy = tc ? L.bytes_fp64 : L.off_nuT;
+    P.tc_bytes = tc ? (int64_t)16 * 32 * L.nst * L.nrt : 0;
   }
   LaunchPlan plan;
   rc = plan_for<32>(chem_point_kernel<32>, mech, P.S, 8, ncell, false, &plan, 0, false, P.mech_copy + P.tc_bytes);
@@ -554,8 +555,8 @@ int rk_chem_rhs(const rk_mech* mech, const double* Y, const double* src, double 
 
 int rk_chem_jvp(const rk_mech* mech, const double* Y, const double* V, double p, double* JV, int64_t ncell,
                 int32_t mode, void* stream) {
-  if (mode < 0 || mode > 4) return set_error(RK_E_INVALID_ARGUMENT, "mode must be 0..4");
-  static const int point_mode[5] = {1, 2, 4, 5, 7};
+  if (mode < 0 || mode > 5) return set_error(RK_E_INVALID_ARGUMENT, "mode must be 0..5");
+  static const int point_mode[6] = {1, 2, 4, 5, 7, 8};
   return point_call(mech, Y, nullptr, V, p, JV, ncell, point_mode[mode], stream);
 }
 

@@ -7,7 +7,8 @@ polynomial tails in FP32; level 2 also runs the Jacobian-vector products in
 FP32; level 3 keeps the Krylov path in FP64 with a double-float J v core;
 level 4 keeps everything FP64 but forms w = nu^T q on the tensor cores from
 exact 8-bit digit slices of q; level 5 keeps everything FP64 but the
-exponentials' polynomial tails.
+exponentials' polynomial tails; level 6 adds an FP32 J v computed on the FP64
+caches.
 The bar is the library's, for every level: |dY| <= 1e-8 + 1e-6 |Y| and
 |dT| <= 1e-6 K against the FP64 oracle replaying the GPU run's own step
 sequence.
@@ -70,6 +71,29 @@ def test_fp32_jvp_close_to_oracle(rk, name):
     ref = np.array([kin.jvp(u, P, v) for u, v in zip(U, V)])
     scale = np.max(np.abs(ref), axis=1, keepdims=True)
     assert np.max(np.abs(out - ref) / scale) < 1e-4
+
+
+@pytest.mark.parametrize("name", ["small", "flame1d", "batched"])
+def test_fp32_jvp_on_fp64_caches_close_to_oracle(rk, name):
+    """The J v of precision level 6 (FP32 arithmetic on the FP64 caches,
+    rk_chem_jvp mode 5) against the oracle's analytic Jacobian: FP32 rounding
+    amplified where forward and reverse rates nearly cancel, the same order
+    as the FP32 J v of level 2."""
+    from oracle.kinetics import Kinetics
+    from synth.fields import field_uniform
+
+    w, mech = _mech(name)
+    kin = Kinetics(mech)
+    U = field_uniform(48, mech.n_species, 31, 600.0, 2500.0)
+    V = np.random.default_rng(9).normal(size=U.shape)
+    V /= np.linalg.norm(V, axis=1, keepdims=True)
+    m = rk.mech_load(mech)
+    out = rk.chem_jvp(m, torch.tensor(U, device="cuda"), torch.tensor(V, device="cuda"), P, mode=5).cpu().numpy()
+    ref = np.array([kin.jvp(u, P, v) for u, v in zip(U, V)])
+    scale = np.max(np.abs(ref), axis=1, keepdims=True)
+    err = np.max(np.abs(out - ref) / scale)
+    print(f"{name}: FP32 J v on the FP64 caches vs oracle {err:.2e} of the row scale")
+    assert err < 1e-4
 
 
 @pytest.mark.parametrize("name", ["small", "flame1d", "batched"])
@@ -200,7 +224,7 @@ def _run(rk, mech, U, w, precision, cap=8192, M=4):
     return Y.cpu().numpy(), st.cpu().numpy(), tr.cpu().numpy()
 
 
-@pytest.mark.parametrize("precision", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("precision", [1, 2, 3, 4, 5, 6])
 def test_mixed_integration_error_vs_fp64_oracle(rk, precision):
     """Mixed-precision ROK4E on the small workload (10 species / 24
     reactions, one 1e-6 s step), replayed through the FP64 oracle, at the
@@ -224,7 +248,7 @@ def test_mixed_integration_error_vs_fp64_oracle(rk, precision):
     assert dT.max() <= 1e-6, dT.max()
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3, 4, 5, 6])
 def test_flame_mechanism_levels_vs_fp64_oracle(rk, precision):
     """The precision levels on the 1-D flame's mechanism (30 species / 150
     reactions, 4 third-body, 2 Troe) and tanh field: the reaction sub-step of
@@ -280,7 +304,7 @@ def test_mixed_split_steps_vs_fp64_gpu(rk):
     _, U0 = field_tanh_front(512, mech.n_species, w.field_seed)
     dx = 1e-2 / 512
     res = {}
-    for prec in (0, 1, 2, 3, 4, 5):
+    for prec in (0, 1, 2, 3, 4, 5, 6):
         U = torch.tensor(U0, device="cuda")
         hc = torch.zeros(512, dtype=torch.float64, device="cuda")
         for _ in range(5):
@@ -289,7 +313,7 @@ def test_mixed_split_steps_vs_fp64_gpu(rk):
         torch.cuda.synchronize()
         res[prec] = U.cpu().numpy()
     ns = mech.n_species
-    for prec in (1, 2, 3, 4, 5):
+    for prec in (1, 2, 3, 4, 5, 6):
         dY = np.abs(res[prec][:, :ns] - res[0][:, :ns])
         dT = np.abs(res[prec][:, ns] - res[0][:, ns])
         print(f"mixed level {prec} vs FP64 GPU after 5 split steps: max |dY| {dY.max():.3e} (per species "
@@ -298,8 +322,10 @@ def test_mixed_split_steps_vs_fp64_gpu(rk):
         assert dY.max() < 1e-6 and dT.max() < 1e-3
 
 
-def test_batched_mechanism_fp32_exp_tails_vs_fp64_oracle(rk):
-    """Precision 5 (FP32 exponential tails only) on the batched workload's
+@pytest.mark.parametrize("precision", [5, 6])
+def test_batched_mechanism_levels_vs_fp64_oracle(rk, precision):
+    """Precision 5 (FP32 exponential tails only) and 6 (also an FP32 J v on
+    the FP64 caches) on the batched workload's
     mechanism and field (53 species / 325 reactions, one 1e-6 s step of 64
     cells spread over the 2^20-cell field), replayed through the FP64 oracle
     at the library's bar."""
@@ -310,13 +336,14 @@ def test_batched_mechanism_fp32_exp_tails_vs_fp64_oracle(rk):
     w, mech = _mech("batched")
     U_all = initial_state(w, n_cells=1 << 14)
     U = U_all[np.linspace(0, U_all.shape[0] - 1, 24).astype(np.int64)]
-    out, st, tr = _run(rk, mech, U, w, 5)
+    out, st, tr = _run(rk, mech, U, w, precision)
     assert np.all(st[:, 3] == 0)
     ref, _ = orok.integrate_cells(Kinetics(mech), U, P, w.dt, w.rtol, w.atol, 4,
                                   replay=[[(abs(h), h > 0) for h in r if h != 0.0] for r in tr])
     ns = mech.n_species
     dY = np.abs(out[:, :ns] - ref[:, :ns])
     dT = np.abs(out[:, ns] - ref[:, ns])
-    print(f"batched mechanism, precision 5 vs FP64 oracle (replay): max |dY| {dY.max():.3e}, max |dT| {dT.max():.3e} K")
+    print(f"batched mechanism, precision {precision} vs FP64 oracle (replay): max |dY| {dY.max():.3e}, "
+          f"max |dT| {dT.max():.3e} K")
     assert np.all(dY <= 1e-8 + 1e-6 * np.abs(ref[:, :ns]))
     assert dT.max() <= 1e-6
