@@ -55,11 +55,11 @@ GOLDEN = 0.6180339887498949
 # dram__bytes_read.sum + dram__bytes_write.sum of one integration launch from
 # an ncu capture of the current kernel (bytes per launch), keyed by workload;
 # None while no capture of the current kernel exists.  batched: 2^18 cells
-# captured (268,743,424 B), scaled by cells to the 2^20-cell launch (the
+# captured (280,948,224 B), scaled by cells to the 2^20-cell launch (the
 # traffic per cell does not depend on the launch size); flame1d: the 8th split
 # step's integration launch, whose 0.5 MB state stays in L2 (writes are not
 # all flushed by the kernel's end).
-TRAFFIC = {"batched": (138423296 + 130320128) * 4, "flame1d": 1398528 + 125696}
+TRAFFIC = {"batched": (140082176 + 140866048) * 4, "flame1d": 1558272 + 560384}
 
 
 def _env_int(k, d):

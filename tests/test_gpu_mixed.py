@@ -347,3 +347,31 @@ def test_batched_mechanism_levels_vs_fp64_oracle(rk, precision):
           f"max |dT| {dT.max():.3e} K")
     assert np.all(dY <= 1e-8 + 1e-6 * np.abs(ref[:, :ns]))
     assert dT.max() <= 1e-6
+
+
+@pytest.mark.parametrize("lanes", [8, 16])
+def test_level_6_with_fewer_lanes_per_cell(rk, lanes):
+    """Precision 6 with 8 and 16 lanes per cell (the FP32 J v's reductions
+    and cache copies over smaller groups) on the small workload, replayed
+    through the FP64 oracle at the library's bar."""
+    from oracle import rok4e as orok
+    from oracle.kinetics import Kinetics
+    from synth.fields import initial_state
+
+    w, mech = _mech("small")
+    U = initial_state(w)[::8]
+    m = rk.mech_load(mech)
+    Y = torch.tensor(U, device="cuda")
+    n = U.shape[0]
+    st = torch.zeros(n, 4, dtype=torch.int32, device="cuda")
+    tr = torch.zeros(n, 8192, dtype=torch.float64, device="cuda")
+    rk.rok4e_integrate(m, Y, w.dt, w.rtol, w.atol, 4, stats=st,
+                       opts=rk.Opts(precision=6, lanes_per_cell=lanes, trace=tr))
+    torch.cuda.synchronize()
+    out, st, tr = Y.cpu().numpy(), st.cpu().numpy(), tr.cpu().numpy()
+    assert np.all(st[:, 3] == 0)
+    ref, _ = orok.integrate_cells(Kinetics(mech), U, P, w.dt, w.rtol, w.atol, 4,
+                                  replay=[[(abs(h), h > 0) for h in r if h != 0.0] for r in tr])
+    ns = mech.n_species
+    assert np.all(np.abs(out[:, :ns] - ref[:, :ns]) <= 1e-8 + 1e-6 * np.abs(ref[:, :ns]))
+    assert np.max(np.abs(out[:, ns] - ref[:, ns])) <= 1e-6
