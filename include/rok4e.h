@@ -155,8 +155,8 @@ int rk_chem_jvp_cv(const rk_mech* mech, const double* Y, const double* V, const 
 /* Mixed-precision source term (the right-hand side of precision levels 1 and
  * 2): as rk_chem_rhs, with w = nu^T q gathered on the FP32 pipe in
  * double-float (FP32 pairs, ~44-bit significands; the small-integer net
- * coefficients are exact in FP32) and the exponentials' polynomial tails in
- * FP32 (~1e-12 relative), while the rate coefficients, Gibbs factors, 1/Kc, the
+ * coefficients are exact in FP32) and the rate-coefficient exponentials'
+ * polynomial tails in FP32 (~1e-13 relative), while the Gibbs factors, 1/Kc, the
  * rates of progress q = m (k prod C - k/Kc prod C) and the assembly of f stay
  * FP64.  Needs |q_j| below the FP32 range (3.4e38 mol/m^3/s); rates below
  * 1.2e-38 drop out of w. */
@@ -187,34 +187,38 @@ typedef struct rk_opts {
   double h0;              /* first step when h_cell is NULL or holds <= 0; <= 0: dt */
   double fixed_h;         /* > 0: fixed steps of this size, no error control */
   int32_t trace_cap;      /* attempts recorded per cell into trace (0: none) */
-  int32_t precision;      /* 0: FP64 throughout (default).  1: mixed -- w = nu^T q (in
-                             the right-hand side and the Jacobian-vector product)
-                             gathered in double-float on the FP32 pipe, the first
-                             Gram-Schmidt pass of Arnoldi with FP32 inner products
-                             (the reorthogonalisation pass and the norms FP64),
-                             the exponentials' polynomial tails in FP32; rate
-                             coefficients, Gibbs factors, 1/Kc, rates of progress,
-                             stage solves, error norm and state update in FP64.
+  int32_t precision;      /* 0: FP64 throughout (default).  Every level keeps in
+                             FP64 the equilibrium-constant exponentials, 1/Kc,
+                             the rates of progress (forward minus reverse), the
+                             stage solves, the error norm and the state update,
+                             and meets the library's bar against the FP64
+                             oracle (1e-8 + 1e-6 |Y|, 1e-6 K).
+                             1: w = nu^T q (in the right-hand side and the
+                             Jacobian-vector product) gathered in double-float
+                             on the FP32 pipe, the first Gram-Schmidt pass of
+                             Arnoldi with FP32 inner products (the
+                             reorthogonalisation pass and the norms FP64), the
+                             rate-coefficient exponentials' polynomial tails in
+                             FP32 (~1e-13 relative).
                              2: as 1 with the Jacobian-vector products in FP32
-                             (~1e-5 relative: does not keep the 1e-6 K bar
-                             against the FP64 oracle).  3: FP64
-                             Arnoldi, stages, norm and update; the exponentials'
-                             polynomial tails in FP32 (~1e-12 relative); the
-                             Jacobian-vector product's reaction-level core
-                             (d(C_a C_b), dq, nu^T dq) in double-float (FP32
-                             pairs, ~44-bit significands) on the FP32 pipe.
+                             (~1e-5 relative; the Krylov basis tolerates it).
+                             3: FP64 Arnoldi; the rate-coefficient exponentials'
+                             polynomial tails in FP32; the Jacobian-vector
+                             product's reaction-level core (d(C_a C_b), dq,
+                             nu^T dq) in double-float on the FP32 pipe.
                              4: FP64 throughout except w = nu^T q (in the
                              right-hand side and the Jacobian-vector product),
                              which is formed on the tensor cores as in
                              rk_chem_rhs_tc; needs lanes_per_cell 0 or 32.
-                             5: FP64 throughout except the exponentials'
-                             polynomial tails (FP32, ~1e-13 relative): the
-                             FP64 kernel's layout and occupancy, three FP64
-                             instructions fewer per exponential.
+                             5: FP64 throughout except the rate-coefficient
+                             exponentials' polynomial tails (FP32): the FP64
+                             kernel's layout and occupancy, three FP64
+                             instructions fewer per reaction and evaluation.
                              6: as 5 with the Jacobian-vector products in FP32
-                             arithmetic on the FP64 caches (no FP32 copies,
-                             so the FP64 kernel's occupancy; ~1e-6 relative
-                             J v, which the Krylov basis tolerates) */
+                             arithmetic on FP32 copies of their caches, which
+                             the caching right-hand side writes into the FP64
+                             caches' own storage (the FP64 kernel's occupancy;
+                             ~1e-6 relative J v) */
   double* trace;          /* device [ncell x trace_cap]: +h accepted, -h rejected, 0 unused */
   void* ev_begin;         /* optional cudaEvent_t recorded on the stream right before the */
   void* ev_end;           /* integration kernel and right after it (timing hook), or NULL;

@@ -834,9 +834,9 @@ __device__ __forceinline__ void rhs_eval(const MechView& m, const SlotPtrs& s, c
       // E = e^{g/RT} (RT/p_ref), Einv = 1/E: 1/Kc of a reaction is the product of
       // E over its products and Einv over its reactants (the pressure factor
       // (RT/p_ref)^dnu included); CE = C E, so k/Kc prod C^nu'' is three products
+      // (in FP64 at every precision level: the equilibrium constants come from these)
       const double a = s.gRT[k] + lnRTp;
-      if (MIXED || cs->prec == 3 || cs->prec >= 5) exp_pm_mixed(a, m.etab, &s.E[k], &s.Einv[k]);
-      else exp_pm(a, m.etab, &s.E[k], &s.Einv[k]);
+      exp_pm(a, m.etab, &s.E[k], &s.Einv[k]);
       s.CE[k] = __dmul_rn(Ck, s.E[k]);
     }
     if (coop_tb) {

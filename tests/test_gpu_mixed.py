@@ -3,12 +3,13 @@
 Precision level 1 gathers w = nu^T q (in the right-hand side and the
 Jacobian-vector product) in double-float on the FP32 pipe, takes the first
 Gram-Schmidt pass of Arnoldi with FP32 inner products and the exponentials'
-polynomial tails in FP32; level 2 also runs the Jacobian-vector products in
+polynomial tails of the rate coefficients in FP32 (the equilibrium constants'
+exponentials stay FP64 at every level); level 2 also runs the Jacobian-vector products in
 FP32; level 3 keeps the Krylov path in FP64 with a double-float J v core;
 level 4 keeps everything FP64 but forms w = nu^T q on the tensor cores from
 exact 8-bit digit slices of q; level 5 keeps everything FP64 but the
-exponentials' polynomial tails; level 6 adds an FP32 J v computed on the FP64
-caches.
+rate-coefficient exponentials' polynomial tails; level 6 adds an FP32 J v on
+FP32 copies of its caches.
 The bar is the library's, for every level: |dY| <= 1e-8 + 1e-6 |Y| and
 |dT| <= 1e-6 K against the FP64 oracle replaying the GPU run's own step
 sequence.
