@@ -151,7 +151,7 @@ __device__ __forceinline__ double gsum(const Grp<G>& g, double a) {
 // tangents are needed (the Jacobian-vector products of the Arnoldi process and
 // their reverse), double where only values are (f at u_n and at the stage
 // arguments, and their reverse), which halves the arithmetic of those passes.
-// The tape keeps Duals either way (tangent 0 after a value pass).
+// The tape keeps Duals either way.
 template <class Sc>
 __device__ __forceinline__ Sc sv(double v);
 template <>
@@ -172,8 +172,10 @@ template <>
 __device__ __forceinline__ Dual rd<Dual>(const Dual& x) {
   return x;
 }
-__device__ __forceinline__ Dual wr(double a) { return Dual{a, 0.0}; }
-__device__ __forceinline__ Dual wr(Dual a) { return a; }
+// A value pass writes the tape's values only (its reverse reads nothing else,
+// and every dual pass writes both parts before it reads them)
+__device__ __forceinline__ void put(Dual& d, double a) { d.v = a; }
+__device__ __forceinline__ void put(Dual& d, Dual a) { d = a; }
 __device__ __forceinline__ double val(double a) { return a; }
 __device__ __forceinline__ double val(Dual a) { return a.v; }
 __device__ __forceinline__ double dexp(double a, const double* tab) { return exp_fast(a, tab); }
@@ -203,16 +205,16 @@ __device__ void adj_rhs_fwd(const MechView& m, const AdjFrame& F, double p) {
     const Sc hrt = hp * T + a1 + c[9 * ns + k] * invT;
     const Sc sp = ((c[12 * ns + k] * T + c[11 * ns + k]) * T + c[10 * ns + k]) * T + a2;
     const Sc sr = a1 * lnT + sp * T + c[13 * ns + k];
-    F.cp[k] = wr(cp);
-    F.h[k] = wr(hrt);
-    F.g[k] = wr(hrt - sr);
-    F.dcp[k] = wr(((c[16 * ns + k] * T + c[15 * ns + k]) * T + c[14 * ns + k]) * T + a2);
+    put(F.cp[k], cp);
+    put(F.h[k], hrt);
+    put(F.g[k], hrt - sr);
+    put(F.dcp[k], ((c[16 * ns + k] * T + c[15 * ns + k]) * T + c[14 * ns + k]) * T + a2);
     S += rd<Sc>(F.ud[k]) * m.invW[k];
   }
   S = gsum(g, S);
   const Sc rho = p / (R_GAS * T * S);
   const Sc irho = 1.0 / rho;
-  for (int k = L; k < ns; k += G) F.C[k] = wr(rho * rd<Sc>(F.ud[k]) * m.invW[k]);
+  for (int k = L; k < ns; k += G) put(F.C[k], rho * rd<Sc>(F.ud[k]) * m.invW[k]);
   if (L == ns % G) {  // the empty reaction slot: C = 1, h = g = 0
     F.h[ns] = Dual{0.0, 0.0};
     F.g[ns] = Dual{0.0, 0.0};
@@ -222,7 +224,7 @@ __device__ void adj_rhs_fwd(const MechView& m, const AdjFrame& F, double p) {
   for (int t = L; t < m.ntb; t += G) {
     Sc Mc = sv<Sc>(0.0);
     for (int k = 0; k < ns; ++k) Mc += m.eff[(size_t)t * ns + k] * rd<Sc>(F.C[k]);
-    F.Ms[t] = wr(Mc);
+    put(F.Ms[t], Mc);
   }
   g.sync();
   const Sc lnRTp = dlog(R_GAS * T / P_REF);
@@ -269,38 +271,38 @@ __device__ void adj_rhs_fwd(const MechView& m, const AdjFrame& F, double p) {
       const Sc dFc =
           -(1.0 - a) * fo[4] * e3 - a * fo[5] * e1 + (fo[6] > 0.0 ? fo[6] * invT * invT * e2 : sv<Sc>(0.0));
       const Sc gg = 1.0 / onePr + dlF_dL;
-      F.dlnk[slot] = wr(dlnkinf + gg * (dlnk0 - dlnkinf) + dlF_dlFc * dFc / Fc);
-      F.dkdM[slot] = wr(k0 * Fb / onePr * gg);
-      F.omg[slot] = wr(1.0 - gg);
+      put(F.dlnk[slot], dlnkinf + gg * (dlnk0 - dlnkinf) + dlF_dlFc * dFc / Fc);
+      put(F.dkdM[slot], k0 * Fb / onePr * gg);
+      put(F.omg[slot], 1.0 - gg);
       k = k * Pr / onePr * Fb;
     }
     const Sc Pf = rd<Sc>(F.C[ra]) * rd<Sc>(F.C[rb]);
     const Sc Pb = rd<Sc>(F.C[pa]) * rd<Sc>(F.C[pb]);
-    F.k[j] = wr(k);
-    F.rfac[j] = wr(rfac);
-    F.q[j] = wr(mfac * (k * Pf - k * rfac * Pb));
+    put(F.k[j], k);
+    put(F.rfac[j], rfac);
+    put(F.q[j], mfac * (k * Pf - k * rfac * Pb));
   }
   g.sync();
   Sc Sh = sv<Sc>(0.0), cb = sv<Sc>(0.0);
   for (int k = L; k < ns; k += G) {
     Sc om = sv<Sc>(0.0);
     for (int e = m.csr_ptr[k]; e < m.csr_ptr[k + 1]; ++e) om += m.csr_nu[e] * rd<Sc>(F.q[m.csr_j[e]]);
-    F.om[k] = wr(om);
-    F.fd[k] = wr(m.W[k] * om * irho);
+    put(F.om[k], om);
+    put(F.fd[k], m.W[k] * om * irho);
     Sh += rd<Sc>(F.h[k]) * om;
     cb += rd<Sc>(F.ud[k]) * rd<Sc>(F.cp[k]) * m.invW[k];
   }
   Sh = gsum(g, Sh);
   cb = gsum(g, cb);
-  if (L == ns % G) F.fd[ns] = wr(-1.0 * T * Sh / (rho * cb));
+  if (L == ns % G) put(F.fd[ns], -1.0 * T * Sh / (rho * cb));
   if (L == 0) {
-    F.sc[SC_T] = wr(T);
-    F.sc[SC_INVT] = wr(invT);
-    F.sc[SC_S] = wr(S);
-    F.sc[SC_RHO] = wr(rho);
-    F.sc[SC_CB] = wr(cb);
-    F.sc[SC_SH] = wr(Sh);
-    F.sc[SC_LNRTP] = wr(lnRTp);
+    put(F.sc[SC_T], T);
+    put(F.sc[SC_INVT], invT);
+    put(F.sc[SC_S], S);
+    put(F.sc[SC_RHO], rho);
+    put(F.sc[SC_CB], cb);
+    put(F.sc[SC_SH], Sh);
+    put(F.sc[SC_LNRTP], lnRTp);
   }
   g.sync();
 }
@@ -328,7 +330,7 @@ __device__ void adj_rhs_rev(const MechView& m, const AdjFrame& F, bool tangent) 
   for (int k = L; k < ns; k += G) {
     const Sc fb = rd<Sc>(F.fbd[k]);
     const Sc wfb = m.W[k] * irho * fb;
-    F.ombar[k] = wr(wfb + rd<Sc>(F.h[k]) * Shbar);
+    put(F.ombar[k], wfb + rd<Sc>(F.h[k]) * Shbar);
     rhobar_l -= wfb * rd<Sc>(F.om[k]) * irho;
   }
   if (L == ns % G) F.ombar[ns] = Dual{0.0, 0.0};
@@ -351,20 +353,20 @@ __device__ void adj_rhs_rev(const MechView& m, const AdjFrame& F, bool tangent) 
     const Sc kr = k * rfac;
     const Sc qm = qbar * mfac;
     const Sc kbar = qm * (Pf - rfac * Pb);
-    if (kind == 1) F.Mbar[slot] = wr(qbar * (k * Pf - kr * Pb));  // slots are one per reaction
-    F.q[j] = wr(qm * k);           // d/d(prod C^nu')
-    F.Pbb[j] = wr(-1.0 * qm * kr);  // d/d(prod C^nu'')
+    if (kind == 1) put(F.Mbar[slot], qbar * (k * Pf - kr * Pb));  // slots are one per reaction
+    put(F.q[j], qm * k);           // d/d(prod C^nu')
+    put(F.Pbb[j], -1.0 * qm * kr);  // d/d(prod C^nu'')
     Sc drf = sv<Sc>(0.0);
     if (rev) {
       drf = rfac * (-1.0 * qm * k * Pb);  // rfac * rfac_bar
       Tbar_l += (double)dnu * drf * invT;
     }
-    F.drf[j] = wr(drf);
+    put(F.drf[j], drf);
     const Sc kk = k * kbar;
     Sc th;
     if (kind == 2) {
       Tbar_l += kk * rd<Sc>(F.dlnk[slot]);
-      F.Mbar[slot] = wr(kbar * rd<Sc>(F.dkdM[slot]));
+      put(F.Mbar[slot], kbar * rd<Sc>(F.dkdM[slot]));
       th = kk * rd<Sc>(F.omg[slot]);
     } else {
       Tbar_l += kk * ((m.bexp[j] + m.EaR[j] * invT) * invT);
@@ -383,8 +385,8 @@ __device__ void adj_rhs_rev(const MechView& m, const AdjFrame& F, bool tangent) 
       gbar = role < 2 ? gbar - rd<Sc>(F.drf[j]) : gbar + rd<Sc>(F.drf[j]);
     }
     for (int t = 0; t < m.ntb; ++t) cbar += m.eff[(size_t)t * ns + k] * rd<Sc>(F.Mbar[t]);
-    F.Cbar[k] = wr(cbar);
-    F.gbar[k] = wr(gbar);
+    put(F.Cbar[k], cbar);
+    put(F.gbar[k], gbar);
     rhobar_l += rd<Sc>(F.ud[k]) * m.invW[k] * cbar;
   }
   const Sc rhobar = rhobar0 + gsum(g, rhobar_l);
@@ -394,13 +396,13 @@ __device__ void adj_rhs_rev(const MechView& m, const AdjFrame& F, bool tangent) 
   for (int k = L; k < ns; k += G) {
     const Sc cpk = rd<Sc>(F.cp[k]), hk = rd<Sc>(F.h[k]);
     const Sc Yb = cpk * m.invW[k] * cbbar + rho * m.invW[k] * rd<Sc>(F.Cbar[k]) + Sbar * m.invW[k];
-    F.ubd[k] = wr(Yb);
+    put(F.ubd[k], Yb);
     const Sc cpbar = rd<Sc>(F.ud[k]) * m.invW[k] * cbbar;
     const Sc hbar = rd<Sc>(F.om[k]) * Shbar;
     T2_l += cpbar * rd<Sc>(F.dcp[k]) + hbar * (cpk - hk) * invT - rd<Sc>(F.gbar[k]) * hk * invT;
   }
   Tbar += gsum(g, T2_l);
-  if (L == ns % G) F.ubd[ns] = wr(Tbar);
+  if (L == ns % G) put(F.ubd[ns], Tbar);
   g.sync();
 }
 
