@@ -1046,7 +1046,8 @@ def run_plain(args):
         for _ in range(args.plain_steps):
             Y = U.clone()
             rk.rok4e_integrate(m, Y, w.dt, w.rtol, w.atol, args.krylov or w.krylov_dim, h_cell=hc,
-                               opts=rk.Opts(cells_per_block=args.cells_per_block, lanes_per_cell=args.lanes))
+                               opts=rk.Opts(cells_per_block=args.cells_per_block, lanes_per_cell=args.lanes,
+                                            precision=PREC[args.precision]))
         torch.cuda.synchronize()
         print(json.dumps({"plain_steps": args.plain_steps, "cells": int(U.shape[0]), "T_max": float(Y[:, -1].max())}))
         return 0

@@ -1482,8 +1482,8 @@ __device__ __forceinline__ float small_int_to_float(double x) {
 // where k Pf and k/Kc Pb nearly cancel) is what the Krylov basis sees; the
 // stages, the error estimate and the state update stay FP64.
 template <int G>
-__device__ __noinline__ void jvp_eval_f32x(const MechView& m, const SlotPtrs& s, const double* uu,
-                                           const CellScalars& cs, const double* v, double* out) {
+__device__ __forceinline__ void jvp_eval_f32x(const MechView& m, const SlotPtrs& s, const double* uu,
+                                              const CellScalars& cs, const double* v, double* out) {
   const Grp<G> g;
   const int ns = m.ns;
   float* fdC = reinterpret_cast<float*>(s.dC);
