@@ -131,12 +131,14 @@ int rk_chem_rhs(const rk_mech* mech, const double* Y, const double* src, double 
  * derivative of rk_chem_rhs); mode 1: forward difference
  * (f(u + d v) - f(u)) / d with d = sqrt(eps) (1 + ||u||_2) / ||v||_2, as in
  * the matrix-free products of Sec. 4.3; mode 2: the analytic product
- * evaluated in FP32 (the mixed-precision integrator's J v); mode 3: the
- * analytic product with its reaction-level core in double-float (precision
- * level 3); mode 4: the analytic product with nu^T dq formed on the tensor
- * cores as in rk_chem_rhs_tc (precision level 4); mode 5: the analytic
- * product in FP32 arithmetic on the FP64 caches (precision level 6).  All
- * arrays device [ncell x N]. */
+ * evaluated in FP32 (precision level 2's J v); mode 3: the analytic product
+ * with its reaction-level core in double-float (precision level 3); mode 4:
+ * the analytic product with nu^T dq formed on the tensor cores as in
+ * rk_chem_rhs_tc (precision level 4); mode 5: the analytic product in FP32
+ * arithmetic on the FP32 copies of its caches that the caching right-hand
+ * side writes at precision level 6 (that level's J v).  Each mode computes
+ * exactly what the integrator's J v at that level computes.  All arrays
+ * device [ncell x N]; RK_E_INVALID_ARGUMENT for a mode outside 0..5. */
 int rk_chem_jvp(const rk_mech* mech, const double* Y, const double* V, double p, double* JV,
                 int64_t ncell, int32_t mode, void* stream);
 
@@ -500,10 +502,13 @@ int rk_probe_throughput(int32_t kind, double* ops_per_s);
  * against the CUDA math library): which 0: y = exp(x); 1: exp(x) and 2:
  * exp(-x) from the shared-reduction pair; 3, 4, 5: the same three in the
  * mixed-precision form (polynomial's small term in FP32, relative error
- * ~1e-12) used by precision levels 1 to 3; 6: y = ln x; 7: y = 1/x.
- * Methods: Tang, ACM TOMS 15(2), 1989 (exp) and 16(4), 1990 (ln), each with
- * a 128-entry table; 1/x by two Newton steps from an FP32 estimate where x
- * and 1/x are FP32-normal, a division elsewhere.  The paper itself delegates
+ * ~1e-13; 3 is the rate-coefficient exponential of precision levels 1, 2, 3,
+ * 5 and 6, while the pair 4, 5 is no longer used by any level, whose
+ * equilibrium-constant exponentials stay FP64); 6: y = ln x; 7: y = 1/x.
+ * Methods: Tang, ACM TOMS 15(2), 1989 (exp: a 256-entry table of 2^(j/256)
+ * and a degree-4 polynomial) and 16(4), 1990 (ln: a 128-entry table and a
+ * degree-7 polynomial); 1/x by two Newton steps from an FP32 estimate where
+ * x and 1/x are FP32-normal, a division elsewhere.  The paper itself delegates
  * kinetics to Cantera and prints none of these.  x, y: n doubles in device
  * memory, distinct arrays; asynchronous on `stream`; RK_E_INVALID_ARGUMENT
  * for n < 0 or which outside 0..7. */
