@@ -469,10 +469,11 @@ int rk_rok4e_fixed_steps(const rk_mech* mech, double* Y, int64_t ncell, double p
  * including the dependence of the Arnoldi basis on the state and on ln A
  * (second derivatives of the source term).  The paper has no adjoint; this is
  * the library's sensitivity extension of its integrator.  Workspace:
- * rk_rok4e_adjoint_workspace_size (about (86 + 14 M) N + (19 + 4 M) Nr
+ * rk_rok4e_adjoint_workspace_size (about (78 + 16 M) N + (19 + 4 M) Nr
  * doubles per cell for Krylov dimension M, one contiguous record per cell: the
- * tapes of every right-hand-side pass of a step are kept for its reverse sweep).  The sums over cells and within a cell have a
- * fixed order: repeated calls give the same bits. */
+ * tapes of every right-hand-side pass of a step are kept for its reverse
+ * sweep).  The sums over cells and within a cell have a fixed order: repeated
+ * calls give the same bits. */
 size_t rk_rok4e_adjoint_workspace_size(const rk_mech* mech, int64_t ncell, int32_t krylov_dim);
 int rk_rok4e_adjoint(const rk_mech* mech, const double* checkpoints, const double* ubar, int64_t ncell,
                      double p, double h, int32_t nsteps, int32_t krylov_dim, double* grad_lnA,
