@@ -137,8 +137,11 @@ class Opts:
         self.h0, self.fixed_h = h0, fixed_h
         self.trace = trace  # CUDA float64 tensor [ncell, cap] or None
         self.events = events  # (begin, end) torch.cuda.Event pair around the integration kernel
-        # 0 FP64, 1 mixed (FP32 nu^T q and inner products), 2 + FP32 J v,
-        # 3 FP64 Krylov path with a double-float J v core and FP32 exp tails
+        # rk_opts.precision: 0 FP64; 1 double-float nu^T q, FP32 first
+        # Gram-Schmidt products and rate-coefficient exp tails; 2 as 1 with an
+        # FP32 J v; 3 FP64 Krylov path, double-float J v core, FP32 exp tails;
+        # 4 nu^T q on the tensor cores; 5 FP32 rate-coefficient exp tails only;
+        # 6 as 5 with an FP32 J v on FP32 copies of its caches
         self.precision = precision
         self.queue_order, self.blocks_per_sm = queue_order, blocks_per_sm
         self.rho_cell = rho_cell  # CUDA float64 [ncell]: constant-volume cells of these densities
