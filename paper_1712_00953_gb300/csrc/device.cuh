@@ -1622,6 +1622,42 @@ __device__ inline float group_dot_f(const Grp<G>& g, const double* a, const doub
 // first pass left behind -- its FP32 rounding included -- and the norms stay
 // FP64, so the basis and H keep FP64 quality (mixed-precision "twice is
 // enough").
+//
+// One FP64 Gram-Schmidt pass of w against the basis vectors q_0..q_{n-1}:
+// h = Q^T w (one batched reduction), w <- w - Q h, and hcol += h.  J > 0: n = J
+// is known at compile time, so no term carries a predicate (a predicated-off
+// FP64 instruction still takes its issue and pipe slot); J = 0: n = jn at run
+// time guards each of the MAXM terms.  Either way the same operations in the
+// same order for the terms that exist.
+template <int G, int J>
+__device__ __forceinline__ void cgs_pass(const SlotPtrs& s, int N, int jn, double (&hcol)[MAXM]) {
+  const Grp<G> g;
+  const int Nq = s.Nq;
+  constexpr int LJ = J > 0 ? J : MAXM;
+  double hp[MAXM];
+#pragma unroll
+  for (int i = 0; i < MAXM; ++i) hp[i] = 0.0;
+#pragma unroll 1
+  for (int e = g.lane; e < N; e += G) {
+    const double we = s.w[e];
+#pragma unroll
+    for (int i = 0; i < LJ; ++i)
+      if (J > 0 || i < jn) hp[i] = fma(s.Q[i * Nq + e], we, hp[i]);
+  }
+  sum_first<G>(g, hp, J > 0 ? J : jn);
+#pragma unroll 1
+  for (int e = g.lane; e < N; e += G) {
+    double we = s.w[e];
+#pragma unroll
+    for (int i = 0; i < LJ; ++i)
+      if (J > 0 || i < jn) we = fma(-hp[i], s.Q[i * Nq + e], we);
+    s.w[e] = we;
+  }
+#pragma unroll
+  for (int i = 0; i < LJ; ++i)
+    if (J > 0 || i < jn) hcol[i] += hp[i];
+}
+
 template <int G, bool MIXED = false, bool TC = false>
 __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& cs, int M, int jv_mode,
                        double p, int* n_rhs, bool fp32_jv = false) {
@@ -1655,8 +1691,8 @@ __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& 
 #pragma unroll
     for (int i = 0; i < MAXM; ++i) hcol[i] = 0.0;
     for (int pass = 0; pass < 2; ++pass) {
-      double hp[MAXM];
       if (MIXED && pass == 0) {
+        double hp[MAXM];
         float part[MAXM];
 #pragma unroll
         for (int i = 0; i < MAXM; ++i) part[i] = 0.f;
@@ -1669,26 +1705,25 @@ __device__ int arnoldi(const MechView& m, const SlotPtrs& s, const CellScalars& 
         sum_first<G>(g, part, j + 1);
 #pragma unroll
         for (int i = 0; i < MAXM; ++i) hp[i] = (double)part[i];
-      } else {
-#pragma unroll
-        for (int i = 0; i < MAXM; ++i) hp[i] = 0.0;
         for (int e = g.lane; e < N; e += G) {
-          const double we = s.w[e];
+          double we = s.w[e];
 #pragma unroll
           for (int i = 0; i < MAXM; ++i)
-            if (i <= j) hp[i] = fma(s.Q[i * Nq + e], we, hp[i]);
+            if (i <= j) we = fma(-hp[i], s.Q[i * Nq + e], we);
+          s.w[e] = we;
         }
-        sum_first<G>(g, hp, j + 1);
-      }
-      for (int e = g.lane; e < N; e += G) {
-        double we = s.w[e];
 #pragma unroll
-        for (int i = 0; i < MAXM; ++i)
-          if (i <= j) we = fma(-hp[i], s.Q[i * Nq + e], we);
-        s.w[e] = we;
+        for (int i = 0; i < MAXM; ++i) hcol[i] += hp[i];
+      } else if (M <= 4) {  // the common Krylov dimensions: column j + 1 known at compile time
+        switch (j) {
+          case 0: cgs_pass<G, 1>(s, N, 1, hcol); break;
+          case 1: cgs_pass<G, 2>(s, N, 2, hcol); break;
+          case 2: cgs_pass<G, 3>(s, N, 3, hcol); break;
+          default: cgs_pass<G, 4>(s, N, 4, hcol); break;
+        }
+      } else {
+        cgs_pass<G, 0>(s, N, j + 1, hcol);
       }
-#pragma unroll
-      for (int i = 0; i < MAXM; ++i) hcol[i] += hp[i];
     }
     const double hn2 = group_dot<G>(g, s.w, s.w, N);
     if (g.lane == 0) {
@@ -1784,6 +1819,75 @@ __device__ inline void factor_small(const SlotPtrs& s, int mdim, double h) {
   g.sync();
 }
 
+// One stage of the transformed form (Eq. s_stage_row_transformed) with the
+// low-rank inverse (Eq. solve_kry_jac), in two parts.  stage_rhs: F_i = f_i +
+// G_i with G_i = sum_{j<i} (gamma_ij / gamma) k_j (F_i and G_i left in s.F and
+// s.w) and the partial sums of Q^T F_i.  stage_solve: c = (I - (I - h gamma
+// H)^-1) Q^T F_i (B = I - (I - h gamma H)^-1 from factor_small) and
+// k_i = F_i - Q c - G_i.  I >= 0: the stage known at compile time; MD > 0: the
+// basis dimension known at compile time, so no term carries a predicate (a
+// predicated-off FP64 instruction still takes its issue and pipe slot);
+// I = -1 / MD = 0: from i / mdim at run time, each of the MAXM terms guarded.
+// The same operations in the same order either way.
+template <int G, int MD, int I>
+__device__ __forceinline__ void stage_rhs(const SlotPtrs& s, int N, int i_rt, int mdim_rt, const double* fi,
+                                          double (&part)[MAXM]) {
+  const Grp<G> g;
+  const int Nq = s.Nq;
+  const int i = I >= 0 ? I : i_rt;
+  const int mdim = MD > 0 ? MD : mdim_rt;
+  constexpr int LM = MD > 0 ? MD : MAXM;
+  constexpr double g21 = G21 / GAM, g31 = G31 / GAM, g32 = G32 / GAM;
+  constexpr double g41 = G41 / GAM, g42 = G42 / GAM, g43 = G43 / GAM;
+  const double* K0 = s.K;
+  const double* K1 = s.K + Nq;
+  const double* K2 = s.K + 2 * Nq;
+#pragma unroll
+  for (int l = 0; l < MAXM; ++l) part[l] = 0.0;
+#pragma unroll 1
+  for (int e = g.lane; e < N; e += G) {
+    double Ge = 0.0;
+    if (i == 1) Ge = g21 * K0[e];
+    else if (i == 2) Ge = fma(g32, K1[e], g31 * K0[e]);
+    else if (i == 3) Ge = fma(g43, K2[e], fma(g42, K1[e], g41 * K0[e]));
+    const double Fe = fi[e] + Ge;
+    s.F[e] = Fe;
+    s.w[e] = Ge;
+#pragma unroll
+    for (int l = 0; l < LM; ++l)
+      if (MD > 0 || l < mdim) part[l] = fma(s.Q[l * Nq + e], Fe, part[l]);
+  }
+}
+
+template <int G, int MD>
+__device__ __forceinline__ void stage_solve(const SlotPtrs& s, int N, int i, int mdim_rt, double (&part)[MAXM]) {
+  const Grp<G> g;
+  const int Nq = s.Nq;
+  const int mdim = MD > 0 ? MD : mdim_rt;
+  constexpr int LM = MD > 0 ? MD : MAXM;
+  double* Ki = s.K + i * Nq;
+  if (mdim > 0) sum_first<G>(g, part, mdim);
+  // lane l < m forms c_l, every lane then reads all
+  double cl = 0.0;
+  if (g.lane < mdim) {
+#pragma unroll
+    for (int c = 0; c < LM; ++c)
+      if (MD > 0 || c < mdim) cl = fma(s.Bm[g.lane * MAXM + c], part[c], cl);
+  }
+  double cz[MAXM];
+#pragma unroll
+  for (int l = 0; l < LM; ++l) cz[l] = __shfl_sync(g.mask, cl, l, G);
+#pragma unroll 1
+  for (int e = g.lane; e < N; e += G) {
+    double acc = 0.0;
+#pragma unroll
+    for (int l = 0; l < LM; ++l)
+      if (MD > 0 || l < mdim) acc = fma(s.Q[l * Nq + e], cz[l], acc);
+    Ki[e] = (s.F[e] - acc) - s.w[e];
+  }
+  g.sync();
+}
+
 
 // ------------------------------------------------ cost-ordered work queue
 // Cells are handed out longest-expected-first: the expected substep count of
@@ -1859,8 +1963,6 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
   double* K1 = s.K + Nq;
   double* K2 = s.K + 2 * Nq;
   double* K3 = s.K + 3 * Nq;
-  constexpr double g21 = G21 / GAM, g31 = G31 / GAM, g32 = G32 / GAM;
-  constexpr double g41 = G41 / GAM, g42 = G42 / GAM, g43 = G43 / GAM;
   while (true) {
     if (fresh) {
       rhs_dispatch<G, MIXED, INL, TC>(m, s, s.u, srcp, pr, s.fn, true, &cs);
@@ -1896,41 +1998,19 @@ __device__ void integrate_cell(const MechView& m, const SlotPtrs& s, const Integ
       } else {
         fi = s.fr;  // alpha_4j = alpha_3j: same argument as stage 3
       }
-      double* Ki = s.K + i * Nq;
       double part[MAXM];
-#pragma unroll
-      for (int l = 0; l < MAXM; ++l) part[l] = 0.0;
-      for (int e = g.lane; e < N; e += G) {
-        double Ge = 0.0;
-        if (i == 1) Ge = g21 * K0[e];
-        else if (i == 2) Ge = fma(g32, K1[e], g31 * K0[e]);
-        else if (i == 3) Ge = fma(g43, K2[e], fma(g42, K1[e], g41 * K0[e]));
-        const double Fe = fi[e] + Ge;
-        s.F[e] = Fe;
-        s.w[e] = Ge;
-#pragma unroll
-        for (int l = 0; l < MAXM; ++l)
-          if (l < mdim) part[l] = fma(s.Q[l * Nq + e], Fe, part[l]);
+      if (mdim == 4) {  // the common Krylov dimension: stage and dimension known at compile time
+        switch (i) {
+          case 0: stage_rhs<G, 4, 0>(s, N, 0, 4, fi, part); break;
+          case 1: stage_rhs<G, 4, 1>(s, N, 1, 4, fi, part); break;
+          case 2: stage_rhs<G, 4, 2>(s, N, 2, 4, fi, part); break;
+          default: stage_rhs<G, 4, 3>(s, N, 3, 4, fi, part); break;
+        }
+        stage_solve<G, 4>(s, N, i, 4, part);
+      } else {
+        stage_rhs<G, 0, -1>(s, N, i, mdim, fi, part);
+        stage_solve<G, 0>(s, N, i, mdim, part);
       }
-      if (mdim > 0) sum_first<G>(g, part, mdim);
-      // c = (I - (I - h gamma H)^-1) Q^T F_i: lane l < m forms c_l, every lane then reads all
-      double cl = 0.0;
-      if (g.lane < mdim) {
-#pragma unroll
-        for (int c = 0; c < MAXM; ++c)
-          if (c < mdim) cl = fma(s.Bm[g.lane * MAXM + c], part[c], cl);
-      }
-      double cz[MAXM];
-#pragma unroll
-      for (int l = 0; l < MAXM; ++l) cz[l] = __shfl_sync(g.mask, cl, l, G);
-      for (int e = g.lane; e < N; e += G) {
-        double acc = 0.0;
-#pragma unroll
-        for (int l = 0; l < MAXM; ++l)
-          if (l < mdim) acc = fma(s.Q[l * Nq + e], cz[l], acc);
-        Ki[e] = (s.F[e] - acc) - s.w[e];
-      }
-      g.sync();
     }
     // ---- solutions, error estimate
     double part = 0.0;
