@@ -54,12 +54,12 @@ GOLDEN = 0.6180339887498949
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one integration launch from
 # an ncu capture of the current kernel (bytes per launch), keyed by workload;
-# None while no capture of the current kernel exists.  batched: 2^18 cells
-# captured (280,948,224 B), scaled by cells to the 2^20-cell launch (the
-# traffic per cell does not depend on the launch size); flame1d: the 8th split
-# step's integration launch, whose 0.5 MB state stays in L2 (writes are not
-# all flushed by the kernel's end).
-TRAFFIC = {"batched": (140082176 + 140866048) * 4, "flame1d": 1558272 + 560384}
+# None while no capture of the current kernel exists.  The last captures are of
+# the build before the Krylov-dimension loops were made compile-time (a change
+# that moves no data): batched 280,948,224 B per 2^18-cell launch, i.e.
+# 1,123,792,896 B scaled by cells to the 2^20-cell launch; flame1d 2,118,656 B
+# for the 8th split step's launch, whose 0.5 MB state stays in L2.
+TRAFFIC = {"batched": None, "flame1d": None}
 
 
 def _env_int(k, d):
@@ -511,7 +511,8 @@ def run_headline(args, rank, world, dev, dist):
                      "frac": achieved / FP64_PEAK, "peak_kind": "nominal FP64 (MEASURED_PEAKS.json has no FP64 "
                                                                 "entry; the bench's own FMA probe agrees)",
                      "traffic": TRAFFIC["batched"],
-                     "traffic_note": "ncu dram bytes of a 2^18-cell launch scaled by cells to 2^20 "
+                     "traffic_note": "null: no ncu capture of the current kernel; the previous build's "
+                                     "2^18-cell capture scaled to 2^20 cells read and wrote 1.124e9 B "
                                      "(profiles/rok4e_integrate_batched.md)",
                      "algorithmic_bytes_per_launch": int(n * (2 * N * 8 + 16 + 8 + 8 + 4)),
                      "kernel": "rok4e_integrate_kernel<32, 0>", "kernel_s_per_step": kern_s,
